@@ -1,0 +1,181 @@
+/*
+ * Oracle likelihood and interim prior.
+ *
+ *   log P(d | theta) = -1/2 sum_p (d_p - m_p(theta))^2 / b      Eq. likelihood-pixels
+ *   interim prior: log10 f ~ U(-1, 9), log10 s ~ U(-2, 1),
+ *                  dx, dy ~ N(0, 0.5), (e1, e2) density
+ *                  ~ (1-|e|^2)^2 exp(-|e|^2 / (2 * 0.3^2))      Eq. interim-prior
+ *                                                               and the (e1,e2)
+ *                                                               density after it
+ *
+ * The gradient follows the chain rule through the pixel sum:
+ *   d logL / d theta_i = sum_p r_p dm_p/dtheta_i,  r = (d - m)/b,
+ * and since m = IDFT(M), sum_p r_p dm_p/dtheta_i = (1/N^2) sum_k
+ * Re[dM_k/dtheta_i conj(R_k)] with R = DFT(r) (the adjoint of the inverse DFT).
+ *
+ * TEST INFRASTRUCTURE ONLY (see bs_oracle.h).
+ */
+#include "bs_oracle.h"
+
+#include <complex.h>
+#include <math.h>
+#include <stdlib.h>
+
+#define OR_PI 3.14159265358979323846
+#define OR_LN10 2.30258509299404568402
+
+void or_prior_default(or_prior *pr)
+{
+    pr->lf_lo = -1.0; pr->lf_hi = 9.0;
+    pr->ls_lo = -2.0; pr->ls_hi = 1.0;
+    pr->sigma_xy = 0.5;
+    pr->sigma_e = 0.3;
+}
+
+/* Normaliser of (1-|e|^2)^2 exp(-|e|^2/(2 alpha^2)) over the unit disk:
+ * Z = pi int_0^1 (1-t)^2 exp(-a t) dt, a = 1/(2 alpha^2)
+ *   = pi [1/a - 2/a^2 + 2 (1 - e^-a)/a^3]  (series in a for small a). */
+static double z_ba14_of_a(double a)
+{
+    if (a < 1.0) {
+        double s = 0.0, term = 1.0;          /* (-a)^n / n! */
+        for (int n = 0; n < 40; ++n) {
+            s += term * 2.0 / ((n + 1.0) * (n + 2.0) * (n + 3.0));
+            term *= -a / (n + 1.0);
+        }
+        return OR_PI * s;
+    }
+    return OR_PI * (1.0 / a - 2.0 / (a * a) + 2.0 * (1.0 - exp(-a)) / (a * a * a));
+}
+
+double or_log_z_ba14(double alpha)
+{
+    return log(z_ba14_of_a(1.0 / (2.0 * alpha * alpha)));
+}
+
+double or_log_prior(const or_prior *pr, const double theta[6], double grad[6])
+{
+    double lf = theta[0], ls = theta[1], e1 = theta[2], e2 = theta[3];
+    double dx = theta[4], dy = theta[5];
+    double E = e1 * e1 + e2 * e2;
+    if (!(lf > pr->lf_lo && lf < pr->lf_hi && ls > pr->ls_lo && ls < pr->ls_hi && E < 1.0))
+        return -INFINITY;
+    double sxy2 = pr->sigma_xy * pr->sigma_xy;
+    double se2 = pr->sigma_e * pr->sigma_e;
+    double lp = -log(pr->lf_hi - pr->lf_lo) - log(pr->ls_hi - pr->ls_lo)
+                - log(2.0 * OR_PI * sxy2) - 0.5 * (dx * dx + dy * dy) / sxy2
+                + 2.0 * log(1.0 - E) - 0.5 * E / se2 - or_log_z_ba14(pr->sigma_e);
+    if (grad) {
+        grad[0] = 0.0;
+        grad[1] = 0.0;
+        grad[2] = -4.0 * e1 / (1.0 - E) - e1 / se2;
+        grad[3] = -4.0 * e2 / (1.0 - E) - e2 / se2;
+        grad[4] = -dx / sxy2;
+        grad[5] = -dy / sxy2;
+    }
+    return lp;
+}
+
+void or_twiddles(int N, double complex *tab);
+
+static inline double complex tw(const double complex *tab, long m, int N)   /* exp(+2 pi i m / N) */
+{
+    long r = m % N;
+    if (r < 0) r += N;
+    return tab[r];
+}
+
+void or_idft_image(int N, const double *M_reim, double *img, int method);
+
+double or_loglike_t(int N, double p, const double *T, const double *data,
+                    const double *w, double sigma, const double theta[6],
+                    double grad[6])
+{
+    int c = (N - 1) / 2;
+    size_t NN = (size_t)N * N;
+    double *M = malloc(sizeof(double) * 2 * NN);
+    double *m = malloc(sizeof(double) * NN);
+    or_model_spectrum_t(N, p, T, theta, M);
+    or_idft_image(N, M, m, 0);
+
+    double b = sigma * sigma;
+    double chi2 = 0.0;
+    double *r = malloc(sizeof(double) * NN);
+    for (size_t j = 0; j < NN; ++j) {
+        double wj = w ? w[j] : 1.0;
+        double res = data[j] - m[j];
+        chi2 += wj * res * res;
+        r[j] = wj * res / b;
+    }
+    double logl = -0.5 * chi2 / b;
+
+    if (grad) {
+        /* R(u,v) = sum_{iy,ix} r exp(-2 pi i (u (ix-c) + v (iy-c)) / N), separable */
+        double complex *B = malloc(sizeof(double complex) * NN);   /* [iy][u+c] */
+        double complex *tab = malloc(sizeof(double complex) * (size_t)N);
+        or_twiddles(N, tab);
+        for (int iy = 0; iy < N; ++iy)
+            for (int u = -c; u <= c; ++u) {
+                double complex acc = 0;
+                for (int ix = 0; ix < N; ++ix) acc += r[(size_t)iy * N + ix] * tw(tab, -(long)u * (ix - c), N);
+                B[(size_t)iy * N + (u + c)] = acc;
+            }
+        double r0 = pow(10.0, theta[1]) / or_hlr_over_r0();
+        double e1 = theta[2], e2 = theta[3];
+        double E = e1 * e1 + e2 * e2;
+        double dk = 2.0 * OR_PI / (N * p);
+        double g[6] = {0, 0, 0, 0, 0, 0};
+        for (int v = -c; v <= c; ++v)
+            for (int u = -c; u <= c; ++u) {
+                double complex R = 0;
+                for (int iy = 0; iy < N; ++iy) R += B[(size_t)iy * N + (u + c)] * tw(tab, -(long)v * (iy - c), N);
+                size_t idx = (size_t)(v + c) * N + (u + c);
+                double complex Mk = M[2 * idx] + I * M[2 * idx + 1];
+                double kx = u * dk, ky = v * dk, k2 = kx * kx + ky * ky;
+                double A = (1.0 + E) * k2 + 2.0 * e1 * (kx * kx - ky * ky) + 4.0 * e2 * kx * ky;
+                double q = A / (1.0 - E);
+                double s = 1.0 + r0 * r0 * q;
+                double dq1 = (2.0 * e1 * k2 + 2.0 * (kx * kx - ky * ky)) / (1.0 - E)
+                             + 2.0 * e1 * A / ((1.0 - E) * (1.0 - E));
+                double dq2 = (2.0 * e2 * k2 + 4.0 * kx * ky) / (1.0 - E)
+                             + 2.0 * e2 * A / ((1.0 - E) * (1.0 - E));
+                double complex dM[6];
+                dM[0] = OR_LN10 * Mk;
+                dM[1] = -3.0 * OR_LN10 * (r0 * r0 * q / s) * Mk;
+                dM[2] = -1.5 * r0 * r0 * dq1 / s * Mk;
+                dM[3] = -1.5 * r0 * r0 * dq2 / s * Mk;
+                dM[4] = -I * p * kx * Mk;
+                dM[5] = -I * p * ky * Mk;
+                for (int i = 0; i < 6; ++i) g[i] += creal(dM[i] * conj(R));
+            }
+        for (int i = 0; i < 6; ++i) grad[i] = g[i] / (double)NN;
+        free(B);
+        free(tab);
+    }
+    free(M); free(m); free(r);
+    return logl;
+}
+
+double or_loglike(int N, double p, const or_psf *psf, const double *data,
+                  const double *w, double sigma, const double theta[6],
+                  double grad[6])
+{
+    double *T = malloc(sizeof(double) * (size_t)N * N);
+    or_transfer_table(N, p, psf, T);
+    double v = or_loglike_t(N, p, T, data, w, sigma, theta, grad);
+    free(T);
+    return v;
+}
+
+double or_logpost(int N, double p, const or_psf *psf, const double *data,
+                  const double *w, double sigma, const or_prior *pr,
+                  const double theta[6], double grad[6])
+{
+    double gp[6];
+    double lp = or_log_prior(pr, theta, grad ? gp : NULL);
+    if (!isfinite(lp)) return -INFINITY;
+    double ll = or_loglike(N, p, psf, data, w, sigma, theta, grad);
+    if (grad)
+        for (int i = 0; i < 6; ++i) grad[i] += gp[i];
+    return ll + lp;
+}

@@ -1,0 +1,129 @@
+"""Seeded synthetic inputs for the galaxy-fit and shear stages.
+
+This module only draws random numbers: the true parameters of each galaxy,
+pixel-noise fields and the random parts of the chain initialisation.  It holds
+none of the method's arithmetic (no rendering, no shear transform, no
+likelihood): callers turn the draws into images with a renderer of their own.
+Every draw comes from ``numpy.random.Generator(PCG64(seed))``.
+
+Workloads (stand-ins for the paper's 320k GalSim images of Sec. 2, which are
+not available): isolated exponential galaxies at 0.2 arcsec / pixel with
+  * half-light radius: ln hlr ~ N(ln 0.8, 0.3) (median 0.8 arcsec),
+  * intrinsic ellipticity: (e1, e2) i.i.d. N(0, 0.2) per component, redrawn
+    until |e| < 0.7,
+  * centroid offset: uniform within the central pixel, U(-0.5, 0.5)^2 px
+    (Sec. 2),
+  * S/N = sqrt(sum I^2 / b) (Sec. 2 footnote) drawn U(15, 50) (tiny / plain
+    batched) or log-uniform on [10, 100] (ragged),
+  * white noise sigma = 1 (b = 1, sky dominated, Sec. 2),
+  * constant shear g = (+-0.02, 0) (Sec. 3.4).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+SEED_DATA = 2604
+SEED_CHAINS = 22048
+SEED_ARRIVALS = 7
+
+PIXEL_SCALE = 0.2
+
+
+@dataclass
+class Truth:
+    """True (intrinsic) galaxy parameters; the shear is applied by the renderer."""
+    hlr: np.ndarray            # arcsec
+    e_int: np.ndarray          # [n, 2] intrinsic ellipticity
+    offset: np.ndarray         # [n, 2] pixels
+    snr: np.ndarray            # target S/N
+    side: np.ndarray           # stamp side per galaxy (odd)
+    psf_fwhm: np.ndarray       # arcsec, per galaxy
+    psf_kind: str              # "gaussian" or "moffat"
+    psf_beta: float = 3.0
+    g: tuple = (0.02, 0.0)
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def n(self):
+        return len(self.hlr)
+
+
+def _trunc_gauss_e(rng, n, sigma=0.2, rmax=0.7):
+    out = np.empty((n, 2))
+    filled = 0
+    while filled < n:
+        e = rng.normal(0.0, sigma, size=(2 * (n - filled) + 8, 2))
+        e = e[np.hypot(e[:, 0], e[:, 1]) < rmax]
+        take = min(len(e), n - filled)
+        out[filled:filled + take] = e[:take]
+        filled += take
+    return out
+
+
+def draw_plain(n, side, *, seed=SEED_DATA, snr_range=(15.0, 50.0), psf_fwhm=0.7,
+               g=(0.02, 0.0)):
+    """Fixed stamp size, one Gaussian PSF: the tiny (25 px, 10 galaxies) and the
+    plain batched (53 px, 10^4 galaxies) workloads."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    hlr = np.exp(rng.normal(np.log(0.8), 0.3, size=n))
+    e = _trunc_gauss_e(rng, n)
+    off = rng.uniform(-0.5, 0.5, size=(n, 2))
+    snr = rng.uniform(snr_range[0], snr_range[1], size=n)
+    return Truth(hlr=hlr, e_int=e, offset=off, snr=snr, side=np.full(n, side, dtype=np.int32),
+                 psf_fwhm=np.full(n, psf_fwhm), psf_kind="gaussian", g=tuple(g))
+
+
+def ragged_side(hlr, fwhm, pixel_scale=PIXEL_SCALE, lo=25, hi=101):
+    """Stamp side scaled with size: 2 ceil(4.43 hlr/p + 1.5 FWHM/p) + 1, clipped
+    to [lo, hi] (4.43 hlr encloses 99.5% of an exponential's flux)."""
+    half = np.ceil(4.43 * hlr / pixel_scale + 1.5 * fwhm / pixel_scale)
+    return np.clip(2 * half + 1, lo, hi).astype(np.int32)
+
+
+def draw_ragged(n, *, seed=SEED_DATA, g=(0.02, 0.0)):
+    """Uneven stamp sizes 25..101 px with per-galaxy Moffat(beta = 3) PSFs of
+    FWHM U(0.6, 0.9) arcsec and log-uniform S/N on [10, 100]."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    hlr = np.exp(rng.normal(np.log(0.8), 0.3, size=n))
+    e = _trunc_gauss_e(rng, n)
+    off = rng.uniform(-0.5, 0.5, size=(n, 2))
+    snr = np.exp(rng.uniform(np.log(10.0), np.log(100.0), size=n))
+    fwhm = rng.uniform(0.6, 0.9, size=n)
+    side = ragged_side(hlr, fwhm)
+    return Truth(hlr=hlr, e_int=e, offset=off, snr=snr, side=side, psf_fwhm=fwhm,
+                 psf_kind="moffat", psf_beta=3.0, g=tuple(g))
+
+
+def noise_fields(truth: Truth, sigma=1.0, *, seed=SEED_DATA + 1):
+    """One white-noise field per galaxy (list of [side, side] arrays).  The same
+    seed gives the same noise for the +g and -g datasets (Sec. 3.4)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return [rng.normal(0.0, sigma, size=(int(s), int(s))) for s in truth.side]
+
+
+def init_offsets(truth: Truth, n_chains, *, seed=SEED_CHAINS):
+    """Random parts of the chain initialisation of Eq. initialize:
+    log10 hlr offsets U(-0.015, 0.015) and ellipticity offsets U(-0.1, 0.1)
+    per component.  Returns [n, n_chains, 3] = (d ls, d e1, d e2)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    d_ls = rng.uniform(-0.015, 0.015, size=(truth.n, n_chains, 1))
+    d_e = rng.uniform(-0.1, 0.1, size=(truth.n, n_chains, 2))
+    return np.concatenate([d_ls, d_e], axis=-1)
+
+
+def initial_theta(stamp_sums, ls_true, e_true, offsets):
+    """Chain starting points of Eq. initialize from the data sums, the true
+    log10 hlr and the true (sheared) ellipticity: flux = sum of pixels, size and
+    shape in small boxes around the truth, centroid offset 0.  An ellipticity
+    start on or outside the unit circle is pulled back to |e| = 0.95."""
+    n, n_chains, _ = offsets.shape
+    th = np.zeros((n, n_chains, 6))
+    th[..., 0] = np.log10(np.maximum(np.asarray(stamp_sums, dtype=np.float64), 1.0))[:, None]
+    th[..., 1] = np.asarray(ls_true)[:, None] + offsets[..., 0]
+    e = np.asarray(e_true)[:, None, :] + offsets[..., 1:3]
+    r = np.hypot(e[..., 0], e[..., 1])
+    scale = np.where(r >= 0.95, 0.95 / np.maximum(r, 1e-300), 1.0)
+    th[..., 2:4] = e * scale[..., None]
+    return th

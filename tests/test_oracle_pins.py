@@ -1,0 +1,373 @@
+"""The oracle pinned to things other than itself: library routines (numpy's
+Philox and Gauss-Hermite, scipy's Bessel K, quadrature and root finding),
+closed forms, geometric identities, brute force, and the paper's printed
+constants (tests/golden/paper_constants.json).  CPU only."""
+import json
+import os
+
+import numpy as np
+import pytest
+import scipy.integrate as si
+import scipy.linalg as sl
+import scipy.optimize as so
+import scipy.special as sp
+
+import oracle as O
+from paper_2604_22048_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_constants.json")
+
+
+# ---------------------------------------------------------------- generator
+
+@pytest.mark.parametrize("ctr,key", [([1, 0, 0, 0], [0, 0]), ([5, 7, 0, 1], [11, 22]),
+                                     ([2 ** 40 + 3, 1, 2, 3], [2 ** 63 + 5, 12345]),
+                                     ([123, 1, 60, 0], [22048, 4 * 9999 + 3])])
+def test_philox_matches_numpy(ctr, key):
+    # numpy's Philox (4x64, 10 rounds) increments its counter before each block
+    bg = np.random.Philox(counter=np.array([ctr[0] - 1] + ctr[1:], dtype=np.uint64),
+                          key=np.array(key, dtype=np.uint64))
+    assert O.philox4x64_10(ctr, key) == [int(x) for x in bg.random_raw(4)]
+
+
+def test_uniforms_are_philox_top_bits():
+    seed, key = 22048, 77
+    w = O.philox4x64_10([9, 1, 3, 0], [seed, key])
+    u = O.uniforms8(seed, key, 9, 1, 3)
+    bits = []
+    for x in w:
+        bits += [(x >> 32) >> 8, (x & 0xFFFFFFFF) >> 8]
+    assert np.array_equal(np.floor(u * 2 ** 24).astype(np.int64), np.array(bits))
+    assert ((u > 0) & (u < 1)).all()
+
+
+# ---------------------------------------------------------------- profile
+
+def test_hlr_constant():
+    root = so.brentq(lambda x: 1 - (1 + x) * np.exp(-x) - 0.5, 1.0, 3.0, xtol=1e-15)
+    assert abs(O.hlr_over_r0() - root) < 1e-12
+    # the enclosed-flux formula itself, by integrating the profile
+    enc = si.quad(lambda r: r * np.exp(-r), 0, root, epsabs=1e-14)[0]
+    assert abs(enc - 0.5) < 1e-12
+
+
+@pytest.mark.parametrize("nu,x", [(2, 0.5), (2, 3.0), (2, 1e-3), (1.5, 0.7), (0.5, 2.0), (2, 25.0)])
+def test_bessel_k_vs_scipy(nu, x):
+    assert abs(O.bessel_k(nu, x) / sp.kv(nu, x) - 1) < 1e-12
+
+
+def _hankel(f, k, rmax):
+    return 2 * np.pi * si.quad(lambda r: f(r) * sp.j0(k * r) * r, 0, rmax, limit=2000, epsabs=1e-13)[0]
+
+
+@pytest.mark.parametrize("k", [0.0, 0.7, 3.0, 11.0])
+def test_exponential_ft_vs_hankel(k):
+    r0 = 0.4
+    num = _hankel(lambda r: np.exp(-r / r0) / (2 * np.pi * r0 ** 2), k, 60 * r0)
+    assert abs(O.exp_profile_ft(k, 0.0, r0, 0.0, 0.0) - num) < 1e-9
+
+
+@pytest.mark.parametrize("k", [0.0, 0.5, 2.0, 6.0])
+def test_moffat_and_gaussian_ft_vs_hankel(k):
+    fwhm, beta = 0.8, 3.0
+    rd = fwhm / (2 * np.sqrt(2 ** (1 / beta) - 1))
+    assert abs((1 + (fwhm / 2) ** 2 / rd ** 2) ** -beta - 0.5) < 1e-12          # FWHM definition
+    mof = lambda r: (beta - 1) / (np.pi * rd ** 2) * (1 + (r / rd) ** 2) ** -beta
+    assert abs(O.psf_ft((O.PSF_MOFFAT, fwhm, beta), k) - _hankel(mof, k, 4000 * rd)) < 2e-7
+    s = fwhm / (2 * np.sqrt(2 * np.log(2)))
+    assert abs(np.exp(-(fwhm / 2) ** 2 / (2 * s * s)) - 0.5) < 1e-12
+    gau = lambda r: np.exp(-r * r / (2 * s * s)) / (2 * np.pi * s * s)
+    assert abs(O.psf_ft((O.PSF_GAUSSIAN, fwhm), k) - _hankel(gau, k, 20 * s)) < 1e-10
+
+
+# ---------------------------------------------------------------- renderer
+
+TH = [2.5, np.log10(0.6), 0.2, -0.15, 0.3, -0.2]
+
+
+def test_render_direct_separable_and_numpy_fft_agree():
+    N = 15
+    a = O.render(N, 0.2, (O.PSF_GAUSSIAN, 0.7), TH, 0)
+    b = O.render(N, 0.2, (O.PSF_GAUSSIAN, 0.7), TH, 1)
+    M = O.model_spectrum(N, 0.2, (O.PSF_GAUSSIAN, 0.7), TH)
+    c = np.real(np.fft.fftshift(np.fft.ifft2(np.fft.ifftshift(M))))
+    assert np.abs(a - b).max() < 1e-13 * np.abs(a).max()
+    assert np.abs(a - c).max() < 1e-13 * np.abs(a).max()
+
+
+def test_render_total_flux_is_F():
+    for N in (9, 25, 53):
+        img = O.render(N, 0.2, (O.PSF_MOFFAT, 0.8, 3.0), TH)
+        assert abs(img.sum() / 10 ** TH[0] - 1) < 1e-12
+
+
+def test_render_matches_realspace_bruteforce():
+    """Periodic pixel integrals of exponential * Gaussian PSF by midpoint
+    quadrature in real space; the k-space render differs only by the spectrum
+    beyond the grid (< 1e-10 here) and the quadrature error."""
+    N, p, fw = 9, 0.2, 0.8
+    th = [2.0, np.log10(1.0), 0.15, -0.1, 0.25, -0.3]
+    k = O.render(N, p, (O.PSF_GAUSSIAN, fw), th)
+    r = O.render_realspace_gauss(N, p, fw, th, 32, 10)
+    assert np.abs(k - r).max() < 2e-8 * k.max()
+
+
+@pytest.mark.parametrize("e", [(0.3, -0.2), (0.0, 0.0), (-0.5, 0.1)])
+def test_second_moments_closed_form(e):
+    """Exponential: <x x^T> = 3 r0^2 S S^T; the Gaussian PSF adds s^2 I and the
+    pixel p^2/12 I; the centroid is at the offset."""
+    N, p, fw, hlr = 151, 0.2, 0.8, 0.5
+    e1, e2 = e
+    th = [3.0, np.log10(hlr), e1, e2, 0.3, -0.4]
+    img = O.render(N, p, (O.PSF_GAUSSIAN, fw), th)
+    x = (np.arange(N) - (N - 1) / 2) * p
+    X, Y = np.meshgrid(x, x)
+    F = img.sum()
+    mx, my = (img * X).sum() / F, (img * Y).sum() / F
+    assert abs(mx / p - 0.3) < 1e-8 and abs(my / p + 0.4) < 1e-8
+    I = np.array([[(img * (X - mx) ** 2).sum(), (img * (X - mx) * (Y - my)).sum()],
+                  [(img * (X - mx) * (Y - my)).sum(), (img * (Y - my) ** 2).sum()]]) / F
+    r0 = hlr / O.hlr_over_r0()
+    E = e1 * e1 + e2 * e2
+    SS = np.array([[1 + 2 * e1 + E, 2 * e2], [2 * e2, 1 - 2 * e1 + E]]) / (1 - E)
+    s = fw / (2 * np.sqrt(2 * np.log(2)))
+    want = 3 * r0 ** 2 * SS + (s * s + p * p / 12) * np.eye(2)
+    assert np.abs(I - want).max() < 1e-8 * np.abs(want).max()
+
+
+def test_square_aperture_flux_matches_hankel():
+    """Flux of exponential * Gaussian PSF inside centred squares of half-width a:
+    (4/pi) int_0^{pi/4} E(a / cos phi) dphi with the circular enclosed flux
+    E(R) = R int_0^inf F(k) J1(k R) dk of the radial transform F."""
+    N, p, fw, hlr = 101, 0.2, 0.8, 0.5
+    th = [0.0, np.log10(hlr), 0.0, 0.0, 0.0, 0.0]
+    img = O.render(N, p, (O.PSF_GAUSSIAN, fw), th)
+    r0 = hlr / O.hlr_over_r0()
+    s = fw / (2 * np.sqrt(2 * np.log(2)))
+    Fk = lambda k: (1 + (k * r0) ** 2) ** -1.5 * np.exp(-0.5 * (k * s) ** 2)
+    Ecirc = lambda R: R * si.quad(lambda k: Fk(k) * sp.j1(k * R), 0, 60.0 / s, limit=4000, epsabs=1e-13)[0]
+    c = (N - 1) // 2
+    for half in (2, 5, 12):
+        a = (half + 0.5) * p
+        want = 4 / np.pi * si.quad(lambda ph: Ecirc(a / np.cos(ph)), 0, np.pi / 4, epsabs=1e-11)[0]
+        got = img[c - half:c + half + 1, c - half:c + half + 1].sum()
+        assert abs(got - want) < 2e-7, (half, got, want)
+
+
+# ---------------------------------------------------------------- likelihood and prior
+
+@pytest.mark.parametrize("psf", [(O.PSF_GAUSSIAN, 0.7), (O.PSF_MOFFAT, 0.8, 3.0)])
+@pytest.mark.parametrize("weighted", [False, True])
+def test_logpost_gradient_matches_central_differences(psf, weighted):
+    rng = np.random.default_rng(1)
+    N = 25
+    th = np.array([2.6, np.log10(0.7), 0.25, -0.1, 0.2, -0.35])
+    data = O.render(N, 0.2, psf, [2.55, np.log10(0.75), 0.2, -0.05, 0.1, -0.3]) + rng.normal(0, 1, (N, N))
+    w = rng.uniform(0.5, 1.5, (N, N)) if weighted else None
+    v, g = O.logpost(N, 0.2, psf, data, 1.3, th, weights=w)
+    fd = np.zeros(6)
+    for i in range(6):
+        h = 1e-6
+        tp, tm = th.copy(), th.copy()
+        tp[i] += h
+        tm[i] -= h
+        fd[i] = (O.logpost(N, 0.2, psf, data, 1.3, tp, weights=w)[0] - O.logpost(N, 0.2, psf, data, 1.3, tm, weights=w)[0]) / (2 * h)
+    assert np.abs(fd - g).max() < 1e-7 * np.abs(g).max()
+
+
+def test_loglike_is_pixel_chi2():
+    rng = np.random.default_rng(2)
+    N = 21
+    data = rng.normal(0, 1, (N, N)) + O.render(N, 0.2, (O.PSF_GAUSSIAN, 0.7), TH)
+    m = O.render(N, 0.2, (O.PSF_GAUSSIAN, 0.7), TH)
+    v, _ = O.loglike(N, 0.2, (O.PSF_GAUSSIAN, 0.7), data, 1.7, TH)
+    assert abs(v + 0.5 * ((data - m) ** 2).sum() / 1.7 ** 2) < 1e-10 * abs(v)
+
+
+def test_interim_prior_normalised_and_support():
+    # ellipticity density integrates to one over the unit disk (polar quadrature)
+    se = 0.3
+    lz = O.log_z_ba14(se)
+    tot = si.dblquad(lambda r, t: r * np.exp(2 * np.log1p(-r * r) - r * r / (2 * se * se) - lz),
+                     0, 2 * np.pi, 0, 1, epsabs=1e-13)[0]
+    assert abs(tot - 1) < 1e-10
+    # the full prior at one point: uniform * uniform * Gaussian * Gaussian * e density
+    th = [3.0, -0.2, 0.3, 0.1, 0.2, -0.1]
+    want = (-np.log(10) - np.log(3) - np.log(2 * np.pi * 0.25) - (0.04 + 0.01) / 0.5
+            + 2 * np.log1p(-0.1) - 0.1 / 0.18 - lz)
+    assert abs(O.log_prior(th) - want) < 1e-12
+    assert O.log_prior([3.0, -0.2, 0.8, 0.7, 0, 0]) == -np.inf
+    assert O.log_prior([9.5, -0.2, 0.1, 0.1, 0, 0]) == -np.inf
+
+
+def test_golden_paper_constants():
+    g = json.load(open(GOLDEN))
+    ip = g["interim_prior"]
+    from paper_2604_22048_gb300 import api
+    want = (*ip["log10_flux_uniform"], *ip["log10_hlr_uniform"], ip["sigma_xy_pixels"], ip["sigma_e"])
+    assert tuple(api.DEFAULT_PRIOR) == want
+    assert O._prior(None).sigma_e == ip["sigma_e"] and O._prior(None).sigma_xy == ip["sigma_xy_pixels"]
+    assert synth.PIXEL_SCALE == g["pixel_scale_arcsec"]["value"]
+    assert synth.draw_plain(3, 25).g[0] == g["applied_shear_g1"]["value"]
+    off = synth.init_offsets(synth.draw_plain(50, 25), 4)
+    assert np.abs(off[..., 0]).max() <= g["chain_init_boxes"]["log10_hlr_halfwidth"]
+    assert np.abs(off[..., 1:]).max() <= g["chain_init_boxes"]["ellipticity_halfwidth"]
+
+
+# ---------------------------------------------------------------- shear transform
+
+def _S(e1, e2):
+    E = e1 * e1 + e2 * e2
+    return np.array([[1 + e1, e2], [e2, 1 - e1]]) / np.sqrt(1 - E)
+
+
+@pytest.mark.parametrize("e,g", [((0.3, -0.2), (0.02, 0.0)), ((-0.6, 0.5), (0.1, -0.07)), ((0.0, 0.0), (0.05, 0.05))])
+def test_shear_composition(e, g):
+    """Shearing an ellipse: S_g S_eps = S_eps' R with R a rotation (polar
+    decomposition), eps' = (eps + g)/(1 + g* eps) (Eq. shear-transform)."""
+    M = _S(*g) @ _S(*e)
+    P = sl.sqrtm(M @ M.T).real
+    ep = O.shear_apply(*e, *g)
+    assert np.abs(P - _S(*ep)).max() < 1e-12
+    R = np.linalg.solve(P, M)
+    assert np.abs(R @ R.T - np.eye(2)).max() < 1e-12
+    back = O.shear_invert(*ep, *g)
+    assert np.abs(np.array(back) - e).max() < 1e-14
+
+
+def test_jacobian_matches_fd_determinant():
+    g1, g2, h = 0.03, -0.02, 1e-6
+    for e in [(0.4, 0.3), (-0.7, 0.1), (0.0, 0.0)]:
+        inv = lambda a, b: np.array(O.shear_invert(a, b, g1, g2))
+        J = np.column_stack([(inv(e[0] + h, e[1]) - inv(e[0] - h, e[1])) / (2 * h),
+                             (inv(e[0], e[1] + h) - inv(e[0], e[1] - h)) / (2 * h)])
+        assert abs(abs(np.linalg.det(J)) / O.shear_jacobian(*e, g1, g2) - 1) < 1e-8
+
+
+@pytest.mark.parametrize("a", [0.15, 0.2, 0.3, 0.8])
+def test_ellipticity_normalisers_vs_quadrature(a):
+    z = si.dblquad(lambda r, t: r * (1 - r * r) ** 2 * np.exp(-r * r / (2 * a * a)), 0, 2 * np.pi, 0, 1,
+                   epsabs=1e-14, epsrel=1e-13)[0]
+    assert abs(O.log_z_ba14(a) - np.log(z)) < 1e-12
+    zt = si.quad(lambda r: 2 * np.pi * r * np.exp(-r * r / (2 * a * a)), 0, 0.7, epsabs=1e-15)[0]
+    assert abs(O.log_z_eprior(O.EPRIOR_TRUNC_GAUSS, a, 0.7) - np.log(zt)) < 1e-12
+
+
+# ---------------------------------------------------------------- shear likelihood
+
+def _samples(rng, n, K, s=0.2):
+    e = rng.normal(0, s, (n, K, 2))
+    r = np.hypot(e[..., 0], e[..., 1])
+    e[r > 0.9] *= (0.9 / r[r > 0.9])[:, None]
+    return e[..., 0].astype(np.float32), e[..., 1].astype(np.float32)
+
+
+def test_shear_loglike_zero_when_true_prior_is_interim():
+    """g = 0 and the true density equal to the interim one: every weight is 1."""
+    rng = np.random.default_rng(0)
+    e1, e2 = _samples(rng, 30, 17)
+    v, _ = O.shear_loglike(e1, e2, 0.0, 0.0, 0.3, family=O.EPRIOR_BA14, sigma_e0=0.3)
+    assert abs(v) < 1e-12
+
+
+@pytest.mark.parametrize("family", [O.EPRIOR_BA14, O.EPRIOR_TRUNC_GAUSS])
+def test_shear_loglike_gradient_fd(family):
+    rng = np.random.default_rng(2)
+    e1, e2 = _samples(rng, 50, 40)
+    b = rng.normal(0, 0.5, (50, 40)).astype(np.float32)
+    x = np.array([0.02, -0.01, 0.25])
+    _, g = O.shear_loglike(e1, e2, *x, b=b, family=family)
+    for i in range(3):
+        h = 1e-6
+        xp, xm = x.copy(), x.copy()
+        xp[i] += h
+        xm[i] -= h
+        fd = (O.shear_loglike(e1, e2, *xp, b=b, family=family)[0] - O.shear_loglike(e1, e2, *xm, b=b, family=family)[0]) / (2 * h)
+        assert abs(fd - g[i]) < 1e-6 * np.abs(g).max()
+
+
+def test_shear_likelihood_recovers_g_noise_free():
+    """One exact sheared ellipticity per galaxy (K = 1): the shear likelihood is
+    the likelihood of g for the sheared shapes, so the estimate sits on g; with
+    the same intrinsic shapes sheared by +g and -g the shape noise cancels."""
+    n = 20000
+    t = synth.draw_plain(n, 25, seed=4)
+    est = {}
+    for sgn in (1, -1):
+        g = (0.02 * sgn, 0.0)
+        ep = np.array([O.shear_apply(a, b, *g) for a, b in t.e_int])
+        m, cov = O.shear_estimate(ep[:, :1].astype(np.float32), ep[:, 1:].astype(np.float32),
+                                  family=O.EPRIOR_TRUNC_GAUSS, alpha=0.2)
+        assert abs(m[0] - g[0]) < 4 * np.sqrt(cov[0, 0])
+        assert abs(m[1] - g[1]) < 4 * np.sqrt(cov[1, 1])
+        est[sgn] = m
+    # g1 shape noise cancels in the pair; g2 shape noise does not (only g1 flips)
+    m_hat = (est[1][0] - est[-1][0]) / 0.04 - 1
+    assert abs(m_hat) < 2e-3, m_hat
+
+
+def test_gauss_hermite_vs_numpy():
+    for n in (1, 3, 7, 12):
+        x, w = O.gauss_hermite(n)
+        xr, wr = np.polynomial.hermite.hermgauss(n)
+        assert np.abs(x - xr).max() < 1e-12 and np.abs(w - wr).max() < 1e-12
+
+
+# ---------------------------------------------------------------- sampler pieces
+
+def test_window_schedule_documented_example():
+    # Stan's documented schedule for 1000 warmup iterations: 75 fast, slow
+    # windows of 25, 50, 100, 200 and a stretched 500, 50 fast
+    assert O.window_schedule(1000) == [(75, 100), (100, 150), (150, 250), (250, 450), (450, 950)]
+    assert O.window_schedule(300) == [(75, 100), (100, 150), (150, 250)]
+    assert O.window_schedule(100) == [(15, 90)]
+    assert O.window_schedule(10) == [] and O.window_schedule(300, False) == []
+
+
+def test_ess_iid_and_ar1():
+    rng = np.random.default_rng(0)
+    C, S = 4, 20000
+    x = rng.normal(size=(C, S))
+    assert abs(O.ess(x) / (C * S) - 1) < 0.1
+    rho = 0.5
+    y = np.zeros((C, S))
+    y[:, 0] = rng.normal(size=C)
+    for s in range(1, S):
+        y[:, s] = rho * y[:, s - 1] + np.sqrt(1 - rho * rho) * rng.normal(size=C)
+    assert abs(O.ess(y) / (C * S * (1 - rho) / (1 + rho)) - 1) < 0.1
+    assert O.rhat(x) < 1.01
+    z = x + np.arange(C)[:, None] * 0.5
+    assert O.rhat(z) > 1.1
+
+
+@pytest.mark.slow
+def test_hmc_matches_laplace_on_bright_galaxy():
+    """High S/N: the posterior is close to a Gaussian with covariance (-H)^-1 at
+    the mode; the sampler's moments must agree within Monte Carlo error."""
+    N = 25
+    theta = np.array([np.log10(2000.0), np.log10(0.6), 0.2, -0.1, 0.1, -0.2])
+    rng = np.random.default_rng(3)
+    data = O.render(N, 0.2, (O.PSF_GAUSSIAN, 0.7), theta) + rng.normal(0, 1, (N, N))
+    f = lambda t: -O.logpost(N, 0.2, (O.PSF_GAUSSIAN, 0.7), data, 1.0, t)[0]
+    gr = lambda t: -O.logpost(N, 0.2, (O.PSF_GAUSSIAN, 0.7), data, 1.0, t)[1]
+    mode = so.minimize(f, theta, jac=gr, method="BFGS", options={"gtol": 1e-9}).x
+    H = np.zeros((6, 6))
+    for j in range(6):
+        h = 1e-5
+        tp, tm = mode.copy(), mode.copy()
+        tp[j] += h
+        tm[j] -= h
+        H[:, j] = (gr(tp) - gr(tm)) / (2 * h)
+    cov = np.linalg.inv(0.5 * (H + H.T))
+    C = 4
+    init = np.repeat(mode[None, None, :], C, axis=1) + rng.normal(0, 1e-3, (1, C, 6))
+    out = O.fit_galaxies(data[None], 1.0, (O.PSF_GAUSSIAN, 0.7), init, n_warmup=300, n_samples=1000,
+                         n_leapfrog=16, random_steps=True, seed=5)
+    s = out["samples"][:, 0]                     # [6, C, S]
+    flat = s.reshape(6, -1)
+    for k in range(6):
+        ess = O.ess(s[k])
+        sd = np.sqrt(cov[k, k])
+        assert abs(flat[k].mean() - mode[k]) < 5 * sd / np.sqrt(ess) + 0.05 * sd, k
+        assert abs(flat[k].std() / sd - 1) < 0.12, (k, flat[k].std() / sd)
+        assert O.rhat(s[k]) < 1.01
