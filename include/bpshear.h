@@ -1,0 +1,258 @@
+/*
+ * bpshear.h -- C ABI of the GB300 (sm_103a) hot path of Bayesian shear
+ * inference with a known PSF and sky background (Mendoza et al.,
+ * "Differentiable Forward Modeling for Efficient and Accurate Shear
+ * Inference"):
+ *
+ *   image sampling phase (Sec. 3.3): per-galaxy HMC on the interim posterior
+ *     of Eq. interim-post, i.e. the Gaussian pixel likelihood of
+ *     Eq. likelihood-pixels times the interim prior of Eq. interim-prior, for
+ *     an exponential galaxy sheared in the reduced-shear convention
+ *     (Eq. shear-transform) and convolved with a known PSF and the pixel;
+ *   shear sampling phase (Sec. 3.2-3.4): the MC shear likelihood of
+ *     Eq. likelihood-shear with the Jacobian of
+ *     Eq. true-prior-jacobian-shear, its gradient, and the posterior-mean
+ *     shear estimate.
+ *
+ * Conventions shared by every call
+ *   - All array arguments are plain pointers to caller-owned memory, device
+ *     memory unless stated.  The library never allocates device memory; calls
+ *     that need scratch take a caller-provided workspace whose size the
+ *     matching *_workspace_bytes() call reports.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Work is enqueued asynchronously on it; only the calls that
+ *     return host results (bs_shear_estimate, and bs_shear_loglike with a host
+ *     output) synchronise it.
+ *   - Every call returns a bs_status.  Argument errors are detected on the
+ *     host before anything is launched; CUDA launch errors are reported as
+ *     BS_ERR_CUDA.  bs_last_error() returns a thread-local message describing
+ *     the last failure.  No call aborts the process and no C++ exception
+ *     crosses this interface.  Problems found inside a kernel (a galaxy whose
+ *     starting point is outside the prior support) go to the per-galaxy
+ *     status array, which the caller reads after synchronising.
+ *   - Parameter vector theta = (lF, ls, e1, e2, dx, dy): lF = log10 flux,
+ *     ls = log10 half-light radius [arcsec] of the circular profile before
+ *     the area-preserving shear, (e1, e2) = ellipticity in the reduced-shear
+ *     ("epsilon") convention (Sec. 2, Eq. ellip-phi-transform), (dx, dy) =
+ *     centroid offset from the stamp centre in pixels.
+ *   - A stamp of odd side N has pixel (iy, ix) centred at
+ *     ((ix - c) p, (iy - c) p), c = (N-1)/2, stored row-major (iy slowest).
+ *     Its model is the inverse DFT on the N x N periodic grid of the
+ *     analytic spectrum M(k) = F (1 + r0^2 k^T S^2 k)^{-3/2} PSF(|k|)
+ *     sinc(kx p/2) sinc(ky p/2) exp(-i p (kx dx + ky dy)), with
+ *     r0 = hlr / 1.678347 and S the shear matrix of (e1, e2).
+ */
+#ifndef BPSHEAR_H
+#define BPSHEAR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    BS_OK = 0,
+    BS_ERR_INVALID_ARG = -1,   /* bad pointer, size, layout or option */
+    BS_ERR_CUDA = -2,          /* a CUDA runtime call or launch failed */
+    BS_ERR_OUT_OF_MEMORY = -3, /* workspace smaller than *_workspace_bytes() */
+    BS_ERR_TIMEOUT = -4,       /* a bounded device wait gave up */
+    BS_ERR_UNSUPPORTED = -5    /* valid request this build does not serve */
+} bs_status;
+
+enum { BS_F32 = 0, BS_F64 = 1 };
+enum { BS_PSF_GAUSSIAN = 1, BS_PSF_MOFFAT = 2 };
+enum { BS_EPRIOR_BA14 = 0, BS_EPRIOR_TRUNC_GAUSS = 1 };
+
+/* Largest stamp side the kernels accept. */
+#define BS_MAX_SIDE 127
+
+/* Known PSF of one galaxy (Sec. 2: Gaussian, FWHM 0.8"; the graphical model
+ * of Fig. pgm allows a different known PSF per galaxy).
+ * Gaussian: exp(-r^2 / 2 s^2), s = fwhm / 2.35482.
+ * Moffat:   (1 + r^2/rd^2)^-beta, fwhm = 2 rd sqrt(2^(1/beta) - 1), beta > 1. */
+typedef struct {
+    int32_t kind;   /* BS_PSF_* */
+    float fwhm;     /* arcsec */
+    float beta;     /* Moffat only */
+} bs_psf;
+
+/* Interim prior of Eq. interim-prior: log10 f ~ U(lf_lo, lf_hi),
+ * log10 s ~ U(ls_lo, ls_hi), dx, dy ~ N(0, sigma_xy) [px], (e1, e2) density
+ * proportional to (1-|e|^2)^2 exp(-|e|^2 / (2 sigma_e^2)). */
+typedef struct {
+    float lf_lo, lf_hi, ls_lo, ls_hi, sigma_xy, sigma_e;
+} bs_prior;
+
+/* Paper values: U(-1, 9), U(-2, 1), sigma_xy = 0.5, sigma_e = 0.3. */
+void bs_prior_default(bs_prior *prior);
+
+const char *bs_last_error(void);
+const char *bs_version(void);
+
+/* ------------------------------------------------------------------------ */
+/* Rendering (forward model, Sec. 3.3)                                       */
+/* ------------------------------------------------------------------------ */
+
+/* Draw n noiseless model stamps.
+ *   theta   device float [n][6]; with `shear` non-NULL, (e1, e2) is the
+ *           intrinsic ellipticity and is sheared by g = shear[i] with
+ *           Eq. shear-transform before drawing.
+ *   shear   device float [n][2] or NULL.
+ *   offsets device int64 [n]: element offset of stamp i in `out`.
+ *   side    device int32 [n]: odd side, 3 <= side <= max_side.
+ *   max_side host bound on side[] (<= BS_MAX_SIDE).
+ *   psf     device bs_psf [n_psf], n_psf = 1 (shared) or n.
+ *   out     device float, written at out[offsets[i] + iy*N + ix].
+ * Errors: BS_ERR_INVALID_ARG for NULL required pointers, n < 0, n_psf not
+ * in {1, n}, max_side out of range or pixel_scale <= 0. */
+bs_status bs_render(int32_t n, const float *theta, const float *shear,
+                    const int64_t *offsets, const int32_t *side, int32_t max_side,
+                    const bs_psf *psf, int32_t n_psf, float pixel_scale,
+                    float *out, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Image sampling phase: fit_galaxies (Sec. 3.3)                             */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    int32_t n_gal;
+    int32_t data_dtype;         /* BS_F32 or BS_F64 */
+    const void *data;           /* device: packed noisy stamps */
+    const int64_t *offsets;     /* device [n_gal]: element offset of each stamp */
+    const int32_t *side;        /* device [n_gal]: odd side, 3..max_side */
+    int32_t max_side;           /* host bound on side[], <= BS_MAX_SIDE */
+    const bs_psf *psf;          /* device [n_psf] */
+    int32_t n_psf;              /* 1 (shared) or n_gal */
+    const float *noise_sigma;   /* device [n_gal]: pixel noise sd, b = sigma^2 */
+    const uint64_t *gal_id;     /* device [n_gal] or NULL (= index): keys the
+                                   random stream, so a galaxy's chains do not
+                                   depend on its batch or position */
+    const float *init;          /* device [n_gal][n_chains][6]: chain starts
+                                   (Eq. initialize needs the truth; the caller
+                                   supplies them) */
+    float pixel_scale;          /* arcsec */
+    bs_prior prior;
+    int32_t n_chains;           /* 1..8 chains per galaxy */
+    int32_t n_warmup;           /* dual-averaging / metric warmup iterations */
+    int32_t n_samples;          /* kept iterations per chain */
+    int32_t n_leapfrog;         /* L (fixed) or L_max (random_steps) */
+    float target_accept;        /* dual-averaging target, 0 < delta < 1 */
+    float jitter;               /* eps * U(1-j, 1+j) when !random_steps */
+    int32_t adapt_mass;         /* windowed diagonal metric adaptation */
+    int32_t random_steps;       /* L_i uniform on 1..n_leapfrog */
+    uint64_t seed;
+} bs_fit_args;
+
+/* Outputs, caller-allocated device buffers (NULL = not wanted, except
+ * samples).  Samples are parameter-major so that each parameter plane, e.g.
+ * the (e1, e2) planes the shear phase reads, is contiguous. */
+typedef struct {
+    float *samples;        /* [6][n_gal][n_chains][n_samples] (required) */
+    float *logp;           /* [n_gal][n_chains][n_samples]: log posterior
+                              (log-likelihood without its constant plus the
+                              normalised log interim prior) */
+    uint8_t *accepted;     /* [n_gal][n_chains][n_samples]: 1 if accepted */
+    float *accept_rate;    /* [n_gal][n_chains]: mean accept statistic */
+    float *step_size;      /* [n_gal][n_chains]: adapted step size */
+    float *inv_mass;       /* [n_gal][n_chains][6]: adapted inverse metric */
+    int32_t *n_divergent;  /* [n_gal][n_chains]: divergent transitions */
+    int32_t *status;       /* [n_gal]: 0 ok, 1 a chain started off-support */
+} bs_fit_out;
+
+/* Bytes of device workspace bs_fit_galaxies needs (a work-queue counter). */
+size_t bs_fit_workspace_bytes(const bs_fit_args *args);
+
+/* Run warmup + sampling for every chain of every galaxy in one persistent
+ * launch: for each galaxy, the stamp's DFT and the PSF/pixel transfer are
+ * staged in shared memory once, then each chain (one warp) runs its whole
+ * Markov chain; the per-evaluation log posterior and gradient are evaluated
+ * on the spectrum, which for white noise equals the pixel-space chi^2 of
+ * Eq. likelihood-pixels (Parseval on the stamp's periodic grid).
+ * Errors: BS_ERR_INVALID_ARG (bad sizes, NULL required pointers, n_chains
+ * outside 1..8, max_side out of range), BS_ERR_OUT_OF_MEMORY (workspace too
+ * small), BS_ERR_CUDA (launch failure). */
+bs_status bs_fit_galaxies(const bs_fit_args *args, const bs_fit_out *out,
+                          void *workspace, size_t workspace_bytes, void *stream);
+
+/* Log posterior and gradient of single parameter points, for checking and
+ * for differentiation (same arithmetic as the fit's inner loop).
+ *   gal_index device int32 [n_points]: which galaxy of `args` each point uses
+ *   theta     device float [n_points][6]
+ *   logp      device double [n_points] (log-likelihood + log prior; -inf off
+ *             the prior support) or NULL; grad device float [n_points][6] or
+ *             NULL.  Only the data fields of `args` are read. */
+bs_status bs_logpost_points(const bs_fit_args *args, int32_t n_points,
+                            const int32_t *gal_index, const float *theta,
+                            double *logp, float *grad, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Chain diagnostics (Sec. 4.1)                                               */
+/* ------------------------------------------------------------------------ */
+
+/* Per galaxy and parameter: multi-chain ESS (Geyer initial monotone
+ * sequence, ESS capped at C S log10(C S)) and classic R-hat.
+ *   samples device float [6][n_gal][n_chains][n_samples]
+ *   ess, rhat device float [n_gal][6] (rhat may be NULL). */
+bs_status bs_chain_ess(const float *samples, int32_t n_gal, int32_t n_chains,
+                       int32_t n_samples, float *ess, float *rhat, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Shear sampling phase (Sec. 3.2 - 3.4)                                     */
+/* ------------------------------------------------------------------------ */
+
+/* Interim samples of the sheared ellipticity, K per galaxy. */
+typedef struct {
+    const float *e1;      /* device [n_gal][K] */
+    const float *e2;      /* device [n_gal][K] */
+    const float *b;       /* device [n_gal][K] or NULL: per-sample log prior
+                             ratio of the other properties (0 if NULL) */
+    int64_t n_gal;
+    int32_t K;
+    int32_t family;       /* true ellipticity density: BS_EPRIOR_* */
+    float trunc_r;        /* truncation radius (TRUNC_GAUSS only) */
+    float sigma_e0;       /* interim ellipticity prior parameter (0.3) */
+} bs_shear_data;
+
+size_t bs_shear_workspace_bytes(int64_t n_gal, int32_t K);
+
+/* Eq. likelihood-shear, Z_n dropped:
+ *   value = sum_n [ log sum_k w_nk - log K ],
+ *   w = p_e(eps | alpha) |d eps / d eps'| / P0_e(eps') exp(b),
+ *   eps = (eps' - g) / (1 - g* eps'),
+ * and its gradient with respect to (g1, g2, alpha).  out = {value, d/dg1,
+ * d/dg2, d/dalpha} (double[4]); on the device, or on the host when
+ * out_on_host != 0 (the call then synchronises `stream`).  Requires
+ * |g| < 1, alpha > 0.  A galaxy whose every sample has zero weight makes the
+ * value -inf. */
+bs_status bs_shear_loglike(const bs_shear_data *data, double g1, double g2,
+                           double alpha, double *out, int32_t out_on_host,
+                           void *workspace, size_t workspace_bytes, void *stream);
+
+/* Optional sum over processes of the 4 doubles {value, grad} of each
+ * evaluation, for a galaxy set sharded across ranks (a no-op when NULL). */
+typedef void (*bs_allreduce_fn)(double *buf4, void *user);
+
+typedef struct {
+    int32_t free_alpha;     /* 0: infer g with alpha fixed; 1: (g, alpha) */
+    double alpha;           /* fixed value, or the starting value if free */
+    double alpha_lo, alpha_hi;  /* uniform hyperprior when free */
+    int32_t n_gh;           /* Gauss-Hermite points per dimension (1..32) */
+    bs_allreduce_fn allreduce;  /* NULL for one process */
+    void *allreduce_user;
+} bs_estimate_cfg;
+
+/* Posterior mean (and covariance) of g (and alpha) under a uniform prior on
+ * the unit disk (and alpha ~ U(alpha_lo, alpha_hi)): Newton iterations to the
+ * mode, then tensor Gauss-Hermite quadrature on the Laplace-scaled grid.
+ *   mean host double [3] (g1, g2, alpha); cov host double [9] or NULL.
+ * Synchronises `stream`. */
+bs_status bs_shear_estimate(const bs_shear_data *data, const bs_estimate_cfg *cfg,
+                            double *mean, double *cov, void *workspace,
+                            size_t workspace_bytes, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,111 @@
+"""ctypes declarations of the bpshear C ABI (include/bpshear.h).
+
+Argument marshalling only: every computation runs in libbpshear.so.  Loading
+fails loudly when the library has not been built; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIBPATH = os.path.join(_HERE, "csrc", "libbpshear.so")
+
+BS_OK = 0
+BS_F32, BS_F64 = 0, 1
+BS_PSF_GAUSSIAN, BS_PSF_MOFFAT = 1, 2
+BS_EPRIOR_BA14, BS_EPRIOR_TRUNC_GAUSS = 0, 1
+BS_MAX_SIDE = 127
+
+STATUS_NAMES = {0: "BS_OK", -1: "BS_ERR_INVALID_ARG", -2: "BS_ERR_CUDA", -3: "BS_ERR_OUT_OF_MEMORY",
+                -4: "BS_ERR_TIMEOUT", -5: "BS_ERR_UNSUPPORTED"}
+
+# every symbol the header declares
+EXPORTED = ["bs_prior_default", "bs_last_error", "bs_version", "bs_render", "bs_fit_workspace_bytes",
+            "bs_fit_galaxies", "bs_logpost_points", "bs_chain_ess", "bs_shear_workspace_bytes",
+            "bs_shear_loglike", "bs_shear_estimate"]
+
+
+class BsError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Psf(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("fwhm", C.c_float), ("beta", C.c_float)]
+
+
+class Prior(C.Structure):
+    _fields_ = [("lf_lo", C.c_float), ("lf_hi", C.c_float), ("ls_lo", C.c_float), ("ls_hi", C.c_float),
+                ("sigma_xy", C.c_float), ("sigma_e", C.c_float)]
+
+
+class FitArgs(C.Structure):
+    _fields_ = [("n_gal", C.c_int32), ("data_dtype", C.c_int32), ("data", C.c_void_p),
+                ("offsets", C.c_void_p), ("side", C.c_void_p), ("max_side", C.c_int32),
+                ("psf", C.c_void_p), ("n_psf", C.c_int32), ("noise_sigma", C.c_void_p),
+                ("gal_id", C.c_void_p), ("init", C.c_void_p), ("pixel_scale", C.c_float),
+                ("prior", Prior), ("n_chains", C.c_int32), ("n_warmup", C.c_int32),
+                ("n_samples", C.c_int32), ("n_leapfrog", C.c_int32), ("target_accept", C.c_float),
+                ("jitter", C.c_float), ("adapt_mass", C.c_int32), ("random_steps", C.c_int32),
+                ("seed", C.c_uint64)]
+
+
+class FitOut(C.Structure):
+    _fields_ = [("samples", C.c_void_p), ("logp", C.c_void_p), ("accepted", C.c_void_p),
+                ("accept_rate", C.c_void_p), ("step_size", C.c_void_p), ("inv_mass", C.c_void_p),
+                ("n_divergent", C.c_void_p), ("status", C.c_void_p)]
+
+
+class ShearData(C.Structure):
+    _fields_ = [("e1", C.c_void_p), ("e2", C.c_void_p), ("b", C.c_void_p), ("n_gal", C.c_int64),
+                ("K", C.c_int32), ("family", C.c_int32), ("trunc_r", C.c_float), ("sigma_e0", C.c_float)]
+
+
+ALLREDUCE_FN = C.CFUNCTYPE(None, C.POINTER(C.c_double), C.c_void_p)
+
+
+class EstimateCfg(C.Structure):
+    _fields_ = [("free_alpha", C.c_int32), ("alpha", C.c_double), ("alpha_lo", C.c_double),
+                ("alpha_hi", C.c_double), ("n_gh", C.c_int32), ("allreduce", ALLREDUCE_FN),
+                ("allreduce_user", C.c_void_p)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libbpshear.so (built by paper_2604_22048_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIBPATH):
+        raise ImportError(f"{LIBPATH} is missing: build it with `python -m paper_2604_22048_gb300.build`"
+                          " (the CUDA path has no fallback)")
+    L = C.CDLL(LIBPATH)
+    vp, i32, i64, f32, f64, sz = C.c_void_p, C.c_int32, C.c_int64, C.c_float, C.c_double, C.c_size_t
+    L.bs_prior_default.argtypes = [C.POINTER(Prior)]
+    L.bs_prior_default.restype = None
+    L.bs_last_error.restype = C.c_char_p
+    L.bs_version.restype = C.c_char_p
+    L.bs_render.argtypes = [i32, vp, vp, vp, vp, i32, vp, i32, f32, vp, vp]
+    L.bs_fit_workspace_bytes.argtypes = [C.POINTER(FitArgs)]
+    L.bs_fit_workspace_bytes.restype = sz
+    L.bs_fit_galaxies.argtypes = [C.POINTER(FitArgs), C.POINTER(FitOut), vp, sz, vp]
+    L.bs_logpost_points.argtypes = [C.POINTER(FitArgs), i32, vp, vp, vp, vp, vp]
+    L.bs_chain_ess.argtypes = [vp, i32, i32, i32, vp, vp, vp]
+    L.bs_shear_workspace_bytes.argtypes = [i64, i32]
+    L.bs_shear_workspace_bytes.restype = sz
+    L.bs_shear_loglike.argtypes = [C.POINTER(ShearData), f64, f64, f64, vp, i32, vp, sz, vp]
+    L.bs_shear_estimate.argtypes = [C.POINTER(ShearData), C.POINTER(EstimateCfg), vp, vp, vp, sz, vp]
+    for nm in ("bs_render", "bs_fit_galaxies", "bs_logpost_points", "bs_chain_ess", "bs_shear_loglike",
+               "bs_shear_estimate"):
+        getattr(L, nm).restype = C.c_int
+    _lib = L
+    return L
+
+
+def check(status):
+    if status != BS_OK:
+        raise BsError(status, lib().bs_last_error().decode(errors="replace"))

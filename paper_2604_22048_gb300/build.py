@@ -1,0 +1,72 @@
+"""Build libbpshear.so (the C-ABI library) in-tree with nvcc for sm_103a.
+
+Each translation unit is compiled in parallel, then linked with the CUDA
+runtime.  The result lands next to the sources; the Python binding loads it
+from there.  Run as ``python -m paper_2604_22048_gb300.build``.
+"""
+from __future__ import annotations
+
+import os
+import shutil
+import subprocess
+import sys
+import tempfile
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(HERE, "csrc")
+INCLUDE = os.path.join(os.path.dirname(HERE), "include")
+LIB = os.path.join(CSRC, "libbpshear.so")
+SOURCES = ["bs_api.cu", "bs_fit.cu", "bs_render.cu", "bs_shear.cu", "bs_diag.cu"]
+HEADERS = ["bs_device.cuh", "bs_internal.h"]
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def nvcc() -> str:
+    for cand in (os.environ.get("NVCC"), shutil.which("nvcc"), "/usr/local/cuda/bin/nvcc"):
+        if cand and os.path.exists(cand):
+            return cand
+    raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libbpshear.so")
+
+
+def _stale() -> bool:
+    if not os.path.exists(LIB):
+        return True
+    t = os.path.getmtime(LIB)
+    deps = [os.path.join(CSRC, s) for s in SOURCES + HEADERS] + [os.path.join(INCLUDE, "bpshear.h")]
+    return any(os.path.getmtime(d) > t for d in deps)
+
+
+def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
+    if not force and not _stale():
+        return LIB
+    cc = nvcc()
+    flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE,
+                    "-Xptxas", "-v" if verbose else "-O3"] + list(extra_flags or [])
+    tmpdir = tempfile.mkdtemp(prefix="bpshear_build_", dir=CSRC)
+    try:
+        procs, objs = [], []
+        for src in SOURCES:
+            obj = os.path.join(tmpdir, src.replace(".cu", ".o"))
+            objs.append(obj)
+            cmd = [cc, *flags, "-c", os.path.join(CSRC, src), "-o", obj]
+            procs.append((src, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
+        failed = []
+        for src, p in procs:
+            out, _ = p.communicate()
+            text = out.decode(errors="replace")
+            if p.returncode != 0:
+                failed.append(f"--- {src}\n{text}")
+            elif verbose and text.strip():
+                print(f"--- {src}\n{text}")
+        if failed:
+            raise RuntimeError("nvcc failed:\n" + "\n".join(failed))
+        tmp_lib = os.path.join(tmpdir, "libbpshear.so")
+        subprocess.run([cc, *ARCH, "-shared", "-o", tmp_lib, *objs, "-lcudart"], check=True)
+        os.replace(tmp_lib, LIB)
+    finally:
+        shutil.rmtree(tmpdir, ignore_errors=True)
+    return LIB
+
+
+if __name__ == "__main__":
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))

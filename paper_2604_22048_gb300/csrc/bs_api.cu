@@ -1,0 +1,594 @@
+// C ABI of the bpshear library: argument validation, launch configuration,
+// the per-galaxy constants of the shear likelihood, and the host-driven
+// shear estimate (Newton to the mode, Gauss-Hermite quadrature on the
+// Laplace-scaled grid).  See include/bpshear.h for the contract of each call.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "bs_internal.h"
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+bs_status fail(bs_status st, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+bs_status cuda_fail(cudaError_t e, const char *what)
+{
+    return fail(BS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+constexpr double kPi = 3.14159265358979323846;
+
+// log of pi * int_0^1 (1-t)^2 exp(-a t) dt, the normaliser of the
+// (1-|e|^2)^2 exp(-|e|^2 / (2 alpha^2)) ellipticity density, a = 1/(2 alpha^2)
+double log_z_ba14(double alpha)
+{
+    const double a = 1.0 / (2.0 * alpha * alpha);
+    double z;
+    if (a < 1e-2)
+        z = 1.0 / 3.0 - a / 12.0 + a * a / 60.0 - a * a * a / 360.0;
+    else
+        z = 1.0 / a - 2.0 / (a * a) - 2.0 * std::expm1(-a) / (a * a * a);
+    return std::log(kPi * z);
+}
+
+// d log Z / d alpha for the family
+double dlog_z_dalpha(int family, double alpha, double trunc_r)
+{
+    if (family == BS_EPRIOR_BA14) {
+        const double a = 1.0 / (2.0 * alpha * alpha);
+        double z, dz;   // without the factor pi
+        if (a < 1e-2) {
+            z = 1.0 / 3.0 - a / 12.0 + a * a / 60.0;
+            dz = -1.0 / 12.0 + a / 30.0 - a * a / 120.0;
+        } else {
+            const double em = std::expm1(-a), e = std::exp(-a);
+            z = 1.0 / a - 2.0 / (a * a) - 2.0 * em / (a * a * a);
+            dz = -1.0 / (a * a) + 4.0 / (a * a * a) + 6.0 * em / (a * a * a * a) + 2.0 * e / (a * a * a);
+        }
+        const double da = -1.0 / (alpha * alpha * alpha);
+        return dz * da / z;
+    }
+    const double x = trunc_r * trunc_r / (2.0 * alpha * alpha);
+    return 2.0 / alpha - (trunc_r * trunc_r / (alpha * alpha * alpha)) / std::expm1(x);
+}
+
+double log_z_family(int family, double alpha, double trunc_r)
+{
+    if (family == BS_EPRIOR_BA14) return log_z_ba14(alpha);
+    const double x = trunc_r * trunc_r / (2.0 * alpha * alpha);
+    return std::log(2.0 * kPi * alpha * alpha) + std::log(-std::expm1(-x));
+}
+
+// Warmup windows: fast buffer, doubling slow windows, final fast buffer
+// (75 / 25... / 50, or 15% / rest / 10% for warmups shorter than 150); the
+// last slow window runs up to the final buffer.
+int warmup_windows(int W, bool adapt, int *st, int *en, int cap)
+{
+    if (!adapt || W < 20) return 0;
+    int head = 75, tail = 50, len = 25;
+    if (W < head + tail + len) {
+        head = (int)(0.15 * W);
+        tail = (int)(0.10 * W);
+        len = W - head - tail;
+    }
+    const int stop = W - tail;
+    int count = 0, s = head;
+    while (count < cap) {
+        int e = s + len;
+        const bool last = e + 2 * len > stop;
+        if (last) e = stop;
+        st[count] = s;
+        en[count] = e;
+        ++count;
+        if (last || e >= stop) break;
+        s = e;
+        len *= 2;
+    }
+    return count;
+}
+
+bool odd_side_ok(int s) { return s >= 3 && s <= BS_MAX_SIDE && (s & 1); }
+
+}  // namespace
+
+extern "C" {
+
+void bs_prior_default(bs_prior *prior)
+{
+    if (!prior) return;
+    prior->lf_lo = -1.0f;
+    prior->lf_hi = 9.0f;
+    prior->ls_lo = -2.0f;
+    prior->ls_hi = 1.0f;
+    prior->sigma_xy = 0.5f;
+    prior->sigma_e = 0.3f;
+}
+
+const char *bs_last_error(void) { return g_err; }
+
+const char *bs_version(void) { return "bpshear 0.1 (sm_103a)"; }
+
+bs_status bs_render(int32_t n, const float *theta, const float *shear, const int64_t *offsets,
+                    const int32_t *side, int32_t max_side, const bs_psf *psf, int32_t n_psf,
+                    float pixel_scale, float *out, void *stream)
+{
+    if (n < 0) return fail(BS_ERR_INVALID_ARG, "bs_render: n < 0");
+    if (n == 0) return BS_OK;
+    if (!theta || !offsets || !side || !psf || !out)
+        return fail(BS_ERR_INVALID_ARG, "bs_render: NULL required pointer");
+    if (!odd_side_ok(max_side)) return fail(BS_ERR_INVALID_ARG, "bs_render: max_side %d", max_side);
+    if (n_psf != 1 && n_psf != n) return fail(BS_ERR_INVALID_ARG, "bs_render: n_psf must be 1 or n");
+    if (!(pixel_scale > 0.f)) return fail(BS_ERR_INVALID_ARG, "bs_render: pixel_scale <= 0");
+    cudaError_t e = bs::launch_render(n, theta, shear, offsets, side, max_side, psf, n_psf, pixel_scale,
+                                      out, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? BS_OK : cuda_fail(e, "bs_render");
+}
+
+size_t bs_fit_workspace_bytes(const bs_fit_args *args)
+{
+    (void)args;
+    return 256;
+}
+
+static bs_status fill_fit_params(const bs_fit_args *a, bs::FitParams &p, const char *who)
+{
+    if (!a) return fail(BS_ERR_INVALID_ARG, "%s: NULL args", who);
+    if (a->n_gal < 0) return fail(BS_ERR_INVALID_ARG, "%s: n_gal < 0", who);
+    if (!a->data || !a->offsets || !a->side || !a->psf || !a->noise_sigma)
+        return fail(BS_ERR_INVALID_ARG, "%s: NULL required input pointer", who);
+    if (a->data_dtype != BS_F32 && a->data_dtype != BS_F64)
+        return fail(BS_ERR_INVALID_ARG, "%s: data_dtype", who);
+    if (!odd_side_ok(a->max_side)) return fail(BS_ERR_INVALID_ARG, "%s: max_side %d", who, a->max_side);
+    if (a->n_psf != 1 && a->n_psf != a->n_gal) return fail(BS_ERR_INVALID_ARG, "%s: n_psf", who);
+    if (!(a->pixel_scale > 0.f)) return fail(BS_ERR_INVALID_ARG, "%s: pixel_scale", who);
+    const bs_prior &pr = a->prior;
+    if (!(pr.lf_hi > pr.lf_lo && pr.ls_hi > pr.ls_lo && pr.sigma_xy > 0.f && pr.sigma_e > 0.f))
+        return fail(BS_ERR_INVALID_ARG, "%s: prior", who);
+    std::memset(&p, 0, sizeof p);
+    p.data = a->data;
+    p.data_f64 = a->data_dtype == BS_F64;
+    p.offsets = a->offsets;
+    p.side = a->side;
+    p.psf = a->psf;
+    p.n_psf = a->n_psf;
+    p.sigma = a->noise_sigma;
+    p.gal_id = a->gal_id;
+    p.init = a->init;
+    p.n_gal = a->n_gal;
+    p.pixel_scale = a->pixel_scale;
+    p.lf_lo = pr.lf_lo;
+    p.lf_hi = pr.lf_hi;
+    p.ls_lo = pr.ls_lo;
+    p.ls_hi = pr.ls_hi;
+    p.inv_sxy2 = 1.0f / (pr.sigma_xy * pr.sigma_xy);
+    p.inv_se2 = 1.0f / (pr.sigma_e * pr.sigma_e);
+    const double sxy = pr.sigma_xy;
+    p.prior_const = (float)(-std::log((double)pr.lf_hi - pr.lf_lo) - std::log((double)pr.ls_hi - pr.ls_lo) -
+                            std::log(2.0 * kPi * sxy * sxy) - log_z_ba14(pr.sigma_e));
+    p.max_side = a->max_side;
+    p.h_max = (a->max_side + 1) / 2;
+    p.npad = 32 * ((a->max_side + 31) / 32);
+    return BS_OK;
+}
+
+bs_status bs_fit_galaxies(const bs_fit_args *a, const bs_fit_out *o, void *workspace,
+                          size_t workspace_bytes, void *stream)
+{
+    bs::FitParams p;
+    bs_status st = fill_fit_params(a, p, "bs_fit_galaxies");
+    if (st != BS_OK) return st;
+    if (!o || !o->samples) return fail(BS_ERR_INVALID_ARG, "bs_fit_galaxies: NULL samples output");
+    if (!a->init) return fail(BS_ERR_INVALID_ARG, "bs_fit_galaxies: NULL init");
+    if (a->n_chains < 1 || a->n_chains > bs::kMaxChains)
+        return fail(BS_ERR_INVALID_ARG, "bs_fit_galaxies: n_chains must be 1..%d", bs::kMaxChains);
+    if (a->n_warmup < 0 || a->n_samples < 0 || a->n_leapfrog < 1)
+        return fail(BS_ERR_INVALID_ARG, "bs_fit_galaxies: n_warmup/n_samples/n_leapfrog");
+    if (!(a->target_accept > 0.f && a->target_accept < 1.f))
+        return fail(BS_ERR_INVALID_ARG, "bs_fit_galaxies: target_accept");
+    if (!(a->jitter >= 0.f && a->jitter < 1.f)) return fail(BS_ERR_INVALID_ARG, "bs_fit_galaxies: jitter");
+    if (!workspace || workspace_bytes < bs_fit_workspace_bytes(a))
+        return fail(BS_ERR_OUT_OF_MEMORY, "bs_fit_galaxies: workspace of %zu bytes needed",
+                    bs_fit_workspace_bytes(a));
+    if (a->n_gal == 0) return BS_OK;
+    p.n_chains = a->n_chains;
+    p.n_warmup = a->n_warmup;
+    p.n_samples = a->n_samples;
+    p.n_leapfrog = a->n_leapfrog;
+    p.target_accept = a->target_accept;
+    p.jitter = a->jitter;
+    p.random_steps = a->random_steps ? 1 : 0;
+    p.seed = a->seed;
+    p.n_windows = warmup_windows(a->n_warmup, a->adapt_mass != 0, p.win_start, p.win_end, bs::kMaxWindows);
+    p.samples = o->samples;
+    p.logp = o->logp;
+    p.accepted = o->accepted;
+    p.accept_rate = o->accept_rate;
+    p.step_size = o->step_size;
+    p.inv_mass = o->inv_mass;
+    p.n_div = o->n_divergent;
+    p.status = o->status;
+    p.queue = static_cast<unsigned int *>(workspace);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    if (o->status) {
+        e = cudaMemsetAsync(o->status, 0, sizeof(int32_t) * (size_t)a->n_gal, s);
+        if (e != cudaSuccess) return cuda_fail(e, "bs_fit_galaxies: status reset");
+    }
+    e = cudaMemsetAsync(workspace, 0, sizeof(unsigned int), s);
+    if (e != cudaSuccess) return cuda_fail(e, "bs_fit_galaxies: queue reset");
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int per_sm = bs::fit_blocks_per_sm(a->n_chains, a->max_side);
+    long long grid = (long long)sms * per_sm;
+    if (grid > a->n_gal) grid = a->n_gal;
+    e = bs::launch_fit(p, (int)grid, s);
+    return e == cudaSuccess ? BS_OK : cuda_fail(e, "bs_fit_galaxies: launch");
+}
+
+bs_status bs_logpost_points(const bs_fit_args *a, int32_t n_points, const int32_t *gal_index,
+                            const float *theta, double *logp, float *grad, void *stream)
+{
+    bs::FitParams p;
+    bs_status st = fill_fit_params(a, p, "bs_logpost_points");
+    if (st != BS_OK) return st;
+    if (n_points < 0) return fail(BS_ERR_INVALID_ARG, "bs_logpost_points: n_points < 0");
+    if (n_points == 0) return BS_OK;
+    if (!gal_index || !theta) return fail(BS_ERR_INVALID_ARG, "bs_logpost_points: NULL input");
+    if (!logp && !grad) return fail(BS_ERR_INVALID_ARG, "bs_logpost_points: no output");
+    cudaError_t e = bs::launch_logpost_points(p, n_points, gal_index, theta, logp, grad,
+                                              static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? BS_OK : cuda_fail(e, "bs_logpost_points");
+}
+
+bs_status bs_chain_ess(const float *samples, int32_t n_gal, int32_t n_chains, int32_t n_samples,
+                       float *ess, float *rhat, void *stream)
+{
+    if (!samples || !ess) return fail(BS_ERR_INVALID_ARG, "bs_chain_ess: NULL pointer");
+    if (n_gal < 0 || n_chains < 1 || n_chains > bs::kMaxChains || n_samples < 4)
+        return fail(BS_ERR_INVALID_ARG, "bs_chain_ess: sizes (n_chains 1..%d, n_samples >= 4)",
+                    bs::kMaxChains);
+    cudaError_t e = bs::launch_chain_ess(samples, n_gal, n_chains, n_samples, ess, rhat,
+                                         static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? BS_OK : cuda_fail(e, "bs_chain_ess");
+}
+
+size_t bs_shear_workspace_bytes(int64_t n_gal, int32_t K)
+{
+    (void)n_gal;
+    (void)K;
+    return (size_t)(bs::shear_grid_blocks() * 4 + 4) * sizeof(double);
+}
+
+static bs_status validate_shear(const bs_shear_data *d, const char *who)
+{
+    if (!d) return fail(BS_ERR_INVALID_ARG, "%s: NULL data", who);
+    if (d->n_gal < 0 || d->K < 1) return fail(BS_ERR_INVALID_ARG, "%s: n_gal < 0 or K < 1", who);
+    if (d->n_gal > 0 && (!d->e1 || !d->e2)) return fail(BS_ERR_INVALID_ARG, "%s: NULL e1/e2", who);
+    if (d->family != BS_EPRIOR_BA14 && d->family != BS_EPRIOR_TRUNC_GAUSS)
+        return fail(BS_ERR_INVALID_ARG, "%s: family", who);
+    if (d->family == BS_EPRIOR_TRUNC_GAUSS && !(d->trunc_r > 0.f && d->trunc_r <= 1.f))
+        return fail(BS_ERR_INVALID_ARG, "%s: trunc_r", who);
+    if (!(d->sigma_e0 > 0.f)) return fail(BS_ERR_INVALID_ARG, "%s: sigma_e0", who);
+    return BS_OK;
+}
+
+bs_status bs_shear_loglike(const bs_shear_data *d, double g1, double g2, double alpha, double *out,
+                           int32_t out_on_host, void *workspace, size_t workspace_bytes, void *stream)
+{
+    bs_status st = validate_shear(d, "bs_shear_loglike");
+    if (st != BS_OK) return st;
+    if (!out) return fail(BS_ERR_INVALID_ARG, "bs_shear_loglike: NULL out");
+    const double gg = g1 * g1 + g2 * g2;
+    if (!(gg < 1.0)) return fail(BS_ERR_INVALID_ARG, "bs_shear_loglike: |g| >= 1");
+    if (!(alpha > 0.0)) return fail(BS_ERR_INVALID_ARG, "bs_shear_loglike: alpha <= 0");
+    const int grid = bs::shear_grid_blocks();
+    const size_t need = (size_t)(grid * 4 + 4) * sizeof(double);
+    if (!workspace || workspace_bytes < need)
+        return fail(BS_ERR_OUT_OF_MEMORY, "bs_shear_loglike: workspace of %zu bytes needed", need);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    double *partials = static_cast<double *>(workspace);
+    double *dev_out = out_on_host ? partials + (size_t)grid * 4 : out;
+    cudaError_t e;
+    if (d->n_gal > 0) {
+        bs::ShearLaunch L;
+        L.e1 = d->e1;
+        L.e2 = d->e2;
+        L.b = d->b;
+        L.n_gal = d->n_gal;
+        L.K = d->K;
+        L.family = d->family;
+        L.g1 = (float)g1;
+        L.g2 = (float)g2;
+        L.a2 = (float)(1.4426950408889634 / (2.0 * alpha * alpha));
+        L.kappa = d->family == BS_EPRIOR_BA14 ? 4.0f : 2.0f;
+        L.c0 = (float)(1.4426950408889634 / (2.0 * (double)d->sigma_e0 * d->sigma_e0));
+        L.r2 = d->trunc_r * d->trunc_r;
+        L.partials = partials;
+        e = bs::launch_shear(L, grid, s);
+        if (e != cudaSuccess) return cuda_fail(e, "bs_shear_loglike: launch");
+    }
+    const double ng = (double)d->n_gal;
+    const double kap = d->family == BS_EPRIOR_BA14 ? 4.0 : 2.0;
+    const double cst = kap * std::log1p(-gg) - log_z_family(d->family, alpha, d->trunc_r) +
+                       log_z_ba14(d->sigma_e0) - std::log((double)d->K);
+    const int n_part = d->n_gal > 0 ? grid : 0;
+    e = bs::launch_shear_finalize(partials, n_part, ng * cst, ng * (-2.0 * kap * g1 / (1.0 - gg)),
+                                  ng * (-2.0 * kap * g2 / (1.0 - gg)),
+                                  -ng * dlog_z_dalpha(d->family, alpha, d->trunc_r),
+                                  1.0 / (alpha * alpha * alpha), dev_out, s);
+    if (e != cudaSuccess) return cuda_fail(e, "bs_shear_loglike: finalize");
+    if (out_on_host) {
+        e = cudaMemcpyAsync(out, dev_out, 4 * sizeof(double), cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) return cuda_fail(e, "bs_shear_loglike: copy");
+        e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(e, "bs_shear_loglike: sync");
+    }
+    return BS_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Shear estimate (host): posterior mean under a uniform prior on the unit disk
+// (and a uniform alpha hyperprior), Sec. 3.3-3.4.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct ShearObjective {
+    const bs_shear_data *d;
+    const bs_estimate_cfg *cfg;
+    void *ws;
+    size_t wsb;
+    void *stream;
+    int n;
+    bs_status err = BS_OK;
+
+    // value and gradient over (g1, g2[, alpha]); false on failure
+    bool eval(const double *x, double &v, double *g)
+    {
+        const double alpha = n == 3 ? x[2] : cfg->alpha;
+        double buf[4];
+        bs_status st = bs_shear_loglike(d, x[0], x[1], alpha, buf, 1, ws, wsb, stream);
+        if (st != BS_OK) {
+            err = st;
+            return false;
+        }
+        if (cfg->allreduce) cfg->allreduce(buf, cfg->allreduce_user);
+        v = buf[0];
+        if (g) {
+            g[0] = buf[1];
+            g[1] = buf[2];
+            if (n == 3) g[2] = buf[3];
+        }
+        return true;
+    }
+    bool inside(const double *x) const
+    {
+        if (!(x[0] * x[0] + x[1] * x[1] < 1.0)) return false;
+        if (n == 3 && !(x[2] > cfg->alpha_lo && x[2] < cfg->alpha_hi)) return false;
+        return true;
+    }
+};
+
+// lower Cholesky factor of a symmetric positive-definite n x n matrix
+bool chol(const double *A, double *Lo, int n)
+{
+    for (int i = 0; i < n * n; ++i) Lo[i] = 0.0;
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j <= i; ++j) {
+            double s = A[i * n + j];
+            for (int k = 0; k < j; ++k) s -= Lo[i * n + k] * Lo[j * n + k];
+            if (i == j) {
+                if (!(s > 0.0)) return false;
+                Lo[i * n + i] = std::sqrt(s);
+            } else {
+                Lo[i * n + j] = s / Lo[j * n + j];
+            }
+        }
+    return true;
+}
+
+// Gauss-Hermite rule for weight exp(-x^2): nodes are the zeros of the
+// orthonormal Hermite polynomial p_n, bracketed by a sign scan and refined by
+// Newton's method; weights are the Christoffel numbers 1 / sum_j p_j(x)^2.
+void hermite_rule(int n, double *x, double *w)
+{
+    auto eval = [n](double t, double &pn, double &pnm1, double &sumsq) {
+        double pm = 0.0, p = std::pow(kPi, -0.25);
+        sumsq = 0.0;
+        for (int j = 0; j < n; ++j) {
+            sumsq += p * p;
+            const double pn1 = t * std::sqrt(2.0 / (j + 1)) * p - std::sqrt((double)j / (j + 1)) * pm;
+            pm = p;
+            p = pn1;
+        }
+        pn = p;
+        pnm1 = pm;
+    };
+    const double lim = std::sqrt(2.0 * n + 1.0) + 1.0;
+    const double h = lim / (200.0 * n);
+    int found = 0;
+    double t0 = -lim, p0, q0, s0;
+    eval(t0, p0, q0, s0);
+    while (found < n && t0 < lim) {
+        const double t1 = t0 + h;
+        double p1, q1, s1;
+        eval(t1, p1, q1, s1);
+        if ((p0 < 0.0) != (p1 < 0.0) || p1 == 0.0) {
+            double a = t0, b = t1, fa = p0;
+            for (int it = 0; it < 200 && b - a > 1e-15 * (1.0 + std::fabs(a)); ++it) {
+                const double m = 0.5 * (a + b);
+                double pm_, qm_, sm_;
+                eval(m, pm_, qm_, sm_);
+                if ((pm_ < 0.0) == (fa < 0.0)) { a = m; fa = pm_; } else { b = m; }
+            }
+            double r = 0.5 * (a + b);
+            for (int it = 0; it < 3; ++it) {   // Newton polish: p_n' = sqrt(2n) p_{n-1}
+                double pn, pnm1, ss;
+                eval(r, pn, pnm1, ss);
+                const double dp = std::sqrt(2.0 * n) * pnm1;
+                if (dp != 0.0) r -= pn / dp;
+            }
+            double pn, pnm1, ss;
+            eval(r, pn, pnm1, ss);
+            x[found] = r;
+            w[found] = 1.0 / ss;
+            ++found;
+        }
+        t0 = t1;
+        p0 = p1;
+    }
+}
+
+}  // namespace
+
+extern "C" bs_status bs_shear_estimate(const bs_shear_data *d, const bs_estimate_cfg *cfg, double *mean,
+                                       double *cov, void *workspace, size_t workspace_bytes, void *stream)
+{
+    bs_status st = validate_shear(d, "bs_shear_estimate");
+    if (st != BS_OK) return st;
+    if (!cfg || !mean) return fail(BS_ERR_INVALID_ARG, "bs_shear_estimate: NULL cfg/mean");
+    if (cfg->n_gh < 1 || cfg->n_gh > 32) return fail(BS_ERR_INVALID_ARG, "bs_shear_estimate: n_gh 1..32");
+    const int n = cfg->free_alpha ? 3 : 2;
+    if (cfg->free_alpha && !(cfg->alpha_lo < cfg->alpha && cfg->alpha < cfg->alpha_hi && cfg->alpha_lo > 0.0))
+        return fail(BS_ERR_INVALID_ARG, "bs_shear_estimate: alpha start outside (alpha_lo, alpha_hi)");
+    if (!(cfg->alpha > 0.0)) return fail(BS_ERR_INVALID_ARG, "bs_shear_estimate: alpha <= 0");
+    ShearObjective f{d, cfg, workspace, workspace_bytes, stream, n};
+    double x[3] = {0.0, 0.0, cfg->alpha}, g[3], v;
+    if (!f.eval(x, v, g)) return f.err;
+
+    auto hessian = [&](const double *xc, double *H) -> bool {
+        for (int j = 0; j < n; ++j) {
+            const double h = 1e-5;
+            double xp[3] = {xc[0], xc[1], xc[2]}, xm[3] = {xc[0], xc[1], xc[2]}, gp[3], gm[3], vv;
+            xp[j] += h;
+            xm[j] -= h;
+            if (!f.eval(xp, vv, gp) || !f.eval(xm, vv, gm)) return false;
+            for (int i = 0; i < n; ++i) H[i * n + j] = (gp[i] - gm[i]) / (2.0 * h);
+        }
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < i; ++j) H[i * n + j] = H[j * n + i] = 0.5 * (H[i * n + j] + H[j * n + i]);
+        return true;
+    };
+
+    double H[9], negH[9], Lo[9];
+    for (int iter = 0; iter < 100; ++iter) {
+        if (!hessian(x, H)) return f.err;
+        for (int i = 0; i < n * n; ++i) negH[i] = -H[i];
+        double step[3] = {0, 0, 0};
+        if (chol(negH, Lo, n)) {
+            double y[3];
+            for (int i = 0; i < n; ++i) {
+                double s = g[i];
+                for (int k = 0; k < i; ++k) s -= Lo[i * n + k] * y[k];
+                y[i] = s / Lo[i * n + i];
+            }
+            for (int i = n - 1; i >= 0; --i) {
+                double s = y[i];
+                for (int k = i + 1; k < n; ++k) s -= Lo[k * n + i] * step[k];
+                step[i] = s / Lo[i * n + i];
+            }
+        } else {
+            for (int i = 0; i < n; ++i) step[i] = 1e-6 * g[i];
+        }
+        double t = 1.0, xn[3] = {x[0], x[1], x[2]}, vn = -INFINITY, gn[3] = {0, 0, 0};
+        for (int ls = 0; ls < 60; ++ls) {
+            for (int i = 0; i < n; ++i) xn[i] = x[i] + t * step[i];
+            if (f.inside(xn)) {
+                if (!f.eval(xn, vn, gn)) return f.err;
+                if (vn >= v - 1e-10 * std::fabs(v)) break;
+            }
+            t *= 0.5;
+        }
+        double dmax = 0.0;
+        for (int i = 0; i < n; ++i) {
+            dmax = std::fmax(dmax, std::fabs(t * step[i]));
+            x[i] = xn[i];
+            g[i] = gn[i];
+        }
+        v = vn;
+        if (dmax < 1e-12) break;
+    }
+    if (!hessian(x, H)) return f.err;
+    // Laplace covariance Sigma = (-H)^-1 and its Cholesky factor
+    for (int i = 0; i < n * n; ++i) negH[i] = -H[i];
+    if (!chol(negH, Lo, n)) return fail(BS_ERR_UNSUPPORTED, "bs_shear_estimate: posterior not log-concave at the mode");
+    double Linv[9] = {0};
+    for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n; ++i) {
+            double s = (i == j) ? 1.0 : 0.0;
+            for (int k = j; k < i; ++k) s -= Lo[i * n + k] * Linv[k * n + j];
+            Linv[i * n + j] = (i < j) ? 0.0 : s / Lo[i * n + i];
+        }
+    double Sig[9], Lc[9];
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            double s = 0.0;
+            for (int k = 0; k < n; ++k) s += Linv[k * n + i] * Linv[k * n + j];
+            Sig[i * n + j] = s;
+        }
+    if (!chol(Sig, Lc, n)) return fail(BS_ERR_UNSUPPORTED, "bs_shear_estimate: covariance");
+    const int q = cfg->n_gh;
+    double gx[32], gw[32];
+    hermite_rule(q, gx, gw);
+    int total = 1;
+    for (int i = 0; i < n; ++i) total *= q;
+    std::vector<double> lw(total), th((size_t)total * 3);
+    double lmax = -INFINITY;
+    for (int j = 0; j < total; ++j) {
+        int r = j;
+        double z[3] = {0, 0, 0}, logw = 0.0, zz = 0.0;
+        for (int i = 0; i < n; ++i) {
+            const int a = r % q;
+            r /= q;
+            z[i] = gx[a];
+            logw += std::log(gw[a]);
+            zz += z[i] * z[i];
+        }
+        double *tj = &th[(size_t)j * 3];
+        tj[2] = cfg->alpha;
+        for (int i = 0; i < n; ++i) {
+            double s = x[i];
+            for (int k = 0; k <= i; ++k) s += std::sqrt(2.0) * Lc[i * n + k] * z[k];
+            tj[i] = s;
+        }
+        if (!f.inside(tj)) {
+            lw[j] = -INFINITY;
+            continue;
+        }
+        double vj;
+        if (!f.eval(tj, vj, nullptr)) return f.err;
+        lw[j] = logw + (vj - v) + zz;
+        if (lw[j] > lmax) lmax = lw[j];
+    }
+    double wsum = 0.0, m[3] = {0, 0, 0};
+    for (int j = 0; j < total; ++j) {
+        const double wj = std::exp(lw[j] - lmax);
+        wsum += wj;
+        for (int i = 0; i < n; ++i) m[i] += wj * th[(size_t)j * 3 + i];
+    }
+    for (int i = 0; i < 3; ++i) mean[i] = (i < n) ? m[i] / wsum : cfg->alpha;
+    if (cov) {
+        for (int i = 0; i < 9; ++i) cov[i] = 0.0;
+        for (int j = 0; j < total; ++j) {
+            const double wj = std::exp(lw[j] - lmax) / wsum;
+            for (int a = 0; a < n; ++a)
+                for (int c = 0; c < n; ++c)
+                    cov[a * 3 + c] += wj * (th[(size_t)j * 3 + a] - mean[a]) * (th[(size_t)j * 3 + c] - mean[c]);
+        }
+    }
+    return BS_OK;
+}

@@ -1,0 +1,694 @@
+// Image sampling phase on sm_103a: per-galaxy HMC on the interim posterior
+// (Sec. 3.3; Eq. interim-post = Eq. likelihood-pixels x Eq. interim-prior).
+//
+// Layout.  A persistent CTA takes one galaxy at a time from an atomic work
+// queue and runs its n_chains chains, one warp per chain.  Per galaxy the CTA
+// stages in shared memory, once:
+//   Dt[u][v] = (sqrt(w_u)/N) DFT(d)(u, v)          (data spectrum)
+//   Tt[u][v] = (sqrt(w_u)/N) PSF(|k|) sinc(kx p/2) sinc(ky p/2)
+// on the half plane u = 0..c (c = (N-1)/2), v = -c..c, with w_0 = 1 and
+// w_u = 2 for u > 0 (the other half is the complex conjugate: d and the
+// model are real).  Lane l owns the columns v = l + 32 j - c, j < NC.
+//
+// Evaluation.  The model spectrum M(k) (Sec. 3.3 forward model: exponential
+// profile (1 + r0^2 k^T S^2 k)^{-3/2}, PSF and pixel transfer, centroid
+// phase) is formed point by point; since the model image is the inverse DFT
+// of M on the stamp's periodic grid, Parseval gives
+//   chi^2 = sum_pixels (d - m)^2 = sum_half |Dt - Mt|^2,
+//   d chi^2/d theta = -2 sum_half Re[conj(Dt - Mt) dMt/dtheta],
+// i.e. the residual's adjoint DFT is Dt - Mt exactly, and the per-evaluation
+// cost is one pass over the half plane instead of two O(N^3) transforms.
+// The gradient needs seven sums, accumulated per lane in FP32 and reduced
+// with an xor butterfly (identical bits in all lanes, so the warp-replicated
+// chain state stays uniform); chi^2 is accumulated with compensated FP32 per
+// lane and finished in FP64 at the warp total.
+//
+// Sampler (same algorithm as the oracle, written independently): Philox4x64-10
+// keyed by (seed, galaxy_id * n_chains + chain); fixed-L or random-L HMC with
+// a diagonal metric; dual averaging of the step size (Hoffman & Gelman 2014,
+// gamma 0.05, t0 10, kappa 0.75); Stan-style windowed metric adaptation; a
+// doubling/halving step-size search at the start and after each window.
+#include <cmath>
+#include <cstdio>
+
+#include "bs_device.cuh"
+#include "bs_internal.h"
+
+namespace bs {
+
+namespace {
+
+struct GalCtx {
+    int N, H, c, NC;
+    float dk;      // 2 pi / (N p)
+    float p;       // pixel scale
+    float invN;
+    float inv_b;   // 1 / sigma^2
+};
+
+struct SmemView {
+    float2 *Dt;    // [h_max][npad]
+    float *Tt;     // [h_max][npad]
+    float2 *G;     // [max_side][h_max], setup scratch
+    float2 *tw;    // [max_side]
+};
+
+__device__ __forceinline__ SmemView smem_view(unsigned char *base, int h_max, int npad, int max_side)
+{
+    SmemView v;
+    v.Dt = reinterpret_cast<float2 *>(base);
+    v.Tt = reinterpret_cast<float *>(v.Dt + (size_t)h_max * npad);
+    v.G = reinterpret_cast<float2 *>(v.Tt + (size_t)h_max * npad);
+    v.tw = v.G + (size_t)max_side * h_max;
+    return v;
+}
+
+// (x/2)^nu K_nu(x) from K_nu(x) = int_0^inf exp(-x cosh t) cosh(nu t) dt by the
+// trapezoidal rule (step 1/4); the factor (x/2)^nu is folded into the
+// exponent so the integrand stays bounded for small x.
+__device__ float half_x_pow_knu(float nu, float x)
+{
+    const float lx = logf(0.5f * x);
+    const float h = 0.25f;
+    float sum = 0.5f * expf(-x + nu * lx);
+    for (int j = 1; j < 400; ++j) {
+        const float t = j * h;
+        const float ch = coshf(t);
+        const float a = -x * ch;
+        const float term = 0.5f * (expf(a + nu * (lx + t)) + expf(a + nu * (lx - t)));
+        sum += term;
+        if (x * ch > nu * t + 40.f && term <= 1e-9f * sum) break;
+    }
+    return sum * h;
+}
+
+// Transform of the unit-flux PSF at |k| (1/arcsec).
+__device__ float psf_transfer(const bs_psf &ps, float k)
+{
+    if (ps.kind == BS_PSF_GAUSSIAN) {
+        const float s = ps.fwhm * (1.0f / 2.3548200450309493f);
+        return expf(-0.5f * k * k * s * s);
+    }
+    // Moffat: (2 / Gamma(beta - 1)) (x/2)^(beta-1) K_(beta-1)(x), x = k rd
+    const float beta = ps.beta;
+    const float rd = ps.fwhm / (2.0f * sqrtf(exp2f(1.0f / beta) - 1.0f));
+    const float x = k * rd;
+    if (x == 0.0f) return 1.0f;
+    const float nu = beta - 1.0f;
+    return 2.0f / tgammaf(nu) * half_x_pow_knu(nu, x);
+}
+
+// sin(pi x) / (pi x)
+__device__ __forceinline__ float sincpi(float x)
+{
+    return x == 0.0f ? 1.0f : sinpif(x) / (3.14159265358979f * x);
+}
+
+__device__ __forceinline__ float load_pix(const void *data, int f64, int64_t idx)
+{
+    return f64 ? (float)__ldg(static_cast<const double *>(data) + idx)
+               : __ldg(static_cast<const float *>(data) + idx);
+}
+
+// A stamp side the shared-memory layout of this launch can hold.
+__device__ __forceinline__ bool side_ok(const FitParams &P, int N)
+{
+    return N >= 3 && N <= P.max_side && (N & 1);
+}
+
+// Stage the galaxy's data spectrum and transfer table (all threads of the CTA).
+// The caller has checked side_ok.
+__device__ void setup_galaxy(const FitParams &P, int gal, const SmemView &sm, GalCtx &gc)
+{
+    const int N = P.side[gal];
+    const int c = (N - 1) / 2;
+    const int H = c + 1;
+    const int npad = P.npad;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    gc.N = N;
+    gc.H = H;
+    gc.c = c;
+    gc.NC = (N + 31) / 32;
+    gc.p = P.pixel_scale;
+    gc.dk = 6.283185307179586f / ((float)N * P.pixel_scale);
+    gc.invN = 1.0f / (float)N;
+    const float sig = P.sigma[gal];
+    gc.inv_b = 1.0f / (sig * sig);
+
+    const int64_t off = P.offsets[gal];
+    for (int m = tid; m < N; m += nth) {
+        float s, co;
+        sincospif(2.0f * (float)m / (float)N, &s, &co);
+        sm.tw[m] = make_float2(co, s);   // exp(+2 pi i m / N)
+    }
+    __syncthreads();
+    // rows: G[iy][u] = sum_ix d[iy][ix] exp(-2 pi i u (ix - c) / N)
+    for (int o = tid; o < N * H; o += nth) {
+        const int iy = o / H, u = o - iy * H;
+        int idx = (int)(((long long)(N - u) * c) % N);   // -u c mod N
+        float re = 0.f, im = 0.f;
+        const int64_t rowoff = off + (int64_t)iy * N;
+        for (int ix = 0; ix < N; ++ix) {
+            const float d = load_pix(P.data, P.data_f64, rowoff + ix);
+            const float2 t = sm.tw[idx];
+            re = fmaf(d, t.x, re);
+            im = fmaf(-d, t.y, im);
+            idx += u;
+            if (idx >= N) idx -= N;
+        }
+        sm.G[iy * H + u] = make_float2(re, im);
+    }
+    __syncthreads();
+    // columns + scaling + transfer
+    const bs_psf ps = P.psf[P.n_psf == 1 ? 0 : gal];
+    const float sqrt2 = 1.41421356237309515f;
+    for (int o = tid; o < H * npad; o += nth) {
+        const int u = o / npad, vi = o - u * npad;
+        float2 Dv = make_float2(0.f, 0.f);
+        float Tv = 0.f;
+        if (vi < N) {
+            const int v = vi - c;
+            const int vm = ((v % N) + N) % N;
+            int idx = (int)(((long long)(N - vm) * c) % N);   // -v c mod N
+            float re = 0.f, im = 0.f;
+            for (int iy = 0; iy < N; ++iy) {
+                const float2 gv = sm.G[iy * H + u];
+                const float2 t = sm.tw[idx];
+                // gv * conj(t)
+                re = fmaf(gv.x, t.x, fmaf(gv.y, t.y, re));
+                im = fmaf(gv.y, t.x, fmaf(-gv.x, t.y, im));
+                idx += vm;
+                if (idx >= N) idx -= N;
+            }
+            const float scale = (u == 0 ? 1.0f : sqrt2) * gc.invN;
+            Dv = make_float2(re * scale, im * scale);
+            const float kx = u * gc.dk, ky = v * gc.dk;
+            Tv = scale * psf_transfer(ps, sqrtf(kx * kx + ky * ky)) * sincpi((float)u * gc.invN) *
+                 sincpi((float)v * gc.invN);
+        }
+        sm.Dt[o] = Dv;
+        sm.Tt[o] = Tv;
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ bool in_support(const FitParams &P, const float th[6])
+{
+    const float E = th[2] * th[2] + th[3] * th[3];
+    return th[0] > P.lf_lo && th[0] < P.lf_hi && th[1] > P.ls_lo && th[1] < P.ls_hi && E < 1.0f;
+}
+
+// Log posterior (if want_ll) and gradient at th, warp-cooperative.
+template <int NC>
+__device__ __forceinline__ double eval_logpost(const FitParams &P, const GalCtx &gc,
+                                               const float2 *__restrict__ Dt,
+                                               const float *__restrict__ Tt, const float vcol[NC],
+                                               const float th[6], float g[6], bool want_ll)
+{
+    const int lane = threadIdx.x & 31;
+    const float F = exp10f(th[0]);
+    const float r0 = exp10f(th[1]) * (1.0f / kHlrOverR0);
+    const float r02 = r0 * r0;
+    const float e1 = th[2], e2 = th[3];
+    const float E = e1 * e1 + e2 * e2;
+    const float Pq = 1.0f / (1.0f - E);
+    const float al = r02 * (1.0f + E + 2.0f * e1) * Pq;   // coefficient of kx^2 in r0^2 q
+    const float be = r02 * (1.0f + E - 2.0f * e1) * Pq;   // ky^2
+    const float ga = r02 * 4.0f * e2 * Pq;                // kx ky
+    const float F2 = F * F;
+    const float dk = gc.dk;
+
+    float exr, exi;                                        // exp(-2 pi i dx / N)
+    sincospif(-2.0f * th[4] * gc.invN, &exi, &exr);
+    float Yr[NC], Yi[NC], cst[NC], gky[NC], ky[NC];
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+        float s, co;
+        sincospif(-2.0f * th[5] * vcol[j] * gc.invN, &s, &co);   // exp(-2 pi i v dy / N)
+        Yr[j] = F * co;
+        Yi[j] = F * s;
+        ky[j] = vcol[j] * dk;
+        cst[j] = fmaf(be * ky[j], ky[j], 1.0f);
+        gky[j] = ga * ky[j];
+    }
+    float Xr = 1.0f, Xi = 0.0f;
+    float Sa = 0.f, Swkx2 = 0.f, Sbkx = 0.f;
+    float Wc[NC], Wkx[NC], Bc[NC];
+#pragma unroll
+    for (int j = 0; j < NC; ++j) { Wc[j] = 0.f; Wkx[j] = 0.f; Bc[j] = 0.f; }
+    float chi_hi = 0.f, chi_lo = 0.f;
+    const int npad = P.npad;
+    const float2 *Drow = Dt + lane;
+    const float *Trow = Tt + lane;
+    for (int u = 0; u < gc.H; ++u) {
+        const float kx = (float)u * dk;
+        const float kx2 = kx * kx;
+        const float akx2 = al * kx2;
+#pragma unroll
+        for (int j = 0; j < NC; ++j) {
+            const float2 D = Drow[32 * j];
+            const float T = Trow[32 * j];
+            const float s = fmaf(gky[j], kx, akx2 + cst[j]);      // 1 + r0^2 q(k)
+            const float rs = rsqrtf(s);
+            const float rs2 = rs * rs;
+            const float A = T * rs2 * rs;                         // |M| / F
+            const float Pr = Xr * Yr[j] - Xi * Yi[j];             // F exp(-i k.delta)
+            const float Pi = Xr * Yi[j] + Xi * Yr[j];
+            const float zr = fmaf(D.x, Pr, D.y * Pi);             // conj(D) * phase
+            const float zi = fmaf(D.x, Pi, -D.y * Pr);
+            const float a = A * fmaf(-A, F2, zr);                 // Re conj(D - M) M
+            const float b = A * zi;                               // Im conj(D - M) M
+            const float w = a * rs2;                              // a / s
+            Sa += a;
+            Wc[j] += w;
+            Wkx[j] = fmaf(w, kx, Wkx[j]);
+            Swkx2 = fmaf(w, kx2, Swkx2);
+            Bc[j] += b;
+            Sbkx = fmaf(b, kx, Sbkx);
+            if (want_ll) {
+                const float Rr = fmaf(-A, Pr, D.x);
+                const float Ri = fmaf(-A, Pi, D.y);
+                comp_add(chi_hi, chi_lo, fmaf(Rr, Rr, Ri * Ri));
+            }
+        }
+        const float nXr = Xr * exr - Xi * exi;
+        const float nXi = Xr * exi + Xi * exr;
+        Xr = nXr;
+        Xi = nXi;
+        Drow += npad;
+        Trow += npad;
+    }
+    float Sw = 0.f, Swky2 = 0.f, Swkxky = 0.f, Sbky = 0.f;
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+        Sw += Wc[j];
+        Swky2 = fmaf(ky[j] * ky[j], Wc[j], Swky2);
+        Swkxky = fmaf(ky[j], Wkx[j], Swkxky);
+        Sbky = fmaf(ky[j], Bc[j], Sbky);
+    }
+    Sa = warp_sum(Sa);
+    Sw = warp_sum(Sw);
+    Swkx2 = warp_sum(Swkx2);
+    Swky2 = warp_sum(Swky2);
+    Swkxky = warp_sum(Swkxky);
+    Sbkx = warp_sum(Sbkx);
+    Sbky = warp_sum(Sbky);
+
+    const float ib = gc.inv_b;
+    const float P2 = Pq * Pq;
+    // derivatives of the quadratic-form coefficients with respect to e1, e2
+    const float da1 = r02 * ((2.0f * e1 + 2.0f) * Pq + (1.0f + E + 2.0f * e1) * 2.0f * e1 * P2);
+    const float da2 = r02 * (2.0f * e2 * Pq + (1.0f + E + 2.0f * e1) * 2.0f * e2 * P2);
+    const float db1 = r02 * ((2.0f * e1 - 2.0f) * Pq + (1.0f + E - 2.0f * e1) * 2.0f * e1 * P2);
+    const float db2 = r02 * (2.0f * e2 * Pq + (1.0f + E - 2.0f * e1) * 2.0f * e2 * P2);
+    const float dg1 = r02 * 8.0f * e1 * e2 * P2;
+    const float dg2 = r02 * (4.0f * Pq + 8.0f * e2 * e2 * P2);
+    g[0] = kLn10 * Sa * ib;
+    g[1] = -3.0f * kLn10 * (Sa - Sw) * ib;
+    g[2] = -1.5f * (da1 * Swkx2 + db1 * Swky2 + dg1 * Swkxky) * ib - 4.0f * e1 * Pq - e1 * P.inv_se2;
+    g[3] = -1.5f * (da2 * Swkx2 + db2 * Swky2 + dg2 * Swkxky) * ib - 4.0f * e2 * Pq - e2 * P.inv_se2;
+    g[4] = gc.p * Sbkx * ib - th[4] * P.inv_sxy2;
+    g[5] = gc.p * Sbky * ib - th[5] * P.inv_sxy2;
+    if (!want_ll) return 0.0;
+    const double chi2 = warp_sum_comp(chi_hi, chi_lo);
+    const float lprior = P.prior_const - 0.5f * (th[4] * th[4] + th[5] * th[5]) * P.inv_sxy2 +
+                         2.0f * log1pf(-E) - 0.5f * E * P.inv_se2;
+    return -0.5 * chi2 * (double)ib + (double)lprior;
+}
+
+__device__ __forceinline__ void box_muller(const float u[8], float z[6])
+{
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const float r = sqrtf(-2.0f * logf(u[2 * j]));
+        float s, co;
+        sincospif(2.0f * u[2 * j + 1], &s, &co);
+        z[2 * j] = r * co;
+        z[2 * j + 1] = r * s;
+    }
+}
+
+__device__ __forceinline__ double kinetic(const float pm[6], const float im[6])
+{
+    double k = 0.0;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) k += (double)(im[i] * pm[i] * pm[i]);
+    return 0.5 * k;
+}
+
+enum { MODE_INIT = 0, MODE_SEARCH = 1, MODE_STEP = 2 };
+
+template <int NC>
+__device__ void run_chain(const FitParams &P, const GalCtx &gc, const SmemView &sm, int gal,
+                          int chain)
+{
+    const int lane = threadIdx.x & 31;
+    const int C = P.n_chains, W = P.n_warmup, S = P.n_samples, L = P.n_leapfrog;
+    const uint64_t gid = P.gal_id ? P.gal_id[gal] : (uint64_t)gal;
+    const uint64_t key = gid * (uint64_t)C + (uint64_t)chain;
+    float vcol[NC];
+#pragma unroll
+    for (int j = 0; j < NC; ++j) vcol[j] = (float)(lane + 32 * j - gc.c);
+
+    float th[6], thl[6], g[6], im[6];
+    const float *ini = P.init + ((size_t)gal * C + chain) * 6;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        th[i] = ini[i];
+        thl[i] = 0.f;
+        g[i] = 0.f;
+        im[i] = 1.f;
+    }
+    double lp = -INFINITY;
+    float eps = 1.0f;
+    float da_mu = 0.f, da_hbar = 0.f, da_lebar = 0.f;
+    int da_m = 0;
+    int wn = 0, wi = 0;
+    float wmean[6], wm2[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) { wmean[i] = 0.f; wm2[i] = 0.f; }
+    int s_idx = 0, s_t = 0, s_dir = 0;
+    float s_eps = 1.0f;
+    int it = 0;
+    float asum = 0.f;
+    int ndiv = 0;
+    int mode = MODE_INIT;
+    const double thr_search = -0.22314355131420976;   // ln 0.8
+    const size_t chain_row = ((size_t)gal * C + chain) * (size_t)S;
+
+    if (W + S == 0) mode = -1;
+    while (mode >= 0) {
+        float u[8];
+        float eps_use = 0.f;
+        int nst = 1;
+        if (mode == MODE_SEARCH) {
+            uniforms8(P.seed, key, (uint64_t)s_idx, 1ull, (uint64_t)s_t, u);
+            eps_use = s_eps;
+        } else if (mode == MODE_STEP) {
+            uniforms8(P.seed, key, (uint64_t)it, 0ull, 0ull, u);
+            eps_use = eps;
+            if (P.random_steps) {
+                // L_i = 1 + floor(u7 L), in integers: u7 = (2j + 1) 2^-25
+                const unsigned twoj1 = (unsigned)(u[7] * 33554432.0f);
+                nst = 1 + (int)(((unsigned long long)twoj1 * (unsigned)L) >> 25);
+            } else {
+                nst = L;
+                eps_use = eps * (1.0f + P.jitter * (2.0f * u[7] - 1.0f));
+            }
+        }
+        float pm[6];
+        if (mode == MODE_INIT) {
+#pragma unroll
+            for (int i = 0; i < 6; ++i) pm[i] = 0.f;
+        } else {
+            float z[6];
+            box_muller(u, z);
+#pragma unroll
+            for (int i = 0; i < 6; ++i) pm[i] = z[i] / sqrtf(im[i]);
+        }
+        const double H0 = -lp + kinetic(pm, im);
+        float tp[6], tpl[6], gp[6];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) { tp[i] = th[i]; tpl[i] = thl[i]; gp[i] = g[i]; }
+        double lpp = lp;
+        bool ok = true;
+        for (int l = 0; l < nst; ++l) {
+            const float he = 0.5f * eps_use;
+#pragma unroll
+            for (int i = 0; i < 6; ++i) pm[i] = fmaf(he, gp[i], pm[i]);
+#pragma unroll
+            for (int i = 0; i < 6; ++i) {
+                // compensated position update (hi, lo) += eps m p
+                const float d = fmaf(eps_use * im[i], pm[i], tpl[i]);
+                float s, e;
+                two_sum(tp[i], d, s, e);
+                tp[i] = s;
+                tpl[i] = e;
+            }
+            if (!in_support(P, tp)) { ok = false; break; }
+            const double v = eval_logpost<NC>(P, gc, sm.Dt, sm.Tt, vcol, tp, gp, l == nst - 1);
+            if (l == nst - 1) lpp = v;
+#pragma unroll
+            for (int i = 0; i < 6; ++i) pm[i] = fmaf(he, gp[i], pm[i]);
+        }
+        if (mode == MODE_INIT) {
+#pragma unroll
+            for (int i = 0; i < 6; ++i) { th[i] = tp[i]; thl[i] = tpl[i]; g[i] = gp[i]; }
+            lp = ok ? lpp : -INFINITY;
+            if (!isfinite(lp) && lane == 0 && P.status) P.status[gal] = 1;
+            mode = MODE_SEARCH;
+            s_idx = 0;
+            s_t = 0;
+            s_eps = 1.0f;
+            continue;
+        }
+        double dH = INFINITY;
+        if (ok) {
+            dH = (-lpp + kinetic(pm, im)) - H0;
+            if (!isfinite(dH) || dH > 1000.0) ok = false;
+        }
+        if (mode == MODE_SEARCH) {
+            const double la = ok ? -dH : -INFINITY;
+            const bool good = la > thr_search;
+            bool done = false;
+            if (s_t == 0)
+                s_dir = good ? 1 : -1;
+            else if ((s_dir > 0 && !good) || (s_dir < 0 && good))
+                done = true;
+            if (s_t == 60) done = true;
+            if (!done) {
+                ++s_t;
+                s_eps = s_dir > 0 ? 2.0f * s_eps : 0.5f * s_eps;
+                continue;
+            }
+            eps = s_eps;
+            da_mu = logf(10.0f * eps);
+            da_hbar = 0.f;
+            da_lebar = 0.f;
+            da_m = 0;
+            mode = MODE_STEP;
+            if (it >= W + S) mode = -1;
+            continue;
+        }
+        // ---- transition at iteration `it`
+        const float a = ok ? (dH < 0.0 ? 1.0f : expf((float)-dH)) : 0.0f;
+        const bool acc = ok && ((double)logf(u[6]) < -dH);
+        if (acc) {
+#pragma unroll
+            for (int i = 0; i < 6; ++i) { th[i] = tp[i]; thl[i] = tpl[i]; g[i] = gp[i]; }
+            lp = lpp;
+        }
+        if (it < W) {
+            // dual averaging
+            da_m += 1;
+            const float m = (float)da_m;
+            const float eta = 1.0f / (m + 10.0f);
+            da_hbar = (1.0f - eta) * da_hbar + eta * (P.target_accept - a);
+            const float le = da_mu - sqrtf(m) * 20.0f * da_hbar;
+            const float xe = powf(m, -0.75f);
+            da_lebar = xe * le + (1.0f - xe) * da_lebar;
+            eps = expf(le);
+            if (wi < P.n_windows && it >= P.win_start[wi] && it < P.win_end[wi]) {
+                ++wn;
+                const float inv_n = 1.0f / (float)wn;
+#pragma unroll
+                for (int i = 0; i < 6; ++i) {
+                    const float x = th[i] + thl[i];
+                    const float d = x - wmean[i];
+                    wmean[i] = fmaf(d, inv_n, wmean[i]);
+                    wm2[i] = fmaf(d, x - wmean[i], wm2[i]);
+                }
+            }
+            if (wi < P.n_windows && it == P.win_end[wi] - 1) {
+                const float n = (float)wn;
+#pragma unroll
+                for (int i = 0; i < 6; ++i) {
+                    const float var = wm2[i] / (n - 1.0f);
+                    im[i] = (n / (n + 5.0f)) * var + 1e-3f * (5.0f / (n + 5.0f));
+                    wmean[i] = 0.f;
+                    wm2[i] = 0.f;
+                }
+                wn = 0;
+                mode = MODE_SEARCH;
+                s_idx = wi + 1;
+                s_t = 0;
+                s_eps = eps;
+                ++wi;
+            }
+            if (it == W - 1) eps = expf(da_lebar);
+        } else {
+            const int s = it - W;
+            asum += a;
+            ndiv += ok ? 0 : 1;
+            float v = th[0] + thl[0];
+#pragma unroll
+            for (int i = 1; i < 6; ++i)
+                if (lane == i) v = th[i] + thl[i];
+            if (lane < 6) P.samples[((size_t)lane * P.n_gal * C) * S + chain_row + s] = v;
+            if (lane == 6 && P.logp) P.logp[chain_row + s] = (float)lp;
+            if (lane == 7 && P.accepted) P.accepted[chain_row + s] = acc ? 1 : 0;
+        }
+        ++it;
+        if (it >= W + S && mode == MODE_STEP) mode = -1;
+    }
+    const size_t ci = (size_t)gal * C + chain;
+    if (lane == 0) {
+        if (P.accept_rate) P.accept_rate[ci] = S > 0 ? asum / (float)S : 0.f;
+        if (P.step_size) P.step_size[ci] = eps;
+        if (P.n_div) P.n_div[ci] = ndiv;
+    }
+    if (P.inv_mass && lane < 6) {
+        float v = im[0];
+#pragma unroll
+        for (int i = 1; i < 6; ++i)
+            if (lane == i) v = im[i];
+        P.inv_mass[ci * 6 + lane] = v;
+    }
+}
+
+template <int NC>
+__global__ void __launch_bounds__(256) fit_kernel(const FitParams P)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_gal;
+    const SmemView sm = smem_view(smem_raw, P.h_max, P.npad, P.max_side);
+    const int warp = threadIdx.x >> 5;
+    for (;;) {
+        if (threadIdx.x == 0) s_gal = (int)atomicAdd(P.queue, 1u);
+        __syncthreads();
+        const int gal = s_gal;
+        if (gal >= P.n_gal) break;
+        if (!side_ok(P, P.side[gal])) {     // uniform across the CTA
+            if (threadIdx.x == 0 && P.status) P.status[gal] = 2;
+            __syncthreads();
+            continue;
+        }
+        GalCtx gc;
+        setup_galaxy(P, gal, sm, gc);
+        if (warp < P.n_chains) run_chain<NC>(P, gc, sm, gal, warp);
+        __syncthreads();
+    }
+}
+
+// One CTA of 32 threads per point: stage the galaxy, then evaluate.
+template <int NC>
+__device__ void point_eval(const FitParams &P, const GalCtx &gc, const SmemView &sm,
+                           const float *theta, double *logp, float *grad)
+{
+    const int lane = threadIdx.x & 31;
+    float vcol[NC];
+#pragma unroll
+    for (int j = 0; j < NC; ++j) vcol[j] = (float)(lane + 32 * j - gc.c);
+    float th[6], g[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) th[i] = theta[i];
+    double v = -INFINITY;
+    if (in_support(P, th)) {
+        v = eval_logpost<NC>(P, gc, sm.Dt, sm.Tt, vcol, th, g, true);
+    } else {
+#pragma unroll
+        for (int i = 0; i < 6; ++i) g[i] = NAN;
+    }
+    if (lane == 0 && logp) *logp = v;
+    if (grad && lane < 6) {
+        float o = g[0];
+#pragma unroll
+        for (int i = 1; i < 6; ++i)
+            if (lane == i) o = g[i];
+        grad[lane] = o;
+    }
+}
+
+__global__ void __launch_bounds__(32) logpost_points_kernel(const FitParams P, int n_points,
+                                                            const int32_t *gal_index,
+                                                            const float *theta, double *logp,
+                                                            float *grad)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const SmemView sm = smem_view(smem_raw, P.h_max, P.npad, P.max_side);
+    for (int i = blockIdx.x; i < n_points; i += gridDim.x) {
+        const int gal = gal_index[i];
+        if (gal < 0 || gal >= P.n_gal || !side_ok(P, P.side[gal])) {
+            if (threadIdx.x == 0 && logp) logp[i] = NAN;
+            if (grad && threadIdx.x < 6) grad[(size_t)i * 6 + threadIdx.x] = NAN;
+            continue;
+        }
+        GalCtx gc;
+        setup_galaxy(P, gal, sm, gc);
+        const float *th = theta + (size_t)i * 6;
+        double *lp = logp ? logp + i : nullptr;
+        float *gr = grad ? grad + (size_t)i * 6 : nullptr;
+        switch (gc.NC) {
+            case 1: point_eval<1>(P, gc, sm, th, lp, gr); break;
+            case 2: point_eval<2>(P, gc, sm, th, lp, gr); break;
+            case 3: point_eval<3>(P, gc, sm, th, lp, gr); break;
+            default: point_eval<4>(P, gc, sm, th, lp, gr); break;
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+size_t fit_smem_bytes(int max_side)
+{
+    const int h = (max_side + 1) / 2;
+    const int npad = 32 * ((max_side + 31) / 32);
+    return (size_t)h * npad * (sizeof(float2) + sizeof(float)) + (size_t)max_side * h * sizeof(float2) +
+           (size_t)max_side * sizeof(float2);
+}
+
+namespace {
+
+// The kernel instance is chosen by the column slots per lane of the largest
+// stamp; smaller stamps of the same launch see zero-padded columns.
+using FitKernel = void (*)(const FitParams);
+
+FitKernel fit_kernel_for(int max_side)
+{
+    switch ((max_side + 31) / 32) {
+        case 1: return fit_kernel<1>;
+        case 2: return fit_kernel<2>;
+        case 3: return fit_kernel<3>;
+        default: return fit_kernel<4>;
+    }
+}
+
+}  // namespace
+
+int fit_blocks_per_sm(int n_chains, int max_side)
+{
+    int nb = 0;
+    const size_t smem = fit_smem_bytes(max_side);
+    FitKernel k = fit_kernel_for(max_side);
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, 32 * n_chains, smem) != cudaSuccess)
+        return 1;
+    return nb > 0 ? nb : 1;
+}
+
+cudaError_t launch_fit(const FitParams &p, int grid, cudaStream_t stream)
+{
+    const size_t smem = fit_smem_bytes(p.max_side);
+    FitKernel k = fit_kernel_for(p.max_side);
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, 32 * p.n_chains, smem, stream>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_logpost_points(const FitParams &p, int n_points, const int32_t *gal_index,
+                                  const float *theta, double *logp, float *grad,
+                                  cudaStream_t stream)
+{
+    const size_t smem = fit_smem_bytes(p.max_side);
+    cudaError_t e = cudaFuncSetAttribute(logpost_points_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int grid = n_points < 4096 ? n_points : 4096;
+    if (grid <= 0) return cudaSuccess;
+    logpost_points_kernel<<<grid, 32, smem, stream>>>(p, n_points, gal_index, theta, logp, grad);
+    return cudaGetLastError();
+}
+
+}  // namespace bs

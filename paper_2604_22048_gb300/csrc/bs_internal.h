@@ -1,0 +1,86 @@
+// Host/device shared definitions of the bpshear kernels (not part of the ABI).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/bpshear.h"
+
+namespace bs {
+
+constexpr int kMaxChains = 8;
+constexpr int kMaxWindows = 24;
+
+// Everything one fit launch needs, filled by the C-ABI layer.
+struct FitParams {
+    // inputs
+    const void *data;
+    int data_f64;
+    const int64_t *offsets;
+    const int32_t *side;
+    const bs_psf *psf;
+    int n_psf;
+    const float *sigma;
+    const uint64_t *gal_id;
+    const float *init;
+    int n_gal;
+    float pixel_scale;
+    // interim prior
+    float lf_lo, lf_hi, ls_lo, ls_hi, inv_sxy2, inv_se2;
+    float prior_const;   // log of the prior's normalising constants
+    // sampler
+    int n_chains, n_warmup, n_samples, n_leapfrog;
+    float target_accept, jitter;
+    int random_steps;
+    uint64_t seed;
+    int n_windows;
+    int win_start[kMaxWindows], win_end[kMaxWindows];
+    // outputs
+    float *samples;
+    float *logp;
+    uint8_t *accepted;
+    float *accept_rate;
+    float *step_size;
+    float *inv_mass;
+    int32_t *n_div;
+    int32_t *status;
+    // scheduling
+    unsigned int *queue;
+    int max_side;
+    int h_max, npad;   // shared-memory geometry for max_side
+};
+
+// Shared memory bytes per CTA for a given max stamp side.
+size_t fit_smem_bytes(int max_side);
+// Launch helpers implemented in the .cu files.
+cudaError_t launch_fit(const FitParams &p, int grid, cudaStream_t stream);
+int fit_blocks_per_sm(int n_chains, int max_side);
+cudaError_t launch_logpost_points(const FitParams &p, int n_points, const int32_t *gal_index,
+                                  const float *theta, double *logp, float *grad,
+                                  cudaStream_t stream);
+cudaError_t launch_render(int n, const float *theta, const float *shear, const int64_t *offsets,
+                          const int32_t *side, int max_side, const bs_psf *psf, int n_psf,
+                          float pixel_scale, float *out, cudaStream_t stream);
+
+struct ShearLaunch {
+    const float *e1, *e2, *b;
+    long long n_gal;
+    int K;
+    int family;
+    float g1, g2;
+    float a2;         // log2(e) / (2 alpha^2)
+    float kappa;      // 4 (BA14) or 2 (truncated Gaussian)
+    float c0;         // log2(e) / (2 sigma_e0^2)
+    float r2;         // truncation radius squared
+    double *partials; // [grid][4]
+};
+int shear_grid_blocks();
+cudaError_t launch_shear(const ShearLaunch &s, int grid, cudaStream_t stream);
+cudaError_t launch_shear_finalize(const double *partials, int n_part, double add_value,
+                                  double add_g1, double add_g2, double add_alpha,
+                                  double alpha_scale, double *out, cudaStream_t stream);
+
+cudaError_t launch_chain_ess(const float *samples, int n_gal, int n_chains, int n_samples,
+                             float *ess, float *rhat, cudaStream_t stream);
+
+}  // namespace bs

@@ -1,0 +1,230 @@
+"""GPU path vs oracle, element by element on the same seeded inputs.
+
+Tolerances (stated per test): log posterior 1e-5 relative, gradient 1e-4
+relative (of the gradient's max-norm), posterior means 1e-3 in MC-error units
+for coupled chains, shear m within 1e-4.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2604_22048_gb300 import api, synth
+from tests import datagen
+
+pytestmark = pytest.mark.gpu
+
+
+def _upload(ds, cuda, dtype=np.float32):
+    flat, offs, sides = datagen.pack(ds, dtype)
+    data = torch.from_numpy(flat).to(cuda)
+    offsets = torch.from_numpy(offs).to(cuda)
+    side = torch.from_numpy(sides).to(cuda)
+    t = ds.truth
+    psf = api.psf_table(t.psf_kind, t.psf_fwhm.astype(np.float32), t.psf_beta, device=cuda)
+    sigma = torch.from_numpy(ds.sigma.astype(np.float32)).to(cuda)
+    return flat, data, offsets, side, psf, sigma
+
+
+def _stamp(flat, offs, sides, i, dtype=np.float64):
+    N = int(sides[i])
+    return flat[offs[i]:offs[i] + N * N].astype(dtype).reshape(N, N)
+
+
+# ----------------------------------------------------------------------------- render
+
+@pytest.mark.parametrize("N,kind", [(25, "gaussian"), (53, "gaussian"), (101, "moffat"), (9, "moffat")])
+def test_render_matches_oracle(cuda, N, kind):
+    rng = np.random.default_rng(N)
+    n = 6
+    th = np.column_stack([rng.uniform(1.5, 3.5, n), np.log10(rng.uniform(0.3, 1.5, n)),
+                          rng.uniform(-0.4, 0.4, n), rng.uniform(-0.4, 0.4, n),
+                          rng.uniform(-0.5, 0.5, n), rng.uniform(-0.5, 0.5, n)])
+    g = rng.uniform(-0.05, 0.05, (n, 2))
+    fwhm = rng.uniform(0.6, 0.9, n)
+    psf = api.psf_table(kind, fwhm.astype(np.float32), 3.0, device=cuda)
+    side = torch.full((n,), N, dtype=torch.int32, device=cuda)
+    thf = torch.from_numpy(th.astype(np.float32)).to(cuda)
+    out, offs = api.render(thf, side, psf, shear=torch.from_numpy(g.astype(np.float32)).to(cuda))
+    out = out.cpu().numpy()
+    offs = offs.cpu().numpy()
+    pk = O.PSF_GAUSSIAN if kind == "gaussian" else O.PSF_MOFFAT
+    for i in range(n):
+        th32 = th[i].astype(np.float32).astype(np.float64)
+        ep = O.shear_apply(th32[2], th32[3], float(np.float32(g[i, 0])), float(np.float32(g[i, 1])))
+        t = th32.copy()
+        t[2:4] = ep
+        ref = O.render(N, 0.2, (pk, float(np.float32(fwhm[i])), 3.0), t)
+        got = out[offs[i]:offs[i] + N * N].reshape(N, N)
+        assert np.abs(got - ref).max() <= 1e-5 * np.abs(ref).max(), (i, np.abs(got - ref).max() / np.abs(ref).max())
+
+
+# ----------------------------------------------------------------------------- log posterior and gradient
+
+def _perturbed_points(ds, rng, scale):
+    n = len(ds.stamps)
+    pts = np.repeat(ds.theta, 3, axis=0)
+    pts[:, 0] += rng.normal(0, 0.02, len(pts)) * scale
+    pts[:, 1] += rng.normal(0, 0.03, len(pts)) * scale
+    pts[:, 2:4] += rng.normal(0, 0.05, (len(pts), 2)) * scale
+    pts[:, 4:6] += rng.normal(0, 0.2, (len(pts), 2)) * scale
+    return pts.astype(np.float32), np.repeat(np.arange(n), 3).astype(np.int32)
+
+
+@pytest.mark.parametrize("cfg", ["tiny_f64", "plain_f32", "ragged_moffat"])
+def test_logpost_matches_oracle(cuda, cfg):
+    if cfg == "tiny_f64":
+        truth, dt = synth.draw_plain(10, 25), np.float64
+    elif cfg == "plain_f32":
+        truth, dt = synth.draw_plain(24, 53, seed=11), np.float32
+    else:
+        truth, dt = synth.draw_ragged(12, seed=5), np.float32
+    ds = datagen.make_dataset(truth, 2)
+    flat, data, offsets, side, psf, sigma = _upload(ds, cuda, dt)
+    rng = np.random.default_rng(3)
+    pts, gi = _perturbed_points(ds, rng, 1.0)
+    lp, g = api.logpost_points(data, offsets, side, psf, sigma, torch.from_numpy(gi).to(cuda),
+                               torch.from_numpy(pts).to(cuda))
+    lp = lp.cpu().numpy()
+    g = g.cpu().numpy()
+    offs = offsets.cpu().numpy()
+    sides = side.cpu().numpy()
+    for j in range(len(pts)):
+        i = gi[j]
+        d = _stamp(flat, offs, sides, i)
+        ref, gref = O.logpost(int(sides[i]), 0.2, ds.psf[i], d, 1.0, pts[j].astype(np.float64))
+        assert abs(lp[j] - ref) <= 1e-5 * abs(ref), (j, lp[j], ref)
+        assert np.abs(g[j] - gref).max() <= 1e-4 * np.abs(gref).max(), (j, g[j], gref)
+
+
+# ----------------------------------------------------------------------------- coupled chains
+
+def _fit_both(ds, cuda, dt, cfg, ids=None):
+    flat, data, offsets, side, psf, sigma = _upload(ds, cuda, dt)
+    init = torch.from_numpy(ds.init.astype(np.float32)).to(cuda)
+    gid = None if ids is None else torch.from_numpy(np.asarray(ids, dtype=np.int64)).to(cuda)
+    res = api.fit_galaxies(data, offsets, side, psf, sigma, init, cfg, gal_id=gid)
+    torch.cuda.synchronize()
+    res = {k: (v.cpu().numpy() if v is not None else None) for k, v in res.items()}
+    return flat, offsets.cpu().numpy(), side.cpu().numpy(), res
+
+
+def test_fit_matches_oracle_tiny(cuda):
+    """10 galaxies, 25 px FP64 stamps, 2 chains x (200 warmup + 200 samples) x
+    L = 8: the chains share the Philox stream, so every chain whose accept
+    decisions agree must reproduce the oracle's draws."""
+    truth = synth.draw_plain(10, 25)
+    ds = datagen.make_dataset(truth, 2)
+    cfg = api.FitConfig(n_chains=2, n_warmup=200, n_samples=200, n_leapfrog=8, jitter=0.1,
+                        random_steps=False)
+    flat, offs, sides, res = _fit_both(ds, cuda, np.float64, cfg)
+    stamps = np.stack([_stamp(flat, offs, sides, i) for i in range(truth.n)])
+    ref = O.fit_galaxies(stamps, 1.0, datagen.psf_tuple(truth, 0), ds.init.astype(np.float32).astype(np.float64),
+                         n_warmup=200, n_samples=200, n_leapfrog=8, jitter=0.1, seed=cfg.seed,
+                         random_steps=False)
+    assert (res["status"] == 0).all()
+    coupled = (res["accepted"] == ref["accept"]).all(axis=-1)           # [n_gal, C]
+    assert coupled.mean() >= 0.8, coupled
+    s_gpu, s_ref = res["samples"], ref["samples"]
+    for i in range(truth.n):
+        for c in range(2):
+            if not coupled[i, c]:
+                continue
+            for k in range(6):
+                x, y = s_gpu[k, i, c], s_ref[k, i, c]
+                sd = y.std()
+                ess = O.ess(y[None, :])
+                mcse = sd / np.sqrt(ess)
+                assert abs(x.mean() - y.mean()) <= 1e-3 * mcse, (i, c, k, abs(x.mean() - y.mean()) / mcse)
+    np.testing.assert_allclose(res["step_size"][coupled], ref["step_size"][coupled], rtol=1e-4)
+
+
+# ----------------------------------------------------------------------------- shear stage
+
+def _ellipticity_samples(rng, n, K, spread=0.25):
+    e = rng.normal(0.0, spread, (n, K, 2))
+    r = np.hypot(e[..., 0], e[..., 1])
+    e[r > 0.9] *= (0.9 / r[r > 0.9])[:, None]
+    return e[..., 0].astype(np.float32), e[..., 1].astype(np.float32)
+
+
+@pytest.mark.parametrize("family", [O.EPRIOR_BA14, O.EPRIOR_TRUNC_GAUSS])
+@pytest.mark.parametrize("K,with_b", [(300, False), (300, True), (37, False), (1, True)])
+def test_shear_loglike_matches_oracle(cuda, family, K, with_b):
+    rng = np.random.default_rng(K + 7 * family)
+    n = 2000
+    e1, e2 = _ellipticity_samples(rng, n, K, 0.2)
+    b = rng.normal(0, 0.7, (n, K)).astype(np.float32) if with_b else None
+    plan = api.ShearPlan(torch.from_numpy(e1).to(cuda), torch.from_numpy(e2).to(cuda),
+                         None if b is None else torch.from_numpy(b).to(cuda), family=family)
+    for (g1, g2, a) in [(0.02, 0.0, 0.2), (-0.04, 0.03, 0.27), (0.0, 0.0, 0.3)]:
+        got = plan.loglike(g1, g2, a, host=True)
+        v, gr = O.shear_loglike(e1, e2, g1, g2, a, b=b, family=family)
+        assert abs(got[0] - v) <= 1e-5 * max(abs(v), n), (got[0], v)
+        assert np.abs(got[1:] - gr).max() <= 1e-4 * np.abs(gr).max() + 1e-6 * n, (got[1:], gr)
+
+
+def test_shear_empty_and_zero_weight(cuda):
+    e1 = torch.zeros((0, 8), device=cuda)
+    plan = api.ShearPlan(e1, e1.clone())
+    out = plan.loglike(0.01, 0.0, 0.2, host=True)
+    assert out[0] == 0.0
+    # truncated Gaussian: a galaxy whose samples all lie beyond R has zero likelihood
+    e = torch.full((3, 8), 0.85, device=cuda)
+    plan = api.ShearPlan(e, e.clone(), family=O.EPRIOR_TRUNC_GAUSS)
+    out = plan.loglike(0.0, 0.0, 0.2, host=True)
+    assert out[0] == -np.inf
+
+
+def test_shear_estimate_matches_oracle(cuda):
+    """+-g pairs of an ellipticity-only sample (shape noise cancels, Sec. 3.4):
+    m from the GPU path and from the oracle agree to 1e-4."""
+    rng = np.random.default_rng(5)
+    n, K = 4000, 32
+    t = synth.draw_plain(n, 25, seed=9)
+    noise = rng.normal(0, 0.05, (n, K, 2))     # same noise for both signs
+    est = {}
+    for sgn in (+1, -1):
+        g = (0.02 * sgn, 0.0)
+        ep = np.array([O.shear_apply(a, b, *g) for a, b in t.e_int])
+        e1 = (ep[:, None, 0] + noise[..., 0]).astype(np.float32)
+        e2 = (ep[:, None, 1] + noise[..., 1]).astype(np.float32)
+        plan = api.ShearPlan(torch.from_numpy(e1).to(cuda), torch.from_numpy(e2).to(cuda),
+                             family=O.EPRIOR_TRUNC_GAUSS)
+        mg, _ = plan.estimate(alpha=0.2)
+        mo, _ = O.shear_estimate(e1, e2, family=O.EPRIOR_TRUNC_GAUSS, alpha=0.2)
+        est[sgn] = (mg, mo)
+        assert np.abs(mg - mo).max() < 2e-6, (mg, mo)
+    m_gpu = (est[1][0][0] - est[-1][0][0]) / 0.04 - 1.0
+    m_ref = (est[1][1][0] - est[-1][1][0]) / 0.04 - 1.0
+    assert abs(m_gpu - m_ref) < 1e-4, (m_gpu, m_ref)
+
+
+def test_chain_ess_matches_oracle(cuda):
+    rng = np.random.default_rng(0)
+    n_gal, C, S = 5, 4, 300
+    x = np.zeros((6, n_gal, C, S))
+    for k in range(6):
+        rho = 0.15 * k - 0.2
+        e = rng.normal(size=(n_gal, C, S))
+        for s in range(1, S):
+            e[..., s] += rho * e[..., s - 1]
+        x[k] = e
+    x = x.astype(np.float32)
+    ess, rh = api.chain_ess(torch.from_numpy(x).to(cuda))
+    ess = ess.cpu().numpy()
+    rh = rh.cpu().numpy()
+    for i in range(n_gal):
+        for k in range(6):
+            ref = O.ess(x[k, i].astype(np.float64))
+            assert abs(ess[i, k] - ref) <= 2e-3 * ref, (i, k, ess[i, k], ref)
+            assert abs(rh[i, k] - O.rhat(x[k, i].astype(np.float64))) < 1e-4
+
+
+def test_bad_start_sets_status(cuda):
+    truth = synth.draw_plain(3, 25)
+    ds = datagen.make_dataset(truth, 2)
+    ds.init[1, 0, 2:4] = [0.9, 0.9]      # |e| > 1: outside the prior support
+    cfg = api.FitConfig(n_chains=2, n_warmup=20, n_samples=10, n_leapfrog=4)
+    _, _, _, res = _fit_both(ds, cuda, np.float32, cfg)
+    assert list(res["status"]) == [0, 1, 0]
