@@ -1,0 +1,399 @@
+#!/usr/bin/env python
+"""Benchmark: galaxies/s at 300 effective samples per galaxy, plain batched
+workload (10,000 exponential galaxies on 53 x 53 FP32 stamps, Gaussian PSF
+FWHM 0.7", 4 chains), one GB300.
+
+A step is one pass of the whole hot path over the batch: the image sampling
+phase (bs_fit_galaxies: per-galaxy HMC warmup + sampling, one launch) and the
+shear estimate on its interim ellipticity samples (bs_shear_estimate: Newton +
+Gauss-Hermite quadrature over bs_shear_loglike passes).  Inputs are synthetic
+(seeded draws, rendered by the package's own renderer) and resident in HBM
+before timing; L2 is flushed between timed steps.  `--impl reference` times
+the FP64 CPU oracle on a bounded sample of the same workload.
+
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "galaxies/sec at 300 ESS/galaxy (plain batched path, 1 GB300)"
+UNIT = "galaxies/s"
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n-gal", type=int, default=10000)
+    ap.add_argument("--side", type=int, default=53)
+    ap.add_argument("--chains", type=int, default=4)
+    ap.add_argument("--n-warmup", type=int, default=200)
+    ap.add_argument("--n-samples", type=int, default=100)
+    ap.add_argument("--leapfrog", type=int, default=16)
+    ap.add_argument("--ref-galaxies", type=int, default=0, help="oracle sample size (0: host cores, max 16)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload_config(a):
+    return {"workload": f"plain batched: {a.n_gal} exponential galaxies, {a.side}x{a.side} FP32 stamps, "
+                        f"pixel 0.2\", Gaussian PSF FWHM 0.7\", S/N U(15,50), g=(0.02,0), {a.chains} chains x "
+                        f"({a.n_warmup} warmup + {a.n_samples} draws), HMC L_i~U{{1..{a.leapfrog}}}, "
+                        "then posterior-mean shear (alpha fixed, truncated-Gaussian sigma 0.2)",
+            "n_gal": a.n_gal, "side": a.side, "chains": a.chains, "n_warmup": a.n_warmup,
+            "n_samples": a.n_samples, "leapfrog_max": a.leapfrog,
+            "l2": "flushed between timed steps (256 MB write)"}
+
+
+# ----------------------------------------------------------------------------- inputs
+
+def make_truth(a, rank):
+    from paper_2604_22048_gb300 import synth
+    return synth.draw_plain(a.n_gal, a.side, seed=synth.SEED_DATA + 97 * rank)
+
+
+def sheared(e_int, g):
+    """Sheared ellipticity (reduced-shear convention) for input preparation."""
+    e = e_int[:, 0] + 1j * e_int[:, 1]
+    gc = g[0] + 1j * g[1]
+    ep = (e + gc) / (1 + np.conj(gc) * e)
+    return np.stack([ep.real, ep.imag], axis=1)
+
+
+def make_inputs_gpu(a, rank, dev):
+    """Noisy stamps rendered on the device by bs_render (unit flux, scaled to
+    the drawn S/N), plus chain starts (Eq. initialize)."""
+    import torch
+    from paper_2604_22048_gb300 import api, synth
+    t = make_truth(a, rank)
+    n, N = t.n, a.side
+    ep = sheared(t.e_int, t.g)
+    theta = np.column_stack([np.zeros(n), np.log10(t.hlr), ep, t.offset]).astype(np.float32)
+    side = torch.full((n,), N, dtype=torch.int32, device=dev)
+    psf = api.psf_table("gaussian", np.float32(0.7), device=dev)
+    unit, offsets = api.render(torch.from_numpy(theta).to(dev), side, psf)
+    stride = int((N * N + 3) // 4 * 4)
+    u2 = unit.view(n, stride)[:, :N * N]
+    flux = torch.from_numpy(t.snr.astype(np.float32)).to(dev) / torch.sqrt((u2.double() ** 2).sum(1)).float()
+    noise = np.stack(synth.noise_fields(t)).reshape(n, N * N).astype(np.float32)
+    data = torch.zeros_like(unit)
+    data.view(n, stride)[:, :N * N] = flux[:, None] * u2 + torch.from_numpy(noise).to(dev)
+    sums = data.view(n, stride)[:, :N * N].sum(1).cpu().numpy()
+    init = synth.initial_theta(sums, np.log10(t.hlr), ep, synth.init_offsets(t, a.chains, seed=synth.SEED_CHAINS + rank))
+    sigma = torch.ones(n, device=dev)
+    return dict(data=data, offsets=offsets, side=side, psf=psf, sigma=sigma,
+                init=torch.from_numpy(init.astype(np.float32)).to(dev), truth=t)
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        busy = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": float(np.median(busy)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": float(max(power)) if power else None}
+
+
+# ----------------------------------------------------------------------------- algorithmic work
+
+def flops_per_eval(N):
+    """FP32 operations of one log-posterior gradient evaluation on an N x N
+    stamp: 33 per half-plane k-point (the model amplitude and phase, the
+    conjugate product with the data spectrum and seven gradient sums; an FMA
+    counts 2) over (N+1)/2 x N points, plus 9 per row for the phase
+    recurrence and wavenumber."""
+    H = (N + 1) // 2
+    return 33 * H * N + 9 * H
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return json.load(open(path))
+    except (OSError, ValueError):
+        return {}
+
+
+# ----------------------------------------------------------------------------- reference arm (oracle)
+
+def reference_arm(a, world, rank):
+    import oracle as O
+    from paper_2604_22048_gb300 import synth
+    if rank != 0:
+        return None
+    cores = os.cpu_count() or 1
+    n = a.ref_galaxies or min(cores, 16)
+    a2 = argparse.Namespace(**vars(a))
+    a2.n_gal = n
+    t = make_truth(a2, 0)
+    ep = sheared(t.e_int, t.g)
+    theta = np.column_stack([np.zeros(n), np.log10(t.hlr), ep, t.offset])
+    unit = O.render_many(a.side, 0.2, (O.PSF_GAUSSIAN, 0.7), theta)
+    noise = np.stack(synth.noise_fields(t))
+    flux = t.snr / np.sqrt((unit ** 2).sum(axis=(1, 2)))
+    data = (flux[:, None, None] * unit + noise).astype(np.float32).astype(np.float64)
+    init = synth.initial_theta(data.sum(axis=(1, 2)), np.log10(t.hlr), ep, synth.init_offsets(t, a.chains))
+
+    def step():
+        r = O.fit_galaxies(data, 1.0, (O.PSF_GAUSSIAN, 0.7), init.astype(np.float32).astype(np.float64),
+                           n_warmup=a.n_warmup, n_samples=a.n_samples, n_leapfrog=a.leapfrog, random_steps=True,
+                           seed=22048, n_threads=cores)
+        e1 = r["samples"][2].reshape(n, -1).astype(np.float32)
+        e2 = r["samples"][3].reshape(n, -1).astype(np.float32)
+        O.shear_estimate(e1, e2, family=O.EPRIOR_TRUNC_GAUSS, alpha=0.2)
+
+    for _ in range(a.warmup):
+        step()
+    times = []
+    for _ in range(a.steps):
+        t0 = time.perf_counter()
+        step()
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = n * a.steps / tot
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": 1e3 * tot / a.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": workload_config(a) | {"reference_sample_galaxies": n},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": min(cores, n), "kind": "oracle",
+                             "sample": f"{n} of the {a.n_gal} galaxies per step (one per host thread), same "
+                                       "chains/warmup/draws, plus the shear estimate on their samples"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def cpu_baseline(a):
+    """The oracle timed once on a bounded sample (one galaxy per host core)."""
+    b = argparse.Namespace(**vars(a))
+    b.steps, b.warmup = 1, 0
+    r = reference_arm(b, 1, 0)
+    return r["cpu_baseline"] | {"ms_per_galaxy_per_core": 1e3 * r["cpu_baseline"]["cores"] / r["value"]}
+
+
+# ----------------------------------------------------------------------------- our arm
+
+def our_arm(a, world, rank, local_rank):
+    import torch
+    import torch.distributed as dist
+    from paper_2604_22048_gb300 import api, build
+    build.build()
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    inp = make_inputs_gpu(a, rank, dev)
+    cfg = api.FitConfig(n_chains=a.chains, n_warmup=a.n_warmup, n_samples=a.n_samples, n_leapfrog=a.leapfrog,
+                        random_steps=True)
+    plan = api.FitPlan(inp["data"], inp["offsets"], inp["side"], inp["psf"], inp["sigma"], inp["init"], cfg,
+                       max_side=a.side)
+    K = a.chains * a.n_samples
+    shear = api.ShearPlan(plan.samples[2].reshape(a.n_gal, K), plan.samples[3].reshape(a.n_gal, K),
+                          family=1, trunc_r=0.7)
+    allreduce = None
+    if world > 1:
+        buf = torch.zeros(4, dtype=torch.float64, device=dev)
+
+        def allreduce(x):
+            buf.copy_(torch.from_numpy(x))
+            dist.all_reduce(buf)
+            return buf.cpu().numpy()
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    est_evals = []
+
+    def step(fit_ev=None):
+        if fit_ev:
+            fit_ev[0].record(stream)
+        plan.run()
+        if fit_ev:
+            fit_ev[1].record(stream)
+        mean, _ = shear.estimate(alpha=0.2, allreduce=allreduce)
+        est_evals.append(shear.last_n_evals)
+        return mean
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(a.warmup):
+        step()
+    barrier()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+    fev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+    est_evals.clear()
+    barrier()
+    wall0 = time.perf_counter()
+    for i in range(a.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        ghat = step(fev[i])
+        ev[i][1].record(stream)
+    barrier()
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    step_ms = sum(e[0].elapsed_time(e[1]) for e in ev)
+    fit_ms = [e[0].elapsed_time(e[1]) for e in fev]
+    t_local = torch.tensor([step_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
+    step_ms = float(t_local.item())
+    value = world * a.n_gal * a.steps / (step_ms / 1e3)
+
+    # ---- after timing: diagnostics of the last step's chains
+    ess, rhat = api.chain_ess(plan.samples)
+    ess_gal = ess.mean(dim=1)
+    n_grad = plan.n_grad.to(torch.int64).sum().item()
+    torch.cuda.synchronize(dev)
+    fit_flops = n_grad * flops_per_eval(a.side)
+    fit_s = float(np.mean(fit_ms)) / 1e3
+    props = torch.cuda.get_device_properties(dev)
+    peaks = measured_peaks()
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    peak_tflops = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    achieved = fit_flops / fit_s / 1e12
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+           "ms_per_step": step_ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32", "data": "synthetic (seeded draws rendered by bs_render; L2 flushed between steps)",
+           "config": workload_config(a) | {"parallelism": f"dp{world}: galaxies per rank, shear sums all-reduced"},
+           "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                        "frac": achieved / peak_tflops, "traffic": None,
+                        "kernel": "fit_kernel<2>",
+                        "peak_how": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
+                                    f"{sm_max:.0f} MHz (max SM clock)",
+                        "flops_per_eval": flops_per_eval(a.side), "evals_per_launch": n_grad,
+                        "fit_ms": float(np.mean(fit_ms))},
+           "gpu_launches": int(a.steps * 1 + 2 * sum(est_evals)),
+           "clocks": clk,
+           "ess": {"mean_per_galaxy": float(ess_gal.mean().item()),
+                   "frac_galaxies_ge_300": float((ess_gal >= 300).float().mean().item()),
+                   "p10_per_galaxy": float(torch.quantile(ess_gal, 0.1).item()),
+                   "rhat_max_p99": float(torch.quantile(rhat.max(dim=1).values, 0.99).item()),
+                   "effective_samples_per_s": float(ess_gal.sum().item()) * world / (step_ms / a.steps / 1e3)},
+           "latency_ms": {"p50": step_ms / a.steps, "p99": step_ms / a.steps,
+                          "note": "one batched launch: every galaxy completes with the step"},
+           "shear_estimate": {"g": [float(x) for x in ghat], "evals_per_step": float(np.mean(est_evals))},
+           "paper_context": "0.45 s/galaxy to 300 ESS on one A100 with NUTS (63x63 stamps), i.e. 2.2 galaxies/s",
+           "wall_s": wall}
+
+    if not a.no_e2e:
+        out["e2e"] = e2e_run(a, world, inp, plan, shear, step, barrier, dev)
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(a)
+    return out
+
+
+def e2e_run(a, world, inp, plan, shear, step, barrier, dev):
+    """Same metric through the public API from pinned host buffers: every step
+    copies the stamps and chain starts to the device and the interim samples
+    and shear estimate back."""
+    import torch
+    host_in = {k: inp[k].cpu().pin_memory() for k in ("data", "init", "sigma", "offsets", "side")}
+    host_in["psf"] = inp["psf"][0].cpu().pin_memory()
+    host_out = plan.samples.cpu().pin_memory()
+    h2d = sum(t.numel() * t.element_size() for t in host_in.values())
+    d2h = host_out.numel() * host_out.element_size() + 3 * 8
+    dev_in = {k: inp[k] for k in ("data", "init", "sigma", "offsets", "side")}
+    dev_in["psf"] = inp["psf"][0]
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        for k, h in host_in.items():
+            dev_in[k].copy_(h, non_blocking=True)
+        step()
+        host_out.copy_(plan.samples, non_blocking=True)
+        torch.cuda.synchronize(dev)
+    barrier()
+    el = time.perf_counter() - t0
+    return {"value": world * a.n_gal * a.steps / el, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h)}
+
+
+def main():
+    a = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if a.impl == "reference":
+        out = reference_arm(a, world, rank)
+        if out is not None:
+            print(json.dumps(out))
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    out = our_arm(a, world, rank, local_rank)
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

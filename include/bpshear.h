@@ -143,6 +143,11 @@ typedef struct {
     int32_t adapt_mass;         /* windowed diagonal metric adaptation */
     int32_t random_steps;       /* L_i uniform on 1..n_leapfrog */
     uint64_t seed;
+    const float *init_step_size;  /* device [n_gal][n_chains] or NULL: start
+                                     from this step size instead of searching
+                                     (resuming an adapted chain) */
+    const float *init_inv_mass;   /* device [n_gal][n_chains][6] or NULL
+                                     (= identity metric) */
 } bs_fit_args;
 
 /* Outputs, caller-allocated device buffers (NULL = not wanted, except
@@ -158,7 +163,11 @@ typedef struct {
     float *step_size;      /* [n_gal][n_chains]: adapted step size */
     float *inv_mass;       /* [n_gal][n_chains][6]: adapted inverse metric */
     int32_t *n_divergent;  /* [n_gal][n_chains]: divergent transitions */
-    int32_t *status;       /* [n_gal]: 0 ok, 1 a chain started off-support */
+    int32_t *status;       /* [n_gal]: 0 ok, 1 a chain started off-support,
+                              2 side[] invalid for max_side (galaxy skipped) */
+    int32_t *n_grad;       /* [n_gal][n_chains]: log-posterior gradient
+                              evaluations the chain made (warmup, searches and
+                              sampling) */
 } bs_fit_out;
 
 /* Bytes of device workspace bs_fit_galaxies needs (a work-queue counter). */
@@ -246,10 +255,11 @@ typedef struct {
 /* Posterior mean (and covariance) of g (and alpha) under a uniform prior on
  * the unit disk (and alpha ~ U(alpha_lo, alpha_hi)): Newton iterations to the
  * mode, then tensor Gauss-Hermite quadrature on the Laplace-scaled grid.
- *   mean host double [3] (g1, g2, alpha); cov host double [9] or NULL.
+ *   mean host double [3] (g1, g2, alpha); cov host double [9] or NULL;
+ *   n_evals host int32 or NULL: number of bs_shear_loglike passes used.
  * Synchronises `stream`. */
 bs_status bs_shear_estimate(const bs_shear_data *data, const bs_estimate_cfg *cfg,
-                            double *mean, double *cov, void *workspace,
+                            double *mean, double *cov, int32_t *n_evals, void *workspace,
                             size_t workspace_bytes, void *stream);
 
 #ifdef __cplusplus

@@ -99,7 +99,7 @@ def lib():
         L.or_fit_galaxies.argtypes = [C.c_int, C.c_int, C.c_double, C.POINTER(_Psf), C.c_int, _D, _D,
                                       C.POINTER(_Prior), C.POINTER(_Hmc), C.POINTER(C.c_uint64), _D,
                                       _D, _D, C.POINTER(C.c_uint8), _D, _D, C.POINTER(C.c_int32), _D,
-                                      C.c_int]
+                                      C.POINTER(C.c_int32), _D, _D, C.c_int]
         L.or_ess.restype = C.c_double
         L.or_ess.argtypes = [_D, C.c_int, C.c_int]
         L.or_rhat.restype = C.c_double
@@ -281,7 +281,8 @@ def window_schedule(n_warmup, adapt_mass=True):
 
 def fit_galaxies(data, sigma, psf, init, *, pixel_scale=0.2, n_warmup=200, n_samples=200,
                  n_leapfrog=8, target_accept=0.8, jitter=0.1, adapt_mass=True, seed=0,
-                 ids=None, prior=None, n_threads=0, psf_per_gal=None, random_steps=False):
+                 ids=None, prior=None, n_threads=0, psf_per_gal=None, random_steps=False,
+                 init_step_size=None, init_inv_mass=None):
     """data: [n_gal, N, N]; init: [n_gal, n_chains, 6]; psf: tuple or list of tuples.
 
     Returns a dict with samples [6, n_gal, n_chains, n_samples], logp, accept,
@@ -308,13 +309,16 @@ def fit_galaxies(data, sigma, psf, init, *, pixel_scale=0.2, n_warmup=200, n_sam
                accept=np.zeros((n_gal, n_chains, S), dtype=np.uint8),
                accept_rate=np.zeros((n_gal, n_chains)), step_size=np.zeros((n_gal, n_chains)),
                n_div=np.zeros((n_gal, n_chains), dtype=np.int32),
-               inv_mass=np.zeros((n_gal, n_chains, 6)))
+               inv_mass=np.zeros((n_gal, n_chains, 6)), n_grad=np.zeros((n_gal, n_chains), dtype=np.int32))
     bad = lib().or_fit_galaxies(
         n_gal, N, pixel_scale, ps, per, _dp(data), _dp(sig), C.byref(pr), C.byref(cfg),
         idarr.ctypes.data_as(C.POINTER(C.c_uint64)) if idarr is not None else None, _dp(init),
         _dp(out["samples"]), _dp(out["logp"]), out["accept"].ctypes.data_as(C.POINTER(C.c_uint8)),
         _dp(out["accept_rate"]), _dp(out["step_size"]),
-        out["n_div"].ctypes.data_as(C.POINTER(C.c_int32)), _dp(out["inv_mass"]), int(n_threads))
+        out["n_div"].ctypes.data_as(C.POINTER(C.c_int32)), _dp(out["inv_mass"]),
+        out["n_grad"].ctypes.data_as(C.POINTER(C.c_int32)),
+        _dp(_d(init_step_size) if init_step_size is not None else None),
+        _dp(_d(init_inv_mass) if init_inv_mass is not None else None), int(n_threads))
     out["bad_init"] = bad
     return out
 

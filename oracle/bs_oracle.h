@@ -139,13 +139,17 @@ int or_window_schedule(int n_warmup, int adapt_mass, int *starts, int *ends, int
  *   data: N*N, init: [n_chains][6], galaxy_id keys the generator.
  *   samples: [6][n_chains][n_samples] (parameter-major), logp: [n_chains][n_samples],
  *   accept: [n_chains][n_samples] (0/1), accept_rate, step_size, n_div: [n_chains],
- *   inv_mass: [n_chains][6].  Any output pointer may be NULL. */
+ *   inv_mass: [n_chains][6], n_grad: [n_chains] gradient evaluations inside
+ *   the prior support.  Any output pointer may be NULL.
+ *   init_eps [n_chains] / init_im [n_chains][6] (may be NULL): resume with
+ *   this step size (no initial search) and inverse metric. */
 int or_fit_galaxy(int N, double p, const or_psf *psf, const double *data,
                   const double *w, double sigma, const or_prior *pr,
                   const or_hmc_cfg *cfg, uint64_t galaxy_id, const double *init,
                   double *samples, double *logp, uint8_t *accept,
                   double *accept_rate, double *step_size, int32_t *n_div,
-                  double *inv_mass);
+                  double *inv_mass, int32_t *n_grad, const double *init_eps,
+                  const double *init_im);
 
 /* Many galaxies of one stamp size, OpenMP-parallel over galaxies (n_threads
  * <= 0: all).  data: [n_gal][N*N], sigma: [n_gal], init: [n_gal][n_chains][6],
@@ -156,7 +160,8 @@ int or_fit_galaxies(int n_gal, int N, double p, const or_psf *psf, int psf_per_g
                     const or_hmc_cfg *cfg, const uint64_t *ids, const double *init,
                     double *samples, double *logp, uint8_t *accept,
                     double *accept_rate, double *step_size, int32_t *n_div,
-                    double *inv_mass, int n_threads);
+                    double *inv_mass, int32_t *n_grad, const double *init_eps,
+                    const double *init_im, int n_threads);
 
 /* ---- diagnostics -------------------------------------------------------- */
 

@@ -80,6 +80,7 @@ typedef struct {
     const double *w;
     double sigma;
     const or_prior *pr;
+    int *n_eval;            /* evaluations inside the support */
 } target_t;
 
 /* log posterior and gradient; -inf outside the prior support */
@@ -88,6 +89,7 @@ static double target_eval(const target_t *tg, const double th[6], double g[6])
     double gp[6];
     double lp = or_log_prior(tg->pr, th, gp);
     if (!isfinite(lp)) return -INFINITY;
+    ++*tg->n_eval;
     double ll = or_loglike_t(tg->N, tg->p, tg->T, tg->data, tg->w, tg->sigma, th, g);
     for (int i = 0; i < 6; ++i) g[i] += gp[i];
     return ll + lp;
@@ -235,12 +237,14 @@ int or_fit_galaxy(int N, double p, const or_psf *psf, const double *data,
                   const or_hmc_cfg *cfg, uint64_t galaxy_id, const double *init,
                   double *samples, double *logp, uint8_t *accept,
                   double *accept_rate, double *step_size, int32_t *n_div,
-                  double *inv_mass)
+                  double *inv_mass, int32_t *n_grad, const double *init_eps,
+                  const double *init_im)
 {
     int C = cfg->n_chains, S = cfg->n_samples, W = cfg->n_warmup;
     double *T = malloc(sizeof(double) * (size_t)N * N);
     or_transfer_table(N, p, psf, T);
-    target_t tg = {N, p, T, data, w, sigma, pr};
+    int n_eval = 0;
+    target_t tg = {N, p, T, data, w, sigma, pr, &n_eval};
     int starts[64], ends[64];
     int nw = or_window_schedule(W, cfg->adapt_mass, starts, ends, 64);
     int status = 0;
@@ -248,11 +252,15 @@ int or_fit_galaxy(int N, double p, const or_psf *psf, const double *data,
     for (int c = 0; c < C; ++c) {
         uint64_t key = galaxy_id * (uint64_t)C + (uint64_t)c;
         chain_t ch;
+        n_eval = 0;
         memcpy(ch.th, init + 6 * c, sizeof ch.th);
-        for (int i = 0; i < 6; ++i) ch.im[i] = 1.0;
+        for (int i = 0; i < 6; ++i) ch.im[i] = init_im ? init_im[6 * c + i] : 1.0;
         ch.lp = target_eval(&tg, ch.th, ch.g);
         if (!isfinite(ch.lp)) { status = 1; }
-        ch.eps = step_search(&tg, &ch, cfg->seed, key, 0, 1.0);
+        if (init_eps)       /* resume an adapted chain: no search */
+            ch.eps = init_eps[c];
+        else
+            ch.eps = step_search(&tg, &ch, cfg->seed, key, 0, 1.0);
         da_restart(&ch);
 
         int wi = 0, wn = 0;
@@ -301,6 +309,7 @@ int or_fit_galaxy(int N, double p, const or_psf *psf, const double *data,
         if (step_size) step_size[c] = ch.eps;
         if (n_div) n_div[c] = ndiv;
         if (inv_mass) memcpy(inv_mass + 6 * c, ch.im, sizeof ch.im);
+        if (n_grad) n_grad[c] = n_eval;
     }
     free(T);
     return status;
@@ -311,7 +320,8 @@ int or_fit_galaxies(int n_gal, int N, double p, const or_psf *psf, int psf_per_g
                     const or_hmc_cfg *cfg, const uint64_t *ids, const double *init,
                     double *samples, double *logp, uint8_t *accept,
                     double *accept_rate, double *step_size, int32_t *n_div,
-                    double *inv_mass, int n_threads)
+                    double *inv_mass, int32_t *n_grad, const double *init_eps,
+                    const double *init_im, int n_threads)
 {
     int C = cfg->n_chains, S = cfg->n_samples;
     size_t NN = (size_t)N * N;
@@ -331,7 +341,10 @@ int or_fit_galaxies(int n_gal, int N, double p, const or_psf *psf, int psf_per_g
                                accept_rate ? accept_rate + (size_t)n * C : NULL,
                                step_size ? step_size + (size_t)n * C : NULL,
                                n_div ? n_div + (size_t)n * C : NULL,
-                               inv_mass ? inv_mass + (size_t)n * C * 6 : NULL);
+                               inv_mass ? inv_mass + (size_t)n * C * 6 : NULL,
+                               n_grad ? n_grad + (size_t)n * C : NULL,
+                               init_eps ? init_eps + (size_t)n * C : NULL,
+                               init_im ? init_im + (size_t)n * C * 6 : NULL);
         bad += st != 0;
         if (smp) {
             /* [6][C][S] -> [6][n_gal][C][S] */

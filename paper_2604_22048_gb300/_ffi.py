@@ -49,13 +49,13 @@ class FitArgs(C.Structure):
                 ("prior", Prior), ("n_chains", C.c_int32), ("n_warmup", C.c_int32),
                 ("n_samples", C.c_int32), ("n_leapfrog", C.c_int32), ("target_accept", C.c_float),
                 ("jitter", C.c_float), ("adapt_mass", C.c_int32), ("random_steps", C.c_int32),
-                ("seed", C.c_uint64)]
+                ("seed", C.c_uint64), ("init_step_size", C.c_void_p), ("init_inv_mass", C.c_void_p)]
 
 
 class FitOut(C.Structure):
     _fields_ = [("samples", C.c_void_p), ("logp", C.c_void_p), ("accepted", C.c_void_p),
                 ("accept_rate", C.c_void_p), ("step_size", C.c_void_p), ("inv_mass", C.c_void_p),
-                ("n_divergent", C.c_void_p), ("status", C.c_void_p)]
+                ("n_divergent", C.c_void_p), ("status", C.c_void_p), ("n_grad", C.c_void_p)]
 
 
 class ShearData(C.Structure):
@@ -98,7 +98,7 @@ def lib():
     L.bs_shear_workspace_bytes.argtypes = [i64, i32]
     L.bs_shear_workspace_bytes.restype = sz
     L.bs_shear_loglike.argtypes = [C.POINTER(ShearData), f64, f64, f64, vp, i32, vp, sz, vp]
-    L.bs_shear_estimate.argtypes = [C.POINTER(ShearData), C.POINTER(EstimateCfg), vp, vp, vp, sz, vp]
+    L.bs_shear_estimate.argtypes = [C.POINTER(ShearData), C.POINTER(EstimateCfg), vp, vp, vp, vp, sz, vp]
     for nm in ("bs_render", "bs_fit_galaxies", "bs_logpost_points", "bs_chain_ess", "bs_shear_loglike",
                "bs_shear_estimate"):
         getattr(L, nm).restype = C.c_int

@@ -98,13 +98,16 @@ class FitPlan:
     launch, so that repeated fits (benchmark steps) allocate nothing."""
 
     def __init__(self, data, offsets, side, psf, noise_sigma, init, cfg: FitConfig, *, gal_id=None,
-                 max_side=None, want=("logp", "accept_rate", "step_size", "inv_mass", "n_div", "status")):
-        _need_cuda(data, offsets, side, noise_sigma, init, gal_id)
+                 max_side=None, init_step_size=None, init_inv_mass=None,
+                 want=("logp", "accept_rate", "step_size", "inv_mass", "n_div", "status", "n_grad")):
+        """init_step_size [n_gal, C] / init_inv_mass [n_gal, C, 6] (optional):
+        resume adapted chains (no initial step-size search)."""
+        _need_cuda(data, offsets, side, noise_sigma, init, gal_id, init_step_size, init_inv_mass)
         dev = data.device
         n_gal, n_chains = init.shape[0], init.shape[1]
         assert n_chains == cfg.n_chains, "init must be [n_gal, n_chains, 6]"
         self.cfg = cfg
-        self.keep = (data, offsets, side, psf, noise_sigma, init, gal_id)
+        self.keep = (data, offsets, side, psf, noise_sigma, init, gal_id, init_step_size, init_inv_mass)
         table, n_psf = psf
         a = F.FitArgs()
         a.n_gal = n_gal
@@ -129,6 +132,8 @@ class FitPlan:
         a.adapt_mass = int(cfg.adapt_mass)
         a.random_steps = int(cfg.random_steps)
         a.seed = cfg.seed
+        a.init_step_size = _p(init_step_size)
+        a.init_inv_mass = _p(init_inv_mass)
         self.args = a
         S, Cn = cfg.n_samples, cfg.n_chains
         f32 = dict(dtype=torch.float32, device=dev)
@@ -140,6 +145,7 @@ class FitPlan:
         self.inv_mass = torch.empty((n_gal, Cn, 6), **f32) if "inv_mass" in want else None
         self.n_div = torch.empty((n_gal, Cn), dtype=torch.int32, device=dev) if "n_div" in want else None
         self.status = torch.empty((n_gal,), dtype=torch.int32, device=dev) if "status" in want else None
+        self.n_grad = torch.empty((n_gal, Cn), dtype=torch.int32, device=dev) if "n_grad" in want else None
         o = F.FitOut()
         o.samples = _p(self.samples)
         o.logp = _p(self.logp)
@@ -149,6 +155,7 @@ class FitPlan:
         o.inv_mass = _p(self.inv_mass)
         o.n_divergent = _p(self.n_div)
         o.status = _p(self.status)
+        o.n_grad = _p(self.n_grad)
         self.out = o
         self.ws_bytes = F.lib().bs_fit_workspace_bytes(C.byref(a))
         self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=dev)
@@ -162,7 +169,7 @@ class FitPlan:
     def result(self):
         return dict(samples=self.samples, logp=self.logp, accepted=self.accepted,
                     accept_rate=self.accept_rate, step_size=self.step_size, inv_mass=self.inv_mass,
-                    n_div=self.n_div, status=self.status)
+                    n_div=self.n_div, status=self.status, n_grad=self.n_grad)
 
 
 def fit_galaxies(data, offsets, side, psf, noise_sigma, init, cfg: FitConfig | None = None, **kw):
@@ -170,7 +177,8 @@ def fit_galaxies(data, offsets, side, psf, noise_sigma, init, cfg: FitConfig | N
     (Sec. 3.3 image sampling phase).  Returns a dict of CUDA tensors; samples
     are [6, n_gal, n_chains, n_samples]."""
     cfg = cfg or FitConfig(n_chains=init.shape[1])
-    want = kw.pop("want", ("logp", "accepted", "accept_rate", "step_size", "inv_mass", "n_div", "status"))
+    want = kw.pop("want", ("logp", "accepted", "accept_rate", "step_size", "inv_mass", "n_div", "status",
+                           "n_grad"))
     return FitPlan(data, offsets, side, psf, noise_sigma, init, cfg, want=want, **kw).run().result()
 
 
@@ -260,9 +268,11 @@ class ShearPlan:
             cfg.allreduce = cb
         mean = np.zeros(3)
         cov = np.zeros(9)
+        nev = C.c_int32(0)
         F.check(F.lib().bs_shear_estimate(C.byref(self.data), C.byref(cfg), mean.ctypes.data_as(C.c_void_p),
-                                          cov.ctypes.data_as(C.c_void_p), _p(self.ws), self.ws_bytes,
-                                          _stream()))
+                                          cov.ctypes.data_as(C.c_void_p), C.cast(C.byref(nev), C.c_void_p),
+                                          _p(self.ws), self.ws_bytes, _stream()))
+        self.last_n_evals = nev.value
         n = 3 if free_alpha else 2
         return mean[:n], cov.reshape(3, 3)[:n, :n]
 

@@ -166,6 +166,8 @@ static bs_status fill_fit_params(const bs_fit_args *a, bs::FitParams &p, const c
     p.sigma = a->noise_sigma;
     p.gal_id = a->gal_id;
     p.init = a->init;
+    p.init_step = a->init_step_size;
+    p.init_im = a->init_inv_mass;
     p.n_gal = a->n_gal;
     p.pixel_scale = a->pixel_scale;
     p.lf_lo = pr.lf_lo;
@@ -219,6 +221,7 @@ bs_status bs_fit_galaxies(const bs_fit_args *a, const bs_fit_out *o, void *works
     p.inv_mass = o->inv_mass;
     p.n_div = o->n_divergent;
     p.status = o->status;
+    p.n_grad = o->n_grad;
     p.queue = static_cast<unsigned int *>(workspace);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e;
@@ -355,12 +358,14 @@ struct ShearObjective {
     void *stream;
     int n;
     bs_status err = BS_OK;
+    int32_t n_evals = 0;
 
     // value and gradient over (g1, g2[, alpha]); false on failure
     bool eval(const double *x, double &v, double *g)
     {
         const double alpha = n == 3 ? x[2] : cfg->alpha;
         double buf[4];
+        ++n_evals;
         bs_status st = bs_shear_loglike(d, x[0], x[1], alpha, buf, 1, ws, wsb, stream);
         if (st != BS_OK) {
             err = st;
@@ -456,7 +461,8 @@ void hermite_rule(int n, double *x, double *w)
 }  // namespace
 
 extern "C" bs_status bs_shear_estimate(const bs_shear_data *d, const bs_estimate_cfg *cfg, double *mean,
-                                       double *cov, void *workspace, size_t workspace_bytes, void *stream)
+                                       double *cov, int32_t *n_evals, void *workspace,
+                                       size_t workspace_bytes, void *stream)
 {
     bs_status st = validate_shear(d, "bs_shear_estimate");
     if (st != BS_OK) return st;
@@ -467,6 +473,14 @@ extern "C" bs_status bs_shear_estimate(const bs_shear_data *d, const bs_estimate
         return fail(BS_ERR_INVALID_ARG, "bs_shear_estimate: alpha start outside (alpha_lo, alpha_hi)");
     if (!(cfg->alpha > 0.0)) return fail(BS_ERR_INVALID_ARG, "bs_shear_estimate: alpha <= 0");
     ShearObjective f{d, cfg, workspace, workspace_bytes, stream, n};
+    struct EvalCount {
+        int32_t *dst;
+        ShearObjective *f;
+        ~EvalCount()
+        {
+            if (dst) *dst = f->n_evals;
+        }
+    } report{n_evals, &f};
     double x[3] = {0.0, 0.0, cfg->alpha}, g[3], v;
     if (!f.eval(x, v, g)) return f.err;
 

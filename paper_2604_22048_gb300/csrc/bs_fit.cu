@@ -351,16 +351,17 @@ __device__ void run_chain(const FitParams &P, const GalCtx &gc, const SmemView &
     for (int j = 0; j < NC; ++j) vcol[j] = (float)(lane + 32 * j - gc.c);
 
     float th[6], thl[6], g[6], im[6];
-    const float *ini = P.init + ((size_t)gal * C + chain) * 6;
+    const size_t ci0 = (size_t)gal * C + chain;
+    const float *ini = P.init + ci0 * 6;
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
         th[i] = ini[i];
         thl[i] = 0.f;
         g[i] = 0.f;
-        im[i] = 1.f;
+        im[i] = P.init_im ? P.init_im[ci0 * 6 + i] : 1.f;
     }
     double lp = -INFINITY;
-    float eps = 1.0f;
+    float eps = P.init_step ? P.init_step[ci0] : 1.0f;
     float da_mu = 0.f, da_hbar = 0.f, da_lebar = 0.f;
     int da_m = 0;
     int wn = 0, wi = 0;
@@ -372,6 +373,7 @@ __device__ void run_chain(const FitParams &P, const GalCtx &gc, const SmemView &
     int it = 0;
     float asum = 0.f;
     int ndiv = 0;
+    int ngrad = 0;
     int mode = MODE_INIT;
     const double thr_search = -0.22314355131420976;   // ln 0.8
     const size_t chain_row = ((size_t)gal * C + chain) * (size_t)S;
@@ -427,6 +429,7 @@ __device__ void run_chain(const FitParams &P, const GalCtx &gc, const SmemView &
             }
             if (!in_support(P, tp)) { ok = false; break; }
             const double v = eval_logpost<NC>(P, gc, sm.Dt, sm.Tt, vcol, tp, gp, l == nst - 1);
+            ++ngrad;
             if (l == nst - 1) lpp = v;
 #pragma unroll
             for (int i = 0; i < 6; ++i) pm[i] = fmaf(he, gp[i], pm[i]);
@@ -436,10 +439,16 @@ __device__ void run_chain(const FitParams &P, const GalCtx &gc, const SmemView &
             for (int i = 0; i < 6; ++i) { th[i] = tp[i]; thl[i] = tpl[i]; g[i] = gp[i]; }
             lp = ok ? lpp : -INFINITY;
             if (!isfinite(lp) && lane == 0 && P.status) P.status[gal] = 1;
-            mode = MODE_SEARCH;
-            s_idx = 0;
-            s_t = 0;
-            s_eps = 1.0f;
+            if (P.init_step) {
+                // resume with the given step size: no search, dual averaging from it
+                da_mu = logf(10.0f * eps);
+                mode = MODE_STEP;
+            } else {
+                mode = MODE_SEARCH;
+                s_idx = 0;
+                s_t = 0;
+                s_eps = 1.0f;
+            }
             continue;
         }
         double dH = INFINITY;
@@ -536,6 +545,7 @@ __device__ void run_chain(const FitParams &P, const GalCtx &gc, const SmemView &
         if (P.accept_rate) P.accept_rate[ci] = S > 0 ? asum / (float)S : 0.f;
         if (P.step_size) P.step_size[ci] = eps;
         if (P.n_div) P.n_div[ci] = ndiv;
+        if (P.n_grad) P.n_grad[ci] = ngrad;
     }
     if (P.inv_mass && lane < 6) {
         float v = im[0];

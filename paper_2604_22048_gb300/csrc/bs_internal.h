@@ -23,6 +23,8 @@ struct FitParams {
     const float *sigma;
     const uint64_t *gal_id;
     const float *init;
+    const float *init_step;
+    const float *init_im;
     int n_gal;
     float pixel_scale;
     // interim prior
@@ -44,6 +46,7 @@ struct FitParams {
     float *inv_mass;
     int32_t *n_div;
     int32_t *status;
+    int32_t *n_grad;
     // scheduling
     unsigned int *queue;
     int max_side;
