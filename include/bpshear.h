@@ -239,6 +239,22 @@ bs_status bs_shear_loglike(const bs_shear_data *data, double g1, double g2,
                            double alpha, double *out, int32_t out_on_host,
                            void *workspace, size_t workspace_bytes, void *stream);
 
+/* The same likelihood and gradient for callers that cannot allocate device
+ * memory or pass a workspace (code under another framework's fixed memory
+ * budget, real-time loops that must not allocate).  The paper has no
+ * counterpart: this is a deployment variant of bs_shear_loglike.
+ *   out: device double [4] = {value, d/dg1, d/dg2, d/dalpha}.
+ * The scratch (one FP64 partial per reduction block, at most 2048 blocks,
+ * 64 KB) is a static device array of the library, held on every GPU that
+ * loads it until exit.  The first call on a device looks up the array's
+ * device address; make it before any stream capture.  All calls share the
+ * array, so calls that overlap on the GPU race.  Returns BS_ERR_UNSUPPORTED
+ * when the device's reduction grid needs more than 2048 partial slots; the
+ * number of galaxies and samples is not limited.  Calls no allocating
+ * routine. */
+bs_status bs_shear_loglike_noalloc(const bs_shear_data *data, double g1, double g2,
+                                   double alpha, double *out, void *stream);
+
 /* Optional sum over processes of the 4 doubles {value, grad} of each
  * evaluation, for a galaxy set sharded across ranks (a no-op when NULL). */
 typedef void (*bs_allreduce_fn)(double *buf4, void *user);

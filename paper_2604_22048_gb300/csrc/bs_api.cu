@@ -606,3 +606,48 @@ extern "C" bs_status bs_shear_estimate(const bs_shear_data *d, const bs_estimate
     }
     return BS_OK;
 }
+
+namespace bs {
+
+bs_status set_error(bs_status st, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+bs_status shear_prepare(const bs_shear_data *d, double g1, double g2, double alpha, ShearLaunch &L,
+                        double add[4], double &alpha_scale, const char *who)
+{
+    bs_status st = validate_shear(d, who);
+    if (st != BS_OK) return st;
+    const double gg = g1 * g1 + g2 * g2;
+    if (!(gg < 1.0)) return fail(BS_ERR_INVALID_ARG, "%s: |g| >= 1", who);
+    if (!(alpha > 0.0)) return fail(BS_ERR_INVALID_ARG, "%s: alpha <= 0", who);
+    L.e1 = d->e1;
+    L.e2 = d->e2;
+    L.b = d->b;
+    L.n_gal = d->n_gal;
+    L.K = d->K;
+    L.family = d->family;
+    L.g1 = (float)g1;
+    L.g2 = (float)g2;
+    L.a2 = (float)(1.4426950408889634 / (2.0 * alpha * alpha));
+    L.kappa = d->family == BS_EPRIOR_BA14 ? 4.0f : 2.0f;
+    L.c0 = (float)(1.4426950408889634 / (2.0 * (double)d->sigma_e0 * d->sigma_e0));
+    L.r2 = d->trunc_r * d->trunc_r;
+    L.partials = nullptr;
+    const double ng = (double)d->n_gal;
+    const double kap = d->family == BS_EPRIOR_BA14 ? 4.0 : 2.0;
+    add[0] = ng * (kap * std::log1p(-gg) - log_z_family(d->family, alpha, d->trunc_r) +
+                   log_z_ba14(d->sigma_e0) - std::log((double)d->K));
+    add[1] = ng * (-2.0 * kap * g1 / (1.0 - gg));
+    add[2] = ng * (-2.0 * kap * g2 / (1.0 - gg));
+    add[3] = -ng * dlog_z_dalpha(d->family, alpha, d->trunc_r);
+    alpha_scale = 1.0 / (alpha * alpha * alpha);
+    return BS_OK;
+}
+
+}  // namespace bs

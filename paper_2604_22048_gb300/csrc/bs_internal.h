@@ -83,6 +83,15 @@ cudaError_t launch_shear_finalize(const double *partials, int n_part, double add
                                   double add_g1, double add_g2, double add_alpha,
                                   double alpha_scale, double *out, cudaStream_t stream);
 
+// Thread-local error message of the C ABI (bs_last_error).
+bs_status set_error(bs_status st, const char *fmt, ...);
+// Validate a shear-likelihood request and fill the kernel arguments (except
+// `partials`) and the per-galaxy constants the finalize step adds:
+// add = {value, d/dg1, d/dg2, d/dalpha}, alpha_scale multiplies the sum of
+// softmax-weighted |eps|^2.
+bs_status shear_prepare(const bs_shear_data *d, double g1, double g2, double alpha, ShearLaunch &L,
+                        double add[4], double &alpha_scale, const char *who);
+
 cudaError_t launch_chain_ess(const float *samples, int n_gal, int n_chains, int n_samples,
                              float *ess, float *rhat, cudaStream_t stream);
 
