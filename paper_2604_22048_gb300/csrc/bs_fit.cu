@@ -19,9 +19,14 @@
 // i.e. the residual's adjoint DFT is Dt - Mt exactly, and the per-evaluation
 // cost is one pass over the half plane instead of two O(N^3) transforms.
 // The gradient needs seven sums, accumulated per lane in FP32 and reduced
-// with an xor butterfly (identical bits in all lanes, so the warp-replicated
-// chain state stays uniform); chi^2 is accumulated with compensated FP32 per
+// with an xor butterfly (identical bits in all lanes, so warp-uniform
+// decisions stay uniform); chi^2 is accumulated with compensated FP32 per
 // lane and finished in FP64 at the warp total.
+//
+// Chain state.  Lane i < 6 owns parameter i of the chain (position hi/lo,
+// momentum, gradient, inverse metric, Welford moments) as scalars; the six
+// positions are gathered with shuffles before each evaluation.  Energies are
+// butterfly sums, so accept and divergence decisions are warp-uniform.
 //
 // Sampler (same algorithm as the oracle, written independently): Philox4x64-10
 // keyed by (seed, galaxy_id * n_chains + chain); fixed-L or random-L HMC with
@@ -30,6 +35,7 @@
 // doubling/halving step-size search at the start and after each window.
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 
 #include "bs_device.cuh"
 #include "bs_internal.h"
@@ -198,6 +204,83 @@ __device__ __forceinline__ bool in_support(const FitParams &P, const float th[6]
     return th[0] > P.lf_lo && th[0] < P.lf_hi && th[1] > P.ls_lo && th[1] < P.ls_hi && E < 1.0f;
 }
 
+// Per-lane partial sums of one evaluation.
+template <int NC>
+struct Sums {
+    float Sa, Swkx2, Sbkx;              // sum a, sum w kx^2, sum b kx
+    float Wc[NC], Wkx[NC], Bc[NC];      // per column: sum w, sum w kx, sum b
+    float chi_hi, chi_lo;               // compensated sum |Dt - Mt|^2
+};
+
+// Model-data terms of one row u (all NC column slots of this lane).
+template <int NC, bool LL>
+__device__ __forceinline__ void row_terms(Sums<NC> &S, const float2 *__restrict__ Drow,
+                                          const float *__restrict__ Trow, float kx, float akx2,
+                                          float Xr, float Xi, const float (&Yr)[NC], const float (&Yi)[NC],
+                                          const float (&cst)[NC], const float (&gky)[NC], float F2)
+{
+    const float kx2 = kx * kx;
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+        const float2 D = Drow[32 * j];
+        const float T = Trow[32 * j];
+        const float s = fmaf(gky[j], kx, akx2 + cst[j]);      // 1 + r0^2 q(k)
+        const float rs = rsqrtf(s);
+        const float rs2 = rs * rs;
+        const float A = T * rs2 * rs;                         // |M| / F
+        const float Pr = Xr * Yr[j] - Xi * Yi[j];             // F exp(-i k.delta)
+        const float Pi = Xr * Yi[j] + Xi * Yr[j];
+        const float zr = fmaf(D.x, Pr, D.y * Pi);             // conj(D) * phase
+        const float zi = fmaf(D.x, Pi, -D.y * Pr);
+        const float a = A * fmaf(-A, F2, zr);                 // Re conj(D - M) M
+        const float b = A * zi;                               // Im conj(D - M) M
+        const float w = a * rs2;                              // a / s
+        S.Sa += a;
+        S.Wc[j] += w;
+        S.Wkx[j] = fmaf(w, kx, S.Wkx[j]);
+        S.Swkx2 = fmaf(w, kx2, S.Swkx2);
+        S.Bc[j] += b;
+        S.Sbkx = fmaf(b, kx, S.Sbkx);
+        if (LL) {
+            const float Rr = fmaf(-A, Pr, D.x);
+            const float Ri = fmaf(-A, Pi, D.y);
+            comp_add(S.chi_hi, S.chi_lo, fmaf(Rr, Rr, Ri * Ri));
+        }
+    }
+}
+
+// Half-plane pass, two rows per iteration (the row phase advances by
+// exp(-2 pi i dx / N) per row).
+template <int NC, bool LL>
+__device__ __forceinline__ void half_plane(Sums<NC> &S, const float2 *__restrict__ Dt,
+                                           const float *__restrict__ Tt, int npad, int H, float dk,
+                                           float al, float exr, float exi, const float (&Yr)[NC],
+                                           const float (&Yi)[NC], const float (&cst)[NC],
+                                           const float (&gky)[NC], float F2)
+{
+    const int lane = threadIdx.x & 31;
+    const float2 *Drow = Dt + lane;
+    const float *Trow = Tt + lane;
+    const float e2r = exr * exr - exi * exi, e2i = 2.0f * exr * exi;   // two-row step
+    float Xr = 1.0f, Xi = 0.0f;
+    int u = 0;
+    for (; u + 1 < H; u += 2) {
+        const float kx0 = (float)u * dk, kx1 = (float)(u + 1) * dk;
+        const float X1r = Xr * exr - Xi * exi, X1i = Xr * exi + Xi * exr;
+        row_terms<NC, LL>(S, Drow, Trow, kx0, al * kx0 * kx0, Xr, Xi, Yr, Yi, cst, gky, F2);
+        row_terms<NC, LL>(S, Drow + npad, Trow + npad, kx1, al * kx1 * kx1, X1r, X1i, Yr, Yi, cst, gky, F2);
+        const float nXr = Xr * e2r - Xi * e2i;
+        Xi = Xr * e2i + Xi * e2r;
+        Xr = nXr;
+        Drow += 2 * npad;
+        Trow += 2 * npad;
+    }
+    if (u < H) {
+        const float kx0 = (float)u * dk;
+        row_terms<NC, LL>(S, Drow, Trow, kx0, al * kx0 * kx0, Xr, Xi, Yr, Yi, cst, gky, F2);
+    }
+}
+
 // Log posterior (if want_ll) and gradient at th, warp-cooperative.
 template <int NC>
 __device__ __forceinline__ double eval_logpost(const FitParams &P, const GalCtx &gc,
@@ -205,7 +288,6 @@ __device__ __forceinline__ double eval_logpost(const FitParams &P, const GalCtx 
                                                const float *__restrict__ Tt, const float vcol[NC],
                                                const float th[6], float g[6], bool want_ll)
 {
-    const int lane = threadIdx.x & 31;
     const float F = exp10f(th[0]);
     const float r0 = exp10f(th[1]) * (1.0f / kHlrOverR0);
     const float r02 = r0 * r0;
@@ -231,60 +313,27 @@ __device__ __forceinline__ double eval_logpost(const FitParams &P, const GalCtx 
         cst[j] = fmaf(be * ky[j], ky[j], 1.0f);
         gky[j] = ga * ky[j];
     }
-    float Xr = 1.0f, Xi = 0.0f;
-    float Sa = 0.f, Swkx2 = 0.f, Sbkx = 0.f;
-    float Wc[NC], Wkx[NC], Bc[NC];
+    Sums<NC> S;
+    S.Sa = 0.f;
+    S.Swkx2 = 0.f;
+    S.Sbkx = 0.f;
+    S.chi_hi = 0.f;
+    S.chi_lo = 0.f;
 #pragma unroll
-    for (int j = 0; j < NC; ++j) { Wc[j] = 0.f; Wkx[j] = 0.f; Bc[j] = 0.f; }
-    float chi_hi = 0.f, chi_lo = 0.f;
-    const int npad = P.npad;
-    const float2 *Drow = Dt + lane;
-    const float *Trow = Tt + lane;
-    for (int u = 0; u < gc.H; ++u) {
-        const float kx = (float)u * dk;
-        const float kx2 = kx * kx;
-        const float akx2 = al * kx2;
-#pragma unroll
-        for (int j = 0; j < NC; ++j) {
-            const float2 D = Drow[32 * j];
-            const float T = Trow[32 * j];
-            const float s = fmaf(gky[j], kx, akx2 + cst[j]);      // 1 + r0^2 q(k)
-            const float rs = rsqrtf(s);
-            const float rs2 = rs * rs;
-            const float A = T * rs2 * rs;                         // |M| / F
-            const float Pr = Xr * Yr[j] - Xi * Yi[j];             // F exp(-i k.delta)
-            const float Pi = Xr * Yi[j] + Xi * Yr[j];
-            const float zr = fmaf(D.x, Pr, D.y * Pi);             // conj(D) * phase
-            const float zi = fmaf(D.x, Pi, -D.y * Pr);
-            const float a = A * fmaf(-A, F2, zr);                 // Re conj(D - M) M
-            const float b = A * zi;                               // Im conj(D - M) M
-            const float w = a * rs2;                              // a / s
-            Sa += a;
-            Wc[j] += w;
-            Wkx[j] = fmaf(w, kx, Wkx[j]);
-            Swkx2 = fmaf(w, kx2, Swkx2);
-            Bc[j] += b;
-            Sbkx = fmaf(b, kx, Sbkx);
-            if (want_ll) {
-                const float Rr = fmaf(-A, Pr, D.x);
-                const float Ri = fmaf(-A, Pi, D.y);
-                comp_add(chi_hi, chi_lo, fmaf(Rr, Rr, Ri * Ri));
-            }
-        }
-        const float nXr = Xr * exr - Xi * exi;
-        const float nXi = Xr * exi + Xi * exr;
-        Xr = nXr;
-        Xi = nXi;
-        Drow += npad;
-        Trow += npad;
-    }
+    for (int j = 0; j < NC; ++j) { S.Wc[j] = 0.f; S.Wkx[j] = 0.f; S.Bc[j] = 0.f; }
+    if (want_ll)
+        half_plane<NC, true>(S, Dt, Tt, P.npad, gc.H, dk, al, exr, exi, Yr, Yi, cst, gky, F2);
+    else
+        half_plane<NC, false>(S, Dt, Tt, P.npad, gc.H, dk, al, exr, exi, Yr, Yi, cst, gky, F2);
+
+    float Sa = S.Sa, Swkx2 = S.Swkx2, Sbkx = S.Sbkx;
     float Sw = 0.f, Swky2 = 0.f, Swkxky = 0.f, Sbky = 0.f;
 #pragma unroll
     for (int j = 0; j < NC; ++j) {
-        Sw += Wc[j];
-        Swky2 = fmaf(ky[j] * ky[j], Wc[j], Swky2);
-        Swkxky = fmaf(ky[j], Wkx[j], Swkxky);
-        Sbky = fmaf(ky[j], Bc[j], Sbky);
+        Sw += S.Wc[j];
+        Swky2 = fmaf(ky[j] * ky[j], S.Wc[j], Swky2);
+        Swkxky = fmaf(ky[j], S.Wkx[j], Swkxky);
+        Sbky = fmaf(ky[j], S.Bc[j], Sbky);
     }
     Sa = warp_sum(Sa);
     Sw = warp_sum(Sw);
@@ -310,30 +359,25 @@ __device__ __forceinline__ double eval_logpost(const FitParams &P, const GalCtx 
     g[4] = gc.p * Sbkx * ib - th[4] * P.inv_sxy2;
     g[5] = gc.p * Sbky * ib - th[5] * P.inv_sxy2;
     if (!want_ll) return 0.0;
-    const double chi2 = warp_sum_comp(chi_hi, chi_lo);
+    const double chi2 = warp_sum_comp(S.chi_hi, S.chi_lo);
     const float lprior = P.prior_const - 0.5f * (th[4] * th[4] + th[5] * th[5]) * P.inv_sxy2 +
                          2.0f * log1pf(-E) - 0.5f * E * P.inv_se2;
     return -0.5 * chi2 * (double)ib + (double)lprior;
 }
 
-__device__ __forceinline__ void box_muller(const float u[8], float z[6])
+__device__ __forceinline__ float pick6(const float (&v)[6], int i)
 {
+    float r = v[0];
 #pragma unroll
-    for (int j = 0; j < 3; ++j) {
-        const float r = sqrtf(-2.0f * logf(u[2 * j]));
-        float s, co;
-        sincospif(2.0f * u[2 * j + 1], &s, &co);
-        z[2 * j] = r * co;
-        z[2 * j + 1] = r * s;
-    }
+    for (int k = 1; k < 6; ++k)
+        if (i == k) r = v[k];
+    return r;
 }
 
-__device__ __forceinline__ double kinetic(const float pm[6], const float im[6])
+// 1/2 sum_i m_i p_i^2 over the six parameter lanes (identical in all lanes).
+__device__ __forceinline__ double kinetic(float pm, float im, bool own)
 {
-    double k = 0.0;
-#pragma unroll
-    for (int i = 0; i < 6; ++i) k += (double)(im[i] * pm[i] * pm[i]);
-    return 0.5 * k;
+    return 0.5 * (double)warp_sum(own ? im * pm * pm : 0.0f);
 }
 
 enum { MODE_INIT = 0, MODE_SEARCH = 1, MODE_STEP = 2 };
@@ -343,6 +387,8 @@ __device__ void run_chain(const FitParams &P, const GalCtx &gc, const SmemView &
                           int chain)
 {
     const int lane = threadIdx.x & 31;
+    const int pi = lane < 6 ? lane : 5;     // parameter of this lane (lanes 6.. shadow parameter 5)
+    const bool own = lane < 6;
     const int C = P.n_chains, W = P.n_warmup, S = P.n_samples, L = P.n_leapfrog;
     const uint64_t gid = P.gal_id ? P.gal_id[gal] : (uint64_t)gal;
     const uint64_t key = gid * (uint64_t)C + (uint64_t)chain;
@@ -350,24 +396,16 @@ __device__ void run_chain(const FitParams &P, const GalCtx &gc, const SmemView &
 #pragma unroll
     for (int j = 0; j < NC; ++j) vcol[j] = (float)(lane + 32 * j - gc.c);
 
-    float th[6], thl[6], g[6], im[6];
     const size_t ci0 = (size_t)gal * C + chain;
-    const float *ini = P.init + ci0 * 6;
-#pragma unroll
-    for (int i = 0; i < 6; ++i) {
-        th[i] = ini[i];
-        thl[i] = 0.f;
-        g[i] = 0.f;
-        im[i] = P.init_im ? P.init_im[ci0 * 6 + i] : 1.f;
-    }
+    // this lane's parameter: position (hi, lo), gradient, inverse metric
+    float th = P.init[ci0 * 6 + pi], thl = 0.f, g = 0.f;
+    float im = P.init_im ? P.init_im[ci0 * 6 + pi] : 1.f;
+    float wmean = 0.f, wm2 = 0.f;
     double lp = -INFINITY;
     float eps = P.init_step ? P.init_step[ci0] : 1.0f;
     float da_mu = 0.f, da_hbar = 0.f, da_lebar = 0.f;
     int da_m = 0;
     int wn = 0, wi = 0;
-    float wmean[6], wm2[6];
-#pragma unroll
-    for (int i = 0; i < 6; ++i) { wmean[i] = 0.f; wm2[i] = 0.f; }
     int s_idx = 0, s_t = 0, s_dir = 0;
     float s_eps = 1.0f;
     int it = 0;
@@ -376,7 +414,8 @@ __device__ void run_chain(const FitParams &P, const GalCtx &gc, const SmemView &
     int ngrad = 0;
     int mode = MODE_INIT;
     const double thr_search = -0.22314355131420976;   // ln 0.8
-    const size_t chain_row = ((size_t)gal * C + chain) * (size_t)S;
+    const size_t chain_row = ci0 * (size_t)S;
+    const size_t plane = (size_t)P.n_gal * C * S;
 
     if (W + S == 0) mode = -1;
     while (mode >= 0) {
@@ -398,45 +437,47 @@ __device__ void run_chain(const FitParams &P, const GalCtx &gc, const SmemView &
                 eps_use = eps * (1.0f + P.jitter * (2.0f * u[7] - 1.0f));
             }
         }
-        float pm[6];
-        if (mode == MODE_INIT) {
-#pragma unroll
-            for (int i = 0; i < 6; ++i) pm[i] = 0.f;
-        } else {
-            float z[6];
-            box_muller(u, z);
-#pragma unroll
-            for (int i = 0; i < 6; ++i) pm[i] = z[i] / sqrtf(im[i]);
+        // momentum of this lane's parameter: Box-Muller on the pair (u_2j, u_2j+1)
+        float pm = 0.f;
+        if (mode != MODE_INIT) {
+            const int j = pi >> 1;
+            const float ua = j == 0 ? u[0] : (j == 1 ? u[2] : u[4]);
+            const float ub = j == 0 ? u[1] : (j == 1 ? u[3] : u[5]);
+            const float r = sqrtf(-2.0f * logf(ua));
+            float sn, cs;
+            sincospif(2.0f * ub, &sn, &cs);
+            pm = ((pi & 1) ? r * sn : r * cs) / sqrtf(im);
         }
-        const double H0 = -lp + kinetic(pm, im);
-        float tp[6], tpl[6], gp[6];
-#pragma unroll
-        for (int i = 0; i < 6; ++i) { tp[i] = th[i]; tpl[i] = thl[i]; gp[i] = g[i]; }
+        const double H0 = -lp + kinetic(pm, im, own);
+        float tp = th, tpl = thl, gp = g;
         double lpp = lp;
         bool ok = true;
         for (int l = 0; l < nst; ++l) {
             const float he = 0.5f * eps_use;
-#pragma unroll
-            for (int i = 0; i < 6; ++i) pm[i] = fmaf(he, gp[i], pm[i]);
-#pragma unroll
-            for (int i = 0; i < 6; ++i) {
+            pm = fmaf(he, gp, pm);
+            {
                 // compensated position update (hi, lo) += eps m p
-                const float d = fmaf(eps_use * im[i], pm[i], tpl[i]);
+                const float d = fmaf(eps_use * im, pm, tpl);
                 float s, e;
-                two_sum(tp[i], d, s, e);
-                tp[i] = s;
-                tpl[i] = e;
+                two_sum(tp, d, s, e);
+                tp = s;
+                tpl = e;
             }
-            if (!in_support(P, tp)) { ok = false; break; }
-            const double v = eval_logpost<NC>(P, gc, sm.Dt, sm.Tt, vcol, tp, gp, l == nst - 1);
+            float x[6];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) x[k] = __shfl_sync(BS_FULL_MASK, tp, k);
+            if (!in_support(P, x)) { ok = false; break; }
+            float gg[6];
+            const double v = eval_logpost<NC>(P, gc, sm.Dt, sm.Tt, vcol, x, gg, l == nst - 1);
             ++ngrad;
             if (l == nst - 1) lpp = v;
-#pragma unroll
-            for (int i = 0; i < 6; ++i) pm[i] = fmaf(he, gp[i], pm[i]);
+            gp = pick6(gg, pi);
+            pm = fmaf(he, gp, pm);
         }
         if (mode == MODE_INIT) {
-#pragma unroll
-            for (int i = 0; i < 6; ++i) { th[i] = tp[i]; thl[i] = tpl[i]; g[i] = gp[i]; }
+            th = tp;
+            thl = tpl;
+            g = gp;
             lp = ok ? lpp : -INFINITY;
             if (!isfinite(lp) && lane == 0 && P.status) P.status[gal] = 1;
             if (P.init_step) {
@@ -453,7 +494,7 @@ __device__ void run_chain(const FitParams &P, const GalCtx &gc, const SmemView &
         }
         double dH = INFINITY;
         if (ok) {
-            dH = (-lpp + kinetic(pm, im)) - H0;
+            dH = (-lpp + kinetic(pm, im, own)) - H0;
             if (!isfinite(dH) || dH > 1000.0) ok = false;
         }
         if (mode == MODE_SEARCH) {
@@ -483,8 +524,9 @@ __device__ void run_chain(const FitParams &P, const GalCtx &gc, const SmemView &
         const float a = ok ? (dH < 0.0 ? 1.0f : expf((float)-dH)) : 0.0f;
         const bool acc = ok && ((double)logf(u[6]) < -dH);
         if (acc) {
-#pragma unroll
-            for (int i = 0; i < 6; ++i) { th[i] = tp[i]; thl[i] = tpl[i]; g[i] = gp[i]; }
+            th = tp;
+            thl = tpl;
+            g = gp;
             lp = lpp;
         }
         if (it < W) {
@@ -499,24 +541,17 @@ __device__ void run_chain(const FitParams &P, const GalCtx &gc, const SmemView &
             eps = expf(le);
             if (wi < P.n_windows && it >= P.win_start[wi] && it < P.win_end[wi]) {
                 ++wn;
-                const float inv_n = 1.0f / (float)wn;
-#pragma unroll
-                for (int i = 0; i < 6; ++i) {
-                    const float x = th[i] + thl[i];
-                    const float d = x - wmean[i];
-                    wmean[i] = fmaf(d, inv_n, wmean[i]);
-                    wm2[i] = fmaf(d, x - wmean[i], wm2[i]);
-                }
+                const float x = th + thl;
+                const float d = x - wmean;
+                wmean = fmaf(d, 1.0f / (float)wn, wmean);
+                wm2 = fmaf(d, x - wmean, wm2);
             }
             if (wi < P.n_windows && it == P.win_end[wi] - 1) {
                 const float n = (float)wn;
-#pragma unroll
-                for (int i = 0; i < 6; ++i) {
-                    const float var = wm2[i] / (n - 1.0f);
-                    im[i] = (n / (n + 5.0f)) * var + 1e-3f * (5.0f / (n + 5.0f));
-                    wmean[i] = 0.f;
-                    wm2[i] = 0.f;
-                }
+                const float var = wm2 / (n - 1.0f);
+                im = (n / (n + 5.0f)) * var + 1e-3f * (5.0f / (n + 5.0f));
+                wmean = 0.f;
+                wm2 = 0.f;
                 wn = 0;
                 mode = MODE_SEARCH;
                 s_idx = wi + 1;
@@ -529,35 +564,27 @@ __device__ void run_chain(const FitParams &P, const GalCtx &gc, const SmemView &
             const int s = it - W;
             asum += a;
             ndiv += ok ? 0 : 1;
-            float v = th[0] + thl[0];
-#pragma unroll
-            for (int i = 1; i < 6; ++i)
-                if (lane == i) v = th[i] + thl[i];
-            if (lane < 6) P.samples[((size_t)lane * P.n_gal * C) * S + chain_row + s] = v;
+            if (own) P.samples[(size_t)pi * plane + chain_row + s] = th + thl;
             if (lane == 6 && P.logp) P.logp[chain_row + s] = (float)lp;
             if (lane == 7 && P.accepted) P.accepted[chain_row + s] = acc ? 1 : 0;
         }
         ++it;
         if (it >= W + S && mode == MODE_STEP) mode = -1;
     }
-    const size_t ci = (size_t)gal * C + chain;
     if (lane == 0) {
-        if (P.accept_rate) P.accept_rate[ci] = S > 0 ? asum / (float)S : 0.f;
-        if (P.step_size) P.step_size[ci] = eps;
-        if (P.n_div) P.n_div[ci] = ndiv;
-        if (P.n_grad) P.n_grad[ci] = ngrad;
+        if (P.accept_rate) P.accept_rate[ci0] = S > 0 ? asum / (float)S : 0.f;
+        if (P.step_size) P.step_size[ci0] = eps;
+        if (P.n_div) P.n_div[ci0] = ndiv;
+        if (P.n_grad) P.n_grad[ci0] = ngrad;
     }
-    if (P.inv_mass && lane < 6) {
-        float v = im[0];
-#pragma unroll
-        for (int i = 1; i < 6; ++i)
-            if (lane == i) v = im[i];
-        P.inv_mass[ci * 6 + lane] = v;
-    }
+    if (P.inv_mass && own) P.inv_mass[ci0 * 6 + pi] = im;
 }
 
-template <int NC>
-__global__ void __launch_bounds__(256) fit_kernel(const FitParams P)
+// MINB bounds the registers so that MINB CTAs of 256 threads fit an SM
+// (2: <= 128 registers, no spills; 3: <= 85, a few spills outside the
+// half-plane loop), i.e. 4 or 6 CTAs of 4 chains.
+template <int NC, int MINB>
+__global__ void __launch_bounds__(256, MINB) fit_kernel(const FitParams P)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_gal;
@@ -600,13 +627,7 @@ __device__ void point_eval(const FitParams &P, const GalCtx &gc, const SmemView 
         for (int i = 0; i < 6; ++i) g[i] = NAN;
     }
     if (lane == 0 && logp) *logp = v;
-    if (grad && lane < 6) {
-        float o = g[0];
-#pragma unroll
-        for (int i = 1; i < 6; ++i)
-            if (lane == i) o = g[i];
-        grad[lane] = o;
-    }
+    if (grad && lane < 6) grad[lane] = pick6(g, lane);
 }
 
 __global__ void __launch_bounds__(32) logpost_points_kernel(const FitParams P, int n_points,
@@ -638,6 +659,31 @@ __global__ void __launch_bounds__(32) logpost_points_kernel(const FitParams P, i
     }
 }
 
+// The kernel instance is chosen by the column slots per lane of the largest
+// stamp; smaller stamps of the same launch see zero-padded columns.
+using FitKernel = void (*)(const FitParams);
+
+template <int MINB>
+FitKernel fit_kernel_nc(int max_side)
+{
+    switch ((max_side + 31) / 32) {
+        case 1: return fit_kernel<1, MINB>;
+        case 2: return fit_kernel<2, MINB>;
+        case 3: return fit_kernel<3, MINB>;
+        default: return fit_kernel<4, MINB>;
+    }
+}
+
+// Register budget of the launch: BS_FIT_MINB=3 selects the 85-register build.
+FitKernel fit_kernel_for(int max_side)
+{
+    static const int minb = [] {
+        const char *s = getenv("BS_FIT_MINB");
+        return (s && s[0] == '3') ? 3 : 2;
+    }();
+    return minb == 3 ? fit_kernel_nc<3>(max_side) : fit_kernel_nc<2>(max_side);
+}
+
 }  // namespace
 
 size_t fit_smem_bytes(int max_side)
@@ -647,24 +693,6 @@ size_t fit_smem_bytes(int max_side)
     return (size_t)h * npad * (sizeof(float2) + sizeof(float)) + (size_t)max_side * h * sizeof(float2) +
            (size_t)max_side * sizeof(float2);
 }
-
-namespace {
-
-// The kernel instance is chosen by the column slots per lane of the largest
-// stamp; smaller stamps of the same launch see zero-padded columns.
-using FitKernel = void (*)(const FitParams);
-
-FitKernel fit_kernel_for(int max_side)
-{
-    switch ((max_side + 31) / 32) {
-        case 1: return fit_kernel<1>;
-        case 2: return fit_kernel<2>;
-        case 3: return fit_kernel<3>;
-        default: return fit_kernel<4>;
-    }
-}
-
-}  // namespace
 
 int fit_blocks_per_sm(int n_chains, int max_side)
 {
