@@ -39,25 +39,35 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n-gal", type=int, default=10000)
+    ap.add_argument("--workload", default="plain", choices=["plain", "ragged"],
+                    help="plain: 10^4 x 53 px, one Gaussian PSF; ragged: 10^5, 25-101 px, per-galaxy Moffat")
+    ap.add_argument("--n-gal", type=int, default=None)
     ap.add_argument("--side", type=int, default=53)
     ap.add_argument("--chains", type=int, default=4)
-    ap.add_argument("--n-warmup", type=int, default=200)
+    ap.add_argument("--n-warmup", type=int, default=100)
     ap.add_argument("--n-samples", type=int, default=100)
     ap.add_argument("--leapfrog", type=int, default=16)
     ap.add_argument("--ref-galaxies", type=int, default=0, help="oracle sample size (0: host cores, max 16)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    return ap.parse_args()
+    a = ap.parse_args()
+    if a.n_gal is None:
+        a.n_gal = 10000 if a.workload == "plain" else 100000
+    return a
 
 
 def workload_config(a):
-    return {"workload": f"plain batched: {a.n_gal} exponential galaxies, {a.side}x{a.side} FP32 stamps, "
-                        f"pixel 0.2\", Gaussian PSF FWHM 0.7\", S/N U(15,50), g=(0.02,0), {a.chains} chains x "
-                        f"({a.n_warmup} warmup + {a.n_samples} draws), HMC L_i~U{{1..{a.leapfrog}}}, "
-                        "then posterior-mean shear (alpha fixed, truncated-Gaussian sigma 0.2)",
-            "n_gal": a.n_gal, "side": a.side, "chains": a.chains, "n_warmup": a.n_warmup,
-            "n_samples": a.n_samples, "leapfrog_max": a.leapfrog,
+    chain = (f"{a.chains} chains x ({a.n_warmup} warmup + {a.n_samples} draws), HMC L_i~U{{1..{a.leapfrog}}}, "
+             "then posterior-mean shear (alpha fixed, truncated-Gaussian sigma 0.2)")
+    if a.workload == "plain":
+        desc = (f"plain batched: {a.n_gal} exponential galaxies, {a.side}x{a.side} FP32 stamps, pixel 0.2\", "
+                f"Gaussian PSF FWHM 0.7\", S/N U(15,50), g=(0.02,0), {chain}")
+    else:
+        desc = (f"batching: {a.n_gal} exponential galaxies, stamp side 2ceil(4.43hlr/p+1.5FWHM/p)+1 in [25,101] "
+                f"(uneven), per-galaxy Moffat beta=3 PSF FWHM U(0.6\",0.9\"), S/N log-U(10,100), FP32 with FP64 "
+                f"accumulation, class launches replayed as one CUDA graph, {chain}")
+    return {"workload": desc, "n_gal": a.n_gal, "side": a.side if a.workload == "plain" else "25-101",
+            "chains": a.chains, "n_warmup": a.n_warmup, "n_samples": a.n_samples, "leapfrog_max": a.leapfrog,
             "l2": "flushed between timed steps (256 MB write)"}
 
 
@@ -65,6 +75,8 @@ def workload_config(a):
 
 def make_truth(a, rank):
     from paper_2604_22048_gb300 import synth
+    if a.workload == "ragged":
+        return synth.draw_ragged(a.n_gal, seed=synth.SEED_DATA + 97 * rank)
     return synth.draw_plain(a.n_gal, a.side, seed=synth.SEED_DATA + 97 * rank)
 
 
@@ -82,22 +94,31 @@ def make_inputs_gpu(a, rank, dev):
     import torch
     from paper_2604_22048_gb300 import api, synth
     t = make_truth(a, rank)
-    n, N = t.n, a.side
+    n = t.n
     ep = sheared(t.e_int, t.g)
     theta = np.column_stack([np.zeros(n), np.log10(t.hlr), ep, t.offset]).astype(np.float32)
-    side = torch.full((n,), N, dtype=torch.int32, device=dev)
-    psf = api.psf_table("gaussian", np.float32(0.7), device=dev)
+    side = torch.from_numpy(t.side.astype(np.int32)).to(dev)
+    if t.psf_kind == "gaussian":
+        psf = api.psf_table("gaussian", np.float32(0.7), device=dev)
+    else:
+        psf = api.psf_table("moffat", t.psf_fwhm.astype(np.float32), t.psf_beta, device=dev)
     unit, offsets = api.render(torch.from_numpy(theta).to(dev), side, psf)
-    stride = int((N * N + 3) // 4 * 4)
-    u2 = unit.view(n, stride)[:, :N * N]
-    flux = torch.from_numpy(t.snr.astype(np.float32)).to(dev) / torch.sqrt((u2.double() ** 2).sum(1)).float()
-    noise = np.stack(synth.noise_fields(t)).reshape(n, N * N).astype(np.float32)
-    data = torch.zeros_like(unit)
-    data.view(n, stride)[:, :N * N] = flux[:, None] * u2 + torch.from_numpy(noise).to(dev)
-    sums = data.view(n, stride)[:, :N * N].sum(1).cpu().numpy()
+    # flux from the drawn S/N (sum of squares of the unit-flux stamp), noise added on the host
+    unit_h = unit.cpu().numpy()
+    offs_h = offsets.cpu().numpy()
+    noise = synth.noise_fields(t)
+    data_h = np.zeros_like(unit_h)
+    sums = np.zeros(n)
+    for i in range(n):
+        N = int(t.side[i])
+        u = unit_h[offs_h[i]:offs_h[i] + N * N]
+        flux = t.snr[i] / np.sqrt(np.dot(u.astype(np.float64), u))
+        d = (flux * u + noise[i].ravel()).astype(np.float32)
+        data_h[offs_h[i]:offs_h[i] + N * N] = d
+        sums[i] = d.sum(dtype=np.float64)
     init = synth.initial_theta(sums, np.log10(t.hlr), ep, synth.init_offsets(t, a.chains, seed=synth.SEED_CHAINS + rank))
     sigma = torch.ones(n, device=dev)
-    return dict(data=data, offsets=offsets, side=side, psf=psf, sigma=sigma,
+    return dict(data=torch.from_numpy(data_h).to(dev), offsets=offsets, side=side, psf=psf, sigma=sigma,
                 init=torch.from_numpy(init.astype(np.float32)).to(dev), truth=t)
 
 
@@ -190,18 +211,33 @@ def reference_arm(a, world, rank):
     t = make_truth(a2, 0)
     ep = sheared(t.e_int, t.g)
     theta = np.column_stack([np.zeros(n), np.log10(t.hlr), ep, t.offset])
-    unit = O.render_many(a.side, 0.2, (O.PSF_GAUSSIAN, 0.7), theta)
-    noise = np.stack(synth.noise_fields(t))
-    flux = t.snr / np.sqrt((unit ** 2).sum(axis=(1, 2)))
-    data = (flux[:, None, None] * unit + noise).astype(np.float32).astype(np.float64)
-    init = synth.initial_theta(data.sum(axis=(1, 2)), np.log10(t.hlr), ep, synth.init_offsets(t, a.chains))
+    noise = synth.noise_fields(t)
+    if t.psf_kind == "gaussian":
+        psfs = [(O.PSF_GAUSSIAN, 0.7)] * n
+    else:
+        psfs = [(O.PSF_MOFFAT, float(np.float32(f)), t.psf_beta) for f in t.psf_fwhm]
+    groups = {}
+    for i in range(n):
+        groups.setdefault(int(t.side[i]), []).append(i)
+    data, inits = {}, {}
+    for N, idx in groups.items():
+        unit = O.render_many(N, 0.2, [psfs[i] for i in idx], theta[idx])
+        flux = t.snr[idx] / np.sqrt((unit ** 2).sum(axis=(1, 2)))
+        d = (flux[:, None, None] * unit + np.stack([noise[i] for i in idx])).astype(np.float32).astype(np.float64)
+        data[N] = d
+    init_all = synth.initial_theta(np.array([data[int(t.side[i])][groups[int(t.side[i])].index(i)].sum()
+                                             for i in range(n)]), np.log10(t.hlr), ep, synth.init_offsets(t, a.chains))
 
     def step():
-        r = O.fit_galaxies(data, 1.0, (O.PSF_GAUSSIAN, 0.7), init.astype(np.float32).astype(np.float64),
-                           n_warmup=a.n_warmup, n_samples=a.n_samples, n_leapfrog=a.leapfrog, random_steps=True,
-                           seed=22048, n_threads=cores)
-        e1 = r["samples"][2].reshape(n, -1).astype(np.float32)
-        e2 = r["samples"][3].reshape(n, -1).astype(np.float32)
+        e1s, e2s = [], []
+        for N, idx in groups.items():
+            r = O.fit_galaxies(data[N], 1.0, [psfs[i] for i in idx], init_all[idx].astype(np.float32).astype(np.float64),
+                               n_warmup=a.n_warmup, n_samples=a.n_samples, n_leapfrog=a.leapfrog, random_steps=True,
+                               seed=22048, n_threads=cores, ids=np.array(idx, dtype=np.uint64))
+            e1s.append(r["samples"][2].reshape(len(idx), -1))
+            e2s.append(r["samples"][3].reshape(len(idx), -1))
+        e1 = np.concatenate(e1s).astype(np.float32)
+        e2 = np.concatenate(e2s).astype(np.float32)
         O.shear_estimate(e1, e2, family=O.EPRIOR_TRUNC_GAUSS, alpha=0.2)
 
     for _ in range(a.warmup):
@@ -243,8 +279,12 @@ def our_arm(a, world, rank, local_rank):
     inp = make_inputs_gpu(a, rank, dev)
     cfg = api.FitConfig(n_chains=a.chains, n_warmup=a.n_warmup, n_samples=a.n_samples, n_leapfrog=a.leapfrog,
                         random_steps=True)
-    plan = api.FitPlan(inp["data"], inp["offsets"], inp["side"], inp["psf"], inp["sigma"], inp["init"], cfg,
-                       max_side=a.side)
+    if a.workload == "ragged":
+        plan = api.RaggedFitPlan(inp["data"], inp["offsets"], inp["side"], inp["psf"], inp["sigma"], inp["init"],
+                                 cfg, capture=True)
+    else:
+        plan = api.FitPlan(inp["data"], inp["offsets"], inp["side"], inp["psf"], inp["sigma"], inp["init"], cfg,
+                           max_side=a.side)
     K = a.chains * a.n_samples
     shear = api.ShearPlan(plan.samples[2].reshape(a.n_gal, K), plan.samples[3].reshape(a.n_gal, K),
                           family=1, trunc_r=0.7)
@@ -305,9 +345,11 @@ def our_arm(a, world, rank, local_rank):
     # ---- after timing: diagnostics of the last step's chains
     ess, rhat = api.chain_ess(plan.samples)
     ess_gal = ess.mean(dim=1)
-    n_grad = plan.n_grad.to(torch.int64).sum().item()
+    grads_per_gal = plan.n_grad.to(torch.int64).sum(dim=1).cpu().numpy()
+    n_grad = int(grads_per_gal.sum())
     torch.cuda.synchronize(dev)
-    fit_flops = n_grad * flops_per_eval(a.side)
+    sides = inp["truth"].side.astype(np.int64)
+    fit_flops = float(np.sum(grads_per_gal * np.array([flops_per_eval(int(N)) for N in sides])))
     fit_s = float(np.mean(fit_ms)) / 1e3
     props = torch.cuda.get_device_properties(dev)
     peaks = measured_peaks()
@@ -321,12 +363,13 @@ def our_arm(a, world, rank, local_rank):
            "config": workload_config(a) | {"parallelism": f"dp{world}: galaxies per rank, shear sums all-reduced"},
            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                         "frac": achieved / peak_tflops, "traffic": None,
-                        "kernel": "fit_kernel<2>",
+                        "kernel": "fit_kernel<2,2>" if a.workload == "plain" else "fit_kernel<1..4,2> (graph)",
                         "peak_how": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
                                     f"{sm_max:.0f} MHz (max SM clock)",
-                        "flops_per_eval": flops_per_eval(a.side), "evals_per_launch": n_grad,
+                        "flops_per_launch": fit_flops, "evals_per_launch": n_grad,
                         "fit_ms": float(np.mean(fit_ms))},
-           "gpu_launches": int(a.steps * 1 + 2 * sum(est_evals)),
+           "gpu_launches": int(a.steps * (1 if a.workload == "plain" else len(np.unique((sides + 31) // 32)))
+                               + 2 * sum(est_evals)),
            "clocks": clk,
            "ess": {"mean_per_galaxy": float(ess_gal.mean().item()),
                    "frac_galaxies_ge_300": float((ess_gal >= 300).float().mean().item()),

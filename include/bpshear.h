@@ -185,6 +185,30 @@ size_t bs_fit_workspace_bytes(const bs_fit_args *args);
 bs_status bs_fit_galaxies(const bs_fit_args *args, const bs_fit_out *out,
                           void *workspace, size_t workspace_bytes, void *stream);
 
+/* Ragged batches: a launch plan over galaxies of mixed stamp sizes and
+ * per-galaxy PSFs (the graphical model of Fig. pgm allows a known PSF per
+ * galaxy).  Galaxies are split by the 32-column slots their side needs
+ * (<= 31, <= 63, <= 95, <= 127 px) and ordered largest first inside each
+ * class; each class gets its own persistent launch sized for its largest
+ * stamp.  With capture != 0 the class launches are recorded once as parallel
+ * branches of a CUDA graph that bs_fit_plan_launch replays (one graph launch
+ * per batch); otherwise they are issued one after another.
+ *   side_host: host copy of args->side (n_gal).
+ *   workspace: bs_fit_plan_workspace_bytes(args) bytes of device memory
+ *              (work lists and per-class counters), owned by the caller.
+ * The plan keeps the device pointers of args and out: those arrays must stay
+ * allocated at the same addresses while the plan is used; their contents may
+ * change between launches.  Creation synchronises `stream`.
+ * Errors: as bs_fit_galaxies, plus BS_ERR_INVALID_ARG for a side_host entry
+ * that is even or outside 3..max_side. */
+typedef struct bs_fit_plan_s *bs_fit_plan;
+size_t bs_fit_plan_workspace_bytes(const bs_fit_args *args);
+bs_status bs_fit_plan_create(const bs_fit_args *args, const bs_fit_out *out,
+                             const int32_t *side_host, int32_t capture, void *workspace,
+                             size_t workspace_bytes, void *stream, bs_fit_plan *plan);
+bs_status bs_fit_plan_launch(bs_fit_plan plan, void *stream);
+bs_status bs_fit_plan_destroy(bs_fit_plan plan);
+
 /* Log posterior and gradient of single parameter points, for checking and
  * for differentiation (same arithmetic as the fit's inner loop).
  *   gal_index device int32 [n_points]: which galaxy of `args` each point uses

@@ -12,12 +12,13 @@ The C ABI lives in include/bpshear.h; this package only marshals torch
 tensors into it (see ``api``), and ``synth`` draws seeded synthetic inputs.
 """
 from . import _ffi
-from .api import (DEFAULT_PRIOR, PIXEL_SCALE, FitConfig, FitPlan, RenderLogPost, ShearLogLike, ShearPlan,
-                  chain_ess, fit_galaxies, logpost_points, pack_stamps, psf_table, render, shear_loglike)
+from .api import (DEFAULT_PRIOR, PIXEL_SCALE, FitConfig, FitPlan, RaggedFitPlan, RenderLogPost, ShearLogLike,
+                  ShearPlan, chain_ess, fit_galaxies, logpost_points, pack_stamps, psf_table, render,
+                  shear_loglike)
 
-__all__ = ["DEFAULT_PRIOR", "PIXEL_SCALE", "FitConfig", "FitPlan", "RenderLogPost", "ShearLogLike",
-           "ShearPlan", "chain_ess", "fit_galaxies", "logpost_points", "pack_stamps", "psf_table", "render",
-           "shear_loglike", "lib"]
+__all__ = ["DEFAULT_PRIOR", "PIXEL_SCALE", "FitConfig", "FitPlan", "RaggedFitPlan", "RenderLogPost",
+           "ShearLogLike", "ShearPlan", "chain_ess", "fit_galaxies", "logpost_points", "pack_stamps", "psf_table",
+           "render", "shear_loglike", "lib"]
 
 
 def lib():

@@ -23,7 +23,8 @@ STATUS_NAMES = {0: "BS_OK", -1: "BS_ERR_INVALID_ARG", -2: "BS_ERR_CUDA", -3: "BS
 # every symbol the header declares
 EXPORTED = ["bs_prior_default", "bs_last_error", "bs_version", "bs_render", "bs_fit_workspace_bytes",
             "bs_fit_galaxies", "bs_logpost_points", "bs_chain_ess", "bs_shear_workspace_bytes",
-            "bs_shear_loglike", "bs_shear_estimate", "bs_shear_loglike_noalloc"]
+            "bs_shear_loglike", "bs_shear_estimate", "bs_shear_loglike_noalloc",
+            "bs_fit_plan_workspace_bytes", "bs_fit_plan_create", "bs_fit_plan_launch", "bs_fit_plan_destroy"]
 
 
 class BsError(RuntimeError):
@@ -100,8 +101,15 @@ def lib():
     L.bs_shear_loglike.argtypes = [C.POINTER(ShearData), f64, f64, f64, vp, i32, vp, sz, vp]
     L.bs_shear_estimate.argtypes = [C.POINTER(ShearData), C.POINTER(EstimateCfg), vp, vp, vp, vp, sz, vp]
     L.bs_shear_loglike_noalloc.argtypes = [C.POINTER(ShearData), f64, f64, f64, vp, vp]
+    L.bs_fit_plan_workspace_bytes.argtypes = [C.POINTER(FitArgs)]
+    L.bs_fit_plan_workspace_bytes.restype = sz
+    L.bs_fit_plan_create.argtypes = [C.POINTER(FitArgs), C.POINTER(FitOut), vp, i32, vp, sz, vp,
+                                     C.POINTER(C.c_void_p)]
+    L.bs_fit_plan_launch.argtypes = [vp, vp]
+    L.bs_fit_plan_destroy.argtypes = [vp]
     for nm in ("bs_render", "bs_fit_galaxies", "bs_logpost_points", "bs_chain_ess", "bs_shear_loglike",
-               "bs_shear_estimate", "bs_shear_loglike_noalloc"):
+               "bs_shear_estimate", "bs_shear_loglike_noalloc", "bs_fit_plan_create", "bs_fit_plan_launch",
+               "bs_fit_plan_destroy"):
         getattr(L, nm).restype = C.c_int
     _lib = L
     return L

@@ -81,7 +81,7 @@ def render(theta, side, psf, *, shear=None, offsets=None, total=None, pixel_scal
 @dataclass
 class FitConfig:
     n_chains: int = 4
-    n_warmup: int = 200
+    n_warmup: int = 100
     n_samples: int = 100
     n_leapfrog: int = 16
     target_accept: float = 0.8
@@ -170,6 +170,34 @@ class FitPlan:
         return dict(samples=self.samples, logp=self.logp, accepted=self.accepted,
                     accept_rate=self.accept_rate, step_size=self.step_size, inv_mass=self.inv_mass,
                     n_div=self.n_div, status=self.status, n_grad=self.n_grad)
+
+
+class RaggedFitPlan(FitPlan):
+    """A FitPlan over stamps of mixed sizes: galaxies are grouped by column-slot
+    class, each class runs its own persistent launch sized for it, and (with
+    capture) the launches replay as one CUDA graph (bs_fit_plan_*)."""
+
+    def __init__(self, data, offsets, side, psf, noise_sigma, init, cfg: FitConfig, *, capture=True, **kw):
+        super().__init__(data, offsets, side, psf, noise_sigma, init, cfg, **kw)
+        side_h = np.ascontiguousarray(side.cpu().numpy(), dtype=np.int32)
+        self.plan_ws_bytes = F.lib().bs_fit_plan_workspace_bytes(C.byref(self.args))
+        self.plan_ws = torch.empty(self.plan_ws_bytes, dtype=torch.uint8, device=data.device)
+        h = C.c_void_p()
+        F.check(F.lib().bs_fit_plan_create(C.byref(self.args), C.byref(self.out), side_h.ctypes.data_as(C.c_void_p),
+                                           int(capture), _p(self.plan_ws), self.plan_ws_bytes, _stream(),
+                                           C.byref(h)))
+        self.handle = h
+
+    def run(self, stream=None):
+        st = C.c_void_p(stream.cuda_stream) if stream is not None else _stream()
+        F.check(F.lib().bs_fit_plan_launch(self.handle, st))
+        return self
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            F.lib().bs_fit_plan_destroy(h)
+            self.handle = None
 
 
 def fit_galaxies(data, offsets, side, psf, noise_sigma, init, cfg: FitConfig | None = None, **kw):

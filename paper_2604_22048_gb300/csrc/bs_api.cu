@@ -185,21 +185,59 @@ static bs_status fill_fit_params(const bs_fit_args *a, bs::FitParams &p, const c
     return BS_OK;
 }
 
+}  // extern "C"
+
+namespace bs {
+
+// Validate a fit request and fill every launch parameter except the
+// scheduling fields (work list, counter).
+bs_status fit_params_from_args(const bs_fit_args *a, const bs_fit_out *o, FitParams &p, const char *who)
+{
+    bs_status st = fill_fit_params(a, p, who);
+    if (st != BS_OK) return st;
+    if (!o || !o->samples) return fail(BS_ERR_INVALID_ARG, "%s: NULL samples output", who);
+    if (!a->init) return fail(BS_ERR_INVALID_ARG, "%s: NULL init", who);
+    if (a->n_chains < 1 || a->n_chains > bs::kMaxChains)
+        return fail(BS_ERR_INVALID_ARG, "%s: n_chains must be 1..%d", who, bs::kMaxChains);
+    if (a->n_warmup < 0 || a->n_samples < 0 || a->n_leapfrog < 1)
+        return fail(BS_ERR_INVALID_ARG, "%s: n_warmup/n_samples/n_leapfrog", who);
+    if (!(a->target_accept > 0.f && a->target_accept < 1.f))
+        return fail(BS_ERR_INVALID_ARG, "%s: target_accept", who);
+    if (!(a->jitter >= 0.f && a->jitter < 1.f)) return fail(BS_ERR_INVALID_ARG, "%s: jitter", who);
+    p.n_chains = a->n_chains;
+    p.n_warmup = a->n_warmup;
+    p.n_samples = a->n_samples;
+    p.n_leapfrog = a->n_leapfrog;
+    p.target_accept = a->target_accept;
+    p.jitter = a->jitter;
+    p.random_steps = a->random_steps ? 1 : 0;
+    p.seed = a->seed;
+    p.n_windows = warmup_windows(a->n_warmup, a->adapt_mass != 0, p.win_start, p.win_end, bs::kMaxWindows);
+    p.samples = o->samples;
+    p.logp = o->logp;
+    p.accepted = o->accepted;
+    p.accept_rate = o->accept_rate;
+    p.step_size = o->step_size;
+    p.inv_mass = o->inv_mass;
+    p.n_div = o->n_divergent;
+    p.status = o->status;
+    p.n_grad = o->n_grad;
+    p.work = nullptr;
+    p.n_work = a->n_gal;
+    p.queue = nullptr;
+    return BS_OK;
+}
+
+}  // namespace bs
+
+extern "C" {
+
 bs_status bs_fit_galaxies(const bs_fit_args *a, const bs_fit_out *o, void *workspace,
                           size_t workspace_bytes, void *stream)
 {
     bs::FitParams p;
-    bs_status st = fill_fit_params(a, p, "bs_fit_galaxies");
+    bs_status st = bs::fit_params_from_args(a, o, p, "bs_fit_galaxies");
     if (st != BS_OK) return st;
-    if (!o || !o->samples) return fail(BS_ERR_INVALID_ARG, "bs_fit_galaxies: NULL samples output");
-    if (!a->init) return fail(BS_ERR_INVALID_ARG, "bs_fit_galaxies: NULL init");
-    if (a->n_chains < 1 || a->n_chains > bs::kMaxChains)
-        return fail(BS_ERR_INVALID_ARG, "bs_fit_galaxies: n_chains must be 1..%d", bs::kMaxChains);
-    if (a->n_warmup < 0 || a->n_samples < 0 || a->n_leapfrog < 1)
-        return fail(BS_ERR_INVALID_ARG, "bs_fit_galaxies: n_warmup/n_samples/n_leapfrog");
-    if (!(a->target_accept > 0.f && a->target_accept < 1.f))
-        return fail(BS_ERR_INVALID_ARG, "bs_fit_galaxies: target_accept");
-    if (!(a->jitter >= 0.f && a->jitter < 1.f)) return fail(BS_ERR_INVALID_ARG, "bs_fit_galaxies: jitter");
     if (!workspace || workspace_bytes < bs_fit_workspace_bytes(a))
         return fail(BS_ERR_OUT_OF_MEMORY, "bs_fit_galaxies: workspace of %zu bytes needed",
                     bs_fit_workspace_bytes(a));
@@ -223,6 +261,8 @@ bs_status bs_fit_galaxies(const bs_fit_args *a, const bs_fit_out *o, void *works
     p.status = o->status;
     p.n_grad = o->n_grad;
     p.queue = static_cast<unsigned int *>(workspace);
+    p.work = nullptr;
+    p.n_work = a->n_gal;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e;
     if (o->status) {

@@ -52,21 +52,45 @@ struct GalCtx {
     float inv_b;   // 1 / sigma^2
 };
 
+// Row layout of the staged tables for NCT = npad / 32 column slots per lane
+// (3 * npad floats per row u).  Slots are paired, (2p, 2p+1), so that a lane
+// loads both slots of a pair with one 8-byte access and the pair is processed
+// with packed FP32x2 arithmetic:
+//   pair p:      [Dx pairs: 64][Dy pairs: 64][T pairs: 64]   (float2 per lane)
+//   odd slot:    [D (x, y): 64][T: 32]                        (last slot, NCT odd)
+__host__ __device__ __forceinline__ int row_floats(int npad) { return 3 * npad; }
+
 struct SmemView {
-    float2 *Dt;    // [h_max][npad]
-    float *Tt;     // [h_max][npad]
-    float2 *G;     // [max_side][h_max], setup scratch
+    float *tab;    // [h_max][3 npad] data spectrum and transfer, paired layout
+    float2 *G;     // [max_side], setup scratch (one frequency row)
     float2 *tw;    // [max_side]
 };
 
 __device__ __forceinline__ SmemView smem_view(unsigned char *base, int h_max, int npad, int max_side)
 {
     SmemView v;
-    v.Dt = reinterpret_cast<float2 *>(base);
-    v.Tt = reinterpret_cast<float *>(v.Dt + (size_t)h_max * npad);
-    v.G = reinterpret_cast<float2 *>(v.Tt + (size_t)h_max * npad);
-    v.tw = v.G + (size_t)max_side * h_max;
+    v.tab = reinterpret_cast<float *>(base);
+    v.G = reinterpret_cast<float2 *>(v.tab + (size_t)h_max * row_floats(npad));
+    v.tw = v.G + (size_t)max_side;
     return v;
+}
+
+// Positions of slot j of lane l within a row: Dx, Dy, T.
+__device__ __forceinline__ void slot_offsets(int npad, int j, int l, int &ox, int &oy, int &ot)
+{
+    const int nct = npad >> 5, npair = nct >> 1;
+    const int p = j >> 1;
+    if (p < npair) {
+        const int base = p * 192, h = j & 1;
+        ox = base + 2 * l + h;
+        oy = base + 64 + 2 * l + h;
+        ot = base + 128 + 2 * l + h;
+    } else {
+        const int base = npair * 192;
+        ox = base + 2 * l;
+        oy = base + 2 * l + 1;
+        ot = base + 64 + l;
+    }
 }
 
 // (x/2)^nu K_nu(x) from K_nu(x) = int_0^inf exp(-x cosh t) cosh(nu t) dt by the
@@ -148,54 +172,60 @@ __device__ void setup_galaxy(const FitParams &P, int gal, const SmemView &sm, Ga
         sm.tw[m] = make_float2(co, s);   // exp(+2 pi i m / N)
     }
     __syncthreads();
-    // rows: G[iy][u] = sum_ix d[iy][ix] exp(-2 pi i u (ix - c) / N)
-    for (int o = tid; o < N * H; o += nth) {
-        const int iy = o / H, u = o - iy * H;
-        int idx = (int)(((long long)(N - u) * c) % N);   // -u c mod N
-        float re = 0.f, im = 0.f;
-        const int64_t rowoff = off + (int64_t)iy * N;
-        for (int ix = 0; ix < N; ++ix) {
-            const float d = load_pix(P.data, P.data_f64, rowoff + ix);
-            const float2 t = sm.tw[idx];
-            re = fmaf(d, t.x, re);
-            im = fmaf(-d, t.y, im);
-            idx += u;
-            if (idx >= N) idx -= N;
-        }
-        sm.G[iy * H + u] = make_float2(re, im);
-    }
-    __syncthreads();
-    // columns + scaling + transfer
     const bs_psf ps = P.psf[P.n_psf == 1 ? 0 : gal];
     const float sqrt2 = 1.41421356237309515f;
-    for (int o = tid; o < H * npad; o += nth) {
-        const int u = o / npad, vi = o - u * npad;
-        float2 Dv = make_float2(0.f, 0.f);
-        float Tv = 0.f;
-        if (vi < N) {
-            const int v = vi - c;
-            const int vm = ((v % N) + N) % N;
-            int idx = (int)(((long long)(N - vm) * c) % N);   // -v c mod N
+    const int rowf = row_floats(npad);
+    // one frequency row u at a time, so the scratch is a single column G[iy]
+    for (int u = 0; u < H; ++u) {
+        // G[iy] = sum_ix d[iy][ix] exp(-2 pi i u (ix - c) / N)
+        for (int iy = tid; iy < N; iy += nth) {
+            int idx = (int)(((long long)(N - u) * c) % N);   // -u c mod N
             float re = 0.f, im = 0.f;
-            for (int iy = 0; iy < N; ++iy) {
-                const float2 gv = sm.G[iy * H + u];
+            const int64_t rowoff = off + (int64_t)iy * N;
+            for (int ix = 0; ix < N; ++ix) {
+                const float d = load_pix(P.data, P.data_f64, rowoff + ix);
                 const float2 t = sm.tw[idx];
-                // gv * conj(t)
-                re = fmaf(gv.x, t.x, fmaf(gv.y, t.y, re));
-                im = fmaf(gv.y, t.x, fmaf(-gv.x, t.y, im));
-                idx += vm;
+                re = fmaf(d, t.x, re);
+                im = fmaf(-d, t.y, im);
+                idx += u;
                 if (idx >= N) idx -= N;
             }
-            const float scale = (u == 0 ? 1.0f : sqrt2) * gc.invN;
-            Dv = make_float2(re * scale, im * scale);
-            const float kx = u * gc.dk, ky = v * gc.dk;
-            Tv = scale * psf_transfer(ps, sqrtf(kx * kx + ky * ky)) * sincpi((float)u * gc.invN) *
-                 sincpi((float)v * gc.invN);
+            sm.G[iy] = make_float2(re, im);
         }
-        sm.Dt[o] = Dv;
-        sm.Tt[o] = Tv;
+        __syncthreads();
+        // D(u, v) = sum_iy G[iy] exp(-2 pi i v (iy - c) / N), scaled; transfer T(u, v)
+        float *row = sm.tab + (size_t)u * rowf;
+        const float scale = (u == 0 ? 1.0f : sqrt2) * gc.invN;
+        for (int vi = tid; vi < npad; vi += nth) {
+            float2 Dv = make_float2(0.f, 0.f);
+            float Tv = 0.f;
+            if (vi < N) {
+                const int v = vi - c;
+                const int vm = ((v % N) + N) % N;
+                int idx = (int)(((long long)(N - vm) * c) % N);   // -v c mod N
+                float re = 0.f, im = 0.f;
+                for (int iy = 0; iy < N; ++iy) {
+                    const float2 gv = sm.G[iy];
+                    const float2 t = sm.tw[idx];
+                    // gv * conj(t)
+                    re = fmaf(gv.x, t.x, fmaf(gv.y, t.y, re));
+                    im = fmaf(gv.y, t.x, fmaf(-gv.x, t.y, im));
+                    idx += vm;
+                    if (idx >= N) idx -= N;
+                }
+                Dv = make_float2(re * scale, im * scale);
+                const float kx = u * gc.dk, ky = v * gc.dk;
+                Tv = scale * psf_transfer(ps, sqrtf(kx * kx + ky * ky)) * sincpi((float)u * gc.invN) *
+                     sincpi((float)v * gc.invN);
+            }
+            int ox, oy, ot;
+            slot_offsets(npad, vi >> 5, vi & 31, ox, oy, ot);
+            row[ox] = Dv.x;
+            row[oy] = Dv.y;
+            row[ot] = Tv;
+        }
+        __syncthreads();
     }
-    __syncthreads();
 }
 
 __device__ __forceinline__ bool in_support(const FitParams &P, const float th[6])
@@ -204,88 +234,143 @@ __device__ __forceinline__ bool in_support(const FitParams &P, const float th[6]
     return th[0] > P.lf_lo && th[0] < P.lf_hi && th[1] > P.ls_lo && th[1] < P.ls_hi && E < 1.0f;
 }
 
-// Per-lane partial sums of one evaluation.
-template <int NC>
+// Packed FP32x2 helpers (two column slots of a lane in one instruction; each
+// half is rounded exactly like the scalar operation).
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+
+// Compensated accumulation of both halves (Knuth's TwoSum, packed).
+__device__ __forceinline__ void comp_add2(float2 &hi, float2 &lo, float2 x)
+{
+    const float2 s = add2(hi, x);
+    const float2 bp = add2(s, neg2(hi));
+    const float2 ap = add2(s, neg2(bp));
+    const float2 e = add2(add2(hi, neg2(ap)), add2(x, neg2(bp)));
+    hi = s;
+    lo = add2(lo, e);
+}
+
+// Per-lane partial sums of one evaluation: slot pairs packed, odd slot scalar.
+template <int NCT>
 struct Sums {
-    float Sa, Swkx2, Sbkx;              // sum a, sum w kx^2, sum b kx
-    float Wc[NC], Wkx[NC], Bc[NC];      // per column: sum w, sum w kx, sum b
-    float chi_hi, chi_lo;               // compensated sum |Dt - Mt|^2
+    static constexpr int NP = NCT / 2 > 0 ? NCT / 2 : 1;
+    float2 Sa, Swkx2, Sbkx;                 // sum a, sum w kx^2, sum b kx (both halves)
+    float2 Wc[NP], Wkx[NP], Bc[NP];         // per slot: sum w, sum w kx, sum b
+    float sWc, sWkx, sBc;                   // odd slot
+    float2 chi_hi, chi_lo;                  // compensated sum |Dt - Mt|^2
 };
 
-// Model-data terms of one row u (all NC column slots of this lane).
-template <int NC, bool LL>
-__device__ __forceinline__ void row_terms(Sums<NC> &S, const float2 *__restrict__ Drow,
-                                          const float *__restrict__ Trow, float kx, float akx2,
-                                          float Xr, float Xi, const float (&Yr)[NC], const float (&Yi)[NC],
-                                          const float (&cst)[NC], const float (&gky)[NC], float F2)
+// Per-lane, per-slot constants of one evaluation.
+template <int NCT>
+struct SlotConst {
+    static constexpr int NP = NCT / 2 > 0 ? NCT / 2 : 1;
+    float2 Yr[NP], Yi[NP], cst[NP], gky[NP];   // F exp(-i ky p dy), 1 + be ky^2, ga ky
+    float sYr, sYi, scst, sgky;
+};
+
+// Model-data terms of one row u for all column slots of this lane.
+template <int NCT, bool LL>
+__device__ __forceinline__ void row_terms(Sums<NCT> &S, const SlotConst<NCT> &K,
+                                          const float *__restrict__ row, float kx, float akx2,
+                                          float Xr, float Xi, float F2)
 {
+    constexpr int NPAIR = NCT / 2;
+    const int lane = threadIdx.x & 31;
     const float kx2 = kx * kx;
+    const float2 kxv = f2(kx), kx2v = f2(kx2), akv = f2(akx2), Xrv = f2(Xr), Xiv = f2(Xi), nXiv = f2(-Xi);
 #pragma unroll
-    for (int j = 0; j < NC; ++j) {
-        const float2 D = Drow[32 * j];
-        const float T = Trow[32 * j];
-        const float s = fmaf(gky[j], kx, akx2 + cst[j]);      // 1 + r0^2 q(k)
+    for (int p = 0; p < NPAIR; ++p) {
+        const float *b = row + p * 192 + 2 * lane;
+        const float2 Dx = *reinterpret_cast<const float2 *>(b);
+        const float2 Dy = *reinterpret_cast<const float2 *>(b + 64);
+        const float2 T = *reinterpret_cast<const float2 *>(b + 128);
+        const float2 s = fma2(K.gky[p], kxv, add2(akv, K.cst[p]));     // 1 + r0^2 q(k)
+        const float2 rs = make_float2(rsqrtf(s.x), rsqrtf(s.y));
+        const float2 rs2 = mul2(rs, rs);
+        const float2 A = mul2(mul2(T, rs2), rs);                        // |M| / F
+        const float2 Pr = fma2(nXiv, K.Yi[p], mul2(Xrv, K.Yr[p]));      // F exp(-i k.delta)
+        const float2 Pi = fma2(Xiv, K.Yr[p], mul2(Xrv, K.Yi[p]));
+        const float2 zr = fma2(Dx, Pr, mul2(Dy, Pi));                  // conj(D) * phase
+        const float2 zi = fma2(Dx, Pi, neg2(mul2(Dy, Pr)));
+        const float2 a = mul2(A, fma2(neg2(A), f2(F2), zr));            // Re conj(D - M) M
+        const float2 bb = mul2(A, zi);                                  // Im conj(D - M) M
+        const float2 w = mul2(a, rs2);                                  // a / s
+        S.Sa = add2(S.Sa, a);
+        S.Wc[p] = add2(S.Wc[p], w);
+        S.Wkx[p] = fma2(w, kxv, S.Wkx[p]);
+        S.Swkx2 = fma2(w, kx2v, S.Swkx2);
+        S.Bc[p] = add2(S.Bc[p], bb);
+        S.Sbkx = fma2(bb, kxv, S.Sbkx);
+        if (LL) {
+            const float2 Rr = fma2(neg2(A), Pr, Dx);
+            const float2 Ri = fma2(neg2(A), Pi, Dy);
+            comp_add2(S.chi_hi, S.chi_lo, fma2(Rr, Rr, mul2(Ri, Ri)));
+        }
+    }
+    if (NCT & 1) {
+        const float *b = row + NPAIR * 192;
+        const float2 D = *reinterpret_cast<const float2 *>(b + 2 * lane);
+        const float T = b[64 + lane];
+        const float s = fmaf(K.sgky, kx, akx2 + K.scst);
         const float rs = rsqrtf(s);
         const float rs2 = rs * rs;
-        const float A = T * rs2 * rs;                         // |M| / F
-        const float Pr = Xr * Yr[j] - Xi * Yi[j];             // F exp(-i k.delta)
-        const float Pi = Xr * Yi[j] + Xi * Yr[j];
-        const float zr = fmaf(D.x, Pr, D.y * Pi);             // conj(D) * phase
+        const float A = T * rs2 * rs;
+        const float Pr = Xr * K.sYr - Xi * K.sYi;
+        const float Pi = Xr * K.sYi + Xi * K.sYr;
+        const float zr = fmaf(D.x, Pr, D.y * Pi);
         const float zi = fmaf(D.x, Pi, -D.y * Pr);
-        const float a = A * fmaf(-A, F2, zr);                 // Re conj(D - M) M
-        const float b = A * zi;                               // Im conj(D - M) M
-        const float w = a * rs2;                              // a / s
-        S.Sa += a;
-        S.Wc[j] += w;
-        S.Wkx[j] = fmaf(w, kx, S.Wkx[j]);
-        S.Swkx2 = fmaf(w, kx2, S.Swkx2);
-        S.Bc[j] += b;
-        S.Sbkx = fmaf(b, kx, S.Sbkx);
+        const float a = A * fmaf(-A, F2, zr);
+        const float bb = A * zi;
+        const float w = a * rs2;
+        S.Sa.x += a;
+        S.sWc += w;
+        S.sWkx = fmaf(w, kx, S.sWkx);
+        S.Swkx2.x = fmaf(w, kx2, S.Swkx2.x);
+        S.sBc += bb;
+        S.Sbkx.x = fmaf(bb, kx, S.Sbkx.x);
         if (LL) {
             const float Rr = fmaf(-A, Pr, D.x);
             const float Ri = fmaf(-A, Pi, D.y);
-            comp_add(S.chi_hi, S.chi_lo, fmaf(Rr, Rr, Ri * Ri));
+            comp_add(S.chi_hi.x, S.chi_lo.x, fmaf(Rr, Rr, Ri * Ri));
         }
     }
 }
 
 // Half-plane pass, two rows per iteration (the row phase advances by
 // exp(-2 pi i dx / N) per row).
-template <int NC, bool LL>
-__device__ __forceinline__ void half_plane(Sums<NC> &S, const float2 *__restrict__ Dt,
-                                           const float *__restrict__ Tt, int npad, int H, float dk,
-                                           float al, float exr, float exi, const float (&Yr)[NC],
-                                           const float (&Yi)[NC], const float (&cst)[NC],
-                                           const float (&gky)[NC], float F2)
+template <int NCT, bool LL>
+__device__ __forceinline__ void half_plane(Sums<NCT> &S, const SlotConst<NCT> &K,
+                                           const float *__restrict__ tab, int H, float dk, float al,
+                                           float exr, float exi, float F2)
 {
-    const int lane = threadIdx.x & 31;
-    const float2 *Drow = Dt + lane;
-    const float *Trow = Tt + lane;
+    constexpr int ROWF = 96 * NCT;
     const float e2r = exr * exr - exi * exi, e2i = 2.0f * exr * exi;   // two-row step
     float Xr = 1.0f, Xi = 0.0f;
+    const float *row = tab;
     int u = 0;
     for (; u + 1 < H; u += 2) {
         const float kx0 = (float)u * dk, kx1 = (float)(u + 1) * dk;
         const float X1r = Xr * exr - Xi * exi, X1i = Xr * exi + Xi * exr;
-        row_terms<NC, LL>(S, Drow, Trow, kx0, al * kx0 * kx0, Xr, Xi, Yr, Yi, cst, gky, F2);
-        row_terms<NC, LL>(S, Drow + npad, Trow + npad, kx1, al * kx1 * kx1, X1r, X1i, Yr, Yi, cst, gky, F2);
+        row_terms<NCT, LL>(S, K, row, kx0, al * kx0 * kx0, Xr, Xi, F2);
+        row_terms<NCT, LL>(S, K, row + ROWF, kx1, al * kx1 * kx1, X1r, X1i, F2);
         const float nXr = Xr * e2r - Xi * e2i;
         Xi = Xr * e2i + Xi * e2r;
         Xr = nXr;
-        Drow += 2 * npad;
-        Trow += 2 * npad;
+        row += 2 * ROWF;
     }
     if (u < H) {
         const float kx0 = (float)u * dk;
-        row_terms<NC, LL>(S, Drow, Trow, kx0, al * kx0 * kx0, Xr, Xi, Yr, Yi, cst, gky, F2);
+        row_terms<NCT, LL>(S, K, row, kx0, al * kx0 * kx0, Xr, Xi, F2);
     }
 }
 
 // Log posterior (if want_ll) and gradient at th, warp-cooperative.
 template <int NC>
 __device__ __forceinline__ double eval_logpost(const FitParams &P, const GalCtx &gc,
-                                               const float2 *__restrict__ Dt,
-                                               const float *__restrict__ Tt, const float vcol[NC],
+                                               const float *__restrict__ tab, const float vcol[NC],
                                                const float th[6], float g[6], bool want_ll)
 {
     const float F = exp10f(th[0]);
@@ -313,27 +398,57 @@ __device__ __forceinline__ double eval_logpost(const FitParams &P, const GalCtx 
         cst[j] = fmaf(be * ky[j], ky[j], 1.0f);
         gky[j] = ga * ky[j];
     }
+    SlotConst<NC> K;
     Sums<NC> S;
-    S.Sa = 0.f;
-    S.Swkx2 = 0.f;
-    S.Sbkx = 0.f;
-    S.chi_hi = 0.f;
-    S.chi_lo = 0.f;
+    constexpr int NPAIR = NC / 2;
 #pragma unroll
-    for (int j = 0; j < NC; ++j) { S.Wc[j] = 0.f; S.Wkx[j] = 0.f; S.Bc[j] = 0.f; }
+    for (int p = 0; p < NPAIR; ++p) {
+        K.Yr[p] = make_float2(Yr[2 * p], Yr[2 * p + 1]);
+        K.Yi[p] = make_float2(Yi[2 * p], Yi[2 * p + 1]);
+        K.cst[p] = make_float2(cst[2 * p], cst[2 * p + 1]);
+        K.gky[p] = make_float2(gky[2 * p], gky[2 * p + 1]);
+        S.Wc[p] = f2(0.f);
+        S.Wkx[p] = f2(0.f);
+        S.Bc[p] = f2(0.f);
+    }
+    if (NC & 1) {
+        K.sYr = Yr[NC - 1];
+        K.sYi = Yi[NC - 1];
+        K.scst = cst[NC - 1];
+        K.sgky = gky[NC - 1];
+    }
+    S.Sa = f2(0.f);
+    S.Swkx2 = f2(0.f);
+    S.Sbkx = f2(0.f);
+    S.sWc = 0.f;
+    S.sWkx = 0.f;
+    S.sBc = 0.f;
+    S.chi_hi = f2(0.f);
+    S.chi_lo = f2(0.f);
     if (want_ll)
-        half_plane<NC, true>(S, Dt, Tt, P.npad, gc.H, dk, al, exr, exi, Yr, Yi, cst, gky, F2);
+        half_plane<NC, true>(S, K, tab, gc.H, dk, al, exr, exi, F2);
     else
-        half_plane<NC, false>(S, Dt, Tt, P.npad, gc.H, dk, al, exr, exi, Yr, Yi, cst, gky, F2);
+        half_plane<NC, false>(S, K, tab, gc.H, dk, al, exr, exi, F2);
 
-    float Sa = S.Sa, Swkx2 = S.Swkx2, Sbkx = S.Sbkx;
+    float Sa = S.Sa.x + S.Sa.y, Swkx2 = S.Swkx2.x + S.Swkx2.y, Sbkx = S.Sbkx.x + S.Sbkx.y;
     float Sw = 0.f, Swky2 = 0.f, Swkxky = 0.f, Sbky = 0.f;
 #pragma unroll
     for (int j = 0; j < NC; ++j) {
-        Sw += S.Wc[j];
-        Swky2 = fmaf(ky[j] * ky[j], S.Wc[j], Swky2);
-        Swkxky = fmaf(ky[j], S.Wkx[j], Swkxky);
-        Sbky = fmaf(ky[j], S.Bc[j], Sbky);
+        float wc, wkx, bc;
+        if (j < 2 * NPAIR) {
+            const int p = j >> 1;
+            wc = (j & 1) ? S.Wc[p].y : S.Wc[p].x;
+            wkx = (j & 1) ? S.Wkx[p].y : S.Wkx[p].x;
+            bc = (j & 1) ? S.Bc[p].y : S.Bc[p].x;
+        } else {
+            wc = S.sWc;
+            wkx = S.sWkx;
+            bc = S.sBc;
+        }
+        Sw += wc;
+        Swky2 = fmaf(ky[j] * ky[j], wc, Swky2);
+        Swkxky = fmaf(ky[j], wkx, Swkxky);
+        Sbky = fmaf(ky[j], bc, Sbky);
     }
     Sa = warp_sum(Sa);
     Sw = warp_sum(Sw);
@@ -359,7 +474,11 @@ __device__ __forceinline__ double eval_logpost(const FitParams &P, const GalCtx 
     g[4] = gc.p * Sbkx * ib - th[4] * P.inv_sxy2;
     g[5] = gc.p * Sbky * ib - th[5] * P.inv_sxy2;
     if (!want_ll) return 0.0;
-    const double chi2 = warp_sum_comp(S.chi_hi, S.chi_lo);
+    // merge the two halves of the compensated pair, then the warp
+    float chi_hi, chi_lo;
+    two_sum(S.chi_hi.x, S.chi_hi.y, chi_hi, chi_lo);
+    chi_lo += S.chi_lo.x + S.chi_lo.y;
+    const double chi2 = warp_sum_comp(chi_hi, chi_lo);
     const float lprior = P.prior_const - 0.5f * (th[4] * th[4] + th[5] * th[5]) * P.inv_sxy2 +
                          2.0f * log1pf(-E) - 0.5f * E * P.inv_se2;
     return -0.5 * chi2 * (double)ib + (double)lprior;
@@ -468,7 +587,7 @@ __device__ void run_chain(const FitParams &P, const GalCtx &gc, const SmemView &
             for (int k = 0; k < 6; ++k) x[k] = __shfl_sync(BS_FULL_MASK, tp, k);
             if (!in_support(P, x)) { ok = false; break; }
             float gg[6];
-            const double v = eval_logpost<NC>(P, gc, sm.Dt, sm.Tt, vcol, x, gg, l == nst - 1);
+            const double v = eval_logpost<NC>(P, gc, sm.tab, vcol, x, gg, l == nst - 1);
             ++ngrad;
             if (l == nst - 1) lpp = v;
             gp = pick6(gg, pi);
@@ -591,10 +710,14 @@ __global__ void __launch_bounds__(256, MINB) fit_kernel(const FitParams P)
     const SmemView sm = smem_view(smem_raw, P.h_max, P.npad, P.max_side);
     const int warp = threadIdx.x >> 5;
     for (;;) {
-        if (threadIdx.x == 0) s_gal = (int)atomicAdd(P.queue, 1u);
+        if (threadIdx.x == 0) {
+            // positions in the work list (or galaxy indices when there is none)
+            const int q = (int)atomicAdd(P.queue, 1u);
+            s_gal = q < P.n_work ? (P.work ? P.work[q] : q) : -1;
+        }
         __syncthreads();
         const int gal = s_gal;
-        if (gal >= P.n_gal) break;
+        if (gal < 0 || gal >= P.n_gal) break;
         if (!side_ok(P, P.side[gal])) {     // uniform across the CTA
             if (threadIdx.x == 0 && P.status) P.status[gal] = 2;
             __syncthreads();
@@ -621,7 +744,7 @@ __device__ void point_eval(const FitParams &P, const GalCtx &gc, const SmemView 
     for (int i = 0; i < 6; ++i) th[i] = theta[i];
     double v = -INFINITY;
     if (in_support(P, th)) {
-        v = eval_logpost<NC>(P, gc, sm.Dt, sm.Tt, vcol, th, g, true);
+        v = eval_logpost<NC>(P, gc, sm.tab, vcol, th, g, true);
     } else {
 #pragma unroll
         for (int i = 0; i < 6; ++i) g[i] = NAN;
@@ -649,7 +772,7 @@ __global__ void __launch_bounds__(32) logpost_points_kernel(const FitParams P, i
         const float *th = theta + (size_t)i * 6;
         double *lp = logp ? logp + i : nullptr;
         float *gr = grad ? grad + (size_t)i * 6 : nullptr;
-        switch (gc.NC) {
+        switch (P.npad >> 5) {     // the table layout follows the launch's slot count
             case 1: point_eval<1>(P, gc, sm, th, lp, gr); break;
             case 2: point_eval<2>(P, gc, sm, th, lp, gr); break;
             case 3: point_eval<3>(P, gc, sm, th, lp, gr); break;
@@ -690,8 +813,7 @@ size_t fit_smem_bytes(int max_side)
 {
     const int h = (max_side + 1) / 2;
     const int npad = 32 * ((max_side + 31) / 32);
-    return (size_t)h * npad * (sizeof(float2) + sizeof(float)) + (size_t)max_side * h * sizeof(float2) +
-           (size_t)max_side * sizeof(float2);
+    return (size_t)h * row_floats(npad) * sizeof(float) + 2 * (size_t)max_side * sizeof(float2);
 }
 
 int fit_blocks_per_sm(int n_chains, int max_side)

@@ -47,7 +47,10 @@ struct FitParams {
     int32_t *n_div;
     int32_t *status;
     int32_t *n_grad;
-    // scheduling
+    // scheduling: the CTAs take positions 0..n_work-1 of `work` (galaxy
+    // indices; NULL = identity) from the atomic counter `queue`
+    const int32_t *work;
+    int n_work;
     unsigned int *queue;
     int max_side;
     int h_max, npad;   // shared-memory geometry for max_side
