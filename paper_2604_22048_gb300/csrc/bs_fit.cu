@@ -281,6 +281,7 @@ __device__ __forceinline__ void row_terms(Sums<NCT> &S, const SlotConst<NCT> &K,
     const int lane = threadIdx.x & 31;
     const float kx2 = kx * kx;
     const float2 kxv = f2(kx), kx2v = f2(kx2), akv = f2(akx2), Xrv = f2(Xr), Xiv = f2(Xi), nXiv = f2(-Xi);
+    const float2 nF2v = f2(-F2);
 #pragma unroll
     for (int p = 0; p < NPAIR; ++p) {
         const float *b = row + p * 192 + 2 * lane;
@@ -295,7 +296,7 @@ __device__ __forceinline__ void row_terms(Sums<NCT> &S, const SlotConst<NCT> &K,
         const float2 Pi = fma2(Xiv, K.Yr[p], mul2(Xrv, K.Yi[p]));
         const float2 zr = fma2(Dx, Pr, mul2(Dy, Pi));                  // conj(D) * phase
         const float2 zi = fma2(Dx, Pi, neg2(mul2(Dy, Pr)));
-        const float2 a = mul2(A, fma2(neg2(A), f2(F2), zr));            // Re conj(D - M) M
+        const float2 a = mul2(A, fma2(A, nF2v, zr));                    // Re conj(D - M) M
         const float2 bb = mul2(A, zi);                                  // Im conj(D - M) M
         const float2 w = mul2(a, rs2);                                  // a / s
         S.Sa = add2(S.Sa, a);
