@@ -39,8 +39,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="plain", choices=["plain", "ragged"],
-                    help="plain: 10^4 x 53 px, one Gaussian PSF; ragged: 10^5, 25-101 px, per-galaxy Moffat")
+    ap.add_argument("--workload", default="plain", choices=["plain", "ragged", "serve"],
+                    help="plain: 10^4 x 53 px, one Gaussian PSF; ragged: 10^5, 25-101 px, per-galaxy Moffat; "
+                         "serve: 10^6 requests of the ragged kind, served vs plain per-size batches")
+    ap.add_argument("--serve-requests", type=int, default=200000,
+                    help="requests of the serving comparison added to the plain line (0: none)")
     ap.add_argument("--n-gal", type=int, default=None)
     ap.add_argument("--side", type=int, default=53)
     ap.add_argument("--chains", type=int, default=4)
@@ -52,7 +55,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     a = ap.parse_args()
     if a.n_gal is None:
-        a.n_gal = 10000 if a.workload == "plain" else 100000
+        a.n_gal = {"plain": 10000, "ragged": 100000, "serve": 1000000}[a.workload]
     return a
 
 
@@ -384,6 +387,12 @@ def our_arm(a, world, rank, local_rank):
 
     if not a.no_e2e:
         out["e2e"] = e2e_run(a, world, inp, plan, shear, step, barrier, dev)
+    if a.workload == "plain" and a.serve_requests > 0 and world == 1:
+        del inp, plan, shear
+        torch.cuda.empty_cache()
+        res = serve_compare(a, dev, a.serve_requests, min(a.serve_requests, 50000))
+        out["serving"] = {"metric": SERVE_METRIC, "config": "batching-recipe requests (25-101 px, per-galaxy "
+                                                            "Moffat), Poisson arrivals, seed 7"} | res
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(a)
     return out
@@ -415,6 +424,262 @@ def e2e_run(a, world, inp, plan, shear, step, barrier, dev):
             "d2h_bytes_per_step": int(d2h)}
 
 
+# ----------------------------------------------------------------------------- serving
+
+SERVE_METRIC = "galaxies/sec at 300 ESS/galaxy (served vs plain batch, 1 GB300); p50/p99 latency"
+
+
+def serving_pool(a, dev, n_pool):
+    """Host copies of n_pool batching-recipe galaxies (25-101 px, per-galaxy
+    Moffat PSF), the stamps requests are cut from."""
+    b = argparse.Namespace(**vars(a))
+    b.workload, b.n_gal = "ragged", n_pool
+    inp = make_inputs_gpu(b, 0, dev)
+    t = inp["truth"]
+    return {"stamps": np.ascontiguousarray(inp["data"].cpu().numpy(), dtype=np.float32),
+            "offsets": inp["offsets"].cpu().numpy(), "sides": t.side.astype(np.int32),
+            "fwhm": t.psf_fwhm.astype(np.float32),
+            "init": np.ascontiguousarray(inp["init"].cpu().numpy(), dtype=np.float32)}
+
+
+def arrivals(n, rate, seed=7):
+    """Poisson arrival times (ns from the start); rate None: all at once."""
+    if rate is None:
+        return np.zeros(n, dtype=np.int64)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return (np.cumsum(rng.exponential(1.0 / rate, size=n)) * 1e9).astype(np.int64)
+
+
+def _lat_summary(lat_ns, done_ns, arr_ns):
+    span = (done_ns.max() - arr_ns.min()) / 1e9
+    return {"galaxies_per_s": len(lat_ns) / span, "p50_ms": float(np.percentile(lat_ns, 50) / 1e6),
+            "p99_ms": float(np.percentile(lat_ns, 99) / 1e6), "mean_ms": float(lat_ns.mean() / 1e6),
+            "makespan_s": span}
+
+
+def run_served(a, pool, n_req, rate, ess_every=64):
+    """Requests cut from the pool arrive at `rate` (Poisson, or all at once)
+    and go through the server's public API (bs_serve_submit/poll)."""
+    import torch
+    from paper_2604_22048_gb300 import api
+    cfg = api.FitConfig(n_chains=a.chains, n_warmup=a.n_warmup, n_samples=a.n_samples, n_leapfrog=a.leapfrog)
+    srv = api.Server(cfg, max_side=101, arena_bytes=512 << 20)
+    P = len(pool["sides"])
+    item = np.arange(n_req) % P
+    reqs = api.Server.requests(pool["stamps"], pool["offsets"][item], pool["sides"][item], "moffat",
+                               pool["fwhm"][item], 3.0, np.ones(n_req, np.float32), pool["init"],
+                               (10 ** 7 + np.arange(n_req)).astype(np.uint64), init_index=item)
+    t_arr = arrivals(n_req, rate)
+    t0 = srv.now_ns() + 2_000_000
+    reqs["t_arrival_ns"] = t_arr + t0
+    lat, done, side_done = [], [], []
+    kept = []
+    i = 0
+    got = 0
+    while got < n_req:
+        now = srv.now_ns()
+        j = int(np.searchsorted(reqs["t_arrival_ns"], now, side="right"))
+        if j > i:
+            srv.submit(reqs[i:j])
+            i = j
+        comps = srv.poll(timeout_us=0 if i < n_req else 2000)
+        if len(comps):
+            got += len(comps)
+            lat.append(comps["t_done_ns"] - comps["t_arrival_ns"])
+            done.append(comps["t_done_ns"])
+            side_done.append(comps["side"])
+            for c in comps[comps["tag"] % ess_every == 0]:
+                kept.append(srv.result(c)["samples"])
+        elif i < n_req:
+            time.sleep(max(0.0, min(2e-4, (reqs["t_arrival_ns"][i] - now) / 1e9)))
+    stats = srv.stats()
+    srv.close()
+    lat = np.concatenate(lat)
+    done = np.concatenate(done)
+    out = _lat_summary(lat, done, reqs["t_arrival_ns"]) | {
+        "launches": stats["launches"], "admission_rounds": stats["ticks"],
+        "arena_high_water_mb": stats["arena_high_water"] / 2 ** 20, "waits_memory": stats["waits_memory"],
+        "waits_inflight": stats["waits_inflight"], "waits_streams": stats["waits_streams"]}
+    sam = torch.from_numpy(np.stack(kept, axis=1)).cuda()      # [6, m, C, S]
+    ess, _ = api.chain_ess(sam)
+    eg = ess.mean(dim=1)
+    out["ess"] = {"mean_per_galaxy": float(eg.mean()), "frac_ge_300": float((eg >= 300).float().mean()),
+                  "galaxies_checked": int(sam.shape[1])}
+    return out
+
+
+class PlainPerSize:
+    """The plain batched path the served one is compared with: galaxies are
+    bucketed by exact stamp side; a bucket is launched (bs_fit_galaxies, one
+    fixed-size batch of as many galaxies as the GPU holds at once) when it is
+    full or its oldest request has waited 1 s; launches do not overlap; each
+    launch copies its stamps in and its samples out."""
+
+    def __init__(self, a, pool, dev):
+        import torch
+        from paper_2604_22048_gb300 import api
+        self.a, self.pool, self.dev = a, pool, dev
+        self.cfg = api.FitConfig(n_chains=a.chains, n_warmup=a.n_warmup, n_samples=a.n_samples,
+                                 n_leapfrog=a.leapfrog)
+        self.plans = {}
+        self.torch = torch
+        self.api = api
+
+    def plan(self, N):
+        if N not in self.plans:
+            torch, api = self.torch, self.api
+            B = api.resident_galaxies(self.a.chains, N)
+            d = self.dev
+            data = torch.zeros(B * N * N, dtype=torch.float32, device=d)
+            offs = torch.arange(B, dtype=torch.int64, device=d) * (N * N)
+            side = torch.full((B,), N, dtype=torch.int32, device=d)
+            psf_h = np.zeros(B, dtype=[("kind", "<i4"), ("fwhm", "<f4"), ("beta", "<f4")])
+            psf_t = torch.from_numpy(psf_h.view(np.uint8).copy()).to(d)
+            sigma = torch.ones(B, dtype=torch.float32, device=d)
+            init = torch.zeros((B, self.a.chains, 6), dtype=torch.float32, device=d)
+            gid = torch.zeros(B, dtype=torch.int64, device=d)
+            p = api.FitPlan(data, offs, side, (psf_t, B), sigma, init, self.cfg, gal_id=gid, max_side=N,
+                            want=("status",))
+            host = {"data": torch.empty(B * N * N, dtype=torch.float32).pin_memory(),
+                    "psf": torch.empty(psf_t.numel(), dtype=torch.uint8).pin_memory(),
+                    "init": torch.empty((B, self.a.chains, 6), dtype=torch.float32).pin_memory(),
+                    "gid": torch.empty(B, dtype=torch.int64).pin_memory(),
+                    "samples": torch.empty(p.samples.numel(), dtype=torch.float32).pin_memory()}
+            self.plans[N] = (B, p, data, psf_t, init, gid, host)
+        return self.plans[N]
+
+    def launch(self, N, idx, req_item, gal_id):
+        torch = self.torch
+        B, p, data, psf_t, init, gid, host = self.plan(N)
+        n = len(idx)
+        it = req_item[idx]
+        pool = self.pool
+        st = pool["stamps"]
+        hd = host["data"].numpy()
+        for k, m in enumerate(it):
+            o = int(pool["offsets"][m])
+            hd[k * N * N:(k + 1) * N * N] = st[o:o + N * N]
+        ph = host["psf"].numpy().view([("kind", "<i4"), ("fwhm", "<f4"), ("beta", "<f4")])
+        ph["kind"][:n] = 2
+        ph["fwhm"][:n] = pool["fwhm"][it]
+        ph["beta"][:n] = 3.0
+        host["init"].numpy()[:n] = pool["init"][it]
+        host["gid"].numpy()[:n] = gal_id[idx].astype(np.int64)
+        data[:n * N * N].copy_(host["data"][:n * N * N], non_blocking=True)
+        psf_t.copy_(host["psf"], non_blocking=True)
+        init[:n].copy_(host["init"][:n], non_blocking=True)
+        gid[:n].copy_(host["gid"][:n], non_blocking=True)
+        p.args.n_gal = n
+        p.args.n_psf = n
+        p.run()
+        cnt = 6 * n * self.a.chains * self.a.n_samples
+        host["samples"][:cnt].copy_(p.samples.view(-1)[:cnt], non_blocking=True)
+        torch.cuda.synchronize(self.dev)
+
+    def run(self, n_req, rate):
+        from collections import deque
+        P = len(self.pool["sides"])
+        item = np.arange(n_req) % P
+        sides = self.pool["sides"][item]
+        gal_id = (10 ** 7 + np.arange(n_req)).astype(np.uint64)
+        t_arr = arrivals(n_req, rate)
+        for N in np.unique(sides):
+            self.plan(int(N))
+        buckets = {}
+        done = np.zeros(n_req, dtype=np.int64)
+        t0 = time.perf_counter_ns() + 2_000_000
+        i = 0
+        finished = 0
+        launches = 0
+        while finished < n_req:
+            now = time.perf_counter_ns() - t0
+            j = int(np.searchsorted(t_arr, now, side="right"))
+            for k in range(i, j):
+                buckets.setdefault(int(sides[k]), deque()).append(k)
+            i = j
+            pick = None
+            for N, q in buckets.items():
+                if q and len(q) >= self.plans[N][0] and (pick is None or q[0] < buckets[pick][0]):
+                    pick = N
+            if pick is None:
+                for N, q in buckets.items():
+                    if q and now - t_arr[q[0]] >= 1_000_000_000 and (pick is None or q[0] < buckets[pick][0]):
+                        pick = N
+            if pick is None:
+                nxt = [t_arr[q[0]] + 1_000_000_000 for q in buckets.values() if q]
+                if i < n_req:
+                    nxt.append(t_arr[i])
+                wait = (min(nxt) - now) / 1e9 if nxt else 1e-4
+                time.sleep(min(max(wait, 0.0), 0.002))
+                continue
+            q = buckets[pick]
+            B = self.plans[pick][0]
+            idx = np.array([q.popleft() for _ in range(min(B, len(q)))], dtype=np.int64)
+            self.launch(pick, idx, item, gal_id)
+            launches += 1
+            done[idx] = time.perf_counter_ns() - t0
+            finished += len(idx)
+        return _lat_summary(done - t_arr, done, t_arr) | {"launches": launches}
+
+
+def serve_compare(a, dev, n_req, n_pool):
+    """Served vs plain per-size batched path on the same request stream:
+    first the plain path's throughput with every request present at once,
+    then Poisson arrivals at 0.8x and 1.2x that rate through both paths."""
+    pool = serving_pool(a, dev, n_pool)
+    plain = PlainPerSize(a, pool, dev)
+    plain.run(min(n_req, 4 * n_pool) // 8, None)          # warm-up (plans, pinned buffers)
+    sat_plain = plain.run(n_req, None)
+    run_served(a, pool, min(n_req, 20000), None)          # warm-up
+    sat_served = run_served(a, pool, n_req, None)
+    lam = sat_plain["galaxies_per_s"]
+    res = {"requests": n_req, "distinct_stamps": n_pool,
+           "plain_saturated": sat_plain, "served_saturated": sat_served}
+    for f in (0.8, 1.2):
+        res[f"plain_at_{f}x"] = plain.run(n_req, f * lam)
+        res[f"served_at_{f}x"] = run_served(a, pool, n_req, f * lam)
+    res["served_over_plain_at_1.2x"] = (res["served_at_1.2x"]["galaxies_per_s"] /
+                                        res["plain_at_1.2x"]["galaxies_per_s"])
+    res["arrival_rate_1x"] = lam
+    sides = pool["sides"][np.arange(n_req) % n_pool].astype(np.int64)
+    res["h2d_bytes"] = int(np.sum(4 * sides ** 2) + n_req * (24 * a.chains + 40))
+    res["d2h_bytes"] = int(n_req * (29 * a.chains * a.n_samples + 40 * a.chains + 4))
+    return res
+
+
+def serve_arm(a, world, rank, local_rank):
+    import torch
+    from paper_2604_22048_gb300 import build
+    build.build()
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    n_req = a.n_gal
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    res = serve_compare(a, dev, n_req, min(n_req, 50000))
+    clk = clocks.stop()
+    served = res["served_at_1.2x"]
+    return {"metric": SERVE_METRIC, "value": served["galaxies_per_s"], "unit": UNIT, "n_gpus": world,
+            "steps": 1, "warmup": 1, "ms_per_step": 1e3 * served["makespan_s"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded draws rendered by bs_render; Poisson arrivals, seed 7)",
+            "config": {"workload": f"serving: {n_req} fit requests, stamps 25-101 px with per-galaxy Moffat "
+                                   f"beta=3 PSFs (batching recipe), Poisson arrivals at 1.2x the plain per-size "
+                                   f"batched path's saturated throughput, {a.chains} chains x ({a.n_warmup} warmup"
+                                   f" + {a.n_samples} draws), HMC L_i~U{{1..{a.leapfrog}}}",
+                       "l2": "inputs stream from host memory; no flush",
+                       "parallelism": "one GPU"},
+            "latency_ms": {"p50": served["p50_ms"], "p99": served["p99_ms"],
+                           "p50_at_0.8x": res["served_at_0.8x"]["p50_ms"],
+                           "p99_at_0.8x": res["served_at_0.8x"]["p99_ms"]},
+            "serving": res, "clocks": clk,
+            "gpu_launches": int(served["launches"]),
+            "e2e": {"value": served["galaxies_per_s"], "unit": UNIT, "h2d_bytes_per_step": res["h2d_bytes"],
+                    "d2h_bytes_per_step": res["d2h_bytes"],
+                    "note": "the served path is end to end by construction: stamps from host memory, results "
+                            "to pinned host memory, per request"}}
+
+
 def main():
     a = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -430,7 +695,7 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
-    out = our_arm(a, world, rank, local_rank)
+    out = serve_arm(a, world, rank, local_rank) if a.workload == "serve" else our_arm(a, world, rank, local_rank)
     if rank == 0:
         print(json.dumps(out))
     if world > 1:

@@ -209,6 +209,129 @@ bs_status bs_fit_plan_create(const bs_fit_args *args, const bs_fit_out *out,
 bs_status bs_fit_plan_launch(bs_fit_plan plan, void *stream);
 bs_status bs_fit_plan_destroy(bs_fit_plan plan);
 
+/* Galaxies of side max_side (n_chains chains each) that the current device
+ * holds at once in one fit launch (SMs x resident CTAs): the batch size of a
+ * launch that fills the GPU exactly once.  Returns 0 for invalid arguments. */
+int32_t bs_fit_resident_galaxies(int32_t n_chains, int32_t max_side);
+
+/* ------------------------------------------------------------------------ */
+/* Serving: fit requests admitted while others run (continuous batching)     */
+/* ------------------------------------------------------------------------ */
+
+/* The paper fits a fixed catalogue; a survey pipeline instead receives
+ * stamps as they are cut.  A server runs the same per-galaxy fit as
+ * bs_fit_galaxies (same kernel, same random streams keyed by gal_id, so a
+ * request's result does not depend on what else is on the GPU) for requests
+ * that arrive one by one:
+ *   - an engine thread admits pending requests first-in first-out, as long as
+ *     the device arena has room for their inputs and outputs and fewer than
+ *     max_inflight requests are on the GPU ("admission by memory");
+ *   - the requests admitted together are staged with one host-to-device copy
+ *     and launched, one CTA per galaxy, one launch per 32-column slot class,
+ *     each on an idle stream, so the GPU's block scheduler starts them as
+ *     soon as running galaxies retire and SMs free up;
+ *   - chain state and step-size/metric adaptation live on the GPU for the
+ *     whole fit; each CTA copies its galaxy's results into pinned host
+ *     memory and raises a completion flag there, which the engine picks up.
+ * Times are nanoseconds of a steady clock whose zero is the server's
+ * creation (bs_serve_now_ns). */
+typedef struct {
+    int32_t max_side;        /* largest stamp side accepted (odd, <= BS_MAX_SIDE) */
+    float pixel_scale;       /* arcsec */
+    bs_prior prior;
+    int32_t n_chains;        /* 1..8 */
+    int32_t n_warmup, n_samples, n_leapfrog;
+    float target_accept, jitter;
+    int32_t adapt_mass, random_steps;
+    uint64_t seed;
+    int32_t max_inflight;    /* requests on the GPU at once (0: twice the
+                                galaxies of side 63 the GPU holds at once) */
+    int32_t batch_us;        /* admission interval while the GPU is full
+                                (0: 500 us); requests are admitted at once
+                                while fewer than the GPU holds are running */
+    int32_t n_streams;       /* launch streams (0: 96; 4..128) */
+} bs_serve_cfg;
+
+typedef struct {
+    uint64_t tag;            /* caller's identifier, echoed in the completion */
+    uint64_t gal_id;         /* keys the random stream, as bs_fit_args.gal_id */
+    int32_t side;            /* odd, 3..max_side */
+    bs_psf psf;
+    float noise_sigma;       /* pixel noise sd */
+    const float *stamp;      /* host float [side][side], row-major */
+    const float *init;       /* host float [n_chains][6]: chain starts */
+    int64_t t_arrival_ns;    /* arrival time on the server clock, or < 0 for
+                                the time of submission */
+} bs_serve_request;
+
+typedef struct {
+    uint64_t tag;
+    int32_t status;          /* as bs_fit_out.status */
+    int32_t side;
+    int64_t t_arrival_ns, t_submit_ns, t_admit_ns, t_done_ns;
+    /* Results in the server's pinned host memory, valid until the next
+     * bs_serve_poll or bs_serve_destroy call on this server.
+     * samples: parameter k, chain c, draw s at
+     *          samples[k * plane_stride + c * n_samples + s]. */
+    const float *samples;
+    int64_t plane_stride;
+    const float *logp;           /* [n_chains][n_samples] */
+    const uint8_t *accepted;     /* [n_chains][n_samples] */
+    const float *accept_rate;    /* [n_chains] */
+    const float *step_size;      /* [n_chains] */
+    const float *inv_mass;       /* [n_chains][6] */
+    const int32_t *n_divergent;  /* [n_chains] */
+    const int32_t *n_grad;       /* [n_chains] */
+} bs_serve_completion;
+
+typedef struct {
+    int64_t submitted, admitted, completed;
+    int64_t launches;            /* fit launches issued */
+    int64_t ticks;               /* admission rounds that launched work */
+    int64_t waits_memory;        /* admission rounds cut short by the arena */
+    int64_t waits_inflight;      /* ... by max_inflight */
+    int64_t waits_streams;       /* ... by no idle stream */
+    int64_t arena_bytes, arena_used, arena_high_water;
+    int32_t pending, inflight;
+} bs_serve_stats;
+
+typedef struct bs_server_s *bs_server;
+
+/* Arena bytes one request of this side takes while it is admitted (inputs
+ * and outputs, before the per-launch alignment). */
+size_t bs_serve_request_bytes(const bs_serve_cfg *cfg, int32_t side);
+
+/* Create a server on the current device.
+ *   arena: device memory owned by the caller (arena_bytes, >= 1 MiB), which
+ *          the server uses for admitted requests until bs_serve_destroy.
+ * The server allocates, here only, a pinned host mirror of arena_bytes and
+ * its streams, and starts its engine thread.
+ * Errors: BS_ERR_INVALID_ARG (bad configuration), BS_ERR_CUDA. */
+bs_status bs_serve_create(const bs_serve_cfg *cfg, void *arena, size_t arena_bytes,
+                          bs_server *srv);
+
+/* Queue n requests (thread-safe).  The stamp and init arrays are read when a
+ * request is admitted: they must stay valid and unchanged until its
+ * completion is returned.  All n are checked first; nothing is queued if one
+ * is invalid (BS_ERR_INVALID_ARG).  A request larger than the whole arena is
+ * invalid. */
+bs_status bs_serve_submit(bs_server srv, const bs_serve_request *req, int32_t n);
+
+/* Return up to max completions (first the oldest), waiting up to timeout_us
+ * for the first one; *n_out receives the count (0 on timeout).  Completions
+ * returned by the previous call are released first, so their result
+ * pointers become invalid.  BS_ERR_CUDA if the engine met a CUDA error. */
+bs_status bs_serve_poll(bs_server srv, bs_serve_completion *out, int32_t max,
+                        int32_t timeout_us, int32_t *n_out);
+
+bs_status bs_serve_get_stats(bs_server srv, bs_serve_stats *stats);
+int64_t bs_serve_now_ns(bs_server srv);
+
+/* Stop the engine: requests not yet admitted are dropped, admitted ones run
+ * to completion (the call waits for the GPU), then the mirror and the
+ * streams are freed. */
+bs_status bs_serve_destroy(bs_server srv);
+
 /* Log posterior and gradient of single parameter points, for checking and
  * for differentiation (same arithmetic as the fit's inner loop).
  *   gal_index device int32 [n_points]: which galaxy of `args` each point uses

@@ -6,19 +6,21 @@ and Accurate Shear Inference").
       image sampling phase (Sec. 3.3), one persistent CUDA launch;
   ShearPlan(e1, e2).loglike(g1, g2, alpha) -> value, gradient
       MC shear likelihood of Eq. likelihood-shear (Sec. 3.2);
-  ShearPlan.estimate(...) -> posterior mean of g (and alpha) (Sec. 3.4).
+  ShearPlan.estimate(...) -> posterior mean of g (and alpha) (Sec. 3.4);
+  Server(cfg).submit(requests) / .poll() -> the same fits for stamps that
+      arrive one by one (continuous batching, admission by memory).
 
 The C ABI lives in include/bpshear.h; this package only marshals torch
 tensors into it (see ``api``), and ``synth`` draws seeded synthetic inputs.
 """
 from . import _ffi
-from .api import (DEFAULT_PRIOR, PIXEL_SCALE, FitConfig, FitPlan, RaggedFitPlan, RenderLogPost, ShearLogLike,
-                  ShearPlan, chain_ess, fit_galaxies, logpost_points, pack_stamps, psf_table, render,
-                  shear_loglike)
+from .api import (DEFAULT_PRIOR, PIXEL_SCALE, FitConfig, FitPlan, RaggedFitPlan, RenderLogPost, Server,
+                  ShearLogLike, ShearPlan, chain_ess, fit_galaxies, logpost_points, pack_stamps, psf_table,
+                  render, resident_galaxies, shear_loglike)
 
-__all__ = ["DEFAULT_PRIOR", "PIXEL_SCALE", "FitConfig", "FitPlan", "RaggedFitPlan", "RenderLogPost",
+__all__ = ["DEFAULT_PRIOR", "PIXEL_SCALE", "FitConfig", "FitPlan", "RaggedFitPlan", "RenderLogPost", "Server",
            "ShearLogLike", "ShearPlan", "chain_ess", "fit_galaxies", "logpost_points", "pack_stamps", "psf_table",
-           "render", "shear_loglike", "lib"]
+           "render", "resident_galaxies", "shear_loglike", "lib"]
 
 
 def lib():

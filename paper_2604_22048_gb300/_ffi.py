@@ -24,7 +24,9 @@ STATUS_NAMES = {0: "BS_OK", -1: "BS_ERR_INVALID_ARG", -2: "BS_ERR_CUDA", -3: "BS
 EXPORTED = ["bs_prior_default", "bs_last_error", "bs_version", "bs_render", "bs_fit_workspace_bytes",
             "bs_fit_galaxies", "bs_logpost_points", "bs_chain_ess", "bs_shear_workspace_bytes",
             "bs_shear_loglike", "bs_shear_estimate", "bs_shear_loglike_noalloc",
-            "bs_fit_plan_workspace_bytes", "bs_fit_plan_create", "bs_fit_plan_launch", "bs_fit_plan_destroy"]
+            "bs_fit_plan_workspace_bytes", "bs_fit_plan_create", "bs_fit_plan_launch", "bs_fit_plan_destroy",
+            "bs_fit_resident_galaxies", "bs_serve_request_bytes", "bs_serve_create", "bs_serve_submit",
+            "bs_serve_poll", "bs_serve_get_stats", "bs_serve_now_ns", "bs_serve_destroy"]
 
 
 class BsError(RuntimeError):
@@ -73,6 +75,54 @@ class EstimateCfg(C.Structure):
                 ("allreduce_user", C.c_void_p)]
 
 
+class ServeCfg(C.Structure):
+    _fields_ = [("max_side", C.c_int32), ("pixel_scale", C.c_float), ("prior", Prior), ("n_chains", C.c_int32),
+                ("n_warmup", C.c_int32), ("n_samples", C.c_int32), ("n_leapfrog", C.c_int32),
+                ("target_accept", C.c_float), ("jitter", C.c_float), ("adapt_mass", C.c_int32),
+                ("random_steps", C.c_int32), ("seed", C.c_uint64), ("max_inflight", C.c_int32),
+                ("batch_us", C.c_int32), ("n_streams", C.c_int32)]
+
+
+class ServeRequest(C.Structure):
+    _fields_ = [("tag", C.c_uint64), ("gal_id", C.c_uint64), ("side", C.c_int32), ("psf", Psf),
+                ("noise_sigma", C.c_float), ("stamp", C.c_void_p), ("init", C.c_void_p),
+                ("t_arrival_ns", C.c_int64)]
+
+
+class ServeCompletion(C.Structure):
+    _fields_ = [("tag", C.c_uint64), ("status", C.c_int32), ("side", C.c_int32), ("t_arrival_ns", C.c_int64),
+                ("t_submit_ns", C.c_int64), ("t_admit_ns", C.c_int64), ("t_done_ns", C.c_int64),
+                ("samples", C.c_void_p), ("plane_stride", C.c_int64), ("logp", C.c_void_p),
+                ("accepted", C.c_void_p), ("accept_rate", C.c_void_p), ("step_size", C.c_void_p),
+                ("inv_mass", C.c_void_p), ("n_divergent", C.c_void_p), ("n_grad", C.c_void_p)]
+
+
+class ServeStats(C.Structure):
+    _fields_ = [(n, C.c_int64) for n in ("submitted", "admitted", "completed", "launches", "ticks", "waits_memory",
+                                         "waits_inflight", "waits_streams", "arena_bytes", "arena_used",
+                                         "arena_high_water")] + [("pending", C.c_int32), ("inflight", C.c_int32)]
+
+
+def struct_dtype(S):
+    """numpy dtype with the byte layout of ctypes structure S (flat fields;
+    a nested bs_psf is spelled out as psf_kind, psf_fwhm, psf_beta)."""
+    import numpy as np
+    names, formats, offsets = [], [], []
+    conv = {C.c_uint64: "<u8", C.c_int64: "<i8", C.c_int32: "<i4", C.c_float: "<f4", C.c_void_p: "<u8"}
+    for name, t in S._fields_:
+        off = getattr(S, name).offset
+        if t is Psf:
+            for sub, st in Psf._fields_:
+                names.append(f"{name}_{sub}")
+                formats.append(conv[st])
+                offsets.append(off + getattr(Psf, sub).offset)
+        else:
+            names.append(name)
+            formats.append(conv[t])
+            offsets.append(off)
+    return np.dtype({"names": names, "formats": formats, "offsets": offsets, "itemsize": C.sizeof(S)})
+
+
 _lib = None
 
 
@@ -107,9 +157,21 @@ def lib():
                                      C.POINTER(C.c_void_p)]
     L.bs_fit_plan_launch.argtypes = [vp, vp]
     L.bs_fit_plan_destroy.argtypes = [vp]
+    L.bs_fit_resident_galaxies.argtypes = [i32, i32]
+    L.bs_fit_resident_galaxies.restype = i32
+    L.bs_serve_request_bytes.argtypes = [C.POINTER(ServeCfg), i32]
+    L.bs_serve_request_bytes.restype = sz
+    L.bs_serve_create.argtypes = [C.POINTER(ServeCfg), vp, sz, C.POINTER(C.c_void_p)]
+    L.bs_serve_submit.argtypes = [vp, vp, i32]
+    L.bs_serve_poll.argtypes = [vp, vp, i32, i32, C.POINTER(C.c_int32)]
+    L.bs_serve_get_stats.argtypes = [vp, C.POINTER(ServeStats)]
+    L.bs_serve_now_ns.argtypes = [vp]
+    L.bs_serve_now_ns.restype = i64
+    L.bs_serve_destroy.argtypes = [vp]
     for nm in ("bs_render", "bs_fit_galaxies", "bs_logpost_points", "bs_chain_ess", "bs_shear_loglike",
                "bs_shear_estimate", "bs_shear_loglike_noalloc", "bs_fit_plan_create", "bs_fit_plan_launch",
-               "bs_fit_plan_destroy"):
+               "bs_fit_plan_destroy", "bs_serve_create", "bs_serve_submit", "bs_serve_poll", "bs_serve_get_stats",
+               "bs_serve_destroy"):
         getattr(L, nm).restype = C.c_int
     _lib = L
     return L

@@ -200,6 +200,118 @@ class RaggedFitPlan(FitPlan):
             self.handle = None
 
 
+REQUEST_DTYPE = F.struct_dtype(F.ServeRequest)
+COMPLETION_DTYPE = F.struct_dtype(F.ServeCompletion)
+
+
+class Server:
+    """Fit requests admitted while others run (bs_serve_*): FIFO admission by
+    arena memory and an in-flight cap, one CTA per galaxy, results delivered
+    to pinned host memory.  The arena is a torch uint8 tensor owned here."""
+
+    def __init__(self, cfg: FitConfig, *, max_side=101, arena_bytes=256 << 20, max_inflight=0, batch_us=0,
+                 n_streams=0, device="cuda"):
+        self.cfg = cfg
+        self.arena = torch.empty(int(arena_bytes), dtype=torch.uint8, device=device)
+        c = F.ServeCfg()
+        c.max_side = max_side
+        c.pixel_scale = cfg.pixel_scale
+        c.prior = F.Prior(*cfg.prior)
+        c.n_chains, c.n_warmup, c.n_samples, c.n_leapfrog = cfg.n_chains, cfg.n_warmup, cfg.n_samples, cfg.n_leapfrog
+        c.target_accept, c.jitter = cfg.target_accept, cfg.jitter
+        c.adapt_mass, c.random_steps, c.seed = int(cfg.adapt_mass), int(cfg.random_steps), cfg.seed
+        c.max_inflight, c.batch_us, c.n_streams = max_inflight, batch_us, n_streams
+        self.scfg = c
+        torch.cuda.synchronize(self.arena.device)
+        h = C.c_void_p()
+        with torch.cuda.device(self.arena.device):
+            F.check(F.lib().bs_serve_create(C.byref(c), _p(self.arena), int(arena_bytes), C.byref(h)))
+        self.handle = h
+        self._cbuf = (F.ServeCompletion * 8192)()
+        self._keep = []
+
+    @staticmethod
+    def requests(stamps, offsets, sides, psf_kind, fwhm, beta, noise_sigma, init, gal_id, tags=None,
+                 t_arrival_ns=None, init_index=None):
+        """Structured array of bs_serve_request pointing into host arrays:
+        stamps float32 (flat, stamp i at offsets[i]), init float32 [m, C, 6]
+        (request i starts from init[init_index[i]], default init[i]).
+        The caller keeps `stamps` and `init` alive until the completions."""
+        assert stamps.dtype == np.float32 and stamps.flags.c_contiguous
+        assert init.dtype == np.float32 and init.flags.c_contiguous
+        n = len(sides)
+        r = np.zeros(n, dtype=REQUEST_DTYPE)
+        r["tag"] = np.arange(n) if tags is None else tags
+        r["gal_id"] = gal_id
+        r["side"] = sides
+        r["psf_kind"] = {"gaussian": F.BS_PSF_GAUSSIAN, "moffat": F.BS_PSF_MOFFAT}.get(psf_kind, psf_kind)
+        r["psf_fwhm"] = fwhm
+        r["psf_beta"] = beta
+        r["noise_sigma"] = noise_sigma
+        r["stamp"] = stamps.ctypes.data + 4 * np.asarray(offsets, dtype=np.int64)
+        per = init[0].nbytes if len(init) else 0
+        ii = np.arange(n, dtype=np.int64) if init_index is None else np.asarray(init_index, dtype=np.int64)
+        r["init"] = init.ctypes.data + per * ii
+        r["t_arrival_ns"] = -1 if t_arrival_ns is None else t_arrival_ns
+        return r
+
+    def submit(self, reqs):
+        reqs = np.ascontiguousarray(reqs, dtype=REQUEST_DTYPE)
+        F.check(F.lib().bs_serve_submit(self.handle, reqs.ctypes.data, len(reqs)))
+
+    def poll(self, max_n=8192, timeout_us=0):
+        """Completions as a structured array (COMPLETION_DTYPE); their result
+        pointers stay valid until the next poll."""
+        n = C.c_int32(0)
+        F.check(F.lib().bs_serve_poll(self.handle, self._cbuf, min(max_n, len(self._cbuf)), int(timeout_us),
+                                      C.byref(n)))
+        raw = np.frombuffer(self._cbuf, dtype=COMPLETION_DTYPE, count=n.value)
+        return raw.copy()
+
+    def result(self, comp):
+        """Copy one completion's results (valid until the next poll) into numpy."""
+        Cn, S = self.cfg.n_chains, self.cfg.n_samples
+        cs = Cn * S
+
+        def arr(ptr, ctype, count, dtype):
+            return np.frombuffer((ctype * count).from_address(int(ptr)), dtype=dtype).copy()
+        stride = int(comp["plane_stride"])
+        samples = np.stack([arr(int(comp["samples"]) + 4 * k * stride, C.c_float, cs, np.float32)
+                            for k in range(6)]).reshape(6, Cn, S)
+        return dict(samples=samples, logp=arr(comp["logp"], C.c_float, cs, np.float32).reshape(Cn, S),
+                    accepted=arr(comp["accepted"], C.c_uint8, cs, np.uint8).reshape(Cn, S),
+                    accept_rate=arr(comp["accept_rate"], C.c_float, Cn, np.float32),
+                    step_size=arr(comp["step_size"], C.c_float, Cn, np.float32),
+                    inv_mass=arr(comp["inv_mass"], C.c_float, 6 * Cn, np.float32).reshape(Cn, 6),
+                    n_div=arr(comp["n_divergent"], C.c_int32, Cn, np.int32),
+                    n_grad=arr(comp["n_grad"], C.c_int32, Cn, np.int32), status=int(comp["status"]))
+
+    def stats(self):
+        s = F.ServeStats()
+        F.check(F.lib().bs_serve_get_stats(self.handle, C.byref(s)))
+        return {n: getattr(s, n) for n, _ in F.ServeStats._fields_}
+
+    def now_ns(self):
+        return F.lib().bs_serve_now_ns(self.handle)
+
+    def close(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            self.handle = None
+            F.check(F.lib().bs_serve_destroy(h))
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def resident_galaxies(n_chains, max_side):
+    """Galaxies of side max_side one fit launch holds at once on the current GPU."""
+    return int(F.lib().bs_fit_resident_galaxies(n_chains, max_side))
+
+
 def fit_galaxies(data, offsets, side, psf, noise_sigma, init, cfg: FitConfig | None = None, **kw):
     """fit_galaxies(stamps, psf, noise_sigma, prior, n_samples) -> interim samples
     (Sec. 3.3 image sampling phase).  Returns a dict of CUDA tensors; samples

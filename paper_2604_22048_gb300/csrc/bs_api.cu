@@ -242,27 +242,7 @@ bs_status bs_fit_galaxies(const bs_fit_args *a, const bs_fit_out *o, void *works
         return fail(BS_ERR_OUT_OF_MEMORY, "bs_fit_galaxies: workspace of %zu bytes needed",
                     bs_fit_workspace_bytes(a));
     if (a->n_gal == 0) return BS_OK;
-    p.n_chains = a->n_chains;
-    p.n_warmup = a->n_warmup;
-    p.n_samples = a->n_samples;
-    p.n_leapfrog = a->n_leapfrog;
-    p.target_accept = a->target_accept;
-    p.jitter = a->jitter;
-    p.random_steps = a->random_steps ? 1 : 0;
-    p.seed = a->seed;
-    p.n_windows = warmup_windows(a->n_warmup, a->adapt_mass != 0, p.win_start, p.win_end, bs::kMaxWindows);
-    p.samples = o->samples;
-    p.logp = o->logp;
-    p.accepted = o->accepted;
-    p.accept_rate = o->accept_rate;
-    p.step_size = o->step_size;
-    p.inv_mass = o->inv_mass;
-    p.n_div = o->n_divergent;
-    p.status = o->status;
-    p.n_grad = o->n_grad;
     p.queue = static_cast<unsigned int *>(workspace);
-    p.work = nullptr;
-    p.n_work = a->n_gal;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e;
     if (o->status) {
@@ -279,6 +259,15 @@ bs_status bs_fit_galaxies(const bs_fit_args *a, const bs_fit_out *o, void *works
     if (grid > a->n_gal) grid = a->n_gal;
     e = bs::launch_fit(p, (int)grid, s);
     return e == cudaSuccess ? BS_OK : cuda_fail(e, "bs_fit_galaxies: launch");
+}
+
+int32_t bs_fit_resident_galaxies(int32_t n_chains, int32_t max_side)
+{
+    if (n_chains < 1 || n_chains > bs::kMaxChains || !odd_side_ok(max_side)) return 0;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    return sms * bs::fit_blocks_per_sm(n_chains, max_side);
 }
 
 bs_status bs_logpost_points(const bs_fit_args *a, int32_t n_points, const int32_t *gal_index,

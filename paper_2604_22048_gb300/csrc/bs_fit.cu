@@ -700,6 +700,42 @@ __device__ void run_chain(const FitParams &P, const GalCtx &gc, const SmemView &
     if (P.inv_mass && own) P.inv_mass[ci0 * 6 + pi] = im;
 }
 
+// Serving: copy n elements at src (this CTA's galaxy's outputs) to the
+// pinned mirror, src + pub_shift.
+template <typename T>
+__device__ __forceinline__ void publish_range(const T *src, size_t n, long long shift)
+{
+    if (!src) return;
+    T *dst = reinterpret_cast<T *>(reinterpret_cast<char *>(const_cast<T *>(src)) + shift);
+    for (size_t i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+}
+
+// All threads of the CTA, after the galaxy's chains have finished: its
+// outputs go to the host mirror, then done[gal] is raised.  Each thread
+// fences its own stores at system scope before the barrier, so the host that
+// sees the flag sees every result.
+__device__ void publish_galaxy(const FitParams &P, int gal)
+{
+    const size_t C = P.n_chains, cs = C * P.n_samples;
+    const size_t plane = (size_t)P.n_gal * cs;
+    const long long sh = P.pub_shift;
+    for (int k = 0; k < 6; ++k) publish_range(P.samples + k * plane + gal * cs, cs, sh);
+    if (P.logp) publish_range(P.logp + gal * cs, cs, sh);
+    if (P.accepted) publish_range(P.accepted + gal * cs, cs, sh);
+    if (P.accept_rate) publish_range(P.accept_rate + gal * C, C, sh);
+    if (P.step_size) publish_range(P.step_size + gal * C, C, sh);
+    if (P.inv_mass) publish_range(P.inv_mass + gal * C * 6, C * 6, sh);
+    if (P.n_div) publish_range(P.n_div + gal * C, C, sh);
+    if (P.n_grad) publish_range(P.n_grad + gal * C, C, sh);
+    if (P.status) publish_range(P.status + gal, 1, sh);
+    __threadfence_system();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence_system();
+        *reinterpret_cast<volatile uint32_t *>(P.done + gal) = 1u;
+    }
+}
+
 // MINB bounds the registers so that MINB CTAs of 256 threads fit an SM
 // (2: <= 128 registers, no spills; 3: <= 85, a few spills outside the
 // half-plane loop), i.e. 4 or 6 CTAs of 4 chains.
@@ -710,24 +746,34 @@ __global__ void __launch_bounds__(256, MINB) fit_kernel(const FitParams P)
     __shared__ int s_gal;
     const SmemView sm = smem_view(smem_raw, P.h_max, P.npad, P.max_side);
     const int warp = threadIdx.x >> 5;
+    bool first = true;
     for (;;) {
         if (threadIdx.x == 0) {
-            // positions in the work list (or galaxy indices when there is none)
-            const int q = (int)atomicAdd(P.queue, 1u);
-            s_gal = q < P.n_work ? (P.work ? P.work[q] : q) : -1;
+            if (P.done) {
+                // serving: galaxy blockIdx.x only, so that nothing of the
+                // launch's memory is touched after its completion flag
+                s_gal = first ? (int)blockIdx.x : -1;
+            } else {
+                // positions in the work list (or galaxy indices when there is none)
+                const int q = (int)atomicAdd(P.queue, 1u);
+                s_gal = q < P.n_work ? (P.work ? P.work[q] : q) : -1;
+            }
         }
+        first = false;
         __syncthreads();
         const int gal = s_gal;
         if (gal < 0 || gal >= P.n_gal) break;
         if (!side_ok(P, P.side[gal])) {     // uniform across the CTA
             if (threadIdx.x == 0 && P.status) P.status[gal] = 2;
             __syncthreads();
+            if (P.done) publish_galaxy(P, gal);
             continue;
         }
         GalCtx gc;
         setup_galaxy(P, gal, sm, gc);
         if (warp < P.n_chains) run_chain<NC>(P, gc, sm, gal, warp);
         __syncthreads();
+        if (P.done) publish_galaxy(P, gal);
     }
 }
 

@@ -54,6 +54,11 @@ struct FitParams {
     unsigned int *queue;
     int max_side;
     int h_max, npad;   // shared-memory geometry for max_side
+    // serving: when `done` is set (host-mapped), each CTA copies its galaxy's
+    // outputs to (address + pub_shift) -- the pinned mirror of the output
+    // arrays -- then sets done[gal] = 1 with a system-scope fence before it
+    uint32_t *done;
+    long long pub_shift;
 };
 
 // Shared memory bytes per CTA for a given max stamp side.
@@ -61,6 +66,9 @@ size_t fit_smem_bytes(int max_side);
 // Launch helpers implemented in the .cu files.
 cudaError_t launch_fit(const FitParams &p, int grid, cudaStream_t stream);
 int fit_blocks_per_sm(int n_chains, int max_side);
+// Validate a fit request and fill every launch parameter except the
+// scheduling fields (work list, counter) and the serving fields.
+bs_status fit_params_from_args(const bs_fit_args *a, const bs_fit_out *o, FitParams &p, const char *who);
 cudaError_t launch_logpost_points(const FitParams &p, int n_points, const int32_t *gal_index,
                                   const float *theta, double *logp, float *grad,
                                   cudaStream_t stream);

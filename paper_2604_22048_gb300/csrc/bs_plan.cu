@@ -16,10 +16,6 @@
 
 #include "bs_internal.h"
 
-namespace bs {
-bs_status fit_params_from_args(const bs_fit_args *a, const bs_fit_out *o, FitParams &p, const char *who);
-}
-
 struct bs_fit_plan_s {
     struct Launch {
         bs::FitParams p;

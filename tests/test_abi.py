@@ -55,3 +55,30 @@ def test_host_validation(L):
     assert L.bs_shear_loglike(C.byref(d), 0.0, 0.0, 0.2, None, 1, None, 0, None) == -1   # NULL e1/e2
     assert L.bs_chain_ess(None, 1, 4, 100, None, None, None) == -1
     assert L.bs_logpost_points(None, 1, None, None, None, None, None) == -1
+
+
+def test_struct_layouts_match_header(tmp_path):
+    """sizeof/offsetof of every struct, as gcc sees include/bpshear.h, equal the
+    ctypes declarations the binding marshals with."""
+    import subprocess
+    from paper_2604_22048_gb300 import _ffi
+    structs = {"bs_fit_args": _ffi.FitArgs, "bs_fit_out": _ffi.FitOut, "bs_shear_data": _ffi.ShearData,
+               "bs_estimate_cfg": _ffi.EstimateCfg, "bs_serve_cfg": _ffi.ServeCfg,
+               "bs_serve_request": _ffi.ServeRequest, "bs_serve_completion": _ffi.ServeCompletion,
+               "bs_serve_stats": _ffi.ServeStats, "bs_psf": _ffi.Psf, "bs_prior": _ffi.Prior}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "bpshear.h"', "int main(void) {"]
+    for cn, py in structs.items():
+        lines.append(f'printf("{cn} size %zu\\n", sizeof({cn}));')
+        for f, _ in py._fields_:
+            lines.append(f'printf("{cn} {f} %zu\\n", offsetof({cn}, {f}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    for line in filter(None, out):
+        cn, f, v = line.split()
+        py = structs[cn]
+        got = C.sizeof(py) if f == "size" else getattr(py, f).offset
+        assert got == int(v), (cn, f, got, v)
