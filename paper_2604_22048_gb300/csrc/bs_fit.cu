@@ -64,6 +64,7 @@ struct SmemView {
     float *tab;    // [h_max][3 npad] data spectrum and transfer, paired layout
     float2 *G;     // [max_side], setup scratch (one frequency row)
     float2 *tw;    // [max_side]
+    float2 *kxr;   // [h_max]: (kx, kx^2) of row u
 };
 
 __device__ __forceinline__ SmemView smem_view(unsigned char *base, int h_max, int npad, int max_side)
@@ -72,6 +73,7 @@ __device__ __forceinline__ SmemView smem_view(unsigned char *base, int h_max, in
     v.tab = reinterpret_cast<float *>(base);
     v.G = reinterpret_cast<float2 *>(v.tab + (size_t)h_max * row_floats(npad));
     v.tw = v.G + (size_t)max_side;
+    v.kxr = v.tw + (size_t)max_side;
     return v;
 }
 
@@ -171,6 +173,10 @@ __device__ void setup_galaxy(const FitParams &P, int gal, const SmemView &sm, Ga
         sincospif(2.0f * (float)m / (float)N, &s, &co);
         sm.tw[m] = make_float2(co, s);   // exp(+2 pi i m / N)
     }
+    for (int u = tid; u < H; u += nth) {
+        const float kx = (float)u * gc.dk;
+        sm.kxr[u] = make_float2(kx, kx * kx);
+    }
     __syncthreads();
     const bs_psf ps = P.psf[P.n_psf == 1 ? 0 : gal];
     const float sqrt2 = 1.41421356237309515f;
@@ -234,6 +240,16 @@ __device__ __forceinline__ bool in_support(const FitParams &P, const float th[6]
     return th[0] > P.lf_lo && th[0] < P.lf_hi && th[1] > P.ls_lo && th[1] < P.ls_hi && E < 1.0f;
 }
 
+// 1/sqrt(s) for s >= 1 (the profile argument 1 + r0^2 q(k)): the hardware
+// approximation with denormal flushing, which cannot occur here, so no
+// range fix-ups are issued around it.
+__device__ __forceinline__ float rsqrt_ge1(float s)
+{
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(s));
+    return r;
+}
+
 // Packed FP32x2 helpers (two column slots of a lane in one instruction; each
 // half is rounded exactly like the scalar operation).
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
@@ -274,12 +290,11 @@ struct SlotConst {
 // Model-data terms of one row u for all column slots of this lane.
 template <int NCT, bool LL>
 __device__ __forceinline__ void row_terms(Sums<NCT> &S, const SlotConst<NCT> &K,
-                                          const float *__restrict__ row, float kx, float akx2,
+                                          const float *__restrict__ row, float kx, float kx2, float akx2,
                                           float Xr, float Xi, float F2)
 {
     constexpr int NPAIR = NCT / 2;
     const int lane = threadIdx.x & 31;
-    const float kx2 = kx * kx;
     const float2 kxv = f2(kx), kx2v = f2(kx2), akv = f2(akx2), Xrv = f2(Xr), Xiv = f2(Xi), nXiv = f2(-Xi);
     const float2 nF2v = f2(-F2);
 #pragma unroll
@@ -289,7 +304,7 @@ __device__ __forceinline__ void row_terms(Sums<NCT> &S, const SlotConst<NCT> &K,
         const float2 Dy = *reinterpret_cast<const float2 *>(b + 64);
         const float2 T = *reinterpret_cast<const float2 *>(b + 128);
         const float2 s = fma2(K.gky[p], kxv, add2(akv, K.cst[p]));     // 1 + r0^2 q(k)
-        const float2 rs = make_float2(rsqrtf(s.x), rsqrtf(s.y));
+        const float2 rs = make_float2(rsqrt_ge1(s.x), rsqrt_ge1(s.y));
         const float2 rs2 = mul2(rs, rs);
         const float2 A = mul2(mul2(T, rs2), rs);                        // |M| / F
         const float2 Pr = fma2(nXiv, K.Yi[p], mul2(Xrv, K.Yr[p]));      // F exp(-i k.delta)
@@ -316,7 +331,7 @@ __device__ __forceinline__ void row_terms(Sums<NCT> &S, const SlotConst<NCT> &K,
         const float2 D = *reinterpret_cast<const float2 *>(b + 2 * lane);
         const float T = b[64 + lane];
         const float s = fmaf(K.sgky, kx, akx2 + K.scst);
-        const float rs = rsqrtf(s);
+        const float rs = rsqrt_ge1(s);
         const float rs2 = rs * rs;
         const float A = T * rs2 * rs;
         const float Pr = Xr * K.sYr - Xi * K.sYi;
@@ -344,8 +359,8 @@ __device__ __forceinline__ void row_terms(Sums<NCT> &S, const SlotConst<NCT> &K,
 // exp(-2 pi i dx / N) per row).
 template <int NCT, bool LL>
 __device__ __forceinline__ void half_plane(Sums<NCT> &S, const SlotConst<NCT> &K,
-                                           const float *__restrict__ tab, int H, float dk, float al,
-                                           float exr, float exi, float F2)
+                                           const float *__restrict__ tab, const float2 *__restrict__ kxr,
+                                           int H, float al, float exr, float exi, float F2)
 {
     constexpr int ROWF = 96 * NCT;
     const float e2r = exr * exr - exi * exi, e2i = 2.0f * exr * exi;   // two-row step
@@ -353,26 +368,26 @@ __device__ __forceinline__ void half_plane(Sums<NCT> &S, const SlotConst<NCT> &K
     const float *row = tab;
     int u = 0;
     for (; u + 1 < H; u += 2) {
-        const float kx0 = (float)u * dk, kx1 = (float)(u + 1) * dk;
+        const float4 k01 = *reinterpret_cast<const float4 *>(kxr + u);   // (kx, kx^2) of rows u, u+1
         const float X1r = Xr * exr - Xi * exi, X1i = Xr * exi + Xi * exr;
-        row_terms<NCT, LL>(S, K, row, kx0, al * kx0 * kx0, Xr, Xi, F2);
-        row_terms<NCT, LL>(S, K, row + ROWF, kx1, al * kx1 * kx1, X1r, X1i, F2);
+        row_terms<NCT, LL>(S, K, row, k01.x, k01.y, al * k01.y, Xr, Xi, F2);
+        row_terms<NCT, LL>(S, K, row + ROWF, k01.z, k01.w, al * k01.w, X1r, X1i, F2);
         const float nXr = Xr * e2r - Xi * e2i;
         Xi = Xr * e2i + Xi * e2r;
         Xr = nXr;
         row += 2 * ROWF;
     }
     if (u < H) {
-        const float kx0 = (float)u * dk;
-        row_terms<NCT, LL>(S, K, row, kx0, al * kx0 * kx0, Xr, Xi, F2);
+        const float2 k0 = kxr[u];
+        row_terms<NCT, LL>(S, K, row, k0.x, k0.y, al * k0.y, Xr, Xi, F2);
     }
 }
 
 // Log posterior (if want_ll) and gradient at th, warp-cooperative.
 template <int NC>
 __device__ __forceinline__ double eval_logpost(const FitParams &P, const GalCtx &gc,
-                                               const float *__restrict__ tab, const float vcol[NC],
-                                               const float th[6], float g[6], bool want_ll)
+                                               const float *__restrict__ tab, const float2 *__restrict__ kxr,
+                                               const float vcol[NC], const float th[6], float g[6], bool want_ll)
 {
     const float F = exp10f(th[0]);
     const float r0 = exp10f(th[1]) * (1.0f / kHlrOverR0);
@@ -427,9 +442,9 @@ __device__ __forceinline__ double eval_logpost(const FitParams &P, const GalCtx 
     S.chi_hi = f2(0.f);
     S.chi_lo = f2(0.f);
     if (want_ll)
-        half_plane<NC, true>(S, K, tab, gc.H, dk, al, exr, exi, F2);
+        half_plane<NC, true>(S, K, tab, kxr, gc.H, al, exr, exi, F2);
     else
-        half_plane<NC, false>(S, K, tab, gc.H, dk, al, exr, exi, F2);
+        half_plane<NC, false>(S, K, tab, kxr, gc.H, al, exr, exi, F2);
 
     float Sa = S.Sa.x + S.Sa.y, Swkx2 = S.Swkx2.x + S.Swkx2.y, Sbkx = S.Sbkx.x + S.Sbkx.y;
     float Sw = 0.f, Swky2 = 0.f, Swkxky = 0.f, Sbky = 0.f;
@@ -588,7 +603,7 @@ __device__ void run_chain(const FitParams &P, const GalCtx &gc, const SmemView &
             for (int k = 0; k < 6; ++k) x[k] = __shfl_sync(BS_FULL_MASK, tp, k);
             if (!in_support(P, x)) { ok = false; break; }
             float gg[6];
-            const double v = eval_logpost<NC>(P, gc, sm.tab, vcol, x, gg, l == nst - 1);
+            const double v = eval_logpost<NC>(P, gc, sm.tab, sm.kxr, vcol, x, gg, l == nst - 1);
             ++ngrad;
             if (l == nst - 1) lpp = v;
             gp = pick6(gg, pi);
@@ -791,7 +806,7 @@ __device__ void point_eval(const FitParams &P, const GalCtx &gc, const SmemView 
     for (int i = 0; i < 6; ++i) th[i] = theta[i];
     double v = -INFINITY;
     if (in_support(P, th)) {
-        v = eval_logpost<NC>(P, gc, sm.tab, vcol, th, g, true);
+        v = eval_logpost<NC>(P, gc, sm.tab, sm.kxr, vcol, th, g, true);
     } else {
 #pragma unroll
         for (int i = 0; i < 6; ++i) g[i] = NAN;
@@ -860,7 +875,8 @@ size_t fit_smem_bytes(int max_side)
 {
     const int h = (max_side + 1) / 2;
     const int npad = 32 * ((max_side + 31) / 32);
-    return (size_t)h * row_floats(npad) * sizeof(float) + 2 * (size_t)max_side * sizeof(float2);
+    return (size_t)h * row_floats(npad) * sizeof(float) + 2 * (size_t)max_side * sizeof(float2) +
+           (size_t)(h + 1) * sizeof(float2);
 }
 
 int fit_blocks_per_sm(int n_chains, int max_side)
