@@ -256,15 +256,27 @@ __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+// a - b on both halves in one packed instruction (no packed negation exists
+// to fold into an add).
+__device__ __forceinline__ float2 sub2(float2 a, float2 b)
+{
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "sub.rn.f32x2 rd, ra, rb;\n\t"
+        "mov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
 
 // Compensated accumulation of both halves (Knuth's TwoSum, packed).
 __device__ __forceinline__ void comp_add2(float2 &hi, float2 &lo, float2 x)
 {
     const float2 s = add2(hi, x);
-    const float2 bp = add2(s, neg2(hi));
-    const float2 ap = add2(s, neg2(bp));
-    const float2 e = add2(add2(hi, neg2(ap)), add2(x, neg2(bp)));
+    const float2 bp = sub2(s, hi);
+    const float2 ap = sub2(s, bp);
+    const float2 e = add2(sub2(hi, ap), sub2(x, bp));
     hi = s;
     lo = add2(lo, e);
 }
@@ -283,7 +295,7 @@ struct Sums {
 template <int NCT>
 struct SlotConst {
     static constexpr int NP = NCT / 2 > 0 ? NCT / 2 : 1;
-    float2 Yr[NP], Yi[NP], cst[NP], gky[NP];   // F exp(-i ky p dy), 1 + be ky^2, ga ky
+    float2 Yr[NP], Yi[NP], nYi[NP], cst[NP], gky[NP];   // F exp(-i ky p dy) (and -Im), 1 + be ky^2, ga ky
     float sYr, sYi, scst, sgky;
 };
 
@@ -295,7 +307,7 @@ __device__ __forceinline__ void row_terms(Sums<NCT> &S, const SlotConst<NCT> &K,
 {
     constexpr int NPAIR = NCT / 2;
     const int lane = threadIdx.x & 31;
-    const float2 kxv = f2(kx), kx2v = f2(kx2), akv = f2(akx2), Xrv = f2(Xr), Xiv = f2(Xi), nXiv = f2(-Xi);
+    const float2 kxv = f2(kx), kx2v = f2(kx2), akv = f2(akx2), Xrv = f2(Xr), Xiv = f2(Xi);
     const float2 nF2v = f2(-F2);
 #pragma unroll
     for (int p = 0; p < NPAIR; ++p) {
@@ -307,10 +319,10 @@ __device__ __forceinline__ void row_terms(Sums<NCT> &S, const SlotConst<NCT> &K,
         const float2 rs = make_float2(rsqrt_ge1(s.x), rsqrt_ge1(s.y));
         const float2 rs2 = mul2(rs, rs);
         const float2 A = mul2(mul2(T, rs2), rs);                        // |M| / F
-        const float2 Pr = fma2(nXiv, K.Yi[p], mul2(Xrv, K.Yr[p]));      // F exp(-i k.delta)
+        const float2 Pr = fma2(Xiv, K.nYi[p], mul2(Xrv, K.Yr[p]));      // F exp(-i k.delta)
         const float2 Pi = fma2(Xiv, K.Yr[p], mul2(Xrv, K.Yi[p]));
         const float2 zr = fma2(Dx, Pr, mul2(Dy, Pi));                  // conj(D) * phase
-        const float2 zi = fma2(Dx, Pi, neg2(mul2(Dy, Pr)));
+        const float2 zi = sub2(mul2(Dx, Pi), mul2(Dy, Pr));
         const float2 a = mul2(A, fma2(A, nF2v, zr));                    // Re conj(D - M) M
         const float2 bb = mul2(A, zi);                                  // Im conj(D - M) M
         const float2 w = mul2(a, rs2);                                  // a / s
@@ -321,8 +333,8 @@ __device__ __forceinline__ void row_terms(Sums<NCT> &S, const SlotConst<NCT> &K,
         S.Bc[p] = add2(S.Bc[p], bb);
         S.Sbkx = fma2(bb, kxv, S.Sbkx);
         if (LL) {
-            const float2 Rr = fma2(neg2(A), Pr, Dx);
-            const float2 Ri = fma2(neg2(A), Pi, Dy);
+            const float2 Rr = sub2(Dx, mul2(A, Pr));
+            const float2 Ri = sub2(Dy, mul2(A, Pi));
             comp_add2(S.chi_hi, S.chi_lo, fma2(Rr, Rr, mul2(Ri, Ri)));
         }
     }
@@ -383,6 +395,38 @@ __device__ __forceinline__ void half_plane(Sums<NCT> &S, const SlotConst<NCT> &K
     }
 }
 
+// Sums over the warp of seven per-lane values, returned in every lane with
+// identical bits.  Recursive halving: at each xor distance a lane keeps half
+// of its values and receives the partner's partial sums of them, so after
+// distances 16, 8, 4 lane l holds value (l >> 2) & 7 summed over 8 lanes; two
+// butterfly steps finish it (commutative adds, so the 4 lanes of a group
+// agree) and one shuffle per value broadcasts it from lane 4 j.
+__device__ __forceinline__ void warp_sum7(float (&v)[7])
+{
+    const int lane = threadIdx.x & 31;
+    float r4[4];
+    const bool h16 = lane & 16;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float lo = v[k], hi = k + 4 < 7 ? v[k + 4] : 0.0f;
+        const float keep = h16 ? hi : lo, send = h16 ? lo : hi;
+        r4[k] = keep + __shfl_xor_sync(BS_FULL_MASK, send, 16);
+    }
+    float r2[2];
+    const bool h8 = lane & 8;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const float keep = h8 ? r4[k + 2] : r4[k], send = h8 ? r4[k] : r4[k + 2];
+        r2[k] = keep + __shfl_xor_sync(BS_FULL_MASK, send, 8);
+    }
+    const bool h4 = lane & 4;
+    float r = (h4 ? r2[1] : r2[0]) + __shfl_xor_sync(BS_FULL_MASK, h4 ? r2[0] : r2[1], 4);
+    r += __shfl_xor_sync(BS_FULL_MASK, r, 2);
+    r += __shfl_xor_sync(BS_FULL_MASK, r, 1);
+#pragma unroll
+    for (int j = 0; j < 7; ++j) v[j] = __shfl_sync(BS_FULL_MASK, r, 4 * j);
+}
+
 // Log posterior (if want_ll) and gradient at th, warp-cooperative.
 template <int NC>
 __device__ __forceinline__ double eval_logpost(const FitParams &P, const GalCtx &gc,
@@ -421,6 +465,7 @@ __device__ __forceinline__ double eval_logpost(const FitParams &P, const GalCtx 
     for (int p = 0; p < NPAIR; ++p) {
         K.Yr[p] = make_float2(Yr[2 * p], Yr[2 * p + 1]);
         K.Yi[p] = make_float2(Yi[2 * p], Yi[2 * p + 1]);
+        K.nYi[p] = make_float2(-Yi[2 * p], -Yi[2 * p + 1]);
         K.cst[p] = make_float2(cst[2 * p], cst[2 * p + 1]);
         K.gky[p] = make_float2(gky[2 * p], gky[2 * p + 1]);
         S.Wc[p] = f2(0.f);
@@ -466,13 +511,15 @@ __device__ __forceinline__ double eval_logpost(const FitParams &P, const GalCtx 
         Swkxky = fmaf(ky[j], wkx, Swkxky);
         Sbky = fmaf(ky[j], bc, Sbky);
     }
-    Sa = warp_sum(Sa);
-    Sw = warp_sum(Sw);
-    Swkx2 = warp_sum(Swkx2);
-    Swky2 = warp_sum(Swky2);
-    Swkxky = warp_sum(Swkxky);
-    Sbkx = warp_sum(Sbkx);
-    Sbky = warp_sum(Sbky);
+    float sums[7] = {Sa, Sw, Swkx2, Swky2, Swkxky, Sbkx, Sbky};
+    warp_sum7(sums);
+    Sa = sums[0];
+    Sw = sums[1];
+    Swkx2 = sums[2];
+    Swky2 = sums[3];
+    Swkxky = sums[4];
+    Sbkx = sums[5];
+    Sbky = sums[6];
 
     const float ib = gc.inv_b;
     const float P2 = Pq * Pq;

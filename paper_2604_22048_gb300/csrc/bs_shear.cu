@@ -16,9 +16,9 @@
 // dx/dalpha = Q / alpha^3.
 //
 // Each galaxy's K samples are read by a group of 8 lanes (float4 loads when
-// the rows are 16-byte aligned), x is kept in log2 units for the MUFU exp2,
-// and the group keeps an online log-sum-exp (running max, sum of weights and
-// weighted derivative sums), merged with shuffles.  Per-galaxy totals are
+// the rows are 16-byte aligned, one chunk ahead of the arithmetic), x is kept in log2 units for the MUFU exp2, and the group keeps
+// an online log-sum-exp (running max, sum of weights and weighted derivative
+// sums), merged with shuffles.  Per-galaxy totals are
 // accumulated in FP64 and written as per-block partials; a one-block kernel
 // sums the partials in a fixed order (deterministic) and adds the
 // per-galaxy constants.
@@ -34,36 +34,95 @@ namespace {
 constexpr int kGroup = 8;          // lanes per galaxy
 constexpr int kShearThreads = 256;
 
+// Hardware approximations with denormal flushing.  Their arguments here are
+// normal numbers (U in (0, 4], 1 - |eps'|^2 >= 2^-24, sums of weights >= 1),
+// or, for ex2, non-positive differences whose flushed results are weights
+// below 2^-126 of the largest; so no range fix-ups are needed around them.
+__device__ __forceinline__ float ex2_ftz(float x)
+{
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float lg2_ftz(float x)
+{
+    float r;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float rcp_ftz(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// Per sample: log2 weight x and the factors of its derivatives,
+//   dx/dg_i = -2 rU c_i,  c_i = du_i (Q/(2 alpha^2) - kappa) - n_i/(2 alpha^2),
+// returned as (rU, c1, c2, Q); the -2 is applied once per galaxy.
 template <int FAMILY, bool HAS_B>
 __device__ __forceinline__ void sample_terms(const ShearLaunch &s, float a_nat, float e1, float e2,
-                                             float bv, float &x2, float &d1, float &d2, float &q)
+                                             float bv, float &x2, float &ru, float &c1, float &c2,
+                                             float &q)
 {
     const float ur = fmaf(-s.g1, e1, fmaf(-s.g2, e2, 1.0f));
     const float vi = fmaf(s.g1, e2, -s.g2 * e1);
     const float U = fmaf(ur, ur, vi * vi);
     const float n1 = e1 - s.g1, n2 = e2 - s.g2;
     const float Nn = fmaf(n1, n1, n2 * n2);
-    const float rU = __fdividef(1.0f, U);
+    const float rU = rcp_ftz(U);
     const float Q = Nn * rU;
     const float Ep = fmaf(e1, e1, e2 * e2);
-    float x = fmaf(s.c0, Ep, fmaf(-s.kappa, __log2f(U), -s.a2 * Q));
+    float x = fmaf(s.c0, Ep, fmaf(-s.kappa, lg2_ftz(U), -s.a2 * Q));
     if (FAMILY == BS_EPRIOR_TRUNC_GAUSS) {
-        x = fmaf(-2.0f, __log2f(1.0f - Ep), x);
+        x = fmaf(-2.0f, lg2_ftz(1.0f - Ep), x);
         if (!(Q < s.r2)) x = -INFINITY;
     }
     if (HAS_B) x = fmaf(kLog2e, bv, x);
     const float aqk = fmaf(a_nat, Q, -s.kappa);
     const float du1 = fmaf(ur, e1, -vi * e2);
     const float du2 = fmaf(ur, e2, vi * e1);
-    const float m2 = -2.0f * rU;
-    d1 = m2 * fmaf(du1, aqk, -a_nat * n1);
-    d2 = m2 * fmaf(du2, aqk, -a_nat * n2);
+    c1 = fmaf(du1, aqk, -a_nat * n1);
+    c2 = fmaf(du2, aqk, -a_nat * n2);
+    ru = rU;
     q = Q;
     x2 = x;
 }
 
+// Loads of one chunk (4 consecutive samples of this lane).
+template <bool HAS_B, bool VEC>
+__device__ __forceinline__ void load_chunk(const ShearLaunch &s, long long base, int k0, int K, float (&ex)[4],
+                                           float (&ey)[4], float (&eb)[4], bool (&valid)[4])
+{
+    if (VEC) {
+        if (k0 < K) {
+            const float4 v1 = __ldg(reinterpret_cast<const float4 *>(s.e1 + base + k0));
+            const float4 v2 = __ldg(reinterpret_cast<const float4 *>(s.e2 + base + k0));
+            ex[0] = v1.x; ex[1] = v1.y; ex[2] = v1.z; ex[3] = v1.w;
+            ey[0] = v2.x; ey[1] = v2.y; ey[2] = v2.z; ey[3] = v2.w;
+            if (HAS_B) {
+                const float4 vb = __ldg(reinterpret_cast<const float4 *>(s.b + base + k0));
+                eb[0] = vb.x; eb[1] = vb.y; eb[2] = vb.z; eb[3] = vb.w;
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) valid[r] = k0 < K;
+    } else {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            valid[r] = k0 + r < K;
+            if (valid[r]) {
+                const long long j = base + k0 + r;
+                ex[r] = __ldg(s.e1 + j);
+                ey[r] = __ldg(s.e2 + j);
+                eb[r] = HAS_B ? __ldg(s.b + j) : 0.f;
+            }
+        }
+    }
+}
+
 template <int FAMILY, bool HAS_B, bool VEC>
-__global__ void __launch_bounds__(kShearThreads) shear_kernel(const ShearLaunch s)
+__global__ void __launch_bounds__(kShearThreads, 4) shear_kernel(const ShearLaunch s)
 {
     const int lane = threadIdx.x & 31;
     const int sub = lane & (kGroup - 1);
@@ -77,51 +136,48 @@ __global__ void __launch_bounds__(kShearThreads) shear_kernel(const ShearLaunch 
     for (long long n = group; n < s.n_gal; n += ngroups) {
         const long long base = n * (long long)K;
         float m = -1e30f, sw = 0.f, t1 = 0.f, t2 = 0.f, tq = 0.f;
-        for (int k0 = 4 * sub; k0 < K; k0 += 4 * kGroup) {
-            float ex[4], ey[4], eb[4];
-            bool valid[4];
-            if (VEC) {
-                const float4 v1 = __ldg(reinterpret_cast<const float4 *>(s.e1 + base + k0));
-                const float4 v2 = __ldg(reinterpret_cast<const float4 *>(s.e2 + base + k0));
-                ex[0] = v1.x; ex[1] = v1.y; ex[2] = v1.z; ex[3] = v1.w;
-                ey[0] = v2.x; ey[1] = v2.y; ey[2] = v2.z; ey[3] = v2.w;
-                if (HAS_B) {
-                    const float4 vb = __ldg(reinterpret_cast<const float4 *>(s.b + base + k0));
-                    eb[0] = vb.x; eb[1] = vb.y; eb[2] = vb.z; eb[3] = vb.w;
-                }
+        // software pipelined: the next chunk's loads are in flight while the
+        // current chunk is evaluated
+        float ex[4] = {0.f, 0.f, 0.f, 0.f}, ey[4] = {0.f, 0.f, 0.f, 0.f}, eb[4] = {0.f, 0.f, 0.f, 0.f};
+        bool valid[4];
+        int k0 = 4 * sub;
+        load_chunk<HAS_B, VEC>(s, base, k0, K, ex, ey, eb, valid);
+        while (k0 < K) {
+            float cx[4], cy[4], cb[4];
+            bool cv[4];
 #pragma unroll
-                for (int r = 0; r < 4; ++r) valid[r] = true;
-            } else {
-#pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    valid[r] = k0 + r < K;
-                    const long long j = base + k0 + (valid[r] ? r : 0);
-                    ex[r] = __ldg(s.e1 + j);
-                    ey[r] = __ldg(s.e2 + j);
-                    eb[r] = HAS_B ? __ldg(s.b + j) : 0.f;
-                }
+            for (int r = 0; r < 4; ++r) {
+                cx[r] = ex[r];
+                cy[r] = ey[r];
+                cb[r] = eb[r];
+                cv[r] = valid[r];
             }
-            float x[4], d1[4], d2[4], qq[4];
+            k0 += 4 * kGroup;
+            load_chunk<HAS_B, VEC>(s, base, k0, K, ex, ey, eb, valid);
+            float x[4], ru[4], c1[4], c2[4], qq[4];
             float mloc = m;
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
-                sample_terms<FAMILY, HAS_B>(s, a_nat, ex[r], ey[r], HAS_B ? eb[r] : 0.f, x[r], d1[r],
-                                            d2[r], qq[r]);
-                if (!valid[r]) x[r] = -INFINITY;
+                sample_terms<FAMILY, HAS_B>(s, a_nat, cx[r], cy[r], HAS_B ? cb[r] : 0.f, x[r], ru[r], c1[r],
+                                            c2[r], qq[r]);
+                if (!cv[r]) x[r] = -INFINITY;
                 mloc = fmaxf(mloc, x[r]);
             }
-            const float sc = exp2f(m - mloc);
-            sw *= sc;
-            t1 *= sc;
-            t2 *= sc;
-            tq *= sc;
-            m = mloc;
+            if (mloc > m) {          // rescale only when the running maximum rises
+                const float sc = ex2_ftz(m - mloc);
+                sw *= sc;
+                t1 *= sc;
+                t2 *= sc;
+                tq *= sc;
+                m = mloc;
+            }
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
-                const float e = exp2f(x[r] - m);
+                const float e = ex2_ftz(x[r] - m);
+                const float er = e * ru[r];
                 sw += e;
-                t1 = fmaf(e, d1[r], t1);
-                t2 = fmaf(e, d2[r], t2);
+                t1 = fmaf(er, c1[r], t1);
+                t2 = fmaf(er, c2[r], t2);
                 tq = fmaf(e, qq[r], tq);
             }
         }
@@ -133,7 +189,7 @@ __global__ void __launch_bounds__(kShearThreads) shear_kernel(const ShearLaunch 
             const float o2 = __shfl_xor_sync(gmask, t2, o, kGroup);
             const float oq = __shfl_xor_sync(gmask, tq, o, kGroup);
             const float mn = fmaxf(m, mo);
-            const float ca = exp2f(m - mn), cb = exp2f(mo - mn);
+            const float ca = ex2_ftz(m - mn), cb = ex2_ftz(mo - mn);
             sw = sw * ca + so * cb;
             t1 = t1 * ca + o1 * cb;
             t2 = t2 * ca + o2 * cb;
@@ -144,8 +200,8 @@ __global__ void __launch_bounds__(kShearThreads) shear_kernel(const ShearLaunch 
             if (sw > 0.f) {
                 const float inv = 1.0f / sw;
                 av += (double)m + (double)__log2f(sw);
-                a1 += (double)(t1 * inv);
-                a2 += (double)(t2 * inv);
+                a1 += (double)(-2.0f * t1 * inv);
+                a2 += (double)(-2.0f * t2 * inv);
                 aq += (double)(tq * inv);
             } else {
                 av = -INFINITY;
