@@ -194,6 +194,28 @@ def flops_per_eval(N):
     return 33 * H * N + 9 * H
 
 
+# DRAM bytes per unit from ncu captures (read + write per launch / units in
+# the captured launch).  Each figure holds only for
+# the kernel source it was taken on, identified by its sha256; after any change
+# to that file the traffic is reported as null until the next capture.
+CAPTURED_TRAFFIC = {
+    # 53x53 galaxy of the plain workload: (13,885,440 + 2,816) B / 1,216 galaxies
+    "fit": ("paper_2604_22048_gb300/csrc/bs_fit.cu",
+            "4b6c1924531aa5d5382dae29bfd3ced0d9fcce0ced840a7930ed56eda6f81208", 11421.3),
+}
+
+
+def captured_traffic(kind, units):
+    if kind not in CAPTURED_TRAFFIC:
+        return None
+    import hashlib
+    path, sha, per_unit = CAPTURED_TRAFFIC[kind]
+    with open(os.path.join(ROOT, path), "rb") as fh:
+        if hashlib.sha256(fh.read()).hexdigest() != sha:
+            return None
+    return per_unit * units
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -367,7 +389,10 @@ def our_arm(a, world, rank, local_rank):
            "dtype": "f32", "data": "synthetic (seeded draws rendered by bs_render; L2 flushed between steps)",
            "config": workload_config(a) | {"parallelism": f"dp{world}: galaxies per rank, shear sums all-reduced"},
            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                        "frac": achieved / peak_tflops, "traffic": None,
+                        "frac": achieved / peak_tflops,
+                        "traffic": captured_traffic("fit", a.n_gal) if a.workload == "plain" else None,
+                        "traffic_note": "DRAM read+write per launch, scaled from a 1,216-galaxy ncu capture "
+                                        "of the same kernel source by the galaxies per launch",
                         "kernel": "fit_kernel<2,2>" if a.workload == "plain" else "fit_kernel<1..4,2> (graph)",
                         "peak_how": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
                                     f"{sm_max:.0f} MHz (max SM clock)",

@@ -16,7 +16,9 @@
 // dx/dalpha = Q / alpha^3.
 //
 // Each galaxy's K samples are read by a group of 8 lanes (float4 loads when
-// the rows are 16-byte aligned, one chunk ahead of the arithmetic), x is kept in log2 units for the MUFU exp2, and the group keeps
+// the rows are 16-byte aligned, one chunk ahead of the arithmetic); the
+// arithmetic runs on pairs of samples in packed FP32x2 instructions, x is
+// kept in log2 units for the MUFU exp2, and the group keeps
 // an online log-sum-exp (running max, sum of weights and weighted derivative
 // sums), merged with shuffles.  Per-galaxy totals are
 // accumulated in FP64 and written as per-block partials; a one-block kernel
@@ -57,130 +59,198 @@ __device__ __forceinline__ float rcp_ftz(float x)
     return r;
 }
 
-// Per sample: log2 weight x and the factors of its derivatives,
-//   dx/dg_i = -2 rU c_i,  c_i = du_i (Q/(2 alpha^2) - kappa) - n_i/(2 alpha^2),
-// returned as (rU, c1, c2, Q); the -2 is applied once per galaxy.
-template <int FAMILY, bool HAS_B>
-__device__ __forceinline__ void sample_terms(const ShearLaunch &s, float a_nat, float e1, float e2,
-                                             float bv, float &x2, float &ru, float &c1, float &c2,
-                                             float &q)
+// Packed FP32x2 arithmetic: two samples per instruction, each half rounded
+// like the scalar operation.
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b)
 {
-    const float ur = fmaf(-s.g1, e1, fmaf(-s.g2, e2, 1.0f));
-    const float vi = fmaf(s.g1, e2, -s.g2 * e1);
-    const float U = fmaf(ur, ur, vi * vi);
-    const float n1 = e1 - s.g1, n2 = e2 - s.g2;
-    const float Nn = fmaf(n1, n1, n2 * n2);
-    const float rU = rcp_ftz(U);
-    const float Q = Nn * rU;
-    const float Ep = fmaf(e1, e1, e2 * e2);
-    float x = fmaf(s.c0, Ep, fmaf(-s.kappa, lg2_ftz(U), -s.a2 * Q));
-    if (FAMILY == BS_EPRIOR_TRUNC_GAUSS) {
-        x = fmaf(-2.0f, lg2_ftz(1.0f - Ep), x);
-        if (!(Q < s.r2)) x = -INFINITY;
-    }
-    if (HAS_B) x = fmaf(kLog2e, bv, x);
-    const float aqk = fmaf(a_nat, Q, -s.kappa);
-    const float du1 = fmaf(ur, e1, -vi * e2);
-    const float du2 = fmaf(ur, e2, vi * e1);
-    c1 = fmaf(du1, aqk, -a_nat * n1);
-    c2 = fmaf(du2, aqk, -a_nat * n2);
-    ru = rU;
-    q = Q;
-    x2 = x;
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "sub.rn.f32x2 rd, ra, rb;\n\t"
+        "mov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
 }
 
-// Loads of one chunk (4 consecutive samples of this lane).
-template <bool HAS_B, bool VEC>
-__device__ __forceinline__ void load_chunk(const ShearLaunch &s, long long base, int k0, int K, float (&ex)[4],
-                                           float (&ey)[4], float (&eb)[4], bool (&valid)[4])
+// Per-launch constants in registers.
+struct ShearConst {
+    float2 g1, g2, ng1, ng2, G2m2;   // g, -g, |g|^2 - 2
+    float2 a2n, an, nk;              // -a2 (log2 units), a = 1/(2 alpha^2), -kappa
+    float2 c0, lgk;                  // log2(e)/(2 sigma_e0^2); multiplier of the log term
+    float r2;
+};
+
+__device__ __forceinline__ ShearConst shear_const(const ShearLaunch &s, int family)
 {
+    ShearConst c;
+    const float a = s.a2 * kLn2;
+    c.g1 = f2(s.g1);
+    c.g2 = f2(s.g2);
+    c.ng1 = f2(-s.g1);
+    c.ng2 = f2(-s.g2);
+    c.G2m2 = f2(fmaf(s.g1, s.g1, s.g2 * s.g2) - 2.0f);
+    c.a2n = f2(-s.a2);
+    c.an = f2(a);
+    c.nk = f2(-s.kappa);
+    c.c0 = f2(s.c0);
+    // BA14: -kappa log2 U; truncated Gaussian: -2 log2 U - 2 log2(1 - |eps'|^2)
+    // = -2 log2(U (1 - |eps'|^2)) (kappa = 2), one logarithm
+    c.lgk = f2(family == BS_EPRIOR_TRUNC_GAUSS ? -2.0f : -s.kappa);
+    c.r2 = s.r2;
+    return c;
+}
+
+// Two samples: log2 weights x and the factors of the derivatives,
+//   dx/dg_i = -2 rU c_i,  c_i = du_i (a Q - kappa) - a (eps'_i - g_i),
+// with |eps' - g|^2 = |eps'|^2 + 2 ur - 2 + |g|^2 (ur = 1 - g.eps'); the -2 is
+// applied once per galaxy.
+template <int FAMILY, bool HAS_B>
+__device__ __forceinline__ void pair_terms(const ShearConst &c, float2 e1, float2 e2, float2 bv, float2 &x,
+                                           float2 &ru, float2 &c1, float2 &c2, float2 &q)
+{
+    const float2 ur = fma2(c.ng1, e1, fma2(c.ng2, e2, f2(1.0f)));
+    const float2 nvi = fma2(c.g2, e1, mul2(c.ng1, e2));          // -(g1 e2 - g2 e1)
+    const float2 U = fma2(ur, ur, mul2(nvi, nvi));
+    const float2 Ep = fma2(e1, e1, mul2(e2, e2));
+    const float2 Nn = fma2(f2(2.0f), ur, add2(Ep, c.G2m2));
+    const float2 rU = make_float2(rcp_ftz(U.x), rcp_ftz(U.y));
+    const float2 Q = mul2(Nn, rU);
+    float2 larg = U;
+    if (FAMILY == BS_EPRIOR_TRUNC_GAUSS) larg = mul2(U, sub2(f2(1.0f), Ep));
+    const float2 lg = make_float2(lg2_ftz(larg.x), lg2_ftz(larg.y));
+    float2 xx = fma2(c.c0, Ep, fma2(c.lgk, lg, mul2(c.a2n, Q)));
+    if (FAMILY == BS_EPRIOR_TRUNC_GAUSS) {
+        if (!(Q.x < c.r2)) xx.x = -INFINITY;
+        if (!(Q.y < c.r2)) xx.y = -INFINITY;
+    }
+    if (HAS_B) xx = fma2(f2(kLog2e), bv, xx);
+    const float2 aqk = fma2(c.an, Q, c.nk);
+    const float2 du1 = fma2(nvi, e2, mul2(ur, e1));              // ur e1 - vi e2
+    const float2 du2 = sub2(mul2(ur, e2), mul2(nvi, e1));        // ur e2 + vi e1
+    c1 = fma2(du1, aqk, mul2(c.an, sub2(c.g1, e1)));
+    c2 = fma2(du2, aqk, mul2(c.an, sub2(c.g2, e2)));
+    ru = rU;
+    q = Q;
+    x = xx;
+}
+
+// One chunk: 4 consecutive samples of this lane.
+struct Chunk {
+    float4 e1, e2, b;
+    bool full;     // all four samples exist
+    int nvalid;
+};
+
+template <bool HAS_B, bool VEC>
+__device__ __forceinline__ void load_chunk(const ShearLaunch &s, long long base, int k0, int K, Chunk &ch)
+{
+    ch.nvalid = k0 < K ? min(4, K - k0) : 0;
+    ch.full = ch.nvalid == 4;
     if (VEC) {
         if (k0 < K) {
-            const float4 v1 = __ldg(reinterpret_cast<const float4 *>(s.e1 + base + k0));
-            const float4 v2 = __ldg(reinterpret_cast<const float4 *>(s.e2 + base + k0));
-            ex[0] = v1.x; ex[1] = v1.y; ex[2] = v1.z; ex[3] = v1.w;
-            ey[0] = v2.x; ey[1] = v2.y; ey[2] = v2.z; ey[3] = v2.w;
-            if (HAS_B) {
-                const float4 vb = __ldg(reinterpret_cast<const float4 *>(s.b + base + k0));
-                eb[0] = vb.x; eb[1] = vb.y; eb[2] = vb.z; eb[3] = vb.w;
-            }
+            ch.e1 = __ldg(reinterpret_cast<const float4 *>(s.e1 + base + k0));
+            ch.e2 = __ldg(reinterpret_cast<const float4 *>(s.e2 + base + k0));
+            if (HAS_B) ch.b = __ldg(reinterpret_cast<const float4 *>(s.b + base + k0));
         }
-#pragma unroll
-        for (int r = 0; r < 4; ++r) valid[r] = k0 < K;
     } else {
+        float t1[4] = {0.f, 0.f, 0.f, 0.f}, t2[4] = {0.f, 0.f, 0.f, 0.f}, tb[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
-            valid[r] = k0 + r < K;
-            if (valid[r]) {
+            if (r < ch.nvalid) {
                 const long long j = base + k0 + r;
-                ex[r] = __ldg(s.e1 + j);
-                ey[r] = __ldg(s.e2 + j);
-                eb[r] = HAS_B ? __ldg(s.b + j) : 0.f;
+                t1[r] = __ldg(s.e1 + j);
+                t2[r] = __ldg(s.e2 + j);
+                if (HAS_B) tb[r] = __ldg(s.b + j);
             }
         }
+        ch.e1 = make_float4(t1[0], t1[1], t1[2], t1[3]);
+        ch.e2 = make_float4(t2[0], t2[1], t2[2], t2[3]);
+        ch.b = make_float4(tb[0], tb[1], tb[2], tb[3]);
+    }
+}
+
+// Online log-sum-exp state of one lane (both halves share the maximum).
+struct Lse {
+    float m;
+    float2 sw, t1, t2, tq;
+};
+
+template <int FAMILY, bool HAS_B>
+__device__ __forceinline__ void eval_chunk(const ShearConst &c, const Chunk &ch, Lse &L)
+{
+    float2 x[2], ru[2], c1[2], c2[2], qq[2];
+    const float2 e1[2] = {make_float2(ch.e1.x, ch.e1.y), make_float2(ch.e1.z, ch.e1.w)};
+    const float2 e2[2] = {make_float2(ch.e2.x, ch.e2.y), make_float2(ch.e2.z, ch.e2.w)};
+    const float2 bb[2] = {make_float2(ch.b.x, ch.b.y), make_float2(ch.b.z, ch.b.w)};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) pair_terms<FAMILY, HAS_B>(c, e1[h], e2[h], bb[h], x[h], ru[h], c1[h], c2[h], qq[h]);
+    if (!ch.full) {
+        if (ch.nvalid < 4) x[1].y = -INFINITY;
+        if (ch.nvalid < 3) x[1].x = -INFINITY;
+        if (ch.nvalid < 2) x[0].y = -INFINITY;
+        if (ch.nvalid < 1) x[0].x = -INFINITY;
+    }
+    const float mloc = fmaxf(fmaxf(L.m, fmaxf(x[0].x, x[0].y)), fmaxf(x[1].x, x[1].y));
+    if (mloc > L.m) {            // rescale only when the running maximum rises
+        const float2 sc = f2(ex2_ftz(L.m - mloc));
+        L.sw = mul2(L.sw, sc);
+        L.t1 = mul2(L.t1, sc);
+        L.t2 = mul2(L.t2, sc);
+        L.tq = mul2(L.tq, sc);
+        L.m = mloc;
+    }
+    const float2 nm = f2(-L.m);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const float2 d = add2(x[h], nm);
+        const float2 e = make_float2(ex2_ftz(d.x), ex2_ftz(d.y));
+        const float2 er = mul2(e, ru[h]);
+        L.sw = add2(L.sw, e);
+        L.t1 = fma2(er, c1[h], L.t1);
+        L.t2 = fma2(er, c2[h], L.t2);
+        L.tq = fma2(e, qq[h], L.tq);
     }
 }
 
 template <int FAMILY, bool HAS_B, bool VEC>
-__global__ void __launch_bounds__(kShearThreads, 4) shear_kernel(const ShearLaunch s)
+__global__ void __launch_bounds__(kShearThreads, 3) shear_kernel(const ShearLaunch s)
 {
     const int lane = threadIdx.x & 31;
     const int sub = lane & (kGroup - 1);
     const unsigned gmask = 0xFFu << (lane & ~(kGroup - 1));
     const long long group = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / kGroup;
     const long long ngroups = (long long)gridDim.x * blockDim.x / kGroup;
-    const float a_nat = s.a2 * kLn2;    // 1 / (2 alpha^2)
+    const ShearConst c = shear_const(s, FAMILY);
     const int K = s.K;
     double av = 0.0, a1 = 0.0, a2 = 0.0, aq = 0.0;
 
     for (long long n = group; n < s.n_gal; n += ngroups) {
         const long long base = n * (long long)K;
-        float m = -1e30f, sw = 0.f, t1 = 0.f, t2 = 0.f, tq = 0.f;
-        // software pipelined: the next chunk's loads are in flight while the
-        // current chunk is evaluated
-        float ex[4] = {0.f, 0.f, 0.f, 0.f}, ey[4] = {0.f, 0.f, 0.f, 0.f}, eb[4] = {0.f, 0.f, 0.f, 0.f};
-        bool valid[4];
+        Lse L;
+        L.m = -1e30f;
+        L.sw = L.t1 = L.t2 = L.tq = f2(0.f);
+        // two chunk buffers in turn: the next chunk's loads are in flight
+        // while the current one is evaluated
+        Chunk A, B;
         int k0 = 4 * sub;
-        load_chunk<HAS_B, VEC>(s, base, k0, K, ex, ey, eb, valid);
-        while (k0 < K) {
-            float cx[4], cy[4], cb[4];
-            bool cv[4];
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                cx[r] = ex[r];
-                cy[r] = ey[r];
-                cb[r] = eb[r];
-                cv[r] = valid[r];
-            }
+        load_chunk<HAS_B, VEC>(s, base, k0, K, A);
+        for (;;) {
+            if (k0 >= K) break;
+            load_chunk<HAS_B, VEC>(s, base, k0 + 4 * kGroup, K, B);
+            eval_chunk<FAMILY, HAS_B>(c, A, L);
             k0 += 4 * kGroup;
-            load_chunk<HAS_B, VEC>(s, base, k0, K, ex, ey, eb, valid);
-            float x[4], ru[4], c1[4], c2[4], qq[4];
-            float mloc = m;
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                sample_terms<FAMILY, HAS_B>(s, a_nat, cx[r], cy[r], HAS_B ? cb[r] : 0.f, x[r], ru[r], c1[r],
-                                            c2[r], qq[r]);
-                if (!cv[r]) x[r] = -INFINITY;
-                mloc = fmaxf(mloc, x[r]);
-            }
-            if (mloc > m) {          // rescale only when the running maximum rises
-                const float sc = ex2_ftz(m - mloc);
-                sw *= sc;
-                t1 *= sc;
-                t2 *= sc;
-                tq *= sc;
-                m = mloc;
-            }
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                const float e = ex2_ftz(x[r] - m);
-                const float er = e * ru[r];
-                sw += e;
-                t1 = fmaf(er, c1[r], t1);
-                t2 = fmaf(er, c2[r], t2);
-                tq = fmaf(e, qq[r], tq);
-            }
+            if (k0 >= K) break;
+            load_chunk<HAS_B, VEC>(s, base, k0 + 4 * kGroup, K, A);
+            eval_chunk<FAMILY, HAS_B>(c, B, L);
+            k0 += 4 * kGroup;
         }
+        float m = L.m;
+        float sw = L.sw.x + L.sw.y, t1 = L.t1.x + L.t1.y, t2 = L.t2.x + L.t2.y, tq = L.tq.x + L.tq.y;
 #pragma unroll
         for (int o = kGroup / 2; o > 0; o >>= 1) {
             const float mo = __shfl_xor_sync(gmask, m, o, kGroup);
