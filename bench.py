@@ -70,7 +70,8 @@ def workload_config(a):
     else:
         desc = (f"batching: {a.n_gal} exponential galaxies, stamp side 2ceil(4.43hlr/p+1.5FWHM/p)+1 in [25,101] "
                 f"(uneven), per-galaxy Moffat beta=3 PSF FWHM U(0.6\",0.9\"), S/N log-U(10,100), FP32 with FP64 "
-                f"accumulation, class launches replayed as one CUDA graph, {chain}")
+                f"accumulation, class launches (register budget autotuned per class) replayed as one CUDA graph, "
+                f"{chain}")
     return {"workload": desc, "n_gal": a.n_gal, "side": a.side if a.workload == "plain" else "25-101",
             "chains": a.chains, "n_warmup": a.n_warmup, "n_samples": a.n_samples, "leapfrog_max": a.leapfrog,
             "l2": "flushed between timed steps (256 MB write)"}
@@ -308,7 +309,7 @@ def our_arm(a, world, rank, local_rank):
                         random_steps=True)
     if a.workload == "ragged":
         plan = api.RaggedFitPlan(inp["data"], inp["offsets"], inp["side"], inp["psf"], inp["sigma"], inp["init"],
-                                 cfg, capture=True)
+                                 cfg, capture=True, autotune=True)
     else:
         plan = api.FitPlan(inp["data"], inp["offsets"], inp["side"], inp["psf"], inp["sigma"], inp["init"], cfg,
                            max_side=a.side)
@@ -412,6 +413,8 @@ def our_arm(a, world, rank, local_rank):
            "paper_context": "0.45 s/galaxy to 300 ESS on one A100 with NUTS (63x63 stamps), i.e. 2.2 galaxies/s",
            "wall_s": wall}
 
+    if a.workload == "ragged":
+        out["plan"] = plan.info()
     if not a.no_e2e:
         out["e2e"] = e2e_run(a, world, inp, plan, shear, step, barrier, dev)
     if a.workload == "plain" and a.serve_requests > 0 and world == 1:

@@ -190,9 +190,17 @@ bs_status bs_fit_galaxies(const bs_fit_args *args, const bs_fit_out *out,
  * galaxy).  Galaxies are split by the 32-column slots their side needs
  * (<= 31, <= 63, <= 95, <= 127 px) and ordered largest first inside each
  * class; each class gets its own persistent launch sized for its largest
- * stamp.  With capture != 0 the class launches are recorded once as parallel
- * branches of a CUDA graph that bs_fit_plan_launch replays (one graph launch
- * per batch); otherwise they are issued one after another.
+ * stamp.  flags (bitwise or):
+ *   BS_PLAN_CAPTURE:  the class launches are recorded once as parallel
+ *                     branches of a CUDA graph that bs_fit_plan_launch
+ *                     replays (one graph launch per batch); otherwise they
+ *                     are issued one after another;
+ *   BS_PLAN_AUTOTUNE: per class, the kernel's register budget (128 registers,
+ *                     4 CTAs = 16 warps per SM; or 80 registers, more
+ *                     resident warps, some spills) is chosen by timing both on
+ *                     the class's first galaxies at creation (their outputs
+ *                     are overwritten by every later launch); the results
+ *                     are the same either way.
  *   side_host: host copy of args->side (n_gal).
  *   workspace: bs_fit_plan_workspace_bytes(args) bytes of device memory
  *              (work lists and per-class counters), owned by the caller.
@@ -201,13 +209,27 @@ bs_status bs_fit_galaxies(const bs_fit_args *args, const bs_fit_out *out,
  * change between launches.  Creation synchronises `stream`.
  * Errors: as bs_fit_galaxies, plus BS_ERR_INVALID_ARG for a side_host entry
  * that is even or outside 3..max_side. */
+#define BS_PLAN_CAPTURE 1
+#define BS_PLAN_AUTOTUNE 2
 typedef struct bs_fit_plan_s *bs_fit_plan;
 size_t bs_fit_plan_workspace_bytes(const bs_fit_args *args);
 bs_status bs_fit_plan_create(const bs_fit_args *args, const bs_fit_out *out,
-                             const int32_t *side_host, int32_t capture, void *workspace,
+                             const int32_t *side_host, int32_t flags, void *workspace,
                              size_t workspace_bytes, void *stream, bs_fit_plan *plan);
 bs_status bs_fit_plan_launch(bs_fit_plan plan, void *stream);
 bs_status bs_fit_plan_destroy(bs_fit_plan plan);
+
+/* What the plan chose for its i-th class launch (0 <= i < num_launches). */
+typedef struct {
+    int32_t slot_class;      /* 1..4: stamps of up to 32 x slot_class - 1 px */
+    int32_t max_side;        /* largest stamp of the class */
+    int32_t n_gal;           /* galaxies in the class */
+    int32_t grid;            /* persistent CTAs */
+    int32_t registers;       /* register budget of the kernel instance: 128 or 80 */
+    float trial_ms_128, trial_ms_80;  /* autotune trial times (0 if not tuned) */
+} bs_fit_plan_launch_info;
+int32_t bs_fit_plan_num_launches(bs_fit_plan plan);
+bs_status bs_fit_plan_info(bs_fit_plan plan, int32_t i, bs_fit_plan_launch_info *info);
 
 /* Galaxies of side max_side (n_chains chains each) that the current device
  * holds at once in one fit launch (SMs x resident CTAs): the batch size of a

@@ -25,7 +25,7 @@ EXPORTED = ["bs_prior_default", "bs_last_error", "bs_version", "bs_render", "bs_
             "bs_fit_galaxies", "bs_logpost_points", "bs_chain_ess", "bs_shear_workspace_bytes",
             "bs_shear_loglike", "bs_shear_estimate", "bs_shear_loglike_noalloc",
             "bs_fit_plan_workspace_bytes", "bs_fit_plan_create", "bs_fit_plan_launch", "bs_fit_plan_destroy",
-            "bs_fit_resident_galaxies", "bs_serve_request_bytes", "bs_serve_create", "bs_serve_submit",
+            "bs_fit_resident_galaxies", "bs_fit_plan_num_launches", "bs_fit_plan_info", "bs_serve_request_bytes", "bs_serve_create", "bs_serve_submit",
             "bs_serve_poll", "bs_serve_get_stats", "bs_serve_now_ns", "bs_serve_destroy"]
 
 
@@ -73,6 +73,14 @@ class EstimateCfg(C.Structure):
     _fields_ = [("free_alpha", C.c_int32), ("alpha", C.c_double), ("alpha_lo", C.c_double),
                 ("alpha_hi", C.c_double), ("n_gh", C.c_int32), ("allreduce", ALLREDUCE_FN),
                 ("allreduce_user", C.c_void_p)]
+
+
+BS_PLAN_CAPTURE, BS_PLAN_AUTOTUNE = 1, 2
+
+
+class PlanLaunchInfo(C.Structure):
+    _fields_ = [("slot_class", C.c_int32), ("max_side", C.c_int32), ("n_gal", C.c_int32), ("grid", C.c_int32),
+                ("registers", C.c_int32), ("trial_ms_128", C.c_float), ("trial_ms_80", C.c_float)]
 
 
 class ServeCfg(C.Structure):
@@ -157,6 +165,9 @@ def lib():
                                      C.POINTER(C.c_void_p)]
     L.bs_fit_plan_launch.argtypes = [vp, vp]
     L.bs_fit_plan_destroy.argtypes = [vp]
+    L.bs_fit_plan_num_launches.argtypes = [vp]
+    L.bs_fit_plan_num_launches.restype = i32
+    L.bs_fit_plan_info.argtypes = [vp, i32, C.POINTER(PlanLaunchInfo)]
     L.bs_fit_resident_galaxies.argtypes = [i32, i32]
     L.bs_fit_resident_galaxies.restype = i32
     L.bs_serve_request_bytes.argtypes = [C.POINTER(ServeCfg), i32]
@@ -170,7 +181,7 @@ def lib():
     L.bs_serve_destroy.argtypes = [vp]
     for nm in ("bs_render", "bs_fit_galaxies", "bs_logpost_points", "bs_chain_ess", "bs_shear_loglike",
                "bs_shear_estimate", "bs_shear_loglike_noalloc", "bs_fit_plan_create", "bs_fit_plan_launch",
-               "bs_fit_plan_destroy", "bs_serve_create", "bs_serve_submit", "bs_serve_poll", "bs_serve_get_stats",
+               "bs_fit_plan_destroy", "bs_fit_plan_info", "bs_serve_create", "bs_serve_submit", "bs_serve_poll", "bs_serve_get_stats",
                "bs_serve_destroy"):
         getattr(L, nm).restype = C.c_int
     _lib = L

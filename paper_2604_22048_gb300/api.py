@@ -177,16 +177,28 @@ class RaggedFitPlan(FitPlan):
     class, each class runs its own persistent launch sized for it, and (with
     capture) the launches replay as one CUDA graph (bs_fit_plan_*)."""
 
-    def __init__(self, data, offsets, side, psf, noise_sigma, init, cfg: FitConfig, *, capture=True, **kw):
+    def __init__(self, data, offsets, side, psf, noise_sigma, init, cfg: FitConfig, *, capture=True,
+                 autotune=False, **kw):
         super().__init__(data, offsets, side, psf, noise_sigma, init, cfg, **kw)
         side_h = np.ascontiguousarray(side.cpu().numpy(), dtype=np.int32)
         self.plan_ws_bytes = F.lib().bs_fit_plan_workspace_bytes(C.byref(self.args))
         self.plan_ws = torch.empty(self.plan_ws_bytes, dtype=torch.uint8, device=data.device)
         h = C.c_void_p()
         F.check(F.lib().bs_fit_plan_create(C.byref(self.args), C.byref(self.out), side_h.ctypes.data_as(C.c_void_p),
-                                           int(capture), _p(self.plan_ws), self.plan_ws_bytes, _stream(),
-                                           C.byref(h)))
+                                           (F.BS_PLAN_CAPTURE if capture else 0) |
+                                           (F.BS_PLAN_AUTOTUNE if autotune else 0), _p(self.plan_ws),
+                                           self.plan_ws_bytes, _stream(), C.byref(h)))
         self.handle = h
+
+    def info(self):
+        """Per class launch: slot class, largest side, galaxies, grid, register
+        budget and the autotune trial times (ms)."""
+        out = []
+        for i in range(F.lib().bs_fit_plan_num_launches(self.handle)):
+            r = F.PlanLaunchInfo()
+            F.check(F.lib().bs_fit_plan_info(self.handle, i, C.byref(r)))
+            out.append({n: getattr(r, n) for n, _ in F.PlanLaunchInfo._fields_})
+        return out
 
     def run(self, stream=None):
         st = C.c_void_p(stream.cuda_stream) if stream is not None else _stream()

@@ -906,13 +906,15 @@ FitKernel fit_kernel_nc(int max_side)
     }
 }
 
-// Register budget of the launch: BS_FIT_MINB=3 selects the 85-register build.
-FitKernel fit_kernel_for(int max_side)
+// Register budget of a launch: minb 3 selects the 85-register build, 2 the
+// 128-register one; 0 takes the process default (BS_FIT_MINB, else 2).
+FitKernel fit_kernel_for(int max_side, int minb)
 {
-    static const int minb = [] {
+    static const int dflt = [] {
         const char *s = getenv("BS_FIT_MINB");
         return (s && s[0] == '3') ? 3 : 2;
     }();
+    if (minb != 2 && minb != 3) minb = dflt;
     return minb == 3 ? fit_kernel_nc<3>(max_side) : fit_kernel_nc<2>(max_side);
 }
 
@@ -926,11 +928,11 @@ size_t fit_smem_bytes(int max_side)
            (size_t)(h + 1) * sizeof(float2);
 }
 
-int fit_blocks_per_sm(int n_chains, int max_side)
+int fit_blocks_per_sm(int n_chains, int max_side, int minb)
 {
     int nb = 0;
     const size_t smem = fit_smem_bytes(max_side);
-    FitKernel k = fit_kernel_for(max_side);
+    FitKernel k = fit_kernel_for(max_side, minb);
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, 32 * n_chains, smem) != cudaSuccess)
         return 1;
@@ -940,7 +942,7 @@ int fit_blocks_per_sm(int n_chains, int max_side)
 cudaError_t launch_fit(const FitParams &p, int grid, cudaStream_t stream)
 {
     const size_t smem = fit_smem_bytes(p.max_side);
-    FitKernel k = fit_kernel_for(p.max_side);
+    FitKernel k = fit_kernel_for(p.max_side, p.minb);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k<<<grid, 32 * p.n_chains, smem, stream>>>(p);

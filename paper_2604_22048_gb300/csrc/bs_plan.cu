@@ -6,8 +6,13 @@
 // class (longest-processing-time order for the persistent CTAs' work queue).
 // Each class gets its own persistent launch, sized for the largest stamp of
 // the class: shared memory, grid, and the kernel instance (column slots per
-// lane, register budget).  With capture the class launches are recorded once
-// as parallel branches of a CUDA graph (fork/join on the plan's streams); the
+// lane, register budget).  With BS_PLAN_AUTOTUNE the register budget of each
+// class -- 128 registers and 4 CTAs (16 warps) per SM, or 80 registers and
+// up to 6 CTAs (24 warps) -- is chosen by timing both instances on the
+// class's first galaxies (two waves of the larger grid, the second of two runs
+// timed); both instances do the same arithmetic, so the choice changes only
+// the speed.  With BS_PLAN_CAPTURE the class launches are recorded once as
+// parallel branches of a CUDA graph (fork/join on the plan's streams); the
 // graph is replayed by bs_fit_plan_launch on any stream.
 #include <algorithm>
 #include <cstring>
@@ -21,6 +26,8 @@ struct bs_fit_plan_s {
         bs::FitParams p;
         int grid;
         unsigned int *queue;
+        int slot_class;
+        float trial_ms[2];   // autotune: time of the 128- and 80-register instance (0 = not timed)
     };
     std::vector<Launch> launches;
     cudaStream_t streams[4] = {};
@@ -65,6 +72,62 @@ bs_status enqueue(bs_fit_plan_s *pl, cudaStream_t s0, bool forked)
     return BS_OK;
 }
 
+// Time one launch of L on its first n_trial galaxies with register budget
+// minb (a private stream; outputs of those galaxies are overwritten by the
+// plan's own launches later).
+cudaError_t time_variant(const bs_fit_plan_s::Launch &L, int minb, int n_trial, int sms, cudaStream_t st,
+                         cudaEvent_t e0, cudaEvent_t e1, float &ms)
+{
+    bs::FitParams p = L.p;
+    p.minb = minb;
+    p.n_work = n_trial;
+    const int per_sm = bs::fit_blocks_per_sm(p.n_chains, p.max_side, minb);
+    const int grid = std::min(n_trial, sms * per_sm);
+    cudaError_t e = cudaSuccess;
+    for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
+        e = cudaMemsetAsync(L.queue, 0, sizeof(unsigned int), st);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+        if (e == cudaSuccess) e = bs::launch_fit(p, grid, st);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    }
+    return e;
+}
+
+cudaError_t autotune(bs_fit_plan_s *pl, int sms)
+{
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    for (auto &L : pl->launches) {
+        if (e != cudaSuccess) break;
+        const int waves = std::max(bs::fit_blocks_per_sm(L.p.n_chains, L.p.max_side, 2),
+                                   bs::fit_blocks_per_sm(L.p.n_chains, L.p.max_side, 3));
+        const int n_trial = std::min(L.p.n_work, 2 * sms * waves);
+        float best = 0.f;
+        int best_minb = 2;
+        for (int v = 0; v < 2 && e == cudaSuccess; ++v) {
+            const int minb = v == 0 ? 2 : 3;
+            float ms = 0.f;
+            e = time_variant(L, minb, n_trial, sms, st, e0, e1, ms);
+            L.trial_ms[v] = ms;
+            if (e == cudaSuccess && (v == 0 || ms < best)) {
+                best = ms;
+                best_minb = minb;
+            }
+        }
+        L.p.minb = best_minb;
+        L.grid = std::min(L.p.n_work, sms * bs::fit_blocks_per_sm(L.p.n_chains, L.p.max_side, best_minb));
+    }
+    if (st) cudaStreamDestroy(st);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    return e;
+}
+
 void release(bs_fit_plan_s *pl)
 {
     if (pl->exec) cudaGraphExecDestroy(pl->exec);
@@ -87,10 +150,13 @@ size_t bs_fit_plan_workspace_bytes(const bs_fit_args *args)
 }
 
 bs_status bs_fit_plan_create(const bs_fit_args *a, const bs_fit_out *o, const int32_t *side_host,
-                             int32_t capture, void *workspace, size_t workspace_bytes, void *stream,
+                             int32_t flags, void *workspace, size_t workspace_bytes, void *stream,
                              bs_fit_plan *plan)
 {
     if (!plan) return bs::set_error(BS_ERR_INVALID_ARG, "bs_fit_plan_create: NULL plan");
+    if (flags & ~(BS_PLAN_CAPTURE | BS_PLAN_AUTOTUNE))
+        return bs::set_error(BS_ERR_INVALID_ARG, "bs_fit_plan_create: unknown flags 0x%x", (unsigned)flags);
+    const bool capture = (flags & BS_PLAN_CAPTURE) != 0;
     *plan = nullptr;
     bs::FitParams base;
     bs_status st = bs::fit_params_from_args(a, o, base, "bs_fit_plan_create");
@@ -141,10 +207,19 @@ bs_status bs_fit_plan_create(const bs_fit_args *a, const bs_fit_out *o, const in
         L.p.n_work = count[c];
         L.queue = reinterpret_cast<unsigned int *>(counters + kAlign * c);
         L.p.queue = L.queue;
-        const int per_sm = bs::fit_blocks_per_sm(a->n_chains, maxs[c]);
+        L.slot_class = c + 1;
+        L.trial_ms[0] = L.trial_ms[1] = 0.f;
+        const int per_sm = bs::fit_blocks_per_sm(a->n_chains, maxs[c], L.p.minb);
         L.grid = std::min(count[c], sms * per_sm);
         pl->launches.push_back(L);
         start += count[c];
+    }
+    if ((flags & BS_PLAN_AUTOTUNE) && n > 0) {
+        e = autotune(pl, sms);
+        if (e != cudaSuccess) {
+            release(pl);
+            return bs::set_error(BS_ERR_CUDA, "bs_fit_plan_create: autotune: %s", cudaGetErrorString(e));
+        }
     }
     if (capture && !pl->launches.empty()) {
         for (size_t i = 0; i < pl->launches.size() && e == cudaSuccess; ++i) {
@@ -160,7 +235,7 @@ bs_status bs_fit_plan_create(const bs_fit_args *a, const bs_fit_out *o, const in
             return bs::set_error(BS_ERR_CUDA, "bs_fit_plan_create: streams: %s", cudaGetErrorString(e));
         }
         // kernel attributes are set outside the capture
-        for (auto &L : pl->launches) bs::fit_blocks_per_sm(a->n_chains, L.p.max_side);
+        for (auto &L : pl->launches) bs::fit_blocks_per_sm(a->n_chains, L.p.max_side, L.p.minb);
         e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
             st = enqueue(pl, cap, true);
@@ -192,6 +267,24 @@ bs_status bs_fit_plan_launch(bs_fit_plan plan, void *stream)
     }
     return enqueue(plan, s, false);
 }
+
+bs_status bs_fit_plan_info(bs_fit_plan plan, int32_t i, bs_fit_plan_launch_info *info)
+{
+    if (!plan || !info) return bs::set_error(BS_ERR_INVALID_ARG, "bs_fit_plan_info: NULL argument");
+    if (i < 0 || i >= (int32_t)plan->launches.size())
+        return bs::set_error(BS_ERR_INVALID_ARG, "bs_fit_plan_info: launch %d of %zu", i, plan->launches.size());
+    const auto &L = plan->launches[i];
+    info->slot_class = L.slot_class;
+    info->max_side = L.p.max_side;
+    info->n_gal = L.p.n_work;
+    info->grid = L.grid;
+    info->registers = L.p.minb == 3 ? 80 : 128;
+    info->trial_ms_128 = L.trial_ms[0];
+    info->trial_ms_80 = L.trial_ms[1];
+    return BS_OK;
+}
+
+int32_t bs_fit_plan_num_launches(bs_fit_plan plan) { return plan ? (int32_t)plan->launches.size() : 0; }
 
 bs_status bs_fit_plan_destroy(bs_fit_plan plan)
 {

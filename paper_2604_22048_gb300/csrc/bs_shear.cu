@@ -79,8 +79,8 @@ __device__ __forceinline__ float2 sub2(float2 a, float2 b)
 
 // Per-launch constants in registers.
 struct ShearConst {
-    float2 g1, g2, ng1, ng2, G2m2;   // g, -g, |g|^2 - 2
-    float2 a2n, an, nk;              // -a2 (log2 units), a = 1/(2 alpha^2), -kappa
+    float2 g1, g2, ng1, ng2;         // g, -g
+    float2 a2n, an, nan, nk;         // -a2 (log2 units), a = 1/(2 alpha^2), -a, -kappa
     float2 c0, lgk;                  // log2(e)/(2 sigma_e0^2); multiplier of the log term
     float r2;
 };
@@ -93,9 +93,9 @@ __device__ __forceinline__ ShearConst shear_const(const ShearLaunch &s, int fami
     c.g2 = f2(s.g2);
     c.ng1 = f2(-s.g1);
     c.ng2 = f2(-s.g2);
-    c.G2m2 = f2(fmaf(s.g1, s.g1, s.g2 * s.g2) - 2.0f);
     c.a2n = f2(-s.a2);
     c.an = f2(a);
+    c.nan = f2(-a);
     c.nk = f2(-s.kappa);
     c.c0 = f2(s.c0);
     // BA14: -kappa log2 U; truncated Gaussian: -2 log2 U - 2 log2(1 - |eps'|^2)
@@ -106,9 +106,9 @@ __device__ __forceinline__ ShearConst shear_const(const ShearLaunch &s, int fami
 }
 
 // Two samples: log2 weights x and the factors of the derivatives,
-//   dx/dg_i = -2 rU c_i,  c_i = du_i (a Q - kappa) - a (eps'_i - g_i),
-// with |eps' - g|^2 = |eps'|^2 + 2 ur - 2 + |g|^2 (ur = 1 - g.eps'); the -2 is
-// applied once per galaxy.
+//   dx/dg_i = -2 rU c_i,  c_i = du_i (a Q - kappa) - a n_i,  n = eps' - g;
+// the -2 is applied once per galaxy.  n is formed explicitly (not expanded
+// through |eps'|^2 - 2 g.eps' + |g|^2, which cancels when eps' is near g).
 template <int FAMILY, bool HAS_B>
 __device__ __forceinline__ void pair_terms(const ShearConst &c, float2 e1, float2 e2, float2 bv, float2 &x,
                                            float2 &ru, float2 &c1, float2 &c2, float2 &q)
@@ -117,7 +117,8 @@ __device__ __forceinline__ void pair_terms(const ShearConst &c, float2 e1, float
     const float2 nvi = fma2(c.g2, e1, mul2(c.ng1, e2));          // -(g1 e2 - g2 e1)
     const float2 U = fma2(ur, ur, mul2(nvi, nvi));
     const float2 Ep = fma2(e1, e1, mul2(e2, e2));
-    const float2 Nn = fma2(f2(2.0f), ur, add2(Ep, c.G2m2));
+    const float2 n1 = sub2(e1, c.g1), n2 = sub2(e2, c.g2);
+    const float2 Nn = fma2(n1, n1, mul2(n2, n2));
     const float2 rU = make_float2(rcp_ftz(U.x), rcp_ftz(U.y));
     const float2 Q = mul2(Nn, rU);
     float2 larg = U;
@@ -132,8 +133,8 @@ __device__ __forceinline__ void pair_terms(const ShearConst &c, float2 e1, float
     const float2 aqk = fma2(c.an, Q, c.nk);
     const float2 du1 = fma2(nvi, e2, mul2(ur, e1));              // ur e1 - vi e2
     const float2 du2 = sub2(mul2(ur, e2), mul2(nvi, e1));        // ur e2 + vi e1
-    c1 = fma2(du1, aqk, mul2(c.an, sub2(c.g1, e1)));
-    c2 = fma2(du2, aqk, mul2(c.an, sub2(c.g2, e2)));
+    c1 = fma2(du1, aqk, mul2(c.nan, n1));
+    c2 = fma2(du2, aqk, mul2(c.nan, n2));
     ru = rU;
     q = Q;
     x = xx;
@@ -217,69 +218,52 @@ __device__ __forceinline__ void eval_chunk(const ShearConst &c, const Chunk &ch,
     }
 }
 
-template <int FAMILY, bool HAS_B, bool VEC>
-__global__ void __launch_bounds__(kShearThreads, 3) shear_kernel(const ShearLaunch s)
+// Merge the 8 lanes of a galaxy's group and add the galaxy's log-sum-exp and
+// softmax-weighted derivative sums to the lane-0 accumulators.
+__device__ __forceinline__ void finish_galaxy(const Lse &L, unsigned gmask, int sub, double &av, double &a1,
+                                              double &a2, double &aq)
 {
-    const int lane = threadIdx.x & 31;
-    const int sub = lane & (kGroup - 1);
-    const unsigned gmask = 0xFFu << (lane & ~(kGroup - 1));
-    const long long group = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / kGroup;
-    const long long ngroups = (long long)gridDim.x * blockDim.x / kGroup;
-    const ShearConst c = shear_const(s, FAMILY);
-    const int K = s.K;
-    double av = 0.0, a1 = 0.0, a2 = 0.0, aq = 0.0;
-
-    for (long long n = group; n < s.n_gal; n += ngroups) {
-        const long long base = n * (long long)K;
-        Lse L;
-        L.m = -1e30f;
-        L.sw = L.t1 = L.t2 = L.tq = f2(0.f);
-        // two chunk buffers in turn: the next chunk's loads are in flight
-        // while the current one is evaluated
-        Chunk A, B;
-        int k0 = 4 * sub;
-        load_chunk<HAS_B, VEC>(s, base, k0, K, A);
-        for (;;) {
-            if (k0 >= K) break;
-            load_chunk<HAS_B, VEC>(s, base, k0 + 4 * kGroup, K, B);
-            eval_chunk<FAMILY, HAS_B>(c, A, L);
-            k0 += 4 * kGroup;
-            if (k0 >= K) break;
-            load_chunk<HAS_B, VEC>(s, base, k0 + 4 * kGroup, K, A);
-            eval_chunk<FAMILY, HAS_B>(c, B, L);
-            k0 += 4 * kGroup;
-        }
-        float m = L.m;
-        float sw = L.sw.x + L.sw.y, t1 = L.t1.x + L.t1.y, t2 = L.t2.x + L.t2.y, tq = L.tq.x + L.tq.y;
+    float m = L.m;
+    float sw = L.sw.x + L.sw.y, t1 = L.t1.x + L.t1.y, t2 = L.t2.x + L.t2.y, tq = L.tq.x + L.tq.y;
 #pragma unroll
-        for (int o = kGroup / 2; o > 0; o >>= 1) {
-            const float mo = __shfl_xor_sync(gmask, m, o, kGroup);
-            const float so = __shfl_xor_sync(gmask, sw, o, kGroup);
-            const float o1 = __shfl_xor_sync(gmask, t1, o, kGroup);
-            const float o2 = __shfl_xor_sync(gmask, t2, o, kGroup);
-            const float oq = __shfl_xor_sync(gmask, tq, o, kGroup);
-            const float mn = fmaxf(m, mo);
-            const float ca = ex2_ftz(m - mn), cb = ex2_ftz(mo - mn);
-            sw = sw * ca + so * cb;
-            t1 = t1 * ca + o1 * cb;
-            t2 = t2 * ca + o2 * cb;
-            tq = tq * ca + oq * cb;
-            m = mn;
-        }
-        if (sub == 0) {
-            if (sw > 0.f) {
-                const float inv = 1.0f / sw;
-                av += (double)m + (double)__log2f(sw);
-                a1 += (double)(-2.0f * t1 * inv);
-                a2 += (double)(-2.0f * t2 * inv);
-                aq += (double)(tq * inv);
-            } else {
-                av = -INFINITY;
-            }
+    for (int o = kGroup / 2; o > 0; o >>= 1) {
+        const float mo = __shfl_xor_sync(gmask, m, o, kGroup);
+        const float so = __shfl_xor_sync(gmask, sw, o, kGroup);
+        const float o1 = __shfl_xor_sync(gmask, t1, o, kGroup);
+        const float o2 = __shfl_xor_sync(gmask, t2, o, kGroup);
+        const float oq = __shfl_xor_sync(gmask, tq, o, kGroup);
+        const float mn = fmaxf(m, mo);
+        const float ca = ex2_ftz(m - mn), cb = ex2_ftz(mo - mn);
+        sw = sw * ca + so * cb;
+        t1 = t1 * ca + o1 * cb;
+        t2 = t2 * ca + o2 * cb;
+        tq = tq * ca + oq * cb;
+        m = mn;
+    }
+    if (sub == 0) {
+        if (sw > 0.f) {
+            const float inv = 1.0f / sw;
+            av += (double)m + (double)__log2f(sw);
+            a1 += (double)(-2.0f * t1 * inv);
+            a2 += (double)(-2.0f * t2 * inv);
+            aq += (double)(tq * inv);
+        } else {
+            av = -INFINITY;
         }
     }
-    // block reduction in FP64
+}
+
+__device__ __forceinline__ void lse_reset(Lse &L)
+{
+    L.m = -1e30f;
+    L.sw = L.t1 = L.t2 = L.tq = f2(0.f);
+}
+
+// Block reduction of the four FP64 accumulators into this block's partials.
+__device__ __forceinline__ void block_partials(const ShearLaunch &s, double av, double a1, double a2, double aq)
+{
     __shared__ double red[kShearThreads / 32][4];
+    const int lane = threadIdx.x & 31;
     av = warp_sum_d(av);
     a1 = warp_sum_d(a1);
     a2 = warp_sum_d(a2);
@@ -297,6 +281,138 @@ __global__ void __launch_bounds__(kShearThreads, 3) shear_kernel(const ShearLaun
         for (int i = 0; i < kShearThreads / 32; ++i) t += red[i][threadIdx.x];
         s.partials[(size_t)blockIdx.x * 4 + threadIdx.x] = t;
     }
+}
+
+// Any K and alignment: scalar or float4 loads into two register buffers in
+// turn (the next chunk's loads in flight while the current one is evaluated).
+template <int FAMILY, bool HAS_B, bool VEC>
+__global__ void __launch_bounds__(kShearThreads, 3) shear_kernel(const ShearLaunch s)
+{
+    const int lane = threadIdx.x & 31;
+    const int sub = lane & (kGroup - 1);
+    const unsigned gmask = 0xFFu << (lane & ~(kGroup - 1));
+    const long long group = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / kGroup;
+    const long long ngroups = (long long)gridDim.x * blockDim.x / kGroup;
+    const ShearConst c = shear_const(s, FAMILY);
+    const int K = s.K;
+    double av = 0.0, a1 = 0.0, a2 = 0.0, aq = 0.0;
+
+    for (long long n = group; n < s.n_gal; n += ngroups) {
+        const long long base = n * (long long)K;
+        Lse L;
+        lse_reset(L);
+        Chunk A, B;
+        int k0 = 4 * sub;
+        load_chunk<HAS_B, VEC>(s, base, k0, K, A);
+        for (;;) {
+            if (k0 >= K) break;
+            load_chunk<HAS_B, VEC>(s, base, k0 + 4 * kGroup, K, B);
+            eval_chunk<FAMILY, HAS_B>(c, A, L);
+            k0 += 4 * kGroup;
+            if (k0 >= K) break;
+            load_chunk<HAS_B, VEC>(s, base, k0 + 4 * kGroup, K, A);
+            eval_chunk<FAMILY, HAS_B>(c, B, L);
+            k0 += 4 * kGroup;
+        }
+        finish_galaxy(L, gmask, sub, av, a1, a2, aq);
+    }
+    block_partials(s, av, a1, a2, aq);
+}
+
+// Asynchronous 16-byte global -> shared copies (L2 only), grouped per chunk.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+constexpr int kStages = 4;   // chunks per lane in flight: this one and three ahead
+
+__host__ __device__ constexpr size_t async_smem_bytes(bool has_b)
+{
+    return (size_t)kStages * (has_b ? 3 : 2) * kShearThreads * sizeof(float4);
+}
+
+// K % 4 == 0 and 16-byte aligned rows: each lane streams its chunks through
+// a kStages-deep ring of its own shared-memory slots with cp.async, over the
+// flattened sequence (galaxy, chunk) of its group, so the pipeline does not
+// drain between galaxies.  A lane only reads the slots it filled, after
+// cp.async.wait_group; no barrier is needed.
+template <int FAMILY, bool HAS_B>
+__global__ void __launch_bounds__(kShearThreads, 3) shear_kernel_async(const ShearLaunch s)
+{
+    extern __shared__ float4 sbuf[];
+    constexpr int NV = HAS_B ? 3 : 2;
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int sub = lane & (kGroup - 1);
+    const unsigned gmask = 0xFFu << (lane & ~(kGroup - 1));
+    const long long group = ((long long)blockIdx.x * blockDim.x + tid) / kGroup;
+    const long long ngroups = (long long)gridDim.x * blockDim.x / kGroup;
+    const ShearConst c = shear_const(s, FAMILY);
+    const int K = s.K;
+    const int cpg = (K + 4 * kGroup - 1) / (4 * kGroup);     // chunks per galaxy per lane
+    const long long my_gal = group < s.n_gal ? (s.n_gal - 1 - group) / ngroups + 1 : 0;
+    const long long n_items = my_gal * cpg;
+    double av = 0.0, a1 = 0.0, a2 = 0.0, aq = 0.0;
+
+    // issuer position: galaxy, chunk, ring slot
+    long long in = group;
+    int ic = 0, ist = 0;
+    auto issue = [&]() {
+        if (in < s.n_gal) {
+            const int k0 = 4 * sub + 4 * kGroup * ic;
+            if (k0 < K) {
+                const long long off = in * (long long)K + k0;
+                cp_async16(&sbuf[(ist * NV + 0) * kShearThreads + tid], s.e1 + off);
+                cp_async16(&sbuf[(ist * NV + 1) * kShearThreads + tid], s.e2 + off);
+                if (HAS_B) cp_async16(&sbuf[(ist * NV + 2) * kShearThreads + tid], s.b + off);
+            }
+            if (++ic == cpg) {
+                ic = 0;
+                in += ngroups;
+            }
+        }
+        cp_async_commit();
+        ist = ist + 1 == kStages ? 0 : ist + 1;
+    };
+#pragma unroll
+    for (int t = 0; t < kStages - 1; ++t) issue();
+
+    Lse L;
+    lse_reset(L);
+    int cc = 0, cst = 0;     // consumer: chunk within the galaxy, ring slot
+    for (long long t = 0; t < n_items; ++t) {
+        issue();
+        cp_async_wait<kStages - 1>();
+        const int k0 = 4 * sub + 4 * kGroup * cc;
+        Chunk ch;
+        ch.nvalid = k0 < K ? 4 : 0;
+        ch.full = ch.nvalid == 4;
+        if (ch.full) {
+            ch.e1 = sbuf[(cst * NV + 0) * kShearThreads + tid];
+            ch.e2 = sbuf[(cst * NV + 1) * kShearThreads + tid];
+            if (HAS_B) ch.b = sbuf[(cst * NV + 2) * kShearThreads + tid];
+        } else {
+            ch.e1 = ch.e2 = ch.b = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        if (!HAS_B) ch.b = make_float4(0.f, 0.f, 0.f, 0.f);
+        eval_chunk<FAMILY, HAS_B>(c, ch, L);
+        cst = cst + 1 == kStages ? 0 : cst + 1;
+        if (++cc == cpg) {
+            cc = 0;
+            finish_galaxy(L, gmask, sub, av, a1, a2, aq);
+            lse_reset(L);
+        }
+    }
+    cp_async_wait<0>();
+    block_partials(s, av, a1, a2, aq);
 }
 
 __global__ void __launch_bounds__(256) shear_finalize_kernel(const double *partials, int n_part,
@@ -327,7 +443,7 @@ template <int FAMILY, bool HAS_B>
 cudaError_t launch_fb(const ShearLaunch &s, int grid, bool vec, cudaStream_t st)
 {
     if (vec)
-        shear_kernel<FAMILY, HAS_B, true><<<grid, kShearThreads, 0, st>>>(s);
+        shear_kernel_async<FAMILY, HAS_B><<<grid, kShearThreads, async_smem_bytes(HAS_B), st>>>(s);
     else
         shear_kernel<FAMILY, HAS_B, false><<<grid, kShearThreads, 0, st>>>(s);
     return cudaGetLastError();
@@ -340,8 +456,8 @@ int shear_grid_blocks()
     int dev = 0, sms = 0, nb = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, shear_kernel<BS_EPRIOR_BA14, false, true>,
-                                                  kShearThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, shear_kernel_async<BS_EPRIOR_BA14, false>, kShearThreads,
+                                                  async_smem_bytes(false));
     if (sms <= 0) sms = 1;
     if (nb <= 0) nb = 1;
     return sms * nb;

@@ -65,7 +65,8 @@ def test_struct_layouts_match_header(tmp_path):
     structs = {"bs_fit_args": _ffi.FitArgs, "bs_fit_out": _ffi.FitOut, "bs_shear_data": _ffi.ShearData,
                "bs_estimate_cfg": _ffi.EstimateCfg, "bs_serve_cfg": _ffi.ServeCfg,
                "bs_serve_request": _ffi.ServeRequest, "bs_serve_completion": _ffi.ServeCompletion,
-               "bs_serve_stats": _ffi.ServeStats, "bs_psf": _ffi.Psf, "bs_prior": _ffi.Prior}
+               "bs_serve_stats": _ffi.ServeStats, "bs_psf": _ffi.Psf, "bs_prior": _ffi.Prior,
+               "bs_fit_plan_launch_info": _ffi.PlanLaunchInfo}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "bpshear.h"', "int main(void) {"]
     for cn, py in structs.items():
         lines.append(f'printf("{cn} size %zu\\n", sizeof({cn}));')

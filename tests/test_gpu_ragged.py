@@ -67,3 +67,34 @@ def test_ragged_plan_coupled_to_oracle(cuda):
                 mcse = y.std() / np.sqrt(O.ess(y[None, :]))
                 worst = max(worst, abs(x.mean() - y.mean()) / mcse)
     assert worst <= 1e-3, worst
+
+
+def test_autotuned_plan_matches_untuned(cuda):
+    """The autotuner only picks the register budget of each class launch: the
+    chains must be bit-identical to the untuned plan's, and every class must
+    report a budget and its two trial times."""
+    truth = synth.draw_ragged(64, seed=33)
+    truth.side = np.array([SIDES[i % len(SIDES)] for i in range(64)], dtype=np.int32)
+    ds = datagen.make_dataset(truth, 2)
+    flat, offs, sides = datagen.pack(ds, np.float32)
+    t = lambda a, dt=np.float32: torch.from_numpy(np.ascontiguousarray(a, dtype=dt)).to(cuda)
+    psf = api.psf_table("moffat", truth.psf_fwhm.astype(np.float32), 3.0, device=cuda)
+    cfg = api.FitConfig(n_chains=2, n_warmup=30, n_samples=20, n_leapfrog=8, seed=3)
+    args = (t(flat), t(offs, np.int64), t(sides, np.int32), psf, t(np.ones(64)), t(ds.init))
+    want = ("accepted", "step_size", "n_grad", "status")
+    tuned = api.RaggedFitPlan(*args, cfg, capture=True, autotune=True, want=want)
+    plain = api.RaggedFitPlan(*args, cfg, capture=False, autotune=False, want=want)
+    tuned.run()
+    plain.run()
+    torch.cuda.synchronize()
+    a, b = tuned.result(), plain.result()
+    for k in ("samples", "accepted", "step_size", "n_grad", "status"):
+        assert torch.equal(a[k], b[k]), k
+    info = tuned.info()
+    assert sorted(i["slot_class"] for i in info) == [1, 2, 3, 4]
+    for i in info:
+        assert i["registers"] in (80, 128)
+        assert i["trial_ms_128"] > 0 and i["trial_ms_80"] > 0
+        chosen = i["trial_ms_128"] if i["registers"] == 128 else i["trial_ms_80"]
+        assert chosen <= min(i["trial_ms_128"], i["trial_ms_80"])
+    assert all(i["trial_ms_128"] == 0 and i["registers"] == 128 for i in plain.info())
