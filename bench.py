@@ -66,7 +66,8 @@ def workload_config(a):
              "then posterior-mean shear (alpha fixed, truncated-Gaussian sigma 0.2)")
     if a.workload == "plain":
         desc = (f"plain batched: {a.n_gal} exponential galaxies, {a.side}x{a.side} FP32 stamps, pixel 0.2\", "
-                f"Gaussian PSF FWHM 0.7\", S/N U(15,50), g=(0.02,0), {chain}")
+                f"Gaussian PSF FWHM 0.7\", S/N U(15,50), g=(0.02,0), one fixed-size launch (register budget "
+                f"autotuned), {chain}")
     else:
         desc = (f"batching: {a.n_gal} exponential galaxies, stamp side 2ceil(4.43hlr/p+1.5FWHM/p)+1 in [25,101] "
                 f"(uneven), per-galaxy Moffat beta=3 PSF FWHM U(0.6\",0.9\"), S/N log-U(10,100), FP32 with FP64 "
@@ -311,8 +312,9 @@ def our_arm(a, world, rank, local_rank):
         plan = api.RaggedFitPlan(inp["data"], inp["offsets"], inp["side"], inp["psf"], inp["sigma"], inp["init"],
                                  cfg, capture=True, autotune=True)
     else:
-        plan = api.FitPlan(inp["data"], inp["offsets"], inp["side"], inp["psf"], inp["sigma"], inp["init"], cfg,
-                           max_side=a.side)
+        # one size class: a single persistent launch, register budget autotuned
+        plan = api.RaggedFitPlan(inp["data"], inp["offsets"], inp["side"], inp["psf"], inp["sigma"], inp["init"],
+                                 cfg, capture=True, autotune=True, max_side=a.side)
     K = a.chains * a.n_samples
     shear = api.ShearPlan(plan.samples[2].reshape(a.n_gal, K), plan.samples[3].reshape(a.n_gal, K),
                           family=1, trunc_r=0.7)
@@ -394,12 +396,12 @@ def our_arm(a, world, rank, local_rank):
                         "traffic": captured_traffic("fit", a.n_gal) if a.workload == "plain" else None,
                         "traffic_note": "DRAM read+write per launch, scaled from a 1,216-galaxy ncu capture "
                                         "of the same kernel source by the galaxies per launch",
-                        "kernel": "fit_kernel<2,2>" if a.workload == "plain" else "fit_kernel<1..4,2> (graph)",
+                        "kernel": ", ".join(f"fit_kernel_r{i['registers']}<{i['slot_class']}>" for i in plan.info()),
                         "peak_how": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
                                     f"{sm_max:.0f} MHz (max SM clock)",
                         "flops_per_launch": fit_flops, "evals_per_launch": n_grad,
                         "fit_ms": float(np.mean(fit_ms))},
-           "gpu_launches": int(a.steps * (1 if a.workload == "plain" else len(np.unique((sides + 31) // 32)))
+           "gpu_launches": int(a.steps * len(plan.info())
                                + 2 * sum(est_evals)),
            "clocks": clk,
            "ess": {"mean_per_galaxy": float(ess_gal.mean().item()),
@@ -413,8 +415,7 @@ def our_arm(a, world, rank, local_rank):
            "paper_context": "0.45 s/galaxy to 300 ESS on one A100 with NUTS (63x63 stamps), i.e. 2.2 galaxies/s",
            "wall_s": wall}
 
-    if a.workload == "ragged":
-        out["plan"] = plan.info()
+    out["plan"] = plan.info()
     if not a.no_e2e:
         out["e2e"] = e2e_run(a, world, inp, plan, shear, step, barrier, dev)
     if a.workload == "plain" and a.serve_requests > 0 and world == 1:
@@ -582,7 +583,16 @@ def serving_pool(a, dev, n_pool):
     b.workload, b.n_gal = "ragged", n_pool
     inp = make_inputs_gpu(b, 0, dev)
     t = inp["truth"]
-    return {"stamps": np.ascontiguousarray(inp["data"].cpu().numpy(), dtype=np.float32),
+    # register budget per slot class, tuned once on the pool (both paths use it)
+    from paper_2604_22048_gb300 import api
+    cfg = api.FitConfig(n_chains=a.chains, n_warmup=a.n_warmup, n_samples=a.n_samples, n_leapfrog=a.leapfrog)
+    tuner = api.RaggedFitPlan(inp["data"], inp["offsets"], inp["side"], inp["psf"], inp["sigma"], inp["init"], cfg,
+                              capture=False, autotune=True, want=("status",))
+    regs = [0, 0, 0, 0]
+    for i in tuner.info():
+        regs[i["slot_class"] - 1] = i["registers"]
+    del tuner
+    return {"registers": regs, "stamps": np.ascontiguousarray(inp["data"].cpu().numpy(), dtype=np.float32),
             "offsets": inp["offsets"].cpu().numpy(), "sides": t.side.astype(np.int32),
             "fwhm": t.psf_fwhm.astype(np.float32),
             "init": np.ascontiguousarray(inp["init"].cpu().numpy(), dtype=np.float32)}
@@ -609,7 +619,7 @@ def run_served(a, pool, n_req, rate, ess_every=64):
     import torch
     from paper_2604_22048_gb300 import api
     cfg = api.FitConfig(n_chains=a.chains, n_warmup=a.n_warmup, n_samples=a.n_samples, n_leapfrog=a.leapfrog)
-    srv = api.Server(cfg, max_side=101, arena_bytes=512 << 20)
+    srv = api.Server(cfg, max_side=101, arena_bytes=512 << 20, registers=pool["registers"])
     P = len(pool["sides"])
     item = np.arange(n_req) % P
     reqs = api.Server.requests(pool["stamps"], pool["offsets"][item], pool["sides"][item], "moffat",
@@ -674,7 +684,7 @@ class PlainPerSize:
     def plan(self, N):
         if N not in self.plans:
             torch, api = self.torch, self.api
-            B = api.resident_galaxies(self.a.chains, N)
+            B = api.resident_galaxies(self.a.chains, N, self.pool["registers"][(N + 31) // 32 - 1])
             d = self.dev
             data = torch.zeros(B * N * N, dtype=torch.float32, device=d)
             offs = torch.arange(B, dtype=torch.int64, device=d) * (N * N)
@@ -685,7 +695,7 @@ class PlainPerSize:
             init = torch.zeros((B, self.a.chains, 6), dtype=torch.float32, device=d)
             gid = torch.zeros(B, dtype=torch.int64, device=d)
             p = api.FitPlan(data, offs, side, (psf_t, B), sigma, init, self.cfg, gal_id=gid, max_side=N,
-                            want=("status",))
+                            registers=self.pool["registers"][(N + 31) // 32 - 1], want=("status",))
             host = {"data": torch.empty(B * N * N, dtype=torch.float32).pin_memory(),
                     "psf": torch.empty(psf_t.numel(), dtype=torch.uint8).pin_memory(),
                     "init": torch.empty((B, self.a.chains, 6), dtype=torch.float32).pin_memory(),
@@ -779,7 +789,7 @@ def serve_compare(a, dev, n_req, n_pool):
     run_served(a, pool, min(n_req, 20000), None)          # warm-up
     sat_served = run_served(a, pool, n_req, None)
     lam = sat_plain["galaxies_per_s"]
-    res = {"requests": n_req, "distinct_stamps": n_pool,
+    res = {"requests": n_req, "distinct_stamps": n_pool, "registers_by_slot_class": pool["registers"],
            "plain_saturated": sat_plain, "served_saturated": sat_served}
     for f in (0.8, 1.2):
         res[f"plain_at_{f}x"] = plain.run(n_req, f * lam)

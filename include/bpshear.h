@@ -148,6 +148,9 @@ typedef struct {
                                      (resuming an adapted chain) */
     const float *init_inv_mass;   /* device [n_gal][n_chains][6] or NULL
                                      (= identity metric) */
+    int32_t registers;            /* register cap of the fit kernel: 128, 96
+                                     (up to 4 chains) or 80; 0 = 128.  Results
+                                     do not depend on it, only the speed. */
 } bs_fit_args;
 
 /* Outputs, caller-allocated device buffers (NULL = not wanted, except
@@ -195,12 +198,14 @@ bs_status bs_fit_galaxies(const bs_fit_args *args, const bs_fit_out *out,
  *                     branches of a CUDA graph that bs_fit_plan_launch
  *                     replays (one graph launch per batch); otherwise they
  *                     are issued one after another;
- *   BS_PLAN_AUTOTUNE: per class, the kernel's register budget (128 registers,
- *                     4 CTAs = 16 warps per SM; or 80 registers, more
- *                     resident warps, some spills) is chosen by timing both on
- *                     the class's first galaxies at creation (their outputs
- *                     are overwritten by every later launch); the results
- *                     are the same either way.
+ *   BS_PLAN_AUTOTUNE: per class, the kernel's register cap (128: 4 CTAs =
+ *                     16 warps of 4-chain galaxies per SM; 96: 5 CTAs, for
+ *                     up to 4 chains; 80: 6 CTAs; the smaller caps spill a
+ *                     little; as far as shared memory allows) is chosen by
+ *                     timing them on the class's
+ *                     first galaxies at creation (their outputs are
+ *                     overwritten by every later launch); the results are
+ *                     the same whichever is chosen.
  *   side_host: host copy of args->side (n_gal).
  *   workspace: bs_fit_plan_workspace_bytes(args) bytes of device memory
  *              (work lists and per-class counters), owned by the caller.
@@ -225,16 +230,17 @@ typedef struct {
     int32_t max_side;        /* largest stamp of the class */
     int32_t n_gal;           /* galaxies in the class */
     int32_t grid;            /* persistent CTAs */
-    int32_t registers;       /* register budget of the kernel instance: 128 or 80 */
-    float trial_ms_128, trial_ms_80;  /* autotune trial times (0 if not tuned) */
+    int32_t registers;       /* register cap of the kernel instance: 128, 96 or 80 */
+    float trial_ms_128, trial_ms_96, trial_ms_80;  /* autotune trial times (0 if not tuned) */
 } bs_fit_plan_launch_info;
 int32_t bs_fit_plan_num_launches(bs_fit_plan plan);
 bs_status bs_fit_plan_info(bs_fit_plan plan, int32_t i, bs_fit_plan_launch_info *info);
 
 /* Galaxies of side max_side (n_chains chains each) that the current device
- * holds at once in one fit launch (SMs x resident CTAs): the batch size of a
+ * holds at once in one fit launch with the given register cap (as
+ * bs_fit_args.registers; 0 = 128): SMs x resident CTAs, the batch size of a
  * launch that fills the GPU exactly once.  Returns 0 for invalid arguments. */
-int32_t bs_fit_resident_galaxies(int32_t n_chains, int32_t max_side);
+int32_t bs_fit_resident_galaxies(int32_t n_chains, int32_t max_side, int32_t registers);
 
 /* ------------------------------------------------------------------------ */
 /* Serving: fit requests admitted while others run (continuous batching)     */
@@ -272,6 +278,10 @@ typedef struct {
                                 (0: 500 us); requests are admitted at once
                                 while fewer than the GPU holds are running */
     int32_t n_streams;       /* launch streams (0: 96; 4..128) */
+    int32_t registers[4];    /* register cap of the fit kernel per 32-column slot
+                                class (stamps up to 31, 63, 95, 127 px): 128,
+                                96 or 80, e.g. as a bs_fit_plan autotune chose
+                                them; 0 = 128.  Results do not depend on it. */
 } bs_serve_cfg;
 
 typedef struct {

@@ -52,7 +52,8 @@ class FitArgs(C.Structure):
                 ("prior", Prior), ("n_chains", C.c_int32), ("n_warmup", C.c_int32),
                 ("n_samples", C.c_int32), ("n_leapfrog", C.c_int32), ("target_accept", C.c_float),
                 ("jitter", C.c_float), ("adapt_mass", C.c_int32), ("random_steps", C.c_int32),
-                ("seed", C.c_uint64), ("init_step_size", C.c_void_p), ("init_inv_mass", C.c_void_p)]
+                ("seed", C.c_uint64), ("init_step_size", C.c_void_p), ("init_inv_mass", C.c_void_p),
+                ("registers", C.c_int32)]
 
 
 class FitOut(C.Structure):
@@ -80,7 +81,8 @@ BS_PLAN_CAPTURE, BS_PLAN_AUTOTUNE = 1, 2
 
 class PlanLaunchInfo(C.Structure):
     _fields_ = [("slot_class", C.c_int32), ("max_side", C.c_int32), ("n_gal", C.c_int32), ("grid", C.c_int32),
-                ("registers", C.c_int32), ("trial_ms_128", C.c_float), ("trial_ms_80", C.c_float)]
+                ("registers", C.c_int32), ("trial_ms_128", C.c_float), ("trial_ms_96", C.c_float),
+                ("trial_ms_80", C.c_float)]
 
 
 class ServeCfg(C.Structure):
@@ -88,7 +90,7 @@ class ServeCfg(C.Structure):
                 ("n_warmup", C.c_int32), ("n_samples", C.c_int32), ("n_leapfrog", C.c_int32),
                 ("target_accept", C.c_float), ("jitter", C.c_float), ("adapt_mass", C.c_int32),
                 ("random_steps", C.c_int32), ("seed", C.c_uint64), ("max_inflight", C.c_int32),
-                ("batch_us", C.c_int32), ("n_streams", C.c_int32)]
+                ("batch_us", C.c_int32), ("n_streams", C.c_int32), ("registers", C.c_int32 * 4)]
 
 
 class ServeRequest(C.Structure):
@@ -168,7 +170,7 @@ def lib():
     L.bs_fit_plan_num_launches.argtypes = [vp]
     L.bs_fit_plan_num_launches.restype = i32
     L.bs_fit_plan_info.argtypes = [vp, i32, C.POINTER(PlanLaunchInfo)]
-    L.bs_fit_resident_galaxies.argtypes = [i32, i32]
+    L.bs_fit_resident_galaxies.argtypes = [i32, i32, i32]
     L.bs_fit_resident_galaxies.restype = i32
     L.bs_serve_request_bytes.argtypes = [C.POINTER(ServeCfg), i32]
     L.bs_serve_request_bytes.restype = sz

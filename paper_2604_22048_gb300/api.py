@@ -98,10 +98,11 @@ class FitPlan:
     launch, so that repeated fits (benchmark steps) allocate nothing."""
 
     def __init__(self, data, offsets, side, psf, noise_sigma, init, cfg: FitConfig, *, gal_id=None,
-                 max_side=None, init_step_size=None, init_inv_mass=None,
+                 max_side=None, init_step_size=None, init_inv_mass=None, registers=0,
                  want=("logp", "accept_rate", "step_size", "inv_mass", "n_div", "status", "n_grad")):
         """init_step_size [n_gal, C] / init_inv_mass [n_gal, C, 6] (optional):
-        resume adapted chains (no initial step-size search)."""
+        resume adapted chains (no initial step-size search).  registers: the
+        fit kernel's register cap (128, 96, 80; 0 = 128), speed only."""
         _need_cuda(data, offsets, side, noise_sigma, init, gal_id, init_step_size, init_inv_mass)
         dev = data.device
         n_gal, n_chains = init.shape[0], init.shape[1]
@@ -134,6 +135,7 @@ class FitPlan:
         a.seed = cfg.seed
         a.init_step_size = _p(init_step_size)
         a.init_inv_mass = _p(init_inv_mass)
+        a.registers = int(registers)
         self.args = a
         S, Cn = cfg.n_samples, cfg.n_chains
         f32 = dict(dtype=torch.float32, device=dev)
@@ -222,7 +224,9 @@ class Server:
     to pinned host memory.  The arena is a torch uint8 tensor owned here."""
 
     def __init__(self, cfg: FitConfig, *, max_side=101, arena_bytes=256 << 20, max_inflight=0, batch_us=0,
-                 n_streams=0, device="cuda"):
+                 n_streams=0, registers=(0, 0, 0, 0), device="cuda"):
+        """registers: fit-kernel register cap per slot class (e.g. from a
+        RaggedFitPlan(autotune=True).info()); 0 = 128."""
         self.cfg = cfg
         self.arena = torch.empty(int(arena_bytes), dtype=torch.uint8, device=device)
         c = F.ServeCfg()
@@ -233,6 +237,8 @@ class Server:
         c.target_accept, c.jitter = cfg.target_accept, cfg.jitter
         c.adapt_mass, c.random_steps, c.seed = int(cfg.adapt_mass), int(cfg.random_steps), cfg.seed
         c.max_inflight, c.batch_us, c.n_streams = max_inflight, batch_us, n_streams
+        for i, r in enumerate(registers):
+            c.registers[i] = int(r)
         self.scfg = c
         torch.cuda.synchronize(self.arena.device)
         h = C.c_void_p()
@@ -319,9 +325,10 @@ class Server:
             pass
 
 
-def resident_galaxies(n_chains, max_side):
-    """Galaxies of side max_side one fit launch holds at once on the current GPU."""
-    return int(F.lib().bs_fit_resident_galaxies(n_chains, max_side))
+def resident_galaxies(n_chains, max_side, registers=0):
+    """Galaxies of side max_side one fit launch holds at once on the current GPU
+    with the given register cap (0 = 128)."""
+    return int(F.lib().bs_fit_resident_galaxies(n_chains, max_side, int(registers)))
 
 
 def fit_galaxies(data, offsets, side, psf, noise_sigma, init, cfg: FitConfig | None = None, **kw):

@@ -204,6 +204,9 @@ bs_status fit_params_from_args(const bs_fit_args *a, const bs_fit_out *o, FitPar
     if (!(a->target_accept > 0.f && a->target_accept < 1.f))
         return fail(BS_ERR_INVALID_ARG, "%s: target_accept", who);
     if (!(a->jitter >= 0.f && a->jitter < 1.f)) return fail(BS_ERR_INVALID_ARG, "%s: jitter", who);
+    if (a->registers != 0 && a->registers != 128 && a->registers != 96 && a->registers != 80)
+        return fail(BS_ERR_INVALID_ARG, "%s: registers must be 0, 128, 96 or 80", who);
+    p.regs = a->registers;
     p.n_chains = a->n_chains;
     p.n_warmup = a->n_warmup;
     p.n_samples = a->n_samples;
@@ -254,20 +257,21 @@ bs_status bs_fit_galaxies(const bs_fit_args *a, const bs_fit_out *o, void *works
     int dev = 0, sms = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int per_sm = bs::fit_blocks_per_sm(a->n_chains, a->max_side);
+    const int per_sm = bs::fit_blocks_per_sm(a->n_chains, a->max_side, p.regs);
     long long grid = (long long)sms * per_sm;
     if (grid > a->n_gal) grid = a->n_gal;
     e = bs::launch_fit(p, (int)grid, s);
     return e == cudaSuccess ? BS_OK : cuda_fail(e, "bs_fit_galaxies: launch");
 }
 
-int32_t bs_fit_resident_galaxies(int32_t n_chains, int32_t max_side)
+int32_t bs_fit_resident_galaxies(int32_t n_chains, int32_t max_side, int32_t registers)
 {
     if (n_chains < 1 || n_chains > bs::kMaxChains || !odd_side_ok(max_side)) return 0;
+    if (registers != 0 && registers != 128 && registers != 96 && registers != 80) return 0;
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-    return sms * bs::fit_blocks_per_sm(n_chains, max_side);
+    return sms * bs::fit_blocks_per_sm(n_chains, max_side, registers);
 }
 
 bs_status bs_logpost_points(const bs_fit_args *a, int32_t n_points, const int32_t *gal_index,

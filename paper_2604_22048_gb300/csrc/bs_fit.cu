@@ -302,12 +302,12 @@ struct SlotConst {
 // Model-data terms of one row u for all column slots of this lane.
 template <int NCT, bool LL>
 __device__ __forceinline__ void row_terms(Sums<NCT> &S, const SlotConst<NCT> &K,
-                                          const float *__restrict__ row, float kx, float kx2, float akx2,
+                                          const float *__restrict__ row, float kx, float kx2, float al,
                                           float Xr, float Xi, float F2)
 {
     constexpr int NPAIR = NCT / 2;
     const int lane = threadIdx.x & 31;
-    const float2 kxv = f2(kx), kx2v = f2(kx2), akv = f2(akx2), Xrv = f2(Xr), Xiv = f2(Xi);
+    const float2 kxv = f2(kx), kx2v = f2(kx2), alv = f2(al), Xrv = f2(Xr), Xiv = f2(Xi);
     const float2 nF2v = f2(-F2);
 #pragma unroll
     for (int p = 0; p < NPAIR; ++p) {
@@ -315,7 +315,7 @@ __device__ __forceinline__ void row_terms(Sums<NCT> &S, const SlotConst<NCT> &K,
         const float2 Dx = *reinterpret_cast<const float2 *>(b);
         const float2 Dy = *reinterpret_cast<const float2 *>(b + 64);
         const float2 T = *reinterpret_cast<const float2 *>(b + 128);
-        const float2 s = fma2(K.gky[p], kxv, add2(akv, K.cst[p]));     // 1 + r0^2 q(k)
+        const float2 s = fma2(fma2(alv, kxv, K.gky[p]), kxv, K.cst[p]);   // 1 + r0^2 q(k), Horner in kx
         const float2 rs = make_float2(rsqrt_ge1(s.x), rsqrt_ge1(s.y));
         const float2 rs2 = mul2(rs, rs);
         const float2 A = mul2(mul2(T, rs2), rs);                        // |M| / F
@@ -342,7 +342,7 @@ __device__ __forceinline__ void row_terms(Sums<NCT> &S, const SlotConst<NCT> &K,
         const float *b = row + NPAIR * 192;
         const float2 D = *reinterpret_cast<const float2 *>(b + 2 * lane);
         const float T = b[64 + lane];
-        const float s = fmaf(K.sgky, kx, akx2 + K.scst);
+        const float s = fmaf(fmaf(al, kx, K.sgky), kx, K.scst);
         const float rs = rsqrt_ge1(s);
         const float rs2 = rs * rs;
         const float A = T * rs2 * rs;
@@ -382,8 +382,8 @@ __device__ __forceinline__ void half_plane(Sums<NCT> &S, const SlotConst<NCT> &K
     for (; u + 1 < H; u += 2) {
         const float4 k01 = *reinterpret_cast<const float4 *>(kxr + u);   // (kx, kx^2) of rows u, u+1
         const float X1r = Xr * exr - Xi * exi, X1i = Xr * exi + Xi * exr;
-        row_terms<NCT, LL>(S, K, row, k01.x, k01.y, al * k01.y, Xr, Xi, F2);
-        row_terms<NCT, LL>(S, K, row + ROWF, k01.z, k01.w, al * k01.w, X1r, X1i, F2);
+        row_terms<NCT, LL>(S, K, row, k01.x, k01.y, al, Xr, Xi, F2);
+        row_terms<NCT, LL>(S, K, row + ROWF, k01.z, k01.w, al, X1r, X1i, F2);
         const float nXr = Xr * e2r - Xi * e2i;
         Xi = Xr * e2i + Xi * e2r;
         Xr = nXr;
@@ -391,7 +391,7 @@ __device__ __forceinline__ void half_plane(Sums<NCT> &S, const SlotConst<NCT> &K
     }
     if (u < H) {
         const float2 k0 = kxr[u];
-        row_terms<NCT, LL>(S, K, row, k0.x, k0.y, al * k0.y, Xr, Xi, F2);
+        row_terms<NCT, LL>(S, K, row, k0.x, k0.y, al, Xr, Xi, F2);
     }
 }
 
@@ -798,11 +798,9 @@ __device__ void publish_galaxy(const FitParams &P, int gal)
     }
 }
 
-// MINB bounds the registers so that MINB CTAs of 256 threads fit an SM
-// (2: <= 128 registers, no spills; 3: <= 85, a few spills outside the
-// half-plane loop), i.e. 4 or 6 CTAs of 4 chains.
-template <int NC, int MINB>
-__global__ void __launch_bounds__(256, MINB) fit_kernel(const FitParams P)
+// The persistent fit loop of one CTA (all threads).
+template <int NC>
+__device__ __forceinline__ void fit_loop(const FitParams &P)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_gal;
@@ -838,6 +836,17 @@ __global__ void __launch_bounds__(256, MINB) fit_kernel(const FitParams P)
         if (P.done) publish_galaxy(P, gal);
     }
 }
+
+// Register budgets of the kernel instances (the launch bounds give ptxas the
+// occupancy target): 128 registers, 4 CTAs of 4 chains per SM, no spills;
+// at most 102 (5 CTAs; blocks of up to 4 chains only); at most 85 (6 CTAs,
+// a few spills outside the half-plane loop).
+template <int NC>
+__global__ void __launch_bounds__(256, 2) fit_kernel_r128(const FitParams P) { fit_loop<NC>(P); }
+template <int NC>
+__global__ void __launch_bounds__(128, 5) fit_kernel_r96(const FitParams P) { fit_loop<NC>(P); }
+template <int NC>
+__global__ void __launch_bounds__(256, 3) fit_kernel_r80(const FitParams P) { fit_loop<NC>(P); }
 
 // One CTA of 32 threads per point: stage the galaxy, then evaluate.
 template <int NC>
@@ -895,28 +904,31 @@ __global__ void __launch_bounds__(32) logpost_points_kernel(const FitParams P, i
 // stamp; smaller stamps of the same launch see zero-padded columns.
 using FitKernel = void (*)(const FitParams);
 
-template <int MINB>
-FitKernel fit_kernel_nc(int max_side)
-{
-    switch ((max_side + 31) / 32) {
-        case 1: return fit_kernel<1, MINB>;
-        case 2: return fit_kernel<2, MINB>;
-        case 3: return fit_kernel<3, MINB>;
-        default: return fit_kernel<4, MINB>;
+#define BS_FIT_NC_SWITCH(KERNEL)                 \
+    switch ((max_side + 31) / 32) {              \
+        case 1: return KERNEL<1>;                \
+        case 2: return KERNEL<2>;                \
+        case 3: return KERNEL<3>;                \
+        default: return KERNEL<4>;               \
     }
-}
 
-// Register budget of a launch: minb 3 selects the 85-register build, 2 the
-// 128-register one; 0 takes the process default (BS_FIT_MINB, else 2).
-FitKernel fit_kernel_for(int max_side, int minb)
+// Register budget of a launch (128, 96 or 80; 96 only for blocks of up to 4
+// chains); 0 takes the process default (BS_FIT_REGS, else 128).
+FitKernel fit_kernel_for(int max_side, int regs, int n_chains)
 {
     static const int dflt = [] {
-        const char *s = getenv("BS_FIT_MINB");
-        return (s && s[0] == '3') ? 3 : 2;
+        const char *s = getenv("BS_FIT_REGS");
+        const int r = s ? atoi(s) : 128;
+        return (r == 96 || r == 80) ? r : 128;
     }();
-    if (minb != 2 && minb != 3) minb = dflt;
-    return minb == 3 ? fit_kernel_nc<3>(max_side) : fit_kernel_nc<2>(max_side);
+    if (regs != 128 && regs != 96 && regs != 80) regs = dflt;
+    if (regs == 96 && n_chains > 4) regs = 128;
+    if (regs == 80) BS_FIT_NC_SWITCH(fit_kernel_r80)
+    if (regs == 96) BS_FIT_NC_SWITCH(fit_kernel_r96)
+    BS_FIT_NC_SWITCH(fit_kernel_r128)
 }
+
+#undef BS_FIT_NC_SWITCH
 
 }  // namespace
 
@@ -928,11 +940,11 @@ size_t fit_smem_bytes(int max_side)
            (size_t)(h + 1) * sizeof(float2);
 }
 
-int fit_blocks_per_sm(int n_chains, int max_side, int minb)
+int fit_blocks_per_sm(int n_chains, int max_side, int regs)
 {
     int nb = 0;
     const size_t smem = fit_smem_bytes(max_side);
-    FitKernel k = fit_kernel_for(max_side, minb);
+    FitKernel k = fit_kernel_for(max_side, regs, n_chains);
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, 32 * n_chains, smem) != cudaSuccess)
         return 1;
@@ -942,7 +954,7 @@ int fit_blocks_per_sm(int n_chains, int max_side, int minb)
 cudaError_t launch_fit(const FitParams &p, int grid, cudaStream_t stream)
 {
     const size_t smem = fit_smem_bytes(p.max_side);
-    FitKernel k = fit_kernel_for(p.max_side, p.minb);
+    FitKernel k = fit_kernel_for(p.max_side, p.regs, p.n_chains);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k<<<grid, 32 * p.n_chains, smem, stream>>>(p);

@@ -54,8 +54,8 @@ struct FitParams {
     unsigned int *queue;
     int max_side;
     int h_max, npad;   // shared-memory geometry for max_side
-    int minb;          // register budget: CTAs of 256 threads per SM the kernel
-                       // instance is built for (2 or 3; 0 = default)
+    int regs;          // register cap of the kernel instance (128, 96 or 80;
+                       // 0 = default)
     // serving: when `done` is set (host-mapped), each CTA copies its galaxy's
     // outputs to (address + pub_shift) -- the pinned mirror of the output
     // arrays -- then sets done[gal] = 1 with a system-scope fence before it
@@ -67,7 +67,7 @@ struct FitParams {
 size_t fit_smem_bytes(int max_side);
 // Launch helpers implemented in the .cu files.
 cudaError_t launch_fit(const FitParams &p, int grid, cudaStream_t stream);
-int fit_blocks_per_sm(int n_chains, int max_side, int minb = 0);
+int fit_blocks_per_sm(int n_chains, int max_side, int regs = 0);
 // Validate a fit request and fill every launch parameter except the
 // scheduling fields (work list, counter) and the serving fields.
 bs_status fit_params_from_args(const bs_fit_args *a, const bs_fit_out *o, FitParams &p, const char *who);

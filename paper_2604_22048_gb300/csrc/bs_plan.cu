@@ -6,12 +6,12 @@
 // class (longest-processing-time order for the persistent CTAs' work queue).
 // Each class gets its own persistent launch, sized for the largest stamp of
 // the class: shared memory, grid, and the kernel instance (column slots per
-// lane, register budget).  With BS_PLAN_AUTOTUNE the register budget of each
-// class -- 128 registers and 4 CTAs (16 warps) per SM, or 80 registers and
-// up to 6 CTAs (24 warps) -- is chosen by timing both instances on the
-// class's first galaxies (two waves of the larger grid, the second of two runs
-// timed); both instances do the same arithmetic, so the choice changes only
-// the speed.  With BS_PLAN_CAPTURE the class launches are recorded once as
+// lane, register budget).  With BS_PLAN_AUTOTUNE the register cap of each
+// class -- 128 (4 CTAs = 16 warps of 4-chain galaxies per SM), 96 (5 CTAs) or
+// 80 (6 CTAs, some spills), as far as shared memory allows -- is chosen by
+// timing the three instances on the class's first galaxies (two waves of the
+// largest grid, the second of two runs timed); the instances do the same
+// arithmetic, so the choice changes only the speed.  With BS_PLAN_CAPTURE the class launches are recorded once as
 // parallel branches of a CUDA graph (fork/join on the plan's streams); the
 // graph is replayed by bs_fit_plan_launch on any stream.
 #include <algorithm>
@@ -27,7 +27,7 @@ struct bs_fit_plan_s {
         int grid;
         unsigned int *queue;
         int slot_class;
-        float trial_ms[2];   // autotune: time of the 128- and 80-register instance (0 = not timed)
+        float trial_ms[3];   // autotune: time of the 128-, 96- and 80-register instance (0 = not timed)
     };
     std::vector<Launch> launches;
     cudaStream_t streams[4] = {};
@@ -72,16 +72,16 @@ bs_status enqueue(bs_fit_plan_s *pl, cudaStream_t s0, bool forked)
     return BS_OK;
 }
 
-// Time one launch of L on its first n_trial galaxies with register budget
-// minb (a private stream; outputs of those galaxies are overwritten by the
-// plan's own launches later).
-cudaError_t time_variant(const bs_fit_plan_s::Launch &L, int minb, int n_trial, int sms, cudaStream_t st,
+// Time one launch of L on its first n_trial galaxies with register cap regs
+// (a private stream; outputs of those galaxies are overwritten by the plan's
+// own launches later).
+cudaError_t time_variant(const bs_fit_plan_s::Launch &L, int regs, int n_trial, int sms, cudaStream_t st,
                          cudaEvent_t e0, cudaEvent_t e1, float &ms)
 {
     bs::FitParams p = L.p;
-    p.minb = minb;
+    p.regs = regs;
     p.n_work = n_trial;
-    const int per_sm = bs::fit_blocks_per_sm(p.n_chains, p.max_side, minb);
+    const int per_sm = bs::fit_blocks_per_sm(p.n_chains, p.max_side, regs);
     const int grid = std::min(n_trial, sms * per_sm);
     cudaError_t e = cudaSuccess;
     for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
@@ -95,6 +95,8 @@ cudaError_t time_variant(const bs_fit_plan_s::Launch &L, int minb, int n_trial, 
     return e;
 }
 
+constexpr int kRegVariants[3] = {128, 96, 80};
+
 cudaError_t autotune(bs_fit_plan_s *pl, int sms)
 {
     cudaStream_t st = nullptr;
@@ -104,23 +106,23 @@ cudaError_t autotune(bs_fit_plan_s *pl, int sms)
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     for (auto &L : pl->launches) {
         if (e != cudaSuccess) break;
-        const int waves = std::max(bs::fit_blocks_per_sm(L.p.n_chains, L.p.max_side, 2),
-                                   bs::fit_blocks_per_sm(L.p.n_chains, L.p.max_side, 3));
+        int waves = 1;
+        for (int r : kRegVariants) waves = std::max(waves, bs::fit_blocks_per_sm(L.p.n_chains, L.p.max_side, r));
         const int n_trial = std::min(L.p.n_work, 2 * sms * waves);
         float best = 0.f;
-        int best_minb = 2;
-        for (int v = 0; v < 2 && e == cudaSuccess; ++v) {
-            const int minb = v == 0 ? 2 : 3;
+        int best_regs = 128;
+        for (int v = 0; v < 3 && e == cudaSuccess; ++v) {
+            if (kRegVariants[v] == 96 && L.p.n_chains > 4) continue;   // that instance takes <= 128 threads
             float ms = 0.f;
-            e = time_variant(L, minb, n_trial, sms, st, e0, e1, ms);
+            e = time_variant(L, kRegVariants[v], n_trial, sms, st, e0, e1, ms);
             L.trial_ms[v] = ms;
             if (e == cudaSuccess && (v == 0 || ms < best)) {
                 best = ms;
-                best_minb = minb;
+                best_regs = kRegVariants[v];
             }
         }
-        L.p.minb = best_minb;
-        L.grid = std::min(L.p.n_work, sms * bs::fit_blocks_per_sm(L.p.n_chains, L.p.max_side, best_minb));
+        L.p.regs = best_regs;
+        L.grid = std::min(L.p.n_work, sms * bs::fit_blocks_per_sm(L.p.n_chains, L.p.max_side, best_regs));
     }
     if (st) cudaStreamDestroy(st);
     if (e0) cudaEventDestroy(e0);
@@ -208,8 +210,8 @@ bs_status bs_fit_plan_create(const bs_fit_args *a, const bs_fit_out *o, const in
         L.queue = reinterpret_cast<unsigned int *>(counters + kAlign * c);
         L.p.queue = L.queue;
         L.slot_class = c + 1;
-        L.trial_ms[0] = L.trial_ms[1] = 0.f;
-        const int per_sm = bs::fit_blocks_per_sm(a->n_chains, maxs[c], L.p.minb);
+        L.trial_ms[0] = L.trial_ms[1] = L.trial_ms[2] = 0.f;
+        const int per_sm = bs::fit_blocks_per_sm(a->n_chains, maxs[c], L.p.regs);
         L.grid = std::min(count[c], sms * per_sm);
         pl->launches.push_back(L);
         start += count[c];
@@ -235,7 +237,7 @@ bs_status bs_fit_plan_create(const bs_fit_args *a, const bs_fit_out *o, const in
             return bs::set_error(BS_ERR_CUDA, "bs_fit_plan_create: streams: %s", cudaGetErrorString(e));
         }
         // kernel attributes are set outside the capture
-        for (auto &L : pl->launches) bs::fit_blocks_per_sm(a->n_chains, L.p.max_side, L.p.minb);
+        for (auto &L : pl->launches) bs::fit_blocks_per_sm(a->n_chains, L.p.max_side, L.p.regs);
         e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
             st = enqueue(pl, cap, true);
@@ -278,9 +280,10 @@ bs_status bs_fit_plan_info(bs_fit_plan plan, int32_t i, bs_fit_plan_launch_info 
     info->max_side = L.p.max_side;
     info->n_gal = L.p.n_work;
     info->grid = L.grid;
-    info->registers = L.p.minb == 3 ? 80 : 128;
+    info->registers = L.p.regs ? L.p.regs : 128;
     info->trial_ms_128 = L.trial_ms[0];
-    info->trial_ms_80 = L.trial_ms[1];
+    info->trial_ms_96 = L.trial_ms[1];
+    info->trial_ms_80 = L.trial_ms[2];
     return BS_OK;
 }
 

@@ -417,6 +417,7 @@ void admit(bs_server_s *s)
         p.max_side = L.max_side;
         p.h_max = (L.max_side + 1) / 2;
         p.npad = 32 * ((L.max_side + 31) / 32);
+        p.regs = s->cfg.registers[L.cls];
         p.done = reinterpret_cast<uint32_t *>(s->mirror_dev + off + L.done);
         p.pub_shift = shift;
         e = bs::launch_fit(p, L.n, sk);
@@ -493,6 +494,11 @@ bs_status bs_serve_create(const bs_serve_cfg *cfg, void *arena, size_t arena_byt
         return serve_fail(BS_ERR_INVALID_ARG, "bs_serve_create: n_streams must be 0 or 4..128");
     if (cfg->max_inflight < 0 || cfg->batch_us < 0)
         return serve_fail(BS_ERR_INVALID_ARG, "bs_serve_create: max_inflight / batch_us < 0");
+    for (int c = 0; c < 4; ++c) {
+        const int r = cfg->registers[c];
+        if (r != 0 && r != 128 && r != 96 && r != 80)
+            return serve_fail(BS_ERR_INVALID_ARG, "bs_serve_create: registers must be 0, 128, 96 or 80");
+    }
     // validate the sampler configuration through the fit path's checks
     bs_fit_args a;
     std::memset(&a, 0, sizeof a);
@@ -530,7 +536,8 @@ bs_status bs_serve_create(const bs_serve_cfg *cfg, void *arena, size_t arena_byt
     if (s->cfg.n_streams == 0) s->cfg.n_streams = 96;
     cudaError_t e = cudaGetDevice(&s->device);
     if (e != cudaSuccess) return bs::set_error(BS_ERR_CUDA, "bs_serve_create: %s", cudaGetErrorString(e));
-    s->resident = bs_fit_resident_galaxies(cfg->n_chains, 63 < cfg->max_side ? 63 : cfg->max_side);
+    s->resident = bs_fit_resident_galaxies(cfg->n_chains, 63 < cfg->max_side ? 63 : cfg->max_side,
+                                           cfg->max_side > 31 ? cfg->registers[1] : cfg->registers[0]);
     if (s->resident <= 0) s->resident = 1;
     if (s->cfg.max_inflight == 0) s->cfg.max_inflight = 2 * s->resident;
     e = cudaHostAlloc(reinterpret_cast<void **>(&s->mirror), arena_bytes, cudaHostAllocMapped | cudaHostAllocPortable);

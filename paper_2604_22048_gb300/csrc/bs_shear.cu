@@ -442,9 +442,15 @@ __global__ void __launch_bounds__(256) shear_finalize_kernel(const double *parti
 template <int FAMILY, bool HAS_B>
 cudaError_t launch_fb(const ShearLaunch &s, int grid, bool vec, cudaStream_t st)
 {
-    if (vec)
+    if (vec) {
+        // with b the ring is 48 KB, above the default dynamic limit once the
+        // static reduction buffer is added
+        const cudaError_t e = cudaFuncSetAttribute(shear_kernel_async<FAMILY, HAS_B>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)async_smem_bytes(HAS_B));
+        if (e != cudaSuccess) return e;
         shear_kernel_async<FAMILY, HAS_B><<<grid, kShearThreads, async_smem_bytes(HAS_B), st>>>(s);
-    else
+    } else
         shear_kernel<FAMILY, HAS_B, false><<<grid, kShearThreads, 0, st>>>(s);
     return cudaGetLastError();
 }

@@ -93,8 +93,7 @@ def test_autotuned_plan_matches_untuned(cuda):
     info = tuned.info()
     assert sorted(i["slot_class"] for i in info) == [1, 2, 3, 4]
     for i in info:
-        assert i["registers"] in (80, 128)
-        assert i["trial_ms_128"] > 0 and i["trial_ms_80"] > 0
-        chosen = i["trial_ms_128"] if i["registers"] == 128 else i["trial_ms_80"]
-        assert chosen <= min(i["trial_ms_128"], i["trial_ms_80"])
+        t = {128: i["trial_ms_128"], 96: i["trial_ms_96"], 80: i["trial_ms_80"]}
+        assert i["registers"] in t and all(v > 0 for v in t.values())
+        assert t[i["registers"]] <= min(t.values())
     assert all(i["trial_ms_128"] == 0 and i["registers"] == 128 for i in plain.info())
