@@ -332,18 +332,19 @@ __device__ __forceinline__ void cp_async_wait()
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-constexpr int kStages = 4;   // chunks per lane in flight: this one and three ahead
+constexpr int kStages = 3;   // chunks per lane in flight: this one and two ahead
+constexpr int kChunk = 8;    // samples per lane per chunk (two 16-byte copies per array)
 
 __host__ __device__ constexpr size_t async_smem_bytes(bool has_b)
 {
-    return (size_t)kStages * (has_b ? 3 : 2) * kShearThreads * sizeof(float4);
+    return (size_t)kStages * (has_b ? 3 : 2) * 2 * kShearThreads * sizeof(float4);
 }
 
-// K % 4 == 0 and 16-byte aligned rows: each lane streams its chunks through
-// a kStages-deep ring of its own shared-memory slots with cp.async, over the
-// flattened sequence (galaxy, chunk) of its group, so the pipeline does not
-// drain between galaxies.  A lane only reads the slots it filled, after
-// cp.async.wait_group; no barrier is needed.
+// K % 4 == 0 and 16-byte aligned rows: each lane streams its 8-sample chunks
+// through a kStages-deep ring of its own shared-memory slots with cp.async,
+// over the flattened sequence (galaxy, chunk) of its group, so the pipeline
+// does not drain between galaxies.  A lane only reads the slots it filled,
+// after cp.async.wait_group; no barrier is needed.
 template <int FAMILY, bool HAS_B>
 __global__ void __launch_bounds__(kShearThreads, 3) shear_kernel_async(const ShearLaunch s)
 {
@@ -357,22 +358,30 @@ __global__ void __launch_bounds__(kShearThreads, 3) shear_kernel_async(const She
     const long long ngroups = (long long)gridDim.x * blockDim.x / kGroup;
     const ShearConst c = shear_const(s, FAMILY);
     const int K = s.K;
-    const int cpg = (K + 4 * kGroup - 1) / (4 * kGroup);     // chunks per galaxy per lane
+    constexpr int span = kChunk * kGroup;                    // samples of a group per chunk step
+    const int cpg = (K + span - 1) / span;                   // chunks per galaxy per lane
     const long long my_gal = group < s.n_gal ? (s.n_gal - 1 - group) / ngroups + 1 : 0;
     const long long n_items = my_gal * cpg;
     double av = 0.0, a1 = 0.0, a2 = 0.0, aq = 0.0;
+    // slot (stage, array, half) of this thread
+    auto slot = [&](int st, int arr, int half) -> float4 * {
+        return &sbuf[((st * NV + arr) * 2 + half) * kShearThreads + tid];
+    };
 
     // issuer position: galaxy, chunk, ring slot
     long long in = group;
     int ic = 0, ist = 0;
     auto issue = [&]() {
         if (in < s.n_gal) {
-            const int k0 = 4 * sub + 4 * kGroup * ic;
-            if (k0 < K) {
-                const long long off = in * (long long)K + k0;
-                cp_async16(&sbuf[(ist * NV + 0) * kShearThreads + tid], s.e1 + off);
-                cp_async16(&sbuf[(ist * NV + 1) * kShearThreads + tid], s.e2 + off);
-                if (HAS_B) cp_async16(&sbuf[(ist * NV + 2) * kShearThreads + tid], s.b + off);
+            const int k0 = kChunk * sub + span * ic;
+            const long long off = in * (long long)K + k0;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                if (k0 + 4 * h < K) {
+                    cp_async16(slot(ist, 0, h), s.e1 + off + 4 * h);
+                    cp_async16(slot(ist, 1, h), s.e2 + off + 4 * h);
+                    if (HAS_B) cp_async16(slot(ist, 2, h), s.b + off + 4 * h);
+                }
             }
             if (++ic == cpg) {
                 ic = 0;
@@ -391,19 +400,19 @@ __global__ void __launch_bounds__(kShearThreads, 3) shear_kernel_async(const She
     for (long long t = 0; t < n_items; ++t) {
         issue();
         cp_async_wait<kStages - 1>();
-        const int k0 = 4 * sub + 4 * kGroup * cc;
-        Chunk ch;
-        ch.nvalid = k0 < K ? 4 : 0;
-        ch.full = ch.nvalid == 4;
-        if (ch.full) {
-            ch.e1 = sbuf[(cst * NV + 0) * kShearThreads + tid];
-            ch.e2 = sbuf[(cst * NV + 1) * kShearThreads + tid];
-            if (HAS_B) ch.b = sbuf[(cst * NV + 2) * kShearThreads + tid];
-        } else {
-            ch.e1 = ch.e2 = ch.b = make_float4(0.f, 0.f, 0.f, 0.f);
+        const int k0 = kChunk * sub + span * cc;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            Chunk ch;
+            ch.nvalid = k0 + 4 * h < K ? 4 : 0;
+            ch.full = ch.nvalid == 4;
+            if (ch.full) {
+                ch.e1 = *slot(cst, 0, h);
+                ch.e2 = *slot(cst, 1, h);
+                ch.b = HAS_B ? *slot(cst, 2, h) : make_float4(0.f, 0.f, 0.f, 0.f);
+                eval_chunk<FAMILY, HAS_B>(c, ch, L);
+            }
         }
-        if (!HAS_B) ch.b = make_float4(0.f, 0.f, 0.f, 0.f);
-        eval_chunk<FAMILY, HAS_B>(c, ch, L);
         cst = cst + 1 == kStages ? 0 : cst + 1;
         if (++cc == cpg) {
             cc = 0;
@@ -443,8 +452,8 @@ template <int FAMILY, bool HAS_B>
 cudaError_t launch_fb(const ShearLaunch &s, int grid, bool vec, cudaStream_t st)
 {
     if (vec) {
-        // with b the ring is 48 KB, above the default dynamic limit once the
-        // static reduction buffer is added
+        // the ring (48 KB, 72 KB with b) plus the static reduction buffer is
+        // above the default dynamic shared-memory limit
         const cudaError_t e = cudaFuncSetAttribute(shear_kernel_async<FAMILY, HAS_B>,
                                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                    (int)async_smem_bytes(HAS_B));
@@ -462,6 +471,8 @@ int shear_grid_blocks()
     int dev = 0, sms = 0, nb = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncSetAttribute(shear_kernel_async<BS_EPRIOR_BA14, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)async_smem_bytes(false));
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, shear_kernel_async<BS_EPRIOR_BA14, false>, kShearThreads,
                                                   async_smem_bytes(false));
     if (sms <= 0) sms = 1;
