@@ -115,6 +115,13 @@ def lib():
         L.or_shear_estimate.argtypes = [_F, _F, _F, C.c_int64, C.c_int, C.c_int, C.c_double,
                                         C.c_double, C.c_int, C.c_double, C.c_double, C.c_double,
                                         C.c_int, _D, _D]
+        L.or_log_ndtr.restype = C.c_double
+        L.or_log_ndtr.argtypes = [C.c_double]
+        L.or_log_skewnorm.restype = C.c_double
+        L.or_log_skewnorm.argtypes = [C.c_double] * 4
+        L.or_shear_loglike_full.restype = C.c_double
+        L.or_shear_loglike_full.argtypes = [_F, _F, _F, _F, C.c_int64, C.c_int, C.c_int, C.c_double,
+                                            C.c_double, _D, _D, _D]
         L.or_gauss_hermite.restype = C.c_int
         L.or_gauss_hermite.argtypes = [C.c_int, _D, _D]
         for nm in ("or_shear_apply", "or_shear_invert"):
@@ -376,6 +383,28 @@ def shear_loglike(e1p, e2p, g1, g2, alpha, *, b=None, family=EPRIOR_BA14, trunc_
     g = np.zeros(3)
     v = lib().or_shear_loglike(_fp(e1p), _fp(e2p), _fp(bb), n_gal, K, family, trunc_r, sigma_e0,
                                g1, g2, alpha, _dp(g))
+    return v, g
+
+
+def log_ndtr(t):
+    return lib().or_log_ndtr(float(t))
+
+
+def log_skewnorm(x, mu, sigma, a):
+    return lib().or_log_skewnorm(float(x), float(mu), float(sigma), float(a))
+
+
+def shear_loglike_full(e1p, e2p, lfp, lsp, theta, *, family=EPRIOR_BA14, trunc_r=0.7, sigma_e0=0.3,
+                       interim=(-1.0, 9.0, -2.0, 1.0)):
+    """All-free shear likelihood; theta = (g1, g2, sigma_e, mu_f, sigma_f, a_f,
+    mu_s, sigma_s).  Returns (value, grad[8])."""
+    e1p, e2p, lfp, lsp = _f32(e1p), _f32(e2p), _f32(lfp), _f32(lsp)
+    n_gal, K = e1p.shape
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    im = np.ascontiguousarray(interim, dtype=np.float64)
+    g = np.zeros(8)
+    v = lib().or_shear_loglike_full(_fp(e1p), _fp(e2p), _fp(lfp), _fp(lsp), n_gal, K, family, trunc_r, sigma_e0,
+                                    _dp(im), _dp(th), _dp(g))
     return v, g
 
 

@@ -187,6 +187,23 @@ double or_shear_loglike(const float *e1p, const float *e2p, const float *b,
                         double sigma_e0, double g1, double g2, double alpha,
                         double grad[3]);
 
+/* Standard normal log CDF, log Phi(t), stable in both tails. */
+double or_log_ndtr(double t);
+/* Log density of the skew normal of Eq. lflux-lsize-dist: location mu,
+ * scale sigma, shape a: log[2 phi(z) Phi(a z) / sigma], z = (x - mu)/sigma. */
+double or_log_skewnorm(double x, double mu, double sigma, double a);
+
+/* Eq. likelihood-shear with every property's true prior (Sec. 3.2 setting
+ * with all hyperparameters free): the ellipticity part as or_shear_loglike,
+ * times, per sample, SkewNormal(log10 f; mu_f, sigma_f, a_f) N(log10 s; mu_s,
+ * sigma_s) over the interim uniforms U(lf_lo, lf_hi) U(ls_lo, ls_hi)
+ * (interim = {lf_lo, lf_hi, ls_lo, ls_hi}).  lfp, lsp: log10 flux and log10
+ * hlr samples [n_gal][K].  theta = (g1, g2, sigma_e, mu_f, sigma_f, a_f, mu_s,
+ * sigma_s); grad (may be NULL) gets the 8 derivatives. */
+double or_shear_loglike_full(const float *e1p, const float *e2p, const float *lfp, const float *lsp,
+                             int64_t n_gal, int K, int family, double trunc_r, double sigma_e0,
+                             const double interim[4], const double theta[8], double grad[8]);
+
 /* Posterior mean of (g1, g2[, alpha]) under a uniform prior on the unit disk
  * (and alpha ~ U(alpha_lo, alpha_hi) when free_alpha): Newton to the mode on
  * the analytic gradient, then n_gh-point Gauss-Hermite quadrature on the

@@ -103,13 +103,44 @@ double or_log_eprior(int family, double alpha, double trunc_r, double e1, double
     return -E / (2.0 * alpha * alpha) - or_log_z_eprior(family, alpha, trunc_r);
 }
 
+/* Log weight of one sample from its ellipticity: log p_e(eps | alpha)
+ * + log|d eps / d eps'| - log P0_e(eps'), and (if dl) its derivatives with
+ * respect to (g1, g2, alpha). */
+static double eps_log_weight(double e1p, double e2p, int family, double trunc_r, double sigma_e0,
+                             double g1, double g2, double alpha, double dlz, double dl[3])
+{
+    double complex g = g1 + I * g2;
+    double gg = g1 * g1 + g2 * g2;
+    double complex ep = e1p + I * e2p;
+    double complex D = 1.0 - conj(g) * ep;
+    double complex eps = (ep - g) / D;
+    double E = creal(eps * conj(eps));
+    double lpt = or_log_eprior(family, alpha, trunc_r, creal(eps), cimag(eps));
+    double lJ = log(or_shear_jacobian(e1p, e2p, g1, g2));
+    double lp0 = or_log_eprior(OR_EPRIOR_BA14, sigma_e0, 0.0, e1p, e2p);
+    double lw = lpt + lJ - lp0;
+    if (dl && isfinite(lw)) {
+        double complex de1 = (-D + ep * (ep - g)) / (D * D);
+        double complex de2 = -I * (D + ep * (ep - g)) / (D * D);
+        double dE1 = 2.0 * creal(conj(eps) * de1);
+        double dE2 = 2.0 * creal(conj(eps) * de2);
+        double dlpt_dE = -1.0 / (2.0 * alpha * alpha);
+        if (family == OR_EPRIOR_BA14) dlpt_dE += -2.0 / (1.0 - E);
+        double absD2 = creal(D * conj(D));
+        double dlJ1 = -4.0 * g1 / (1.0 - gg) - 4.0 * creal(conj(D) * (-ep)) / absD2;
+        double dlJ2 = -4.0 * g2 / (1.0 - gg) - 4.0 * creal(conj(D) * (I * ep)) / absD2;
+        dl[0] = dlpt_dE * dE1 + dlJ1;
+        dl[1] = dlpt_dE * dE2 + dlJ2;
+        dl[2] = E / (alpha * alpha * alpha) - dlz;
+    }
+    return lw;
+}
+
 double or_shear_loglike(const float *e1p, const float *e2p, const float *b,
                         int64_t n_gal, int K, int family, double trunc_r,
                         double sigma_e0, double g1, double g2, double alpha,
                         double grad[3])
 {
-    double complex g = g1 + I * g2;
-    double gg = g1 * g1 + g2 * g2;
     double dlz = dlogz_dalpha(family, alpha, trunc_r);
     double *lw = malloc(sizeof(double) * K);
     double (*dl)[3] = malloc(sizeof(double[3]) * K);
@@ -118,29 +149,10 @@ double or_shear_loglike(const float *e1p, const float *e2p, const float *b,
         double mx = -INFINITY;
         for (int k = 0; k < K; ++k) {
             size_t j = (size_t)n * K + k;
-            double complex ep = (double)e1p[j] + I * (double)e2p[j];
-            double complex D = 1.0 - conj(g) * ep;
-            double complex eps = (ep - g) / D;
-            double E = creal(eps * conj(eps));
-            double lpt = or_log_eprior(family, alpha, trunc_r, creal(eps), cimag(eps));
-            double lJ = log(or_shear_jacobian(creal(ep), cimag(ep), g1, g2));
-            double lp0 = or_log_eprior(OR_EPRIOR_BA14, sigma_e0, 0.0, creal(ep), cimag(ep));
-            lw[k] = lpt + lJ - lp0 + (b ? (double)b[j] : 0.0);
+            lw[k] = eps_log_weight((double)e1p[j], (double)e2p[j], family, trunc_r, sigma_e0, g1, g2, alpha,
+                                   dlz, grad ? dl[k] : NULL) +
+                    (b ? (double)b[j] : 0.0);
             if (lw[k] > mx) mx = lw[k];
-            if (grad && isfinite(lw[k])) {
-                double complex de1 = (-D + ep * (ep - g)) / (D * D);
-                double complex de2 = -I * (D + ep * (ep - g)) / (D * D);
-                double dE1 = 2.0 * creal(conj(eps) * de1);
-                double dE2 = 2.0 * creal(conj(eps) * de2);
-                double dlpt_dE = -1.0 / (2.0 * alpha * alpha);
-                if (family == OR_EPRIOR_BA14) dlpt_dE += -2.0 / (1.0 - E);
-                double absD2 = creal(D * conj(D));
-                double dlJ1 = -4.0 * g1 / (1.0 - gg) - 4.0 * creal(conj(D) * (-ep)) / absD2;
-                double dlJ2 = -4.0 * g2 / (1.0 - gg) - 4.0 * creal(conj(D) * (I * ep)) / absD2;
-                dl[k][0] = dlpt_dE * dE1 + dlJ1;
-                dl[k][1] = dlpt_dE * dE2 + dlJ2;
-                dl[k][2] = E / (alpha * alpha * alpha) - dlz;
-            }
         }
         if (!isfinite(mx)) {
             total = -INFINITY;
@@ -154,6 +166,86 @@ double or_shear_loglike(const float *e1p, const float *e2p, const float *b,
                 double pk = exp(lw[k] - mx) / s;
                 if (pk == 0.0) continue;
                 for (int i = 0; i < 3; ++i) G[i] += pk * dl[k][i];
+            }
+    }
+    free(lw);
+    free(dl);
+    if (grad) memcpy(grad, G, sizeof G);
+    return total;
+}
+
+/* ---- all properties free (Sec. 3.3 hyperpriors; Eq. lflux-lsize-dist) ---- */
+
+double or_log_ndtr(double t)
+{
+    if (t > 5.0) return log1p(-0.5 * erfc(t / sqrt(2.0)));
+    if (t >= -20.0) return log(0.5 * erfc(-t / sqrt(2.0)));
+    /* Phi(t) = phi(t) / |t| (1 - 1/t^2 + 3/t^4 - 15/t^6 + 105/t^8 - ...) */
+    double u = 1.0 / (t * t);
+    double series = 1.0 - u * (1.0 - u * (3.0 - u * (15.0 - u * 105.0)));
+    return -0.5 * t * t - log(-t) - 0.5 * log(2.0 * OR_PI) + log(series);
+}
+
+double or_log_skewnorm(double x, double mu, double sigma, double a)
+{
+    double z = (x - mu) / sigma;
+    return log(2.0) - log(sigma) - 0.5 * z * z - 0.5 * log(2.0 * OR_PI) + or_log_ndtr(a * z);
+}
+
+/* Per-sample log prior ratio of log-flux and log-size, true over interim,
+ * and its derivatives with respect to (mu_f, sigma_f, a_f, mu_s, sigma_s). */
+static double flux_size_log_weight(double lf, double ls, const double hyp[5], const double interim[4],
+                                   double dh[5])
+{
+    double mu_f = hyp[0], sig_f = hyp[1], a_f = hyp[2], mu_s = hyp[3], sig_s = hyp[4];
+    double z = (lf - mu_f) / sig_f;
+    double az = a_f * z;
+    double lnorm = -0.5 * log(2.0 * OR_PI);
+    double r = exp(lnorm - 0.5 * az * az - or_log_ndtr(az));   /* phi(az) / Phi(az) */
+    double y = (ls - mu_s) / sig_s;
+    double lw = or_log_skewnorm(lf, mu_f, sig_f, a_f) + (-log(sig_s) + lnorm - 0.5 * y * y) +
+                log(interim[1] - interim[0]) + log(interim[3] - interim[2]);
+    if (dh) {
+        dh[0] = (z - a_f * r) / sig_f;
+        dh[1] = (-1.0 + z * z - a_f * z * r) / sig_f;
+        dh[2] = r * z;
+        dh[3] = y / sig_s;
+        dh[4] = (-1.0 + y * y) / sig_s;
+    }
+    return lw;
+}
+
+double or_shear_loglike_full(const float *e1p, const float *e2p, const float *lfp, const float *lsp,
+                             int64_t n_gal, int K, int family, double trunc_r, double sigma_e0,
+                             const double interim[4], const double theta[8], double grad[8])
+{
+    const double g1 = theta[0], g2 = theta[1], alpha = theta[2];
+    const double *hyp = theta + 3;
+    double dlz = dlogz_dalpha(family, alpha, trunc_r);
+    double *lw = malloc(sizeof(double) * K);
+    double (*dl)[8] = malloc(sizeof(double[8]) * K);
+    double total = 0.0, G[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int64_t n = 0; n < n_gal; ++n) {
+        double mx = -INFINITY;
+        for (int k = 0; k < K; ++k) {
+            size_t j = (size_t)n * K + k;
+            lw[k] = eps_log_weight((double)e1p[j], (double)e2p[j], family, trunc_r, sigma_e0, g1, g2, alpha, dlz,
+                                   grad ? dl[k] : NULL) +
+                    flux_size_log_weight((double)lfp[j], (double)lsp[j], hyp, interim, grad ? dl[k] + 3 : NULL);
+            if (lw[k] > mx) mx = lw[k];
+        }
+        if (!isfinite(mx)) {
+            total = -INFINITY;
+            continue;
+        }
+        double s = 0.0;
+        for (int k = 0; k < K; ++k) s += exp(lw[k] - mx);
+        total += mx + log(s) - log((double)K);
+        if (grad)
+            for (int k = 0; k < K; ++k) {
+                double pk = exp(lw[k] - mx) / s;
+                if (pk == 0.0) continue;
+                for (int i = 0; i < 8; ++i) G[i] += pk * dl[k][i];
             }
     }
     free(lw);

@@ -371,3 +371,89 @@ def test_hmc_matches_laplace_on_bright_galaxy():
         assert abs(flat[k].mean() - mode[k]) < 5 * sd / np.sqrt(ess) + 0.05 * sd, k
         assert abs(flat[k].std() / sd - 1) < 0.12, (k, flat[k].std() / sd)
         assert O.rhat(s[k]) < 1.01
+
+
+# ---- all properties free: skew-normal log-flux, normal log-size (Eq. lflux-lsize-dist)
+
+def test_log_ndtr_matches_scipy():
+    from scipy import special
+    for t in np.concatenate([np.linspace(-80.0, 12.0, 185), [-20.0, -20.000001, -19.99999, 5.0, 5.000001]]):
+        ref = special.log_ndtr(t)
+        assert abs(O.log_ndtr(t) - ref) <= 1e-11 * max(1.0, abs(ref)), (t, O.log_ndtr(t), ref)
+
+
+def test_log_skewnorm_matches_scipy_and_normalises():
+    from scipy import integrate, stats
+    rng = np.random.default_rng(8)
+    for _ in range(200):
+        mu, sig, a = rng.uniform(-2, 6), rng.uniform(0.05, 2), rng.uniform(-100, 100)
+        x = mu + sig * rng.normal(0, 3)
+        ref = stats.skewnorm.logpdf(x, a, loc=mu, scale=sig)
+        if np.isfinite(ref) and ref > -700:
+            assert abs(O.log_skewnorm(x, mu, sig, a) - ref) <= 1e-9 * max(1.0, abs(ref)), (x, mu, sig, a)
+    # the paper's log-flux distribution integrates to one
+    tot, _ = integrate.quad(lambda x: np.exp(O.log_skewnorm(x, 2.45, 0.4, 14.0)), -2, 8, points=[2.45], limit=200)
+    assert abs(tot - 1.0) < 1e-9
+
+
+def _full_inputs(rng, n, K, const_fs=False):
+    e1, e2 = [], []
+    for _ in range(n):
+        r = 0.25 * np.sqrt(rng.uniform(0, 1, K))
+        ph = rng.uniform(0, 2 * np.pi, K)
+        e1.append(r * np.cos(ph))
+        e2.append(r * np.sin(ph))
+    e1, e2 = np.array(e1, np.float32), np.array(e2, np.float32)
+    if const_fs:
+        lf = np.repeat(rng.uniform(2.3, 3.3, (n, 1)), K, axis=1).astype(np.float32)
+        ls = np.repeat(rng.normal(-0.4, 0.05, (n, 1)), K, axis=1).astype(np.float32)
+    else:
+        lf = rng.uniform(2.3, 3.3, (n, K)).astype(np.float32)
+        ls = rng.normal(-0.4, 0.06, (n, K)).astype(np.float32)
+    return e1, e2, lf, ls
+
+
+def test_full_loglike_reduces_to_ellipticity_part_plus_constants():
+    """With one log-flux and log-size per galaxy (the same for all its samples)
+    the flux/size ratio is a per-galaxy constant: the value is the
+    ellipticity-only likelihood plus the sum of the scipy log densities, and
+    the hyperparameter gradient is the sum of their parameter derivatives
+    (central differences of scipy)."""
+    from scipy import stats
+    rng = np.random.default_rng(12)
+    e1, e2, lf, ls = _full_inputs(rng, 6, 9, const_fs=True)
+    th = np.array([0.02, -0.01, 0.22, 2.5, 0.45, 9.0, -0.38, 0.06])
+    v, g = O.shear_loglike_full(e1, e2, lf, ls, th, family=O.EPRIOR_BA14)
+    ve, ge = O.shear_loglike(e1, e2, th[0], th[1], th[2], family=O.EPRIOR_BA14)
+
+    def b_sum(h):
+        x, y = lf[:, 0].astype(np.float64), ls[:, 0].astype(np.float64)
+        return float(np.sum(stats.skewnorm.logpdf(x, h[2], loc=h[0], scale=h[1]) +
+                            stats.norm.logpdf(y, loc=h[3], scale=h[4]) + np.log(10.0) + np.log(3.0)))
+
+    assert abs(v - (ve + b_sum(th[3:]))) < 1e-9 * max(1.0, abs(v))
+    assert np.allclose(g[:3], ge, rtol=1e-10, atol=1e-10)
+    for i in range(5):
+        h = 1e-6 * max(1.0, abs(th[3 + i]))
+        hp, hm = th[3:].copy(), th[3:].copy()
+        hp[i] += h
+        hm[i] -= h
+        fd = (b_sum(hp) - b_sum(hm)) / (2 * h)
+        assert abs(g[3 + i] - fd) <= 1e-5 * max(1.0, abs(fd)), (i, g[3 + i], fd)
+
+
+def test_full_loglike_gradient_by_central_differences():
+    rng = np.random.default_rng(13)
+    e1, e2, lf, ls = _full_inputs(rng, 5, 12)
+    for fam in (O.EPRIOR_BA14, O.EPRIOR_TRUNC_GAUSS):
+        th = np.array([0.03, 0.02, 0.24, 2.55, 0.5, 6.0, -0.41, 0.07])
+        v, g = O.shear_loglike_full(e1, e2, lf, ls, th, family=fam)
+        assert np.isfinite(v)
+        for i in range(8):
+            h = 1e-6 * max(1.0, abs(th[i]))
+            tp, tm = th.copy(), th.copy()
+            tp[i] += h
+            tm[i] -= h
+            fd = (O.shear_loglike_full(e1, e2, lf, ls, tp, family=fam)[0] -
+                  O.shear_loglike_full(e1, e2, lf, ls, tm, family=fam)[0]) / (2 * h)
+            assert abs(g[i] - fd) <= 2e-5 * max(1.0, abs(fd)), (fam, i, g[i], fd)
