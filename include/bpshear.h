@@ -277,7 +277,7 @@ typedef struct {
     int32_t batch_us;        /* admission interval while the GPU is full
                                 (0: 500 us); requests are admitted at once
                                 while fewer than the GPU holds are running */
-    int32_t n_streams;       /* launch streams (0: 96; 4..128) */
+    int32_t n_streams;       /* launch streams (0: 128; 4..128) */
     int32_t registers[4];    /* register cap of the fit kernel per 32-column slot
                                 class (stamps up to 31, 63, 95, 127 px): 128,
                                 96 or 80, e.g. as a bs_fit_plan autotune chose

@@ -533,7 +533,7 @@ bs_status bs_serve_create(const bs_serve_cfg *cfg, void *arena, size_t arena_byt
     if (st != BS_OK) return st;
     s->cfg = *cfg;
     if (s->cfg.batch_us == 0) s->cfg.batch_us = 500;
-    if (s->cfg.n_streams == 0) s->cfg.n_streams = 96;
+    if (s->cfg.n_streams == 0) s->cfg.n_streams = 128;
     cudaError_t e = cudaGetDevice(&s->device);
     if (e != cudaSuccess) return bs::set_error(BS_ERR_CUDA, "bs_serve_create: %s", cudaGetErrorString(e));
     s->resident = bs_fit_resident_galaxies(cfg->n_chains, 63 < cfg->max_side ? 63 : cfg->max_side,

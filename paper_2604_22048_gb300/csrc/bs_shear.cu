@@ -346,7 +346,7 @@ __host__ __device__ constexpr size_t async_smem_bytes(bool has_b)
 // does not drain between galaxies.  A lane only reads the slots it filled,
 // after cp.async.wait_group; no barrier is needed.
 template <int FAMILY, bool HAS_B>
-__global__ void __launch_bounds__(kShearThreads, 3) shear_kernel_async(const ShearLaunch s)
+__global__ void __launch_bounds__(kShearThreads, 4) shear_kernel_async(const ShearLaunch s)
 {
     extern __shared__ float4 sbuf[];
     constexpr int NV = HAS_B ? 3 : 2;
