@@ -418,6 +418,25 @@ bs_status bs_shear_loglike(const bs_shear_data *data, double g1, double g2,
                            double alpha, double *out, int32_t out_on_host,
                            void *workspace, size_t workspace_bytes, void *stream);
 
+/* Eq. likelihood-shear with every galaxy property's true prior free (the
+ * paper's all-free setting, Sec. 3.3): per sample, the ellipticity weight of
+ * bs_shear_loglike times the log-flux and log-size prior ratio
+ *   SkewNormal(lf; mu_f, sigma_f, a_f) N(ls; mu_s, sigma_s)
+ *     / [U(lf; lf_lo, lf_hi) U(ls; ls_lo, ls_hi)]       (Eq. lflux-lsize-dist
+ * over the interim uniforms of Eq. interim-prior), with the skew normal
+ * 2 phi(z) Phi(a z) / sigma, z = (lf - mu_f)/sigma_f.
+ *   lf, ls   device float [n_gal][K]: log10 flux and log10 hlr samples.
+ *   interim  host double [4]: lf_lo, lf_hi, ls_lo, ls_hi.
+ *   theta    host double [8]: g1, g2, sigma_e, mu_f, sigma_f, a_f, mu_s, sigma_s.
+ *   out      double [9] = {value, d/dtheta[0..7]}, device or host as in
+ *            bs_shear_loglike.  data->b must be NULL.
+ * Workspace: bs_shear_workspace_bytes.  Requires |g| < 1, sigma_e, sigma_f,
+ * sigma_s > 0. */
+bs_status bs_shear_loglike_full(const bs_shear_data *data, const float *lf, const float *ls,
+                                const double interim[4], const double theta[8], double *out,
+                                int32_t out_on_host, void *workspace, size_t workspace_bytes,
+                                void *stream);
+
 /* The same likelihood and gradient for callers that cannot allocate device
  * memory or pass a workspace (code under another framework's fixed memory
  * budget, real-time loops that must not allocate).  The paper has no
@@ -456,6 +475,49 @@ typedef struct {
 bs_status bs_shear_estimate(const bs_shear_data *data, const bs_estimate_cfg *cfg,
                             double *mean, double *cov, int32_t *n_evals, void *workspace,
                             size_t workspace_bytes, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Shear sampling phase as MCMC (Sec. 3.2 "Shear Sampling Phase")            */
+/* ------------------------------------------------------------------------ */
+
+/* The paper's uniform hyperpriors (Sec. 3.3): sigma_e ~ U(1e-4, 1),
+ * mu_f ~ U(-2, 6), sigma_f ~ U(0, 2), a_f ~ U(-100, 100), mu_s ~ U(-2, 2),
+ * sigma_s ~ U(0, 0.5); entries 0, 1 (g, on the unit disk) are -1, 1. */
+void bs_shear_hyperprior_default(double lo[8], double hi[8]);
+
+typedef struct {
+    uint32_t free_mask;       /* bit i: theta[i] is sampled; bits 0 and 1 (g)
+                                 must be set.  theta = (g1, g2, sigma_e, mu_f,
+                                 sigma_f, a_f, mu_s, sigma_s) */
+    double theta0[8];         /* start, and the value of each fixed parameter */
+    double lo[8], hi[8];      /* uniform prior of each sampled theta[2..7]
+                                 (open interval); g: uniform on the unit disk */
+    const float *lf, *ls;     /* device [n_gal][K] log10 flux and log10 hlr
+                                 samples (bs_shear_loglike_full), or both NULL:
+                                 ellipticities only (bs_shear_loglike; only
+                                 bits 0..2 may be set) */
+    double interim[4];        /* lf_lo, lf_hi, ls_lo, ls_hi of the interim prior */
+    int32_t n_warmup, n_samples, n_leapfrog;
+    float target_accept;      /* dual-averaging target */
+    int32_t random_steps;     /* L_i uniform on 1..n_leapfrog, else fixed */
+    uint64_t seed;
+    bs_allreduce_fn allreduce;  /* sums each evaluation over ranks (or NULL) */
+    void *allreduce_user;
+} bs_shear_sample_cfg;
+
+/* HMC on g and the chosen hyperparameters with the likelihood of
+ * Eq. likelihood-shear evaluated on the GPU at every leapfrog step; the chain
+ * itself runs on the host in FP64 (diagonal metric and step size adapted in
+ * the warmup, as in the image phase).
+ *   samples     host double [n_samples][8] (fixed parameters repeated)
+ *   accept_rate, step_size (host double, may be NULL), n_evals (host int32,
+ *   may be NULL): likelihood passes used.
+ * Workspace: bs_shear_workspace_bytes.  Synchronises `stream` at every
+ * step.  Errors: BS_ERR_INVALID_ARG (bad mask or sizes, theta0 outside the
+ * prior support), and those of the likelihood calls. */
+bs_status bs_shear_sample(const bs_shear_data *data, const bs_shear_sample_cfg *cfg, double *samples,
+                          double *accept_rate, double *step_size, int32_t *n_evals, void *workspace,
+                          size_t workspace_bytes, void *stream);
 
 #ifdef __cplusplus
 }

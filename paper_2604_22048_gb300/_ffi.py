@@ -23,10 +23,11 @@ STATUS_NAMES = {0: "BS_OK", -1: "BS_ERR_INVALID_ARG", -2: "BS_ERR_CUDA", -3: "BS
 # every symbol the header declares
 EXPORTED = ["bs_prior_default", "bs_last_error", "bs_version", "bs_render", "bs_fit_workspace_bytes",
             "bs_fit_galaxies", "bs_logpost_points", "bs_chain_ess", "bs_shear_workspace_bytes",
-            "bs_shear_loglike", "bs_shear_estimate", "bs_shear_loglike_noalloc",
+            "bs_shear_loglike", "bs_shear_estimate", "bs_shear_loglike_noalloc", "bs_shear_loglike_full",
             "bs_fit_plan_workspace_bytes", "bs_fit_plan_create", "bs_fit_plan_launch", "bs_fit_plan_destroy",
             "bs_fit_resident_galaxies", "bs_fit_plan_num_launches", "bs_fit_plan_info", "bs_serve_request_bytes", "bs_serve_create", "bs_serve_submit",
-            "bs_serve_poll", "bs_serve_get_stats", "bs_serve_now_ns", "bs_serve_destroy"]
+            "bs_serve_poll", "bs_serve_get_stats", "bs_serve_now_ns", "bs_serve_destroy",
+            "bs_shear_hyperprior_default", "bs_shear_sample"]
 
 
 class BsError(RuntimeError):
@@ -107,6 +108,14 @@ class ServeCompletion(C.Structure):
                 ("inv_mass", C.c_void_p), ("n_divergent", C.c_void_p), ("n_grad", C.c_void_p)]
 
 
+class ShearSampleCfg(C.Structure):
+    _fields_ = [("free_mask", C.c_uint32), ("theta0", C.c_double * 8), ("lo", C.c_double * 8),
+                ("hi", C.c_double * 8), ("lf", C.c_void_p), ("ls", C.c_void_p), ("interim", C.c_double * 4),
+                ("n_warmup", C.c_int32), ("n_samples", C.c_int32), ("n_leapfrog", C.c_int32),
+                ("target_accept", C.c_float), ("random_steps", C.c_int32), ("seed", C.c_uint64),
+                ("allreduce", ALLREDUCE_FN), ("allreduce_user", C.c_void_p)]
+
+
 class ServeStats(C.Structure):
     _fields_ = [(n, C.c_int64) for n in ("submitted", "admitted", "completed", "launches", "ticks", "waits_memory",
                                          "waits_inflight", "waits_streams", "arena_bytes", "arena_used",
@@ -161,12 +170,16 @@ def lib():
     L.bs_shear_loglike.argtypes = [C.POINTER(ShearData), f64, f64, f64, vp, i32, vp, sz, vp]
     L.bs_shear_estimate.argtypes = [C.POINTER(ShearData), C.POINTER(EstimateCfg), vp, vp, vp, vp, sz, vp]
     L.bs_shear_loglike_noalloc.argtypes = [C.POINTER(ShearData), f64, f64, f64, vp, vp]
+    L.bs_shear_loglike_full.argtypes = [C.POINTER(ShearData), vp, vp, vp, vp, vp, i32, vp, sz, vp]
     L.bs_fit_plan_workspace_bytes.argtypes = [C.POINTER(FitArgs)]
     L.bs_fit_plan_workspace_bytes.restype = sz
     L.bs_fit_plan_create.argtypes = [C.POINTER(FitArgs), C.POINTER(FitOut), vp, i32, vp, sz, vp,
                                      C.POINTER(C.c_void_p)]
     L.bs_fit_plan_launch.argtypes = [vp, vp]
     L.bs_fit_plan_destroy.argtypes = [vp]
+    L.bs_shear_hyperprior_default.argtypes = [vp, vp]
+    L.bs_shear_hyperprior_default.restype = None
+    L.bs_shear_sample.argtypes = [C.POINTER(ShearData), C.POINTER(ShearSampleCfg), vp, vp, vp, vp, vp, sz, vp]
     L.bs_fit_plan_num_launches.argtypes = [vp]
     L.bs_fit_plan_num_launches.restype = i32
     L.bs_fit_plan_info.argtypes = [vp, i32, C.POINTER(PlanLaunchInfo)]
@@ -182,6 +195,7 @@ def lib():
     L.bs_serve_now_ns.restype = i64
     L.bs_serve_destroy.argtypes = [vp]
     for nm in ("bs_render", "bs_fit_galaxies", "bs_logpost_points", "bs_chain_ess", "bs_shear_loglike",
+               "bs_shear_loglike_full", "bs_shear_sample",
                "bs_shear_estimate", "bs_shear_loglike_noalloc", "bs_fit_plan_create", "bs_fit_plan_launch",
                "bs_fit_plan_destroy", "bs_fit_plan_info", "bs_serve_create", "bs_serve_submit", "bs_serve_poll", "bs_serve_get_stats",
                "bs_serve_destroy"):

@@ -410,6 +410,63 @@ class ShearPlan:
                                          self.ws_bytes, _stream()))
         return self.out
 
+    def loglike_full(self, lf, ls, theta, *, interim=(-1.0, 9.0, -2.0, 1.0)):
+        """All properties free: lf, ls [n_gal, K] float32 CUDA (log10 flux and
+        log10 hlr samples); theta = (g1, g2, sigma_e, mu_f, sigma_f, a_f, mu_s,
+        sigma_s).  Returns numpy (value, gradient[8]) (synchronises)."""
+        _need_cuda(lf, ls)
+        if self.keep[2] is not None:
+            raise ValueError("the all-free likelihood takes no b offsets")
+        self._full_keep = (lf.contiguous(), ls.contiguous())
+        th = np.ascontiguousarray(theta, dtype=np.float64)
+        im = np.ascontiguousarray(interim, dtype=np.float64)
+        buf = np.zeros(9)
+        F.check(F.lib().bs_shear_loglike_full(C.byref(self.data), _p(self._full_keep[0]), _p(self._full_keep[1]),
+                                              im.ctypes.data_as(C.c_void_p), th.ctypes.data_as(C.c_void_p),
+                                              buf.ctypes.data_as(C.c_void_p), 1, _p(self.ws), self.ws_bytes,
+                                              _stream()))
+        return buf[0], buf[1:].copy()
+
+    def sample(self, theta0, *, free=("g1", "g2"), lf=None, ls=None, lo=None, hi=None, n_warmup=500,
+               n_samples=1000, n_leapfrog=8, target_accept=0.8, random_steps=True, seed=2604,
+               interim=(-1.0, 9.0, -2.0, 1.0), allreduce=None):
+        """HMC over g and the named hyperparameters (bs_shear_sample).
+        theta0: (g1, g2, sigma_e, mu_f, sigma_f, a_f, mu_s, sigma_s) start and
+        fixed values; lf, ls: log-flux / log-size samples (CUDA, [n_gal, K]) for
+        the all-free likelihood.  Returns (samples [n_samples, 8], info)."""
+        names = ("g1", "g2", "sigma_e", "mu_f", "sigma_f", "a_f", "mu_s", "sigma_s")
+        c = F.ShearSampleCfg()
+        c.free_mask = sum(1 << names.index(n) for n in free)
+        dlo, dhi = (C.c_double * 8)(), (C.c_double * 8)()
+        F.lib().bs_shear_hyperprior_default(dlo, dhi)
+        for i in range(8):
+            c.theta0[i] = float(theta0[i])
+            c.lo[i] = float(lo[i]) if lo is not None else dlo[i]
+            c.hi[i] = float(hi[i]) if hi is not None else dhi[i]
+        keep = None
+        if lf is not None or ls is not None:
+            _need_cuda(lf, ls)
+            keep = (lf.contiguous(), ls.contiguous())
+            c.lf, c.ls = _p(keep[0]), _p(keep[1])
+        for i in range(4):
+            c.interim[i] = float(interim[i])
+        c.n_warmup, c.n_samples, c.n_leapfrog = n_warmup, n_samples, n_leapfrog
+        c.target_accept, c.random_steps, c.seed = target_accept, int(random_steps), seed
+        cb = None
+        if allreduce is not None:
+            def _cb(buf, user):
+                arr = np.ctypeslib.as_array(buf, shape=(4,))
+                arr[:] = allreduce(arr.copy())
+            cb = F.ALLREDUCE_FN(_cb)
+            c.allreduce = cb
+        out = np.zeros((n_samples, 8))
+        acc, eps, nev = C.c_double(0), C.c_double(0), C.c_int32(0)
+        F.check(F.lib().bs_shear_sample(C.byref(self.data), C.byref(c), out.ctypes.data_as(C.c_void_p),
+                                        C.cast(C.byref(acc), C.c_void_p), C.cast(C.byref(eps), C.c_void_p),
+                                        C.cast(C.byref(nev), C.c_void_p), _p(self.ws), self.ws_bytes, _stream()))
+        del keep, cb
+        return out, {"accept_rate": acc.value, "step_size": eps.value, "n_evals": nev.value}
+
     def estimate(self, *, free_alpha=False, alpha=0.2, alpha_lo=1e-4, alpha_hi=1.0, n_gh=7, allreduce=None):
         """Posterior mean and covariance of (g1, g2[, alpha]) (numpy)."""
         cfg = F.EstimateCfg()

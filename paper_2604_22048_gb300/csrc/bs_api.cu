@@ -71,6 +71,10 @@ double log_z_family(int family, double alpha, double trunc_r)
     return std::log(2.0 * kPi * alpha * alpha) + std::log(-std::expm1(-x));
 }
 
+}  // namespace
+
+namespace bs {
+
 // Warmup windows: fast buffer, doubling slow windows, final fast buffer
 // (75 / 25... / 50, or 15% / rest / 10% for warmups shorter than 150); the
 // last slow window runs up to the final buffer.
@@ -98,6 +102,12 @@ int warmup_windows(int W, bool adapt, int *st, int *en, int cap)
     }
     return count;
 }
+
+}  // namespace bs
+
+namespace {
+
+using bs::warmup_windows;
 
 bool odd_side_ok(int s) { return s >= 3 && s <= BS_MAX_SIDE && (s & 1); }
 
@@ -305,7 +315,10 @@ size_t bs_shear_workspace_bytes(int64_t n_gal, int32_t K)
 {
     (void)n_gal;
     (void)K;
-    return (size_t)(bs::shear_grid_blocks() * 4 + 4) * sizeof(double);
+    // per-block partials of the 4-output kernel or of the all-free one, plus
+    // the device copy of the result
+    const size_t a = (size_t)bs::shear_grid_blocks() * 4, b = (size_t)bs::shear_full_grid_blocks() * bs::kShearFullOut;
+    return ((a > b ? a : b) + bs::kShearFullOut) * sizeof(double);
 }
 
 static bs_status validate_shear(const bs_shear_data *d, const char *who)
@@ -324,12 +337,11 @@ static bs_status validate_shear(const bs_shear_data *d, const char *who)
 bs_status bs_shear_loglike(const bs_shear_data *d, double g1, double g2, double alpha, double *out,
                            int32_t out_on_host, void *workspace, size_t workspace_bytes, void *stream)
 {
-    bs_status st = validate_shear(d, "bs_shear_loglike");
+    bs::ShearLaunch L;
+    double add[4], alpha_scale = 0.0;
+    bs_status st = bs::shear_prepare(d, g1, g2, alpha, L, add, alpha_scale, "bs_shear_loglike");
     if (st != BS_OK) return st;
     if (!out) return fail(BS_ERR_INVALID_ARG, "bs_shear_loglike: NULL out");
-    const double gg = g1 * g1 + g2 * g2;
-    if (!(gg < 1.0)) return fail(BS_ERR_INVALID_ARG, "bs_shear_loglike: |g| >= 1");
-    if (!(alpha > 0.0)) return fail(BS_ERR_INVALID_ARG, "bs_shear_loglike: alpha <= 0");
     const int grid = bs::shear_grid_blocks();
     const size_t need = (size_t)(grid * 4 + 4) * sizeof(double);
     if (!workspace || workspace_bytes < need)
@@ -339,38 +351,87 @@ bs_status bs_shear_loglike(const bs_shear_data *d, double g1, double g2, double 
     double *dev_out = out_on_host ? partials + (size_t)grid * 4 : out;
     cudaError_t e;
     if (d->n_gal > 0) {
-        bs::ShearLaunch L;
-        L.e1 = d->e1;
-        L.e2 = d->e2;
-        L.b = d->b;
-        L.n_gal = d->n_gal;
-        L.K = d->K;
-        L.family = d->family;
-        L.g1 = (float)g1;
-        L.g2 = (float)g2;
-        L.a2 = (float)(1.4426950408889634 / (2.0 * alpha * alpha));
-        L.kappa = d->family == BS_EPRIOR_BA14 ? 4.0f : 2.0f;
-        L.c0 = (float)(1.4426950408889634 / (2.0 * (double)d->sigma_e0 * d->sigma_e0));
-        L.r2 = d->trunc_r * d->trunc_r;
         L.partials = partials;
         e = bs::launch_shear(L, grid, s);
         if (e != cudaSuccess) return cuda_fail(e, "bs_shear_loglike: launch");
     }
-    const double ng = (double)d->n_gal;
-    const double kap = d->family == BS_EPRIOR_BA14 ? 4.0 : 2.0;
-    const double cst = kap * std::log1p(-gg) - log_z_family(d->family, alpha, d->trunc_r) +
-                       log_z_ba14(d->sigma_e0) - std::log((double)d->K);
     const int n_part = d->n_gal > 0 ? grid : 0;
-    e = bs::launch_shear_finalize(partials, n_part, ng * cst, ng * (-2.0 * kap * g1 / (1.0 - gg)),
-                                  ng * (-2.0 * kap * g2 / (1.0 - gg)),
-                                  -ng * dlog_z_dalpha(d->family, alpha, d->trunc_r),
-                                  1.0 / (alpha * alpha * alpha), dev_out, s);
+    e = bs::launch_shear_finalize(partials, n_part, add[0], add[1], add[2], add[3], alpha_scale, dev_out, s);
     if (e != cudaSuccess) return cuda_fail(e, "bs_shear_loglike: finalize");
     if (out_on_host) {
         e = cudaMemcpyAsync(out, dev_out, 4 * sizeof(double), cudaMemcpyDeviceToHost, s);
         if (e != cudaSuccess) return cuda_fail(e, "bs_shear_loglike: copy");
         e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return cuda_fail(e, "bs_shear_loglike: sync");
+    }
+    return BS_OK;
+}
+
+bs_status bs_shear_loglike_full(const bs_shear_data *d, const float *lf, const float *ls, const double interim[4],
+                                const double theta[8], double *out, int32_t out_on_host, void *workspace,
+                                size_t workspace_bytes, void *stream)
+{
+    const char *who = "bs_shear_loglike_full";
+    if (!theta || !interim || !out) return fail(BS_ERR_INVALID_ARG, "%s: NULL theta/interim/out", who);
+    bs::ShearFullLaunch F;
+    double add[bs::kShearFullOut], scale[bs::kShearFullOut];
+    double alpha_scale = 0.0;
+    bs_status st = bs::shear_prepare(d, theta[0], theta[1], theta[2], F.s, add, alpha_scale, who);
+    if (st != BS_OK) return st;
+    if (d->b) return fail(BS_ERR_INVALID_ARG, "%s: b must be NULL (the flux/size terms are explicit)", who);
+    if (d->n_gal > 0 && (!lf || !ls)) return fail(BS_ERR_INVALID_ARG, "%s: NULL lf/ls", who);
+    const double mu_f = theta[3], sig_f = theta[4], a_f = theta[5], mu_s = theta[6], sig_s = theta[7];
+    if (!(sig_f > 0.0 && sig_s > 0.0 && std::isfinite(mu_f) && std::isfinite(a_f) && std::isfinite(mu_s)))
+        return fail(BS_ERR_INVALID_ARG, "%s: sigma_f, sigma_s must be > 0", who);
+    if (!(interim[1] > interim[0] && interim[3] > interim[2]))
+        return fail(BS_ERR_INVALID_ARG, "%s: interim bounds", who);
+    const int grid = bs::shear_full_grid_blocks();
+    const size_t need = (size_t)(grid + 1) * bs::kShearFullOut * sizeof(double);
+    if (!workspace || workspace_bytes < need)
+        return fail(BS_ERR_OUT_OF_MEMORY, "%s: workspace of %zu bytes needed", who, need);
+    F.lf = lf;
+    F.ls = ls;
+    F.mu_f = (float)mu_f;
+    F.inv_sf = (float)(1.0 / sig_f);
+    F.a_f = (float)a_f;
+    F.mu_s = (float)mu_s;
+    F.inv_ss = (float)(1.0 / sig_s);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    double *partials = static_cast<double *>(workspace);
+    double *dev_out = out_on_host ? partials + (size_t)grid * bs::kShearFullOut : out;
+    cudaError_t e;
+    if (d->n_gal > 0) {
+        F.s.partials = partials;
+        e = bs::launch_shear_full(F, grid, s);
+        if (e != cudaSuccess) return cuda_fail(e, "bs_shear_loglike_full: launch");
+    }
+    // per-galaxy constants of the flux/size ratio: log 2 - log sigma_f - log sigma_s
+    // - log 2 pi + log of the interim widths (Eq. lflux-lsize-dist over the
+    // interim uniforms); d/dsigma of the -log sigma terms
+    const double ng = (double)d->n_gal;
+    const double kPiD = 3.14159265358979323846;
+    add[0] += ng * (std::log(2.0) - std::log(sig_f) - std::log(sig_s) - std::log(2.0 * kPiD) +
+                    std::log(interim[1] - interim[0]) + std::log(interim[3] - interim[2]));
+    for (int i = 0; i < bs::kShearFullOut; ++i) scale[i] = 1.0;
+    scale[0] = 0.6931471805599453;   // log2 -> natural log
+    scale[3] = alpha_scale;
+    scale[4] = 1.0 / sig_f;
+    add[4] = 0.0;
+    scale[5] = 1.0 / sig_f;
+    add[5] = -ng / sig_f;
+    add[6] = 0.0;
+    scale[7] = 1.0 / sig_s;
+    add[7] = 0.0;
+    scale[8] = 1.0 / sig_s;
+    add[8] = -ng / sig_s;
+    const int n_part = d->n_gal > 0 ? grid : 0;
+    e = bs::launch_shear_finalize_n(partials, n_part, bs::kShearFullOut, scale, add, dev_out, s);
+    if (e != cudaSuccess) return cuda_fail(e, "bs_shear_loglike_full: finalize");
+    if (out_on_host) {
+        e = cudaMemcpyAsync(out, dev_out, bs::kShearFullOut * sizeof(double), cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) return cuda_fail(e, "bs_shear_loglike_full: copy");
+        e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(e, "bs_shear_loglike_full: sync");
     }
     return BS_OK;
 }

@@ -28,15 +28,24 @@ struct Philox4x64 {
     uint64_t w[4];
 };
 
-__device__ __forceinline__ Philox4x64 philox4x64_10(uint64_t c0, uint64_t c1, uint64_t c2,
-                                                   uint64_t c3, uint64_t k0, uint64_t k1)
+__host__ __device__ __forceinline__ uint64_t mulhi64(uint64_t a, uint64_t b)
+{
+#ifdef __CUDA_ARCH__
+    return __umul64hi(a, b);
+#else
+    return (uint64_t)(((unsigned __int128)a * b) >> 64);
+#endif
+}
+
+__host__ __device__ __forceinline__ Philox4x64 philox4x64_10(uint64_t c0, uint64_t c1, uint64_t c2,
+                                                            uint64_t c3, uint64_t k0, uint64_t k1)
 {
     const uint64_t m0 = 0xD2E7470EE14C6C93ull, m1 = 0xCA5A826395121157ull;
     const uint64_t w0 = 0x9E3779B97F4A7C15ull, w1 = 0xBB67AE8584CAA73Bull;
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-        const uint64_t p0hi = __umul64hi(m0, c0), p0lo = m0 * c0;
-        const uint64_t p1hi = __umul64hi(m1, c2), p1lo = m1 * c2;
+        const uint64_t p0hi = mulhi64(m0, c0), p0lo = m0 * c0;
+        const uint64_t p1hi = mulhi64(m1, c2), p1lo = m1 * c2;
         const uint64_t n0 = p1hi ^ c1 ^ k0;
         const uint64_t n2 = p0hi ^ c3 ^ k1;
         c0 = n0;

@@ -90,11 +90,29 @@ struct ShearLaunch {
     float r2;         // truncation radius squared
     double *partials; // [grid][4]
 };
+// All properties free: per sample also log10 flux and log10 hlr, with the
+// skew-normal / normal true priors of their hyperparameters.
+struct ShearFullLaunch {
+    ShearLaunch s;         // ellipticity part (b must be NULL); partials: [grid][kShearFullOut]
+    const float *lf, *ls;
+    float mu_f, inv_sf, a_f, mu_s, inv_ss;
+};
+constexpr int kShearFullOut = 9;   // value, d/d(g1, g2, sigma_e, mu_f, sigma_f, a_f, mu_s, sigma_s)
+
 int shear_grid_blocks();
+int shear_full_grid_blocks();
 cudaError_t launch_shear(const ShearLaunch &s, int grid, cudaStream_t stream);
+cudaError_t launch_shear_full(const ShearFullLaunch &f, int grid, cudaStream_t stream);
+// out[i] = scale[i] * sum over blocks of partials[.][i] + add[i], i < n_out (<= kShearFullOut)
+cudaError_t launch_shear_finalize_n(const double *partials, int n_part, int n_out, const double *scale,
+                                    const double *add, double *out, cudaStream_t stream);
 cudaError_t launch_shear_finalize(const double *partials, int n_part, double add_value,
                                   double add_g1, double add_g2, double add_alpha,
                                   double alpha_scale, double *out, cudaStream_t stream);
+
+// Stan-style metric-adaptation windows of a warmup of W iterations (none when
+// !adapt or W < 20): [st[i], en[i]), returns the count (<= cap).
+int warmup_windows(int W, bool adapt, int *st, int *en, int cap);
 
 // Thread-local error message of the C ABI (bs_last_error).
 bs_status set_error(bs_status st, const char *fmt, ...);

@@ -448,6 +448,173 @@ __global__ void __launch_bounds__(256) shear_finalize_kernel(const double *parti
     }
 }
 
+// ---- all properties free ----------------------------------------------------
+
+// log Phi(t) and the inverse Mills ratio phi(t)/Phi(t) of the standard normal,
+// through erfcx on the left tail so that neither underflows.
+__device__ __forceinline__ void log_ndtr_mills(float t, float &lphi, float &r)
+{
+    if (t < 0.0f) {
+        const float u = -t * 0.70710678118654752f;
+        const float ex = erfcxf(u);                 // exp(u^2) erfc(u)
+        lphi = logf(0.5f * ex) - u * u;
+        r = 0.79788456080286536f / ex;              // sqrt(2/pi) / erfcx
+    } else {
+        const float q = 0.5f * erfcf(t * 0.70710678118654752f);   // 1 - Phi(t)
+        lphi = log1pf(-q);
+        r = 0.39894228040143268f * expf(-0.5f * t * t) / (1.0f - q);
+    }
+}
+
+struct FullAcc {
+    float m, sw, t1, t2, tq, h[5];
+};
+
+// One sample: log2 weight of the ellipticity part (as pair_terms, scalar) plus
+// the flux/size log prior ratio up to per-galaxy constants,
+//   -z^2/2 + log Phi(a z) - y^2/2,  z = (lf - mu_f)/sigma_f, y = (ls - mu_s)/sigma_s,
+// and the factors of its derivatives (times sigma where that is constant):
+//   (z - a r), z (z - a r), r z, y, y^2,  r = phi(a z)/Phi(a z).
+template <int FAMILY>
+__device__ __forceinline__ void full_sample(const ShearFullLaunch &f, float an, float e1, float e2, float lf,
+                                            float ls, bool valid, FullAcc &A)
+{
+    const ShearLaunch &s = f.s;
+    const float ur = fmaf(-s.g1, e1, fmaf(-s.g2, e2, 1.0f));
+    const float nvi = fmaf(s.g2, e1, -s.g1 * e2);
+    const float U = fmaf(ur, ur, nvi * nvi);
+    const float Ep = fmaf(e1, e1, e2 * e2);
+    const float n1 = e1 - s.g1, n2 = e2 - s.g2;
+    const float rU = rcp_ftz(U);
+    const float Q = fmaf(n1, n1, n2 * n2) * rU;
+    const float larg = FAMILY == BS_EPRIOR_TRUNC_GAUSS ? U * (1.0f - Ep) : U;
+    const float lgk = FAMILY == BS_EPRIOR_TRUNC_GAUSS ? -2.0f : -s.kappa;
+    float x = fmaf(s.c0, Ep, fmaf(lgk, lg2_ftz(larg), -s.a2 * Q));
+    if (FAMILY == BS_EPRIOR_TRUNC_GAUSS && !(Q < s.r2)) x = -INFINITY;
+    const float aqk = fmaf(an, Q, -s.kappa);
+    const float du1 = fmaf(nvi, e2, ur * e1);
+    const float du2 = fmaf(-nvi, e1, ur * e2);
+    const float c1 = fmaf(du1, aqk, -an * n1);
+    const float c2 = fmaf(du2, aqk, -an * n2);
+    const float z = (lf - f.mu_f) * f.inv_sf;
+    const float y = (ls - f.mu_s) * f.inv_ss;
+    float lphi, r;
+    log_ndtr_mills(f.a_f * z, lphi, r);
+    x = fmaf(kLog2e, lphi - 0.5f * fmaf(z, z, y * y), x);
+    if (!valid) x = -INFINITY;
+    if (x > A.m) {
+        const float sc = ex2_ftz(A.m - x);
+        A.sw *= sc;
+        A.t1 *= sc;
+        A.t2 *= sc;
+        A.tq *= sc;
+#pragma unroll
+        for (int i = 0; i < 5; ++i) A.h[i] *= sc;
+        A.m = x;
+    }
+    const float e = ex2_ftz(x - A.m);
+    const float er = e * rU;
+    const float h0 = fmaf(-f.a_f, r, z);
+    A.sw += e;
+    A.t1 = fmaf(er, c1, A.t1);
+    A.t2 = fmaf(er, c2, A.t2);
+    A.tq = fmaf(e, Q, A.tq);
+    A.h[0] = fmaf(e, h0, A.h[0]);
+    A.h[1] = fmaf(e, z * h0, A.h[1]);
+    A.h[2] = fmaf(e, r * z, A.h[2]);
+    A.h[3] = fmaf(e, y, A.h[3]);
+    A.h[4] = fmaf(e, y * y, A.h[4]);
+}
+
+template <int FAMILY>
+__global__ void __launch_bounds__(kShearThreads, 2) shear_full_kernel(const ShearFullLaunch f)
+{
+    const ShearLaunch &s = f.s;
+    const int lane = threadIdx.x & 31;
+    const int sub = lane & (kGroup - 1);
+    const unsigned gmask = 0xFFu << (lane & ~(kGroup - 1));
+    const long long group = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / kGroup;
+    const long long ngroups = (long long)gridDim.x * blockDim.x / kGroup;
+    const float an = s.a2 * kLn2;
+    const int K = s.K;
+    double acc[kShearFullOut];
+#pragma unroll
+    for (int i = 0; i < kShearFullOut; ++i) acc[i] = 0.0;
+
+    for (long long n = group; n < s.n_gal; n += ngroups) {
+        const long long base = n * (long long)K;
+        FullAcc A;
+        A.m = -1e30f;
+        A.sw = A.t1 = A.t2 = A.tq = 0.f;
+#pragma unroll
+        for (int i = 0; i < 5; ++i) A.h[i] = 0.f;
+        for (int k = sub; k < K; k += kGroup) {
+            const long long j = base + k;
+            full_sample<FAMILY>(f, an, __ldg(s.e1 + j), __ldg(s.e2 + j), __ldg(f.lf + j), __ldg(f.ls + j), true, A);
+        }
+        // merge the 8 lanes of the group
+        float v[10] = {A.m, A.sw, A.t1, A.t2, A.tq, A.h[0], A.h[1], A.h[2], A.h[3], A.h[4]};
+#pragma unroll
+        for (int o = kGroup / 2; o > 0; o >>= 1) {
+            float w[10];
+#pragma unroll
+            for (int i = 0; i < 10; ++i) w[i] = __shfl_xor_sync(gmask, v[i], o, kGroup);
+            const float mn = fmaxf(v[0], w[0]);
+            const float ca = ex2_ftz(v[0] - mn), cb = ex2_ftz(w[0] - mn);
+#pragma unroll
+            for (int i = 1; i < 10; ++i) v[i] = v[i] * ca + w[i] * cb;
+            v[0] = mn;
+        }
+        if (sub == 0) {
+            if (v[1] > 0.f) {
+                const float inv = 1.0f / v[1];
+                acc[0] += (double)v[0] + (double)__log2f(v[1]);
+                acc[1] += (double)(-2.0f * v[2] * inv);
+                acc[2] += (double)(-2.0f * v[3] * inv);
+                acc[3] += (double)(v[4] * inv);
+#pragma unroll
+                for (int i = 0; i < 5; ++i) acc[4 + i] += (double)(v[5 + i] * inv);
+            } else {
+                acc[0] = -INFINITY;
+            }
+        }
+    }
+    __shared__ double red[kShearThreads / 32][kShearFullOut];
+#pragma unroll
+    for (int i = 0; i < kShearFullOut; ++i) acc[i] = warp_sum_d(acc[i]);
+    const int w = threadIdx.x >> 5;
+    if (lane == 0)
+        for (int i = 0; i < kShearFullOut; ++i) red[w][i] = acc[i];
+    __syncthreads();
+    if (threadIdx.x < kShearFullOut) {
+        double t = 0.0;
+        for (int i = 0; i < kShearThreads / 32; ++i) t += red[i][threadIdx.x];
+        s.partials[(size_t)blockIdx.x * kShearFullOut + threadIdx.x] = t;
+    }
+}
+
+struct FinalizeN {
+    double scale[kShearFullOut], add[kShearFullOut];
+};
+
+__global__ void __launch_bounds__(256) shear_finalize_n_kernel(const double *partials, int n_part, int n_out,
+                                                                FinalizeN c, double *out)
+{
+    __shared__ double red[256];
+    for (int k = 0; k < n_out; ++k) {
+        double t = 0.0;
+        for (int i = threadIdx.x; i < n_part; i += blockDim.x) t += partials[(size_t)i * n_out + k];
+        red[threadIdx.x] = t;
+        __syncthreads();
+        for (int o = 128; o > 0; o >>= 1) {
+            if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) out[k] = red[0] * c.scale[k] + c.add[k];
+        __syncthreads();
+    }
+}
+
 template <int FAMILY, bool HAS_B>
 cudaError_t launch_fb(const ShearLaunch &s, int grid, bool vec, cudaStream_t st)
 {
@@ -491,6 +658,39 @@ cudaError_t launch_shear(const ShearLaunch &s, int grid, cudaStream_t stream)
                   : launch_fb<BS_EPRIOR_BA14, false>(s, grid, vec, stream);
     return hb ? launch_fb<BS_EPRIOR_TRUNC_GAUSS, true>(s, grid, vec, stream)
               : launch_fb<BS_EPRIOR_TRUNC_GAUSS, false>(s, grid, vec, stream);
+}
+
+int shear_full_grid_blocks()
+{
+    int dev = 0, sms = 0, nb = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, shear_full_kernel<BS_EPRIOR_BA14>, kShearThreads, 0);
+    if (sms <= 0) sms = 1;
+    if (nb <= 0) nb = 1;
+    return sms * nb;
+}
+
+cudaError_t launch_shear_full(const ShearFullLaunch &f, int grid, cudaStream_t stream)
+{
+    if (f.s.family == BS_EPRIOR_BA14)
+        shear_full_kernel<BS_EPRIOR_BA14><<<grid, kShearThreads, 0, stream>>>(f);
+    else
+        shear_full_kernel<BS_EPRIOR_TRUNC_GAUSS><<<grid, kShearThreads, 0, stream>>>(f);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_shear_finalize_n(const double *partials, int n_part, int n_out, const double *scale,
+                                    const double *add, double *out, cudaStream_t stream)
+{
+    if (n_out < 1 || n_out > kShearFullOut) return cudaErrorInvalidValue;
+    FinalizeN c;
+    for (int i = 0; i < kShearFullOut; ++i) {
+        c.scale[i] = i < n_out ? scale[i] : 0.0;
+        c.add[i] = i < n_out ? add[i] : 0.0;
+    }
+    shear_finalize_n_kernel<<<1, 256, 0, stream>>>(partials, n_part, n_out, c, out);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_shear_finalize(const double *partials, int n_part, double add_value,

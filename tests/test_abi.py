@@ -66,7 +66,7 @@ def test_struct_layouts_match_header(tmp_path):
                "bs_estimate_cfg": _ffi.EstimateCfg, "bs_serve_cfg": _ffi.ServeCfg,
                "bs_serve_request": _ffi.ServeRequest, "bs_serve_completion": _ffi.ServeCompletion,
                "bs_serve_stats": _ffi.ServeStats, "bs_psf": _ffi.Psf, "bs_prior": _ffi.Prior,
-               "bs_fit_plan_launch_info": _ffi.PlanLaunchInfo}
+               "bs_fit_plan_launch_info": _ffi.PlanLaunchInfo, "bs_shear_sample_cfg": _ffi.ShearSampleCfg}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "bpshear.h"', "int main(void) {"]
     for cn, py in structs.items():
         lines.append(f'printf("{cn} size %zu\\n", sizeof({cn}));')

@@ -203,6 +203,30 @@ def test_shear_loglike_matches_oracle(cuda, family, K, with_b):
         assert np.abs(got[1:] - gr).max() <= 1e-4 * np.abs(gr).max() + 1e-6 * n, (got[1:], gr)
 
 
+@pytest.mark.parametrize("family", [O.EPRIOR_BA14, O.EPRIOR_TRUNC_GAUSS])
+def test_shear_loglike_full_matches_oracle(cuda, family):
+    """All properties free: value within 1e-5 relative and the 8 derivatives
+    within 1e-4 of the oracle, with skew-normal shapes whose log Phi runs deep
+    into the left tail (a z down to about -60)."""
+    rng = np.random.default_rng(21 + family)
+    n, K = 1500, 96
+    e1, e2 = _ellipticity_samples(rng, n, K, 0.2)
+    if family == O.EPRIOR_TRUNC_GAUSS:
+        e1, e2 = 0.6 * e1, 0.6 * e2
+    lf = rng.normal(2.8, 0.35, (n, K)).astype(np.float32)
+    ls = rng.normal(-0.4, 0.06, (n, K)).astype(np.float32)
+    t = lambda a: torch.from_numpy(a).to(cuda)
+    plan = api.ShearPlan(t(e1), t(e2), family=family)
+    for th in ([0.02, -0.01, 0.21, 2.45, 0.4, 14.0, -0.4, 0.05],
+               [-0.03, 0.04, 0.26, 2.7, 0.6, -5.0, -0.35, 0.08],
+               [0.0, 0.0, 0.2, 2.2, 0.3, 0.0, -0.45, 0.04]):
+        got_v, got_g = plan.loglike_full(t(lf), t(ls), th)
+        v, g = O.shear_loglike_full(e1, e2, lf, ls, th, family=family)
+        assert np.isfinite(v)
+        assert abs(got_v - v) <= 1e-5 * max(abs(v), n), (got_v, v)
+        assert np.abs(got_g - g).max() <= 1e-4 * np.abs(g).max() + 1e-6 * n, (th, got_g, g)
+
+
 def test_shear_empty_and_zero_weight(cuda):
     e1 = torch.zeros((0, 8), device=cuda)
     plan = api.ShearPlan(e1, e1.clone())
