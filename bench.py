@@ -551,6 +551,13 @@ def shear_arm(a, world, rank, local_rank):
     e2.copy_(h2, non_blocking=True)
     mean, cov = plan.estimate(free_alpha=True, alpha=0.2, alpha_lo=0.15, alpha_hi=0.3)
     est_s = time.perf_counter() - t0
+    # the shear sampling phase as MCMC: HMC on (g1, g2, sigma_e), one GPU
+    # likelihood-and-gradient pass per leapfrog step
+    t1 = time.perf_counter()
+    draws, hinfo = plan.sample([0.0, 0.0, 0.2, 2.45, 0.4, 14.0, -0.4, 0.05], free=("g1", "g2", "sigma_e"),
+                               lo=[-1, -1, 0.15, -2, 0, -100, -2, 0], hi=[1, 1, 0.3, 6, 2, 100, 2, 0.5],
+                               n_warmup=300, n_samples=1000, n_leapfrog=8, seed=22048)
+    hmc_s = time.perf_counter() - t1
     return {"metric": SHEAR_METRIC, "value": passes / (ms / 1e3), "unit": "passes/s", "n_gpus": world,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -567,6 +574,10 @@ def shear_arm(a, world, rank, local_rank):
             "estimate": {"g": [float(x) for x in mean[:2]], "alpha": float(mean[2]),
                          "sd": [float(np.sqrt(cov[i, i])) for i in range(3)], "truth": list(g_true) + [alpha_true],
                          "passes": plan.last_n_evals, "seconds": est_s},
+            "hmc": {"free": ["g1", "g2", "sigma_e"], "mean": [float(x) for x in draws[:, :3].mean(axis=0)],
+                    "sd": [float(x) for x in draws[:, :3].std(axis=0)], "draws": int(draws.shape[0]),
+                    "accept_rate": hinfo["accept_rate"], "passes": hinfo["n_evals"], "seconds": hmc_s,
+                    "ms_per_pass": 1e3 * hmc_s / max(1, hinfo["n_evals"])},
             "e2e": {"value": 1.0 / est_s, "unit": "joint estimates/s (host samples in, estimate out)",
                     "h2d_bytes_per_step": int(bytes_per_pass), "d2h_bytes_per_step": 8 * 12}}
 
