@@ -147,32 +147,25 @@ struct Chunk {
     int nvalid;
 };
 
-template <bool HAS_B, bool VEC>
+// Scalar loads of one chunk (any K, any alignment); missing samples are zero.
+template <bool HAS_B>
 __device__ __forceinline__ void load_chunk(const ShearLaunch &s, long long base, int k0, int K, Chunk &ch)
 {
     ch.nvalid = k0 < K ? min(4, K - k0) : 0;
     ch.full = ch.nvalid == 4;
-    if (VEC) {
-        if (k0 < K) {
-            ch.e1 = __ldg(reinterpret_cast<const float4 *>(s.e1 + base + k0));
-            ch.e2 = __ldg(reinterpret_cast<const float4 *>(s.e2 + base + k0));
-            if (HAS_B) ch.b = __ldg(reinterpret_cast<const float4 *>(s.b + base + k0));
-        }
-    } else {
-        float t1[4] = {0.f, 0.f, 0.f, 0.f}, t2[4] = {0.f, 0.f, 0.f, 0.f}, tb[4] = {0.f, 0.f, 0.f, 0.f};
+    float t1[4] = {0.f, 0.f, 0.f, 0.f}, t2[4] = {0.f, 0.f, 0.f, 0.f}, tb[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            if (r < ch.nvalid) {
-                const long long j = base + k0 + r;
-                t1[r] = __ldg(s.e1 + j);
-                t2[r] = __ldg(s.e2 + j);
-                if (HAS_B) tb[r] = __ldg(s.b + j);
-            }
+    for (int r = 0; r < 4; ++r) {
+        if (r < ch.nvalid) {
+            const long long j = base + k0 + r;
+            t1[r] = __ldg(s.e1 + j);
+            t2[r] = __ldg(s.e2 + j);
+            if (HAS_B) tb[r] = __ldg(s.b + j);
         }
-        ch.e1 = make_float4(t1[0], t1[1], t1[2], t1[3]);
-        ch.e2 = make_float4(t2[0], t2[1], t2[2], t2[3]);
-        ch.b = make_float4(tb[0], tb[1], tb[2], tb[3]);
     }
+    ch.e1 = make_float4(t1[0], t1[1], t1[2], t1[3]);
+    ch.e2 = make_float4(t2[0], t2[1], t2[2], t2[3]);
+    ch.b = make_float4(tb[0], tb[1], tb[2], tb[3]);
 }
 
 // Online log-sum-exp state of one lane (both halves share the maximum).
@@ -283,9 +276,9 @@ __device__ __forceinline__ void block_partials(const ShearLaunch &s, double av, 
     }
 }
 
-// Any K and alignment: scalar or float4 loads into two register buffers in
-// turn (the next chunk's loads in flight while the current one is evaluated).
-template <int FAMILY, bool HAS_B, bool VEC>
+// Any K and alignment: scalar loads into two register buffers in turn (the
+// next chunk's loads in flight while the current one is evaluated).
+template <int FAMILY, bool HAS_B>
 __global__ void __launch_bounds__(kShearThreads, 3) shear_kernel(const ShearLaunch s)
 {
     const int lane = threadIdx.x & 31;
@@ -303,14 +296,14 @@ __global__ void __launch_bounds__(kShearThreads, 3) shear_kernel(const ShearLaun
         lse_reset(L);
         Chunk A, B;
         int k0 = 4 * sub;
-        load_chunk<HAS_B, VEC>(s, base, k0, K, A);
+        load_chunk<HAS_B>(s, base, k0, K, A);
         for (;;) {
             if (k0 >= K) break;
-            load_chunk<HAS_B, VEC>(s, base, k0 + 4 * kGroup, K, B);
+            load_chunk<HAS_B>(s, base, k0 + 4 * kGroup, K, B);
             eval_chunk<FAMILY, HAS_B>(c, A, L);
             k0 += 4 * kGroup;
             if (k0 >= K) break;
-            load_chunk<HAS_B, VEC>(s, base, k0 + 4 * kGroup, K, A);
+            load_chunk<HAS_B>(s, base, k0 + 4 * kGroup, K, A);
             eval_chunk<FAMILY, HAS_B>(c, B, L);
             k0 += 4 * kGroup;
         }
@@ -627,7 +620,7 @@ cudaError_t launch_fb(const ShearLaunch &s, int grid, bool vec, cudaStream_t st)
         if (e != cudaSuccess) return e;
         shear_kernel_async<FAMILY, HAS_B><<<grid, kShearThreads, async_smem_bytes(HAS_B), st>>>(s);
     } else
-        shear_kernel<FAMILY, HAS_B, false><<<grid, kShearThreads, 0, st>>>(s);
+        shear_kernel<FAMILY, HAS_B><<<grid, kShearThreads, 0, st>>>(s);
     return cudaGetLastError();
 }
 

@@ -127,3 +127,54 @@ def initial_theta(stamp_sums, ls_true, e_true, offsets):
     scale = np.where(r >= 0.95, 0.95 / np.maximum(r, 1e-300), 1.0)
     th[..., 2:4] = e * scale[..., None]
     return th
+
+
+def draw_ba14_e(rng, n, sigma=0.2):
+    """Intrinsic ellipticities from the (1 - |e|^2)^2 exp(-|e|^2 / 2 sigma^2)
+    density on the unit disk (Eq. ellip-mag-prior with its orientation
+    uniform): Gaussian proposals of width sigma inside the disk, accepted with
+    probability (1 - |e|^2)^2."""
+    out = np.empty((n, 2))
+    filled = 0
+    while filled < n:
+        m = 2 * (n - filled) + 16
+        e = rng.normal(0.0, sigma, size=(m, 2))
+        E = (e ** 2).sum(axis=1)
+        keep = (E < 1.0) & (rng.uniform(size=m) < (1.0 - np.minimum(E, 1.0)) ** 2)
+        e = e[keep]
+        take = min(len(e), n - filled)
+        out[filled:filled + take] = e[:take]
+        filled += take
+    return out
+
+
+def toy_interim_ellipticities(e_int, g, K, rng, *, sigma_eta=0.1, n_prop=3000, sigma_e0=0.3):
+    """Appendix-A toy, first phase: the intrinsic ellipticities e_int [n, 2] are
+    sheared by g (Eq. shear-transform), mapped to eta = 2 atanh|e| e/|e|
+    (Eq. eta-transform) and observed with N(0, sigma_eta) noise per component
+    (Eq. noisy-eta-like); K draws per galaxy from the interim posterior of
+    eta' -- that likelihood times the interim ellipticity prior (width
+    sigma_e0) times |d eps'/d eta'| -- by sampling-importance-resampling of
+    n_prop proposals drawn from the likelihood.  Returns the sheared
+    ellipticity samples e1, e2 [n, K] (float32)."""
+    n = len(e_int)
+    e = e_int[:, 0] + 1j * e_int[:, 1]
+    gc = complex(g[0], g[1])
+    ep = (e + gc) / (1 + np.conj(gc) * e)
+    r = np.maximum(np.abs(ep), 1e-12)
+    eta = ep * (2 * np.arctanh(r) / r)
+    eta_obs = eta + sigma_eta * (rng.normal(size=n) + 1j * rng.normal(size=n))
+    e1 = np.empty((n, K), np.float32)
+    e2 = np.empty((n, K), np.float32)
+    for i in range(n):
+        prop = eta_obs[i] + sigma_eta * (rng.normal(size=n_prop) + 1j * rng.normal(size=n_prop))
+        rho = np.maximum(np.abs(prop), 1e-12)
+        t = np.tanh(rho / 2)
+        eps = prop * (t / rho)
+        E = t * t
+        logw = 2 * np.log1p(-E) - E / (2 * sigma_e0 ** 2) + np.log(0.5 * (1 - E) * t / rho)
+        w = np.exp(logw - logw.max())
+        pick = rng.choice(n_prop, size=K, replace=True, p=w / w.sum())
+        e1[i] = eps[pick].real
+        e2[i] = eps[pick].imag
+    return e1, e2
