@@ -554,7 +554,10 @@ def shear_arm(a, world, rank, local_rank):
     # the shear sampling phase as MCMC: HMC on (g1, g2, sigma_e), one GPU
     # likelihood-and-gradient pass per leapfrog step
     t1 = time.perf_counter()
-    draws, hinfo = plan.sample([0.0, 0.0, 0.2, 2.45, 0.4, 14.0, -0.4, 0.05], free=("g1", "g2", "sigma_e"),
+    # started at the Gauss-Hermite estimate: at g = 0 the truncated family can
+    # give a galaxy no sample of non-zero weight
+    draws, hinfo = plan.sample([mean[0], mean[1], mean[2], 2.45, 0.4, 14.0, -0.4, 0.05],
+                               free=("g1", "g2", "sigma_e"),
                                lo=[-1, -1, 0.15, -2, 0, -100, -2, 0], hi=[1, 1, 0.3, 6, 2, 100, 2, 0.5],
                                n_warmup=300, n_samples=1000, n_leapfrog=8, seed=22048)
     hmc_s = time.perf_counter() - t1
