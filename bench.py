@@ -386,6 +386,7 @@ def our_arm(a, world, rank, local_rank):
     sm_max = peaks.get("sm_max_mhz", 2070.0)
     peak_tflops = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     achieved = fit_flops / fit_s / 1e12
+    ffma_tf, ffma2_tf = api.fp32_peak_tflops(False), api.fp32_peak_tflops(True)
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
            "ms_per_step": step_ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -399,6 +400,7 @@ def our_arm(a, world, rank, local_rank):
                         "kernel": ", ".join(f"fit_kernel_r{i['registers']}<{i['slot_class']}>" for i in plan.info()),
                         "peak_how": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
                                     f"{sm_max:.0f} MHz (max SM clock)",
+                        "ffma_microbenchmark_tflops": {"ffma": ffma_tf, "ffma2": ffma2_tf},
                         "flops_per_launch": fit_flops, "evals_per_launch": n_grad,
                         "fit_ms": float(np.mean(fit_ms))},
            "gpu_launches": int(a.steps * len(plan.info())

@@ -386,6 +386,14 @@ bs_status bs_logpost_points(const bs_fit_args *args, int32_t n_points,
 bs_status bs_chain_ess(const float *samples, int32_t n_gal, int32_t n_chains,
                        int32_t n_samples, float *ess, float *rhat, void *stream);
 
+/* FP32 FMA throughput of the current device in TFLOP/s (an FMA counts 2),
+ * measured with independent FFMA chains (packed = 0) or packed FFMA2 chains
+ * (packed != 0) over SMs x 8 blocks of 256 threads: the check on the derived
+ * FP32 peak that the fit kernel's roofline uses.  Allocates a scratch buffer
+ * (stream-ordered) and synchronises `stream`.  Measurement helper, not a
+ * step of the method. */
+bs_status bs_fp32_peak(int32_t packed, double *tflops, void *stream);
+
 /* ------------------------------------------------------------------------ */
 /* Shear sampling phase (Sec. 3.2 - 3.4)                                     */
 /* ------------------------------------------------------------------------ */

@@ -311,6 +311,16 @@ bs_status bs_chain_ess(const float *samples, int32_t n_gal, int32_t n_chains, in
     return e == cudaSuccess ? BS_OK : cuda_fail(e, "bs_chain_ess");
 }
 
+bs_status bs_fp32_peak(int32_t packed, double *tflops, void *stream)
+{
+    if (!tflops) return fail(BS_ERR_INVALID_ARG, "bs_fp32_peak: NULL tflops");
+    double t = 0.0;
+    const cudaError_t e = bs::measure_fp32_peak(packed != 0, t, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "bs_fp32_peak");
+    *tflops = t;
+    return BS_OK;
+}
+
 size_t bs_shear_workspace_bytes(int64_t n_gal, int32_t K)
 {
     (void)n_gal;

@@ -78,7 +78,69 @@ __global__ void __launch_bounds__(128) ess_kernel(const float *samples, int n_ga
     }
 }
 
+// FP32 FMA throughput: eight independent chains per thread of x = x a + b on
+// float pairs, as scalar FFMA or as packed FFMA2 (16 FMAs per iteration either
+// way); the sum is stored so the chains are not removed.
+template <bool PACKED>
+__global__ void __launch_bounds__(256) ffma_kernel(float *out, int iters, float a, float b)
+{
+    float2 x[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x[i] = make_float2(1e-3f * (float)threadIdx.x + (float)i, 0.5f * (float)i);
+    const float2 av = make_float2(a, a), bv = make_float2(b, b);
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            if (PACKED) {
+                x[i] = __ffma2_rn(x[i], av, bv);
+            } else {
+                x[i].x = fmaf(x[i].x, a, b);
+                x[i].y = fmaf(x[i].y, a, b);
+            }
+        }
+    }
+    float sum = 0.f;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) sum += x[i].x + x[i].y;
+    out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = sum;
+}
+
 }  // namespace
+
+cudaError_t measure_fp32_peak(bool packed, double &tflops, cudaStream_t stream)
+{
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const int grid = sms * 8, block = 256, iters = 16384;
+    float *out = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    e = cudaMallocAsync(&out, sizeof(float) * (size_t)grid * block, stream);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    float best = 0.f;
+    for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+        e = cudaEventRecord(e0, stream);
+        if (packed)
+            ffma_kernel<true><<<grid, block, 0, stream>>>(out, iters, 1.0000001f, 1e-7f);
+        else
+            ffma_kernel<false><<<grid, block, 0, stream>>>(out, iters, 1.0000001f, 1e-7f);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaEventRecord(e1, stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && rep > 0 && (best == 0.f || ms < best)) best = ms;
+    }
+    if (out) cudaFreeAsync(out, stream);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (e != cudaSuccess) return e;
+    const double flops = 2.0 * 16.0 * (double)iters * grid * block;
+    tflops = flops / (best * 1e-3) / 1e12;
+    return cudaStreamSynchronize(stream);
+}
 
 cudaError_t launch_chain_ess(const float *samples, int n_gal, int n_chains, int n_samples,
                              float *ess, float *rhat, cudaStream_t stream)

@@ -125,5 +125,6 @@ bs_status shear_prepare(const bs_shear_data *d, double g1, double g2, double alp
 
 cudaError_t launch_chain_ess(const float *samples, int n_gal, int n_chains, int n_samples,
                              float *ess, float *rhat, cudaStream_t stream);
+cudaError_t measure_fp32_peak(bool packed, double &tflops, cudaStream_t stream);
 
 }  // namespace bs

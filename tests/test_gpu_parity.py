@@ -291,3 +291,14 @@ def test_bad_start_sets_status(cuda):
     cfg = api.FitConfig(n_chains=2, n_warmup=20, n_samples=10, n_leapfrog=4)
     _, _, _, res = _fit_both(ds, cuda, np.float32, cfg)
     assert list(res["status"]) == [0, 1, 0]
+
+
+def test_fp32_peak_microbenchmark(cuda):
+    """The measured FFMA throughput lies below the derived peak (SMs x 128
+    lanes x 2 flop x the maximum SM clock) and not far under it."""
+    props = torch.cuda.get_device_properties(cuda)
+    clock_mhz = 2070.0
+    derived = props.multi_processor_count * 128 * 2 * clock_mhz * 1e6 / 1e12
+    for packed in (False, True):
+        t = api.fp32_peak_tflops(packed)
+        assert 0.5 * derived < t < 1.05 * derived, (packed, t, derived)
