@@ -204,6 +204,9 @@ CAPTURED_TRAFFIC = {
     # 53x53 galaxy of the plain workload: (13,959,168 + 6,656) B / 1,216 galaxies
     "fit": ("paper_2604_22048_gb300/csrc/bs_fit.cu",
             "e539407da8b89149d2635beb4e7b85b173bd6ce2955127758af98460f7ae9367", 11485.0),
+    # one interim sample of the shear workload: (481,524,480 + 3,041,024) B / (200,000 x 300)
+    "shear": ("paper_2604_22048_gb300/csrc/bs_shear.cu",
+              "c7db3fdf99f29840405240fbaddc34fc87ecab2d124ea9e933a9dc81372cf5bc", 8.0761),
 }
 
 
@@ -573,7 +576,10 @@ def shear_arm(a, world, rank, local_rank):
                        "n_gal": n, "K": K, "step": "27 likelihood+gradient passes",
                        "l2": f"inputs {bytes_per_pass / 1e9:.1f} GB per pass, larger than L2"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "kernel": "shear_kernel<1,0,1>",
+                         "frac": achieved / peak, "traffic": captured_traffic("shear", n * K),
+                         "traffic_note": "DRAM read+write per pass, scaled from a 200,000-galaxy ncu capture of "
+                                         "the same kernel source by the samples per pass",
+                         "kernel": "shear_kernel_async<1,0>",
                          "bytes_per_pass": bytes_per_pass, "peak_how": "measured copy bandwidth"},
             "gpu_launches": 2 * passes, "clocks": clk,
             "estimate": {"g": [float(x) for x in mean[:2]], "alpha": float(mean[2]),
