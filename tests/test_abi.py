@@ -83,3 +83,49 @@ def test_struct_layouts_match_header(tmp_path):
         py = structs[cn]
         got = C.sizeof(py) if f == "size" else getattr(py, f).offset
         assert got == int(v), (cn, f, got, v)
+
+
+def test_host_validation_of_plan_serve_and_sampler(L):
+    """Argument errors of the batching, serving and shear-sampling calls are
+    caught on the host, before any CUDA call."""
+    from paper_2604_22048_gb300 import _ffi
+    assert L.bs_fit_resident_galaxies(0, 53, 0) == 0          # n_chains < 1
+    assert L.bs_fit_resident_galaxies(4, 54, 0) == 0          # even side
+    assert L.bs_fit_resident_galaxies(4, 53, 100) == 0        # register cap not offered
+    # serving: NULL / undersized arena, bad stream count, bad register cap
+    cfg = _ffi.ServeCfg()
+    h = C.c_void_p()
+    assert L.bs_serve_create(None, None, 0, C.byref(h)) == -1
+    assert L.bs_serve_create(C.byref(cfg), C.c_void_p(1), 1 << 10, C.byref(h)) == -1
+    assert b"arena" in L.bs_last_error()
+    cfg.n_streams = 2
+    assert L.bs_serve_create(C.byref(cfg), C.c_void_p(1), 1 << 20, C.byref(h)) == -1
+    assert b"n_streams" in L.bs_last_error()
+    cfg.n_streams = 0
+    cfg.registers[1] = 100
+    assert L.bs_serve_create(C.byref(cfg), C.c_void_p(1), 1 << 20, C.byref(h)) == -1
+    assert b"registers" in L.bs_last_error()
+    # shear sampler: g must be free, flux/size parameters need lf/ls
+    d = _ffi.ShearData()
+    d.n_gal, d.K, d.family, d.sigma_e0 = 2, 4, 0, 0.3
+    sc = _ffi.ShearSampleCfg()
+    out = (C.c_double * 16)()
+    sc.free_mask = 0b100
+    assert L.bs_shear_sample(C.byref(d), C.byref(sc), out, None, None, None, None, 0, None) == -1
+    assert b"free_mask" in L.bs_last_error()
+    sc.free_mask = 0b1011
+    assert L.bs_shear_sample(C.byref(d), C.byref(sc), out, None, None, None, None, 0, None) == -1
+    assert b"lf and ls" in L.bs_last_error()
+    sc.free_mask = 0b11
+    sc.n_samples = 0
+    assert L.bs_shear_sample(C.byref(d), C.byref(sc), out, None, None, None, None, 0, None) == -1
+    # all-free likelihood: b must be NULL, sigma_f > 0
+    th = (C.c_double * 8)(0.0, 0.0, 0.2, 2.4, -0.1, 1.0, -0.4, 0.05)
+    im = (C.c_double * 4)(-1.0, 9.0, -2.0, 1.0)
+    assert L.bs_shear_loglike_full(None, None, None, im, th, out, 1, None, 0, None) == -1
+    # plan: unknown flags
+    a = _ffi.FitArgs()
+    o = _ffi.FitOut()
+    p = C.c_void_p()
+    assert L.bs_fit_plan_create(C.byref(a), C.byref(o), None, 8, None, 0, None, C.byref(p)) == -1
+    assert b"flags" in L.bs_last_error()
