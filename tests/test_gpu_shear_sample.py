@@ -85,3 +85,20 @@ def test_sample_all_free_factorises(cuda):
     for k, true in ((3, 2.45), (4, 0.4), (5, 14.0)):
         x = draws[:, k]
         assert abs(x.mean() - true) < 5 * x.std() + 0.05 * abs(true), (k, x.mean(), x.std(), true)
+
+
+def test_sample_allreduce_hook(cuda):
+    """A hook that doubles each evaluation stands for two ranks holding the same
+    galaxies: the posterior keeps its mean and narrows by sqrt(2)."""
+    e1, e2 = _interim_ellipticities(2000, 24, (0.02, -0.01), 45)
+    t = lambda a: torch.from_numpy(a).to(cuda)
+    plan = api.ShearPlan(t(e1), t(e2), family=O.EPRIOR_TRUNC_GAUSS, trunc_r=0.7)
+    th0 = [0.02, -0.01, 0.2, 2.45, 0.4, 14.0, -0.4, 0.05]
+    one, _ = plan.sample(th0, free=("g1", "g2"), n_warmup=300, n_samples=3000, seed=11)
+    two, info = plan.sample(th0, free=("g1", "g2"), n_warmup=300, n_samples=3000, seed=11,
+                            allreduce=lambda x: 2.0 * x)
+    assert info["accept_rate"] > 0.5
+    for k in range(2):
+        ratio = two[:, k].std() / one[:, k].std()
+        assert 0.6 < ratio < 0.85, (k, ratio)
+        assert abs(two[:, k].mean() - one[:, k].mean()) < 4.5 * math.hypot(_mcse(one[:, k]), _mcse(two[:, k]))
