@@ -60,20 +60,40 @@ struct GalCtx {
 //   odd slot:    [D (x, y): 64][T: 32]                        (last slot, NCT odd)
 __host__ __device__ __forceinline__ int row_floats(int npad) { return 3 * npad; }
 
+// Per-chain phase tables X(u) = exp(-2 pi i u dx / N) of one evaluation, in
+// the setup scratch (free once the galaxy is staged), extended when the
+// chains need more than it holds.
+// Per-chain stride of the phase tables: even, so that every table (read as
+// pairs X(u), X(u+1) with 16-byte loads, u even) starts 16-byte aligned.
+__host__ __device__ __forceinline__ int phase_stride(int h_max) { return (h_max + 1) & ~1; }
+
+// float2 slots of the scratch: the setup's two rows, or the chains' phase
+// tables if larger; even, so that the (kx, kx^2) table after it stays 16-byte
+// aligned.
+__host__ __device__ __forceinline__ int scratch_float2(int max_side, int h_max, int n_chains)
+{
+    const int setup = 2 * max_side + 4;
+    const int phase = n_chains * phase_stride(h_max);
+    const int n = setup > phase ? setup : phase;
+    return (n + 1) & ~1;
+}
+
 struct SmemView {
     float *tab;    // [h_max][3 npad] data spectrum and transfer, paired layout
     float2 *G;     // [max_side], setup scratch (one frequency row)
     float2 *tw;    // [max_side]
+    float2 *xph;   // [n_chains][phase_stride(h_max)] phase tables (aliases G, tw after setup)
     float2 *kxr;   // [h_max]: (kx, kx^2) of row u
 };
 
-__device__ __forceinline__ SmemView smem_view(unsigned char *base, int h_max, int npad, int max_side)
+__device__ __forceinline__ SmemView smem_view(unsigned char *base, int h_max, int npad, int max_side, int n_chains)
 {
     SmemView v;
     v.tab = reinterpret_cast<float *>(base);
     v.G = reinterpret_cast<float2 *>(v.tab + (size_t)h_max * row_floats(npad));
     v.tw = v.G + (size_t)max_side;
-    v.kxr = v.tw + (size_t)max_side;
+    v.xph = v.G;
+    v.kxr = v.G + (size_t)scratch_float2(max_side, h_max, n_chains);
     return v;
 }
 
@@ -372,26 +392,22 @@ __device__ __forceinline__ void row_terms(Sums<NCT> &S, const SlotConst<NCT> &K,
 template <int NCT, bool LL>
 __device__ __forceinline__ void half_plane(Sums<NCT> &S, const SlotConst<NCT> &K,
                                            const float *__restrict__ tab, const float2 *__restrict__ kxr,
-                                           int H, float al, float exr, float exi, float F2)
+                                           const float2 *__restrict__ xph, int H, float al, float F2)
 {
     constexpr int ROWF = 96 * NCT;
-    const float e2r = exr * exr - exi * exi, e2i = 2.0f * exr * exi;   // two-row step
-    float Xr = 1.0f, Xi = 0.0f;
     const float *row = tab;
     int u = 0;
     for (; u + 1 < H; u += 2) {
         const float4 k01 = *reinterpret_cast<const float4 *>(kxr + u);   // (kx, kx^2) of rows u, u+1
-        const float X1r = Xr * exr - Xi * exi, X1i = Xr * exi + Xi * exr;
-        row_terms<NCT, LL>(S, K, row, k01.x, k01.y, al, Xr, Xi, F2);
-        row_terms<NCT, LL>(S, K, row + ROWF, k01.z, k01.w, al, X1r, X1i, F2);
-        const float nXr = Xr * e2r - Xi * e2i;
-        Xi = Xr * e2i + Xi * e2r;
-        Xr = nXr;
+        const float4 x01 = *reinterpret_cast<const float4 *>(xph + u);   // X(u), X(u+1)
+        row_terms<NCT, LL>(S, K, row, k01.x, k01.y, al, x01.x, x01.y, F2);
+        row_terms<NCT, LL>(S, K, row + ROWF, k01.z, k01.w, al, x01.z, x01.w, F2);
         row += 2 * ROWF;
     }
     if (u < H) {
         const float2 k0 = kxr[u];
-        row_terms<NCT, LL>(S, K, row, k0.x, k0.y, al, Xr, Xi, F2);
+        const float2 x0 = xph[u];
+        row_terms<NCT, LL>(S, K, row, k0.x, k0.y, al, x0.x, x0.y, F2);
     }
 }
 
@@ -431,7 +447,8 @@ __device__ __forceinline__ void warp_sum7(float (&v)[7])
 template <int NC>
 __device__ __forceinline__ double eval_logpost(const FitParams &P, const GalCtx &gc,
                                                const float *__restrict__ tab, const float2 *__restrict__ kxr,
-                                               const float vcol[NC], const float th[6], float g[6], bool want_ll)
+                                               float2 *__restrict__ xph, const float vcol[NC], const float th[6],
+                                               float g[6], bool want_ll)
 {
     const float F = exp10f(th[0]);
     const float r0 = exp10f(th[1]) * (1.0f / kHlrOverR0);
@@ -445,8 +462,16 @@ __device__ __forceinline__ double eval_logpost(const FitParams &P, const GalCtx 
     const float F2 = F * F;
     const float dk = gc.dk;
 
-    float exr, exi;                                        // exp(-2 pi i dx / N)
-    sincospif(-2.0f * th[4] * gc.invN, &exi, &exr);
+    // this chain's phase table X(u) = exp(-2 pi i u dx / N), u < H
+    {
+        const int lane = threadIdx.x & 31;
+        for (int u = lane; u < gc.H; u += 32) {
+            float sx, cx;
+            sincospif(-2.0f * th[4] * (float)u * gc.invN, &sx, &cx);
+            xph[u] = make_float2(cx, sx);
+        }
+        __syncwarp();
+    }
     float Yr[NC], Yi[NC], cst[NC], gky[NC], ky[NC];
 #pragma unroll
     for (int j = 0; j < NC; ++j) {
@@ -487,9 +512,10 @@ __device__ __forceinline__ double eval_logpost(const FitParams &P, const GalCtx 
     S.chi_hi = f2(0.f);
     S.chi_lo = f2(0.f);
     if (want_ll)
-        half_plane<NC, true>(S, K, tab, kxr, gc.H, al, exr, exi, F2);
+        half_plane<NC, true>(S, K, tab, kxr, xph, gc.H, al, F2);
     else
-        half_plane<NC, false>(S, K, tab, kxr, gc.H, al, exr, exi, F2);
+        half_plane<NC, false>(S, K, tab, kxr, xph, gc.H, al, F2);
+    __syncwarp();   // the table is rewritten by the next evaluation
 
     float Sa = S.Sa.x + S.Sa.y, Swkx2 = S.Swkx2.x + S.Swkx2.y, Sbkx = S.Sbkx.x + S.Sbkx.y;
     float Sw = 0.f, Swky2 = 0.f, Swkxky = 0.f, Sbky = 0.f;
@@ -650,7 +676,8 @@ __device__ void run_chain(const FitParams &P, const GalCtx &gc, const SmemView &
             for (int k = 0; k < 6; ++k) x[k] = __shfl_sync(BS_FULL_MASK, tp, k);
             if (!in_support(P, x)) { ok = false; break; }
             float gg[6];
-            const double v = eval_logpost<NC>(P, gc, sm.tab, sm.kxr, vcol, x, gg, l == nst - 1);
+            const double v = eval_logpost<NC>(P, gc, sm.tab, sm.kxr, sm.xph + (size_t)chain * phase_stride(P.h_max), vcol, x, gg,
+                                              l == nst - 1);
             ++ngrad;
             if (l == nst - 1) lpp = v;
             gp = pick6(gg, pi);
@@ -804,7 +831,7 @@ __device__ __forceinline__ void fit_loop(const FitParams &P)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_gal;
-    const SmemView sm = smem_view(smem_raw, P.h_max, P.npad, P.max_side);
+    const SmemView sm = smem_view(smem_raw, P.h_max, P.npad, P.max_side, P.n_chains);
     const int warp = threadIdx.x >> 5;
     bool first = true;
     for (;;) {
@@ -862,7 +889,7 @@ __device__ void point_eval(const FitParams &P, const GalCtx &gc, const SmemView 
     for (int i = 0; i < 6; ++i) th[i] = theta[i];
     double v = -INFINITY;
     if (in_support(P, th)) {
-        v = eval_logpost<NC>(P, gc, sm.tab, sm.kxr, vcol, th, g, true);
+        v = eval_logpost<NC>(P, gc, sm.tab, sm.kxr, sm.xph, vcol, th, g, true);
     } else {
 #pragma unroll
         for (int i = 0; i < 6; ++i) g[i] = NAN;
@@ -877,7 +904,7 @@ __global__ void __launch_bounds__(32) logpost_points_kernel(const FitParams P, i
                                                             float *grad)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const SmemView sm = smem_view(smem_raw, P.h_max, P.npad, P.max_side);
+    const SmemView sm = smem_view(smem_raw, P.h_max, P.npad, P.max_side, 1);
     for (int i = blockIdx.x; i < n_points; i += gridDim.x) {
         const int gal = gal_index[i];
         if (gal < 0 || gal >= P.n_gal || !side_ok(P, P.side[gal])) {
@@ -932,18 +959,18 @@ FitKernel fit_kernel_for(int max_side, int regs, int n_chains)
 
 }  // namespace
 
-size_t fit_smem_bytes(int max_side)
+size_t fit_smem_bytes(int max_side, int n_chains)
 {
     const int h = (max_side + 1) / 2;
     const int npad = 32 * ((max_side + 31) / 32);
-    return (size_t)h * row_floats(npad) * sizeof(float) + 2 * (size_t)max_side * sizeof(float2) +
-           (size_t)(h + 1) * sizeof(float2);
+    return (size_t)h * row_floats(npad) * sizeof(float) +
+           (size_t)scratch_float2(max_side, h, n_chains) * sizeof(float2) + (size_t)(h + 1) * sizeof(float2);
 }
 
 int fit_blocks_per_sm(int n_chains, int max_side, int regs)
 {
     int nb = 0;
-    const size_t smem = fit_smem_bytes(max_side);
+    const size_t smem = fit_smem_bytes(max_side, n_chains);
     FitKernel k = fit_kernel_for(max_side, regs, n_chains);
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, 32 * n_chains, smem) != cudaSuccess)
@@ -953,7 +980,7 @@ int fit_blocks_per_sm(int n_chains, int max_side, int regs)
 
 cudaError_t launch_fit(const FitParams &p, int grid, cudaStream_t stream)
 {
-    const size_t smem = fit_smem_bytes(p.max_side);
+    const size_t smem = fit_smem_bytes(p.max_side, p.n_chains);
     FitKernel k = fit_kernel_for(p.max_side, p.regs, p.n_chains);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -965,7 +992,7 @@ cudaError_t launch_logpost_points(const FitParams &p, int n_points, const int32_
                                   const float *theta, double *logp, float *grad,
                                   cudaStream_t stream)
 {
-    const size_t smem = fit_smem_bytes(p.max_side);
+    const size_t smem = fit_smem_bytes(p.max_side, 1);
     cudaError_t e = cudaFuncSetAttribute(logpost_points_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

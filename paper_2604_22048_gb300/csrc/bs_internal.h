@@ -63,8 +63,8 @@ struct FitParams {
     long long pub_shift;
 };
 
-// Shared memory bytes per CTA for a given max stamp side.
-size_t fit_smem_bytes(int max_side);
+// Shared memory bytes per CTA for a given max stamp side and chains per galaxy.
+size_t fit_smem_bytes(int max_side, int n_chains);
 // Launch helpers implemented in the .cu files.
 cudaError_t launch_fit(const FitParams &p, int grid, cudaStream_t stream);
 int fit_blocks_per_sm(int n_chains, int max_side, int regs = 0);
