@@ -129,3 +129,42 @@ def test_serve_rejects_bad_requests(cuda, data):
         assert srv.stats()["submitted"] == 0
     finally:
         srv.close()
+
+
+def test_serve_stress_bursts_and_teardown(cuda, data):
+    """Random bursts of all four slot classes through a 4 MiB arena with at
+    most 24 requests on the GPU: every request completes exactly once with a
+    clean status, the counters agree and the arena drains; a server destroyed
+    with requests still queued and running shuts down cleanly."""
+    rng = np.random.default_rng(3)
+    cfg = api.FitConfig(n_chains=4, n_warmup=20, n_samples=10, n_leapfrog=4, seed=5)
+    truth, flat, offs, sides, init, gal_id = data
+    srv = api.Server(cfg, max_side=101, arena_bytes=4 << 20, max_inflight=24, batch_us=100)
+    n_total, sent, got = 600, 0, {}
+    try:
+        while len(got) < n_total:
+            if sent < n_total and rng.uniform() < 0.3:
+                k = int(min(rng.integers(1, 40), n_total - sent))
+                idx = rng.integers(0, len(SIDES), k)
+                srv.submit(api.Server.requests(flat, offs[idx], sides[idx], "moffat", truth.psf_fwhm[idx], 3.0,
+                                               np.ones(k, np.float32), init, gal_id[idx],
+                                               tags=np.arange(sent, sent + k), init_index=idx))
+                sent += k
+            for c in srv.poll(timeout_us=2000):
+                tag = int(c["tag"])
+                assert tag not in got
+                assert c["status"] == 0
+                got[tag] = int(c["side"])
+        srv.poll()           # release the last completions
+        st = srv.stats()
+        assert st["submitted"] == st["admitted"] == st["completed"] == n_total
+        assert st["inflight"] == 0 and st["pending"] == 0 and st["arena_used"] == 0
+        assert 0 < st["arena_high_water"] <= 4 << 20
+    finally:
+        srv.close()
+    # teardown with work in flight
+    srv = api.Server(cfg, max_side=101, arena_bytes=4 << 20)
+    idx = np.arange(len(SIDES)).repeat(20)
+    srv.submit(api.Server.requests(flat, offs[idx], sides[idx], "moffat", truth.psf_fwhm[idx], 3.0,
+                                   np.ones(len(idx), np.float32), init, gal_id[idx], init_index=idx))
+    srv.close()
