@@ -81,11 +81,11 @@ __device__ __forceinline__ float2 sub2(float2 a, float2 b)
 struct ShearConst {
     float2 g1, g2, ng1, ng2;         // g, -g
     float2 a2n, an, nan, nk;         // -a2 (log2 units), a = 1/(2 alpha^2), -a, -kappa
-    float2 c0, lgk;                  // log2(e)/(2 sigma_e0^2); multiplier of the log term
+    float2 c0;                       // log2(e)/(2 sigma_e0^2)
     float r2;
 };
 
-__device__ __forceinline__ ShearConst shear_const(const ShearLaunch &s, int family)
+__device__ __forceinline__ ShearConst shear_const(const ShearLaunch &s)
 {
     ShearConst c;
     const float a = s.a2 * kLn2;
@@ -98,20 +98,22 @@ __device__ __forceinline__ ShearConst shear_const(const ShearLaunch &s, int fami
     c.nan = f2(-a);
     c.nk = f2(-s.kappa);
     c.c0 = f2(s.c0);
-    // BA14: -kappa log2 U; truncated Gaussian: -2 log2 U - 2 log2(1 - |eps'|^2)
-    // = -2 log2(U (1 - |eps'|^2)) (kappa = 2), one logarithm
-    c.lgk = f2(family == BS_EPRIOR_TRUNC_GAUSS ? -2.0f : -s.kappa);
     c.r2 = s.r2;
     return c;
 }
 
-// Two samples: log2 weights x and the factors of the derivatives,
+// Two samples: the weight split as exp2(x) f, with x = c0 |eps'|^2 -
+// a2 Q (+ b log2 e) the exponent and f the power of U the log term stands for:
+//   BA14:               -4 log2 U                    -> f = (1/U)^4
+//   truncated Gaussian: -2 log2 U - 2 log2(1 - |eps'|^2) -> f = (1/(U (1 - |eps'|^2)))^2
+// (f lies in about [0.004, 16], so it cannot overflow a weight; no logarithm
+// per sample), and the factors of the derivatives,
 //   dx/dg_i = -2 rU c_i,  c_i = du_i (a Q - kappa) - a n_i,  n = eps' - g;
 // the -2 is applied once per galaxy.  n is formed explicitly (not expanded
 // through |eps'|^2 - 2 g.eps' + |g|^2, which cancels when eps' is near g).
 template <int FAMILY, bool HAS_B>
 __device__ __forceinline__ void pair_terms(const ShearConst &c, float2 e1, float2 e2, float2 bv, float2 &x,
-                                           float2 &ru, float2 &c1, float2 &c2, float2 &q)
+                                           float2 &fw, float2 &ru, float2 &c1, float2 &c2, float2 &q)
 {
     const float2 ur = fma2(c.ng1, e1, fma2(c.ng2, e2, f2(1.0f)));
     const float2 nvi = fma2(c.g2, e1, mul2(c.ng1, e2));          // -(g1 e2 - g2 e1)
@@ -119,12 +121,20 @@ __device__ __forceinline__ void pair_terms(const ShearConst &c, float2 e1, float
     const float2 Ep = fma2(e1, e1, mul2(e2, e2));
     const float2 n1 = sub2(e1, c.g1), n2 = sub2(e2, c.g2);
     const float2 Nn = fma2(n1, n1, mul2(n2, n2));
-    const float2 rU = make_float2(rcp_ftz(U.x), rcp_ftz(U.y));
+    float2 rU, f;
+    if (FAMILY == BS_EPRIOR_TRUNC_GAUSS) {
+        const float2 om = sub2(f2(1.0f), Ep);
+        const float2 uo = mul2(U, om);
+        const float2 r = make_float2(rcp_ftz(uo.x), rcp_ftz(uo.y));   // 1 / (U (1 - |eps'|^2))
+        rU = mul2(r, om);
+        f = mul2(r, r);
+    } else {
+        rU = make_float2(rcp_ftz(U.x), rcp_ftz(U.y));
+        const float2 r2 = mul2(rU, rU);
+        f = mul2(r2, r2);
+    }
     const float2 Q = mul2(Nn, rU);
-    float2 larg = U;
-    if (FAMILY == BS_EPRIOR_TRUNC_GAUSS) larg = mul2(U, sub2(f2(1.0f), Ep));
-    const float2 lg = make_float2(lg2_ftz(larg.x), lg2_ftz(larg.y));
-    float2 xx = fma2(c.c0, Ep, fma2(c.lgk, lg, mul2(c.a2n, Q)));
+    float2 xx = fma2(c.c0, Ep, mul2(c.a2n, Q));
     if (FAMILY == BS_EPRIOR_TRUNC_GAUSS) {
         if (!(Q.x < c.r2)) xx.x = -INFINITY;
         if (!(Q.y < c.r2)) xx.y = -INFINITY;
@@ -135,6 +145,7 @@ __device__ __forceinline__ void pair_terms(const ShearConst &c, float2 e1, float
     const float2 du2 = sub2(mul2(ur, e2), mul2(nvi, e1));        // ur e2 + vi e1
     c1 = fma2(du1, aqk, mul2(c.nan, n1));
     c2 = fma2(du2, aqk, mul2(c.nan, n2));
+    fw = f;
     ru = rU;
     q = Q;
     x = xx;
@@ -177,12 +188,13 @@ struct Lse {
 template <int FAMILY, bool HAS_B>
 __device__ __forceinline__ void eval_chunk(const ShearConst &c, const Chunk &ch, Lse &L)
 {
-    float2 x[2], ru[2], c1[2], c2[2], qq[2];
+    float2 x[2], fw[2], ru[2], c1[2], c2[2], qq[2];
     const float2 e1[2] = {make_float2(ch.e1.x, ch.e1.y), make_float2(ch.e1.z, ch.e1.w)};
     const float2 e2[2] = {make_float2(ch.e2.x, ch.e2.y), make_float2(ch.e2.z, ch.e2.w)};
     const float2 bb[2] = {make_float2(ch.b.x, ch.b.y), make_float2(ch.b.z, ch.b.w)};
 #pragma unroll
-    for (int h = 0; h < 2; ++h) pair_terms<FAMILY, HAS_B>(c, e1[h], e2[h], bb[h], x[h], ru[h], c1[h], c2[h], qq[h]);
+    for (int h = 0; h < 2; ++h)
+        pair_terms<FAMILY, HAS_B>(c, e1[h], e2[h], bb[h], x[h], fw[h], ru[h], c1[h], c2[h], qq[h]);
     if (!ch.full) {
         if (ch.nvalid < 4) x[1].y = -INFINITY;
         if (ch.nvalid < 3) x[1].x = -INFINITY;
@@ -202,7 +214,7 @@ __device__ __forceinline__ void eval_chunk(const ShearConst &c, const Chunk &ch,
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         const float2 d = add2(x[h], nm);
-        const float2 e = make_float2(ex2_ftz(d.x), ex2_ftz(d.y));
+        const float2 e = mul2(make_float2(ex2_ftz(d.x), ex2_ftz(d.y)), fw[h]);
         const float2 er = mul2(e, ru[h]);
         L.sw = add2(L.sw, e);
         L.t1 = fma2(er, c1[h], L.t1);
@@ -286,7 +298,7 @@ __global__ void __launch_bounds__(kShearThreads, 3) shear_kernel(const ShearLaun
     const unsigned gmask = 0xFFu << (lane & ~(kGroup - 1));
     const long long group = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / kGroup;
     const long long ngroups = (long long)gridDim.x * blockDim.x / kGroup;
-    const ShearConst c = shear_const(s, FAMILY);
+    const ShearConst c = shear_const(s);
     const int K = s.K;
     double av = 0.0, a1 = 0.0, a2 = 0.0, aq = 0.0;
 
@@ -339,7 +351,7 @@ __host__ __device__ constexpr size_t async_smem_bytes(bool has_b)
 // does not drain between galaxies.  A lane only reads the slots it filled,
 // after cp.async.wait_group; no barrier is needed.
 template <int FAMILY, bool HAS_B>
-__global__ void __launch_bounds__(kShearThreads, 4) shear_kernel_async(const ShearLaunch s)
+__global__ void __launch_bounds__(kShearThreads, 3) shear_kernel_async(const ShearLaunch s)
 {
     extern __shared__ float4 sbuf[];
     constexpr int NV = HAS_B ? 3 : 2;
@@ -349,7 +361,7 @@ __global__ void __launch_bounds__(kShearThreads, 4) shear_kernel_async(const She
     const unsigned gmask = 0xFFu << (lane & ~(kGroup - 1));
     const long long group = ((long long)blockIdx.x * blockDim.x + tid) / kGroup;
     const long long ngroups = (long long)gridDim.x * blockDim.x / kGroup;
-    const ShearConst c = shear_const(s, FAMILY);
+    const ShearConst c = shear_const(s);
     const int K = s.K;
     constexpr int span = kChunk * kGroup;                    // samples of a group per chunk step
     const int cpg = (K + span - 1) / span;                   // chunks per galaxy per lane
