@@ -111,6 +111,13 @@ def lib():
         L.or_shear_loglike.restype = C.c_double
         L.or_shear_loglike.argtypes = [_F, _F, _F, C.c_int64, C.c_int, C.c_int, C.c_double,
                                        C.c_double, C.c_double, C.c_double, C.c_double, _D]
+        L.or_shear_loglike_w.restype = C.c_double
+        L.or_shear_loglike_w.argtypes = [_F, _F, _F, _F, C.c_int64, C.c_int, C.c_int, C.c_double,
+                                         C.c_double, C.c_double, C.c_double, C.c_double, _D]
+        L.or_shear_estimate_w.restype = C.c_int
+        L.or_shear_estimate_w.argtypes = [_F, _F, _F, _F, C.c_int64, C.c_int, C.c_int, C.c_double,
+                                          C.c_double, C.c_int, C.c_double, C.c_double, C.c_double,
+                                          C.c_int, _D, _D]
         L.or_shear_estimate.restype = C.c_int
         L.or_shear_estimate.argtypes = [_F, _F, _F, C.c_int64, C.c_int, C.c_int, C.c_double,
                                         C.c_double, C.c_int, C.c_double, C.c_double, C.c_double,
@@ -374,15 +381,17 @@ def _f32(a):
 
 
 def shear_loglike(e1p, e2p, g1, g2, alpha, *, b=None, family=EPRIOR_BA14, trunc_r=0.7,
-                  sigma_e0=0.3):
-    """e1p, e2p: [n_gal, K] float32.  Returns (value, grad[3])."""
+                  sigma_e0=0.3, weights=None):
+    """e1p, e2p: [n_gal, K] float32; weights: per-galaxy weights or None.
+    Returns (value, grad[3])."""
     e1p = _f32(e1p)
     e2p = _f32(e2p)
     n_gal, K = e1p.shape
     bb = _f32(b) if b is not None else None
+    ww = _f32(weights) if weights is not None else None
     g = np.zeros(3)
-    v = lib().or_shear_loglike(_fp(e1p), _fp(e2p), _fp(bb), n_gal, K, family, trunc_r, sigma_e0,
-                               g1, g2, alpha, _dp(g))
+    v = lib().or_shear_loglike_w(_fp(e1p), _fp(e2p), _fp(bb), _fp(ww), n_gal, K, family, trunc_r, sigma_e0,
+                                 g1, g2, alpha, _dp(g))
     return v, g
 
 
@@ -409,15 +418,16 @@ def shear_loglike_full(e1p, e2p, lfp, lsp, theta, *, family=EPRIOR_BA14, trunc_r
 
 
 def shear_estimate(e1p, e2p, *, b=None, family=EPRIOR_BA14, trunc_r=0.7, sigma_e0=0.3,
-                   free_alpha=False, alpha=0.2, alpha_lo=1e-4, alpha_hi=1.0, n_gh=7):
+                   free_alpha=False, alpha=0.2, alpha_lo=1e-4, alpha_hi=1.0, n_gh=7, weights=None):
     e1p = _f32(e1p)
     e2p = _f32(e2p)
     n_gal, K = e1p.shape
     bb = _f32(b) if b is not None else None
+    ww = _f32(weights) if weights is not None else None
     mean = np.zeros(3)
     cov = np.zeros(9)
-    st = lib().or_shear_estimate(_fp(e1p), _fp(e2p), _fp(bb), n_gal, K, family, trunc_r, sigma_e0,
-                                 int(free_alpha), alpha, alpha_lo, alpha_hi, n_gh, _dp(mean), _dp(cov))
+    st = lib().or_shear_estimate_w(_fp(e1p), _fp(e2p), _fp(bb), _fp(ww), n_gal, K, family, trunc_r, sigma_e0,
+                                   int(free_alpha), alpha, alpha_lo, alpha_hi, n_gh, _dp(mean), _dp(cov))
     if st != 0:
         raise RuntimeError("oracle shear estimate failed")
     n = 3 if free_alpha else 2

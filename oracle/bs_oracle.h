@@ -187,6 +187,20 @@ double or_shear_loglike(const float *e1p, const float *e2p, const float *b,
                         double sigma_e0, double g1, double g2, double alpha,
                         double grad[3]);
 
+/* The same with per-galaxy weights w[n_gal] (NULL = 1): value and gradient
+ * are sum_n w_n [log sum_k w_nk - log K] and its derivatives -- with integer
+ * weights, the likelihood of the sample in which galaxy n appears w_n times
+ * (the bootstrap of Sec. 3.4's m and c). */
+double or_shear_loglike_w(const float *e1p, const float *e2p, const float *b, const float *w,
+                          int64_t n_gal, int K, int family, double trunc_r,
+                          double sigma_e0, double g1, double g2, double alpha,
+                          double grad[3]);
+int or_shear_estimate_w(const float *e1p, const float *e2p, const float *b, const float *w,
+                        int64_t n_gal, int K, int family, double trunc_r,
+                        double sigma_e0, int free_alpha, double alpha_fixed,
+                        double alpha_lo, double alpha_hi, int n_gh,
+                        double *mean, double *cov);
+
 /* Standard normal log CDF, log Phi(t), stable in both tails. */
 double or_log_ndtr(double t);
 /* Log density of the skew normal of Eq. lflux-lsize-dist: location mu,

@@ -141,6 +141,14 @@ double or_shear_loglike(const float *e1p, const float *e2p, const float *b,
                         double sigma_e0, double g1, double g2, double alpha,
                         double grad[3])
 {
+    return or_shear_loglike_w(e1p, e2p, b, NULL, n_gal, K, family, trunc_r, sigma_e0, g1, g2, alpha, grad);
+}
+
+double or_shear_loglike_w(const float *e1p, const float *e2p, const float *b, const float *w,
+                          int64_t n_gal, int K, int family, double trunc_r,
+                          double sigma_e0, double g1, double g2, double alpha,
+                          double grad[3])
+{
     double dlz = dlogz_dalpha(family, alpha, trunc_r);
     double *lw = malloc(sizeof(double) * K);
     double (*dl)[3] = malloc(sizeof(double[3]) * K);
@@ -154,18 +162,20 @@ double or_shear_loglike(const float *e1p, const float *e2p, const float *b,
                     (b ? (double)b[j] : 0.0);
             if (lw[k] > mx) mx = lw[k];
         }
+        double wn = w ? (double)w[n] : 1.0;
+        if (wn == 0.0) continue;
         if (!isfinite(mx)) {
             total = -INFINITY;
             continue;
         }
         double s = 0.0;
         for (int k = 0; k < K; ++k) s += exp(lw[k] - mx);
-        total += mx + log(s) - log((double)K);
+        total += wn * (mx + log(s) - log((double)K));
         if (grad)
             for (int k = 0; k < K; ++k) {
                 double pk = exp(lw[k] - mx) / s;
                 if (pk == 0.0) continue;
-                for (int i = 0; i < 3; ++i) G[i] += pk * dl[k][i];
+                for (int i = 0; i < 3; ++i) G[i] += wn * pk * dl[k][i];
             }
     }
     free(lw);
@@ -309,7 +319,7 @@ int or_gauss_hermite(int n, double *x, double *w)
 }
 
 typedef struct {
-    const float *e1p, *e2p, *b;
+    const float *e1p, *e2p, *b, *w;
     int64_t n_gal;
     int K, family;
     double trunc_r, sigma_e0;
@@ -328,7 +338,7 @@ static double sfun(const sdat_t *d, const double *x, double *gr)
 {
     double a = d->free_alpha ? x[2] : d->alpha_fixed;
     double g3[3];
-    double v = or_shear_loglike(d->e1p, d->e2p, d->b, d->n_gal, d->K, d->family, d->trunc_r,
+    double v = or_shear_loglike_w(d->e1p, d->e2p, d->b, d->w, d->n_gal, d->K, d->family, d->trunc_r,
                                 d->sigma_e0, x[0], x[1], a, gr ? g3 : NULL);
     if (gr) {
         gr[0] = g3[0]; gr[1] = g3[1];
@@ -382,7 +392,17 @@ int or_shear_estimate(const float *e1p, const float *e2p, const float *b,
                       double alpha_lo, double alpha_hi, int n_gh,
                       double *mean, double *cov)
 {
-    sdat_t d = {e1p, e2p, b, n_gal, K, family, trunc_r, sigma_e0,
+    return or_shear_estimate_w(e1p, e2p, b, NULL, n_gal, K, family, trunc_r, sigma_e0, free_alpha, alpha_fixed,
+                               alpha_lo, alpha_hi, n_gh, mean, cov);
+}
+
+int or_shear_estimate_w(const float *e1p, const float *e2p, const float *b, const float *w,
+                        int64_t n_gal, int K, int family, double trunc_r,
+                        double sigma_e0, int free_alpha, double alpha_fixed,
+                        double alpha_lo, double alpha_hi, int n_gh,
+                        double *mean, double *cov)
+{
+    sdat_t d = {e1p, e2p, b, w, n_gal, K, family, trunc_r, sigma_e0,
                 free_alpha, alpha_fixed, alpha_lo, alpha_hi};
     int n = free_alpha ? 3 : 2;
     double x[3] = {0.0, 0.0, alpha_fixed};

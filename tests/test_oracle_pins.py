@@ -457,3 +457,23 @@ def test_full_loglike_gradient_by_central_differences():
             fd = (O.shear_loglike_full(e1, e2, lf, ls, tp, family=fam)[0] -
                   O.shear_loglike_full(e1, e2, lf, ls, tm, family=fam)[0]) / (2 * h)
             assert abs(g[i] - fd) <= 2e-5 * max(1.0, abs(fd)), (fam, i, g[i], fd)
+
+
+def test_weighted_likelihood_equals_duplicated_galaxies():
+    """Integer galaxy weights (a bootstrap resample) give exactly the likelihood
+    of the sample in which each galaxy appears that many times; weight 0
+    removes a galaxy."""
+    rng = np.random.default_rng(31)
+    n, K = 7, 11
+    e1 = (0.3 * rng.uniform(-1, 1, (n, K))).astype(np.float32)
+    e2 = (0.3 * rng.uniform(-1, 1, (n, K))).astype(np.float32)
+    w = np.array([0, 1, 2, 3, 1, 0, 2], dtype=np.float32)
+    rep = np.repeat(np.arange(n), w.astype(int))
+    for fam in (O.EPRIOR_BA14, O.EPRIOR_TRUNC_GAUSS):
+        vw, gw = O.shear_loglike(e1, e2, 0.03, -0.02, 0.25, family=fam, weights=w)
+        vr, gr = O.shear_loglike(e1[rep], e2[rep], 0.03, -0.02, 0.25, family=fam)
+        assert abs(vw - vr) <= 1e-12 * max(1.0, abs(vr))
+        assert np.allclose(gw, gr, rtol=1e-12, atol=1e-12)
+    mw, cw = O.shear_estimate(e1, e2, family=O.EPRIOR_BA14, alpha=0.25, weights=w)
+    mr, cr = O.shear_estimate(e1[rep], e2[rep], family=O.EPRIOR_BA14, alpha=0.25)
+    assert np.allclose(mw, mr, rtol=1e-9, atol=1e-12) and np.allclose(cw, cr, rtol=1e-8, atol=1e-14)
