@@ -129,6 +129,9 @@ def lib():
         L.or_shear_loglike_full.restype = C.c_double
         L.or_shear_loglike_full.argtypes = [_F, _F, _F, _F, C.c_int64, C.c_int, C.c_int, C.c_double,
                                             C.c_double, _D, _D, _D]
+        L.or_shear_loglike_full_w.restype = C.c_double
+        L.or_shear_loglike_full_w.argtypes = [_F, _F, _F, _F, _F, C.c_int64, C.c_int, C.c_int, C.c_double,
+                                              C.c_double, _D, _D, _D]
         L.or_gauss_hermite.restype = C.c_int
         L.or_gauss_hermite.argtypes = [C.c_int, _D, _D]
         for nm in ("or_shear_apply", "or_shear_invert"):
@@ -404,16 +407,17 @@ def log_skewnorm(x, mu, sigma, a):
 
 
 def shear_loglike_full(e1p, e2p, lfp, lsp, theta, *, family=EPRIOR_BA14, trunc_r=0.7, sigma_e0=0.3,
-                       interim=(-1.0, 9.0, -2.0, 1.0)):
+                       interim=(-1.0, 9.0, -2.0, 1.0), weights=None):
     """All-free shear likelihood; theta = (g1, g2, sigma_e, mu_f, sigma_f, a_f,
-    mu_s, sigma_s).  Returns (value, grad[8])."""
+    mu_s, sigma_s); optional per-galaxy weights.  Returns (value, grad[8])."""
     e1p, e2p, lfp, lsp = _f32(e1p), _f32(e2p), _f32(lfp), _f32(lsp)
+    ww = _f32(weights) if weights is not None else None
     n_gal, K = e1p.shape
     th = np.ascontiguousarray(theta, dtype=np.float64)
     im = np.ascontiguousarray(interim, dtype=np.float64)
     g = np.zeros(8)
-    v = lib().or_shear_loglike_full(_fp(e1p), _fp(e2p), _fp(lfp), _fp(lsp), n_gal, K, family, trunc_r, sigma_e0,
-                                    _dp(im), _dp(th), _dp(g))
+    v = lib().or_shear_loglike_full_w(_fp(e1p), _fp(e2p), _fp(lfp), _fp(lsp), _fp(ww), n_gal, K, family, trunc_r,
+                                      sigma_e0, _dp(im), _dp(th), _dp(g))
     return v, g
 
 

@@ -217,6 +217,11 @@ double or_log_skewnorm(double x, double mu, double sigma, double a);
 double or_shear_loglike_full(const float *e1p, const float *e2p, const float *lfp, const float *lsp,
                              int64_t n_gal, int K, int family, double trunc_r, double sigma_e0,
                              const double interim[4], const double theta[8], double grad[8]);
+/* The same with per-galaxy weights w[n] (NULL: all 1) on each galaxy's term,
+ * as or_shear_loglike_w. */
+double or_shear_loglike_full_w(const float *e1p, const float *e2p, const float *lfp, const float *lsp,
+                               const float *w, int64_t n_gal, int K, int family, double trunc_r, double sigma_e0,
+                               const double interim[4], const double theta[8], double grad[8]);
 
 /* Posterior mean of (g1, g2[, alpha]) under a uniform prior on the unit disk
  * (and alpha ~ U(alpha_lo, alpha_hi) when free_alpha): Newton to the mode on

@@ -225,9 +225,9 @@ static double flux_size_log_weight(double lf, double ls, const double hyp[5], co
     return lw;
 }
 
-double or_shear_loglike_full(const float *e1p, const float *e2p, const float *lfp, const float *lsp,
-                             int64_t n_gal, int K, int family, double trunc_r, double sigma_e0,
-                             const double interim[4], const double theta[8], double grad[8])
+double or_shear_loglike_full_w(const float *e1p, const float *e2p, const float *lfp, const float *lsp,
+                               const float *w, int64_t n_gal, int K, int family, double trunc_r, double sigma_e0,
+                               const double interim[4], const double theta[8], double grad[8])
 {
     const double g1 = theta[0], g2 = theta[1], alpha = theta[2];
     const double *hyp = theta + 3;
@@ -236,7 +236,8 @@ double or_shear_loglike_full(const float *e1p, const float *e2p, const float *lf
     double (*dl)[8] = malloc(sizeof(double[8]) * K);
     double total = 0.0, G[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (int64_t n = 0; n < n_gal; ++n) {
-        double mx = -INFINITY;
+        double wn = w ? (double)w[n] : 1.0, mx = -INFINITY;
+        if (wn == 0.0) continue;
         for (int k = 0; k < K; ++k) {
             size_t j = (size_t)n * K + k;
             lw[k] = eps_log_weight((double)e1p[j], (double)e2p[j], family, trunc_r, sigma_e0, g1, g2, alpha, dlz,
@@ -250,18 +251,26 @@ double or_shear_loglike_full(const float *e1p, const float *e2p, const float *lf
         }
         double s = 0.0;
         for (int k = 0; k < K; ++k) s += exp(lw[k] - mx);
-        total += mx + log(s) - log((double)K);
+        total += wn * (mx + log(s) - log((double)K));
         if (grad)
             for (int k = 0; k < K; ++k) {
                 double pk = exp(lw[k] - mx) / s;
                 if (pk == 0.0) continue;
-                for (int i = 0; i < 8; ++i) G[i] += pk * dl[k][i];
+                for (int i = 0; i < 8; ++i) G[i] += wn * pk * dl[k][i];
             }
     }
     free(lw);
     free(dl);
     if (grad) memcpy(grad, G, sizeof G);
     return total;
+}
+
+double or_shear_loglike_full(const float *e1p, const float *e2p, const float *lfp, const float *lsp,
+                             int64_t n_gal, int K, int family, double trunc_r, double sigma_e0,
+                             const double interim[4], const double theta[8], double grad[8])
+{
+    return or_shear_loglike_full_w(e1p, e2p, lfp, lsp, NULL, n_gal, K, family, trunc_r, sigma_e0, interim, theta,
+                                   grad);
 }
 
 /* ---- Gauss-Hermite by Golub-Welsch: nodes are the eigenvalues of the

@@ -474,6 +474,12 @@ def test_weighted_likelihood_equals_duplicated_galaxies():
         vr, gr = O.shear_loglike(e1[rep], e2[rep], 0.03, -0.02, 0.25, family=fam)
         assert abs(vw - vr) <= 1e-12 * max(1.0, abs(vr))
         assert np.allclose(gw, gr, rtol=1e-12, atol=1e-12)
+    lf = rng.uniform(1.5, 4.0, (n, K)).astype(np.float32)
+    ls = rng.uniform(-1.0, 0.3, (n, K)).astype(np.float32)
+    th = (0.03, -0.02, 0.25, 2.45, 0.4, 5.0, -0.4, 0.2)
+    vw, gw = O.shear_loglike_full(e1, e2, lf, ls, th, weights=w)
+    vr, gr = O.shear_loglike_full(e1[rep], e2[rep], lf[rep], ls[rep], th)
+    assert abs(vw - vr) <= 1e-12 * max(1.0, abs(vr)) and np.allclose(gw, gr, rtol=1e-12, atol=1e-12)
     mw, cw = O.shear_estimate(e1, e2, family=O.EPRIOR_BA14, alpha=0.25, weights=w)
     mr, cr = O.shear_estimate(e1[rep], e2[rep], family=O.EPRIOR_BA14, alpha=0.25)
     assert np.allclose(mw, mr, rtol=1e-9, atol=1e-12) and np.allclose(cw, cr, rtol=1e-8, atol=1e-14)
