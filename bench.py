@@ -44,6 +44,8 @@ def parse():
                          "serve: 10^6 requests of the ragged kind, served vs plain per-size batches; "
                          "shear: shear stage on 10^6 galaxies x 300 samples")
     ap.add_argument("--shear-k", type=int, default=300, help="interim samples per galaxy (shear workload)")
+    ap.add_argument("--n-boot", type=int, default=50,
+                    help="bootstrap resamples of the m, c errors (shear workload; 0: skip)")
     ap.add_argument("--serve-requests", type=int, default=200000,
                     help="requests of the serving comparison added to the plain line (0: none)")
     ap.add_argument("--n-gal", type=int, default=None)
@@ -566,6 +568,27 @@ def shear_arm(a, world, rank, local_rank):
                                lo=[-1, -1, 0.15, -2, 0, -100, -2, 0], hi=[1, 1, 0.3, 6, 2, 100, 2, 0.5],
                                n_warmup=300, n_samples=1000, n_leapfrog=8, seed=22048)
     hmc_s = time.perf_counter() - t1
+    # m and c by shape-noise cancellation with bootstrap errors (Sec. 3.4):
+    # datasets sheared by +g and -g, g = (0.02, 0), sharing intrinsic shapes
+    # and noise; each resample reweights the same galaxies in both
+    bias = None
+    if a.n_boot > 0:
+        del plan, e1, e2, h1, h2
+        torch.cuda.empty_cache()
+        pair = []
+        for sgn in (1, -1):
+            p1, p2 = toy_interim_samples(n, K, (sgn * 0.02, 0.0), alpha_true, dev, seed=2605)
+            pair.append(api.ShearPlan(p1, p2, family=1, trunc_r=0.7))
+            del p1, p2
+            torch.cuda.empty_cache()
+        t2 = time.perf_counter()
+        r = api.shear_bias_plans(*pair, g_abs=0.02, n_boot=a.n_boot, seed=1, alpha=alpha_true)
+        boot_s = time.perf_counter() - t2
+        bias = {"g": [0.02, 0.0], "m": r["m"], "m_sd": r["m_sd"], "c": r["c"], "c_sd": r["c_sd"],
+                "n_boot": a.n_boot, "seconds": boot_s,
+                "seconds_per_resample": boot_s / (a.n_boot + 1),
+                "estimator": "posterior mean of g (Gauss-Hermite, alpha fixed at the truth)"}
+        del pair
     return {"metric": SHEAR_METRIC, "value": passes / (ms / 1e3), "unit": "passes/s", "n_gpus": world,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -589,6 +612,7 @@ def shear_arm(a, world, rank, local_rank):
                     "sd": [float(x) for x in draws[:, :3].std(axis=0)], "draws": int(draws.shape[0]),
                     "accept_rate": hinfo["accept_rate"], "passes": hinfo["n_evals"], "seconds": hmc_s,
                     "ms_per_pass": 1e3 * hmc_s / max(1, hinfo["n_evals"])},
+            "bias": bias,
             "e2e": {"value": 1.0 / est_s, "unit": "joint estimates/s (host samples in, estimate out)",
                     "h2d_bytes_per_step": int(bytes_per_pass), "d2h_bytes_per_step": 8 * 12}}
 

@@ -409,6 +409,13 @@ typedef struct {
     int32_t family;       /* true ellipticity density: BS_EPRIOR_* */
     float trunc_r;        /* truncation radius (TRUNC_GAUSS only) */
     float sigma_e0;       /* interim ellipticity prior parameter (0.3) */
+    const float *gal_weight;  /* device [n_gal] or NULL (all 1): weight w_n >= 0
+                                 of galaxy n's term in the log-likelihood,
+                                 sum_n w_n L_n; integer weights are a bootstrap
+                                 resample (w_n copies of galaxy n), 0 drops it */
+    double gal_weight_sum;    /* sum_n w_n when gal_weight != NULL (the
+                                 per-galaxy constants scale with it); not read
+                                 otherwise.  Must be finite and >= 0. */
 } bs_shear_data;
 
 size_t bs_shear_workspace_bytes(int64_t n_gal, int32_t K);

@@ -65,7 +65,8 @@ class FitOut(C.Structure):
 
 class ShearData(C.Structure):
     _fields_ = [("e1", C.c_void_p), ("e2", C.c_void_p), ("b", C.c_void_p), ("n_gal", C.c_int64),
-                ("K", C.c_int32), ("family", C.c_int32), ("trunc_r", C.c_float), ("sigma_e0", C.c_float)]
+                ("K", C.c_int32), ("family", C.c_int32), ("trunc_r", C.c_float), ("sigma_e0", C.c_float),
+                ("gal_weight", C.c_void_p), ("gal_weight_sum", C.c_double)]
 
 
 ALLREDUCE_FN = C.CFUNCTYPE(None, C.POINTER(C.c_double), C.c_void_p)

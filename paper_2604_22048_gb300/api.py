@@ -386,7 +386,7 @@ def chain_ess(samples):
 class ShearPlan:
     """Interim ellipticity samples plus the workspace of bs_shear_loglike."""
 
-    def __init__(self, e1, e2, b=None, *, family=F.BS_EPRIOR_BA14, trunc_r=0.7, sigma_e0=0.3):
+    def __init__(self, e1, e2, b=None, *, family=F.BS_EPRIOR_BA14, trunc_r=0.7, sigma_e0=0.3, weights=None):
         _need_cuda(e1, e2, b)
         if e1.dim() != 2 or e1.shape != e2.shape:
             raise ValueError("e1, e2 must be [n_gal, K]")
@@ -403,6 +403,36 @@ class ShearPlan:
         self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=e1.device)
         self.out = torch.empty(4, dtype=torch.float64, device=e1.device)
         self._host = np.zeros(4)
+        self.set_weights(weights)
+
+    def set_weights(self, weights, weight_sum=None):
+        """Per-galaxy weights w_n >= 0 of the galaxies' log-likelihood terms
+        (None: all 1).  Integer weights are a bootstrap resample: w_n copies of
+        galaxy n.  numpy or CUDA [n_gal]; weight_sum (sum of w) is computed when
+        not given (a device sync for a CUDA tensor)."""
+        d = self.data
+        if weights is None:
+            self._w = None
+            d.gal_weight, d.gal_weight_sum = None, 0.0
+            return
+        dev = self.keep[0].device
+        if isinstance(weights, torch.Tensor):
+            w = weights.to(device=dev, dtype=torch.float32).contiguous()
+        else:
+            wn = np.ascontiguousarray(weights, dtype=np.float32)
+            if weight_sum is None:
+                if not (np.isfinite(wn).all() and (wn >= 0).all()):
+                    raise ValueError("weights must be finite and >= 0")
+                weight_sum = float(wn.astype(np.float64).sum())
+            w = torch.from_numpy(wn).to(dev)
+        if w.shape != (d.n_gal,):
+            raise ValueError("weights must be [n_gal]")
+        if weight_sum is None:
+            if not bool(torch.isfinite(w).all() and (w >= 0).all()):
+                raise ValueError("weights must be finite and >= 0")
+            weight_sum = float(w.double().sum())
+        self._w = w
+        d.gal_weight, d.gal_weight_sum = _p(w), float(weight_sum)
 
     def loglike(self, g1, g2, alpha, *, host=False):
         """(value, d/dg1, d/dg2, d/dalpha): a float64 CUDA tensor (async) or,
@@ -498,6 +528,62 @@ class ShearPlan:
         self.last_n_evals = nev.value
         n = 3 if free_alpha else 2
         return mean[:n], cov.reshape(3, 3)[:n, :n]
+
+
+def bootstrap_weights(n_gal, rng):
+    """One bootstrap resample of n_gal galaxies drawn with replacement, as
+    per-galaxy counts (float32 [n_gal], summing to n_gal)."""
+    return np.bincount(rng.integers(0, n_gal, n_gal), minlength=n_gal).astype(np.float32)
+
+
+def shear_bias(estimate_plus, estimate_minus, n_gal, *, g_abs=0.02, n_boot=500, seed=0):
+    """Multiplicative and additive bias by shape-noise cancellation (Sec. 3.4)
+    with bootstrap errors.  estimate_plus / estimate_minus map per-galaxy
+    weights (None for the original sample) to the shear estimate (g1, g2) of
+    the datasets sheared by +g and -g, g = (g_abs, 0), which share their
+    galaxies and noise:
+        m = (g+_1 - g-_1) / (2 |g|) - 1,   c = (g+_2 + g-_2) / 2.
+    Each bootstrap resample draws the galaxies once and applies the same
+    counts to both datasets (the image-phase samples are reused); the errors
+    are the standard deviations of m and c over the resamples, while m and c
+    themselves come from the original sample."""
+    def mc(gp, gm):
+        return (gp[0] - gm[0]) / (2.0 * g_abs) - 1.0, 0.5 * (gp[1] + gm[1])
+
+    m, c = mc(estimate_plus(None), estimate_minus(None))
+    rng = np.random.default_rng(seed)
+    boot = np.empty((n_boot, 2))
+    for i in range(n_boot):
+        w = bootstrap_weights(n_gal, rng)
+        boot[i] = mc(estimate_plus(w), estimate_minus(w))
+    sd = boot.std(axis=0, ddof=1) if n_boot > 1 else np.full(2, np.nan)
+    return {"m": m, "c": c, "m_sd": float(sd[0]), "c_sd": float(sd[1]), "m_boot": boot[:, 0], "c_boot": boot[:, 1]}
+
+
+def shear_bias_plans(plan_plus, plan_minus, *, g_abs=0.02, n_boot=500, seed=0, method="quadrature", **kw):
+    """shear_bias with the posterior mean of g from two ShearPlans as the
+    estimator: method "quadrature" (ShearPlan.estimate, keyword arguments kw)
+    or "hmc" (the mean of ShearPlan.sample draws, keyword arguments kw).  The
+    plans' weights are reset afterwards."""
+    n = plan_plus.data.n_gal
+    if plan_minus.data.n_gal != n:
+        raise ValueError("the +g and -g datasets must hold the same galaxies")
+
+    def estimator(plan):
+        def f(w):
+            plan.set_weights(w, None if w is None else float(n))
+            if method == "quadrature":
+                return plan.estimate(**kw)[0][:2]
+            if method == "hmc":
+                return plan.sample(**kw)[0][:, :2].mean(axis=0)
+            raise ValueError("method: quadrature or hmc")
+        return f
+
+    try:
+        return shear_bias(estimator(plan_plus), estimator(plan_minus), n, g_abs=g_abs, n_boot=n_boot, seed=seed)
+    finally:
+        plan_plus.set_weights(None)
+        plan_minus.set_weights(None)
 
 
 def shear_loglike(e1, e2, g1, g2, alpha, *, b=None, family=F.BS_EPRIOR_BA14, trunc_r=0.7, sigma_e0=0.3):

@@ -341,8 +341,11 @@ static bs_status validate_shear(const bs_shear_data *d, const char *who)
     if (d->family == BS_EPRIOR_TRUNC_GAUSS && !(d->trunc_r > 0.f && d->trunc_r <= 1.f))
         return fail(BS_ERR_INVALID_ARG, "%s: trunc_r", who);
     if (!(d->sigma_e0 > 0.f)) return fail(BS_ERR_INVALID_ARG, "%s: sigma_e0", who);
+    if (d->gal_weight && !(std::isfinite(d->gal_weight_sum) && d->gal_weight_sum >= 0.0))
+        return fail(BS_ERR_INVALID_ARG, "%s: gal_weight_sum must be finite and >= 0", who);
     return BS_OK;
 }
+
 
 bs_status bs_shear_loglike(const bs_shear_data *d, double g1, double g2, double alpha, double *out,
                            int32_t out_on_host, void *workspace, size_t workspace_bytes, void *stream)
@@ -418,7 +421,7 @@ bs_status bs_shear_loglike_full(const bs_shear_data *d, const float *lf, const f
     // per-galaxy constants of the flux/size ratio: log 2 - log sigma_f - log sigma_s
     // - log 2 pi + log of the interim widths (Eq. lflux-lsize-dist over the
     // interim uniforms); d/dsigma of the -log sigma terms
-    const double ng = (double)d->n_gal;
+    const double ng = bs::shear_weight_total(d);
     const double kPiD = 3.14159265358979323846;
     add[0] += ng * (std::log(2.0) - std::log(sig_f) - std::log(sig_s) - std::log(2.0 * kPiD) +
                     std::log(interim[1] - interim[0]) + std::log(interim[3] - interim[2]));
@@ -722,6 +725,13 @@ bs_status set_error(bs_status st, const char *fmt, ...)
     return st;
 }
 
+// Number of galaxies the per-galaxy constants count: the weight sum when
+// galaxies carry weights.
+double shear_weight_total(const bs_shear_data *d)
+{
+    return d->gal_weight ? d->gal_weight_sum : (double)d->n_gal;
+}
+
 bs_status shear_prepare(const bs_shear_data *d, double g1, double g2, double alpha, ShearLaunch &L,
                         double add[4], double &alpha_scale, const char *who)
 {
@@ -733,6 +743,7 @@ bs_status shear_prepare(const bs_shear_data *d, double g1, double g2, double alp
     L.e1 = d->e1;
     L.e2 = d->e2;
     L.b = d->b;
+    L.w = d->gal_weight;
     L.n_gal = d->n_gal;
     L.K = d->K;
     L.family = d->family;
@@ -743,7 +754,7 @@ bs_status shear_prepare(const bs_shear_data *d, double g1, double g2, double alp
     L.c0 = (float)(1.4426950408889634 / (2.0 * (double)d->sigma_e0 * d->sigma_e0));
     L.r2 = d->trunc_r * d->trunc_r;
     L.partials = nullptr;
-    const double ng = (double)d->n_gal;
+    const double ng = shear_weight_total(d);
     const double kap = d->family == BS_EPRIOR_BA14 ? 4.0 : 2.0;
     add[0] = ng * (kap * std::log1p(-gg) - log_z_family(d->family, alpha, d->trunc_r) +
                    log_z_ba14(d->sigma_e0) - std::log((double)d->K));

@@ -80,6 +80,7 @@ cudaError_t launch_render(int n, const float *theta, const float *shear, const i
 
 struct ShearLaunch {
     const float *e1, *e2, *b;
+    const float *w;   // per-galaxy weight of the galaxy's term, or NULL (all 1)
     long long n_gal;
     int K;
     int family;
@@ -100,6 +101,7 @@ struct ShearFullLaunch {
 constexpr int kShearFullOut = 9;   // value, d/d(g1, g2, sigma_e, mu_f, sigma_f, a_f, mu_s, sigma_s)
 
 int shear_grid_blocks();
+double shear_weight_total(const bs_shear_data *d);
 int shear_full_grid_blocks();
 cudaError_t launch_shear(const ShearLaunch &s, int grid, cudaStream_t stream);
 cudaError_t launch_shear_full(const ShearFullLaunch &f, int grid, cudaStream_t stream);

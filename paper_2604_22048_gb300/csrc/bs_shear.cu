@@ -224,9 +224,10 @@ __device__ __forceinline__ void eval_chunk(const ShearConst &c, const Chunk &ch,
 }
 
 // Merge the 8 lanes of a galaxy's group and add the galaxy's log-sum-exp and
-// softmax-weighted derivative sums to the lane-0 accumulators.
-__device__ __forceinline__ void finish_galaxy(const Lse &L, unsigned gmask, int sub, double &av, double &a1,
-                                              double &a2, double &aq)
+// softmax-weighted derivative sums, times the galaxy's weight w[n] (1 when w
+// is NULL; a zero weight drops the galaxy), to the lane-0 accumulators.
+__device__ __forceinline__ void finish_galaxy(const Lse &L, unsigned gmask, int sub, const float *w, long long n,
+                                              double &av, double &a1, double &a2, double &aq)
 {
     float m = L.m;
     float sw = L.sw.x + L.sw.y, t1 = L.t1.x + L.t1.y, t2 = L.t2.x + L.t2.y, tq = L.tq.x + L.tq.y;
@@ -246,12 +247,14 @@ __device__ __forceinline__ void finish_galaxy(const Lse &L, unsigned gmask, int 
         m = mn;
     }
     if (sub == 0) {
+        const double wn = w ? (double)__ldg(w + n) : 1.0;
+        if (wn == 0.0) return;
         if (sw > 0.f) {
             const float inv = 1.0f / sw;
-            av += (double)m + (double)__log2f(sw);
-            a1 += (double)(-2.0f * t1 * inv);
-            a2 += (double)(-2.0f * t2 * inv);
-            aq += (double)(tq * inv);
+            av += wn * ((double)m + (double)__log2f(sw));
+            a1 += wn * (double)(-2.0f * t1 * inv);
+            a2 += wn * (double)(-2.0f * t2 * inv);
+            aq += wn * (double)(tq * inv);
         } else {
             av = -INFINITY;
         }
@@ -319,7 +322,7 @@ __global__ void __launch_bounds__(kShearThreads, 3) shear_kernel(const ShearLaun
             eval_chunk<FAMILY, HAS_B>(c, B, L);
             k0 += 4 * kGroup;
         }
-        finish_galaxy(L, gmask, sub, av, a1, a2, aq);
+        finish_galaxy(L, gmask, sub, s.w, n, av, a1, a2, aq);
     }
     block_partials(s, av, a1, a2, aq);
 }
@@ -402,6 +405,7 @@ __global__ void __launch_bounds__(kShearThreads, 3) shear_kernel_async(const She
     Lse L;
     lse_reset(L);
     int cc = 0, cst = 0;     // consumer: chunk within the galaxy, ring slot
+    long long cn = group;    // consumer galaxy
     for (long long t = 0; t < n_items; ++t) {
         issue();
         cp_async_wait<kStages - 1>();
@@ -421,7 +425,8 @@ __global__ void __launch_bounds__(kShearThreads, 3) shear_kernel_async(const She
         cst = cst + 1 == kStages ? 0 : cst + 1;
         if (++cc == cpg) {
             cc = 0;
-            finish_galaxy(L, gmask, sub, av, a1, a2, aq);
+            finish_galaxy(L, gmask, sub, s.w, cn, av, a1, a2, aq);
+            cn += ngroups;
             lse_reset(L);
         }
     }
@@ -570,15 +575,16 @@ __global__ void __launch_bounds__(kShearThreads, 2) shear_full_kernel(const Shea
             for (int i = 1; i < 10; ++i) v[i] = v[i] * ca + w[i] * cb;
             v[0] = mn;
         }
-        if (sub == 0) {
+        const double wn = sub == 0 && s.w ? (double)__ldg(s.w + n) : 1.0;
+        if (sub == 0 && wn != 0.0) {
             if (v[1] > 0.f) {
                 const float inv = 1.0f / v[1];
-                acc[0] += (double)v[0] + (double)__log2f(v[1]);
-                acc[1] += (double)(-2.0f * v[2] * inv);
-                acc[2] += (double)(-2.0f * v[3] * inv);
-                acc[3] += (double)(v[4] * inv);
+                acc[0] += wn * ((double)v[0] + (double)__log2f(v[1]));
+                acc[1] += wn * (double)(-2.0f * v[2] * inv);
+                acc[2] += wn * (double)(-2.0f * v[3] * inv);
+                acc[3] += wn * (double)(v[4] * inv);
 #pragma unroll
-                for (int i = 0; i < 5; ++i) acc[4 + i] += (double)(v[5 + i] * inv);
+                for (int i = 0; i < 5; ++i) acc[4 + i] += wn * (double)(v[5 + i] * inv);
             } else {
                 acc[0] = -INFINITY;
             }

@@ -119,6 +119,14 @@ def test_host_validation_of_plan_serve_and_sampler(L):
     sc.free_mask = 0b11
     sc.n_samples = 0
     assert L.bs_shear_sample(C.byref(d), C.byref(sc), out, None, None, None, None, 0, None) == -1
+    # weighted galaxies: the weight sum must be finite and >= 0
+    wd = _ffi.ShearData()
+    wd.n_gal, wd.K, wd.family, wd.sigma_e0 = 2, 4, 0, 0.3
+    wd.e1 = wd.e2 = wd.gal_weight = 16
+    for bad in (-1.0, float("nan"), float("inf")):
+        wd.gal_weight_sum = bad
+        assert L.bs_shear_loglike(C.byref(wd), 0.0, 0.0, 0.2, out, 1, None, 0, None) == -1
+        assert b"gal_weight_sum" in L.bs_last_error()
     # all-free likelihood: b must be NULL, sigma_f > 0
     th = (C.c_double * 8)(0.0, 0.0, 0.2, 2.4, -0.1, 1.0, -0.4, 0.05)
     im = (C.c_double * 4)(-1.0, 9.0, -2.0, 1.0)
