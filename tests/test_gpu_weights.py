@@ -100,7 +100,10 @@ def test_weighted_estimate_matches_oracle(cuda):
     mo, co = O.shear_estimate(e1, e2, family=O.EPRIOR_BA14, free_alpha=True, alpha=0.2, alpha_lo=0.1,
                               alpha_hi=0.4, weights=w)
     assert np.abs(mg - mo).max() < 2e-6, (mg, mo)
-    assert np.allclose(cg, co, rtol=1e-3, atol=1e-10)
+    # covariance relative to the scale of its entries, sqrt(c_ii c_jj): the
+    # cross terms are ~1e-4 of it and carry the FP32 rounding of the passes
+    scale = np.sqrt(np.outer(np.diag(co), np.diag(co)))
+    assert np.abs(cg - co).max() <= 1e-3 * scale.min(), (cg, co)
 
 
 def test_bootstrap_bias_on_the_toy(cuda):
