@@ -394,6 +394,12 @@ bs_status bs_chain_ess(const float *samples, int32_t n_gal, int32_t n_chains,
  * step of the method. */
 bs_status bs_fp32_peak(int32_t packed, double *tflops, void *stream);
 
+/* FP64 FMA throughput of the current device in TFLOP/s (an FMA counts 2),
+ * measured the same way with independent DFMA chains: the rate an FP64 path
+ * (the precision of the CPU restatement) would run at on this GPU.  Same
+ * allocation and synchronisation as bs_fp32_peak; measurement helper. */
+bs_status bs_fp64_peak(double *tflops, void *stream);
+
 /* ------------------------------------------------------------------------ */
 /* Shear sampling phase (Sec. 3.2 - 3.4)                                     */
 /* ------------------------------------------------------------------------ */

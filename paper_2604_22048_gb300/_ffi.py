@@ -27,7 +27,7 @@ EXPORTED = ["bs_prior_default", "bs_last_error", "bs_version", "bs_render", "bs_
             "bs_fit_plan_workspace_bytes", "bs_fit_plan_create", "bs_fit_plan_launch", "bs_fit_plan_destroy",
             "bs_fit_resident_galaxies", "bs_fit_plan_num_launches", "bs_fit_plan_info", "bs_serve_request_bytes", "bs_serve_create", "bs_serve_submit",
             "bs_serve_poll", "bs_serve_get_stats", "bs_serve_now_ns", "bs_serve_destroy",
-            "bs_shear_hyperprior_default", "bs_shear_sample", "bs_fp32_peak"]
+            "bs_shear_hyperprior_default", "bs_shear_sample", "bs_fp32_peak", "bs_fp64_peak"]
 
 
 class BsError(RuntimeError):
@@ -179,6 +179,7 @@ def lib():
     L.bs_fit_plan_launch.argtypes = [vp, vp]
     L.bs_fit_plan_destroy.argtypes = [vp]
     L.bs_fp32_peak.argtypes = [i32, vp, vp]
+    L.bs_fp64_peak.argtypes = [vp, vp]
     L.bs_shear_hyperprior_default.argtypes = [vp, vp]
     L.bs_shear_hyperprior_default.restype = None
     L.bs_shear_sample.argtypes = [C.POINTER(ShearData), C.POINTER(ShearSampleCfg), vp, vp, vp, vp, vp, sz, vp]
@@ -197,7 +198,7 @@ def lib():
     L.bs_serve_now_ns.restype = i64
     L.bs_serve_destroy.argtypes = [vp]
     for nm in ("bs_render", "bs_fit_galaxies", "bs_logpost_points", "bs_chain_ess", "bs_shear_loglike",
-               "bs_shear_loglike_full", "bs_shear_sample", "bs_fp32_peak",
+               "bs_shear_loglike_full", "bs_shear_sample", "bs_fp32_peak", "bs_fp64_peak",
                "bs_shear_estimate", "bs_shear_loglike_noalloc", "bs_fit_plan_create", "bs_fit_plan_launch",
                "bs_fit_plan_destroy", "bs_fit_plan_info", "bs_serve_create", "bs_serve_submit", "bs_serve_poll", "bs_serve_get_stats",
                "bs_serve_destroy"):

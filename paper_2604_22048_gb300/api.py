@@ -332,6 +332,13 @@ def fp32_peak_tflops(packed=False):
     return t.value
 
 
+def fp64_peak_tflops():
+    """Measured FP64 FMA throughput of the current GPU (TFLOP/s, FMA = 2)."""
+    t = C.c_double(0)
+    F.check(F.lib().bs_fp64_peak(C.cast(C.byref(t), C.c_void_p), _stream()))
+    return t.value
+
+
 def resident_galaxies(n_chains, max_side, registers=0):
     """Galaxies of side max_side one fit launch holds at once on the current GPU
     with the given register cap (0 = 128)."""

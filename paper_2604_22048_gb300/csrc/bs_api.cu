@@ -315,8 +315,18 @@ bs_status bs_fp32_peak(int32_t packed, double *tflops, void *stream)
 {
     if (!tflops) return fail(BS_ERR_INVALID_ARG, "bs_fp32_peak: NULL tflops");
     double t = 0.0;
-    const cudaError_t e = bs::measure_fp32_peak(packed != 0, t, static_cast<cudaStream_t>(stream));
+    const cudaError_t e = bs::measure_fma_peak(packed != 0 ? 1 : 0, t, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "bs_fp32_peak");
+    *tflops = t;
+    return BS_OK;
+}
+
+bs_status bs_fp64_peak(double *tflops, void *stream)
+{
+    if (!tflops) return fail(BS_ERR_INVALID_ARG, "bs_fp64_peak: NULL tflops");
+    double t = 0.0;
+    const cudaError_t e = bs::measure_fma_peak(2, t, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "bs_fp64_peak");
     *tflops = t;
     return BS_OK;
 }

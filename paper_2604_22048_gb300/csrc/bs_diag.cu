@@ -105,15 +105,31 @@ __global__ void __launch_bounds__(256) ffma_kernel(float *out, int iters, float 
     out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = sum;
 }
 
+// FP64 FMA throughput: sixteen independent DFMA chains per thread.
+__global__ void __launch_bounds__(256) dfma_kernel(float *out, int iters, double a, double b)
+{
+    double x[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) x[i] = 1e-3 * (double)threadIdx.x + (double)i;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) x[i] = fma(x[i], a, b);
+    }
+    double sum = 0.0;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) sum += x[i];
+    out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = (float)sum;
+}
+
 }  // namespace
 
-cudaError_t measure_fp32_peak(bool packed, double &tflops, cudaStream_t stream)
+cudaError_t measure_fma_peak(int kind, double &tflops, cudaStream_t stream)
 {
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    const int grid = sms * 8, block = 256, iters = 16384;
+    const int grid = sms * 8, block = 256, iters = kind == 2 ? 512 : 16384;
     float *out = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     e = cudaMallocAsync(&out, sizeof(float) * (size_t)grid * block, stream);
@@ -122,8 +138,10 @@ cudaError_t measure_fp32_peak(bool packed, double &tflops, cudaStream_t stream)
     float best = 0.f;
     for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
         e = cudaEventRecord(e0, stream);
-        if (packed)
+        if (kind == 1)
             ffma_kernel<true><<<grid, block, 0, stream>>>(out, iters, 1.0000001f, 1e-7f);
+        else if (kind == 2)
+            dfma_kernel<<<grid, block, 0, stream>>>(out, iters, 1.0000000001, 1e-10);
         else
             ffma_kernel<false><<<grid, block, 0, stream>>>(out, iters, 1.0000001f, 1e-7f);
         if (e == cudaSuccess) e = cudaGetLastError();

@@ -127,6 +127,7 @@ bs_status shear_prepare(const bs_shear_data *d, double g1, double g2, double alp
 
 cudaError_t launch_chain_ess(const float *samples, int n_gal, int n_chains, int n_samples,
                              float *ess, float *rhat, cudaStream_t stream);
-cudaError_t measure_fp32_peak(bool packed, double &tflops, cudaStream_t stream);
+// FMA throughput in TFLOP/s (an FMA counts 2): kind 0 FFMA, 1 packed FFMA2, 2 DFMA.
+cudaError_t measure_fma_peak(int kind, double &tflops, cudaStream_t stream);
 
 }  // namespace bs

@@ -302,3 +302,11 @@ def test_fp32_peak_microbenchmark(cuda):
     for packed in (False, True):
         t = api.fp32_peak_tflops(packed)
         assert 0.5 * derived < t < 1.05 * derived, (packed, t, derived)
+
+
+def test_fp64_peak_microbenchmark(cuda):
+    """The DFMA rate is positive and far below the FP32 rate on this part (the
+    reason the kernels compute in FP32 and keep FP64 for totals)."""
+    t64 = api.fp64_peak_tflops()
+    t32 = api.fp32_peak_tflops(False)
+    assert 0.0 < t64 < 0.25 * t32, (t64, t32)
