@@ -567,18 +567,24 @@ def shear_bias(estimate_plus, estimate_minus, n_gal, *, g_abs=0.02, n_boot=500, 
     return {"m": m, "c": c, "m_sd": float(sd[0]), "c_sd": float(sd[1]), "m_boot": boot[:, 0], "c_boot": boot[:, 1]}
 
 
-def shear_bias_plans(plan_plus, plan_minus, *, g_abs=0.02, n_boot=500, seed=0, method="quadrature", **kw):
+def shear_bias_plans(plan_plus, plan_minus, *, g_abs=0.02, n_boot=500, seed=0, method="quadrature",
+                     base_weights=None, **kw):
     """shear_bias with the posterior mean of g from two ShearPlans as the
     estimator: method "quadrature" (ShearPlan.estimate, keyword arguments kw)
-    or "hmc" (the mean of ShearPlan.sample draws, keyword arguments kw).  The
-    plans' weights are reset afterwards."""
+    or "hmc" (the mean of ShearPlan.sample draws, keyword arguments kw).
+    base_weights (numpy [n_gal], optional) multiply every resample's counts,
+    e.g. 0 for galaxies left out of both datasets.  The plans' weights are
+    reset afterwards."""
     n = plan_plus.data.n_gal
     if plan_minus.data.n_gal != n:
         raise ValueError("the +g and -g datasets must hold the same galaxies")
+    base = None if base_weights is None else np.ascontiguousarray(base_weights, dtype=np.float32)
 
     def estimator(plan):
         def f(w):
-            plan.set_weights(w, None if w is None else float(n))
+            if base is not None:
+                w = base if w is None else w * base
+            plan.set_weights(w, None if w is None else float(w.astype(np.float64).sum()))
             if method == "quadrature":
                 return plan.estimate(**kw)[0][:2]
             if method == "hmc":

@@ -600,6 +600,10 @@ extern "C" bs_status bs_shear_estimate(const bs_shear_data *d, const bs_estimate
     } report{n_evals, &f};
     double x[3] = {0.0, 0.0, cfg->alpha}, g[3], v;
     if (!f.eval(x, v, g)) return f.err;
+    if (!std::isfinite(v))
+        return fail(BS_ERR_INVALID_ARG,
+                    "bs_shear_estimate: log-likelihood %g at g = 0 (a galaxy with no sample of non-zero weight, "
+                    "e.g. every sample beyond the truncation radius): give it weight 0", v);
 
     auto hessian = [&](const double *xc, double *H) -> bool {
         for (int j = 0; j < n; ++j) {
@@ -636,14 +640,16 @@ extern "C" bs_status bs_shear_estimate(const bs_shear_data *d, const bs_estimate
             for (int i = 0; i < n; ++i) step[i] = 1e-6 * g[i];
         }
         double t = 1.0, xn[3] = {x[0], x[1], x[2]}, vn = -INFINITY, gn[3] = {0, 0, 0};
-        for (int ls = 0; ls < 60; ++ls) {
+        bool accepted = false;
+        for (int ls = 0; ls < 60 && !accepted; ++ls) {
             for (int i = 0; i < n; ++i) xn[i] = x[i] + t * step[i];
             if (f.inside(xn)) {
                 if (!f.eval(xn, vn, gn)) return f.err;
-                if (vn >= v - 1e-10 * std::fabs(v)) break;
+                accepted = vn >= v - 1e-10 * std::fabs(v);
             }
-            t *= 0.5;
+            if (!accepted) t *= 0.5;
         }
+        if (!accepted) break;   // no ascent along the step: x is the mode to working precision
         double dmax = 0.0;
         for (int i = 0; i < n; ++i) {
             dmax = std::fmax(dmax, std::fabs(t * step[i]));

@@ -79,8 +79,11 @@ def test_zero_weight_drops_a_zero_likelihood_galaxy(cuda):
     t = lambda a: torch.from_numpy(a).to(cuda)
     plan = api.ShearPlan(t(e1), t(e2), family=O.EPRIOR_TRUNC_GAUSS)
     assert plan.loglike(0.0, 0.0, 0.2, host=True)[0] == -np.inf
+    with pytest.raises(F.BsError, match="weight 0"):     # fails loudly, no NaN estimate
+        plan.estimate(alpha=0.2)
     w[5] = 0.0
     plan.set_weights(w)
+    assert np.isfinite(plan.estimate(alpha=0.2)[0]).all()
     got = plan.loglike(0.01, 0.0, 0.2, host=True)
     keep = np.arange(64) != 5
     v, gr = O.shear_loglike(e1[keep], e2[keep], 0.01, 0.0, 0.2, family=O.EPRIOR_TRUNC_GAUSS)
