@@ -206,9 +206,9 @@ CAPTURED_TRAFFIC = {
     # 53x53 galaxy of the plain workload: (13,895,424 + 6,144) B / 1,216 galaxies
     "fit": ("paper_2604_22048_gb300/csrc/bs_fit.cu",
             "2e3d178d7a98193e539c45262e8d3b9dff129d21b2d7ac383b413197b56d8d2f", 11432.2),
-    # one interim sample of the shear workload: (481,524,480 + 3,041,024) B / (200,000 x 300)
+    # one interim sample of the shear workload: (480,250,624 + 3,216,896) B / (200,000 x 300)
     "shear": ("paper_2604_22048_gb300/csrc/bs_shear.cu",
-              "c7db3fdf99f29840405240fbaddc34fc87ecab2d124ea9e933a9dc81372cf5bc", 8.0761),
+              "ad6ae397103918b2dc2970353671f7063e3e8d6ed1da86462426731f70ddefa5", 8.0578),
 }
 
 
