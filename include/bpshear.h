@@ -151,7 +151,31 @@ typedef struct {
     int32_t registers;            /* register cap of the fit kernel: 128, 96
                                      (up to 4 chains) or 80; 0 = 128.  Results
                                      do not depend on it, only the speed. */
+    /* Pixel-likelihood extensions of Appendix C (zero-initialised: one
+     * exposure, white noise, the likelihood of Eq. likelihood-pixels). */
+    int32_t n_exposures;          /* J, 0 or 1..BS_MAX_EXPOSURES: exposures of
+                                     each galaxy on one pixel grid, stored one
+                                     after another from offsets[n] (J side^2
+                                     pixels); psf holds n_gal * J entries
+                                     (exposure j of galaxy n at n J + j)
+                                     unless n_psf == 1, noise_sigma n_gal * J.
+                                     The likelihood is the sum over exposures
+                                     of Eq. covar-pixel-likelihood with the same
+                                     galaxy parameters and each exposure's PSF. */
+    const float *noise_corr;      /* NULL (white noise) or device float with the
+                                     layout of data (J stamps of side^2 per
+                                     galaxy, from offsets[n]): the noise
+                                     correlation of exposure j at pixel lag
+                                     (dy, dx) in element (dy + c) side + (dx + c),
+                                     c = (side - 1)/2; the pixel covariance is
+                                     noise_sigma^2 corr(x_a - x_b), stationary
+                                     and periodic on the stamp (a circulant
+                                     Sigma), corr(0) = 1 for a noise_sigma that
+                                     is the pixel sd.  Its spectrum must be
+                                     positive (status 3 otherwise). */
 } bs_fit_args;
+
+#define BS_MAX_EXPOSURES 64
 
 /* Outputs, caller-allocated device buffers (NULL = not wanted, except
  * samples).  Samples are parameter-major so that each parameter plane, e.g.
@@ -167,7 +191,9 @@ typedef struct {
     float *inv_mass;       /* [n_gal][n_chains][6]: adapted inverse metric */
     int32_t *n_divergent;  /* [n_gal][n_chains]: divergent transitions */
     int32_t *status;       /* [n_gal]: 0 ok, 1 a chain started off-support,
-                              2 side[] invalid for max_side (galaxy skipped) */
+                              2 side[] invalid for max_side (galaxy skipped),
+                              3 noise_corr of an exposure has a spectrum that is
+                              not positive, i.e. no covariance (galaxy skipped) */
     int32_t *n_grad;       /* [n_gal][n_chains]: log-posterior gradient
                               evaluations the chain made (warmup, searches and
                               sampling) */

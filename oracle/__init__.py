@@ -90,6 +90,8 @@ def lib():
         L.or_log_z_ba14.argtypes = [C.c_double]
         L.or_loglike.restype = C.c_double
         L.or_loglike.argtypes = [C.c_int, C.c_double, C.POINTER(_Psf), _D, _D, C.c_double, _D, _D]
+        L.or_loglike_cov.restype = C.c_double
+        L.or_loglike_cov.argtypes = [C.c_int, C.c_int, C.c_double, C.POINTER(_Psf), _D, _D, _D, _D, _D]
         L.or_logpost.restype = C.c_double
         L.or_logpost.argtypes = [C.c_int, C.c_double, C.POINTER(_Psf), _D, _D, C.c_double,
                                  C.POINTER(_Prior), _D, _D]
@@ -284,6 +286,19 @@ def logpost(N, p, psf, data, sigma, theta, prior=None, weights=None):
     w = _d(weights) if weights is not None else None
     v = lib().or_logpost(N, p, C.byref(ps), _dp(_d(data)), _dp(w), sigma, C.byref(pr),
                          _dp(_d(theta)), _dp(g))
+    return v, g
+
+
+def loglike_cov(N, p, psfs, data, sigmas, theta, corr=None):
+    """Appendix C: exposures data [J, N, N] with PSFs psfs (J tuples), pixel
+    sds sigmas [J] and noise correlations corr [J, N, N] at centred lag (None:
+    white).  Returns (log-likelihood, gradient[6])."""
+    data = _d(data).reshape(-1, N, N)
+    J = data.shape[0]
+    ps = (_Psf * J)(*[_psf(x) for x in psfs])
+    cr = _d(corr).reshape(J, N, N) if corr is not None else None
+    g = np.zeros(6)
+    v = lib().or_loglike_cov(J, N, p, ps, _dp(data), _dp(_d(sigmas)), _dp(cr), _dp(_d(theta)), _dp(g))
     return v, g
 
 

@@ -126,6 +126,17 @@ double or_loglike(int N, double p, const or_psf *psf, const double *data,
 double or_loglike_t(int N, double p, const double *T, const double *data,
                     const double *w, double sigma, const double theta[6],
                     double grad[6]);
+/* Appendix C (Eq. covar-pixel-likelihood summed over exposures): J exposures
+ * d_j [J][N][N] of one galaxy on one grid, exposure j with PSF psf[j] and
+ * pixel covariance Sigma_j = sigma_j^2 C_j, C_j[a][b] = corr_j(x_a - x_b) with
+ * the lag wrapped periodically to -c..c (corr [J][N][N], lag (dy, dx) at
+ * [dy + c][dx + c], symmetric; NULL: white).  Returns
+ *   -1/2 sum_j (d_j - m_j)^T Sigma_j^-1 (d_j - m_j)
+ * with Sigma_j built densely in pixel space and solved by Cholesky, and the
+ * gradient sum_j (Sigma_j^-1 (d_j - m_j))^T dm_j/dtheta by the adjoint DFT;
+ * NAN when some Sigma_j is not positive definite. */
+double or_loglike_cov(int J, int N, double p, const or_psf *psf, const double *data, const double *sigma,
+                      const double *corr, const double theta[6], double grad[6]);
 double or_logpost(int N, double p, const or_psf *psf, const double *data,
                   const double *w, double sigma, const or_prior *pr,
                   const double theta[6], double grad[6]);

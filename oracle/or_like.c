@@ -87,11 +87,61 @@ static inline double complex tw(const double complex *tab, long m, int N)   /* e
 
 void or_idft_image(int N, const double *M_reim, double *img, int method);
 
+/* Gradient of sum_x r(x) m(x) with respect to theta, r fixed: by Parseval
+ * sum_k Re[dM_k/dtheta conj(R_k)] / N^2 with R the DFT of r (the adjoint DFT of
+ * the residual), dM from the derivatives of the model spectrum M. */
+static void adjoint_grad(int N, double p, const double *M, const double *r, const double theta[6],
+                         double grad[6])
+{
+    int c = (N - 1) / 2;
+    size_t NN = (size_t)N * N;
+    /* R(u,v) = sum_{iy,ix} r exp(-2 pi i (u (ix-c) + v (iy-c)) / N), separable */
+    double complex *B = malloc(sizeof(double complex) * NN);   /* [iy][u+c] */
+    double complex *tab = malloc(sizeof(double complex) * (size_t)N);
+    or_twiddles(N, tab);
+    for (int iy = 0; iy < N; ++iy)
+        for (int u = -c; u <= c; ++u) {
+            double complex acc = 0;
+            for (int ix = 0; ix < N; ++ix) acc += r[(size_t)iy * N + ix] * tw(tab, -(long)u * (ix - c), N);
+            B[(size_t)iy * N + (u + c)] = acc;
+        }
+    double r0 = pow(10.0, theta[1]) / or_hlr_over_r0();
+    double e1 = theta[2], e2 = theta[3];
+    double E = e1 * e1 + e2 * e2;
+    double dk = 2.0 * OR_PI / (N * p);
+    double g[6] = {0, 0, 0, 0, 0, 0};
+    for (int v = -c; v <= c; ++v)
+        for (int u = -c; u <= c; ++u) {
+            double complex R = 0;
+            for (int iy = 0; iy < N; ++iy) R += B[(size_t)iy * N + (u + c)] * tw(tab, -(long)v * (iy - c), N);
+            size_t idx = (size_t)(v + c) * N + (u + c);
+            double complex Mk = M[2 * idx] + I * M[2 * idx + 1];
+            double kx = u * dk, ky = v * dk, k2 = kx * kx + ky * ky;
+            double A = (1.0 + E) * k2 + 2.0 * e1 * (kx * kx - ky * ky) + 4.0 * e2 * kx * ky;
+            double q = A / (1.0 - E);
+            double s = 1.0 + r0 * r0 * q;
+            double dq1 = (2.0 * e1 * k2 + 2.0 * (kx * kx - ky * ky)) / (1.0 - E)
+                         + 2.0 * e1 * A / ((1.0 - E) * (1.0 - E));
+            double dq2 = (2.0 * e2 * k2 + 4.0 * kx * ky) / (1.0 - E)
+                         + 2.0 * e2 * A / ((1.0 - E) * (1.0 - E));
+            double complex dM[6];
+            dM[0] = OR_LN10 * Mk;
+            dM[1] = -3.0 * OR_LN10 * (r0 * r0 * q / s) * Mk;
+            dM[2] = -1.5 * r0 * r0 * dq1 / s * Mk;
+            dM[3] = -1.5 * r0 * r0 * dq2 / s * Mk;
+            dM[4] = -I * p * kx * Mk;
+            dM[5] = -I * p * ky * Mk;
+            for (int i = 0; i < 6; ++i) g[i] += creal(dM[i] * conj(R));
+        }
+    for (int i = 0; i < 6; ++i) grad[i] = g[i] / (double)NN;
+    free(B);
+    free(tab);
+}
+
 double or_loglike_t(int N, double p, const double *T, const double *data,
                     const double *w, double sigma, const double theta[6],
                     double grad[6])
 {
-    int c = (N - 1) / 2;
     size_t NN = (size_t)N * N;
     double *M = malloc(sizeof(double) * 2 * NN);
     double *m = malloc(sizeof(double) * NN);
@@ -109,49 +159,7 @@ double or_loglike_t(int N, double p, const double *T, const double *data,
     }
     double logl = -0.5 * chi2 / b;
 
-    if (grad) {
-        /* R(u,v) = sum_{iy,ix} r exp(-2 pi i (u (ix-c) + v (iy-c)) / N), separable */
-        double complex *B = malloc(sizeof(double complex) * NN);   /* [iy][u+c] */
-        double complex *tab = malloc(sizeof(double complex) * (size_t)N);
-        or_twiddles(N, tab);
-        for (int iy = 0; iy < N; ++iy)
-            for (int u = -c; u <= c; ++u) {
-                double complex acc = 0;
-                for (int ix = 0; ix < N; ++ix) acc += r[(size_t)iy * N + ix] * tw(tab, -(long)u * (ix - c), N);
-                B[(size_t)iy * N + (u + c)] = acc;
-            }
-        double r0 = pow(10.0, theta[1]) / or_hlr_over_r0();
-        double e1 = theta[2], e2 = theta[3];
-        double E = e1 * e1 + e2 * e2;
-        double dk = 2.0 * OR_PI / (N * p);
-        double g[6] = {0, 0, 0, 0, 0, 0};
-        for (int v = -c; v <= c; ++v)
-            for (int u = -c; u <= c; ++u) {
-                double complex R = 0;
-                for (int iy = 0; iy < N; ++iy) R += B[(size_t)iy * N + (u + c)] * tw(tab, -(long)v * (iy - c), N);
-                size_t idx = (size_t)(v + c) * N + (u + c);
-                double complex Mk = M[2 * idx] + I * M[2 * idx + 1];
-                double kx = u * dk, ky = v * dk, k2 = kx * kx + ky * ky;
-                double A = (1.0 + E) * k2 + 2.0 * e1 * (kx * kx - ky * ky) + 4.0 * e2 * kx * ky;
-                double q = A / (1.0 - E);
-                double s = 1.0 + r0 * r0 * q;
-                double dq1 = (2.0 * e1 * k2 + 2.0 * (kx * kx - ky * ky)) / (1.0 - E)
-                             + 2.0 * e1 * A / ((1.0 - E) * (1.0 - E));
-                double dq2 = (2.0 * e2 * k2 + 4.0 * kx * ky) / (1.0 - E)
-                             + 2.0 * e2 * A / ((1.0 - E) * (1.0 - E));
-                double complex dM[6];
-                dM[0] = OR_LN10 * Mk;
-                dM[1] = -3.0 * OR_LN10 * (r0 * r0 * q / s) * Mk;
-                dM[2] = -1.5 * r0 * r0 * dq1 / s * Mk;
-                dM[3] = -1.5 * r0 * r0 * dq2 / s * Mk;
-                dM[4] = -I * p * kx * Mk;
-                dM[5] = -I * p * ky * Mk;
-                for (int i = 0; i < 6; ++i) g[i] += creal(dM[i] * conj(R));
-            }
-        for (int i = 0; i < 6; ++i) grad[i] = g[i] / (double)NN;
-        free(B);
-        free(tab);
-    }
+    if (grad) adjoint_grad(N, p, M, r, theta, grad);
     free(M); free(m); free(r);
     return logl;
 }
@@ -165,6 +173,80 @@ double or_loglike(int N, double p, const or_psf *psf, const double *data,
     double v = or_loglike_t(N, p, T, data, w, sigma, theta, grad);
     free(T);
     return v;
+}
+
+/* Lower Cholesky factor of the n x n symmetric matrix A (row-major) in place;
+ * returns 0 if A is not positive definite. */
+static int cholesky(double *A, int n)
+{
+    for (int j = 0; j < n; ++j) {
+        double d = A[(size_t)j * n + j];
+        for (int k = 0; k < j; ++k) d -= A[(size_t)j * n + k] * A[(size_t)j * n + k];
+        if (!(d > 0.0)) return 0;
+        d = sqrt(d);
+        A[(size_t)j * n + j] = d;
+        for (int i = j + 1; i < n; ++i) {
+            double s = A[(size_t)i * n + j];
+            for (int k = 0; k < j; ++k) s -= A[(size_t)i * n + k] * A[(size_t)j * n + k];
+            A[(size_t)i * n + j] = s / d;
+        }
+    }
+    return 1;
+}
+
+double or_loglike_cov(int J, int N, double p, const or_psf *psf, const double *data, const double *sigma,
+                      const double *corr, const double theta[6], double grad[6])
+{
+    int c = (N - 1) / 2, n = N * N;
+    size_t NN = (size_t)n;
+    double *M = malloc(sizeof(double) * 2 * NN);
+    double *m = malloc(sizeof(double) * NN);
+    double *T = malloc(sizeof(double) * NN);
+    double *S = malloc(sizeof(double) * NN * NN);
+    double *z = malloc(sizeof(double) * NN);
+    double logl = 0.0, gj[6];
+    if (grad)
+        for (int i = 0; i < 6; ++i) grad[i] = 0.0;
+    for (int j = 0; j < J && isfinite(logl); ++j) {
+        or_transfer_table(N, p, &psf[j], T);
+        or_model_spectrum_t(N, p, T, theta, M);
+        or_idft_image(N, M, m, 0);
+        const double *d = data + (size_t)j * NN;
+        /* Sigma_j[a][b] = sigma_j^2 corr_j(x_a - x_b), lags wrapped to -c..c */
+        double s2 = sigma[j] * sigma[j];
+        for (int a = 0; a < n; ++a)
+            for (int b = 0; b < n; ++b) {
+                int dy = a / N - b / N, dx = a % N - b % N;
+                dy = ((dy + c) % N + N) % N - c;
+                dx = ((dx + c) % N + N) % N - c;
+                double cv = corr ? corr[(size_t)j * NN + (size_t)(dy + c) * N + (dx + c)] : (dy == 0 && dx == 0);
+                S[(size_t)a * n + b] = s2 * cv;
+            }
+        if (!cholesky(S, n)) {
+            logl = NAN;
+            break;
+        }
+        /* z = Sigma^-1 (d - m): forward then back substitution */
+        for (int a = 0; a < n; ++a) {
+            double t = d[a] - m[a];
+            for (int k = 0; k < a; ++k) t -= S[(size_t)a * n + k] * z[k];
+            z[a] = t / S[(size_t)a * n + a];
+        }
+        for (int a = n - 1; a >= 0; --a) {
+            double t = z[a];
+            for (int k = a + 1; k < n; ++k) t -= S[(size_t)k * n + a] * z[k];
+            z[a] = t / S[(size_t)a * n + a];
+        }
+        double q = 0.0;
+        for (int a = 0; a < n; ++a) q += (d[a] - m[a]) * z[a];
+        logl -= 0.5 * q;
+        if (grad) {
+            adjoint_grad(N, p, M, z, theta, gj);
+            for (int i = 0; i < 6; ++i) grad[i] += gj[i];
+        }
+    }
+    free(M); free(m); free(T); free(S); free(z);
+    return logl;
 }
 
 double or_logpost(int N, double p, const or_psf *psf, const double *data,

@@ -98,17 +98,22 @@ class FitPlan:
     launch, so that repeated fits (benchmark steps) allocate nothing."""
 
     def __init__(self, data, offsets, side, psf, noise_sigma, init, cfg: FitConfig, *, gal_id=None,
-                 max_side=None, init_step_size=None, init_inv_mass=None, registers=0,
+                 max_side=None, init_step_size=None, init_inv_mass=None, registers=0, n_exposures=1,
+                 noise_corr=None,
                  want=("logp", "accept_rate", "step_size", "inv_mass", "n_div", "status", "n_grad")):
         """init_step_size [n_gal, C] / init_inv_mass [n_gal, C, 6] (optional):
         resume adapted chains (no initial step-size search).  registers: the
-        fit kernel's register cap (128, 96, 80; 0 = 128), speed only."""
-        _need_cuda(data, offsets, side, noise_sigma, init, gal_id, init_step_size, init_inv_mass)
+        fit kernel's register cap (128, 96, 80; 0 = 128), speed only.
+        n_exposures J: each galaxy's J stamps lie one after another from its
+        offset, psf has n_gal * J entries (or one), noise_sigma n_gal * J;
+        noise_corr (float32, layout of data): per-exposure noise correlation
+        at pixel lag, centred (Appendix C)."""
+        _need_cuda(data, offsets, side, noise_sigma, init, gal_id, init_step_size, init_inv_mass, noise_corr)
         dev = data.device
         n_gal, n_chains = init.shape[0], init.shape[1]
         assert n_chains == cfg.n_chains, "init must be [n_gal, n_chains, 6]"
         self.cfg = cfg
-        self.keep = (data, offsets, side, psf, noise_sigma, init, gal_id, init_step_size, init_inv_mass)
+        self.keep = (data, offsets, side, psf, noise_sigma, init, gal_id, init_step_size, init_inv_mass, noise_corr)
         table, n_psf = psf
         a = F.FitArgs()
         a.n_gal = n_gal
@@ -136,6 +141,8 @@ class FitPlan:
         a.init_step_size = _p(init_step_size)
         a.init_inv_mass = _p(init_inv_mass)
         a.registers = int(registers)
+        a.n_exposures = int(n_exposures)
+        a.noise_corr = _p(noise_corr)
         self.args = a
         S, Cn = cfg.n_samples, cfg.n_chains
         f32 = dict(dtype=torch.float32, device=dev)
@@ -356,9 +363,10 @@ def fit_galaxies(data, offsets, side, psf, noise_sigma, init, cfg: FitConfig | N
 
 
 def logpost_points(data, offsets, side, psf, noise_sigma, gal_index, theta, *, max_side=None,
-                   pixel_scale=PIXEL_SCALE, prior=DEFAULT_PRIOR):
-    """Log posterior (float64) and gradient (float32) at points theta [n, 6]."""
-    _need_cuda(data, offsets, side, noise_sigma, gal_index, theta)
+                   pixel_scale=PIXEL_SCALE, prior=DEFAULT_PRIOR, n_exposures=1, noise_corr=None):
+    """Log posterior (float64) and gradient (float32) at points theta [n, 6]
+    (n_exposures, noise_corr as in FitPlan)."""
+    _need_cuda(data, offsets, side, noise_sigma, gal_index, theta, noise_corr)
     table, n_psf = psf
     a = F.FitArgs()
     a.n_gal = int(side.shape[0])
@@ -372,6 +380,8 @@ def logpost_points(data, offsets, side, psf, noise_sigma, gal_index, theta, *, m
     a.noise_sigma = _p(noise_sigma)
     a.pixel_scale = pixel_scale
     a.prior = F.Prior(*prior)
+    a.n_exposures = int(n_exposures)
+    a.noise_corr = _p(noise_corr)
     n = theta.shape[0]
     lp = torch.empty(n, dtype=torch.float64, device=theta.device)
     g = torch.empty((n, 6), dtype=torch.float32, device=theta.device)

@@ -161,7 +161,11 @@ static bs_status fill_fit_params(const bs_fit_args *a, bs::FitParams &p, const c
     if (a->data_dtype != BS_F32 && a->data_dtype != BS_F64)
         return fail(BS_ERR_INVALID_ARG, "%s: data_dtype", who);
     if (!odd_side_ok(a->max_side)) return fail(BS_ERR_INVALID_ARG, "%s: max_side %d", who, a->max_side);
-    if (a->n_psf != 1 && a->n_psf != a->n_gal) return fail(BS_ERR_INVALID_ARG, "%s: n_psf", who);
+    if (a->n_exposures < 0 || a->n_exposures > BS_MAX_EXPOSURES)
+        return fail(BS_ERR_INVALID_ARG, "%s: n_exposures 0..%d", who, BS_MAX_EXPOSURES);
+    const int n_exp = a->n_exposures > 1 ? a->n_exposures : 1;
+    if (a->n_psf != 1 && (int64_t)a->n_psf != (int64_t)a->n_gal * n_exp)
+        return fail(BS_ERR_INVALID_ARG, "%s: n_psf must be 1 or n_gal x n_exposures", who);
     if (!(a->pixel_scale > 0.f)) return fail(BS_ERR_INVALID_ARG, "%s: pixel_scale", who);
     const bs_prior &pr = a->prior;
     if (!(pr.lf_hi > pr.lf_lo && pr.ls_hi > pr.ls_lo && pr.sigma_xy > 0.f && pr.sigma_e > 0.f))
@@ -174,6 +178,8 @@ static bs_status fill_fit_params(const bs_fit_args *a, bs::FitParams &p, const c
     p.psf = a->psf;
     p.n_psf = a->n_psf;
     p.sigma = a->noise_sigma;
+    p.n_exp = n_exp;
+    p.noise_corr = a->noise_corr;
     p.gal_id = a->gal_id;
     p.init = a->init;
     p.init_step = a->init_step_size;

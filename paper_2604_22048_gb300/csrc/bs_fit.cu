@@ -49,8 +49,13 @@ struct GalCtx {
     float dk;      // 2 pi / (N p)
     float p;       // pixel scale
     float invN;
-    float inv_b;   // 1 / sigma^2
+    float inv_b;   // 1 / sigma^2 (1 when the exposures are folded into the table)
 };
+
+// chi^2 of the galaxy's exposures minus that of its folded table (a constant
+// of the galaxy, 0 for one exposure with white noise); in shared memory, so
+// that it takes no register in the chains' loop.
+__shared__ double s_chi2_off;
 
 // Row layout of the staged tables for NCT = npad / 32 column slots per lane
 // (3 * npad floats per row u).  Slots are paired, (2p, 2p+1), so that a lane
@@ -67,12 +72,12 @@ __host__ __device__ __forceinline__ int row_floats(int npad) { return 3 * npad; 
 // pairs X(u), X(u+1) with 16-byte loads, u even) starts 16-byte aligned.
 __host__ __device__ __forceinline__ int phase_stride(int h_max) { return (h_max + 1) & ~1; }
 
-// float2 slots of the scratch: the setup's two rows, or the chains' phase
+// float2 slots of the scratch: the setup's three rows, or the chains' phase
 // tables if larger; even, so that the (kx, kx^2) table after it stays 16-byte
 // aligned.
 __host__ __device__ __forceinline__ int scratch_float2(int max_side, int h_max, int n_chains)
 {
-    const int setup = 2 * max_side + 4;
+    const int setup = 3 * max_side + 4;
     const int phase = n_chains * phase_stride(h_max);
     const int n = setup > phase ? setup : phase;
     return (n + 1) & ~1;
@@ -82,6 +87,7 @@ struct SmemView {
     float *tab;    // [h_max][3 npad] data spectrum and transfer, paired layout
     float2 *G;     // [max_side], setup scratch (one frequency row)
     float2 *tw;    // [max_side]
+    float2 *Gc;    // [max_side], setup scratch (a row of the noise correlation's transform)
     float2 *xph;   // [n_chains][phase_stride(h_max)] phase tables (aliases G, tw after setup)
     float2 *kxr;   // [h_max]: (kx, kx^2) of row u
 };
@@ -92,6 +98,7 @@ __device__ __forceinline__ SmemView smem_view(unsigned char *base, int h_max, in
     v.tab = reinterpret_cast<float *>(base);
     v.G = reinterpret_cast<float2 *>(v.tab + (size_t)h_max * row_floats(npad));
     v.tw = v.G + (size_t)max_side;
+    v.Gc = v.tw + (size_t)max_side;
     v.xph = v.G;
     v.kxr = v.G + (size_t)scratch_float2(max_side, h_max, n_chains);
     return v;
@@ -168,9 +175,162 @@ __device__ __forceinline__ bool side_ok(const FitParams &P, int N)
     return N >= 3 && N <= P.max_side && (N & 1);
 }
 
+// G[iy] = sum_ix img[iy][ix] exp(-2 pi i u (ix - c) / N): the x transform of
+// the N x N image at `off`, frequency u (threads of the CTA over rows).
+__device__ __forceinline__ void row_dft(const void *img, int f64, int64_t off, int N, int c, int u,
+                                        const float2 *tw, float2 *G)
+{
+    for (int iy = threadIdx.x; iy < N; iy += blockDim.x) {
+        int idx = (int)(((long long)(N - u) * c) % N);   // -u c mod N
+        float re = 0.f, im = 0.f;
+        const int64_t rowoff = off + (int64_t)iy * N;
+        for (int ix = 0; ix < N; ++ix) {
+            const float d = load_pix(img, f64, rowoff + ix);
+            const float2 t = tw[idx];
+            re = fmaf(d, t.x, re);
+            im = fmaf(-d, t.y, im);
+            idx += u;
+            if (idx >= N) idx -= N;
+        }
+        G[iy] = make_float2(re, im);
+    }
+}
+
+// sum_iy G[iy] exp(-2 pi i v (iy - c) / N): the y transform at frequency v.
+__device__ __forceinline__ float2 col_dft(const float2 *G, int N, int c, int v, const float2 *tw)
+{
+    const int vm = ((v % N) + N) % N;
+    int idx = (int)(((long long)(N - vm) * c) % N);   // -v c mod N
+    float re = 0.f, im = 0.f;
+    for (int iy = 0; iy < N; ++iy) {
+        const float2 gv = G[iy];
+        const float2 t = tw[idx];
+        // gv * conj(t)
+        re = fmaf(gv.x, t.x, fmaf(gv.y, t.y, re));
+        im = fmaf(gv.y, t.x, fmaf(-gv.x, t.y, im));
+        idx += vm;
+        if (idx >= N) idx -= N;
+    }
+    return make_float2(re, im);
+}
+
+// scale x the PSF x pixel transfer of psf `ps` at grid point (u, v).
+__device__ __forceinline__ float transfer_at(const bs_psf &ps, const GalCtx &gc, int u, int v, float scale)
+{
+    const float kx = u * gc.dk, ky = v * gc.dk;
+    return scale * psf_transfer(ps, sqrtf(kx * kx + ky * ky)) * sincpi((float)u * gc.invN) *
+           sincpi((float)v * gc.invN);
+}
+
+// Sum over the CTA of one double per thread, in a fixed order.
+__device__ double block_sum_d(double v)
+{
+    __shared__ double part[32];
+    v = warp_sum_d(v);
+    const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    if ((threadIdx.x & 31) == 0) part[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int i = 0; i < nw; ++i) t += part[i];
+    __syncthreads();
+    return t;
+}
+
+// Appendix C: the galaxy's J exposures on one grid, exposure j with its own
+// transfer T_j and noise covariance sigma_j^2 C_j, C_j circulant with
+// spectrum lambda_j(k) (the transform of the correlation at lag).  Each
+// Gaussian term is diagonal in k,
+//   r_j^T Sigma_j^-1 r_j = (1/N^2) sum_k |D_j - T_j G|^2 / (sigma_j^2 lambda_j),
+// with G the galaxy's (PSF-free) spectrum, and the sum over exposures is one
+// term of the single-exposure form plus a constant:
+//   sum_j W_j |D_j - T_j G|^2 = S |C/S - G|^2 + (E - |C|^2/S),
+//   W_j = 1/(sigma_j^2 lambda_j), S = sum_j W_j T_j^2, C = sum_j W_j T_j D_j,
+//   E = sum_j W_j |D_j|^2.
+// So the table holds T' = sqrt(S) and D' = C/sqrt(S) (with inv_b = 1) and the
+// fit kernel runs unchanged; the constant goes to chi2_off so that the
+// log posterior is that of the exposures.  Returns false (uniform across the
+// CTA) when some lambda_j is not positive.
+__device__ bool setup_folded(const FitParams &P, int gal, const SmemView &sm, GalCtx &gc)
+{
+    const int N = gc.N, c = gc.c, H = gc.H, J = P.n_exp;
+    const int npad = P.npad, rowf = row_floats(npad);
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const float sqrt2 = 1.41421356237309515f;
+    const int64_t off0 = P.offsets[gal];
+    const int64_t NN = (int64_t)N * N;
+    double cacc = 0.0;
+    bool bad = false;
+    for (int u = 0; u < H; ++u) {
+        float *row = sm.tab + (size_t)u * rowf;
+        const float scale = (u == 0 ? 1.0f : sqrt2) * gc.invN;
+        const double s2 = (double)scale * scale;
+        for (int j = 0; j < J; ++j) {
+            const int64_t off = off0 + (int64_t)j * NN;
+            row_dft(P.data, P.data_f64, off, N, c, u, sm.tw, sm.G);
+            if (P.noise_corr) row_dft(P.noise_corr, 0, off, N, c, u, sm.tw, sm.Gc);
+            __syncthreads();
+            const bs_psf ps = P.psf[P.n_psf == 1 ? 0 : (int64_t)gal * J + j];
+            const float sig = P.sigma[(int64_t)gal * J + j];
+            for (int vi = tid; vi < npad; vi += nth) {
+                float Cx = 0.f, Cy = 0.f, S = 0.f;
+                if (vi < N) {
+                    const int v = vi - c;
+                    const float2 D = col_dft(sm.G, N, c, v, sm.tw);
+                    float lam = P.noise_corr ? col_dft(sm.Gc, N, c, v, sm.tw).x : 1.0f;
+                    if (!(lam > 0.f)) {
+                        bad = true;
+                        lam = 1.0f;
+                    }
+                    const float Wj = 1.0f / (sig * sig * lam);
+                    const float T = transfer_at(ps, gc, u, v, 1.0f);
+                    const float WT = Wj * T;
+                    Cx = WT * D.x;
+                    Cy = WT * D.y;
+                    S = WT * T;
+                    cacc += s2 * (double)Wj * ((double)D.x * D.x + (double)D.y * D.y);
+                }
+                int ox, oy, ot;
+                slot_offsets(npad, vi >> 5, vi & 31, ox, oy, ot);
+                if (j == 0) {
+                    row[ox] = Cx;
+                    row[oy] = Cy;
+                    row[ot] = S;
+                } else {
+                    row[ox] += Cx;
+                    row[oy] += Cy;
+                    row[ot] += S;
+                }
+            }
+            __syncthreads();   // G and Gc are rewritten by the next exposure
+        }
+        // (C, S) -> (D', T'), each thread on the columns it accumulated
+        for (int vi = tid; vi < N; vi += nth) {
+            int ox, oy, ot;
+            slot_offsets(npad, vi >> 5, vi & 31, ox, oy, ot);
+            const float Cx = row[ox], Cy = row[oy], S = row[ot];
+            float Dx = 0.f, Dy = 0.f, T = 0.f;
+            if (S > 0.f) {
+                const float rs = rsqrtf(S);
+                T = scale * S * rs;
+                Dx = scale * Cx * rs;
+                Dy = scale * Cy * rs;
+                cacc -= s2 * ((double)Cx * Cx + (double)Cy * Cy) / (double)S;
+            }
+            row[ox] = Dx;
+            row[oy] = Dy;
+            row[ot] = T;
+        }
+    }
+    gc.inv_b = 1.0f;
+    const double off = block_sum_d(cacc);
+    if (tid == 0) s_chi2_off = off;
+    return __syncthreads_or(bad) == 0;
+}
+
 // Stage the galaxy's data spectrum and transfer table (all threads of the CTA).
-// The caller has checked side_ok.
-__device__ void setup_galaxy(const FitParams &P, int gal, const SmemView &sm, GalCtx &gc)
+// The caller has checked side_ok.  Returns false, uniformly, when the galaxy
+// cannot be fitted (a noise correlation without a positive spectrum).
+__device__ bool setup_galaxy(const FitParams &P, int gal, const SmemView &sm, GalCtx &gc)
 {
     const int N = P.side[gal];
     const int c = (N - 1) / 2;
@@ -184,10 +344,8 @@ __device__ void setup_galaxy(const FitParams &P, int gal, const SmemView &sm, Ga
     gc.p = P.pixel_scale;
     gc.dk = 6.283185307179586f / ((float)N * P.pixel_scale);
     gc.invN = 1.0f / (float)N;
-    const float sig = P.sigma[gal];
-    gc.inv_b = 1.0f / (sig * sig);
+    if (tid == 0) s_chi2_off = 0.0;
 
-    const int64_t off = P.offsets[gal];
     for (int m = tid; m < N; m += nth) {
         float s, co;
         sincospif(2.0f * (float)m / (float)N, &s, &co);
@@ -198,26 +356,17 @@ __device__ void setup_galaxy(const FitParams &P, int gal, const SmemView &sm, Ga
         sm.kxr[u] = make_float2(kx, kx * kx);
     }
     __syncthreads();
+    if (P.n_exp > 1 || P.noise_corr) return setup_folded(P, gal, sm, gc);
+
+    const float sig = P.sigma[gal];
+    gc.inv_b = 1.0f / (sig * sig);
+    const int64_t off = P.offsets[gal];
     const bs_psf ps = P.psf[P.n_psf == 1 ? 0 : gal];
     const float sqrt2 = 1.41421356237309515f;
     const int rowf = row_floats(npad);
     // one frequency row u at a time, so the scratch is a single column G[iy]
     for (int u = 0; u < H; ++u) {
-        // G[iy] = sum_ix d[iy][ix] exp(-2 pi i u (ix - c) / N)
-        for (int iy = tid; iy < N; iy += nth) {
-            int idx = (int)(((long long)(N - u) * c) % N);   // -u c mod N
-            float re = 0.f, im = 0.f;
-            const int64_t rowoff = off + (int64_t)iy * N;
-            for (int ix = 0; ix < N; ++ix) {
-                const float d = load_pix(P.data, P.data_f64, rowoff + ix);
-                const float2 t = sm.tw[idx];
-                re = fmaf(d, t.x, re);
-                im = fmaf(-d, t.y, im);
-                idx += u;
-                if (idx >= N) idx -= N;
-            }
-            sm.G[iy] = make_float2(re, im);
-        }
+        row_dft(P.data, P.data_f64, off, N, c, u, sm.tw, sm.G);
         __syncthreads();
         // D(u, v) = sum_iy G[iy] exp(-2 pi i v (iy - c) / N), scaled; transfer T(u, v)
         float *row = sm.tab + (size_t)u * rowf;
@@ -227,22 +376,9 @@ __device__ void setup_galaxy(const FitParams &P, int gal, const SmemView &sm, Ga
             float Tv = 0.f;
             if (vi < N) {
                 const int v = vi - c;
-                const int vm = ((v % N) + N) % N;
-                int idx = (int)(((long long)(N - vm) * c) % N);   // -v c mod N
-                float re = 0.f, im = 0.f;
-                for (int iy = 0; iy < N; ++iy) {
-                    const float2 gv = sm.G[iy];
-                    const float2 t = sm.tw[idx];
-                    // gv * conj(t)
-                    re = fmaf(gv.x, t.x, fmaf(gv.y, t.y, re));
-                    im = fmaf(gv.y, t.x, fmaf(-gv.x, t.y, im));
-                    idx += vm;
-                    if (idx >= N) idx -= N;
-                }
-                Dv = make_float2(re * scale, im * scale);
-                const float kx = u * gc.dk, ky = v * gc.dk;
-                Tv = scale * psf_transfer(ps, sqrtf(kx * kx + ky * ky)) * sincpi((float)u * gc.invN) *
-                     sincpi((float)v * gc.invN);
+                const float2 D = col_dft(sm.G, N, c, v, sm.tw);
+                Dv = make_float2(D.x * scale, D.y * scale);
+                Tv = transfer_at(ps, gc, u, v, scale);
             }
             int ox, oy, ot;
             slot_offsets(npad, vi >> 5, vi & 31, ox, oy, ot);
@@ -252,6 +388,7 @@ __device__ void setup_galaxy(const FitParams &P, int gal, const SmemView &sm, Ga
         }
         __syncthreads();
     }
+    return true;
 }
 
 __device__ __forceinline__ bool in_support(const FitParams &P, const float th[6])
@@ -570,7 +707,7 @@ __device__ __forceinline__ double eval_logpost(const FitParams &P, const GalCtx 
     const double chi2 = warp_sum_comp(chi_hi, chi_lo);
     const float lprior = P.prior_const - 0.5f * (th[4] * th[4] + th[5] * th[5]) * P.inv_sxy2 +
                          2.0f * log1pf(-E) - 0.5f * E * P.inv_se2;
-    return -0.5 * chi2 * (double)ib + (double)lprior;
+    return -0.5 * (chi2 + s_chi2_off) * (double)ib + (double)lprior;
 }
 
 __device__ __forceinline__ float pick6(const float (&v)[6], int i)
@@ -857,7 +994,12 @@ __device__ __forceinline__ void fit_loop(const FitParams &P)
             continue;
         }
         GalCtx gc;
-        setup_galaxy(P, gal, sm, gc);
+        if (!setup_galaxy(P, gal, sm, gc)) {
+            if (threadIdx.x == 0 && P.status) P.status[gal] = 3;
+            __syncthreads();
+            if (P.done) publish_galaxy(P, gal);
+            continue;
+        }
         if (warp < P.n_chains) run_chain<NC>(P, gc, sm, gal, warp);
         __syncthreads();
         if (P.done) publish_galaxy(P, gal);
@@ -913,7 +1055,11 @@ __global__ void __launch_bounds__(32) logpost_points_kernel(const FitParams P, i
             continue;
         }
         GalCtx gc;
-        setup_galaxy(P, gal, sm, gc);
+        if (!setup_galaxy(P, gal, sm, gc)) {
+            if (threadIdx.x == 0 && logp) logp[i] = NAN;
+            if (grad && threadIdx.x < 6) grad[(size_t)i * 6 + threadIdx.x] = NAN;
+            continue;
+        }
         const float *th = theta + (size_t)i * 6;
         double *lp = logp ? logp + i : nullptr;
         float *gr = grad ? grad + (size_t)i * 6 : nullptr;

@@ -21,6 +21,8 @@ struct FitParams {
     const bs_psf *psf;
     int n_psf;
     const float *sigma;
+    int n_exp;                 // exposures per galaxy (>= 1)
+    const float *noise_corr;   // per-exposure noise correlation (layout of data) or NULL
     const uint64_t *gal_id;
     const float *init;
     const float *init_step;

@@ -178,3 +178,31 @@ def toy_interim_ellipticities(e_int, g, K, rng, *, sigma_eta=0.1, n_prop=3000, s
         e1[i] = eps[pick].real
         e2[i] = eps[pick].imag
     return e1, e2
+
+
+def smoothing_kernel_1d(a):
+    """Taps (a, 1, a) of the separable smoothing that correlates pixel noise."""
+    return np.array([a, 1.0, a])
+
+
+def noise_correlation(N, a):
+    """Correlation at centred pixel lag [N, N] (lag (dy, dx) at [dy + c, dx + c])
+    of white noise smoothed periodically by the separable kernel (a, 1, a) in
+    each axis: c1(l) = sum_i k(i) k(i + l), corr = c1(dy) c1(dx) / c1(0)^2."""
+    k = smoothing_kernel_1d(a)
+    c1 = np.zeros(N)
+    cc = (N - 1) // 2
+    for lag in range(-2, 3):
+        c1[cc + lag] = sum(k[i] * k[i + lag] for i in range(3) if 0 <= i + lag < 3)
+    return np.outer(c1, c1) / c1[cc] ** 2
+
+
+def correlated_noise(rng, n, N, a, sigma=1.0):
+    """n periodic N x N noise fields with pixel sd sigma and the correlation of
+    noise_correlation(N, a): white noise smoothed by (a, 1, a) in each axis
+    (periodic), rescaled."""
+    k = smoothing_kernel_1d(a)
+    w = rng.normal(size=(n, N, N))
+    x = sum(k[i] * np.roll(w, i - 1, axis=2) for i in range(3))
+    y = sum(k[i] * np.roll(x, i - 1, axis=1) for i in range(3))
+    return sigma * y / float((k ** 2).sum())

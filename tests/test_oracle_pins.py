@@ -483,3 +483,79 @@ def test_weighted_likelihood_equals_duplicated_galaxies():
     mw, cw = O.shear_estimate(e1, e2, family=O.EPRIOR_BA14, alpha=0.25, weights=w)
     mr, cr = O.shear_estimate(e1[rep], e2[rep], family=O.EPRIOR_BA14, alpha=0.25)
     assert np.allclose(mw, mr, rtol=1e-9, atol=1e-12) and np.allclose(cw, cr, rtol=1e-8, atol=1e-14)
+
+
+# ---- Appendix C: pixel covariance and exposures ------------------------------------------
+
+def _cov_case(N=11, J=2, a=0.3, seed=5):
+    rng = np.random.default_rng(seed)
+    th = np.array([2.3, -0.45, 0.12, -0.2, 0.3, -0.25])
+    psfs = [(O.PSF_GAUSSIAN, 0.7), (O.PSF_MOFFAT, 0.9, 3.0)][:J]
+    sig = np.array([1.0, 1.7])[:J]
+    corr = np.stack([synth.noise_correlation(N, a)] * J)
+    noise = synth.correlated_noise(rng, J, N, a)
+    data = np.stack([O.render(N, 0.2, psfs[j], th) + sig[j] * noise[j] for j in range(J)])
+    return N, th, psfs, sig, corr, data
+
+
+def _circulant(corr, s2):
+    """Dense pixel covariance s2 corr(x_a - x_b), lags wrapped to -c..c."""
+    N = corr.shape[0]
+    c = (N - 1) // 2
+    y, x = np.divmod(np.arange(N * N), N)
+    dy = (y[:, None] - y[None, :] + c) % N
+    dx = (x[:, None] - x[None, :] + c) % N
+    return s2 * corr[dy, dx]
+
+
+def test_loglike_cov_white_is_the_pixel_likelihood():
+    """One exposure, white noise: the covariance form is Eq. likelihood-pixels."""
+    N, th, psfs, sig, corr, data = _cov_case(J=1)
+    v, g = O.loglike_cov(N, 0.2, psfs, data, sig, th)
+    vr, gr = O.loglike(N, 0.2, psfs[0], data[0], sig[0], th)
+    assert abs(v - vr) <= 1e-11 * abs(vr) and np.allclose(g, gr, rtol=1e-10, atol=1e-10)
+
+
+def test_loglike_cov_matches_multivariate_normal_and_the_circulant_spectrum():
+    """Two exposures (Gaussian and Moffat PSFs, sigma 1 and 1.7) with
+    correlated noise: the value equals scipy's multivariate normal log density
+    of each exposure without its normalisation, and the circulant identity
+    r^T Sigma^-1 r = sum_k |R_k|^2 / (sigma^2 N^2 lambda_k), lambda = FFT of the
+    correlation at lag."""
+    from scipy import stats
+    N, th, psfs, sig, corr, data = _cov_case()
+    v, _ = O.loglike_cov(N, 0.2, psfs, data, sig, th, corr=corr)
+    ref = fft = 0.0
+    for j in range(2):
+        m = O.render(N, 0.2, psfs[j], th)
+        S = _circulant(corr[j], sig[j] ** 2)
+        _, logdet = np.linalg.slogdet(2 * np.pi * S)
+        ref += stats.multivariate_normal(mean=m.ravel(), cov=S).logpdf(data[j].ravel()) + 0.5 * logdet
+        lam = np.fft.fft2(np.fft.ifftshift(corr[j])).real
+        R = np.fft.fft2(data[j] - m)
+        fft += -0.5 * (np.abs(R) ** 2 / lam).sum() / (sig[j] ** 2 * N * N)
+    assert abs(v - ref) <= 1e-9 * abs(ref), (v, ref)
+    assert abs(v - fft) <= 1e-9 * abs(fft), (v, fft)
+
+
+def test_loglike_cov_gradient_central_differences():
+    N, th, psfs, sig, corr, data = _cov_case()
+    _, g = O.loglike_cov(N, 0.2, psfs, data, sig, th, corr=corr)
+    for i in range(6):
+        h = 1e-6
+        tp, tm = th.copy(), th.copy()
+        tp[i] += h
+        tm[i] -= h
+        fd = (O.loglike_cov(N, 0.2, psfs, data, sig, tp, corr=corr)[0] -
+              O.loglike_cov(N, 0.2, psfs, data, sig, tm, corr=corr)[0]) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-5 * max(1.0, abs(g[i])), (i, fd, g[i])
+
+
+def test_loglike_cov_rejects_a_covariance_that_is_not_positive_definite():
+    N, th, psfs, sig, corr, data = _cov_case(J=1)
+    bad = np.zeros((1, N, N))
+    c = (N - 1) // 2
+    bad[0, c, c] = 1.0
+    bad[0, c + 1, c] = bad[0, c - 1, c] = bad[0, c, c + 1] = bad[0, c, c - 1] = 0.8
+    v, _ = O.loglike_cov(N, 0.2, psfs, data, sig, th, corr=bad)
+    assert np.isnan(v)
