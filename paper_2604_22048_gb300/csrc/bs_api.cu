@@ -606,10 +606,6 @@ extern "C" bs_status bs_shear_estimate(const bs_shear_data *d, const bs_estimate
     } report{n_evals, &f};
     double x[3] = {0.0, 0.0, cfg->alpha}, g[3], v;
     if (!f.eval(x, v, g)) return f.err;
-    if (!std::isfinite(v))
-        return fail(BS_ERR_INVALID_ARG,
-                    "bs_shear_estimate: log-likelihood %g at g = 0 (a galaxy with no sample of non-zero weight, "
-                    "e.g. every sample beyond the truncation radius): give it weight 0", v);
 
     auto hessian = [&](const double *xc, double *H) -> bool {
         for (int j = 0; j < n; ++j) {
@@ -665,6 +661,10 @@ extern "C" bs_status bs_shear_estimate(const bs_shear_data *d, const bs_estimate
         v = vn;
         if (dmax < 1e-12) break;
     }
+    if (!std::isfinite(v))
+        return fail(BS_ERR_INVALID_ARG,
+                    "bs_shear_estimate: log-likelihood %g at the mode (a galaxy with no sample of non-zero weight "
+                    "near it, e.g. every sample beyond the truncation radius): give it weight 0", v);
     if (!hessian(x, H)) return f.err;
     // Laplace covariance Sigma = (-H)^-1 and its Cholesky factor
     for (int i = 0; i < n * n; ++i) negH[i] = -H[i];
