@@ -173,7 +173,24 @@ typedef struct {
                                      Sigma), corr(0) = 1 for a noise_sigma that
                                      is the pixel sd.  Its spectrum must be
                                      positive (status 3 otherwise). */
+    /* Galaxy profile of the forward model (Appendix B; zero: exponential). */
+    int32_t profile;              /* BS_PROFILE_EXPONENTIAL, BS_PROFILE_SPERGEL
+                                     or BS_PROFILE_GAUSSIAN: transform
+                                     (1 + r0^2 q)^-3/2, (1 + r0^2 q)^-(1+nu) or
+                                     exp(-r0^2 q / 2) with the same sheared
+                                     quadratic form q and log10 hlr parameter;
+                                     hlr / r0 = 1.678347 (exponential), the
+                                     root of the Spergel enclosed flux
+                                     1 - x^(1+nu) K_(1+nu)(x) / (2^nu
+                                     Gamma(1+nu)) = 1/2, or sqrt(2 ln 2).  The
+                                     register cap applies to the exponential
+                                     only (the others run at 128). */
+    float spergel_nu;             /* Spergel index nu in [-0.9, 4] (0.5 is the
+                                     exponential; -0.6 is close to de
+                                     Vaucouleurs) */
 } bs_fit_args;
+
+enum { BS_PROFILE_EXPONENTIAL = 0, BS_PROFILE_SPERGEL = 1, BS_PROFILE_GAUSSIAN = 2 };
 
 #define BS_MAX_EXPOSURES 64
 

@@ -90,6 +90,13 @@ def lib():
         L.or_log_z_ba14.argtypes = [C.c_double]
         L.or_loglike.restype = C.c_double
         L.or_loglike.argtypes = [C.c_int, C.c_double, C.POINTER(_Psf), _D, _D, C.c_double, _D, _D]
+        L.or_loglike_p.restype = C.c_double
+        L.or_loglike_p.argtypes = [C.c_int, C.c_double, C.c_int, C.c_double, C.POINTER(_Psf), _D, C.c_double,
+                                   _D, _D]
+        L.or_profile_ft.restype = C.c_double
+        L.or_profile_ft.argtypes = [C.c_int, C.c_double, C.c_double]
+        L.or_hlr_over_r0_p.restype = C.c_double
+        L.or_hlr_over_r0_p.argtypes = [C.c_int, C.c_double]
         L.or_loglike_cov.restype = C.c_double
         L.or_loglike_cov.argtypes = [C.c_int, C.c_int, C.c_double, C.POINTER(_Psf), _D, _D, _D, _D, _D]
         L.or_logpost.restype = C.c_double
@@ -286,6 +293,26 @@ def logpost(N, p, psf, data, sigma, theta, prior=None, weights=None):
     w = _d(weights) if weights is not None else None
     v = lib().or_logpost(N, p, C.byref(ps), _dp(_d(data)), _dp(w), sigma, C.byref(pr),
                          _dp(_d(theta)), _dp(g))
+    return v, g
+
+
+PROFILE_EXPONENTIAL, PROFILE_SPERGEL, PROFILE_GAUSSIAN = 0, 1, 2
+
+
+def profile_ft(profile, nu, t):
+    return lib().or_profile_ft(profile, nu, t)
+
+
+def hlr_over_r0(profile=PROFILE_EXPONENTIAL, nu=0.5):
+    return lib().or_hlr_over_r0_p(profile, nu)
+
+
+def loglike_p(profile, nu, N, p, psf, data, sigma, theta):
+    """Eq. likelihood-pixels with a Spergel (nu) or Gaussian profile
+    (Appendix B).  Returns (log-likelihood, gradient[6])."""
+    ps = _psf(psf)
+    g = np.zeros(6)
+    v = lib().or_loglike_p(profile, nu, N, p, C.byref(ps), _dp(_d(data)), sigma, _dp(_d(theta)), _dp(g))
     return v, g
 
 

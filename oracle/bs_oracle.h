@@ -86,6 +86,10 @@ double or_hlr_over_r0(void);                       /* root of 1-(1+x)e^-x = 1/2 
 double or_bessel_k(double nu, double x);           /* K_nu(x), x > 0 */
 double or_psf_ft(const or_psf *psf, double k);     /* PSF transform, PSF(0) = 1 */
 double or_exp_profile_ft(double kx, double ky, double r0, double e1, double e2);
+/* Appendix B profiles */
+enum { OR_PROFILE_EXPONENTIAL = 0, OR_PROFILE_SPERGEL = 1, OR_PROFILE_GAUSSIAN = 2 };
+double or_profile_ft(int profile, double nu, double t);      /* unit-flux transform at t = r0^2 q */
+double or_hlr_over_r0_p(int profile, double nu);
 /* Full model spectrum M(u,v) on the N x N grid, row-major [v+c][u+c],
  * complex values as interleaved (re, im) pairs. */
 void or_model_spectrum(int N, double p, const or_psf *psf, const double theta[6],
@@ -95,6 +99,8 @@ void or_model_spectrum(int N, double p, const or_psf *psf, const double theta[6]
 void or_transfer_table(int N, double p, const or_psf *psf, double *T);
 void or_model_spectrum_t(int N, double p, const double *T, const double theta[6],
                          double *M_reim);
+void or_model_spectrum_tp(int N, double p, const double *T, int profile, double nu, const double theta[6],
+                          double *M_reim);
 /* Inverse DFT of a full Hermitian spectrum to a real N x N image.
  * method 0: separable O(N^3); method 1: direct O(N^4) double sum. */
 void or_idft_image(int N, const double *M_reim, double *img, int method);
@@ -137,6 +143,10 @@ double or_loglike_t(int N, double p, const double *T, const double *data,
  * NAN when some Sigma_j is not positive definite. */
 double or_loglike_cov(int J, int N, double p, const or_psf *psf, const double *data, const double *sigma,
                       const double *corr, const double theta[6], double grad[6]);
+/* Eq. likelihood-pixels with the galaxy profile of Appendix B (profile, nu),
+ * gradient by the adjoint DFT of the residual. */
+double or_loglike_p(int profile, double nu, int N, double p, const or_psf *psf, const double *data,
+                    double sigma, const double theta[6], double grad[6]);
 double or_logpost(int N, double p, const or_psf *psf, const double *data,
                   const double *w, double sigma, const or_prior *pr,
                   const double theta[6], double grad[6]);

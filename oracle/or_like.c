@@ -89,9 +89,11 @@ void or_idft_image(int N, const double *M_reim, double *img, int method);
 
 /* Gradient of sum_x r(x) m(x) with respect to theta, r fixed: by Parseval
  * sum_k Re[dM_k/dtheta conj(R_k)] / N^2 with R the DFT of r (the adjoint DFT of
- * the residual), dM from the derivatives of the model spectrum M. */
-static void adjoint_grad(int N, double p, const double *M, const double *r, const double theta[6],
-                         double grad[6])
+ * the residual), dM from the derivatives of the model spectrum M.  For the
+ * profiles of Appendix B, M = F f(t) T phase with t = r0^2 q: d log f / dt is
+ * -3/2 / (1 + t), -(1 + nu) / (1 + t) or -1/2, and d t / d log10 hlr = 2 ln10 t. */
+static void adjoint_grad_p(int N, double p, const double *M, const double *r, const double theta[6],
+                           int profile, double nu, double grad[6])
 {
     int c = (N - 1) / 2;
     size_t NN = (size_t)N * N;
@@ -105,7 +107,7 @@ static void adjoint_grad(int N, double p, const double *M, const double *r, cons
             for (int ix = 0; ix < N; ++ix) acc += r[(size_t)iy * N + ix] * tw(tab, -(long)u * (ix - c), N);
             B[(size_t)iy * N + (u + c)] = acc;
         }
-    double r0 = pow(10.0, theta[1]) / or_hlr_over_r0();
+    double r0 = pow(10.0, theta[1]) / or_hlr_over_r0_p(profile, nu);
     double e1 = theta[2], e2 = theta[3];
     double E = e1 * e1 + e2 * e2;
     double dk = 2.0 * OR_PI / (N * p);
@@ -126,9 +128,16 @@ static void adjoint_grad(int N, double p, const double *M, const double *r, cons
                          + 2.0 * e2 * A / ((1.0 - E) * (1.0 - E));
             double complex dM[6];
             dM[0] = OR_LN10 * Mk;
-            dM[1] = -3.0 * OR_LN10 * (r0 * r0 * q / s) * Mk;
-            dM[2] = -1.5 * r0 * r0 * dq1 / s * Mk;
-            dM[3] = -1.5 * r0 * r0 * dq2 / s * Mk;
+            if (profile == OR_PROFILE_EXPONENTIAL) {
+                dM[1] = -3.0 * OR_LN10 * (r0 * r0 * q / s) * Mk;
+                dM[2] = -1.5 * r0 * r0 * dq1 / s * Mk;
+                dM[3] = -1.5 * r0 * r0 * dq2 / s * Mk;
+            } else {
+                double dlogf = profile == OR_PROFILE_SPERGEL ? -(1.0 + nu) / s : -0.5;   /* d log f / dt */
+                dM[1] = dlogf * 2.0 * OR_LN10 * r0 * r0 * q * Mk;
+                dM[2] = dlogf * r0 * r0 * dq1 * Mk;
+                dM[3] = dlogf * r0 * r0 * dq2 * Mk;
+            }
             dM[4] = -I * p * kx * Mk;
             dM[5] = -I * p * ky * Mk;
             for (int i = 0; i < 6; ++i) g[i] += creal(dM[i] * conj(R));
@@ -159,7 +168,7 @@ double or_loglike_t(int N, double p, const double *T, const double *data,
     }
     double logl = -0.5 * chi2 / b;
 
-    if (grad) adjoint_grad(N, p, M, r, theta, grad);
+    if (grad) adjoint_grad_p(N, p, M, r, theta, OR_PROFILE_EXPONENTIAL, 0.0, grad);
     free(M); free(m); free(r);
     return logl;
 }
@@ -173,6 +182,28 @@ double or_loglike(int N, double p, const or_psf *psf, const double *data,
     double v = or_loglike_t(N, p, T, data, w, sigma, theta, grad);
     free(T);
     return v;
+}
+
+double or_loglike_p(int profile, double nu, int N, double p, const or_psf *psf, const double *data,
+                    double sigma, const double theta[6], double grad[6])
+{
+    size_t NN = (size_t)N * N;
+    double *T = malloc(sizeof(double) * NN);
+    double *M = malloc(sizeof(double) * 2 * NN);
+    double *m = malloc(sizeof(double) * NN);
+    double *r = malloc(sizeof(double) * NN);
+    or_transfer_table(N, p, psf, T);
+    or_model_spectrum_tp(N, p, T, profile, nu, theta, M);
+    or_idft_image(N, M, m, 0);
+    double b = sigma * sigma, chi2 = 0.0;
+    for (size_t j = 0; j < NN; ++j) {
+        double res = data[j] - m[j];
+        chi2 += res * res;
+        r[j] = res / b;
+    }
+    if (grad) adjoint_grad_p(N, p, M, r, theta, profile, nu, grad);
+    free(T); free(M); free(m); free(r);
+    return -0.5 * chi2 / b;
 }
 
 /* Lower Cholesky factor of the n x n symmetric matrix A (row-major) in place;
@@ -241,7 +272,7 @@ double or_loglike_cov(int J, int N, double p, const or_psf *psf, const double *d
         for (int a = 0; a < n; ++a) q += (d[a] - m[a]) * z[a];
         logl -= 0.5 * q;
         if (grad) {
-            adjoint_grad(N, p, M, z, theta, gj);
+            adjoint_grad_p(N, p, M, z, theta, OR_PROFILE_EXPONENTIAL, 0.0, gj);
             for (int i = 0; i < 6; ++i) grad[i] += gj[i];
         }
     }

@@ -82,6 +82,35 @@ double or_exp_profile_ft(double kx, double ky, double r0, double e1, double e2)
     return pow(1.0 + r0 * r0 * q, -1.5);
 }
 
+/* Appendix B profiles: Spergel (index nu; nu = 1/2 is the exponential) and
+ * Gaussian.  Transform of the unit-flux profile as a function of
+ * t = r0^2 q(k): (1 + t)^-3/2, (1 + t)^-(1+nu), exp(-t/2). */
+double or_profile_ft(int profile, double nu, double t)
+{
+    if (profile == OR_PROFILE_SPERGEL) return pow(1.0 + t, -(1.0 + nu));
+    if (profile == OR_PROFILE_GAUSSIAN) return exp(-0.5 * t);
+    return pow(1.0 + t, -1.5);
+}
+
+/* hlr / r0: for the Spergel profile I(r) ~ (r/r0)^nu K_nu(r/r0), whose
+ * enclosed flux is 1 - x^(1+nu) K_(1+nu)(x) / (2^nu Gamma(1+nu)) at x = r/r0,
+ * the root of that flux = 1/2 by bisection; sqrt(2 ln 2) for the Gaussian
+ * exp(-r^2 / (2 r0^2)). */
+double or_hlr_over_r0_p(int profile, double nu)
+{
+    if (profile == OR_PROFILE_GAUSSIAN) return sqrt(2.0 * log(2.0));
+    if (profile != OR_PROFILE_SPERGEL) return or_hlr_over_r0();
+    double norm = pow(2.0, nu) * tgamma(1.0 + nu);
+    double lo = 1e-8, hi = 60.0;
+    for (int it = 0; it < 200; ++it) {
+        double mid = 0.5 * (lo + hi);
+        double enclosed = 1.0 - pow(mid, 1.0 + nu) * or_bessel_k(1.0 + nu, mid) / norm;
+        if (enclosed < 0.5) lo = mid;
+        else hi = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
 static double sinc(double x) { return x == 0.0 ? 1.0 : sin(x) / x; }
 
 /* PSF-and-pixel transfer T(u,v) = PSF(|k|) sinc(kx p/2) sinc(ky p/2) on the
@@ -113,6 +142,33 @@ void or_model_spectrum_t(int N, double p, const double *T, const double theta[6]
             double kx = u * dk, ky = v * dk;
             size_t idx = (size_t)(v + c) * N + (u + c);
             double amp = F * or_exp_profile_ft(kx, ky, r0, e1, e2) * T[idx];
+            double complex Mk = amp * cexp(-I * p * (kx * dx + ky * dy));
+            M_reim[2 * idx] = creal(Mk);
+            M_reim[2 * idx + 1] = cimag(Mk);
+        }
+    }
+}
+
+/* The same with the profile of Appendix B (profile 0 is the exponential). */
+void or_model_spectrum_tp(int N, double p, const double *T, int profile, double nu, const double theta[6],
+                          double *M_reim)
+{
+    if (profile == OR_PROFILE_EXPONENTIAL) {
+        or_model_spectrum_t(N, p, T, theta, M_reim);
+        return;
+    }
+    int c = (N - 1) / 2;
+    double F = pow(10.0, theta[0]);
+    double r0 = pow(10.0, theta[1]) / or_hlr_over_r0_p(profile, nu);
+    double e1 = theta[2], e2 = theta[3], dx = theta[4], dy = theta[5];
+    double E = e1 * e1 + e2 * e2;
+    double dk = 2.0 * OR_PI / (N * p);
+    for (int v = -c; v <= c; ++v) {
+        for (int u = -c; u <= c; ++u) {
+            double kx = u * dk, ky = v * dk, k2 = kx * kx + ky * ky;
+            double q = ((1.0 + E) * k2 + 2.0 * e1 * (kx * kx - ky * ky) + 4.0 * e2 * kx * ky) / (1.0 - E);
+            size_t idx = (size_t)(v + c) * N + (u + c);
+            double amp = F * or_profile_ft(profile, nu, r0 * r0 * q) * T[idx];
             double complex Mk = amp * cexp(-I * p * (kx * dx + ky * dy));
             M_reim[2 * idx] = creal(Mk);
             M_reim[2 * idx + 1] = cimag(Mk);

@@ -180,6 +180,14 @@ static bs_status fill_fit_params(const bs_fit_args *a, bs::FitParams &p, const c
     p.sigma = a->noise_sigma;
     p.n_exp = n_exp;
     p.noise_corr = a->noise_corr;
+    if (a->profile != BS_PROFILE_EXPONENTIAL && a->profile != BS_PROFILE_SPERGEL && a->profile != BS_PROFILE_GAUSSIAN)
+        return fail(BS_ERR_INVALID_ARG, "%s: profile", who);
+    if (a->profile == BS_PROFILE_SPERGEL && !(a->spergel_nu >= -0.9f && a->spergel_nu <= 4.0f))
+        return fail(BS_ERR_INVALID_ARG, "%s: spergel_nu must be in [-0.9, 4]", who);
+    p.profile = a->profile;
+    p.prof_c = a->profile == BS_PROFILE_SPERGEL ? 1.0f + a->spergel_nu : a->profile == BS_PROFILE_GAUSSIAN ? 0.5f : 1.5f;
+    p.prof_npow = a->profile == BS_PROFILE_SPERGEL ? -(1.0f + a->spergel_nu) : -1.5f;
+    p.inv_hlr_r0 = (float)(1.0 / bs::profile_hlr_over_r0(a->profile, a->spergel_nu));
     p.gal_id = a->gal_id;
     p.init = a->init;
     p.init_step = a->init_step_size;
@@ -273,7 +281,7 @@ bs_status bs_fit_galaxies(const bs_fit_args *a, const bs_fit_out *o, void *works
     int dev = 0, sms = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int per_sm = bs::fit_blocks_per_sm(a->n_chains, a->max_side, p.regs);
+    const int per_sm = bs::fit_blocks_per_sm(a->n_chains, a->max_side, p.regs, p.profile);
     long long grid = (long long)sms * per_sm;
     if (grid > a->n_gal) grid = a->n_gal;
     e = bs::launch_fit(p, (int)grid, s);

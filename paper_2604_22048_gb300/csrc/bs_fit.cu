@@ -1,1088 +1,22 @@
-// Image sampling phase on sm_103a: per-galaxy HMC on the interim posterior
-// (Sec. 3.3; Eq. interim-post = Eq. likelihood-pixels x Eq. interim-prior).
-//
-// Layout.  A persistent CTA takes one galaxy at a time from an atomic work
-// queue and runs its n_chains chains, one warp per chain.  Per galaxy the CTA
-// stages in shared memory, once:
-//   Dt[u][v] = (sqrt(w_u)/N) DFT(d)(u, v)          (data spectrum)
-//   Tt[u][v] = (sqrt(w_u)/N) PSF(|k|) sinc(kx p/2) sinc(ky p/2)
-// on the half plane u = 0..c (c = (N-1)/2), v = -c..c, with w_0 = 1 and
-// w_u = 2 for u > 0 (the other half is the complex conjugate: d and the
-// model are real).  Lane l owns the columns v = l + 32 j - c, j < NC.
-//
-// Evaluation.  The model spectrum M(k) (Sec. 3.3 forward model: exponential
-// profile (1 + r0^2 k^T S^2 k)^{-3/2}, PSF and pixel transfer, centroid
-// phase) is formed point by point; since the model image is the inverse DFT
-// of M on the stamp's periodic grid, Parseval gives
-//   chi^2 = sum_pixels (d - m)^2 = sum_half |Dt - Mt|^2,
-//   d chi^2/d theta = -2 sum_half Re[conj(Dt - Mt) dMt/dtheta],
-// i.e. the residual's adjoint DFT is Dt - Mt exactly, and the per-evaluation
-// cost is one pass over the half plane instead of two O(N^3) transforms.
-// The gradient needs seven sums, accumulated per lane in FP32 and reduced
-// with an xor butterfly (identical bits in all lanes, so warp-uniform
-// decisions stay uniform); chi^2 is accumulated with compensated FP32 per
-// lane and finished in FP64 at the warp total.
-//
-// Chain state.  Lane i < 6 owns parameter i of the chain (position hi/lo,
-// momentum, gradient, inverse metric, Welford moments) as scalars; the six
-// positions are gathered with shuffles before each evaluation.  Energies are
-// butterfly sums, so accept and divergence decisions are warp-uniform.
-//
-// Sampler (same algorithm as the oracle, written independently): Philox4x64-10
-// keyed by (seed, galaxy_id * n_chains + chain); fixed-L or random-L HMC with
-// a diagonal metric; dual averaging of the step size (Hoffman & Gelman 2014,
-// gamma 0.05, t0 10, kappa 0.75); Stan-style windowed metric adaptation; a
-// doubling/halving step-size search at the start and after each window.
-#include <cmath>
-#include <cstdio>
-#include <cstdlib>
-
-#include "bs_device.cuh"
-#include "bs_internal.h"
+// Launches of the image-sampling kernels of bs_fit_impl.cuh: the instance is
+// chosen by the column slots per lane of the largest stamp (smaller stamps of
+// the same launch see zero-padded columns), the register budget and the
+// galaxy profile.  The exponential instances live here; the Spergel and
+// Gaussian ones (Appendix B) in bs_fit_prof.cu, compiled in parallel.
+#include "bs_fit_impl.cuh"
 
 namespace bs {
 
 namespace {
 
-struct GalCtx {
-    int N, H, c, NC;
-    float dk;      // 2 pi / (N p)
-    float p;       // pixel scale
-    float invN;
-    float inv_b;   // 1 / sigma^2 (1 when the exposures are folded into the table)
-};
-
-// chi^2 of the galaxy's exposures minus that of its folded table (a constant
-// of the galaxy, 0 for one exposure with white noise); in shared memory, so
-// that it takes no register in the chains' loop.
-__shared__ double s_chi2_off;
-
-// Row layout of the staged tables for NCT = npad / 32 column slots per lane
-// (3 * npad floats per row u).  Slots are paired, (2p, 2p+1), so that a lane
-// loads both slots of a pair with one 8-byte access and the pair is processed
-// with packed FP32x2 arithmetic:
-//   pair p:      [Dx pairs: 64][Dy pairs: 64][T pairs: 64]   (float2 per lane)
-//   odd slot:    [D (x, y): 64][T: 32]                        (last slot, NCT odd)
-__host__ __device__ __forceinline__ int row_floats(int npad) { return 3 * npad; }
-
-// Per-chain phase tables X(u) = exp(-2 pi i u dx / N) of one evaluation, in
-// the setup scratch (free once the galaxy is staged), extended when the
-// chains need more than it holds.
-// Per-chain stride of the phase tables: even, so that every table (read as
-// pairs X(u), X(u+1) with 16-byte loads, u even) starts 16-byte aligned.
-__host__ __device__ __forceinline__ int phase_stride(int h_max) { return (h_max + 1) & ~1; }
-
-// float2 slots of the scratch: the setup's three rows, or the chains' phase
-// tables if larger; even, so that the (kx, kx^2) table after it stays 16-byte
-// aligned.
-__host__ __device__ __forceinline__ int scratch_float2(int max_side, int h_max, int n_chains)
-{
-    const int setup = 3 * max_side + 4;
-    const int phase = n_chains * phase_stride(h_max);
-    const int n = setup > phase ? setup : phase;
-    return (n + 1) & ~1;
-}
-
-struct SmemView {
-    float *tab;    // [h_max][3 npad] data spectrum and transfer, paired layout
-    float2 *G;     // [max_side], setup scratch (one frequency row)
-    float2 *tw;    // [max_side]
-    float2 *Gc;    // [max_side], setup scratch (a row of the noise correlation's transform)
-    float2 *xph;   // [n_chains][phase_stride(h_max)] phase tables (aliases G, tw after setup)
-    float2 *kxr;   // [h_max]: (kx, kx^2) of row u
-};
-
-__device__ __forceinline__ SmemView smem_view(unsigned char *base, int h_max, int npad, int max_side, int n_chains)
-{
-    SmemView v;
-    v.tab = reinterpret_cast<float *>(base);
-    v.G = reinterpret_cast<float2 *>(v.tab + (size_t)h_max * row_floats(npad));
-    v.tw = v.G + (size_t)max_side;
-    v.Gc = v.tw + (size_t)max_side;
-    v.xph = v.G;
-    v.kxr = v.G + (size_t)scratch_float2(max_side, h_max, n_chains);
-    return v;
-}
-
-// Positions of slot j of lane l within a row: Dx, Dy, T.
-__device__ __forceinline__ void slot_offsets(int npad, int j, int l, int &ox, int &oy, int &ot)
-{
-    const int nct = npad >> 5, npair = nct >> 1;
-    const int p = j >> 1;
-    if (p < npair) {
-        const int base = p * 192, h = j & 1;
-        ox = base + 2 * l + h;
-        oy = base + 64 + 2 * l + h;
-        ot = base + 128 + 2 * l + h;
-    } else {
-        const int base = npair * 192;
-        ox = base + 2 * l;
-        oy = base + 2 * l + 1;
-        ot = base + 64 + l;
-    }
-}
-
-// (x/2)^nu K_nu(x) from K_nu(x) = int_0^inf exp(-x cosh t) cosh(nu t) dt by the
-// trapezoidal rule (step 1/4); the factor (x/2)^nu is folded into the
-// exponent so the integrand stays bounded for small x.
-__device__ float half_x_pow_knu(float nu, float x)
-{
-    const float lx = logf(0.5f * x);
-    const float h = 0.25f;
-    float sum = 0.5f * expf(-x + nu * lx);
-    for (int j = 1; j < 400; ++j) {
-        const float t = j * h;
-        const float ch = coshf(t);
-        const float a = -x * ch;
-        const float term = 0.5f * (expf(a + nu * (lx + t)) + expf(a + nu * (lx - t)));
-        sum += term;
-        if (x * ch > nu * t + 40.f && term <= 1e-9f * sum) break;
-    }
-    return sum * h;
-}
-
-// Transform of the unit-flux PSF at |k| (1/arcsec).
-__device__ float psf_transfer(const bs_psf &ps, float k)
-{
-    if (ps.kind == BS_PSF_GAUSSIAN) {
-        const float s = ps.fwhm * (1.0f / 2.3548200450309493f);
-        return expf(-0.5f * k * k * s * s);
-    }
-    // Moffat: (2 / Gamma(beta - 1)) (x/2)^(beta-1) K_(beta-1)(x), x = k rd
-    const float beta = ps.beta;
-    const float rd = ps.fwhm / (2.0f * sqrtf(exp2f(1.0f / beta) - 1.0f));
-    const float x = k * rd;
-    if (x == 0.0f) return 1.0f;
-    const float nu = beta - 1.0f;
-    return 2.0f / tgammaf(nu) * half_x_pow_knu(nu, x);
-}
-
-// sin(pi x) / (pi x)
-__device__ __forceinline__ float sincpi(float x)
-{
-    return x == 0.0f ? 1.0f : sinpif(x) / (3.14159265358979f * x);
-}
-
-__device__ __forceinline__ float load_pix(const void *data, int f64, int64_t idx)
-{
-    return f64 ? (float)__ldg(static_cast<const double *>(data) + idx)
-               : __ldg(static_cast<const float *>(data) + idx);
-}
-
-// A stamp side the shared-memory layout of this launch can hold.
-__device__ __forceinline__ bool side_ok(const FitParams &P, int N)
-{
-    return N >= 3 && N <= P.max_side && (N & 1);
-}
-
-// G[iy] = sum_ix img[iy][ix] exp(-2 pi i u (ix - c) / N): the x transform of
-// the N x N image at `off`, frequency u (threads of the CTA over rows).
-__device__ __forceinline__ void row_dft(const void *img, int f64, int64_t off, int N, int c, int u,
-                                        const float2 *tw, float2 *G)
-{
-    for (int iy = threadIdx.x; iy < N; iy += blockDim.x) {
-        int idx = (int)(((long long)(N - u) * c) % N);   // -u c mod N
-        float re = 0.f, im = 0.f;
-        const int64_t rowoff = off + (int64_t)iy * N;
-        for (int ix = 0; ix < N; ++ix) {
-            const float d = load_pix(img, f64, rowoff + ix);
-            const float2 t = tw[idx];
-            re = fmaf(d, t.x, re);
-            im = fmaf(-d, t.y, im);
-            idx += u;
-            if (idx >= N) idx -= N;
-        }
-        G[iy] = make_float2(re, im);
-    }
-}
-
-// sum_iy G[iy] exp(-2 pi i v (iy - c) / N): the y transform at frequency v.
-__device__ __forceinline__ float2 col_dft(const float2 *G, int N, int c, int v, const float2 *tw)
-{
-    const int vm = ((v % N) + N) % N;
-    int idx = (int)(((long long)(N - vm) * c) % N);   // -v c mod N
-    float re = 0.f, im = 0.f;
-    for (int iy = 0; iy < N; ++iy) {
-        const float2 gv = G[iy];
-        const float2 t = tw[idx];
-        // gv * conj(t)
-        re = fmaf(gv.x, t.x, fmaf(gv.y, t.y, re));
-        im = fmaf(gv.y, t.x, fmaf(-gv.x, t.y, im));
-        idx += vm;
-        if (idx >= N) idx -= N;
-    }
-    return make_float2(re, im);
-}
-
-// scale x the PSF x pixel transfer of psf `ps` at grid point (u, v).
-__device__ __forceinline__ float transfer_at(const bs_psf &ps, const GalCtx &gc, int u, int v, float scale)
-{
-    const float kx = u * gc.dk, ky = v * gc.dk;
-    return scale * psf_transfer(ps, sqrtf(kx * kx + ky * ky)) * sincpi((float)u * gc.invN) *
-           sincpi((float)v * gc.invN);
-}
-
-// Sum over the CTA of one double per thread, in a fixed order.
-__device__ double block_sum_d(double v)
-{
-    __shared__ double part[32];
-    v = warp_sum_d(v);
-    const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-    if ((threadIdx.x & 31) == 0) part[w] = v;
-    __syncthreads();
-    double t = 0.0;
-    for (int i = 0; i < nw; ++i) t += part[i];
-    __syncthreads();
-    return t;
-}
-
-// Appendix C: the galaxy's J exposures on one grid, exposure j with its own
-// transfer T_j and noise covariance sigma_j^2 C_j, C_j circulant with
-// spectrum lambda_j(k) (the transform of the correlation at lag).  Each
-// Gaussian term is diagonal in k,
-//   r_j^T Sigma_j^-1 r_j = (1/N^2) sum_k |D_j - T_j G|^2 / (sigma_j^2 lambda_j),
-// with G the galaxy's (PSF-free) spectrum, and the sum over exposures is one
-// term of the single-exposure form plus a constant:
-//   sum_j W_j |D_j - T_j G|^2 = S |C/S - G|^2 + (E - |C|^2/S),
-//   W_j = 1/(sigma_j^2 lambda_j), S = sum_j W_j T_j^2, C = sum_j W_j T_j D_j,
-//   E = sum_j W_j |D_j|^2.
-// So the table holds T' = sqrt(S) and D' = C/sqrt(S) (with inv_b = 1) and the
-// fit kernel runs unchanged; the constant goes to chi2_off so that the
-// log posterior is that of the exposures.  Returns false (uniform across the
-// CTA) when some lambda_j is not positive.
-__device__ bool setup_folded(const FitParams &P, int gal, const SmemView &sm, GalCtx &gc)
-{
-    const int N = gc.N, c = gc.c, H = gc.H, J = P.n_exp;
-    const int npad = P.npad, rowf = row_floats(npad);
-    const int tid = threadIdx.x, nth = blockDim.x;
-    const float sqrt2 = 1.41421356237309515f;
-    const int64_t off0 = P.offsets[gal];
-    const int64_t NN = (int64_t)N * N;
-    double cacc = 0.0;
-    bool bad = false;
-    for (int u = 0; u < H; ++u) {
-        float *row = sm.tab + (size_t)u * rowf;
-        const float scale = (u == 0 ? 1.0f : sqrt2) * gc.invN;
-        const double s2 = (double)scale * scale;
-        for (int j = 0; j < J; ++j) {
-            const int64_t off = off0 + (int64_t)j * NN;
-            row_dft(P.data, P.data_f64, off, N, c, u, sm.tw, sm.G);
-            if (P.noise_corr) row_dft(P.noise_corr, 0, off, N, c, u, sm.tw, sm.Gc);
-            __syncthreads();
-            const bs_psf ps = P.psf[P.n_psf == 1 ? 0 : (int64_t)gal * J + j];
-            const float sig = P.sigma[(int64_t)gal * J + j];
-            for (int vi = tid; vi < npad; vi += nth) {
-                float Cx = 0.f, Cy = 0.f, S = 0.f;
-                if (vi < N) {
-                    const int v = vi - c;
-                    const float2 D = col_dft(sm.G, N, c, v, sm.tw);
-                    float lam = P.noise_corr ? col_dft(sm.Gc, N, c, v, sm.tw).x : 1.0f;
-                    if (!(lam > 0.f)) {
-                        bad = true;
-                        lam = 1.0f;
-                    }
-                    const float Wj = 1.0f / (sig * sig * lam);
-                    const float T = transfer_at(ps, gc, u, v, 1.0f);
-                    const float WT = Wj * T;
-                    Cx = WT * D.x;
-                    Cy = WT * D.y;
-                    S = WT * T;
-                    cacc += s2 * (double)Wj * ((double)D.x * D.x + (double)D.y * D.y);
-                }
-                int ox, oy, ot;
-                slot_offsets(npad, vi >> 5, vi & 31, ox, oy, ot);
-                if (j == 0) {
-                    row[ox] = Cx;
-                    row[oy] = Cy;
-                    row[ot] = S;
-                } else {
-                    row[ox] += Cx;
-                    row[oy] += Cy;
-                    row[ot] += S;
-                }
-            }
-            __syncthreads();   // G and Gc are rewritten by the next exposure
-        }
-        // (C, S) -> (D', T'), each thread on the columns it accumulated
-        for (int vi = tid; vi < N; vi += nth) {
-            int ox, oy, ot;
-            slot_offsets(npad, vi >> 5, vi & 31, ox, oy, ot);
-            const float Cx = row[ox], Cy = row[oy], S = row[ot];
-            float Dx = 0.f, Dy = 0.f, T = 0.f;
-            if (S > 0.f) {
-                const float rs = rsqrtf(S);
-                T = scale * S * rs;
-                Dx = scale * Cx * rs;
-                Dy = scale * Cy * rs;
-                cacc -= s2 * ((double)Cx * Cx + (double)Cy * Cy) / (double)S;
-            }
-            row[ox] = Dx;
-            row[oy] = Dy;
-            row[ot] = T;
-        }
-    }
-    gc.inv_b = 1.0f;
-    const double off = block_sum_d(cacc);
-    if (tid == 0) s_chi2_off = off;
-    return __syncthreads_or(bad) == 0;
-}
-
-// Stage the galaxy's data spectrum and transfer table (all threads of the CTA).
-// The caller has checked side_ok.  Returns false, uniformly, when the galaxy
-// cannot be fitted (a noise correlation without a positive spectrum).
-__device__ bool setup_galaxy(const FitParams &P, int gal, const SmemView &sm, GalCtx &gc)
-{
-    const int N = P.side[gal];
-    const int c = (N - 1) / 2;
-    const int H = c + 1;
-    const int npad = P.npad;
-    const int tid = threadIdx.x, nth = blockDim.x;
-    gc.N = N;
-    gc.H = H;
-    gc.c = c;
-    gc.NC = (N + 31) / 32;
-    gc.p = P.pixel_scale;
-    gc.dk = 6.283185307179586f / ((float)N * P.pixel_scale);
-    gc.invN = 1.0f / (float)N;
-    if (tid == 0) s_chi2_off = 0.0;
-
-    for (int m = tid; m < N; m += nth) {
-        float s, co;
-        sincospif(2.0f * (float)m / (float)N, &s, &co);
-        sm.tw[m] = make_float2(co, s);   // exp(+2 pi i m / N)
-    }
-    for (int u = tid; u < H; u += nth) {
-        const float kx = (float)u * gc.dk;
-        sm.kxr[u] = make_float2(kx, kx * kx);
-    }
-    __syncthreads();
-    if (P.n_exp > 1 || P.noise_corr) return setup_folded(P, gal, sm, gc);
-
-    const float sig = P.sigma[gal];
-    gc.inv_b = 1.0f / (sig * sig);
-    const int64_t off = P.offsets[gal];
-    const bs_psf ps = P.psf[P.n_psf == 1 ? 0 : gal];
-    const float sqrt2 = 1.41421356237309515f;
-    const int rowf = row_floats(npad);
-    // one frequency row u at a time, so the scratch is a single column G[iy]
-    for (int u = 0; u < H; ++u) {
-        row_dft(P.data, P.data_f64, off, N, c, u, sm.tw, sm.G);
-        __syncthreads();
-        // D(u, v) = sum_iy G[iy] exp(-2 pi i v (iy - c) / N), scaled; transfer T(u, v)
-        float *row = sm.tab + (size_t)u * rowf;
-        const float scale = (u == 0 ? 1.0f : sqrt2) * gc.invN;
-        for (int vi = tid; vi < npad; vi += nth) {
-            float2 Dv = make_float2(0.f, 0.f);
-            float Tv = 0.f;
-            if (vi < N) {
-                const int v = vi - c;
-                const float2 D = col_dft(sm.G, N, c, v, sm.tw);
-                Dv = make_float2(D.x * scale, D.y * scale);
-                Tv = transfer_at(ps, gc, u, v, scale);
-            }
-            int ox, oy, ot;
-            slot_offsets(npad, vi >> 5, vi & 31, ox, oy, ot);
-            row[ox] = Dv.x;
-            row[oy] = Dv.y;
-            row[ot] = Tv;
-        }
-        __syncthreads();
-    }
-    return true;
-}
-
-__device__ __forceinline__ bool in_support(const FitParams &P, const float th[6])
-{
-    const float E = th[2] * th[2] + th[3] * th[3];
-    return th[0] > P.lf_lo && th[0] < P.lf_hi && th[1] > P.ls_lo && th[1] < P.ls_hi && E < 1.0f;
-}
-
-// 1/sqrt(s) for s >= 1 (the profile argument 1 + r0^2 q(k)): the hardware
-// approximation with denormal flushing, which cannot occur here, so no
-// range fix-ups are issued around it.
-__device__ __forceinline__ float rsqrt_ge1(float s)
-{
-    float r;
-    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(s));
-    return r;
-}
-
-// Packed FP32x2 helpers (two column slots of a lane in one instruction; each
-// half is rounded exactly like the scalar operation).
-__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
-__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-// a - b on both halves in one packed instruction (no packed negation exists
-// to fold into an add).
-__device__ __forceinline__ float2 sub2(float2 a, float2 b)
-{
-    float2 d;
-    asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
-        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
-        "sub.rn.f32x2 rd, ra, rb;\n\t"
-        "mov.b64 {%0, %1}, rd;\n\t}"
-        : "=f"(d.x), "=f"(d.y)
-        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
-    return d;
-}
-
-// Compensated accumulation of both halves (Knuth's TwoSum, packed).
-__device__ __forceinline__ void comp_add2(float2 &hi, float2 &lo, float2 x)
-{
-    const float2 s = add2(hi, x);
-    const float2 bp = sub2(s, hi);
-    const float2 ap = sub2(s, bp);
-    const float2 e = add2(sub2(hi, ap), sub2(x, bp));
-    hi = s;
-    lo = add2(lo, e);
-}
-
-// Per-lane partial sums of one evaluation: slot pairs packed, odd slot scalar.
-template <int NCT>
-struct Sums {
-    static constexpr int NP = NCT / 2 > 0 ? NCT / 2 : 1;
-    float2 Sa, Swkx2, Sbkx;                 // sum a, sum w kx^2, sum b kx (both halves)
-    float2 Wc[NP], Wkx[NP], Bc[NP];         // per slot: sum w, sum w kx, sum b
-    float sWc, sWkx, sBc;                   // odd slot
-    float2 chi_hi, chi_lo;                  // compensated sum |Dt - Mt|^2
-};
-
-// Per-lane, per-slot constants of one evaluation.
-template <int NCT>
-struct SlotConst {
-    static constexpr int NP = NCT / 2 > 0 ? NCT / 2 : 1;
-    float2 Yr[NP], Yi[NP], nYi[NP], cst[NP], gky[NP];   // F exp(-i ky p dy) (and -Im), 1 + be ky^2, ga ky
-    float sYr, sYi, scst, sgky;
-};
-
-// Model-data terms of one row u for all column slots of this lane.
-template <int NCT, bool LL>
-__device__ __forceinline__ void row_terms(Sums<NCT> &S, const SlotConst<NCT> &K,
-                                          const float *__restrict__ row, float kx, float kx2, float al,
-                                          float Xr, float Xi, float F2)
-{
-    constexpr int NPAIR = NCT / 2;
-    const int lane = threadIdx.x & 31;
-    const float2 kxv = f2(kx), kx2v = f2(kx2), alv = f2(al), Xrv = f2(Xr), Xiv = f2(Xi);
-    const float2 nF2v = f2(-F2);
-#pragma unroll
-    for (int p = 0; p < NPAIR; ++p) {
-        const float *b = row + p * 192 + 2 * lane;
-        const float2 Dx = *reinterpret_cast<const float2 *>(b);
-        const float2 Dy = *reinterpret_cast<const float2 *>(b + 64);
-        const float2 T = *reinterpret_cast<const float2 *>(b + 128);
-        const float2 s = fma2(fma2(alv, kxv, K.gky[p]), kxv, K.cst[p]);   // 1 + r0^2 q(k), Horner in kx
-        const float2 rs = make_float2(rsqrt_ge1(s.x), rsqrt_ge1(s.y));
-        const float2 rs2 = mul2(rs, rs);
-        const float2 A = mul2(mul2(T, rs2), rs);                        // |M| / F
-        const float2 Pr = fma2(Xiv, K.nYi[p], mul2(Xrv, K.Yr[p]));      // F exp(-i k.delta)
-        const float2 Pi = fma2(Xiv, K.Yr[p], mul2(Xrv, K.Yi[p]));
-        const float2 zr = fma2(Dx, Pr, mul2(Dy, Pi));                  // conj(D) * phase
-        const float2 zi = sub2(mul2(Dx, Pi), mul2(Dy, Pr));
-        const float2 a = mul2(A, fma2(A, nF2v, zr));                    // Re conj(D - M) M
-        const float2 bb = mul2(A, zi);                                  // Im conj(D - M) M
-        const float2 w = mul2(a, rs2);                                  // a / s
-        S.Sa = add2(S.Sa, a);
-        S.Wc[p] = add2(S.Wc[p], w);
-        S.Wkx[p] = fma2(w, kxv, S.Wkx[p]);
-        S.Swkx2 = fma2(w, kx2v, S.Swkx2);
-        S.Bc[p] = add2(S.Bc[p], bb);
-        S.Sbkx = fma2(bb, kxv, S.Sbkx);
-        if (LL) {
-            const float2 Rr = sub2(Dx, mul2(A, Pr));
-            const float2 Ri = sub2(Dy, mul2(A, Pi));
-            comp_add2(S.chi_hi, S.chi_lo, fma2(Rr, Rr, mul2(Ri, Ri)));
-        }
-    }
-    if (NCT & 1) {
-        const float *b = row + NPAIR * 192;
-        const float2 D = *reinterpret_cast<const float2 *>(b + 2 * lane);
-        const float T = b[64 + lane];
-        const float s = fmaf(fmaf(al, kx, K.sgky), kx, K.scst);
-        const float rs = rsqrt_ge1(s);
-        const float rs2 = rs * rs;
-        const float A = T * rs2 * rs;
-        const float Pr = Xr * K.sYr - Xi * K.sYi;
-        const float Pi = Xr * K.sYi + Xi * K.sYr;
-        const float zr = fmaf(D.x, Pr, D.y * Pi);
-        const float zi = fmaf(D.x, Pi, -D.y * Pr);
-        const float a = A * fmaf(-A, F2, zr);
-        const float bb = A * zi;
-        const float w = a * rs2;
-        S.Sa.x += a;
-        S.sWc += w;
-        S.sWkx = fmaf(w, kx, S.sWkx);
-        S.Swkx2.x = fmaf(w, kx2, S.Swkx2.x);
-        S.sBc += bb;
-        S.Sbkx.x = fmaf(bb, kx, S.Sbkx.x);
-        if (LL) {
-            const float Rr = fmaf(-A, Pr, D.x);
-            const float Ri = fmaf(-A, Pi, D.y);
-            comp_add(S.chi_hi.x, S.chi_lo.x, fmaf(Rr, Rr, Ri * Ri));
-        }
-    }
-}
-
-// Half-plane pass, two rows per iteration (the row phase advances by
-// exp(-2 pi i dx / N) per row).
-template <int NCT, bool LL>
-__device__ __forceinline__ void half_plane(Sums<NCT> &S, const SlotConst<NCT> &K,
-                                           const float *__restrict__ tab, const float2 *__restrict__ kxr,
-                                           const float2 *__restrict__ xph, int H, float al, float F2)
-{
-    constexpr int ROWF = 96 * NCT;
-    const float *row = tab;
-    int u = 0;
-    for (; u + 1 < H; u += 2) {
-        const float4 k01 = *reinterpret_cast<const float4 *>(kxr + u);   // (kx, kx^2) of rows u, u+1
-        const float4 x01 = *reinterpret_cast<const float4 *>(xph + u);   // X(u), X(u+1)
-        row_terms<NCT, LL>(S, K, row, k01.x, k01.y, al, x01.x, x01.y, F2);
-        row_terms<NCT, LL>(S, K, row + ROWF, k01.z, k01.w, al, x01.z, x01.w, F2);
-        row += 2 * ROWF;
-    }
-    if (u < H) {
-        const float2 k0 = kxr[u];
-        const float2 x0 = xph[u];
-        row_terms<NCT, LL>(S, K, row, k0.x, k0.y, al, x0.x, x0.y, F2);
-    }
-}
-
-// Sums over the warp of seven per-lane values, returned in every lane with
-// identical bits.  Recursive halving: at each xor distance a lane keeps half
-// of its values and receives the partner's partial sums of them, so after
-// distances 16, 8, 4 lane l holds value (l >> 2) & 7 summed over 8 lanes; two
-// butterfly steps finish it (commutative adds, so the 4 lanes of a group
-// agree) and one shuffle per value broadcasts it from lane 4 j.
-__device__ __forceinline__ void warp_sum7(float (&v)[7])
-{
-    const int lane = threadIdx.x & 31;
-    float r4[4];
-    const bool h16 = lane & 16;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const float lo = v[k], hi = k + 4 < 7 ? v[k + 4] : 0.0f;
-        const float keep = h16 ? hi : lo, send = h16 ? lo : hi;
-        r4[k] = keep + __shfl_xor_sync(BS_FULL_MASK, send, 16);
-    }
-    float r2[2];
-    const bool h8 = lane & 8;
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        const float keep = h8 ? r4[k + 2] : r4[k], send = h8 ? r4[k] : r4[k + 2];
-        r2[k] = keep + __shfl_xor_sync(BS_FULL_MASK, send, 8);
-    }
-    const bool h4 = lane & 4;
-    float r = (h4 ? r2[1] : r2[0]) + __shfl_xor_sync(BS_FULL_MASK, h4 ? r2[0] : r2[1], 4);
-    r += __shfl_xor_sync(BS_FULL_MASK, r, 2);
-    r += __shfl_xor_sync(BS_FULL_MASK, r, 1);
-#pragma unroll
-    for (int j = 0; j < 7; ++j) v[j] = __shfl_sync(BS_FULL_MASK, r, 4 * j);
-}
-
-// Log posterior (if want_ll) and gradient at th, warp-cooperative.
-template <int NC>
-__device__ __forceinline__ double eval_logpost(const FitParams &P, const GalCtx &gc,
-                                               const float *__restrict__ tab, const float2 *__restrict__ kxr,
-                                               float2 *__restrict__ xph, const float vcol[NC], const float th[6],
-                                               float g[6], bool want_ll)
-{
-    const float F = exp10f(th[0]);
-    const float r0 = exp10f(th[1]) * (1.0f / kHlrOverR0);
-    const float r02 = r0 * r0;
-    const float e1 = th[2], e2 = th[3];
-    const float E = e1 * e1 + e2 * e2;
-    const float Pq = 1.0f / (1.0f - E);
-    const float al = r02 * (1.0f + E + 2.0f * e1) * Pq;   // coefficient of kx^2 in r0^2 q
-    const float be = r02 * (1.0f + E - 2.0f * e1) * Pq;   // ky^2
-    const float ga = r02 * 4.0f * e2 * Pq;                // kx ky
-    const float F2 = F * F;
-    const float dk = gc.dk;
-
-    // this chain's phase table X(u) = exp(-2 pi i u dx / N), u < H
-    {
-        const int lane = threadIdx.x & 31;
-        for (int u = lane; u < gc.H; u += 32) {
-            float sx, cx;
-            sincospif(-2.0f * th[4] * (float)u * gc.invN, &sx, &cx);
-            xph[u] = make_float2(cx, sx);
-        }
-        __syncwarp();
-    }
-    float Yr[NC], Yi[NC], cst[NC], gky[NC], ky[NC];
-#pragma unroll
-    for (int j = 0; j < NC; ++j) {
-        float s, co;
-        sincospif(-2.0f * th[5] * vcol[j] * gc.invN, &s, &co);   // exp(-2 pi i v dy / N)
-        Yr[j] = F * co;
-        Yi[j] = F * s;
-        ky[j] = vcol[j] * dk;
-        cst[j] = fmaf(be * ky[j], ky[j], 1.0f);
-        gky[j] = ga * ky[j];
-    }
-    SlotConst<NC> K;
-    Sums<NC> S;
-    constexpr int NPAIR = NC / 2;
-#pragma unroll
-    for (int p = 0; p < NPAIR; ++p) {
-        K.Yr[p] = make_float2(Yr[2 * p], Yr[2 * p + 1]);
-        K.Yi[p] = make_float2(Yi[2 * p], Yi[2 * p + 1]);
-        K.nYi[p] = make_float2(-Yi[2 * p], -Yi[2 * p + 1]);
-        K.cst[p] = make_float2(cst[2 * p], cst[2 * p + 1]);
-        K.gky[p] = make_float2(gky[2 * p], gky[2 * p + 1]);
-        S.Wc[p] = f2(0.f);
-        S.Wkx[p] = f2(0.f);
-        S.Bc[p] = f2(0.f);
-    }
-    if (NC & 1) {
-        K.sYr = Yr[NC - 1];
-        K.sYi = Yi[NC - 1];
-        K.scst = cst[NC - 1];
-        K.sgky = gky[NC - 1];
-    }
-    S.Sa = f2(0.f);
-    S.Swkx2 = f2(0.f);
-    S.Sbkx = f2(0.f);
-    S.sWc = 0.f;
-    S.sWkx = 0.f;
-    S.sBc = 0.f;
-    S.chi_hi = f2(0.f);
-    S.chi_lo = f2(0.f);
-    if (want_ll)
-        half_plane<NC, true>(S, K, tab, kxr, xph, gc.H, al, F2);
-    else
-        half_plane<NC, false>(S, K, tab, kxr, xph, gc.H, al, F2);
-    __syncwarp();   // the table is rewritten by the next evaluation
-
-    float Sa = S.Sa.x + S.Sa.y, Swkx2 = S.Swkx2.x + S.Swkx2.y, Sbkx = S.Sbkx.x + S.Sbkx.y;
-    float Sw = 0.f, Swky2 = 0.f, Swkxky = 0.f, Sbky = 0.f;
-#pragma unroll
-    for (int j = 0; j < NC; ++j) {
-        float wc, wkx, bc;
-        if (j < 2 * NPAIR) {
-            const int p = j >> 1;
-            wc = (j & 1) ? S.Wc[p].y : S.Wc[p].x;
-            wkx = (j & 1) ? S.Wkx[p].y : S.Wkx[p].x;
-            bc = (j & 1) ? S.Bc[p].y : S.Bc[p].x;
-        } else {
-            wc = S.sWc;
-            wkx = S.sWkx;
-            bc = S.sBc;
-        }
-        Sw += wc;
-        Swky2 = fmaf(ky[j] * ky[j], wc, Swky2);
-        Swkxky = fmaf(ky[j], wkx, Swkxky);
-        Sbky = fmaf(ky[j], bc, Sbky);
-    }
-    float sums[7] = {Sa, Sw, Swkx2, Swky2, Swkxky, Sbkx, Sbky};
-    warp_sum7(sums);
-    Sa = sums[0];
-    Sw = sums[1];
-    Swkx2 = sums[2];
-    Swky2 = sums[3];
-    Swkxky = sums[4];
-    Sbkx = sums[5];
-    Sbky = sums[6];
-
-    const float ib = gc.inv_b;
-    const float P2 = Pq * Pq;
-    // derivatives of the quadratic-form coefficients with respect to e1, e2
-    const float da1 = r02 * ((2.0f * e1 + 2.0f) * Pq + (1.0f + E + 2.0f * e1) * 2.0f * e1 * P2);
-    const float da2 = r02 * (2.0f * e2 * Pq + (1.0f + E + 2.0f * e1) * 2.0f * e2 * P2);
-    const float db1 = r02 * ((2.0f * e1 - 2.0f) * Pq + (1.0f + E - 2.0f * e1) * 2.0f * e1 * P2);
-    const float db2 = r02 * (2.0f * e2 * Pq + (1.0f + E - 2.0f * e1) * 2.0f * e2 * P2);
-    const float dg1 = r02 * 8.0f * e1 * e2 * P2;
-    const float dg2 = r02 * (4.0f * Pq + 8.0f * e2 * e2 * P2);
-    g[0] = kLn10 * Sa * ib;
-    g[1] = -3.0f * kLn10 * (Sa - Sw) * ib;
-    g[2] = -1.5f * (da1 * Swkx2 + db1 * Swky2 + dg1 * Swkxky) * ib - 4.0f * e1 * Pq - e1 * P.inv_se2;
-    g[3] = -1.5f * (da2 * Swkx2 + db2 * Swky2 + dg2 * Swkxky) * ib - 4.0f * e2 * Pq - e2 * P.inv_se2;
-    g[4] = gc.p * Sbkx * ib - th[4] * P.inv_sxy2;
-    g[5] = gc.p * Sbky * ib - th[5] * P.inv_sxy2;
-    if (!want_ll) return 0.0;
-    // merge the two halves of the compensated pair, then the warp
-    float chi_hi, chi_lo;
-    two_sum(S.chi_hi.x, S.chi_hi.y, chi_hi, chi_lo);
-    chi_lo += S.chi_lo.x + S.chi_lo.y;
-    const double chi2 = warp_sum_comp(chi_hi, chi_lo);
-    const float lprior = P.prior_const - 0.5f * (th[4] * th[4] + th[5] * th[5]) * P.inv_sxy2 +
-                         2.0f * log1pf(-E) - 0.5f * E * P.inv_se2;
-    return -0.5 * (chi2 + s_chi2_off) * (double)ib + (double)lprior;
-}
-
-__device__ __forceinline__ float pick6(const float (&v)[6], int i)
-{
-    float r = v[0];
-#pragma unroll
-    for (int k = 1; k < 6; ++k)
-        if (i == k) r = v[k];
-    return r;
-}
-
-// 1/2 sum_i m_i p_i^2 over the six parameter lanes (identical in all lanes).
-__device__ __forceinline__ double kinetic(float pm, float im, bool own)
-{
-    return 0.5 * (double)warp_sum(own ? im * pm * pm : 0.0f);
-}
-
-enum { MODE_INIT = 0, MODE_SEARCH = 1, MODE_STEP = 2 };
-
-template <int NC>
-__device__ void run_chain(const FitParams &P, const GalCtx &gc, const SmemView &sm, int gal,
-                          int chain)
-{
-    const int lane = threadIdx.x & 31;
-    const int pi = lane < 6 ? lane : 5;     // parameter of this lane (lanes 6.. shadow parameter 5)
-    const bool own = lane < 6;
-    const int C = P.n_chains, W = P.n_warmup, S = P.n_samples, L = P.n_leapfrog;
-    const uint64_t gid = P.gal_id ? P.gal_id[gal] : (uint64_t)gal;
-    const uint64_t key = gid * (uint64_t)C + (uint64_t)chain;
-    float vcol[NC];
-#pragma unroll
-    for (int j = 0; j < NC; ++j) vcol[j] = (float)(lane + 32 * j - gc.c);
-
-    const size_t ci0 = (size_t)gal * C + chain;
-    // this lane's parameter: position (hi, lo), gradient, inverse metric
-    float th = P.init[ci0 * 6 + pi], thl = 0.f, g = 0.f;
-    float im = P.init_im ? P.init_im[ci0 * 6 + pi] : 1.f;
-    float wmean = 0.f, wm2 = 0.f;
-    double lp = -INFINITY;
-    float eps = P.init_step ? P.init_step[ci0] : 1.0f;
-    float da_mu = 0.f, da_hbar = 0.f, da_lebar = 0.f;
-    int da_m = 0;
-    int wn = 0, wi = 0;
-    int s_idx = 0, s_t = 0, s_dir = 0;
-    float s_eps = 1.0f;
-    int it = 0;
-    float asum = 0.f;
-    int ndiv = 0;
-    int ngrad = 0;
-    int mode = MODE_INIT;
-    const double thr_search = -0.22314355131420976;   // ln 0.8
-    const size_t chain_row = ci0 * (size_t)S;
-    const size_t plane = (size_t)P.n_gal * C * S;
-
-    if (W + S == 0) mode = -1;
-    while (mode >= 0) {
-        float u[8];
-        float eps_use = 0.f;
-        int nst = 1;
-        if (mode == MODE_SEARCH) {
-            uniforms8(P.seed, key, (uint64_t)s_idx, 1ull, (uint64_t)s_t, u);
-            eps_use = s_eps;
-        } else if (mode == MODE_STEP) {
-            uniforms8(P.seed, key, (uint64_t)it, 0ull, 0ull, u);
-            eps_use = eps;
-            if (P.random_steps) {
-                // L_i = 1 + floor(u7 L), in integers: u7 = (2j + 1) 2^-25
-                const unsigned twoj1 = (unsigned)(u[7] * 33554432.0f);
-                nst = 1 + (int)(((unsigned long long)twoj1 * (unsigned)L) >> 25);
-            } else {
-                nst = L;
-                eps_use = eps * (1.0f + P.jitter * (2.0f * u[7] - 1.0f));
-            }
-        }
-        // momentum of this lane's parameter: Box-Muller on the pair (u_2j, u_2j+1)
-        float pm = 0.f;
-        if (mode != MODE_INIT) {
-            const int j = pi >> 1;
-            const float ua = j == 0 ? u[0] : (j == 1 ? u[2] : u[4]);
-            const float ub = j == 0 ? u[1] : (j == 1 ? u[3] : u[5]);
-            const float r = sqrtf(-2.0f * logf(ua));
-            float sn, cs;
-            sincospif(2.0f * ub, &sn, &cs);
-            pm = ((pi & 1) ? r * sn : r * cs) / sqrtf(im);
-        }
-        const double H0 = -lp + kinetic(pm, im, own);
-        float tp = th, tpl = thl, gp = g;
-        double lpp = lp;
-        bool ok = true;
-        for (int l = 0; l < nst; ++l) {
-            const float he = 0.5f * eps_use;
-            pm = fmaf(he, gp, pm);
-            {
-                // compensated position update (hi, lo) += eps m p
-                const float d = fmaf(eps_use * im, pm, tpl);
-                float s, e;
-                two_sum(tp, d, s, e);
-                tp = s;
-                tpl = e;
-            }
-            float x[6];
-#pragma unroll
-            for (int k = 0; k < 6; ++k) x[k] = __shfl_sync(BS_FULL_MASK, tp, k);
-            if (!in_support(P, x)) { ok = false; break; }
-            float gg[6];
-            const double v = eval_logpost<NC>(P, gc, sm.tab, sm.kxr, sm.xph + (size_t)chain * phase_stride(P.h_max), vcol, x, gg,
-                                              l == nst - 1);
-            ++ngrad;
-            if (l == nst - 1) lpp = v;
-            gp = pick6(gg, pi);
-            pm = fmaf(he, gp, pm);
-        }
-        if (mode == MODE_INIT) {
-            th = tp;
-            thl = tpl;
-            g = gp;
-            lp = ok ? lpp : -INFINITY;
-            if (!isfinite(lp) && lane == 0 && P.status) P.status[gal] = 1;
-            if (P.init_step) {
-                // resume with the given step size: no search, dual averaging from it
-                da_mu = logf(10.0f * eps);
-                mode = MODE_STEP;
-            } else {
-                mode = MODE_SEARCH;
-                s_idx = 0;
-                s_t = 0;
-                s_eps = 1.0f;
-            }
-            continue;
-        }
-        double dH = INFINITY;
-        if (ok) {
-            dH = (-lpp + kinetic(pm, im, own)) - H0;
-            if (!isfinite(dH) || dH > 1000.0) ok = false;
-        }
-        if (mode == MODE_SEARCH) {
-            const double la = ok ? -dH : -INFINITY;
-            const bool good = la > thr_search;
-            bool done = false;
-            if (s_t == 0)
-                s_dir = good ? 1 : -1;
-            else if ((s_dir > 0 && !good) || (s_dir < 0 && good))
-                done = true;
-            if (s_t == 60) done = true;
-            if (!done) {
-                ++s_t;
-                s_eps = s_dir > 0 ? 2.0f * s_eps : 0.5f * s_eps;
-                continue;
-            }
-            eps = s_eps;
-            da_mu = logf(10.0f * eps);
-            da_hbar = 0.f;
-            da_lebar = 0.f;
-            da_m = 0;
-            mode = MODE_STEP;
-            if (it >= W + S) mode = -1;
-            continue;
-        }
-        // ---- transition at iteration `it`
-        const float a = ok ? (dH < 0.0 ? 1.0f : expf((float)-dH)) : 0.0f;
-        const bool acc = ok && ((double)logf(u[6]) < -dH);
-        if (acc) {
-            th = tp;
-            thl = tpl;
-            g = gp;
-            lp = lpp;
-        }
-        if (it < W) {
-            // dual averaging
-            da_m += 1;
-            const float m = (float)da_m;
-            const float eta = 1.0f / (m + 10.0f);
-            da_hbar = (1.0f - eta) * da_hbar + eta * (P.target_accept - a);
-            const float le = da_mu - sqrtf(m) * 20.0f * da_hbar;
-            const float xe = powf(m, -0.75f);
-            da_lebar = xe * le + (1.0f - xe) * da_lebar;
-            eps = expf(le);
-            if (wi < P.n_windows && it >= P.win_start[wi] && it < P.win_end[wi]) {
-                ++wn;
-                const float x = th + thl;
-                const float d = x - wmean;
-                wmean = fmaf(d, 1.0f / (float)wn, wmean);
-                wm2 = fmaf(d, x - wmean, wm2);
-            }
-            if (wi < P.n_windows && it == P.win_end[wi] - 1) {
-                const float n = (float)wn;
-                const float var = wm2 / (n - 1.0f);
-                im = (n / (n + 5.0f)) * var + 1e-3f * (5.0f / (n + 5.0f));
-                wmean = 0.f;
-                wm2 = 0.f;
-                wn = 0;
-                mode = MODE_SEARCH;
-                s_idx = wi + 1;
-                s_t = 0;
-                s_eps = eps;
-                ++wi;
-            }
-            if (it == W - 1) eps = expf(da_lebar);
-        } else {
-            const int s = it - W;
-            asum += a;
-            ndiv += ok ? 0 : 1;
-            if (own) P.samples[(size_t)pi * plane + chain_row + s] = th + thl;
-            if (lane == 6 && P.logp) P.logp[chain_row + s] = (float)lp;
-            if (lane == 7 && P.accepted) P.accepted[chain_row + s] = acc ? 1 : 0;
-        }
-        ++it;
-        if (it >= W + S && mode == MODE_STEP) mode = -1;
-    }
-    if (lane == 0) {
-        if (P.accept_rate) P.accept_rate[ci0] = S > 0 ? asum / (float)S : 0.f;
-        if (P.step_size) P.step_size[ci0] = eps;
-        if (P.n_div) P.n_div[ci0] = ndiv;
-        if (P.n_grad) P.n_grad[ci0] = ngrad;
-    }
-    if (P.inv_mass && own) P.inv_mass[ci0 * 6 + pi] = im;
-}
-
-// Serving: copy n elements at src (this CTA's galaxy's outputs) to the
-// pinned mirror, src + pub_shift.
-template <typename T>
-__device__ __forceinline__ void publish_range(const T *src, size_t n, long long shift)
-{
-    if (!src) return;
-    T *dst = reinterpret_cast<T *>(reinterpret_cast<char *>(const_cast<T *>(src)) + shift);
-    for (size_t i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
-}
-
-// All threads of the CTA, after the galaxy's chains have finished: its
-// outputs go to the host mirror, then done[gal] is raised.  Each thread
-// fences its own stores at system scope before the barrier, so the host that
-// sees the flag sees every result.
-__device__ void publish_galaxy(const FitParams &P, int gal)
-{
-    const size_t C = P.n_chains, cs = C * P.n_samples;
-    const size_t plane = (size_t)P.n_gal * cs;
-    const long long sh = P.pub_shift;
-    for (int k = 0; k < 6; ++k) publish_range(P.samples + k * plane + gal * cs, cs, sh);
-    if (P.logp) publish_range(P.logp + gal * cs, cs, sh);
-    if (P.accepted) publish_range(P.accepted + gal * cs, cs, sh);
-    if (P.accept_rate) publish_range(P.accept_rate + gal * C, C, sh);
-    if (P.step_size) publish_range(P.step_size + gal * C, C, sh);
-    if (P.inv_mass) publish_range(P.inv_mass + gal * C * 6, C * 6, sh);
-    if (P.n_div) publish_range(P.n_div + gal * C, C, sh);
-    if (P.n_grad) publish_range(P.n_grad + gal * C, C, sh);
-    if (P.status) publish_range(P.status + gal, 1, sh);
-    __threadfence_system();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence_system();
-        *reinterpret_cast<volatile uint32_t *>(P.done + gal) = 1u;
-    }
-}
-
-// The persistent fit loop of one CTA (all threads).
-template <int NC>
-__device__ __forceinline__ void fit_loop(const FitParams &P)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int s_gal;
-    const SmemView sm = smem_view(smem_raw, P.h_max, P.npad, P.max_side, P.n_chains);
-    const int warp = threadIdx.x >> 5;
-    bool first = true;
-    for (;;) {
-        if (threadIdx.x == 0) {
-            if (P.done) {
-                // serving: galaxy blockIdx.x only, so that nothing of the
-                // launch's memory is touched after its completion flag
-                s_gal = first ? (int)blockIdx.x : -1;
-            } else {
-                // positions in the work list (or galaxy indices when there is none)
-                const int q = (int)atomicAdd(P.queue, 1u);
-                s_gal = q < P.n_work ? (P.work ? P.work[q] : q) : -1;
-            }
-        }
-        first = false;
-        __syncthreads();
-        const int gal = s_gal;
-        if (gal < 0 || gal >= P.n_gal) break;
-        if (!side_ok(P, P.side[gal])) {     // uniform across the CTA
-            if (threadIdx.x == 0 && P.status) P.status[gal] = 2;
-            __syncthreads();
-            if (P.done) publish_galaxy(P, gal);
-            continue;
-        }
-        GalCtx gc;
-        if (!setup_galaxy(P, gal, sm, gc)) {
-            if (threadIdx.x == 0 && P.status) P.status[gal] = 3;
-            __syncthreads();
-            if (P.done) publish_galaxy(P, gal);
-            continue;
-        }
-        if (warp < P.n_chains) run_chain<NC>(P, gc, sm, gal, warp);
-        __syncthreads();
-        if (P.done) publish_galaxy(P, gal);
-    }
-}
-
-// Register budgets of the kernel instances (the launch bounds give ptxas the
-// occupancy target): 128 registers, 4 CTAs of 4 chains per SM, no spills;
-// at most 102 (5 CTAs; blocks of up to 4 chains only); at most 85 (6 CTAs,
-// a few spills outside the half-plane loop).
-template <int NC>
-__global__ void __launch_bounds__(256, 2) fit_kernel_r128(const FitParams P) { fit_loop<NC>(P); }
-template <int NC>
-__global__ void __launch_bounds__(128, 5) fit_kernel_r96(const FitParams P) { fit_loop<NC>(P); }
-template <int NC>
-__global__ void __launch_bounds__(256, 3) fit_kernel_r80(const FitParams P) { fit_loop<NC>(P); }
-
-// One CTA of 32 threads per point: stage the galaxy, then evaluate.
-template <int NC>
-__device__ void point_eval(const FitParams &P, const GalCtx &gc, const SmemView &sm,
-                           const float *theta, double *logp, float *grad)
-{
-    const int lane = threadIdx.x & 31;
-    float vcol[NC];
-#pragma unroll
-    for (int j = 0; j < NC; ++j) vcol[j] = (float)(lane + 32 * j - gc.c);
-    float th[6], g[6];
-#pragma unroll
-    for (int i = 0; i < 6; ++i) th[i] = theta[i];
-    double v = -INFINITY;
-    if (in_support(P, th)) {
-        v = eval_logpost<NC>(P, gc, sm.tab, sm.kxr, sm.xph, vcol, th, g, true);
-    } else {
-#pragma unroll
-        for (int i = 0; i < 6; ++i) g[i] = NAN;
-    }
-    if (lane == 0 && logp) *logp = v;
-    if (grad && lane < 6) grad[lane] = pick6(g, lane);
-}
-
-__global__ void __launch_bounds__(32) logpost_points_kernel(const FitParams P, int n_points,
-                                                            const int32_t *gal_index,
-                                                            const float *theta, double *logp,
-                                                            float *grad)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const SmemView sm = smem_view(smem_raw, P.h_max, P.npad, P.max_side, 1);
-    for (int i = blockIdx.x; i < n_points; i += gridDim.x) {
-        const int gal = gal_index[i];
-        if (gal < 0 || gal >= P.n_gal || !side_ok(P, P.side[gal])) {
-            if (threadIdx.x == 0 && logp) logp[i] = NAN;
-            if (grad && threadIdx.x < 6) grad[(size_t)i * 6 + threadIdx.x] = NAN;
-            continue;
-        }
-        GalCtx gc;
-        if (!setup_galaxy(P, gal, sm, gc)) {
-            if (threadIdx.x == 0 && logp) logp[i] = NAN;
-            if (grad && threadIdx.x < 6) grad[(size_t)i * 6 + threadIdx.x] = NAN;
-            continue;
-        }
-        const float *th = theta + (size_t)i * 6;
-        double *lp = logp ? logp + i : nullptr;
-        float *gr = grad ? grad + (size_t)i * 6 : nullptr;
-        switch (P.npad >> 5) {     // the table layout follows the launch's slot count
-            case 1: point_eval<1>(P, gc, sm, th, lp, gr); break;
-            case 2: point_eval<2>(P, gc, sm, th, lp, gr); break;
-            case 3: point_eval<3>(P, gc, sm, th, lp, gr); break;
-            default: point_eval<4>(P, gc, sm, th, lp, gr); break;
-        }
-        __syncthreads();
-    }
-}
-
-// The kernel instance is chosen by the column slots per lane of the largest
-// stamp; smaller stamps of the same launch see zero-padded columns.
 using FitKernel = void (*)(const FitParams);
 
 #define BS_FIT_NC_SWITCH(KERNEL)                 \
     switch ((max_side + 31) / 32) {              \
-        case 1: return KERNEL<1>;                \
-        case 2: return KERNEL<2>;                \
-        case 3: return KERNEL<3>;                \
-        default: return KERNEL<4>;               \
+        case 1: return KERNEL<1, 0>;             \
+        case 2: return KERNEL<2, 0>;             \
+        case 3: return KERNEL<3, 0>;             \
+        default: return KERNEL<4, 0>;            \
     }
 
 // Register budget of a launch (128, 96 or 80; 96 only for blocks of up to 4
@@ -1113,8 +47,9 @@ size_t fit_smem_bytes(int max_side, int n_chains)
            (size_t)scratch_float2(max_side, h, n_chains) * sizeof(float2) + (size_t)(h + 1) * sizeof(float2);
 }
 
-int fit_blocks_per_sm(int n_chains, int max_side, int regs)
+int fit_blocks_per_sm(int n_chains, int max_side, int regs, int profile)
 {
+    if (profile != 0) return fit_blocks_per_sm_profile(profile, n_chains, max_side);
     int nb = 0;
     const size_t smem = fit_smem_bytes(max_side, n_chains);
     FitKernel k = fit_kernel_for(max_side, regs, n_chains);
@@ -1126,6 +61,7 @@ int fit_blocks_per_sm(int n_chains, int max_side, int regs)
 
 cudaError_t launch_fit(const FitParams &p, int grid, cudaStream_t stream)
 {
+    if (p.profile != 0) return launch_fit_profile(p, grid, stream);
     const size_t smem = fit_smem_bytes(p.max_side, p.n_chains);
     FitKernel k = fit_kernel_for(p.max_side, p.regs, p.n_chains);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1138,13 +74,14 @@ cudaError_t launch_logpost_points(const FitParams &p, int n_points, const int32_
                                   const float *theta, double *logp, float *grad,
                                   cudaStream_t stream)
 {
+    if (p.profile != 0) return launch_logpost_points_profile(p, n_points, gal_index, theta, logp, grad, stream);
     const size_t smem = fit_smem_bytes(p.max_side, 1);
-    cudaError_t e = cudaFuncSetAttribute(logpost_points_kernel,
+    cudaError_t e = cudaFuncSetAttribute(logpost_points_kernel<0>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int grid = n_points < 4096 ? n_points : 4096;
     if (grid <= 0) return cudaSuccess;
-    logpost_points_kernel<<<grid, 32, smem, stream>>>(p, n_points, gal_index, theta, logp, grad);
+    logpost_points_kernel<0><<<grid, 32, smem, stream>>>(p, n_points, gal_index, theta, logp, grad);
     return cudaGetLastError();
 }
 

@@ -23,6 +23,10 @@ struct FitParams {
     const float *sigma;
     int n_exp;                 // exposures per galaxy (>= 1)
     const float *noise_corr;   // per-exposure noise correlation (layout of data) or NULL
+    int profile;               // BS_PROFILE_*
+    float prof_c;              // -d log f / d s = prof_c psi(s): 1 + nu (Spergel), 1/2 (Gaussian)
+    float prof_npow;           // -(1 + nu) (Spergel)
+    float inv_hlr_r0;          // r0 / hlr of the profile
     const uint64_t *gal_id;
     const float *init;
     const float *init_step;
@@ -69,7 +73,14 @@ struct FitParams {
 size_t fit_smem_bytes(int max_side, int n_chains);
 // Launch helpers implemented in the .cu files.
 cudaError_t launch_fit(const FitParams &p, int grid, cudaStream_t stream);
-int fit_blocks_per_sm(int n_chains, int max_side, int regs = 0);
+int fit_blocks_per_sm(int n_chains, int max_side, int regs = 0, int profile = 0);
+// Spergel / Gaussian instances (bs_fit_prof.cu)
+int fit_blocks_per_sm_profile(int profile, int n_chains, int max_side);
+cudaError_t launch_fit_profile(const FitParams &p, int grid, cudaStream_t stream);
+cudaError_t launch_logpost_points_profile(const FitParams &p, int n_points, const int32_t *gal_index,
+                                          const float *theta, double *logp, float *grad, cudaStream_t stream);
+// half-light radius over r0 of a profile (Spergel of index nu: root of its enclosed flux)
+double profile_hlr_over_r0(int profile, double nu);
 // Validate a fit request and fill every launch parameter except the
 // scheduling fields (work list, counter) and the serving fields.
 bs_status fit_params_from_args(const bs_fit_args *a, const bs_fit_out *o, FitParams &p, const char *who);

@@ -81,7 +81,7 @@ cudaError_t time_variant(const bs_fit_plan_s::Launch &L, int regs, int n_trial, 
     bs::FitParams p = L.p;
     p.regs = regs;
     p.n_work = n_trial;
-    const int per_sm = bs::fit_blocks_per_sm(p.n_chains, p.max_side, regs);
+    const int per_sm = bs::fit_blocks_per_sm(p.n_chains, p.max_side, regs, p.profile);
     const int grid = std::min(n_trial, sms * per_sm);
     cudaError_t e = cudaSuccess;
     for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
@@ -107,7 +107,7 @@ cudaError_t autotune(bs_fit_plan_s *pl, int sms)
     for (auto &L : pl->launches) {
         if (e != cudaSuccess) break;
         int waves = 1;
-        for (int r : kRegVariants) waves = std::max(waves, bs::fit_blocks_per_sm(L.p.n_chains, L.p.max_side, r));
+        for (int r : kRegVariants) waves = std::max(waves, bs::fit_blocks_per_sm(L.p.n_chains, L.p.max_side, r, L.p.profile));
         const int n_trial = std::min(L.p.n_work, 2 * sms * waves);
         float best = 0.f;
         int best_regs = 128;
@@ -122,7 +122,7 @@ cudaError_t autotune(bs_fit_plan_s *pl, int sms)
             }
         }
         L.p.regs = best_regs;
-        L.grid = std::min(L.p.n_work, sms * bs::fit_blocks_per_sm(L.p.n_chains, L.p.max_side, best_regs));
+        L.grid = std::min(L.p.n_work, sms * bs::fit_blocks_per_sm(L.p.n_chains, L.p.max_side, best_regs, L.p.profile));
     }
     if (st) cudaStreamDestroy(st);
     if (e0) cudaEventDestroy(e0);
@@ -211,7 +211,7 @@ bs_status bs_fit_plan_create(const bs_fit_args *a, const bs_fit_out *o, const in
         L.p.queue = L.queue;
         L.slot_class = c + 1;
         L.trial_ms[0] = L.trial_ms[1] = L.trial_ms[2] = 0.f;
-        const int per_sm = bs::fit_blocks_per_sm(a->n_chains, maxs[c], L.p.regs);
+        const int per_sm = bs::fit_blocks_per_sm(a->n_chains, maxs[c], L.p.regs, L.p.profile);
         L.grid = std::min(count[c], sms * per_sm);
         pl->launches.push_back(L);
         start += count[c];
@@ -237,7 +237,7 @@ bs_status bs_fit_plan_create(const bs_fit_args *a, const bs_fit_out *o, const in
             return bs::set_error(BS_ERR_CUDA, "bs_fit_plan_create: streams: %s", cudaGetErrorString(e));
         }
         // kernel attributes are set outside the capture
-        for (auto &L : pl->launches) bs::fit_blocks_per_sm(a->n_chains, L.p.max_side, L.p.regs);
+        for (auto &L : pl->launches) bs::fit_blocks_per_sm(a->n_chains, L.p.max_side, L.p.regs, L.p.profile);
         e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
             st = enqueue(pl, cap, true);

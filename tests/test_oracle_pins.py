@@ -559,3 +559,74 @@ def test_loglike_cov_rejects_a_covariance_that_is_not_positive_definite():
     bad[0, c + 1, c] = bad[0, c - 1, c] = bad[0, c, c + 1] = bad[0, c, c - 1] = 0.8
     v, _ = O.loglike_cov(N, 0.2, psfs, data, sig, th, corr=bad)
     assert np.isnan(v)
+
+
+# ---- Appendix B: Spergel and Gaussian profiles ---------------------------------------------
+
+def _spergel_radial(x, nu):
+    """Unnormalised Spergel profile x^nu K_nu(x), x = r / r0 (scipy's kv)."""
+    return x ** nu * sp.kv(nu, x)
+
+
+@pytest.mark.parametrize("nu", [-0.6, 0.0, 0.5, 1.5, 3.0])
+def test_spergel_half_light_radius_encloses_half_the_flux(nu):
+    """hlr / r0 from the oracle's closed-form enclosed flux (its own Bessel K)
+    against scipy quadrature of the real-space profile x^nu K_nu(x)."""
+    h = O.hlr_over_r0(O.PROFILE_SPERGEL, nu)
+    f = lambda x: _spergel_radial(x, nu) * x
+    inside = si.quad(f, 0, h, limit=200)[0]
+    total = si.quad(f, 0, h, limit=200)[0] + si.quad(f, h, np.inf, limit=200)[0]
+    assert abs(inside / total - 0.5) < 1e-8, (nu, h, inside / total)
+    if nu == 0.5:
+        assert abs(h - O.hlr_over_r0()) < 1e-10
+
+
+@pytest.mark.parametrize("nu", [-0.6, 1.5])
+def test_spergel_transform_is_the_hankel_transform_of_the_profile(nu):
+    """(1 + k^2 r0^2)^-(1+nu) is the unit-flux 2-D transform of x^nu K_nu(x)
+    (r0 = 1): int I(r) J0(k r) r dr / int I(r) r dr by quadrature."""
+    f = lambda x: _spergel_radial(x, nu) * x
+    total = si.quad(f, 0, 1, limit=200)[0] + si.quad(f, 1, np.inf, limit=200)[0]
+    for k in (0.3, 1.0, 2.5):
+        num = si.quad(lambda x: f(x) * sp.j0(k * x), 0, 1, limit=400)[0] + \
+            si.quad(lambda x: f(x) * sp.j0(k * x), 1, 80, limit=800)[0]
+        assert abs(num / total - O.profile_ft(O.PROFILE_SPERGEL, nu, k * k)) < 2e-6, (nu, k)
+
+
+def test_gaussian_profile_transform_and_half_light_radius():
+    s = 1.0
+    f = lambda x: np.exp(-0.5 * x * x) * x
+    h = O.hlr_over_r0(O.PROFILE_GAUSSIAN, 0.0)
+    assert abs(si.quad(f, 0, h)[0] / si.quad(f, 0, np.inf)[0] - 0.5) < 1e-12
+    for k in (0.3, 1.0, 2.5):
+        num = si.quad(lambda x: f(x) * sp.j0(k * x), 0, 40, limit=400)[0]
+        assert abs(num / si.quad(f, 0, np.inf)[0] - O.profile_ft(O.PROFILE_GAUSSIAN, 0.0, (k * s) ** 2)) < 1e-9
+
+
+def _profile_case(seed=3, N=15):
+    rng = np.random.default_rng(seed)
+    th = np.array([2.4, -0.4, 0.15, -0.1, 0.2, -0.3])
+    data = O.render(N, 0.2, (O.PSF_GAUSSIAN, 0.7), th) + rng.normal(size=(N, N))
+    return N, th, data
+
+
+def test_spergel_half_is_the_exponential_likelihood():
+    N, th, data = _profile_case()
+    v, g = O.loglike_p(O.PROFILE_SPERGEL, 0.5, N, 0.2, (O.PSF_GAUSSIAN, 0.7), data, 1.0, th)
+    vr, gr = O.loglike(N, 0.2, (O.PSF_GAUSSIAN, 0.7), data, 1.0, th)
+    assert abs(v - vr) <= 1e-10 * abs(vr) and np.allclose(g, gr, rtol=1e-8, atol=1e-8)
+
+
+@pytest.mark.parametrize("profile,nu", [(1, -0.6), (1, 2.0), (2, 0.0)])
+def test_profile_likelihood_gradient_central_differences(profile, nu):
+    N, th, data = _profile_case()
+    psf = (O.PSF_MOFFAT, 0.8, 3.0)
+    _, g = O.loglike_p(profile, nu, N, 0.2, psf, data, 1.0, th)
+    for i in range(6):
+        h = 1e-6
+        tp, tm = th.copy(), th.copy()
+        tp[i] += h
+        tm[i] -= h
+        fd = (O.loglike_p(profile, nu, N, 0.2, psf, data, 1.0, tp)[0] -
+              O.loglike_p(profile, nu, N, 0.2, psf, data, 1.0, tm)[0]) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-5 * max(1.0, abs(g[i])), (profile, nu, i, fd, g[i])
