@@ -91,6 +91,8 @@ class FitConfig:
     seed: int = 22048
     pixel_scale: float = PIXEL_SCALE
     prior: tuple = DEFAULT_PRIOR
+    profile: int = 0            # 0 exponential, 1 Spergel (spergel_nu), 2 Gaussian (Appendix B)
+    spergel_nu: float = 0.5
 
 
 class FitPlan:
@@ -143,6 +145,8 @@ class FitPlan:
         a.registers = int(registers)
         a.n_exposures = int(n_exposures)
         a.noise_corr = _p(noise_corr)
+        a.profile = int(cfg.profile)
+        a.spergel_nu = float(cfg.spergel_nu)
         self.args = a
         S, Cn = cfg.n_samples, cfg.n_chains
         f32 = dict(dtype=torch.float32, device=dev)
@@ -363,9 +367,11 @@ def fit_galaxies(data, offsets, side, psf, noise_sigma, init, cfg: FitConfig | N
 
 
 def logpost_points(data, offsets, side, psf, noise_sigma, gal_index, theta, *, max_side=None,
-                   pixel_scale=PIXEL_SCALE, prior=DEFAULT_PRIOR, n_exposures=1, noise_corr=None):
+                   pixel_scale=PIXEL_SCALE, prior=DEFAULT_PRIOR, n_exposures=1, noise_corr=None, profile=0,
+                   spergel_nu=0.5):
     """Log posterior (float64) and gradient (float32) at points theta [n, 6]
-    (n_exposures, noise_corr as in FitPlan)."""
+    (n_exposures, noise_corr as in FitPlan; profile, spergel_nu as in
+    FitConfig)."""
     _need_cuda(data, offsets, side, noise_sigma, gal_index, theta, noise_corr)
     table, n_psf = psf
     a = F.FitArgs()
@@ -382,6 +388,8 @@ def logpost_points(data, offsets, side, psf, noise_sigma, gal_index, theta, *, m
     a.prior = F.Prior(*prior)
     a.n_exposures = int(n_exposures)
     a.noise_corr = _p(noise_corr)
+    a.profile = int(profile)
+    a.spergel_nu = float(spergel_nu)
     n = theta.shape[0]
     lp = torch.empty(n, dtype=torch.float64, device=theta.device)
     g = torch.empty((n, 6), dtype=torch.float32, device=theta.device)

@@ -55,6 +55,24 @@ def test_host_validation(L):
     assert L.bs_shear_loglike(C.byref(d), 0.0, 0.0, 0.2, None, 1, None, 0, None) == -1   # NULL e1/e2
     assert L.bs_chain_ess(None, 1, 4, 100, None, None, None) == -1
     assert L.bs_logpost_points(None, 1, None, None, None, None, None) == -1
+    # exposures, profile (host checks before any device access)
+    one = C.c_float(1.0)
+    a = _ffi.FitArgs()
+    a.n_gal, a.data_dtype, a.max_side, a.n_psf, a.pixel_scale = 2, 0, 25, 1, 0.2
+    a.data = a.offsets = a.side = a.psf = a.noise_sigma = C.addressof(one)
+    a.prior = _ffi.Prior(-1.0, 9.0, -2.0, 1.0, 0.5, 0.3)
+    for field, value, msg in (("n_exposures", 65, b"n_exposures"), ("profile", 3, b"profile"),
+                              ("spergel_nu", -0.95, b"spergel_nu")):
+        b = _ffi.FitArgs.from_buffer_copy(a)
+        setattr(b, field, value)
+        if field == "spergel_nu":
+            b.profile = 1
+        assert L.bs_logpost_points(C.byref(b), 1, None, None, None, None, None) == -1
+        assert msg in L.bs_last_error(), L.bs_last_error()
+    b = _ffi.FitArgs.from_buffer_copy(a)
+    b.n_exposures, b.n_psf = 2, 3          # n_psf must be 1 or n_gal x n_exposures
+    assert L.bs_logpost_points(C.byref(b), 1, None, None, None, None, None) == -1
+    assert b"n_psf" in L.bs_last_error()
 
 
 def test_struct_layouts_match_header(tmp_path):
