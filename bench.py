@@ -206,9 +206,9 @@ CAPTURED_TRAFFIC = {
     # 53x53 galaxy of the plain workload: (13,895,424 + 6,144) B / 1,216 galaxies
     "fit": ("paper_2604_22048_gb300/csrc/bs_fit.cu",
             "2e3d178d7a98193e539c45262e8d3b9dff129d21b2d7ac383b413197b56d8d2f", 11432.2),
-    # one interim sample of the shear workload: (480,250,624 + 3,216,896) B / (200,000 x 300)
+    # one interim sample of the shear workload: (480,274,688 + 3,662,080) B / (200,000 x 300)
     "shear": ("paper_2604_22048_gb300/csrc/bs_shear.cu",
-              "ad6ae397103918b2dc2970353671f7063e3e8d6ed1da86462426731f70ddefa5", 8.0578),
+              "0a6a62dc126cf55d68f76bbc69571e3747beaa92f7643e5ca0148ca1bbfd0bff", 8.0656),
 }
 
 

@@ -82,6 +82,7 @@ struct ShearConst {
     float2 g1, g2, ng1, ng2;         // g, -g
     float2 a2n, an, nan, nk;         // -a2 (log2 units), a = 1/(2 alpha^2), -a, -kappa
     float2 c0;                       // log2(e)/(2 sigma_e0^2)
+    float2 gg, m2;                   // |g|^2, -2
     float r2;
 };
 
@@ -98,6 +99,8 @@ __device__ __forceinline__ ShearConst shear_const(const ShearLaunch &s)
     c.nan = f2(-a);
     c.nk = f2(-s.kappa);
     c.c0 = f2(s.c0);
+    c.gg = f2(s.g1 * s.g1 + s.g2 * s.g2);
+    c.m2 = f2(-2.0f);
     c.r2 = s.r2;
     return c;
 }
@@ -108,17 +111,19 @@ __device__ __forceinline__ ShearConst shear_const(const ShearLaunch &s)
 //   truncated Gaussian: -2 log2 U - 2 log2(1 - |eps'|^2) -> f = (1/(U (1 - |eps'|^2)))^2
 // (f lies in about [0.004, 16], so it cannot overflow a weight; no logarithm
 // per sample), and the factors of the derivatives,
-//   dx/dg_i = -2 rU c_i,  c_i = du_i (a Q - kappa) - a n_i,  n = eps' - g;
-// the -2 is applied once per galaxy.  n is formed explicitly (not expanded
-// through |eps'|^2 - 2 g.eps' + |g|^2, which cancels when eps' is near g).
+//   dx/dg_i = -2 rU c_i,  c_i = du_i (a Q - kappa) - a n_i,  n = eps' - g,
+//   du_i = eps'_i - g_i |eps'|^2  (-1/2 dU/dg_i);
+// the -2 is applied once per galaxy.  U = |1 - conj(g) eps'|^2 is taken in the
+// Lagrange form 1 - 2 g.eps' + |g|^2 |eps'|^2 (U is near 1: no cancellation);
+// n is formed explicitly (not expanded through |eps'|^2 - 2 g.eps' + |g|^2,
+// which cancels when eps' is near g).
 template <int FAMILY, bool HAS_B>
 __device__ __forceinline__ void pair_terms(const ShearConst &c, float2 e1, float2 e2, float2 bv, float2 &x,
                                            float2 &fw, float2 &ru, float2 &c1, float2 &c2, float2 &q)
 {
-    const float2 ur = fma2(c.ng1, e1, fma2(c.ng2, e2, f2(1.0f)));
-    const float2 nvi = fma2(c.g2, e1, mul2(c.ng1, e2));          // -(g1 e2 - g2 e1)
-    const float2 U = fma2(ur, ur, mul2(nvi, nvi));
     const float2 Ep = fma2(e1, e1, mul2(e2, e2));
+    const float2 ge = fma2(c.g1, e1, mul2(c.g2, e2));            // g.eps'
+    const float2 U = fma2(c.gg, Ep, fma2(c.m2, ge, f2(1.0f)));
     const float2 n1 = sub2(e1, c.g1), n2 = sub2(e2, c.g2);
     const float2 Nn = fma2(n1, n1, mul2(n2, n2));
     float2 rU, f;
@@ -141,8 +146,8 @@ __device__ __forceinline__ void pair_terms(const ShearConst &c, float2 e1, float
     }
     if (HAS_B) xx = fma2(f2(kLog2e), bv, xx);
     const float2 aqk = fma2(c.an, Q, c.nk);
-    const float2 du1 = fma2(nvi, e2, mul2(ur, e1));              // ur e1 - vi e2
-    const float2 du2 = sub2(mul2(ur, e2), mul2(nvi, e1));        // ur e2 + vi e1
+    const float2 du1 = fma2(c.ng1, Ep, e1);
+    const float2 du2 = fma2(c.ng2, Ep, e2);
     c1 = fma2(du1, aqk, mul2(c.nan, n1));
     c2 = fma2(du2, aqk, mul2(c.nan, n2));
     fw = f;
@@ -490,10 +495,9 @@ __device__ __forceinline__ void full_sample(const ShearFullLaunch &f, float an, 
                                             float ls, bool valid, FullAcc &A)
 {
     const ShearLaunch &s = f.s;
-    const float ur = fmaf(-s.g1, e1, fmaf(-s.g2, e2, 1.0f));
-    const float nvi = fmaf(s.g2, e1, -s.g1 * e2);
-    const float U = fmaf(ur, ur, nvi * nvi);
     const float Ep = fmaf(e1, e1, e2 * e2);
+    const float ge = fmaf(s.g1, e1, s.g2 * e2);
+    const float U = fmaf(s.g1 * s.g1 + s.g2 * s.g2, Ep, fmaf(-2.0f, ge, 1.0f));   // Lagrange form
     const float n1 = e1 - s.g1, n2 = e2 - s.g2;
     const float rU = rcp_ftz(U);
     const float Q = fmaf(n1, n1, n2 * n2) * rU;
@@ -502,8 +506,8 @@ __device__ __forceinline__ void full_sample(const ShearFullLaunch &f, float an, 
     float x = fmaf(s.c0, Ep, fmaf(lgk, lg2_ftz(larg), -s.a2 * Q));
     if (FAMILY == BS_EPRIOR_TRUNC_GAUSS && !(Q < s.r2)) x = -INFINITY;
     const float aqk = fmaf(an, Q, -s.kappa);
-    const float du1 = fmaf(nvi, e2, ur * e1);
-    const float du2 = fmaf(-nvi, e1, ur * e2);
+    const float du1 = fmaf(-s.g1, Ep, e1);
+    const float du2 = fmaf(-s.g2, Ep, e2);
     const float c1 = fmaf(du1, aqk, -an * n1);
     const float c2 = fmaf(du2, aqk, -an * n2);
     const float z = (lf - f.mu_f) * f.inv_sf;
