@@ -203,12 +203,12 @@ def flops_per_eval(N):
 # the kernel source it was taken on, identified by its sha256; after any change
 # to that file the traffic is reported as null until the next capture.
 CAPTURED_TRAFFIC = {
-    # 53x53 galaxy of the plain workload: (13,895,424 + 6,144) B / 1,216 galaxies
-    "fit": ("paper_2604_22048_gb300/csrc/bs_fit.cu",
-            "2e3d178d7a98193e539c45262e8d3b9dff129d21b2d7ac383b413197b56d8d2f", 11432.2),
-    # one interim sample of the shear workload: (480,274,688 + 3,662,080) B / (200,000 x 300)
+    # 53x53 galaxy of the plain workload: (14,223,616 + 5,120) B / 1,216 galaxies
+    "fit": ("paper_2604_22048_gb300/csrc/bs_fit_impl.cuh",
+            "cfcd8c70c3eea4e31f5494a433cfbc8b113676e021516a690f5d3ab75326589e", 11701.3),
+    # one interim sample of the shear workload: (484,250,368 + 3,260,672) B / (200,000 x 300)
     "shear": ("paper_2604_22048_gb300/csrc/bs_shear.cu",
-              "0a6a62dc126cf55d68f76bbc69571e3747beaa92f7643e5ca0148ca1bbfd0bff", 8.0656),
+              "50febd93baed655cf6873e3f26b97696a2c5d2bcc3a7134fe4d6d25f83302d4e", 8.1252),
 }
 
 
