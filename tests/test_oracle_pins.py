@@ -630,3 +630,23 @@ def test_profile_likelihood_gradient_central_differences(profile, nu):
         fd = (O.loglike_p(profile, nu, N, 0.2, psf, data, 1.0, tp)[0] -
               O.loglike_p(profile, nu, N, 0.2, psf, data, 1.0, tm)[0]) / (2 * h)
         assert abs(fd - g[i]) <= 1e-5 * max(1.0, abs(g[i])), (profile, nu, i, fd, g[i])
+
+
+def test_weighted_loglike_is_the_weighted_pixel_chi2():
+    """Appendix C, spatially variable noise: -1/2 sum w (d - m)^2 / sigma^2 with m
+    the oracle's rendered image, summed by numpy; pixels of weight 0 (a mask)
+    do not enter, whatever their data."""
+    rng = np.random.default_rng(12)
+    N, sig = 23, 1.4
+    th = np.array([2.5, -0.4, 0.1, 0.2, -0.3, 0.15])
+    psf = (O.PSF_MOFFAT, 0.8, 3.0)
+    m = O.render(N, 0.2, psf, th)
+    data = m + rng.normal(0, sig, (N, N))
+    w = rng.uniform(0.2, 2.0, (N, N))
+    w[3:7, 10:18] = 0.0
+    v, g = O.loglike(N, 0.2, psf, data, sig, th, weights=w)
+    assert abs(v - (-0.5 * (w * (data - m) ** 2).sum() / sig ** 2)) < 1e-9 * abs(v)
+    bad = data.copy()
+    bad[3:7, 10:18] = 1e6
+    vb, gb = O.loglike(N, 0.2, psf, bad, sig, th, weights=w)
+    assert abs(vb - v) < 1e-9 * abs(v) and np.allclose(gb, g, rtol=1e-9, atol=1e-9)
