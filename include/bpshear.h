@@ -188,6 +188,17 @@ typedef struct {
     float spergel_nu;             /* Spergel index nu in [-0.9, 4] (0.5 is the
                                      exponential; -0.6 is close to de
                                      Vaucouleurs) */
+    const float *pixel_weight;    /* NULL, or device float with the layout of
+                                     data: spatially variable noise (Appendix C),
+                                     log L = -1/2 sum_x w(x) (d - m)^2 / sigma^2,
+                                     w >= 0 (0 masks a pixel).  Each evaluation
+                                     then renders the model image and transforms
+                                     the weighted residual back (two separable
+                                     DFTs of the stamp, tens of times the cost
+                                     of the spectral evaluation).  Requires the
+                                     exponential profile, one exposure, no
+                                     noise_corr, max_side <= 63 and at most 4
+                                     chains (shared memory). */
 } bs_fit_args;
 
 enum { BS_PROFILE_EXPONENTIAL = 0, BS_PROFILE_SPERGEL = 1, BS_PROFILE_GAUSSIAN = 2 };

@@ -55,7 +55,7 @@ class FitArgs(C.Structure):
                 ("jitter", C.c_float), ("adapt_mass", C.c_int32), ("random_steps", C.c_int32),
                 ("seed", C.c_uint64), ("init_step_size", C.c_void_p), ("init_inv_mass", C.c_void_p),
                 ("registers", C.c_int32), ("n_exposures", C.c_int32), ("noise_corr", C.c_void_p),
-                ("profile", C.c_int32), ("spergel_nu", C.c_float)]
+                ("profile", C.c_int32), ("spergel_nu", C.c_float), ("pixel_weight", C.c_void_p)]
 
 
 class FitOut(C.Structure):

@@ -101,7 +101,7 @@ class FitPlan:
 
     def __init__(self, data, offsets, side, psf, noise_sigma, init, cfg: FitConfig, *, gal_id=None,
                  max_side=None, init_step_size=None, init_inv_mass=None, registers=0, n_exposures=1,
-                 noise_corr=None,
+                 noise_corr=None, pixel_weight=None,
                  want=("logp", "accept_rate", "step_size", "inv_mass", "n_div", "status", "n_grad")):
         """init_step_size [n_gal, C] / init_inv_mass [n_gal, C, 6] (optional):
         resume adapted chains (no initial step-size search).  registers: the
@@ -109,13 +109,16 @@ class FitPlan:
         n_exposures J: each galaxy's J stamps lie one after another from its
         offset, psf has n_gal * J entries (or one), noise_sigma n_gal * J;
         noise_corr (float32, layout of data): per-exposure noise correlation
-        at pixel lag, centred (Appendix C)."""
-        _need_cuda(data, offsets, side, noise_sigma, init, gal_id, init_step_size, init_inv_mass, noise_corr)
+        at pixel lag, centred; pixel_weight (float32, layout of data):
+        per-pixel inverse-variance factors, 0 masks a pixel (Appendix C)."""
+        _need_cuda(data, offsets, side, noise_sigma, init, gal_id, init_step_size, init_inv_mass, noise_corr,
+                   pixel_weight)
         dev = data.device
         n_gal, n_chains = init.shape[0], init.shape[1]
         assert n_chains == cfg.n_chains, "init must be [n_gal, n_chains, 6]"
         self.cfg = cfg
-        self.keep = (data, offsets, side, psf, noise_sigma, init, gal_id, init_step_size, init_inv_mass, noise_corr)
+        self.keep = (data, offsets, side, psf, noise_sigma, init, gal_id, init_step_size, init_inv_mass, noise_corr,
+                     pixel_weight)
         table, n_psf = psf
         a = F.FitArgs()
         a.n_gal = n_gal
@@ -147,6 +150,7 @@ class FitPlan:
         a.noise_corr = _p(noise_corr)
         a.profile = int(cfg.profile)
         a.spergel_nu = float(cfg.spergel_nu)
+        a.pixel_weight = _p(pixel_weight)
         self.args = a
         S, Cn = cfg.n_samples, cfg.n_chains
         f32 = dict(dtype=torch.float32, device=dev)
@@ -368,11 +372,11 @@ def fit_galaxies(data, offsets, side, psf, noise_sigma, init, cfg: FitConfig | N
 
 def logpost_points(data, offsets, side, psf, noise_sigma, gal_index, theta, *, max_side=None,
                    pixel_scale=PIXEL_SCALE, prior=DEFAULT_PRIOR, n_exposures=1, noise_corr=None, profile=0,
-                   spergel_nu=0.5):
+                   spergel_nu=0.5, pixel_weight=None):
     """Log posterior (float64) and gradient (float32) at points theta [n, 6]
     (n_exposures, noise_corr as in FitPlan; profile, spergel_nu as in
     FitConfig)."""
-    _need_cuda(data, offsets, side, noise_sigma, gal_index, theta, noise_corr)
+    _need_cuda(data, offsets, side, noise_sigma, gal_index, theta, noise_corr, pixel_weight)
     table, n_psf = psf
     a = F.FitArgs()
     a.n_gal = int(side.shape[0])
@@ -390,6 +394,7 @@ def logpost_points(data, offsets, side, psf, noise_sigma, gal_index, theta, *, m
     a.noise_corr = _p(noise_corr)
     a.profile = int(profile)
     a.spergel_nu = float(spergel_nu)
+    a.pixel_weight = _p(pixel_weight)
     n = theta.shape[0]
     lp = torch.empty(n, dtype=torch.float64, device=theta.device)
     g = torch.empty((n, 6), dtype=torch.float32, device=theta.device)

@@ -188,6 +188,14 @@ static bs_status fill_fit_params(const bs_fit_args *a, bs::FitParams &p, const c
     p.prof_c = a->profile == BS_PROFILE_SPERGEL ? 1.0f + a->spergel_nu : a->profile == BS_PROFILE_GAUSSIAN ? 0.5f : 1.5f;
     p.prof_npow = a->profile == BS_PROFILE_SPERGEL ? -(1.0f + a->spergel_nu) : -1.5f;
     p.inv_hlr_r0 = (float)(1.0 / bs::profile_hlr_over_r0(a->profile, a->spergel_nu));
+    p.pix_w = a->pixel_weight;
+    if (a->pixel_weight) {
+        if (a->profile != BS_PROFILE_EXPONENTIAL || n_exp > 1 || a->noise_corr)
+            return fail(BS_ERR_INVALID_ARG,
+                        "%s: pixel_weight needs the exponential profile, one exposure and no noise_corr", who);
+        if (a->max_side > 63) return fail(BS_ERR_INVALID_ARG, "%s: pixel_weight needs max_side <= 63", who);
+        p.profile = 3;
+    }
     p.gal_id = a->gal_id;
     p.init = a->init;
     p.init_step = a->init_step_size;
@@ -221,6 +229,8 @@ bs_status fit_params_from_args(const bs_fit_args *a, const bs_fit_out *o, FitPar
     if (st != BS_OK) return st;
     if (!o || !o->samples) return fail(BS_ERR_INVALID_ARG, "%s: NULL samples output", who);
     if (!a->init) return fail(BS_ERR_INVALID_ARG, "%s: NULL init", who);
+    if (p.profile == 3 && a->n_chains > 4)
+        return fail(BS_ERR_INVALID_ARG, "%s: pixel_weight allows at most 4 chains", who);
     if (a->n_chains < 1 || a->n_chains > bs::kMaxChains)
         return fail(BS_ERR_INVALID_ARG, "%s: n_chains must be 1..%d", who, bs::kMaxChains);
     if (a->n_warmup < 0 || a->n_samples < 0 || a->n_leapfrog < 1)

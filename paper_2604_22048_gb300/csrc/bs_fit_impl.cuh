@@ -105,6 +105,41 @@ __device__ __forceinline__ SmemView smem_view(unsigned char *base, int h_max, in
     return v;
 }
 
+// Spatially variable noise (Appendix C, per-pixel weights; kernel instance
+// PROF 3): after the shared region, the twiddles exp(+2 pi i m / N) (max_side
+// float2) and, per chain, a private copy of the table ([h_max][3 npad]: the D
+// slots hold the evaluation's effective spectrum, the T slots the transfer),
+// the half-transformed image ([h_max][max_side] float2) and one pixel row (64
+// floats).  Sizes in floats, each chain's block a multiple of 4 floats.
+__host__ __device__ __forceinline__ int pix_chain_floats(int h_max, int npad, int max_side)
+{
+    const int n = h_max * row_floats(npad) + 2 * h_max * max_side + 64;
+    return (n + 3) & ~3;
+}
+__host__ __device__ __forceinline__ size_t pix_region_bytes(int h_max, int npad, int max_side, int n_chains)
+{
+    return ((size_t)2 * ((max_side + 1) & ~1) + (size_t)n_chains * pix_chain_floats(h_max, npad, max_side)) *
+           sizeof(float);
+}
+struct PixView {
+    float2 *tw;    // [max_side] exp(+2 pi i m / N)
+    float *tab;    // this chain's table
+    float2 *G;     // [h_max][max_side]
+    float *row;    // [64]
+};
+// kxr ends at h_max + 1 float2 after its start; the region follows, 16-byte aligned.
+__device__ __forceinline__ PixView pix_view(float2 *kxr, int h_max, int npad, int max_side, int chain)
+{
+    float *base = reinterpret_cast<float *>(kxr + ((h_max + 2) & ~1));
+    PixView v;
+    v.tw = reinterpret_cast<float2 *>(base);
+    float *c0 = base + 2 * ((max_side + 1) & ~1) + (size_t)chain * pix_chain_floats(h_max, npad, max_side);
+    v.tab = c0;
+    v.G = reinterpret_cast<float2 *>(c0 + (size_t)h_max * row_floats(npad));
+    v.row = reinterpret_cast<float *>(v.G + (size_t)h_max * max_side);
+    return v;
+}
+
 // Positions of slot j of lane l within a row: Dx, Dy, T.
 __device__ __forceinline__ void slot_offsets(int npad, int j, int l, int &ox, int &oy, int &ot)
 {
@@ -779,6 +814,188 @@ __device__ __forceinline__ double eval_logpost(const FitParams &P, const GalCtx 
     return -0.5 * (chi2 + s_chi2_off) * (double)ib + (double)lprior;
 }
 
+// ---- Spatially variable noise (Appendix C): log L = -1/2 sum_x w(x) (d - m)^2 / sigma^2.
+// Parseval no longer makes this a sum over k, but its gradient is still
+// sum_k Re[conj(R_k) dM_k/dtheta] / (sigma^2 N^2) with R = DFT(w (d - m)), so the
+// half-plane pass of eval_logpost gives it when its data spectrum is replaced
+// by the effective D' = M + R (scaled as the table).  Each evaluation renders
+// m from M and transforms w (d - m) back, with the separable DFT on the
+// stamp's grid (the same centring as the setup's transform of d).
+
+// Per-galaxy set-up of the pixel path (all threads): the twiddles, and each
+// chain's private table from the staged one (transfer, zero spectrum).
+__device__ void pix_setup(const FitParams &P, const GalCtx &gc, const SmemView &sm, int n_tables)
+{
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const PixView p0 = pix_view(sm.kxr, P.h_max, P.npad, P.max_side, 0);
+    for (int m = tid; m < gc.N; m += nth) {
+        float s, co;
+        sincospif(2.0f * (float)m * gc.invN, &s, &co);
+        p0.tw[m] = make_float2(co, s);
+    }
+    const int rowf = row_floats(P.npad);
+    const int nrow = gc.H * rowf;
+    for (int t = 0; t < n_tables; ++t) {
+        float *dst = pix_view(sm.kxr, P.h_max, P.npad, P.max_side, t).tab;
+        for (int i = tid; i < nrow; i += nth) dst[i] = sm.tab[i];
+    }
+    __syncthreads();
+}
+
+// tw(k) = exp(+2 pi i k / N) for any integer k
+__device__ __forceinline__ float2 twk(const float2 *tw, int k, int N)
+{
+    int r = k % N;
+    if (r < 0) r += N;
+    return tw[r];
+}
+
+template <int NC>
+__device__ double eval_pix(const FitParams &P, const GalCtx &gc, const PixView &pv, int gal,
+                           const float2 *__restrict__ kxr, float2 *__restrict__ xph, const float vcol[NC],
+                           const float th[6], float g[6], bool want_ll)
+{
+    const int lane = threadIdx.x & 31;
+    const int N = gc.N, H = gc.H, c = gc.c, npad = P.npad;
+    const int rowf = row_floats(npad);
+    const float F = exp10f(th[0]);
+    const float r0 = exp10f(th[1]) * (1.0f / kHlrOverR0);
+    const float r02 = r0 * r0;
+    const float e1 = th[2], e2 = th[3];
+    const float E = e1 * e1 + e2 * e2;
+    const float Pq = 1.0f / (1.0f - E);
+    const float al = r02 * (1.0f + E + 2.0f * e1) * Pq;
+    const float be = r02 * (1.0f + E - 2.0f * e1) * Pq;
+    const float ga = r02 * 4.0f * e2 * Pq;
+    const float sqrt2 = 1.41421356237309515f;
+    for (int u = lane; u < H; u += 32) {
+        float sx, cx;
+        sincospif(-2.0f * th[4] * (float)u * gc.invN, &sx, &cx);
+        xph[u] = make_float2(cx, sx);
+    }
+    __syncwarp();
+    // (a) the model's half spectrum Mt = Tt F f(s) X(u) Y(v) into the D slots
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+        const int vi = lane + 32 * j;
+        float sy, cy;
+        sincospif(-2.0f * th[5] * vcol[j] * gc.invN, &sy, &cy);
+        const float Yr = F * cy, Yi = F * sy;
+        const float ky = vcol[j] * gc.dk;
+        const float cst = fmaf(be * ky, ky, 1.0f), gky = ga * ky;
+        int ox, oy, ot;
+        slot_offsets(npad, j, lane, ox, oy, ot);
+        for (int u = 0; u < H; ++u) {
+            float *row = pv.tab + (size_t)u * rowf;
+            const float kx = kxr[u].x;
+            const float s = fmaf(fmaf(al, kx, gky), kx, cst);
+            const float rs = rsqrtf(s);
+            const float A = row[ot] * rs * rs * rs;
+            const float2 X = xph[u];
+            const float Pr = X.x * Yr - X.y * Yi, Pi = X.x * Yi + X.y * Yr;
+            row[ox] = vi < N ? A * Pr : 0.0f;
+            row[oy] = vi < N ? A * Pi : 0.0f;
+        }
+    }
+    __syncwarp();
+    // (b1) G(u, iy) = sum_v M(u, v) exp(+2 pi i v (iy - c) / N), M = Mt / scale_u
+    for (int iy = lane; iy < N; iy += 32) {
+        const int step = iy - c;
+        for (int u = 0; u < H; ++u) {
+            const float *row = pv.tab + (size_t)u * rowf;
+            const float inv_scale = (float)N * (u == 0 ? 1.0f : 0.70710678118654752f);
+            float re = 0.f, im = 0.f;
+            int k = ((-c * step) % N + N) % N;
+            int dk = (step % N + N) % N;
+            for (int vi = 0; vi < N; ++vi) {
+                int ox, oy, ot;
+                slot_offsets(npad, vi >> 5, vi & 31, ox, oy, ot);
+                const float mr = row[ox], mi = row[oy];
+                const float2 t = pv.tw[k];
+                re = fmaf(mr, t.x, fmaf(-mi, t.y, re));
+                im = fmaf(mr, t.y, fmaf(mi, t.x, im));
+                k += dk;
+                if (k >= N) k -= N;
+            }
+            pv.G[(size_t)u * N + iy] = make_float2(re * inv_scale, im * inv_scale);
+        }
+    }
+    __syncwarp();
+    // (b2) per pixel row: m(ix, iy), r = w (d - m), then Q(u, iy) = sum_ix r exp(-2 pi i u (ix - c) / N)
+    const int64_t off = P.offsets[gal];
+    const float invN2 = gc.invN * gc.invN;
+    double chi = 0.0;
+    for (int iy = 0; iy < N; ++iy) {
+        for (int ix = lane; ix < N; ix += 32) {
+            const int step = ix - c;
+            float acc = pv.G[iy].x;                     // u = 0 (real)
+            for (int u = 1; u < H; ++u) {
+                const float2 gv = pv.G[(size_t)u * N + iy];
+                const float2 t = twk(pv.tw, u * step, N);
+                acc = fmaf(2.0f * gv.x, t.x, fmaf(-2.0f * gv.y, t.y, acc));
+            }
+            const float m = acc * invN2;
+            const int64_t idx = off + (int64_t)iy * N + ix;
+            const float res = load_pix(P.data, P.data_f64, idx) - m;
+            const float r = __ldg(P.pix_w + idx) * res;
+            chi += (double)(r * res);
+            pv.row[ix] = r;
+        }
+        __syncwarp();
+        for (int u = lane; u < H; u += 32) {
+            float re = 0.f, im = 0.f;
+            int k = ((u * c) % N + N) % N;               // -u (ix - c) at ix = 0
+            const int dk = (N - u % N) % N;
+            for (int ix = 0; ix < N; ++ix) {
+                const float r = pv.row[ix];
+                const float2 t = pv.tw[k];
+                re = fmaf(r, t.x, re);
+                im = fmaf(r, t.y, im);
+                k += dk;
+                if (k >= N) k -= N;
+            }
+            pv.G[(size_t)u * N + iy] = make_float2(re, im);
+        }
+        __syncwarp();
+    }
+    // (b3) D' = Mt + scale_u R(u, v), R(u, v) = sum_iy Q(u, iy) exp(-2 pi i v (iy - c) / N)
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+        const int vi = lane + 32 * j;
+        if (vi < N) {
+            const int v = vi - c;
+            int ox, oy, ot;
+            slot_offsets(npad, j, lane, ox, oy, ot);
+            const int dk = ((-v) % N + N) % N;
+            const int k0 = ((v * c) % N + N) % N;       // -v (iy - c) at iy = 0
+            for (int u = 0; u < H; ++u) {
+                float re = 0.f, im = 0.f;
+                int k = k0;
+                for (int iy = 0; iy < N; ++iy) {
+                    const float2 q = pv.G[(size_t)u * N + iy];
+                    const float2 t = pv.tw[k];
+                    re = fmaf(q.x, t.x, fmaf(-q.y, t.y, re));
+                    im = fmaf(q.x, t.y, fmaf(q.y, t.x, im));
+                    k += dk;
+                    if (k >= N) k -= N;
+                }
+                const float scale = (u == 0 ? 1.0f : sqrt2) * gc.invN;
+                float *row = pv.tab + (size_t)u * rowf;
+                row[ox] = fmaf(scale, re, row[ox]);
+                row[oy] = fmaf(scale, im, row[oy]);
+            }
+        }
+    }
+    __syncwarp();
+    // (c) the gradient from the half-plane pass on the effective spectrum
+    eval_logpost<NC, 0>(P, gc, pv.tab, kxr, xph, vcol, th, g, false);
+    if (!want_ll) return 0.0;
+    const double chi2 = warp_sum_d(chi);
+    const float lprior = P.prior_const - 0.5f * (th[4] * th[4] + th[5] * th[5]) * P.inv_sxy2 +
+                         2.0f * log1pf(-E) - 0.5f * E * P.inv_se2;
+    return -0.5 * chi2 * (double)gc.inv_b + (double)lprior;
+}
+
 __device__ __forceinline__ float pick6(const float (&v)[6], int i)
 {
     float r = v[0];
@@ -882,8 +1099,13 @@ __device__ void run_chain(const FitParams &P, const GalCtx &gc, const SmemView &
             for (int k = 0; k < 6; ++k) x[k] = __shfl_sync(BS_FULL_MASK, tp, k);
             if (!in_support(P, x)) { ok = false; break; }
             float gg[6];
-            const double v = eval_logpost<NC, PROF>(P, gc, sm.tab, sm.kxr, sm.xph + (size_t)chain * phase_stride(P.h_max), vcol, x, gg,
-                                              l == nst - 1);
+            double v;
+            float2 *xph_c = sm.xph + (size_t)chain * phase_stride(P.h_max);
+            if constexpr (PROF == 3)
+                v = eval_pix<NC>(P, gc, pix_view(sm.kxr, P.h_max, P.npad, P.max_side, chain), gal, sm.kxr, xph_c,
+                                 vcol, x, gg, l == nst - 1);
+            else
+                v = eval_logpost<NC, PROF>(P, gc, sm.tab, sm.kxr, xph_c, vcol, x, gg, l == nst - 1);
             ++ngrad;
             if (l == nst - 1) lpp = v;
             gp = pick6(gg, pi);
@@ -1069,6 +1291,7 @@ __device__ __forceinline__ void fit_loop(const FitParams &P)
             if (P.done) publish_galaxy(P, gal);
             continue;
         }
+        if constexpr (PROF == 3) pix_setup(P, gc, sm, P.n_chains);
         if (warp < P.n_chains) run_chain<NC, PROF>(P, gc, sm, gal, warp);
         __syncthreads();
         if (P.done) publish_galaxy(P, gal);
@@ -1088,7 +1311,7 @@ __global__ void __launch_bounds__(256, 3) fit_kernel_r80(const FitParams P) { fi
 
 // One CTA of 32 threads per point: stage the galaxy, then evaluate.
 template <int NC, int PROF>
-__device__ void point_eval(const FitParams &P, const GalCtx &gc, const SmemView &sm,
+__device__ void point_eval(const FitParams &P, const GalCtx &gc, const SmemView &sm, int gal,
                            const float *theta, double *logp, float *grad)
 {
     const int lane = threadIdx.x & 31;
@@ -1100,7 +1323,11 @@ __device__ void point_eval(const FitParams &P, const GalCtx &gc, const SmemView 
     for (int i = 0; i < 6; ++i) th[i] = theta[i];
     double v = -INFINITY;
     if (in_support(P, th)) {
-        v = eval_logpost<NC, PROF>(P, gc, sm.tab, sm.kxr, sm.xph, vcol, th, g, true);
+        if constexpr (PROF == 3)
+            v = eval_pix<NC>(P, gc, pix_view(sm.kxr, P.h_max, P.npad, P.max_side, 0), gal, sm.kxr, sm.xph, vcol, th,
+                             g, true);
+        else
+            v = eval_logpost<NC, PROF>(P, gc, sm.tab, sm.kxr, sm.xph, vcol, th, g, true);
     } else {
 #pragma unroll
         for (int i = 0; i < 6; ++i) g[i] = NAN;
@@ -1130,14 +1357,15 @@ __global__ void __launch_bounds__(32) logpost_points_kernel(const FitParams P, i
             if (grad && threadIdx.x < 6) grad[(size_t)i * 6 + threadIdx.x] = NAN;
             continue;
         }
+        if constexpr (PROF == 3) pix_setup(P, gc, sm, 1);
         const float *th = theta + (size_t)i * 6;
         double *lp = logp ? logp + i : nullptr;
         float *gr = grad ? grad + (size_t)i * 6 : nullptr;
         switch (P.npad >> 5) {     // the table layout follows the launch's slot count
-            case 1: point_eval<1, PROF>(P, gc, sm, th, lp, gr); break;
-            case 2: point_eval<2, PROF>(P, gc, sm, th, lp, gr); break;
-            case 3: point_eval<3, PROF>(P, gc, sm, th, lp, gr); break;
-            default: point_eval<4, PROF>(P, gc, sm, th, lp, gr); break;
+            case 1: point_eval<1, PROF>(P, gc, sm, gal, th, lp, gr); break;
+            case 2: point_eval<2, PROF>(P, gc, sm, gal, th, lp, gr); break;
+            case 3: point_eval<3, PROF>(P, gc, sm, gal, th, lp, gr); break;
+            default: point_eval<4, PROF>(P, gc, sm, gal, th, lp, gr); break;
         }
         __syncthreads();
     }

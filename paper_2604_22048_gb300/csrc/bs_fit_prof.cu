@@ -23,14 +23,34 @@ FitKernel prof_kernel(int max_side)
     }
 }
 
+// Per-pixel weights (profile 3, exponential): stamps of at most 63 px.
+FitKernel pix_kernel(int max_side)
+{
+    return max_side <= 31 ? fit_kernel_r128<1, 3> : fit_kernel_r128<2, 3>;
+}
+
 FitKernel kernel_for(int profile, int max_side)
 {
+    if (profile == 3) return pix_kernel(max_side);
     return profile == BS_PROFILE_SPERGEL ? prof_kernel<1>(max_side) : prof_kernel<2>(max_side);
 }
 
 PointsKernel points_for(int profile)
 {
+    if (profile == 3) return logpost_points_kernel<3>;
     return profile == BS_PROFILE_SPERGEL ? logpost_points_kernel<1> : logpost_points_kernel<2>;
+}
+
+// Dynamic shared memory of a launch: the pixel path adds its twiddles and
+// per-chain scratch after the row table.
+size_t smem_for(int profile, int max_side, int n_chains)
+{
+    size_t b = fit_smem_bytes(max_side, n_chains);
+    if (profile == 3) {
+        const int h = (max_side + 1) / 2, npad = 32 * ((max_side + 31) / 32);
+        b += 16 + pix_region_bytes(h, npad, max_side, n_chains);
+    }
+    return b;
 }
 
 // K_mu(x) = int_0^inf exp(-x cosh t) cosh(mu t) dt by the trapezoidal rule
@@ -70,7 +90,7 @@ double profile_hlr_over_r0(int profile, double nu)
 int fit_blocks_per_sm_profile(int profile, int n_chains, int max_side)
 {
     int nb = 0;
-    const size_t smem = fit_smem_bytes(max_side, n_chains);
+    const size_t smem = smem_for(profile, max_side, n_chains);
     FitKernel k = kernel_for(profile, max_side);
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, 32 * n_chains, smem) != cudaSuccess) return 1;
@@ -79,7 +99,7 @@ int fit_blocks_per_sm_profile(int profile, int n_chains, int max_side)
 
 cudaError_t launch_fit_profile(const FitParams &p, int grid, cudaStream_t stream)
 {
-    const size_t smem = fit_smem_bytes(p.max_side, p.n_chains);
+    const size_t smem = smem_for(p.profile, p.max_side, p.n_chains);
     FitKernel k = kernel_for(p.profile, p.max_side);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -90,7 +110,7 @@ cudaError_t launch_fit_profile(const FitParams &p, int grid, cudaStream_t stream
 cudaError_t launch_logpost_points_profile(const FitParams &p, int n_points, const int32_t *gal_index,
                                           const float *theta, double *logp, float *grad, cudaStream_t stream)
 {
-    const size_t smem = fit_smem_bytes(p.max_side, 1);
+    const size_t smem = smem_for(p.profile, p.max_side, 1);
     PointsKernel k = points_for(p.profile);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

@@ -27,6 +27,7 @@ struct FitParams {
     float prof_c;              // -d log f / d s = prof_c psi(s): 1 + nu (Spergel), 1/2 (Gaussian)
     float prof_npow;           // -(1 + nu) (Spergel)
     float inv_hlr_r0;          // r0 / hlr of the profile
+    const float *pix_w;        // per-pixel weights (layout of data) or NULL; profile 3 when set
     const uint64_t *gal_id;
     const float *init;
     const float *init_step;

@@ -70,6 +70,13 @@ def test_host_validation(L):
         assert L.bs_logpost_points(C.byref(b), 1, None, None, None, None, None) == -1
         assert msg in L.bs_last_error(), L.bs_last_error()
     b = _ffi.FitArgs.from_buffer_copy(a)
+    b.pixel_weight, b.profile = C.addressof(one), 1      # per-pixel weights: exponential only
+    assert L.bs_logpost_points(C.byref(b), 1, None, None, None, None, None) == -1
+    assert b"pixel_weight" in L.bs_last_error()
+    b.profile, b.max_side = 0, 65                         # and stamps of at most 63 px
+    assert L.bs_logpost_points(C.byref(b), 1, None, None, None, None, None) == -1
+    assert b"63" in L.bs_last_error()
+    b = _ffi.FitArgs.from_buffer_copy(a)
     b.n_exposures, b.n_psf = 2, 3          # n_psf must be 1 or n_gal x n_exposures
     assert L.bs_logpost_points(C.byref(b), 1, None, None, None, None, None) == -1
     assert b"n_psf" in L.bs_last_error()
