@@ -346,14 +346,16 @@ __device__ __forceinline__ void cp_async_wait()
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// 4 lanes per galaxy and 16-sample chunks: a group still spans 64 samples per
-// step (little padding at K = 300), and the ring's per-chunk bookkeeping is
-// shared by twice the samples of 8-sample chunks; two stages (64 KB per CTA)
-// keep 3 CTAs per SM.  Measured against 8 lanes x 8 samples x 3 stages:
-// 3.9% faster; 3 stages of 16 samples (2 CTAs per SM) are slower.
+// 4 lanes per galaxy and 12-sample chunks: a group spans 48 samples per step
+// (336 slots for K = 300), the ring's per-chunk bookkeeping is shared by 12
+// samples per lane, and two stages (48 KB per CTA) at 64 registers fit 4 CTAs
+// (32 warps) per SM to hide the shared-memory and MUFU latency.  Measured on
+// one GPU: 8 lanes x 8 samples x 3 stages (3 CTAs) 1,793 passes/s, 4 x 16 x 2
+// (3 CTAs) 1,864, 4 x 8 x 2 (4 CTAs) 1,883, 4 x 12 x 2 (4 CTAs) 1,904.
 constexpr int kAGroup = 4;     // lanes per galaxy
 constexpr int kStages = 2;     // chunks per lane in flight, this one included
-constexpr int kChunk = 16;     // samples per lane per chunk (kChunk / 4 16-byte copies per array)
+constexpr int kAsyncBlocks = 4;   // CTAs per SM the launch bounds target (3 with b: 72 KB ring)
+constexpr int kChunk = 12;     // samples per lane per chunk (kChunk / 4 16-byte copies per array)
 constexpr int kQuads = kChunk / 4;
 
 __host__ __device__ constexpr size_t async_smem_bytes(bool has_b)
@@ -361,13 +363,13 @@ __host__ __device__ constexpr size_t async_smem_bytes(bool has_b)
     return (size_t)kStages * (has_b ? 3 : 2) * kQuads * kShearThreads * sizeof(float4);
 }
 
-// K % 4 == 0 and 16-byte aligned rows: each lane streams its 16-sample chunks
+// K % 4 == 0 and 16-byte aligned rows: each lane streams its 12-sample chunks
 // through a kStages-deep ring of its own shared-memory slots with cp.async,
 // over the flattened sequence (galaxy, chunk) of its group, so the pipeline
 // does not drain between galaxies.  A lane only reads the slots it filled,
 // after cp.async.wait_group; no barrier is needed.
 template <int FAMILY, bool HAS_B>
-__global__ void __launch_bounds__(kShearThreads, 3) shear_kernel_async(const ShearLaunch s)
+__global__ void __launch_bounds__(kShearThreads, HAS_B ? 3 : kAsyncBlocks) shear_kernel_async(const ShearLaunch s)
 {
     extern __shared__ float4 sbuf[];
     constexpr int NV = HAS_B ? 3 : 2;
