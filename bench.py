@@ -206,9 +206,9 @@ CAPTURED_TRAFFIC = {
     # 53x53 galaxy of the plain workload: (13,924,352 + 6,400) B / 1,216 galaxies
     "fit": ("paper_2604_22048_gb300/csrc/bs_fit_impl.cuh",
             "bbc98d383825d1af11edda377f33efc57eb050acd1453c0f8264f28a6137e380", 11456.2),
-    # one interim sample of the shear workload: (484,250,368 + 3,260,672) B / (200,000 x 300)
+    # one interim sample of the shear workload: (489,431,808 + 3,317,504) B / (200,000 x 300)
     "shear": ("paper_2604_22048_gb300/csrc/bs_shear.cu",
-              "50febd93baed655cf6873e3f26b97696a2c5d2bcc3a7134fe4d6d25f83302d4e", 8.1252),
+              "936a74d2e858e92d9bdbf95cafb9ef4692811a6b1a7a9b4ecc87c2f5b754a608", 8.2125),
 }
 
 
