@@ -316,7 +316,9 @@ int32_t bs_fit_resident_galaxies(int32_t n_chains, int32_t max_side, int32_t reg
  *     whole fit; each CTA copies its galaxy's results into pinned host
  *     memory and raises a completion flag there, which the engine picks up.
  * Times are nanoseconds of a steady clock whose zero is the server's
- * creation (bs_serve_now_ns). */
+ * creation (bs_serve_now_ns).  A request is one exposure with white noise
+ * and the exponential profile (the Appendix B and C options of
+ * bs_fit_args are batch-only). */
 typedef struct {
     int32_t max_side;        /* largest stamp side accepted (odd, <= BS_MAX_SIDE) */
     float pixel_scale;       /* arcsec */
