@@ -589,6 +589,21 @@ def shear_arm(a, world, rank, local_rank):
     ms = e0.elapsed_time(e1v)
     passes = a.steps * len(grid)
     per_pass_s = ms / 1e3 / passes
+    # the same grid with several points per pass over the samples
+    gpts = np.array(grid, dtype=np.float64)
+    for _ in range(a.warmup):
+        plan.loglike_multi(gpts, host=False)
+    torch.cuda.synchronize(dev)
+    m0, m1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    m0.record(stream)
+    for _ in range(a.steps):
+        plan.loglike_multi(gpts, host=False)
+    m1.record(stream)
+    torch.cuda.synchronize(dev)
+    mms = m0.elapsed_time(m1)
+    multi = {"points_per_s": passes / (mms / 1e3), "ms_per_grid": mms / a.steps,
+             "points_per_pass": 4, "speedup_vs_one_point_per_pass": ms / mms,
+             "note": "bs_shear_loglike_multi on the same 27-point grid: one read of the samples per 4 points"}
     bytes_per_pass = 8.0 * n * K
     peak = measured_peaks().get("hbm_gbs", 6800.0)
     achieved = bytes_per_pass / per_pass_s / 1e9
@@ -660,7 +675,7 @@ def shear_arm(a, world, rank, local_rank):
                     "sd": [float(x) for x in draws[:, :3].std(axis=0)], "draws": int(draws.shape[0]),
                     "accept_rate": hinfo["accept_rate"], "passes": hinfo["n_evals"], "seconds": hmc_s,
                     "ms_per_pass": 1e3 * hmc_s / max(1, hinfo["n_evals"])},
-            "bias": bias,
+            "bias": bias, "multi_point": multi,
             "e2e": {"value": 1.0 / est_s, "unit": "joint estimates/s (host samples in, estimate out)",
                     "h2d_bytes_per_step": int(bytes_per_pass), "d2h_bytes_per_step": 8 * 12}}
 

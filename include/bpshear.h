@@ -495,6 +495,21 @@ bs_status bs_shear_loglike(const bs_shear_data *data, double g1, double g2,
                            double alpha, double *out, int32_t out_on_host,
                            void *workspace, size_t workspace_bytes, void *stream);
 
+/* bs_shear_loglike at n_points points (g1, g2, alpha) with one read of the
+ * samples per kMultiPoints (4) points: the per-sample arithmetic is repeated
+ * per point, so a batch of independent points (a Hessian's central
+ * differences, quadrature nodes, a grid) costs about its arithmetic instead
+ * of one HBM pass per point.
+ *   points  host double [n_points][3] = (g1, g2, alpha), each |g| < 1, alpha > 0.
+ *   out     double [n_points][4] = {value, d/dg1, d/dg2, d/dalpha} per point,
+ *           on the device, or on the host when out_on_host != 0 (the call
+ *           then synchronises `stream` after each group of 4 points).
+ * data->b must be NULL.  Results agree with bs_shear_loglike up to the
+ * summation order (a different reduction layout).  Workspace:
+ * bs_shear_workspace_bytes.  n_points == 0 returns BS_OK at once. */
+bs_status bs_shear_loglike_multi(const bs_shear_data *data, int32_t n_points, const double *points, double *out,
+                                 int32_t out_on_host, void *workspace, size_t workspace_bytes, void *stream);
+
 /* Eq. likelihood-shear with every galaxy property's true prior free (the
  * paper's all-free setting, Sec. 3.3): per sample, the ellipticity weight of
  * bs_shear_loglike times the log-flux and log-size prior ratio

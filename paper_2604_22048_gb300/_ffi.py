@@ -27,7 +27,7 @@ EXPORTED = ["bs_prior_default", "bs_last_error", "bs_version", "bs_render", "bs_
             "bs_fit_plan_workspace_bytes", "bs_fit_plan_create", "bs_fit_plan_launch", "bs_fit_plan_destroy",
             "bs_fit_resident_galaxies", "bs_fit_plan_num_launches", "bs_fit_plan_info", "bs_serve_request_bytes", "bs_serve_create", "bs_serve_submit",
             "bs_serve_poll", "bs_serve_get_stats", "bs_serve_now_ns", "bs_serve_destroy",
-            "bs_shear_hyperprior_default", "bs_shear_sample", "bs_fp32_peak", "bs_fp64_peak"]
+            "bs_shear_hyperprior_default", "bs_shear_sample", "bs_fp32_peak", "bs_fp64_peak", "bs_shear_loglike_multi"]
 
 
 class BsError(RuntimeError):
@@ -172,6 +172,7 @@ def lib():
     L.bs_shear_loglike.argtypes = [C.POINTER(ShearData), f64, f64, f64, vp, i32, vp, sz, vp]
     L.bs_shear_estimate.argtypes = [C.POINTER(ShearData), C.POINTER(EstimateCfg), vp, vp, vp, vp, sz, vp]
     L.bs_shear_loglike_noalloc.argtypes = [C.POINTER(ShearData), f64, f64, f64, vp, vp]
+    L.bs_shear_loglike_multi.argtypes = [C.POINTER(ShearData), i32, vp, vp, i32, vp, sz, vp]
     L.bs_shear_loglike_full.argtypes = [C.POINTER(ShearData), vp, vp, vp, vp, vp, i32, vp, sz, vp]
     L.bs_fit_plan_workspace_bytes.argtypes = [C.POINTER(FitArgs)]
     L.bs_fit_plan_workspace_bytes.restype = sz
@@ -199,7 +200,7 @@ def lib():
     L.bs_serve_now_ns.restype = i64
     L.bs_serve_destroy.argtypes = [vp]
     for nm in ("bs_render", "bs_fit_galaxies", "bs_logpost_points", "bs_chain_ess", "bs_shear_loglike",
-               "bs_shear_loglike_full", "bs_shear_sample", "bs_fp32_peak", "bs_fp64_peak",
+               "bs_shear_loglike_full", "bs_shear_sample", "bs_fp32_peak", "bs_fp64_peak", "bs_shear_loglike_multi",
                "bs_shear_estimate", "bs_shear_loglike_noalloc", "bs_fit_plan_create", "bs_fit_plan_launch",
                "bs_fit_plan_destroy", "bs_fit_plan_info", "bs_serve_create", "bs_serve_submit", "bs_serve_poll", "bs_serve_get_stats",
                "bs_serve_destroy"):

@@ -477,6 +477,24 @@ class ShearPlan:
                                          self.ws_bytes, _stream()))
         return self.out
 
+    def loglike_multi(self, points, *, host=True):
+        """(value, d/dg1, d/dg2, d/dalpha) at points [n, 3] = (g1, g2, alpha),
+        several points per pass over the samples (bs_shear_loglike_multi).
+        Returns a numpy [n, 4] array (host=True, synchronises) or a float64
+        CUDA tensor [n, 4]."""
+        pts = np.ascontiguousarray(points, dtype=np.float64).reshape(-1, 3)
+        n = pts.shape[0]
+        if host:
+            out = np.zeros((n, 4))
+            F.check(F.lib().bs_shear_loglike_multi(C.byref(self.data), n, pts.ctypes.data_as(C.c_void_p),
+                                                   out.ctypes.data_as(C.c_void_p), 1, _p(self.ws), self.ws_bytes,
+                                                   _stream()))
+            return out
+        out = torch.empty((n, 4), dtype=torch.float64, device=self.keep[0].device)
+        F.check(F.lib().bs_shear_loglike_multi(C.byref(self.data), n, pts.ctypes.data_as(C.c_void_p), _p(out), 0,
+                                               _p(self.ws), self.ws_bytes, _stream()))
+        return out
+
     def loglike_full(self, lf, ls, theta, *, interim=(-1.0, 9.0, -2.0, 1.0)):
         """All properties free: lf, ls [n_gal, K] float32 CUDA (log10 flux and
         log10 hlr samples); theta = (g1, g2, sigma_e, mu_f, sigma_f, a_f, mu_s,

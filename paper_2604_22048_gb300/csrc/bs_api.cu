@@ -359,10 +359,13 @@ size_t bs_shear_workspace_bytes(int64_t n_gal, int32_t K)
 {
     (void)n_gal;
     (void)K;
-    // per-block partials of the 4-output kernel or of the all-free one, plus
-    // the device copy of the result
+    // per-block partials of the 4-output kernel, of the all-free one or of the
+    // several-point one, plus the device copy of the results
     const size_t a = (size_t)bs::shear_grid_blocks() * 4, b = (size_t)bs::shear_full_grid_blocks() * bs::kShearFullOut;
-    return ((a > b ? a : b) + bs::kShearFullOut) * sizeof(double);
+    const size_t c = (size_t)bs::shear_multi_grid_blocks() * bs::kMultiPoints * 4;
+    size_t m = a > b ? a : b;
+    m = m > c ? m : c;
+    return (m + 4 * bs::kMultiPoints + bs::kShearFullOut) * sizeof(double);
 }
 
 static bs_status validate_shear(const bs_shear_data *d, const char *who)
@@ -410,6 +413,63 @@ bs_status bs_shear_loglike(const bs_shear_data *d, double g1, double g2, double 
         if (e != cudaSuccess) return cuda_fail(e, "bs_shear_loglike: copy");
         e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return cuda_fail(e, "bs_shear_loglike: sync");
+    }
+    return BS_OK;
+}
+
+bs_status bs_shear_loglike_multi(const bs_shear_data *d, int32_t n_points, const double *points, double *out,
+                                 int32_t out_on_host, void *workspace, size_t workspace_bytes, void *stream)
+{
+    const char *who = "bs_shear_loglike_multi";
+    bs_status st = validate_shear(d, who);
+    if (st != BS_OK) return st;
+    if (d->b) return fail(BS_ERR_INVALID_ARG, "%s: data->b must be NULL", who);
+    if (n_points < 0) return fail(BS_ERR_INVALID_ARG, "%s: n_points < 0", who);
+    if (n_points == 0) return BS_OK;
+    if (!points || !out) return fail(BS_ERR_INVALID_ARG, "%s: NULL points/out", who);
+    constexpr int NP = bs::kMultiPoints;
+    const int grid = bs::shear_multi_grid_blocks();
+    const size_t need = ((size_t)grid * NP * 4 + 4 * NP) * sizeof(double);
+    if (!workspace || workspace_bytes < need)
+        return fail(BS_ERR_OUT_OF_MEMORY, "%s: workspace of %zu bytes needed", who, need);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    double *partials = static_cast<double *>(workspace);
+    double *host_stage = partials + (size_t)grid * NP * 4;
+    for (int start = 0; start < n_points; start += NP) {
+        const int np = n_points - start < NP ? n_points - start : NP;
+        bs::ShearMultiLaunch M;
+        double add[NP][4], ascale[NP];
+        for (int p = 0; p < np; ++p) {
+            const double *x = points + 3 * (size_t)(start + p);
+            bs::ShearLaunch L;
+            st = bs::shear_prepare(d, x[0], x[1], x[2], L, add[p], ascale[p], who);
+            if (st != BS_OK) return st;
+            if (p == 0) M.s = L;
+            M.g1[p] = L.g1;
+            M.g2[p] = L.g2;
+            M.a2[p] = L.a2;
+        }
+        for (int p = np; p < NP; ++p) M.g1[p] = M.g2[p] = M.a2[p] = 0.f;
+        M.n_points = np;
+        M.partials = partials;
+        cudaError_t e;
+        if (d->n_gal > 0) {
+            e = bs::launch_shear_multi(M, grid, s);
+            if (e != cudaSuccess) return cuda_fail(e, "bs_shear_loglike_multi: launch");
+        }
+        const int n_part = d->n_gal > 0 ? grid : 0;
+        double *dev_out = out_on_host ? host_stage : out + 4 * (size_t)start;
+        for (int p = 0; p < np; ++p) {
+            e = bs::launch_shear_finalize(partials + (size_t)p * grid * 4, n_part, add[p][0], add[p][1], add[p][2],
+                                          add[p][3], ascale[p], dev_out + 4 * p, s);
+            if (e != cudaSuccess) return cuda_fail(e, "bs_shear_loglike_multi: finalize");
+        }
+        if (out_on_host) {
+            e = cudaMemcpyAsync(out + 4 * (size_t)start, host_stage, 4 * np * sizeof(double), cudaMemcpyDeviceToHost,
+                                s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) return cuda_fail(e, "bs_shear_loglike_multi: copy");
+        }
     }
     return BS_OK;
 }
@@ -521,6 +581,39 @@ struct ShearObjective {
         }
         return true;
     }
+    // values (and gradients, g may be NULL) at m points x[m][3] (alpha in x[.][2]
+    // even when it is fixed): several points per pass over the samples, or
+    // one pass each when the data carry per-sample offsets b
+    bool eval_many(const double *x, int m, double *v, double *g)
+    {
+        if (m == 0) return true;
+        std::vector<double> buf((size_t)4 * m);
+        if (d->b) {
+            for (int i = 0; i < m; ++i) {
+                bs_status st = bs_shear_loglike(d, x[3 * i], x[3 * i + 1], x[3 * i + 2], &buf[4 * (size_t)i], 1, ws,
+                                                wsb, stream);
+                if (st != BS_OK) {
+                    err = st;
+                    return false;
+                }
+            }
+        } else {
+            bs_status st = bs_shear_loglike_multi(d, m, x, buf.data(), 1, ws, wsb, stream);
+            if (st != BS_OK) {
+                err = st;
+                return false;
+            }
+        }
+        n_evals += m;
+        for (int i = 0; i < m; ++i) {
+            double *b4 = &buf[4 * (size_t)i];
+            if (cfg->allreduce) cfg->allreduce(b4, cfg->allreduce_user);
+            v[i] = b4[0];
+            if (g)
+                for (int k = 0; k < 3; ++k) g[3 * (size_t)i + k] = b4[1 + k];
+        }
+        return true;
+    }
     bool inside(const double *x) const
     {
         if (!(x[0] * x[0] + x[1] * x[1] < 1.0)) return false;
@@ -625,15 +718,21 @@ extern "C" bs_status bs_shear_estimate(const bs_shear_data *d, const bs_estimate
     double x[3] = {0.0, 0.0, cfg->alpha}, g[3], v;
     if (!f.eval(x, v, g)) return f.err;
 
+    // Hessian by central differences of the gradient, the 2n points in one batch
     auto hessian = [&](const double *xc, double *H) -> bool {
-        for (int j = 0; j < n; ++j) {
-            const double h = 1e-5;
-            double xp[3] = {xc[0], xc[1], xc[2]}, xm[3] = {xc[0], xc[1], xc[2]}, gp[3], gm[3], vv;
-            xp[j] += h;
-            xm[j] -= h;
-            if (!f.eval(xp, vv, gp) || !f.eval(xm, vv, gm)) return false;
-            for (int i = 0; i < n; ++i) H[i * n + j] = (gp[i] - gm[i]) / (2.0 * h);
-        }
+        const double h = 1e-5;
+        double pts[6][3], vv[6], gg[6][3];
+        for (int j = 0; j < n; ++j)
+            for (int sgn = 0; sgn < 2; ++sgn) {
+                double *q = pts[2 * j + sgn];
+                q[0] = xc[0];
+                q[1] = xc[1];
+                q[2] = n == 3 ? xc[2] : cfg->alpha;
+                q[j] += sgn == 0 ? h : -h;
+            }
+        if (!f.eval_many(&pts[0][0], 2 * n, vv, &gg[0][0])) return false;
+        for (int j = 0; j < n; ++j)
+            for (int i = 0; i < n; ++i) H[i * n + j] = (gg[2 * j][i] - gg[2 * j + 1][i]) / (2.0 * h);
         for (int i = 0; i < n; ++i)
             for (int j = 0; j < i; ++j) H[i * n + j] = H[j * n + i] = 0.5 * (H[i * n + j] + H[j * n + i]);
         return true;
@@ -707,7 +806,8 @@ extern "C" bs_status bs_shear_estimate(const bs_shear_data *d, const bs_estimate
     hermite_rule(q, gx, gw);
     int total = 1;
     for (int i = 0; i < n; ++i) total *= q;
-    std::vector<double> lw(total), th((size_t)total * 3);
+    std::vector<double> lw(total), th((size_t)total * 3), qp, qv;
+    std::vector<int> qidx;
     double lmax = -INFINITY;
     for (int j = 0; j < total; ++j) {
         int r = j;
@@ -730,9 +830,16 @@ extern "C" bs_status bs_shear_estimate(const bs_shear_data *d, const bs_estimate
             lw[j] = -INFINITY;
             continue;
         }
-        double vj;
-        if (!f.eval(tj, vj, nullptr)) return f.err;
-        lw[j] = logw + (vj - v) + zz;
+        lw[j] = logw + zz;      // + (value - v) once the batch is evaluated
+        qidx.push_back(j);
+        qp.insert(qp.end(), {tj[0], tj[1], tj[2]});
+    }
+    // the nodes inside the support in batches of several points per pass
+    qv.resize(qidx.size());
+    if (!f.eval_many(qp.data(), (int)qidx.size(), qv.data(), nullptr)) return f.err;
+    for (size_t q = 0; q < qidx.size(); ++q) {
+        const int j = qidx[q];
+        lw[j] += qv[q] - v;
         if (lw[j] > lmax) lmax = lw[j];
     }
     double wsum = 0.0, m[3] = {0, 0, 0};

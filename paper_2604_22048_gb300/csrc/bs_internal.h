@@ -116,6 +116,16 @@ constexpr int kShearFullOut = 9;   // value, d/d(g1, g2, sigma_e, mu_f, sigma_f,
 
 int shear_grid_blocks();
 double shear_weight_total(const bs_shear_data *d);
+// Several (g1, g2, alpha) points per pass over the samples (no b).
+constexpr int kMultiPoints = 4;
+struct ShearMultiLaunch {
+    ShearLaunch s;                  // data, K, family, kappa, c0, r2, w (g1, g2, a2 unused)
+    int n_points;                   // 1..kMultiPoints
+    float g1[kMultiPoints], g2[kMultiPoints], a2[kMultiPoints];
+    double *partials;               // [kMultiPoints][grid][4]
+};
+int shear_multi_grid_blocks();
+cudaError_t launch_shear_multi(const ShearMultiLaunch &m, int grid, cudaStream_t stream);
 int shear_full_grid_blocks();
 cudaError_t launch_shear(const ShearLaunch &s, int grid, cudaStream_t stream);
 cudaError_t launch_shear_full(const ShearFullLaunch &f, int grid, cudaStream_t stream);

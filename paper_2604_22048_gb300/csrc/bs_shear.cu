@@ -656,6 +656,88 @@ cudaError_t launch_fb(const ShearLaunch &s, int grid, bool vec, cudaStream_t st)
     return cudaGetLastError();
 }
 
+// ---- Several points per pass.  One read of the samples serves up to
+// kMultiPoints (g1, g2, alpha) points: each sample's weight and derivative
+// factors are formed for every point (the same per-sample arithmetic as
+// shear_kernel), so the pass turns from HBM-bound into ALU-bound; the shear
+// estimate's batches (central differences of its Hessian, Gauss-Hermite nodes)
+// then cost about their arithmetic alone.  A galaxy group's FP64 totals go to
+// its own shared-memory slot (one writer), summed over the block in a fixed
+// order; partials are laid out per point so that each point is finalized as
+// a single-point pass.
+__device__ __forceinline__ ShearConst shear_const_point(const ShearMultiLaunch &m, int p)
+{
+    ShearLaunch s = m.s;
+    s.g1 = m.g1[p];
+    s.g2 = m.g2[p];
+    s.a2 = m.a2[p];
+    return shear_const(s);
+}
+
+template <int FAMILY>
+__global__ void __launch_bounds__(kShearThreads, 2) shear_kernel_multi(const ShearMultiLaunch m)
+{
+    constexpr int NP = kMultiPoints;
+    constexpr int kGroups = kShearThreads / kGroup;
+    __shared__ double acc[kGroups][NP][4];
+    const ShearLaunch &s = m.s;
+    const int lane = threadIdx.x & 31;
+    const int sub = lane & (kGroup - 1);
+    const int gi = threadIdx.x / kGroup;
+    const unsigned gmask = 0xFFu << (lane & ~(kGroup - 1));
+    const long long group = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / kGroup;
+    const long long ngroups = (long long)gridDim.x * blockDim.x / kGroup;
+    const int K = s.K;
+    if (sub == 0)
+        for (int p = 0; p < NP; ++p)
+            for (int i = 0; i < 4; ++i) acc[gi][p][i] = 0.0;
+
+    for (long long n = group; n < s.n_gal; n += ngroups) {
+        const long long base = n * (long long)K;
+        Lse L[NP];
+#pragma unroll
+        for (int p = 0; p < NP; ++p) lse_reset(L[p]);
+        Chunk A, B;
+        int k0 = 4 * sub;
+        auto eval_all = [&](const Chunk &ch) {
+#pragma unroll
+            for (int p = 0; p < NP; ++p)
+                if (p < m.n_points) eval_chunk<FAMILY, false>(shear_const_point(m, p), ch, L[p]);
+        };
+        load_chunk<false>(s, base, k0, K, A);
+        for (;;) {
+            if (k0 >= K) break;
+            load_chunk<false>(s, base, k0 + 4 * kGroup, K, B);
+            eval_all(A);
+            k0 += 4 * kGroup;
+            if (k0 >= K) break;
+            load_chunk<false>(s, base, k0 + 4 * kGroup, K, A);
+            eval_all(B);
+            k0 += 4 * kGroup;
+        }
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+            if (p < m.n_points) {
+                double av = 0.0, a1 = 0.0, a2 = 0.0, aq = 0.0;
+                finish_galaxy(L[p], gmask, sub, s.w, n, av, a1, a2, aq);
+                if (sub == 0) {
+                    acc[gi][p][0] += av;
+                    acc[gi][p][1] += a1;
+                    acc[gi][p][2] += a2;
+                    acc[gi][p][3] += aq;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < NP * 4) {
+        const int p = threadIdx.x >> 2, i = threadIdx.x & 3;
+        double t = 0.0;
+        for (int k = 0; k < kGroups; ++k) t += acc[k][p][i];
+        m.partials[((size_t)p * gridDim.x + blockIdx.x) * 4 + i] = t;
+    }
+}
+
 }  // namespace
 
 int shear_grid_blocks()
@@ -715,6 +797,26 @@ cudaError_t launch_shear_finalize_n(const double *partials, int n_part, int n_ou
         c.add[i] = i < n_out ? add[i] : 0.0;
     }
     shear_finalize_n_kernel<<<1, 256, 0, stream>>>(partials, n_part, n_out, c, out);
+    return cudaGetLastError();
+}
+
+int shear_multi_grid_blocks()
+{
+    int dev = 0, sms = 0, nb = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, shear_kernel_multi<BS_EPRIOR_BA14>, kShearThreads, 0);
+    if (sms <= 0) sms = 1;
+    if (nb <= 0) nb = 1;
+    return sms * nb;
+}
+
+cudaError_t launch_shear_multi(const ShearMultiLaunch &m, int grid, cudaStream_t stream)
+{
+    if (m.s.family == BS_EPRIOR_BA14)
+        shear_kernel_multi<BS_EPRIOR_BA14><<<grid, kShearThreads, 0, stream>>>(m);
+    else
+        shear_kernel_multi<BS_EPRIOR_TRUNC_GAUSS><<<grid, kShearThreads, 0, stream>>>(m);
     return cudaGetLastError();
 }
 

@@ -152,6 +152,16 @@ def test_host_validation_of_plan_serve_and_sampler(L):
         wd.gal_weight_sum = bad
         assert L.bs_shear_loglike(C.byref(wd), 0.0, 0.0, 0.2, out, 1, None, 0, None) == -1
         assert b"gal_weight_sum" in L.bs_last_error()
+    # several points per pass: b must be NULL, n_points >= 0
+    pts = (C.c_double * 3)(0.0, 0.0, 0.2)
+    md = _ffi.ShearData()
+    md.n_gal, md.K, md.family, md.sigma_e0 = 2, 4, 0, 0.3
+    md.e1 = md.e2 = md.b = 16
+    assert L.bs_shear_loglike_multi(C.byref(md), 1, pts, out, 1, None, 0, None) == -1
+    assert b"b must be NULL" in L.bs_last_error()
+    md.b = None
+    assert L.bs_shear_loglike_multi(C.byref(md), -1, pts, out, 1, None, 0, None) == -1
+    assert L.bs_shear_loglike_multi(C.byref(md), 0, None, None, 1, None, 0, None) == 0
     # all-free likelihood: b must be NULL, sigma_f > 0
     th = (C.c_double * 8)(0.0, 0.0, 0.2, 2.4, -0.1, 1.0, -0.4, 0.05)
     im = (C.c_double * 4)(-1.0, 9.0, -2.0, 1.0)
