@@ -238,7 +238,8 @@ size_t bs_fit_workspace_bytes(const bs_fit_args *args);
  * Eq. likelihood-pixels (Parseval on the stamp's periodic grid).
  * Errors: BS_ERR_INVALID_ARG (bad sizes, NULL required pointers, n_chains
  * outside 1..8, max_side out of range), BS_ERR_OUT_OF_MEMORY (workspace too
- * small), BS_ERR_CUDA (launch failure). */
+ * small), BS_ERR_CUDA (launch failure).  An empty batch (n_gal == 0) needs no
+ * input or output array and returns BS_OK without a launch. */
 bs_status bs_fit_galaxies(const bs_fit_args *args, const bs_fit_out *out,
                           void *workspace, size_t workspace_bytes, void *stream);
 

@@ -156,7 +156,7 @@ static bs_status fill_fit_params(const bs_fit_args *a, bs::FitParams &p, const c
 {
     if (!a) return fail(BS_ERR_INVALID_ARG, "%s: NULL args", who);
     if (a->n_gal < 0) return fail(BS_ERR_INVALID_ARG, "%s: n_gal < 0", who);
-    if (!a->data || !a->offsets || !a->side || !a->psf || !a->noise_sigma)
+    if (a->n_gal > 0 && (!a->data || !a->offsets || !a->side || !a->psf || !a->noise_sigma))
         return fail(BS_ERR_INVALID_ARG, "%s: NULL required input pointer", who);
     if (a->data_dtype != BS_F32 && a->data_dtype != BS_F64)
         return fail(BS_ERR_INVALID_ARG, "%s: data_dtype", who);
@@ -227,8 +227,9 @@ bs_status fit_params_from_args(const bs_fit_args *a, const bs_fit_out *o, FitPar
 {
     bs_status st = fill_fit_params(a, p, who);
     if (st != BS_OK) return st;
-    if (!o || !o->samples) return fail(BS_ERR_INVALID_ARG, "%s: NULL samples output", who);
-    if (!a->init) return fail(BS_ERR_INVALID_ARG, "%s: NULL init", who);
+    if (!o) return fail(BS_ERR_INVALID_ARG, "%s: NULL outputs", who);
+    if (a->n_gal > 0 && !o->samples) return fail(BS_ERR_INVALID_ARG, "%s: NULL samples output", who);
+    if (a->n_gal > 0 && !a->init) return fail(BS_ERR_INVALID_ARG, "%s: NULL init", who);
     if (p.profile == 3 && a->n_chains > 4)
         return fail(BS_ERR_INVALID_ARG, "%s: pixel_weight allows at most 4 chains", who);
     if (a->n_chains < 1 || a->n_chains > bs::kMaxChains)
