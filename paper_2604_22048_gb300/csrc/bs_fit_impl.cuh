@@ -842,14 +842,6 @@ __device__ void pix_setup(const FitParams &P, const GalCtx &gc, const SmemView &
     __syncthreads();
 }
 
-// tw(k) = exp(+2 pi i k / N) for any integer k
-__device__ __forceinline__ float2 twk(const float2 *tw, int k, int N)
-{
-    int r = k % N;
-    if (r < 0) r += N;
-    return tw[r];
-}
-
 template <int NC>
 __device__ double eval_pix(const FitParams &P, const GalCtx &gc, const PixView &pv, int gal,
                            const float2 *__restrict__ kxr, float2 *__restrict__ xph, const float vcol[NC],
@@ -893,46 +885,60 @@ __device__ double eval_pix(const FitParams &P, const GalCtx &gc, const PixView &
             const float A = row[ot] * rs * rs * rs;
             const float2 X = xph[u];
             const float Pr = X.x * Yr - X.y * Yi, Pi = X.x * Yi + X.y * Yr;
-            row[ox] = vi < N ? A * Pr : 0.0f;
-            row[oy] = vi < N ? A * Pi : 0.0f;
-        }
-    }
-    __syncwarp();
-    // (b1) G(u, iy) = sum_v M(u, v) exp(+2 pi i v (iy - c) / N), M = Mt / scale_u
-    for (int iy = lane; iy < N; iy += 32) {
-        const int step = iy - c;
-        for (int u = 0; u < H; ++u) {
-            const float *row = pv.tab + (size_t)u * rowf;
+            const float mr = vi < N ? A * Pr : 0.0f, mi = vi < N ? A * Pi : 0.0f;
+            row[ox] = mr;
+            row[oy] = mi;
+            // unscaled M(u, v) = Mt / scale_u, contiguous, for the inverse transform
             const float inv_scale = (float)N * (u == 0 ? 1.0f : 0.70710678118654752f);
-            float re = 0.f, im = 0.f;
-            int k = ((-c * step) % N + N) % N;
-            int dk = (step % N + N) % N;
-            for (int vi = 0; vi < N; ++vi) {
-                int ox, oy, ot;
-                slot_offsets(npad, vi >> 5, vi & 31, ox, oy, ot);
-                const float mr = row[ox], mi = row[oy];
-                const float2 t = pv.tw[k];
-                re = fmaf(mr, t.x, fmaf(-mi, t.y, re));
-                im = fmaf(mr, t.y, fmaf(mi, t.x, im));
-                k += dk;
-                if (k >= N) k -= N;
-            }
-            pv.G[(size_t)u * N + iy] = make_float2(re * inv_scale, im * inv_scale);
+            if (vi < N) pv.G[(size_t)u * N + vi] = make_float2(mr * inv_scale, mi * inv_scale);
         }
     }
     __syncwarp();
+    // (b1) G(u, iy) = sum_v M(u, v) exp(+2 pi i v (iy - c) / N), in place row by
+    // row (a row's outputs need only that row's M; lanes over iy, at most 2 each)
+    for (int u = 0; u < H; ++u) {
+        float2 *grow = pv.G + (size_t)u * N;
+        float2 res[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const int iy = lane + 32 * r;
+            if (iy < N) {
+                const int step = iy - c;
+                float re = 0.f, im = 0.f;
+                int k = ((-c * step) % N + N) % N;
+                const int dk = (step % N + N) % N;
+                for (int vi = 0; vi < N; ++vi) {
+                    const float2 mv = grow[vi];
+                    const float2 t = pv.tw[k];
+                    re = fmaf(mv.x, t.x, fmaf(-mv.y, t.y, re));
+                    im = fmaf(mv.x, t.y, fmaf(mv.y, t.x, im));
+                    k += dk;
+                    if (k >= N) k -= N;
+                }
+                res[r] = make_float2(re, im);
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+            if (lane + 32 * r < N) grow[lane + 32 * r] = res[r];
+        __syncwarp();
+    }
     // (b2) per pixel row: m(ix, iy), r = w (d - m), then Q(u, iy) = sum_ix r exp(-2 pi i u (ix - c) / N)
     const int64_t off = P.offsets[gal];
     const float invN2 = gc.invN * gc.invN;
     double chi = 0.0;
     for (int iy = 0; iy < N; ++iy) {
         for (int ix = lane; ix < N; ix += 32) {
-            const int step = ix - c;
+            const int dk = ((ix - c) % N + N) % N;      // u (ix - c) mod N, advanced per u
+            int k = dk;
             float acc = pv.G[iy].x;                     // u = 0 (real)
             for (int u = 1; u < H; ++u) {
                 const float2 gv = pv.G[(size_t)u * N + iy];
-                const float2 t = twk(pv.tw, u * step, N);
+                const float2 t = pv.tw[k];
                 acc = fmaf(2.0f * gv.x, t.x, fmaf(-2.0f * gv.y, t.y, acc));
+                k += dk;
+                if (k >= N) k -= N;
             }
             const float m = acc * invN2;
             const int64_t idx = off + (int64_t)iy * N + ix;
@@ -958,33 +964,28 @@ __device__ double eval_pix(const FitParams &P, const GalCtx &gc, const PixView &
         }
         __syncwarp();
     }
-    // (b3) D' = Mt + scale_u R(u, v), R(u, v) = sum_iy Q(u, iy) exp(-2 pi i v (iy - c) / N)
-#pragma unroll
-    for (int j = 0; j < NC; ++j) {
-        const int vi = lane + 32 * j;
-        if (vi < N) {
-            const int v = vi - c;
-            int ox, oy, ot;
-            slot_offsets(npad, j, lane, ox, oy, ot);
-            const int dk = ((-v) % N + N) % N;
-            const int k0 = ((v * c) % N + N) % N;       // -v (iy - c) at iy = 0
-            for (int u = 0; u < H; ++u) {
-                float re = 0.f, im = 0.f;
-                int k = k0;
-                for (int iy = 0; iy < N; ++iy) {
-                    const float2 q = pv.G[(size_t)u * N + iy];
-                    const float2 t = pv.tw[k];
-                    re = fmaf(q.x, t.x, fmaf(-q.y, t.y, re));
-                    im = fmaf(q.x, t.y, fmaf(q.y, t.x, im));
-                    k += dk;
-                    if (k >= N) k -= N;
-                }
-                const float scale = (u == 0 ? 1.0f : sqrt2) * gc.invN;
-                float *row = pv.tab + (size_t)u * rowf;
-                row[ox] = fmaf(scale, re, row[ox]);
-                row[oy] = fmaf(scale, im, row[oy]);
-            }
+    // (b3) D' = Mt + scale_u R(u, v), R(u, v) = sum_iy Q(u, iy) exp(-2 pi i v (iy - c) / N);
+    // the H x N (u, v) outputs spread over the lanes
+    for (int t = lane; t < H * N; t += 32) {
+        const int u = t / N, vi = t - u * N, v = vi - c;
+        const int dk = ((-v) % N + N) % N;
+        int k = ((v * c) % N + N) % N;                  // -v (iy - c) at iy = 0
+        const float2 *qrow = pv.G + (size_t)u * N;
+        float re = 0.f, im = 0.f;
+        for (int iy = 0; iy < N; ++iy) {
+            const float2 q = qrow[iy];
+            const float2 tw = pv.tw[k];
+            re = fmaf(q.x, tw.x, fmaf(-q.y, tw.y, re));
+            im = fmaf(q.x, tw.y, fmaf(q.y, tw.x, im));
+            k += dk;
+            if (k >= N) k -= N;
         }
+        int ox, oy, ot;
+        slot_offsets(npad, vi >> 5, vi & 31, ox, oy, ot);
+        const float scale = (u == 0 ? 1.0f : sqrt2) * gc.invN;
+        float *row = pv.tab + (size_t)u * rowf;
+        row[ox] = fmaf(scale, re, row[ox]);
+        row[oy] = fmaf(scale, im, row[oy]);
     }
     __syncwarp();
     // (c) the gradient from the half-plane pass on the effective spectrum
