@@ -6,6 +6,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <new>
 #include <vector>
 
 #include "bs_internal.h"
@@ -695,9 +696,9 @@ void hermite_rule(int n, double *x, double *w)
 
 }  // namespace
 
-extern "C" bs_status bs_shear_estimate(const bs_shear_data *d, const bs_estimate_cfg *cfg, double *mean,
-                                       double *cov, int32_t *n_evals, void *workspace,
-                                       size_t workspace_bytes, void *stream)
+static bs_status shear_estimate_impl(const bs_shear_data *d, const bs_estimate_cfg *cfg, double *mean,
+                                     double *cov, int32_t *n_evals, void *workspace, size_t workspace_bytes,
+                                     void *stream)
 {
     bs_status st = validate_shear(d, "bs_shear_estimate");
     if (st != BS_OK) return st;
@@ -860,6 +861,18 @@ extern "C" bs_status bs_shear_estimate(const bs_shear_data *d, const bs_estimate
         }
     }
     return BS_OK;
+}
+
+extern "C" bs_status bs_shear_estimate(const bs_shear_data *d, const bs_estimate_cfg *cfg, double *mean,
+                                       double *cov, int32_t *n_evals, void *workspace,
+                                       size_t workspace_bytes, void *stream)
+{
+    // no C++ exception crosses the C ABI: a failed host allocation is reported
+    try {
+        return shear_estimate_impl(d, cfg, mean, cov, n_evals, workspace, workspace_bytes, stream);
+    } catch (const std::bad_alloc &) {
+        return fail(BS_ERR_OUT_OF_MEMORY, "bs_shear_estimate: host allocation failed");
+    }
 }
 
 namespace bs {

@@ -17,6 +17,8 @@
 #include <algorithm>
 #include <cstring>
 #include <numeric>
+#include <memory>
+#include <new>
 #include <vector>
 
 #include "bs_internal.h"
@@ -151,9 +153,12 @@ size_t bs_fit_plan_workspace_bytes(const bs_fit_args *args)
     return args ? plan_bytes(args->n_gal) : 0;
 }
 
-bs_status bs_fit_plan_create(const bs_fit_args *a, const bs_fit_out *o, const int32_t *side_host,
-                             int32_t flags, void *workspace, size_t workspace_bytes, void *stream,
-                             bs_fit_plan *plan)
+}  // extern "C"
+
+namespace {
+
+bs_status plan_create(const bs_fit_args *a, const bs_fit_out *o, const int32_t *side_host, int32_t flags,
+                      void *workspace, size_t workspace_bytes, void *stream, bs_fit_plan *plan)
 {
     if (!plan) return bs::set_error(BS_ERR_INVALID_ARG, "bs_fit_plan_create: NULL plan");
     if (flags & ~(BS_PLAN_CAPTURE | BS_PLAN_AUTOTUNE))
@@ -191,7 +196,9 @@ bs_status bs_fit_plan_create(const bs_fit_args *a, const bs_fit_out *o, const in
     if (e == cudaSuccess) e = cudaStreamSynchronize(s0);
     if (e != cudaSuccess) return bs::set_error(BS_ERR_CUDA, "bs_fit_plan_create: work list: %s", cudaGetErrorString(e));
 
-    bs_fit_plan_s *pl = new bs_fit_plan_s();
+    // owned until handed out; released (CUDA objects included) on every failure
+    std::unique_ptr<bs_fit_plan_s, void (*)(bs_fit_plan_s *)> owner(new bs_fit_plan_s(), release);
+    bs_fit_plan_s *pl = owner.get();
     pl->status = o->status;
     pl->n_gal = n;
     int dev = 0, sms = 1;
@@ -218,10 +225,8 @@ bs_status bs_fit_plan_create(const bs_fit_args *a, const bs_fit_out *o, const in
     }
     if ((flags & BS_PLAN_AUTOTUNE) && n > 0) {
         e = autotune(pl, sms);
-        if (e != cudaSuccess) {
-            release(pl);
+        if (e != cudaSuccess)
             return bs::set_error(BS_ERR_CUDA, "bs_fit_plan_create: autotune: %s", cudaGetErrorString(e));
-        }
     }
     if (capture && !pl->launches.empty()) {
         for (size_t i = 0; i < pl->launches.size() && e == cudaSuccess; ++i) {
@@ -233,7 +238,6 @@ bs_status bs_fit_plan_create(const bs_fit_args *a, const bs_fit_out *o, const in
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
         if (e != cudaSuccess) {
             if (cap) cudaStreamDestroy(cap);
-            release(pl);
             return bs::set_error(BS_ERR_CUDA, "bs_fit_plan_create: streams: %s", cudaGetErrorString(e));
         }
         // kernel attributes are set outside the capture
@@ -249,13 +253,30 @@ bs_status bs_fit_plan_create(const bs_fit_args *a, const bs_fit_out *o, const in
         if (e == cudaSuccess && st == BS_OK) e = cudaGraphInstantiate(&pl->exec, pl->graph, 0);
         cudaStreamDestroy(cap);
         if (st != BS_OK || e != cudaSuccess) {
-            release(pl);
             if (st != BS_OK) return st;
             return bs::set_error(BS_ERR_CUDA, "bs_fit_plan_create: graph: %s", cudaGetErrorString(e));
         }
     }
-    *plan = pl;
+    *plan = owner.release();
     return BS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+bs_status bs_fit_plan_create(const bs_fit_args *a, const bs_fit_out *o, const int32_t *side_host,
+                             int32_t flags, void *workspace, size_t workspace_bytes, void *stream,
+                             bs_fit_plan *plan)
+{
+    // no C++ exception crosses the C ABI: a failed host allocation is reported
+    try {
+        return plan_create(a, o, side_host, flags, workspace, workspace_bytes, stream, plan);
+    } catch (const std::bad_alloc &) {
+        return bs::set_error(BS_ERR_OUT_OF_MEMORY, "bs_fit_plan_create: host allocation failed");
+    } catch (const std::exception &ex) {
+        return bs::set_error(BS_ERR_CUDA, "bs_fit_plan_create: %s", ex.what());
+    }
 }
 
 bs_status bs_fit_plan_launch(bs_fit_plan plan, void *stream)

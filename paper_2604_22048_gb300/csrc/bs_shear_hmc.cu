@@ -15,6 +15,7 @@
 // numbers: Philox4x64-10 keyed by (seed, 0), counter (iteration, block, 0).
 #include <cmath>
 #include <cstring>
+#include <new>
 #include <vector>
 
 #include "bs_device.cuh"
@@ -149,9 +150,13 @@ void bs_shear_hyperprior_default(double lo[8], double hi[8])
     if (hi) std::memcpy(hi, h, sizeof h);
 }
 
-bs_status bs_shear_sample(const bs_shear_data *d, const bs_shear_sample_cfg *cfg, double *samples,
-                          double *accept_rate, double *step_size, int32_t *n_evals, void *workspace,
-                          size_t workspace_bytes, void *stream)
+}  // extern "C"
+
+namespace {
+
+bs_status shear_sample_impl(const bs_shear_data *d, const bs_shear_sample_cfg *cfg, double *samples,
+                            double *accept_rate, double *step_size, int32_t *n_evals, void *workspace,
+                            size_t workspace_bytes, void *stream)
 {
     const char *who = "bs_shear_sample";
     if (!d || !cfg || !samples) return bs::set_error(BS_ERR_INVALID_ARG, "%s: NULL argument", who);
@@ -284,6 +289,23 @@ bs_status bs_shear_sample(const bs_shear_data *d, const bs_shear_sample_cfg *cfg
     if (step_size) *step_size = eps;
     if (n_evals) *n_evals = T.n_evals;
     return BS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+bs_status bs_shear_sample(const bs_shear_data *d, const bs_shear_sample_cfg *cfg, double *samples,
+                          double *accept_rate, double *step_size, int32_t *n_evals, void *workspace,
+                          size_t workspace_bytes, void *stream)
+{
+    // no C++ exception crosses the C ABI: a failed host allocation is reported
+    try {
+        return shear_sample_impl(d, cfg, samples, accept_rate, step_size, n_evals, workspace, workspace_bytes,
+                                 stream);
+    } catch (const std::bad_alloc &) {
+        return bs::set_error(BS_ERR_OUT_OF_MEMORY, "bs_shear_sample: host allocation failed");
+    }
 }
 
 }  // extern "C"
