@@ -443,6 +443,16 @@ __device__ __forceinline__ float rsqrt_ge1(float s)
     return r;
 }
 
+// 1/s for s >= 1 on the special-function unit: squaring the reciprocal
+// square root would cost the FMA pipe, which bounds the fit kernels, one
+// more packed multiply per point pair.
+__device__ __forceinline__ float rcp_ge1(float s)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(s));
+    return r;
+}
+
 // Packed FP32x2 helpers (two column slots of a lane in one instruction; each
 // half is rounded exactly like the scalar operation).
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
@@ -555,7 +565,7 @@ __device__ __forceinline__ void row_terms(Sums<NCT> &S, const SlotConst<NCT> &K,
         float2 A, rs2;                                                   // |M| / F and psi
         if (PROF == 0) {
             const float2 rs = make_float2(rsqrt_ge1(s.x), rsqrt_ge1(s.y));
-            rs2 = mul2(rs, rs);
+            rs2 = make_float2(rcp_ge1(s.x), rcp_ge1(s.y));
             A = mul2(mul2(T, rs2), rs);
         } else {
             float2 fa;
