@@ -190,10 +190,11 @@ class ClockSampler:
 
 def flops_per_eval(N):
     """FP32 operations of one log-posterior gradient evaluation on an N x N
-    stamp: 33 per half-plane k-point (the model amplitude and phase, the
-    conjugate product with the data spectrum and seven gradient sums; an FMA
-    counts 2) over (N+1)/2 x N points, plus 9 per row for the phase
-    recurrence and wavenumber."""
+    stamp: 33 per half-plane k-point (the model amplitude with its reciprocal
+    square root and reciprocal counted one each, the phase, the conjugate
+    product with the data spectrum and the five gradient sums accumulated per
+    point, from which the other two follow; an FMA counts 2) over (N+1)/2 x N
+    points, plus 9 per row for the phase recurrence and wavenumber."""
     H = (N + 1) // 2
     return 33 * H * N + 9 * H
 
@@ -203,9 +204,9 @@ def flops_per_eval(N):
 # the kernel source it was taken on, identified by its sha256; after any change
 # to that file the traffic is reported as null until the next capture.
 CAPTURED_TRAFFIC = {
-    # 53x53 galaxy of the plain workload: (13,922,560 + 5,888) B / 1,216 galaxies
+    # 53x53 galaxy of the plain workload: (13,920,512 + 3,840) B / 1,216 galaxies
     "fit": ("paper_2604_22048_gb300/csrc/bs_fit_impl.cuh",
-            "c6b855a09f8ab6c10ed0c87f733fda171c86e004dccc1c49888d5a1d8d0f7ab0", 11454.3),
+            "9424babdee6cb934675f6b154bc8929b37863e6f16562f5292608af91deaf5e2", 11450.9),
     # one interim sample of the shear workload: (489,382,400 + 3,253,248) B / (200,000 x 300)
     "shear": ("paper_2604_22048_gb300/csrc/bs_shear.cu",
               "b4890a1fdfa8e5daa61ed60ed9961e71679d96605796c19047562104d32f052d", 8.2106),

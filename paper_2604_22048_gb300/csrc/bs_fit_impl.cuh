@@ -453,6 +453,17 @@ __device__ __forceinline__ float rcp_ge1(float s)
     return r;
 }
 
+// sin(pi x) and cos(pi x) for the per-evaluation phase factors, on the
+// special-function unit: x - 2 rint(x / 2) reduces x to [-1, 1] without
+// rounding error, so the hardware approximation sees an angle in [-pi, pi],
+// where its absolute error is about 2^-21 (the library's sincospif spends a
+// polynomial on the FMA pipe per call for its last bits).
+__device__ __forceinline__ void sincospi_sfu(float x, float *s, float *c)
+{
+    const float r = fmaf(-2.0f, rintf(0.5f * x), x);
+    __sincosf(3.14159265358979f * r, s, c);
+}
+
 // Packed FP32x2 helpers (two column slots of a lane in one instruction; each
 // half is rounded exactly like the scalar operation).
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
@@ -488,7 +499,7 @@ __device__ __forceinline__ void comp_add2(float2 &hi, float2 &lo, float2 x)
 template <int NCT>
 struct Sums {
     static constexpr int NP = NCT / 2 > 0 ? NCT / 2 : 1;
-    float2 Sa, Swkx2, Sbkx;                 // sum a, sum w kx^2, sum b kx (both halves)
+    float2 Swkx2, Sbkx;                     // sum w kx^2, sum b kx (both halves)
     float2 Wc[NP], Wkx[NP], Bc[NP];         // per slot: sum w, sum w kx, sum b
     float sWc, sWkx, sBc;                   // odd slot
     float2 chi_hi, chi_lo;                  // compensated sum |Dt - Mt|^2
@@ -579,7 +590,6 @@ __device__ __forceinline__ void row_terms(Sums<NCT> &S, const SlotConst<NCT> &K,
         const float2 a = mul2(A, fma2(A, nF2v, zr));                    // Re conj(D - M) M
         const float2 bb = mul2(A, zi);                                  // Im conj(D - M) M
         const float2 w = mul2(a, rs2);                                  // a / s
-        S.Sa = add2(S.Sa, a);
         S.Wc[p] = add2(S.Wc[p], w);
         S.Wkx[p] = fma2(w, kxv, S.Wkx[p]);
         S.Swkx2 = fma2(w, kx2v, S.Swkx2);
@@ -613,7 +623,6 @@ __device__ __forceinline__ void row_terms(Sums<NCT> &S, const SlotConst<NCT> &K,
         const float a = A * fmaf(-A, F2, zr);
         const float bb = A * zi;
         const float w = a * rs2;
-        S.Sa.x += a;
         S.sWc += w;
         S.sWkx = fmaf(w, kx, S.sWkx);
         S.Swkx2.x = fmaf(w, kx2, S.Swkx2.x);
@@ -651,20 +660,22 @@ __device__ __forceinline__ void half_plane(Sums<NCT> &S, const SlotConst<NCT> &K
     }
 }
 
-// Sums over the warp of seven per-lane values, returned in every lane with
+// Sums over the warp of NV <= 8 per-lane values, returned in every lane with
 // identical bits.  Recursive halving: at each xor distance a lane keeps half
 // of its values and receives the partner's partial sums of them, so after
 // distances 16, 8, 4 lane l holds value (l >> 2) & 7 summed over 8 lanes; two
 // butterfly steps finish it (commutative adds, so the 4 lanes of a group
 // agree) and one shuffle per value broadcasts it from lane 4 j.
-__device__ __forceinline__ void warp_sum7(float (&v)[7])
+template <int NV>
+__device__ __forceinline__ void warp_sum_n(float (&v)[NV])
 {
+    static_assert(NV >= 5 && NV <= 8, "four values per half at the first step");
     const int lane = threadIdx.x & 31;
     float r4[4];
     const bool h16 = lane & 16;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        const float lo = v[k], hi = k + 4 < 7 ? v[k + 4] : 0.0f;
+        const float lo = v[k], hi = k + 4 < NV ? v[k + 4] : 0.0f;
         const float keep = h16 ? hi : lo, send = h16 ? lo : hi;
         r4[k] = keep + __shfl_xor_sync(BS_FULL_MASK, send, 16);
     }
@@ -680,7 +691,7 @@ __device__ __forceinline__ void warp_sum7(float (&v)[7])
     r += __shfl_xor_sync(BS_FULL_MASK, r, 2);
     r += __shfl_xor_sync(BS_FULL_MASK, r, 1);
 #pragma unroll
-    for (int j = 0; j < 7; ++j) v[j] = __shfl_sync(BS_FULL_MASK, r, 4 * j);
+    for (int j = 0; j < NV; ++j) v[j] = __shfl_sync(BS_FULL_MASK, r, 4 * j);
 }
 
 // Log posterior (if want_ll) and gradient at th, warp-cooperative.
@@ -707,7 +718,7 @@ __device__ __forceinline__ double eval_logpost(const FitParams &P, const GalCtx 
         const int lane = threadIdx.x & 31;
         for (int u = lane; u < gc.H; u += 32) {
             float sx, cx;
-            sincospif(-2.0f * th[4] * (float)u * gc.invN, &sx, &cx);
+            sincospi_sfu(-2.0f * th[4] * (float)u * gc.invN, &sx, &cx);
             xph[u] = make_float2(cx, sx);
         }
         __syncwarp();
@@ -716,7 +727,7 @@ __device__ __forceinline__ double eval_logpost(const FitParams &P, const GalCtx 
 #pragma unroll
     for (int j = 0; j < NC; ++j) {
         float s, co;
-        sincospif(-2.0f * th[5] * vcol[j] * gc.invN, &s, &co);   // exp(-2 pi i v dy / N)
+        sincospi_sfu(-2.0f * th[5] * vcol[j] * gc.invN, &s, &co);   // exp(-2 pi i v dy / N)
         Yr[j] = F * co;
         Yi[j] = F * s;
         ky[j] = vcol[j] * dk;
@@ -743,7 +754,6 @@ __device__ __forceinline__ double eval_logpost(const FitParams &P, const GalCtx 
         K.scst = cst[NC - 1];
         K.sgky = gky[NC - 1];
     }
-    S.Sa = f2(0.f);
     S.Swkx2 = f2(0.f);
     S.Sbkx = f2(0.f);
     S.sWc = 0.f;
@@ -757,7 +767,7 @@ __device__ __forceinline__ double eval_logpost(const FitParams &P, const GalCtx 
         half_plane<NC, false, PROF>(S, K, tab, kxr, xph, gc.H, al, F2, P.prof_npow);
     __syncwarp();   // the table is rewritten by the next evaluation
 
-    float Sa = S.Sa.x + S.Sa.y, Swkx2 = S.Swkx2.x + S.Swkx2.y, Sbkx = S.Sbkx.x + S.Sbkx.y;
+    float Swkx2 = S.Swkx2.x + S.Swkx2.y, Sbkx = S.Sbkx.x + S.Sbkx.y;
     float Sw = 0.f, Swky2 = 0.f, Swkxky = 0.f, Sbky = 0.f;
 #pragma unroll
     for (int j = 0; j < NC; ++j) {
@@ -777,15 +787,19 @@ __device__ __forceinline__ double eval_logpost(const FitParams &P, const GalCtx 
         Swkxky = fmaf(ky[j], wkx, Swkxky);
         Sbky = fmaf(ky[j], bc, Sbky);
     }
-    float sums[7] = {Sa, Sw, Swkx2, Swky2, Swkxky, Sbkx, Sbky};
-    warp_sum7(sums);
-    Sa = sums[0];
-    Sw = sums[1];
-    Swkx2 = sums[2];
-    Swky2 = sums[3];
-    Swkxky = sums[4];
-    Sbkx = sums[5];
-    Sbky = sums[6];
+    float sums[6] = {Sw, Swkx2, Swky2, Swkxky, Sbkx, Sbky};
+    warp_sum_n(sums);
+    Sw = sums[0];
+    Swkx2 = sums[1];
+    Swky2 = sums[2];
+    Swkxky = sums[3];
+    Sbkx = sums[4];
+    Sbky = sums[5];
+    // sum of w (s - 1) = al sum w kx^2 + be sum w ky^2 + ga sum w kx ky.  With
+    // psi = 1/s (exponential, Spergel) a = w s, so sum a = sum w + that; with
+    // psi = 1 (Gaussian) a = w.  The sum of a is therefore not accumulated.
+    const float st = al * Swkx2 + be * Swky2 + ga * Swkxky;
+    const float Sa = PROF == 2 ? Sw : Sw + st;
 
     const float ib = gc.inv_b;
     const float P2 = Pq * Pq;
@@ -798,15 +812,13 @@ __device__ __forceinline__ double eval_logpost(const FitParams &P, const GalCtx 
     const float dg2 = r02 * (4.0f * Pq + 8.0f * e2 * e2 * P2);
     g[0] = kLn10 * Sa * ib;
     if (PROF == 0) {
-        g[1] = -3.0f * kLn10 * (Sa - Sw) * ib;
+        g[1] = -3.0f * kLn10 * st * ib;
         g[2] = -1.5f * (da1 * Swkx2 + db1 * Swky2 + dg1 * Swkxky) * ib - 4.0f * e1 * Pq - e1 * P.inv_se2;
         g[3] = -1.5f * (da2 * Swkx2 + db2 * Swky2 + dg2 * Swkxky) * ib - 4.0f * e2 * Pq - e2 * P.inv_se2;
     } else {
-        // d M / d log10 hlr = -2 c ln10 psi (s - 1) M: psi (s - 1) = 1 - 1/s
-        // (Spergel), or s - 1 = al kx^2 + be ky^2 + ga kx ky itself (Gaussian,
-        // psi = 1, so the w sums are the a sums)
+        // d M / d log10 hlr = -2 c ln10 psi (s - 1) M, and the sum of
+        // a psi (s - 1) = w (s - 1) is st for both profiles
         const float c = P.prof_c;
-        const float st = PROF == 1 ? Sa - Sw : al * Swkx2 + be * Swky2 + ga * Swkxky;
         g[1] = -2.0f * c * kLn10 * st * ib;
         g[2] = -c * (da1 * Swkx2 + db1 * Swky2 + dg1 * Swkxky) * ib - 4.0f * e1 * Pq - e1 * P.inv_se2;
         g[3] = -c * (da2 * Swkx2 + db2 * Swky2 + dg2 * Swkxky) * ib - 4.0f * e2 * Pq - e2 * P.inv_se2;
@@ -872,7 +884,7 @@ __device__ double eval_pix(const FitParams &P, const GalCtx &gc, const PixView &
     const float sqrt2 = 1.41421356237309515f;
     for (int u = lane; u < H; u += 32) {
         float sx, cx;
-        sincospif(-2.0f * th[4] * (float)u * gc.invN, &sx, &cx);
+        sincospi_sfu(-2.0f * th[4] * (float)u * gc.invN, &sx, &cx);
         xph[u] = make_float2(cx, sx);
     }
     __syncwarp();
@@ -881,7 +893,7 @@ __device__ double eval_pix(const FitParams &P, const GalCtx &gc, const PixView &
     for (int j = 0; j < NC; ++j) {
         const int vi = lane + 32 * j;
         float sy, cy;
-        sincospif(-2.0f * th[5] * vcol[j] * gc.invN, &sy, &cy);
+        sincospi_sfu(-2.0f * th[5] * vcol[j] * gc.invN, &sy, &cy);
         const float Yr = F * cy, Yi = F * sy;
         const float ky = vcol[j] * gc.dk;
         const float cst = fmaf(be * ky, ky, 1.0f), gky = ga * ky;
