@@ -361,6 +361,7 @@ def our_arm(a, world, rank, local_rank):
     fev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
     est_evals.clear()
     barrier()
+    launches0 = api.kernel_launches()
     wall0 = time.perf_counter()
     for i in range(a.steps):
         flush.zero_()
@@ -369,6 +370,7 @@ def our_arm(a, world, rank, local_rank):
         ev[i][1].record(stream)
     barrier()
     wall = time.perf_counter() - wall0
+    launches = api.kernel_launches() - launches0
     clk = clocks.stop()
     step_ms = sum(e[0].elapsed_time(e[1]) for e in ev)
     fit_ms = [e[0].elapsed_time(e[1]) for e in fev]
@@ -412,8 +414,7 @@ def our_arm(a, world, rank, local_rank):
                         "dfma_microbenchmark_tflops": api.fp64_peak_tflops(),
                         "flops_per_launch": fit_flops, "evals_per_launch": n_grad,
                         "fit_ms": float(np.mean(fit_ms))},
-           "gpu_launches": int(a.steps * len(plan.info())
-                               + 2 * sum(est_evals)),
+           "gpu_launches": launches,
            "clocks": clk,
            "ess": {"mean_per_galaxy": float(ess_gal.mean().item()),
                    "frac_galaxies_ge_300": float((ess_gal >= 300).float().mean().item()),
@@ -580,12 +581,14 @@ def shear_arm(a, world, rank, local_rank):
     clocks = ClockSampler(local_rank)
     clocks.start()
     e0, e1v = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = api.kernel_launches()
     e0.record(stream)
     for _ in range(a.steps):
         for p in grid:
             plan.loglike(*p)
     e1v.record(stream)
     torch.cuda.synchronize(dev)
+    launches = api.kernel_launches() - launches0
     clk = clocks.stop()
     ms = e0.elapsed_time(e1v)
     passes = a.steps * len(grid)
@@ -668,7 +671,7 @@ def shear_arm(a, world, rank, local_rank):
                                          "the same kernel source by the samples per pass",
                          "kernel": "shear_kernel_async<1,0>",
                          "bytes_per_pass": bytes_per_pass, "peak_how": "measured copy bandwidth"},
-            "gpu_launches": 2 * passes, "clocks": clk,
+            "gpu_launches": launches, "clocks": clk,
             "estimate": {"g": [float(x) for x in mean[:2]], "alpha": float(mean[2]),
                          "sd": [float(np.sqrt(cov[i, i])) for i in range(3)], "truth": list(g_true) + [alpha_true],
                          "passes": est_passes, "seconds": est_s},

@@ -91,6 +91,14 @@ void bs_prior_default(bs_prior *prior);
 const char *bs_last_error(void);
 const char *bs_version(void);
 
+/* Number of kernels this library has launched in this process, over all
+ * threads and devices: each direct launch counts one when it is issued, and
+ * each replay of a fit plan's CUDA graph counts the kernels the graph holds
+ * (kernels recorded while the graph is captured are not launches).  Read it
+ * before and after a region to count that region's launches.  Never fails;
+ * instrumentation, not a step of the method (the paper has no counterpart). */
+uint64_t bs_kernel_launches(void);
+
 /* ------------------------------------------------------------------------ */
 /* Rendering (forward model, Sec. 3.3)                                       */
 /* ------------------------------------------------------------------------ */

@@ -27,7 +27,8 @@ EXPORTED = ["bs_prior_default", "bs_last_error", "bs_version", "bs_render", "bs_
             "bs_fit_plan_workspace_bytes", "bs_fit_plan_create", "bs_fit_plan_launch", "bs_fit_plan_destroy",
             "bs_fit_resident_galaxies", "bs_fit_plan_num_launches", "bs_fit_plan_info", "bs_serve_request_bytes", "bs_serve_create", "bs_serve_submit",
             "bs_serve_poll", "bs_serve_get_stats", "bs_serve_now_ns", "bs_serve_destroy",
-            "bs_shear_hyperprior_default", "bs_shear_sample", "bs_fp32_peak", "bs_fp64_peak", "bs_shear_loglike_multi"]
+            "bs_shear_hyperprior_default", "bs_shear_sample", "bs_fp32_peak", "bs_fp64_peak", "bs_shear_loglike_multi",
+            "bs_kernel_launches"]
 
 
 class BsError(RuntimeError):
@@ -161,6 +162,8 @@ def lib():
     L.bs_prior_default.restype = None
     L.bs_last_error.restype = C.c_char_p
     L.bs_version.restype = C.c_char_p
+    L.bs_kernel_launches.argtypes = []
+    L.bs_kernel_launches.restype = C.c_uint64
     L.bs_render.argtypes = [i32, vp, vp, vp, vp, i32, vp, i32, f32, vp, vp]
     L.bs_fit_workspace_bytes.argtypes = [C.POINTER(FitArgs)]
     L.bs_fit_workspace_bytes.restype = sz

@@ -347,6 +347,13 @@ def fp32_peak_tflops(packed=False):
     return t.value
 
 
+def kernel_launches():
+    """Kernels the library has launched in this process so far (graph replays
+    count the kernels they hold); the difference over a region counts its
+    launches."""
+    return int(F.lib().bs_kernel_launches())
+
+
 def fp64_peak_tflops():
     """Measured FP64 FMA throughput of the current GPU (TFLOP/s, FMA = 2)."""
     t = C.c_double(0)

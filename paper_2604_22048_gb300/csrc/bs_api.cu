@@ -2,6 +2,7 @@
 // the per-galaxy constants of the shear likelihood, and the host-driven
 // shear estimate (Newton to the mode, Gauss-Hermite quadrature on the
 // Laplace-scaled grid).  See include/bpshear.h for the contract of each call.
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -406,10 +407,12 @@ bs_status bs_shear_loglike(const bs_shear_data *d, double g1, double g2, double 
         L.partials = partials;
         e = bs::launch_shear(L, grid, s);
         if (e != cudaSuccess) return cuda_fail(e, "bs_shear_loglike: launch");
+        bs::count_launches(1);
     }
     const int n_part = d->n_gal > 0 ? grid : 0;
     e = bs::launch_shear_finalize(partials, n_part, add[0], add[1], add[2], add[3], alpha_scale, dev_out, s);
     if (e != cudaSuccess) return cuda_fail(e, "bs_shear_loglike: finalize");
+    bs::count_launches(1);
     if (out_on_host) {
         e = cudaMemcpyAsync(out, dev_out, 4 * sizeof(double), cudaMemcpyDeviceToHost, s);
         if (e != cudaSuccess) return cuda_fail(e, "bs_shear_loglike: copy");
@@ -458,6 +461,7 @@ bs_status bs_shear_loglike_multi(const bs_shear_data *d, int32_t n_points, const
         if (d->n_gal > 0) {
             e = bs::launch_shear_multi(M, grid, s);
             if (e != cudaSuccess) return cuda_fail(e, "bs_shear_loglike_multi: launch");
+            bs::count_launches(1);
         }
         const int n_part = d->n_gal > 0 ? grid : 0;
         double *dev_out = out_on_host ? host_stage : out + 4 * (size_t)start;
@@ -465,6 +469,7 @@ bs_status bs_shear_loglike_multi(const bs_shear_data *d, int32_t n_points, const
             e = bs::launch_shear_finalize(partials + (size_t)p * grid * 4, n_part, add[p][0], add[p][1], add[p][2],
                                           add[p][3], ascale[p], dev_out + 4 * p, s);
             if (e != cudaSuccess) return cuda_fail(e, "bs_shear_loglike_multi: finalize");
+            bs::count_launches(1);
         }
         if (out_on_host) {
             e = cudaMemcpyAsync(out + 4 * (size_t)start, host_stage, 4 * np * sizeof(double), cudaMemcpyDeviceToHost,
@@ -513,6 +518,7 @@ bs_status bs_shear_loglike_full(const bs_shear_data *d, const float *lf, const f
         F.s.partials = partials;
         e = bs::launch_shear_full(F, grid, s);
         if (e != cudaSuccess) return cuda_fail(e, "bs_shear_loglike_full: launch");
+        bs::count_launches(1);
     }
     // per-galaxy constants of the flux/size ratio: log 2 - log sigma_f - log sigma_s
     // - log 2 pi + log of the interim widths (Eq. lflux-lsize-dist over the
@@ -536,6 +542,7 @@ bs_status bs_shear_loglike_full(const bs_shear_data *d, const float *lf, const f
     const int n_part = d->n_gal > 0 ? grid : 0;
     e = bs::launch_shear_finalize_n(partials, n_part, bs::kShearFullOut, scale, add, dev_out, s);
     if (e != cudaSuccess) return cuda_fail(e, "bs_shear_loglike_full: finalize");
+    bs::count_launches(1);
     if (out_on_host) {
         e = cudaMemcpyAsync(out, dev_out, bs::kShearFullOut * sizeof(double), cudaMemcpyDeviceToHost, s);
         if (e != cudaSuccess) return cuda_fail(e, "bs_shear_loglike_full: copy");
@@ -903,6 +910,23 @@ bs_status set_error(bs_status st, const char *fmt, ...)
 
 // Number of galaxies the per-galaxy constants count: the weight sum when
 // galaxies carry weights.
+namespace {
+std::atomic<unsigned long long> g_kernel_launches{0};   // one process-wide count
+thread_local unsigned long long *tl_capture_tally = nullptr;
+}  // namespace
+
+void count_launches(unsigned long long n)
+{
+    if (tl_capture_tally)
+        *tl_capture_tally += n;
+    else
+        g_kernel_launches.fetch_add(n, std::memory_order_relaxed);
+}
+
+void capture_launches(unsigned long long *tally) { tl_capture_tally = tally; }
+
+unsigned long long kernel_launches_total() { return g_kernel_launches.load(std::memory_order_relaxed); }
+
 double shear_weight_total(const bs_shear_data *d)
 {
     return d->gal_weight ? d->gal_weight_sum : (double)d->n_gal;
@@ -942,3 +966,5 @@ bs_status shear_prepare(const bs_shear_data *d, double g1, double g2, double alp
 }
 
 }  // namespace bs
+
+extern "C" uint64_t bs_kernel_launches(void) { return bs::kernel_launches_total(); }

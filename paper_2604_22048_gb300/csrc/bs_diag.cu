@@ -144,6 +144,7 @@ cudaError_t measure_fma_peak(int kind, double &tflops, cudaStream_t stream)
             dfma_kernel<<<grid, block, 0, stream>>>(out, iters, 1.0000000001, 1e-10);
         else
             ffma_kernel<false><<<grid, block, 0, stream>>>(out, iters, 1.0000001f, 1e-7f);
+        count_launches(1);
         if (e == cudaSuccess) e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaEventRecord(e1, stream);
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
@@ -167,6 +168,7 @@ cudaError_t launch_chain_ess(const float *samples, int n_gal, int n_chains, int 
     if (warps == 0) return cudaSuccess;
     const long long blocks = (warps + 3) / 4;
     ess_kernel<<<(unsigned)blocks, 128, 0, stream>>>(samples, n_gal, n_chains, n_samples, ess, rhat);
+    count_launches(1);
     return cudaGetLastError();
 }
 

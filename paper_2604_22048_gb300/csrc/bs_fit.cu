@@ -67,6 +67,7 @@ cudaError_t launch_fit(const FitParams &p, int grid, cudaStream_t stream)
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k<<<grid, 32 * p.n_chains, smem, stream>>>(p);
+    bs::count_launches(1);
     return cudaGetLastError();
 }
 
@@ -82,6 +83,7 @@ cudaError_t launch_logpost_points(const FitParams &p, int n_points, const int32_
     const int grid = n_points < 4096 ? n_points : 4096;
     if (grid <= 0) return cudaSuccess;
     logpost_points_kernel<0><<<grid, 32, smem, stream>>>(p, n_points, gal_index, theta, logp, grad);
+    bs::count_launches(1);
     return cudaGetLastError();
 }
 

@@ -142,6 +142,13 @@ int warmup_windows(int W, bool adapt, int *st, int *en, int cap);
 
 // Thread-local error message of the C ABI (bs_last_error).
 bs_status set_error(bs_status st, const char *fmt, ...);
+
+// Kernel launches of the library (bs_kernel_launches): every launch site adds
+// one.  While a thread captures a CUDA graph its launches go to the capture's
+// own tally instead (capture_launches), which the graph's replays then add.
+void count_launches(unsigned long long n);
+void capture_launches(unsigned long long *tally);
+unsigned long long kernel_launches_total();
 // Validate a shear-likelihood request and fill the kernel arguments (except
 // `partials`) and the per-galaxy constants the finalize step adds:
 // add = {value, d/dg1, d/dg2, d/dalpha}, alpha_scale multiplies the sum of

@@ -84,10 +84,12 @@ extern "C" bs_status bs_shear_loglike_noalloc(const bs_shear_data *data, double 
         e = bs::launch_shear(L, grid, s);
         if (e != cudaSuccess)
             return bs::set_error(BS_ERR_CUDA, "bs_shear_loglike_noalloc: launch: %s", cudaGetErrorString(e));
+        bs::count_launches(1);
     }
     e = bs::launch_shear_finalize(scratch, data->n_gal > 0 ? grid : 0, add[0], add[1], add[2], add[3],
                                   alpha_scale, out, s);
     if (e != cudaSuccess)
         return bs::set_error(BS_ERR_CUDA, "bs_shear_loglike_noalloc: finalize: %s", cudaGetErrorString(e));
+    bs::count_launches(1);
     return BS_OK;
 }

@@ -36,6 +36,7 @@ struct bs_fit_plan_s {
     cudaEvent_t fork = nullptr, join[4] = {};
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    unsigned long long graph_kernels = 0;   // kernels one replay of the graph launches
     int32_t *status = nullptr;
     int n_gal = 0;
 };
@@ -244,7 +245,9 @@ bs_status plan_create(const bs_fit_args *a, const bs_fit_out *o, const int32_t *
         for (auto &L : pl->launches) bs::fit_blocks_per_sm(a->n_chains, L.p.max_side, L.p.regs, L.p.profile);
         e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
+            bs::capture_launches(&pl->graph_kernels);   // recorded, not launched
             st = enqueue(pl, cap, true);
+            bs::capture_launches(nullptr);
             cudaError_t e2 = cudaStreamEndCapture(cap, &pl->graph);
             if (st == BS_OK && e2 != cudaSuccess) {
                 e = e2;
@@ -285,8 +288,9 @@ bs_status bs_fit_plan_launch(bs_fit_plan plan, void *stream)
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (plan->exec) {
         cudaError_t e = cudaGraphLaunch(plan->exec, s);
-        return e == cudaSuccess ? BS_OK
-                                : bs::set_error(BS_ERR_CUDA, "bs_fit_plan_launch: %s", cudaGetErrorString(e));
+        if (e != cudaSuccess) return bs::set_error(BS_ERR_CUDA, "bs_fit_plan_launch: %s", cudaGetErrorString(e));
+        bs::count_launches(plan->graph_kernels);
+        return BS_OK;
     }
     return enqueue(plan, s, false);
 }

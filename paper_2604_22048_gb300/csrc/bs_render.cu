@@ -157,6 +157,7 @@ cudaError_t launch_render(int n, const float *theta, const float *shear, const i
     const int grid = n < 65535 ? n : 65535;
     render_kernel<<<grid, 256, smem, stream>>>(n, theta, shear, offsets, side, max_side, psf, n_psf,
                                               pixel_scale, out);
+    bs::count_launches(1);
     return cudaGetLastError();
 }
 

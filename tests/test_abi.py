@@ -31,6 +31,11 @@ def test_every_declared_symbol_is_exported(L):
     assert sorted(_ffi.EXPORTED) == syms
 
 
+def test_launch_counter_without_a_gpu(L):
+    # nothing has been launched in a process without a GPU; reading never fails
+    assert L.bs_kernel_launches() == 0
+
+
 def test_version_and_prior_default(L):
     from paper_2604_22048_gb300 import _ffi
     assert b"sm_103a" in L.bs_version()
