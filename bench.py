@@ -28,7 +28,10 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "galaxies/sec at 300 ESS/galaxy (plain batched path, 1 GB300)"
+# The headline metric as the workload definition names it; the default line's
+# value is the plain batched throughput, with the served-vs-plain comparison
+# and the p50/p99 latencies in the same line.
+METRIC = "galaxies/sec at 300 ESS/galaxy (served vs plain batch, 1 GB300); p50/p99 latency"
 UNIT = "galaxies/s"
 FP32_LANES_PER_SM = 128
 
@@ -686,7 +689,7 @@ def shear_arm(a, world, rank, local_rank):
 
 # ----------------------------------------------------------------------------- serving
 
-SERVE_METRIC = "galaxies/sec at 300 ESS/galaxy (served vs plain batch, 1 GB300); p50/p99 latency"
+SERVE_METRIC = METRIC
 
 
 def serving_pool(a, dev, n_pool):
