@@ -19,10 +19,12 @@
 //   d chi^2/d theta = -2 sum_half Re[conj(Dt - Mt) dMt/dtheta],
 // i.e. the residual's adjoint DFT is Dt - Mt exactly, and the per-evaluation
 // cost is one pass over the half plane instead of two O(N^3) transforms.
-// The gradient needs seven sums, accumulated per lane in FP32 and reduced
-// with an xor butterfly (identical bits in all lanes, so warp-uniform
-// decisions stay uniform); chi^2 is accumulated with compensated FP32 per
-// lane and finished in FP64 at the warp total.
+// The gradient needs seven sums: six are accumulated per lane in FP32 (five
+// per point, three of them per column and weighted by ky once at the end)
+// and reduced with an xor butterfly (identical bits in all lanes, so
+// warp-uniform decisions stay uniform), and the seventh follows from them;
+// chi^2 is accumulated with compensated FP32 per lane and finished in FP64
+// at the warp total.
 //
 // Chain state.  Lane i < 6 owns parameter i of the chain (position hi/lo,
 // momentum, gradient, inverse metric, Welford moments) as scalars; the six
