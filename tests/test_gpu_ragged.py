@@ -72,7 +72,7 @@ def test_ragged_plan_coupled_to_oracle(cuda):
 def test_autotuned_plan_matches_untuned(cuda):
     """The autotuner only picks the register budget of each class launch: the
     chains must be bit-identical to the untuned plan's, and every class must
-    report a budget and its two trial times."""
+    report a budget and the trial times of all three instances."""
     truth = synth.draw_ragged(64, seed=33)
     truth.side = np.array([SIDES[i % len(SIDES)] for i in range(64)], dtype=np.int32)
     ds = datagen.make_dataset(truth, 2)
@@ -94,6 +94,6 @@ def test_autotuned_plan_matches_untuned(cuda):
     assert sorted(i["slot_class"] for i in info) == [1, 2, 3, 4]
     for i in info:
         t = {128: i["trial_ms_128"], 96: i["trial_ms_96"], 80: i["trial_ms_80"]}
-        assert i["registers"] in t and all(v > 0 for v in t.values())
-        assert t[i["registers"]] <= min(t.values())
+        assert i["registers"] in (128, 96) and all(v > 0 for v in t.values())
+        assert t[i["registers"]] <= min(t[128], t[96])     # the 80-register instance is timed, not chosen
     assert all(i["trial_ms_128"] == 0 and i["registers"] == 128 for i in plain.info())
