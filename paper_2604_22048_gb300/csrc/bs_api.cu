@@ -510,6 +510,9 @@ bs_status bs_shear_loglike_full(const bs_shear_data *d, const float *lf, const f
     F.a_f = (float)a_f;
     F.mu_s = (float)mu_s;
     F.inv_ss = (float)(1.0 / sig_s);
+    // the per-galaxy terms at the widths the rounded reciprocals stand for
+    // (as shear_prepare does for alpha): one set of parameters for the total
+    const double sfe = 1.0 / (double)F.inv_sf, sse = 1.0 / (double)F.inv_ss;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     double *partials = static_cast<double *>(workspace);
     double *dev_out = out_on_host ? partials + (size_t)grid * bs::kShearFullOut : out;
@@ -525,20 +528,20 @@ bs_status bs_shear_loglike_full(const bs_shear_data *d, const float *lf, const f
     // interim uniforms); d/dsigma of the -log sigma terms
     const double ng = bs::shear_weight_total(d);
     const double kPiD = 3.14159265358979323846;
-    add[0] += ng * (std::log(2.0) - std::log(sig_f) - std::log(sig_s) - std::log(2.0 * kPiD) +
+    add[0] += ng * (std::log(2.0) - std::log(sfe) - std::log(sse) - std::log(2.0 * kPiD) +
                     std::log(interim[1] - interim[0]) + std::log(interim[3] - interim[2]));
     for (int i = 0; i < bs::kShearFullOut; ++i) scale[i] = 1.0;
     scale[0] = 0.6931471805599453;   // log2 -> natural log
     scale[3] = alpha_scale;
-    scale[4] = 1.0 / sig_f;
+    scale[4] = 1.0 / sfe;
     add[4] = 0.0;
-    scale[5] = 1.0 / sig_f;
-    add[5] = -ng / sig_f;
+    scale[5] = 1.0 / sfe;
+    add[5] = -ng / sfe;
     add[6] = 0.0;
-    scale[7] = 1.0 / sig_s;
+    scale[7] = 1.0 / sse;
     add[7] = 0.0;
-    scale[8] = 1.0 / sig_s;
-    add[8] = -ng / sig_s;
+    scale[8] = 1.0 / sse;
+    add[8] = -ng / sse;
     const int n_part = d->n_gal > 0 ? grid : 0;
     e = bs::launch_shear_finalize_n(partials, n_part, bs::kShearFullOut, scale, add, dev_out, s);
     if (e != cudaSuccess) return cuda_fail(e, "bs_shear_loglike_full: finalize");
@@ -950,18 +953,28 @@ bs_status shear_prepare(const bs_shear_data *d, double g1, double g2, double alp
     L.g1 = (float)g1;
     L.g2 = (float)g2;
     L.a2 = (float)(1.4426950408889634 / (2.0 * alpha * alpha));
+    if (!(L.a2 > 0.0f) || !std::isfinite(L.a2)) return fail(BS_ERR_INVALID_ARG, "%s: alpha %g out of range", who, alpha);
     L.kappa = d->family == BS_EPRIOR_BA14 ? 4.0f : 2.0f;
     L.c0 = (float)(1.4426950408889634 / (2.0 * (double)d->sigma_e0 * d->sigma_e0));
     L.r2 = d->trunc_r * d->trunc_r;
     L.partials = nullptr;
+    // The per-sample terms see g and 1/(2 alpha^2) rounded to FP32; the
+    // per-galaxy constants are taken at the same rounded values, so that the
+    // total is the likelihood at one (g, alpha), a smooth function of it.
+    // With alpha itself here, the constant and the samples' exponent would
+    // stand for two alphas whose difference jumps with every rounding step
+    // of a2, a shift of about 0.03 nat at 10^6 x 300 samples.
+    const double ge1 = (double)L.g1, ge2 = (double)L.g2, gge = ge1 * ge1 + ge2 * ge2;
+    if (!(gge < 1.0)) return fail(BS_ERR_INVALID_ARG, "%s: |g| >= 1 in FP32", who);
+    const double ae = std::sqrt(1.4426950408889634 / (2.0 * (double)L.a2));
     const double ng = shear_weight_total(d);
     const double kap = d->family == BS_EPRIOR_BA14 ? 4.0 : 2.0;
-    add[0] = ng * (kap * std::log1p(-gg) - log_z_family(d->family, alpha, d->trunc_r) +
+    add[0] = ng * (kap * std::log1p(-gge) - log_z_family(d->family, ae, d->trunc_r) +
                    log_z_ba14(d->sigma_e0) - std::log((double)d->K));
-    add[1] = ng * (-2.0 * kap * g1 / (1.0 - gg));
-    add[2] = ng * (-2.0 * kap * g2 / (1.0 - gg));
-    add[3] = -ng * dlog_z_dalpha(d->family, alpha, d->trunc_r);
-    alpha_scale = 1.0 / (alpha * alpha * alpha);
+    add[1] = ng * (-2.0 * kap * ge1 / (1.0 - gge));
+    add[2] = ng * (-2.0 * kap * ge2 / (1.0 - gge));
+    add[3] = -ng * dlog_z_dalpha(d->family, ae, d->trunc_r);
+    alpha_scale = 1.0 / (ae * ae * ae);
     return BS_OK;
 }
 

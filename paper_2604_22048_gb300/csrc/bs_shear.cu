@@ -79,10 +79,10 @@ __device__ __forceinline__ float2 sub2(float2 a, float2 b)
 
 // Per-launch constants in registers.
 struct ShearConst {
-    float2 ng1, ng2;                 // -g
+    float2 g1, g2, ng1, ng2;         // g, -g
     float2 a2n, an, nan, nk;         // -a2 (log2 units), a = 1/(2 alpha^2), -a, -kappa
     float2 c0;                       // log2(e)/(2 sigma_e0^2)
-    float2 gg, two;                  // |g|^2, 2
+    float2 gg, m2;                   // |g|^2, -2
     float r2;
 };
 
@@ -90,6 +90,8 @@ __device__ __forceinline__ ShearConst shear_const(const ShearLaunch &s)
 {
     ShearConst c;
     const float a = s.a2 * kLn2;
+    c.g1 = f2(s.g1);
+    c.g2 = f2(s.g2);
     c.ng1 = f2(-s.g1);
     c.ng2 = f2(-s.g2);
     c.a2n = f2(-s.a2);
@@ -98,7 +100,7 @@ __device__ __forceinline__ ShearConst shear_const(const ShearLaunch &s)
     c.nk = f2(-s.kappa);
     c.c0 = f2(s.c0);
     c.gg = f2(s.g1 * s.g1 + s.g2 * s.g2);
-    c.two = f2(2.0f);
+    c.m2 = f2(-2.0f);
     c.r2 = s.r2;
     return c;
 }
@@ -112,26 +114,21 @@ __device__ __forceinline__ ShearConst shear_const(const ShearLaunch &s)
 //   dx/dg_i = -2 rU c_i,  c_i = du_i (a Q - kappa) - a n_i,  n = eps' - g,
 //   du_i = eps'_i - g_i |eps'|^2  (-1/2 dU/dg_i);
 // the -2 is applied once per galaxy.  U = |1 - conj(g) eps'|^2 is taken in the
-// Lagrange form 1 - 2 g.eps' + |g|^2 |eps'|^2 (U is near 1: no cancellation).
-// Neither n nor du is formed: |n|^2 = (U - (1 - |eps'|^2)) + (1 - |eps'|^2) |g|^2
-// (the identity behind Q), and with k = a Q - kappa
-//   c_i = eps'_i (k - a) - g_i (|eps'|^2 k - a).
-// |n|^2 is summed in that order so that its rounding errors, about 1e-7 in Q
-// and so in the exponent a2 Q, vary from sample to sample: a constant
-// 1 - |g|^2 rounded once per call would shift every sample's exponent alike,
-// a shift of the total log-likelihood that jumps with g (about 1 nat at
-// 10^6 x 300 samples, measured as a 3% change of the posterior width).
+// Lagrange form 1 - 2 g.eps' + |g|^2 |eps'|^2 (U is near 1: no cancellation);
+// n is formed explicitly (not expanded through |eps'|^2 - 2 g.eps' + |g|^2,
+// which cancels when eps' is near g).
 template <int FAMILY, bool HAS_B>
 __device__ __forceinline__ void pair_terms(const ShearConst &c, float2 e1, float2 e2, float2 bv, float2 &x,
                                            float2 &fw, float2 &ru, float2 &c1, float2 &c2, float2 &q)
 {
     const float2 Ep = fma2(e1, e1, mul2(e2, e2));
-    const float2 nge = fma2(c.ng1, e1, mul2(c.ng2, e2));          // -g.eps'
-    const float2 U = fma2(c.gg, Ep, fma2(c.two, nge, f2(1.0f)));
-    const float2 om = sub2(f2(1.0f), Ep);
-    const float2 Nn = fma2(om, c.gg, sub2(U, om));                 // |eps' - g|^2
+    const float2 ge = fma2(c.g1, e1, mul2(c.g2, e2));            // g.eps'
+    const float2 U = fma2(c.gg, Ep, fma2(c.m2, ge, f2(1.0f)));
+    const float2 n1 = sub2(e1, c.g1), n2 = sub2(e2, c.g2);
+    const float2 Nn = fma2(n1, n1, mul2(n2, n2));
     float2 rU, f;
     if (FAMILY == BS_EPRIOR_TRUNC_GAUSS) {
+        const float2 om = sub2(f2(1.0f), Ep);
         const float2 uo = mul2(U, om);
         const float2 r = make_float2(rcp_ftz(uo.x), rcp_ftz(uo.y));   // 1 / (U (1 - |eps'|^2))
         rU = mul2(r, om);
@@ -148,11 +145,11 @@ __device__ __forceinline__ void pair_terms(const ShearConst &c, float2 e1, float
         if (!(Q.y < c.r2)) xx.y = -INFINITY;
     }
     if (HAS_B) xx = fma2(f2(kLog2e), bv, xx);
-    const float2 k = fma2(c.an, Q, c.nk);                          // a Q - kappa
-    const float2 h = add2(k, c.nan);                               // k - a
-    const float2 j = fma2(Ep, k, c.nan);                           // |eps'|^2 k - a
-    c1 = fma2(c.ng1, j, mul2(e1, h));
-    c2 = fma2(c.ng2, j, mul2(e2, h));
+    const float2 aqk = fma2(c.an, Q, c.nk);
+    const float2 du1 = fma2(c.ng1, Ep, e1);
+    const float2 du2 = fma2(c.ng2, Ep, e2);
+    c1 = fma2(du1, aqk, mul2(c.nan, n1));
+    c2 = fma2(du2, aqk, mul2(c.nan, n2));
     fw = f;
     ru = rU;
     q = Q;
