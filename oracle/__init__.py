@@ -108,7 +108,12 @@ def lib():
         L.or_fit_galaxies.argtypes = [C.c_int, C.c_int, C.c_double, C.POINTER(_Psf), C.c_int, _D, _D,
                                       C.POINTER(_Prior), C.POINTER(_Hmc), C.POINTER(C.c_uint64), _D,
                                       _D, _D, C.POINTER(C.c_uint8), _D, _D, C.POINTER(C.c_int32), _D,
-                                      C.POINTER(C.c_int32), _D, _D, C.c_int]
+                                      C.POINTER(C.c_int32), _D, _D, C.POINTER(C.c_uint8), C.c_int]
+        L.or_hmc_gauss.restype = C.c_int
+        L.or_hmc_gauss.argtypes = [_D, _D, C.POINTER(_Hmc), C.c_uint64, _D, _D, _D, _D, _D, _D]
+        L.or_step_search_gauss.restype = C.c_double
+        L.or_step_search_gauss.argtypes = [_D, _D, _D, _D, C.c_uint64, C.c_uint64, C.c_int, C.c_double]
+        L.or_dual_averaging.argtypes = [C.c_int, _D, C.c_double, C.c_double, _D, _D]
         L.or_ess.restype = C.c_double
         L.or_ess.argtypes = [_D, C.c_int, C.c_int]
         L.or_rhat.restype = C.c_double
@@ -368,7 +373,8 @@ def fit_galaxies(data, sigma, psf, init, *, pixel_scale=0.2, n_warmup=200, n_sam
                accept=np.zeros((n_gal, n_chains, S), dtype=np.uint8),
                accept_rate=np.zeros((n_gal, n_chains)), step_size=np.zeros((n_gal, n_chains)),
                n_div=np.zeros((n_gal, n_chains), dtype=np.int32),
-               inv_mass=np.zeros((n_gal, n_chains, 6)), n_grad=np.zeros((n_gal, n_chains), dtype=np.int32))
+               inv_mass=np.zeros((n_gal, n_chains, 6)), n_grad=np.zeros((n_gal, n_chains), dtype=np.int32),
+               warm_accept=np.zeros((n_gal, n_chains, n_warmup), dtype=np.uint8))
     bad = lib().or_fit_galaxies(
         n_gal, N, pixel_scale, ps, per, _dp(data), _dp(sig), C.byref(pr), C.byref(cfg),
         idarr.ctypes.data_as(C.POINTER(C.c_uint64)) if idarr is not None else None, _dp(init),
@@ -377,9 +383,38 @@ def fit_galaxies(data, sigma, psf, init, *, pixel_scale=0.2, n_warmup=200, n_sam
         out["n_div"].ctypes.data_as(C.POINTER(C.c_int32)), _dp(out["inv_mass"]),
         out["n_grad"].ctypes.data_as(C.POINTER(C.c_int32)),
         _dp(_d(init_step_size) if init_step_size is not None else None),
-        _dp(_d(init_inv_mass) if init_inv_mass is not None else None), int(n_threads))
+        _dp(_d(init_inv_mass) if init_inv_mass is not None else None),
+        out["warm_accept"].ctypes.data_as(C.POINTER(C.c_uint8)), int(n_threads))
     out["bad_init"] = bad
     return out
+
+
+def hmc_gauss(mu, s, init, *, n_warmup=1000, n_samples=500, n_leapfrog=8, target_accept=0.8, jitter=0.0,
+              adapt_mass=False, seed=0, random_steps=True, chain_key0=0):
+    """The sampler on the Gaussian N(mu, diag(s^2)); init: [n_chains, 6]."""
+    init = _d(init)
+    n_chains = init.shape[0]
+    cfg = _Hmc(n_chains, n_warmup, n_samples, n_leapfrog, target_accept, jitter, int(adapt_mass), seed,
+               int(random_steps))
+    out = dict(samples=np.zeros((6, n_chains, n_samples)), accept_rate=np.zeros(n_chains),
+               step_size=np.zeros(n_chains), inv_mass=np.zeros((n_chains, 6)),
+               warm_stat=np.zeros((n_chains, n_warmup)))
+    lib().or_hmc_gauss(_dp(_d(mu)), _dp(_d(s)), C.byref(cfg), chain_key0, _dp(init), _dp(out["samples"]),
+                       _dp(out["accept_rate"]), _dp(out["step_size"]), _dp(out["inv_mass"]),
+                       _dp(out["warm_stat"]))
+    return out
+
+
+def step_search_gauss(mu, s, x, im, seed, key, search, eps0):
+    return lib().or_step_search_gauss(_dp(_d(mu)), _dp(_d(s)), _dp(_d(x)), _dp(_d(im)), seed, key, search, eps0)
+
+
+def dual_averaging(accept_stat, delta, eps0):
+    a = _d(accept_stat)
+    le = np.zeros(len(a))
+    lebar = np.zeros(len(a))
+    lib().or_dual_averaging(len(a), _dp(a), delta, eps0, _dp(le), _dp(lebar))
+    return le, lebar
 
 
 # ---- diagnostics ---------------------------------------------------------------------

@@ -163,14 +163,16 @@ int or_window_schedule(int n_warmup, int adapt_mass, int *starts, int *ends, int
  *   inv_mass: [n_chains][6], n_grad: [n_chains] gradient evaluations inside
  *   the prior support.  Any output pointer may be NULL.
  *   init_eps [n_chains] / init_im [n_chains][6] (may be NULL): resume with
- *   this step size (no initial search) and inverse metric. */
+ *   this step size (no initial search) and inverse metric.
+ *   warm_accept [n_chains][n_warmup] (may be NULL): accept flags of the
+ *   warmup transitions. */
 int or_fit_galaxy(int N, double p, const or_psf *psf, const double *data,
                   const double *w, double sigma, const or_prior *pr,
                   const or_hmc_cfg *cfg, uint64_t galaxy_id, const double *init,
                   double *samples, double *logp, uint8_t *accept,
                   double *accept_rate, double *step_size, int32_t *n_div,
                   double *inv_mass, int32_t *n_grad, const double *init_eps,
-                  const double *init_im);
+                  const double *init_im, uint8_t *warm_accept);
 
 /* Many galaxies of one stamp size, OpenMP-parallel over galaxies (n_threads
  * <= 0: all).  data: [n_gal][N*N], sigma: [n_gal], init: [n_gal][n_chains][6],
@@ -182,7 +184,27 @@ int or_fit_galaxies(int n_gal, int N, double p, const or_psf *psf, int psf_per_g
                     double *samples, double *logp, uint8_t *accept,
                     double *accept_rate, double *step_size, int32_t *n_div,
                     double *inv_mass, int32_t *n_grad, const double *init_eps,
-                    const double *init_im, int n_threads);
+                    const double *init_im, uint8_t *warm_accept, int n_threads);
+
+/* The same sampler (search, dual averaging, windowed metric, transitions) on
+ * the Gaussian N(mu, diag(s^2)) over all of R^6: the textbook target on which
+ * its adaptation has closed-form expectations.  Chain c is keyed
+ * chain_key0 + c; samples [6][n_chains][n_samples], accept_rate, step_size
+ * [n_chains], inv_mass [n_chains][6], warm_stat [n_chains][n_warmup] (the
+ * accept statistic min(1, e^-dH) of each warmup transition). */
+int or_hmc_gauss(const double mu[6], const double s[6], const or_hmc_cfg *cfg,
+                 uint64_t chain_key0, const double *init, double *samples,
+                 double *accept_rate, double *step_size, double *inv_mass,
+                 double *warm_stat);
+/* The step-size search (index `search`, from eps0) at position x with
+ * inverse metric im on that Gaussian target. */
+double or_step_search_gauss(const double mu[6], const double s[6], const double x[6],
+                            const double im[6], uint64_t seed, uint64_t key, int search,
+                            double eps0);
+/* Dual averaging fed the accept statistics a[0..n): log eps and log eps-bar
+ * after each update, from a restart at eps0. */
+void or_dual_averaging(int n, const double *accept_stat, double delta, double eps0,
+                       double *le, double *lebar);
 
 /* ---- diagnostics -------------------------------------------------------- */
 

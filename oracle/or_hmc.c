@@ -81,11 +81,25 @@ typedef struct {
     double sigma;
     const or_prior *pr;
     int *n_eval;            /* evaluations inside the support */
+    /* Gaussian test target N(gmu, diag(gs^2)) on all of R^6 instead of the
+     * galaxy posterior when gmu != NULL (the textbook case the sampler's
+     * adaptation is checked on) */
+    const double *gmu, *gs;
 } target_t;
 
 /* log posterior and gradient; -inf outside the prior support */
 static double target_eval(const target_t *tg, const double th[6], double g[6])
 {
+    if (tg->gmu) {
+        double lp = 0.0;
+        for (int i = 0; i < 6; ++i) {
+            double z = (th[i] - tg->gmu[i]) / tg->gs[i];
+            lp -= 0.5 * z * z;
+            g[i] = -z / tg->gs[i];
+        }
+        ++*tg->n_eval;
+        return lp;
+    }
     double gp[6];
     double lp = or_log_prior(tg->pr, th, gp);
     if (!isfinite(lp)) return -INFINITY;
@@ -95,8 +109,10 @@ static double target_eval(const target_t *tg, const double th[6], double g[6])
     return ll + lp;
 }
 
-static int in_support(const or_prior *pr, const double th[6])
+static int in_support(const target_t *tg, const double th[6])
 {
+    if (tg->gmu) return 1;
+    const or_prior *pr = tg->pr;
     double E = th[2] * th[2] + th[3] * th[3];
     return th[0] > pr->lf_lo && th[0] < pr->lf_hi && th[1] > pr->ls_lo && th[1] < pr->ls_hi && E < 1.0;
 }
@@ -156,7 +172,7 @@ static int trajectory(const target_t *tg, const chain_t *ch, double eps, int n,
     for (int l = 0; l < n; ++l) {
         for (int i = 0; i < 6; ++i) pm[i] += 0.5 * eps * g[i];
         for (int i = 0; i < 6; ++i) th[i] += eps * ch->im[i] * pm[i];
-        if (!in_support(tg->pr, th)) return 0;
+        if (!in_support(tg, th)) return 0;
         *lp = target_eval(tg, th, g);
         if (!isfinite(*lp)) return 0;
         for (int i = 0; i < 6; ++i) pm[i] += 0.5 * eps * g[i];
@@ -232,87 +248,177 @@ static double transition(const target_t *tg, chain_t *ch, const or_hmc_cfg *cfg,
     return a;
 }
 
+/* Outputs of one chain; any pointer may be NULL.  samples: parameter i of
+ * draw s at samples[i * sstride + s]; logp, accept: [n_samples];
+ * warm_accept / warm_stat: [n_warmup] accept flags / accept statistics of
+ * the warmup transitions. */
+typedef struct {
+    double *samples;
+    size_t sstride;
+    double *logp;
+    uint8_t *accept, *warm_accept;
+    double *warm_stat;
+    double *accept_rate, *step_size, *inv_mass;
+    int32_t *n_div, *n_grad;
+} chain_out_t;
+
+/* One chain: initial search, warmup (dual averaging, windowed metric),
+ * sampling.  Returns 1 if the start has no finite log density. */
+static int run_chain(const target_t *tg, const or_hmc_cfg *cfg, const int *starts,
+                     const int *ends, int nw, uint64_t key, const double init[6],
+                     const double *init_eps, const double *init_im, const chain_out_t *o)
+{
+    int S = cfg->n_samples, W = cfg->n_warmup;
+    chain_t ch;
+    int status = 0;
+    *tg->n_eval = 0;
+    memcpy(ch.th, init, sizeof ch.th);
+    for (int i = 0; i < 6; ++i) ch.im[i] = init_im ? init_im[i] : 1.0;
+    ch.lp = target_eval(tg, ch.th, ch.g);
+    if (!isfinite(ch.lp)) status = 1;
+    if (init_eps)       /* resume an adapted chain: no search */
+        ch.eps = *init_eps;
+    else
+        ch.eps = step_search(tg, &ch, cfg->seed, key, 0, 1.0);
+    da_restart(&ch);
+
+    int wi = 0, wn = 0;
+    double wmean[6] = {0}, wm2[6] = {0};
+    for (int it = 0; it < W; ++it) {
+        int acc, div;
+        double a = transition(tg, &ch, cfg, key, it, &acc, &div);
+        if (o->warm_accept) o->warm_accept[it] = (uint8_t)acc;
+        if (o->warm_stat) o->warm_stat[it] = a;
+        da_update(&ch, a, cfg->target_accept);
+        if (wi < nw && it >= starts[wi] && it < ends[wi]) {
+            ++wn;
+            for (int i = 0; i < 6; ++i) {
+                double d = ch.th[i] - wmean[i];
+                wmean[i] += d / wn;
+                wm2[i] += d * (ch.th[i] - wmean[i]);
+            }
+        }
+        if (wi < nw && it == ends[wi] - 1) {
+            double n = (double)wn;
+            for (int i = 0; i < 6; ++i) {
+                double var = wm2[i] / (n - 1.0);
+                ch.im[i] = (n / (n + 5.0)) * var + 1e-3 * (5.0 / (n + 5.0));
+                wmean[i] = 0.0;
+                wm2[i] = 0.0;
+            }
+            wn = 0;
+            ch.eps = step_search(tg, &ch, cfg->seed, key, wi + 1, ch.eps);
+            da_restart(&ch);
+            ++wi;
+        }
+    }
+    if (W > 0) ch.eps = exp(ch.lebar);
+
+    double asum = 0.0;
+    int ndiv = 0;
+    for (int s = 0; s < S; ++s) {
+        int acc, div;
+        double a = transition(tg, &ch, cfg, key, W + s, &acc, &div);
+        asum += a;
+        ndiv += div;
+        if (o->samples)
+            for (int i = 0; i < 6; ++i) o->samples[(size_t)i * o->sstride + s] = ch.th[i];
+        if (o->logp) o->logp[s] = ch.lp;
+        if (o->accept) o->accept[s] = (uint8_t)acc;
+    }
+    if (o->accept_rate) *o->accept_rate = S > 0 ? asum / S : 0.0;
+    if (o->step_size) *o->step_size = ch.eps;
+    if (o->n_div) *o->n_div = ndiv;
+    if (o->inv_mass) memcpy(o->inv_mass, ch.im, sizeof ch.im);
+    if (o->n_grad) *o->n_grad = *tg->n_eval;
+    return status;
+}
+
 int or_fit_galaxy(int N, double p, const or_psf *psf, const double *data,
                   const double *w, double sigma, const or_prior *pr,
                   const or_hmc_cfg *cfg, uint64_t galaxy_id, const double *init,
                   double *samples, double *logp, uint8_t *accept,
                   double *accept_rate, double *step_size, int32_t *n_div,
                   double *inv_mass, int32_t *n_grad, const double *init_eps,
-                  const double *init_im)
+                  const double *init_im, uint8_t *warm_accept)
 {
     int C = cfg->n_chains, S = cfg->n_samples, W = cfg->n_warmup;
     double *T = malloc(sizeof(double) * (size_t)N * N);
     or_transfer_table(N, p, psf, T);
     int n_eval = 0;
-    target_t tg = {N, p, T, data, w, sigma, pr, &n_eval};
+    target_t tg = {N, p, T, data, w, sigma, pr, &n_eval, NULL, NULL};
     int starts[64], ends[64];
     int nw = or_window_schedule(W, cfg->adapt_mass, starts, ends, 64);
     int status = 0;
 
     for (int c = 0; c < C; ++c) {
         uint64_t key = galaxy_id * (uint64_t)C + (uint64_t)c;
-        chain_t ch;
-        n_eval = 0;
-        memcpy(ch.th, init + 6 * c, sizeof ch.th);
-        for (int i = 0; i < 6; ++i) ch.im[i] = init_im ? init_im[6 * c + i] : 1.0;
-        ch.lp = target_eval(&tg, ch.th, ch.g);
-        if (!isfinite(ch.lp)) { status = 1; }
-        if (init_eps)       /* resume an adapted chain: no search */
-            ch.eps = init_eps[c];
-        else
-            ch.eps = step_search(&tg, &ch, cfg->seed, key, 0, 1.0);
-        da_restart(&ch);
-
-        int wi = 0, wn = 0;
-        double wmean[6] = {0}, wm2[6] = {0};
-        for (int it = 0; it < W; ++it) {
-            int acc, div;
-            double a = transition(&tg, &ch, cfg, key, it, &acc, &div);
-            da_update(&ch, a, cfg->target_accept);
-            if (wi < nw && it >= starts[wi] && it < ends[wi]) {
-                ++wn;
-                for (int i = 0; i < 6; ++i) {
-                    double d = ch.th[i] - wmean[i];
-                    wmean[i] += d / wn;
-                    wm2[i] += d * (ch.th[i] - wmean[i]);
-                }
-            }
-            if (wi < nw && it == ends[wi] - 1) {
-                double n = (double)wn;
-                for (int i = 0; i < 6; ++i) {
-                    double var = wm2[i] / (n - 1.0);
-                    ch.im[i] = (n / (n + 5.0)) * var + 1e-3 * (5.0 / (n + 5.0));
-                    wmean[i] = 0.0;
-                    wm2[i] = 0.0;
-                }
-                wn = 0;
-                ch.eps = step_search(&tg, &ch, cfg->seed, key, wi + 1, ch.eps);
-                da_restart(&ch);
-                ++wi;
-            }
-        }
-        if (W > 0) ch.eps = exp(ch.lebar);
-
-        double asum = 0.0;
-        int ndiv = 0;
-        for (int s = 0; s < S; ++s) {
-            int acc, div;
-            double a = transition(&tg, &ch, cfg, key, W + s, &acc, &div);
-            asum += a;
-            ndiv += div;
-            if (samples)
-                for (int i = 0; i < 6; ++i) samples[((size_t)i * C + c) * S + s] = ch.th[i];
-            if (logp) logp[(size_t)c * S + s] = ch.lp;
-            if (accept) accept[(size_t)c * S + s] = (uint8_t)acc;
-        }
-        if (accept_rate) accept_rate[c] = S > 0 ? asum / S : 0.0;
-        if (step_size) step_size[c] = ch.eps;
-        if (n_div) n_div[c] = ndiv;
-        if (inv_mass) memcpy(inv_mass + 6 * c, ch.im, sizeof ch.im);
-        if (n_grad) n_grad[c] = n_eval;
+        chain_out_t o = {
+            samples ? samples + (size_t)c * S : NULL, (size_t)C * S,
+            logp ? logp + (size_t)c * S : NULL,
+            accept ? accept + (size_t)c * S : NULL,
+            warm_accept ? warm_accept + (size_t)c * W : NULL, NULL,
+            accept_rate ? accept_rate + c : NULL,
+            step_size ? step_size + c : NULL,
+            inv_mass ? inv_mass + 6 * c : NULL,
+            n_div ? n_div + c : NULL,
+            n_grad ? n_grad + c : NULL};
+        if (run_chain(&tg, cfg, starts, ends, nw, key, init + 6 * c,
+                      init_eps ? init_eps + c : NULL, init_im ? init_im + 6 * c : NULL, &o))
+            status = 1;
     }
     free(T);
     return status;
+}
+
+int or_hmc_gauss(const double mu[6], const double s[6], const or_hmc_cfg *cfg,
+                 uint64_t chain_key0, const double *init, double *samples,
+                 double *accept_rate, double *step_size, double *inv_mass,
+                 double *warm_stat)
+{
+    int C = cfg->n_chains, S = cfg->n_samples, W = cfg->n_warmup;
+    int starts[64], ends[64];
+    int nw = or_window_schedule(W, cfg->adapt_mass, starts, ends, 64);
+    int status = 0;
+    for (int c = 0; c < C; ++c) {
+        int n_eval = 0;
+        target_t tg = {0, 0.0, NULL, NULL, NULL, 0.0, NULL, &n_eval, mu, s};
+        chain_out_t o = {
+            samples ? samples + (size_t)c * S : NULL, (size_t)C * S, NULL, NULL, NULL,
+            warm_stat ? warm_stat + (size_t)c * W : NULL,
+            accept_rate ? accept_rate + c : NULL,
+            step_size ? step_size + c : NULL,
+            inv_mass ? inv_mass + 6 * c : NULL, NULL, NULL};
+        status |= run_chain(&tg, cfg, starts, ends, nw, chain_key0 + (uint64_t)c, init + 6 * c,
+                            NULL, NULL, &o);
+    }
+    return status;
+}
+
+double or_step_search_gauss(const double mu[6], const double s[6], const double x[6],
+                            const double im[6], uint64_t seed, uint64_t key, int search,
+                            double eps0)
+{
+    int n_eval = 0;
+    target_t tg = {0, 0.0, NULL, NULL, NULL, 0.0, NULL, &n_eval, mu, s};
+    chain_t ch;
+    memcpy(ch.th, x, sizeof ch.th);
+    memcpy(ch.im, im, sizeof ch.im);
+    ch.lp = target_eval(&tg, ch.th, ch.g);
+    return step_search(&tg, &ch, seed, key, search, eps0);
+}
+
+void or_dual_averaging(int n, const double *accept_stat, double delta, double eps0,
+                       double *le, double *lebar)
+{
+    chain_t ch;
+    ch.eps = eps0;
+    da_restart(&ch);
+    for (int m = 0; m < n; ++m) {
+        da_update(&ch, accept_stat[m], delta);
+        le[m] = log(ch.eps);
+        lebar[m] = ch.lebar;
+    }
 }
 
 int or_fit_galaxies(int n_gal, int N, double p, const or_psf *psf, int psf_per_gal,
@@ -321,9 +427,9 @@ int or_fit_galaxies(int n_gal, int N, double p, const or_psf *psf, int psf_per_g
                     double *samples, double *logp, uint8_t *accept,
                     double *accept_rate, double *step_size, int32_t *n_div,
                     double *inv_mass, int32_t *n_grad, const double *init_eps,
-                    const double *init_im, int n_threads)
+                    const double *init_im, uint8_t *warm_accept, int n_threads)
 {
-    int C = cfg->n_chains, S = cfg->n_samples;
+    int C = cfg->n_chains, S = cfg->n_samples, W = cfg->n_warmup;
     size_t NN = (size_t)N * N;
     int bad = 0;
 #ifdef _OPENMP
@@ -344,7 +450,8 @@ int or_fit_galaxies(int n_gal, int N, double p, const or_psf *psf, int psf_per_g
                                inv_mass ? inv_mass + (size_t)n * C * 6 : NULL,
                                n_grad ? n_grad + (size_t)n * C : NULL,
                                init_eps ? init_eps + (size_t)n * C : NULL,
-                               init_im ? init_im + (size_t)n * C * 6 : NULL);
+                               init_im ? init_im + (size_t)n * C * 6 : NULL,
+                               warm_accept ? warm_accept + (size_t)n * C * W : NULL);
         bad += st != 0;
         if (smp) {
             /* [6][C][S] -> [6][n_gal][C][S] */

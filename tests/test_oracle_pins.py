@@ -340,6 +340,128 @@ def test_ess_iid_and_ar1():
     assert O.rhat(z) > 1.1
 
 
+def test_rhat_matches_its_large_sample_limit_with_planted_chain_shifts():
+    # Gelman & Rubin (1992): with within-chain variance v and chain means
+    # spread with sample variance b, var+ -> v + b and R-hat -> sqrt(1 + b/v)
+    # as the chains grow.
+    rng = np.random.default_rng(12)
+    C, S, v = 4, 40000, 2.0
+    for shifts in ([-0.6, -0.2, 0.2, 0.6], [0.0, 0.0, 0.0, 1.5], [0.3, -0.1, 0.25, -0.4]):
+        sh = np.asarray(shifts)
+        x = rng.normal(0.0, np.sqrt(v), (C, S)) + sh[:, None]
+        limit = np.sqrt(1.0 + sh.var(ddof=1) / v)
+        assert abs(O.rhat(x) / limit - 1) < 0.01, (shifts, O.rhat(x), limit)
+
+
+# ---- warmup adaptation (Sec. 3.3, the warmup footnote: dual averaging of the
+# step size, Hoffman & Gelman 2014 Sec. 3.2 with gamma 0.05, t0 10, kappa 0.75,
+# mu = log(10 eps); Stan's step-size search and windowed diagonal metric)
+
+_GMU = np.array([0.3, -1.0, 0.0, 2.0, 0.5, -0.2])
+_GS = np.array([0.05, 0.3, 1.0, 2.0, 0.5, 1.5])
+
+
+def test_dual_averaging_equals_the_averaged_form_of_the_iterates():
+    # Hoffman & Gelman write the iterate with the running mean of the
+    # statistics: x_t = mu - sqrt(t)/gamma * (1/(t + t0)) sum_{i<=t} (delta - a_i),
+    # and x-bar_t as the average sum_j x_j eta_j prod_{i>j} (1 - eta_i),
+    # eta_j = j^-kappa; the oracle updates both recursively.
+    rng = np.random.default_rng(4)
+    a = rng.uniform(0.0, 1.0, 300)
+    delta, eps0 = 0.8, 0.37
+    le, lebar = O.dual_averaging(a, delta, eps0)
+    t = np.arange(1, len(a) + 1, dtype=np.float64)
+    x = np.log(10 * eps0) - np.sqrt(t) / 0.05 * np.cumsum(delta - a) / (t + 10.0)
+    assert np.abs(le - x).max() < 1e-9
+    eta = t ** -0.75
+    for M in (1, 2, 7, 60, 300):
+        w = np.array([eta[j] * np.prod(1.0 - eta[j + 1:M]) for j in range(M)])
+        assert abs(w.sum() - 1.0) < 1e-12
+        assert abs(lebar[M - 1] - (w * x[:M]).sum()) < 1e-9, M
+    # statistics equal to the target leave both at mu = log(10 eps0)
+    le, lebar = O.dual_averaging(np.full(40, 0.65), 0.65, 0.2)
+    assert np.abs(le - np.log(2.0)).max() < 1e-14 and np.abs(lebar - np.log(2.0)).max() < 1e-14
+
+
+def _box_muller6(u):
+    z = np.empty(6)
+    for j in range(3):
+        r = np.sqrt(-2.0 * np.log(u[2 * j]))
+        z[2 * j], z[2 * j + 1] = r * np.cos(2 * np.pi * u[2 * j + 1]), r * np.sin(2 * np.pi * u[2 * j + 1])
+    return z
+
+
+def _gauss_one_step_logacc(x, im, z, eps):
+    """log acceptance H0 - H1 of one leapfrog step on N(_GMU, diag(_GS^2))
+    with inverse metric im and momentum z / sqrt(im)."""
+    H = lambda q, p: 0.5 * (((q - _GMU) / _GS) ** 2).sum() + 0.5 * (im * p * p).sum()
+    grad = lambda q: -(q - _GMU) / _GS ** 2
+    p = z / np.sqrt(im)
+    H0 = H(x, p)
+    p = p + 0.5 * eps * grad(x)
+    q = x + eps * im * p
+    p = p + 0.5 * eps * grad(q)
+    return H0 - H(q, p)
+
+
+@pytest.mark.parametrize("eps0,search", [(1e-3, 0), (1.0, 0), (30.0, 2), (0.05, 1)])
+def test_step_search_stops_at_the_first_crossing_of_log_0p8(eps0, search):
+    # Trial t of search s draws its momentum from Philox counter (s, 1, t); the
+    # step doubles while the one-step log acceptance stays above ln 0.8 (or
+    # halves while it stays at or below), and the search returns the first
+    # step on the other side.  The acceptance here is the exact one of the
+    # Gaussian target, computed independently.
+    rng = np.random.default_rng(int(eps0 * 1000) + search)
+    seed, key = 22048, 17
+    for _ in range(4):
+        x = _GMU + _GS * rng.normal(size=6)
+        im = _GS ** 2 * rng.uniform(0.5, 2.0, 6)
+        eps = O.step_search_gauss(_GMU, _GS, x, im, seed, key, search, eps0)
+        t_end = int(round(np.log2(eps / eps0)))
+        assert abs(eps / (eps0 * 2.0 ** t_end) - 1) < 1e-12
+        thr = np.log(0.8)
+        acc = lambda t, e: _gauss_one_step_logacc(x, im, _box_muller6(O.uniforms8(seed, key, search, 1, t)), e)
+        up = acc(0, eps0) > thr
+        assert (t_end > 0) == up and t_end != 0
+        for t in range(abs(t_end)):          # every earlier trial continued the search
+            e = eps0 * 2.0 ** (t if up else -t)
+            assert (acc(t, e) > thr) == up, (t, e)
+        assert (acc(abs(t_end), eps) > thr) != up   # and this one ended it
+
+
+def test_dual_averaging_drives_the_mean_acceptance_to_the_target():
+    # Dual averaging solves E[a] = delta for the statistic the chain sees, so
+    # the mean statistic over the second half of a long warmup (no metric
+    # windows) is delta; a larger delta needs a smaller step.  The warmup ends
+    # on eps-bar: the returned step is exp of the averaged iterate of the
+    # statistics, restarted at the initial search.
+    C, W = 8, 1000
+    init = _GMU + _GS * np.random.default_rng(0).normal(size=(C, 6))
+    med = []
+    for delta in (0.6, 0.8, 0.95):
+        r = O.hmc_gauss(_GMU, _GS, init, n_warmup=W, n_samples=1, n_leapfrog=8, target_accept=delta,
+                        adapt_mass=False, seed=5, chain_key0=100)
+        a = r["warm_stat"]
+        assert np.abs(a[:, W // 2:].mean(axis=1) - delta).max() < 0.01, (delta, a[:, W // 2:].mean(axis=1))
+        for c in range(C):
+            eps0 = O.step_search_gauss(_GMU, _GS, init[c], np.ones(6), 5, 100 + c, 0, 1.0)
+            _, lebar = O.dual_averaging(a[c], delta, eps0)
+            assert abs(r["step_size"][c] / np.exp(lebar[-1]) - 1) < 1e-12
+        med.append(np.median(r["step_size"]))
+    assert med[0] > med[1] > med[2], med
+
+
+def test_windowed_metric_adapts_to_the_target_variances():
+    # Stan's windows estimate the diagonal inverse metric as the regularised
+    # variance of the window's draws, so it approaches diag(s^2) of the target.
+    C = 8
+    init = _GMU + _GS * np.random.default_rng(1).normal(size=(C, 6))
+    r = O.hmc_gauss(_GMU, _GS, init, n_warmup=1000, n_samples=1, n_leapfrog=8, target_accept=0.8,
+                    adapt_mass=True, seed=9)
+    ratio = (r["inv_mass"] / _GS ** 2).mean(axis=0)
+    assert np.abs(ratio - 1).max() < 0.15, ratio
+
+
 @pytest.mark.slow
 def test_hmc_matches_laplace_on_bright_galaxy():
     """High S/N: the posterior is close to a Gaussian with covariance (-H)^-1 at
