@@ -236,6 +236,14 @@ typedef struct {
     int32_t *n_grad;       /* [n_gal][n_chains]: log-posterior gradient
                               evaluations the chain made (warmup, searches and
                               sampling) */
+    /* Warmup trace (diagnostics; each may be NULL), [n_gal][n_chains][n_warmup]:
+     * per warmup transition its accept flag, its accept statistic
+     * min(1, e^-dH) (0 when divergent) and the step size it started from
+     * (before any jitter); with them the step-size adaptation can be replayed
+     * exactly. */
+    uint8_t *warmup_accepted;
+    float *warmup_accept_stat;
+    float *warmup_step_size;
 } bs_fit_out;
 
 /* Bytes of device workspace bs_fit_galaxies needs (a work-queue counter). */
@@ -548,11 +556,15 @@ bs_status bs_shear_loglike_full(const bs_shear_data *data, const float *lf, cons
  * budget, real-time loops that must not allocate).  The paper has no
  * counterpart: this is a deployment variant of bs_shear_loglike.
  *   out: device double [4] = {value, d/dg1, d/dg2, d/dalpha}.
- * The scratch (one FP64 partial per reduction block, at most 2048 blocks,
- * 64 KB) is a static device array of the library, held on every GPU that
- * loads it until exit.  The first call on a device looks up the array's
- * device address; make it before any stream capture.  All calls share the
- * array, so calls that overlap on the GPU race.  Returns BS_ERR_UNSUPPORTED
+ * The scratch (four FP64 partials -- value, d/dg1, d/dg2 and the weighted
+ * sum of |eps|^2 -- per reduction block, at most 2048 blocks, 64 KB) is a
+ * static device array of the library, held on every GPU that loads it until
+ * exit.  The first call on a device looks up the array's device address and
+ * keeps it for the life of the process; make that call before any stream
+ * capture, and do not call this entry point after a cudaDeviceReset of that
+ * device (the reset unloads the library's device data, and the kept address
+ * would then be stale).  All calls share the array, so calls that overlap on
+ * the GPU race.  Returns BS_ERR_UNSUPPORTED
  * when the device's reduction grid needs more than 2048 partial slots; the
  * number of galaxies and samples is not limited.  Calls no allocating
  * routine. */
@@ -624,6 +636,62 @@ typedef struct {
 bs_status bs_shear_sample(const bs_shear_data *data, const bs_shear_sample_cfg *cfg, double *samples,
                           double *accept_rate, double *step_size, int32_t *n_evals, void *workspace,
                           size_t workspace_bytes, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Multiplicative and additive shear bias (Sec. 3.4)                        */
+/* ------------------------------------------------------------------------ */
+
+/* An estimator of the shear of one dataset whose galaxies carry the weights
+ * `weight` (host float [n_gal]: the counts of a bootstrap resample, times the
+ * base weights if any; NULL: the original sample, every galaxy once) summing
+ * to weight_sum.  Writes g[2] = (g1, g2); returns 0 on success, anything else
+ * ends the bias call with BS_ERR_INVALID_ARG. */
+typedef int32_t (*bs_g_estimator_fn)(const float *weight, double weight_sum, double *g, void *user);
+
+typedef struct {
+    double g_abs;             /* |g| of the applied shear: the plus dataset is
+                                 sheared by g = (g_abs, 0), the minus one by -g */
+    int32_t n_boot;           /* bootstrap resamples (>= 0; below 2 the
+                                 standard deviations are NaN) */
+    uint64_t seed;            /* resample r draws galaxy floor(n_gal x / 2^64)
+                                 at draw j, x = word (j mod 4) of the
+                                 Philox4x64-10 block with key (seed, r) and
+                                 counter (floor(j / 4), 0, 1, 0) */
+    const float *base_weight; /* host [n_gal] or NULL: multiplies the weights
+                                 of the original sample and of every resample
+                                 (0 leaves a galaxy out of both datasets) */
+    double *m_boot, *c_boot;  /* host [n_boot] or NULL: m and c per resample */
+} bs_bias_cfg;
+
+/* Shape-noise cancellation (Sec. 3.4): for two datasets that share their
+ * galaxies and noise and are sheared by +g and -g,
+ *     m = (g+_1 - g-_1) / (2 |g|) - 1,   c = (g+_2 + g-_2) / 2
+ * from the original sample, with bootstrap standard deviations (n_boot - 1
+ * in the denominator) over resamples that draw the n_gal galaxies with
+ * replacement and apply the same counts to both datasets.
+ *   out host double [4] = {m, c, sd(m), sd(c)}.
+ * bs_shear_bias_custom takes the two estimators from the caller (any
+ * estimator of g from weighted galaxies); it runs on the host only. */
+bs_status bs_shear_bias_custom(int64_t n_gal, bs_g_estimator_fn est_plus, void *user_plus,
+                               bs_g_estimator_fn est_minus, void *user_minus, const bs_bias_cfg *cfg,
+                               double *out);
+
+enum { BS_BIAS_QUADRATURE = 0, BS_BIAS_HMC = 1 };
+
+/* The same with the library's estimators on two device datasets of equal
+ * n_gal: the posterior mean of g by bs_shear_estimate (method
+ * BS_BIAS_QUADRATURE, configuration est) or the mean of the g draws of
+ * bs_shear_sample (BS_BIAS_HMC, configuration smp; each evaluation reruns
+ * the sampler with the same seed).  Each evaluation's weights are copied to
+ * weight_dev (device float [n_gal], caller-owned; required when n_boot > 0
+ * or base_weight is set) and passed as both datasets' gal_weight, whose own
+ * gal_weight is ignored.  Workspace: bs_shear_workspace_bytes of the
+ * datasets.  Synchronises `stream`.  Errors: BS_ERR_INVALID_ARG (sizes,
+ * method, g_abs, negative or non-finite base weights) and those of the
+ * estimate or sampler calls. */
+bs_status bs_shear_bias(const bs_shear_data *plus, const bs_shear_data *minus, int32_t method,
+                        const bs_estimate_cfg *est, const bs_shear_sample_cfg *smp, const bs_bias_cfg *cfg,
+                        float *weight_dev, double *out, void *workspace, size_t workspace_bytes, void *stream);
 
 #ifdef __cplusplus
 }

@@ -108,7 +108,7 @@ def lib():
         L.or_fit_galaxies.argtypes = [C.c_int, C.c_int, C.c_double, C.POINTER(_Psf), C.c_int, _D, _D,
                                       C.POINTER(_Prior), C.POINTER(_Hmc), C.POINTER(C.c_uint64), _D,
                                       _D, _D, C.POINTER(C.c_uint8), _D, _D, C.POINTER(C.c_int32), _D,
-                                      C.POINTER(C.c_int32), _D, _D, C.POINTER(C.c_uint8), C.c_int]
+                                      C.POINTER(C.c_int32), _D, _D, C.POINTER(C.c_uint8), _D, _D, C.c_int]
         L.or_hmc_gauss.restype = C.c_int
         L.or_hmc_gauss.argtypes = [_D, _D, C.POINTER(_Hmc), C.c_uint64, _D, _D, _D, _D, _D, _D]
         L.or_step_search_gauss.restype = C.c_double
@@ -374,7 +374,8 @@ def fit_galaxies(data, sigma, psf, init, *, pixel_scale=0.2, n_warmup=200, n_sam
                accept_rate=np.zeros((n_gal, n_chains)), step_size=np.zeros((n_gal, n_chains)),
                n_div=np.zeros((n_gal, n_chains), dtype=np.int32),
                inv_mass=np.zeros((n_gal, n_chains, 6)), n_grad=np.zeros((n_gal, n_chains), dtype=np.int32),
-               warm_accept=np.zeros((n_gal, n_chains, n_warmup), dtype=np.uint8))
+               warm_accept=np.zeros((n_gal, n_chains, n_warmup), dtype=np.uint8),
+               warm_stat=np.zeros((n_gal, n_chains, n_warmup)), warm_step=np.zeros((n_gal, n_chains, n_warmup)))
     bad = lib().or_fit_galaxies(
         n_gal, N, pixel_scale, ps, per, _dp(data), _dp(sig), C.byref(pr), C.byref(cfg),
         idarr.ctypes.data_as(C.POINTER(C.c_uint64)) if idarr is not None else None, _dp(init),
@@ -384,7 +385,8 @@ def fit_galaxies(data, sigma, psf, init, *, pixel_scale=0.2, n_warmup=200, n_sam
         out["n_grad"].ctypes.data_as(C.POINTER(C.c_int32)),
         _dp(_d(init_step_size) if init_step_size is not None else None),
         _dp(_d(init_inv_mass) if init_inv_mass is not None else None),
-        out["warm_accept"].ctypes.data_as(C.POINTER(C.c_uint8)), int(n_threads))
+        out["warm_accept"].ctypes.data_as(C.POINTER(C.c_uint8)), _dp(out["warm_stat"]), _dp(out["warm_step"]),
+        int(n_threads))
     out["bad_init"] = bad
     return out
 

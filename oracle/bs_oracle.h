@@ -164,15 +164,17 @@ int or_window_schedule(int n_warmup, int adapt_mass, int *starts, int *ends, int
  *   the prior support.  Any output pointer may be NULL.
  *   init_eps [n_chains] / init_im [n_chains][6] (may be NULL): resume with
  *   this step size (no initial search) and inverse metric.
- *   warm_accept [n_chains][n_warmup] (may be NULL): accept flags of the
- *   warmup transitions. */
+ *   warm_accept / warm_stat / warm_step [n_chains][n_warmup] (each may be
+ *   NULL): accept flags, accept statistics and starting step sizes (before
+ *   jitter) of the warmup transitions. */
 int or_fit_galaxy(int N, double p, const or_psf *psf, const double *data,
                   const double *w, double sigma, const or_prior *pr,
                   const or_hmc_cfg *cfg, uint64_t galaxy_id, const double *init,
                   double *samples, double *logp, uint8_t *accept,
                   double *accept_rate, double *step_size, int32_t *n_div,
                   double *inv_mass, int32_t *n_grad, const double *init_eps,
-                  const double *init_im, uint8_t *warm_accept);
+                  const double *init_im, uint8_t *warm_accept, double *warm_stat,
+                  double *warm_step);
 
 /* Many galaxies of one stamp size, OpenMP-parallel over galaxies (n_threads
  * <= 0: all).  data: [n_gal][N*N], sigma: [n_gal], init: [n_gal][n_chains][6],
@@ -184,7 +186,8 @@ int or_fit_galaxies(int n_gal, int N, double p, const or_psf *psf, int psf_per_g
                     double *samples, double *logp, uint8_t *accept,
                     double *accept_rate, double *step_size, int32_t *n_div,
                     double *inv_mass, int32_t *n_grad, const double *init_eps,
-                    const double *init_im, uint8_t *warm_accept, int n_threads);
+                    const double *init_im, uint8_t *warm_accept, double *warm_stat,
+                    double *warm_step, int n_threads);
 
 /* The same sampler (search, dual averaging, windowed metric, transitions) on
  * the Gaussian N(mu, diag(s^2)) over all of R^6: the textbook target on which

@@ -250,14 +250,15 @@ static double transition(const target_t *tg, chain_t *ch, const or_hmc_cfg *cfg,
 
 /* Outputs of one chain; any pointer may be NULL.  samples: parameter i of
  * draw s at samples[i * sstride + s]; logp, accept: [n_samples];
- * warm_accept / warm_stat: [n_warmup] accept flags / accept statistics of
- * the warmup transitions. */
+ * warm_accept / warm_stat / warm_step: [n_warmup] accept flags, accept
+ * statistics and starting step sizes (before jitter) of the warmup
+ * transitions. */
 typedef struct {
     double *samples;
     size_t sstride;
     double *logp;
     uint8_t *accept, *warm_accept;
-    double *warm_stat;
+    double *warm_stat, *warm_step;
     double *accept_rate, *step_size, *inv_mass;
     int32_t *n_div, *n_grad;
 } chain_out_t;
@@ -286,6 +287,7 @@ static int run_chain(const target_t *tg, const or_hmc_cfg *cfg, const int *start
     double wmean[6] = {0}, wm2[6] = {0};
     for (int it = 0; it < W; ++it) {
         int acc, div;
+        if (o->warm_step) o->warm_step[it] = ch.eps;
         double a = transition(tg, &ch, cfg, key, it, &acc, &div);
         if (o->warm_accept) o->warm_accept[it] = (uint8_t)acc;
         if (o->warm_stat) o->warm_stat[it] = a;
@@ -340,7 +342,8 @@ int or_fit_galaxy(int N, double p, const or_psf *psf, const double *data,
                   double *samples, double *logp, uint8_t *accept,
                   double *accept_rate, double *step_size, int32_t *n_div,
                   double *inv_mass, int32_t *n_grad, const double *init_eps,
-                  const double *init_im, uint8_t *warm_accept)
+                  const double *init_im, uint8_t *warm_accept, double *warm_stat,
+                  double *warm_step)
 {
     int C = cfg->n_chains, S = cfg->n_samples, W = cfg->n_warmup;
     double *T = malloc(sizeof(double) * (size_t)N * N);
@@ -357,7 +360,9 @@ int or_fit_galaxy(int N, double p, const or_psf *psf, const double *data,
             samples ? samples + (size_t)c * S : NULL, (size_t)C * S,
             logp ? logp + (size_t)c * S : NULL,
             accept ? accept + (size_t)c * S : NULL,
-            warm_accept ? warm_accept + (size_t)c * W : NULL, NULL,
+            warm_accept ? warm_accept + (size_t)c * W : NULL,
+            warm_stat ? warm_stat + (size_t)c * W : NULL,
+            warm_step ? warm_step + (size_t)c * W : NULL,
             accept_rate ? accept_rate + c : NULL,
             step_size ? step_size + c : NULL,
             inv_mass ? inv_mass + 6 * c : NULL,
@@ -385,7 +390,7 @@ int or_hmc_gauss(const double mu[6], const double s[6], const or_hmc_cfg *cfg,
         target_t tg = {0, 0.0, NULL, NULL, NULL, 0.0, NULL, &n_eval, mu, s};
         chain_out_t o = {
             samples ? samples + (size_t)c * S : NULL, (size_t)C * S, NULL, NULL, NULL,
-            warm_stat ? warm_stat + (size_t)c * W : NULL,
+            warm_stat ? warm_stat + (size_t)c * W : NULL, NULL,
             accept_rate ? accept_rate + c : NULL,
             step_size ? step_size + c : NULL,
             inv_mass ? inv_mass + 6 * c : NULL, NULL, NULL};
@@ -427,7 +432,8 @@ int or_fit_galaxies(int n_gal, int N, double p, const or_psf *psf, int psf_per_g
                     double *samples, double *logp, uint8_t *accept,
                     double *accept_rate, double *step_size, int32_t *n_div,
                     double *inv_mass, int32_t *n_grad, const double *init_eps,
-                    const double *init_im, uint8_t *warm_accept, int n_threads)
+                    const double *init_im, uint8_t *warm_accept, double *warm_stat,
+                    double *warm_step, int n_threads)
 {
     int C = cfg->n_chains, S = cfg->n_samples, W = cfg->n_warmup;
     size_t NN = (size_t)N * N;
@@ -451,7 +457,9 @@ int or_fit_galaxies(int n_gal, int N, double p, const or_psf *psf, int psf_per_g
                                n_grad ? n_grad + (size_t)n * C : NULL,
                                init_eps ? init_eps + (size_t)n * C : NULL,
                                init_im ? init_im + (size_t)n * C * 6 : NULL,
-                               warm_accept ? warm_accept + (size_t)n * C * W : NULL);
+                               warm_accept ? warm_accept + (size_t)n * C * W : NULL,
+                               warm_stat ? warm_stat + (size_t)n * C * W : NULL,
+                               warm_step ? warm_step + (size_t)n * C * W : NULL);
         bad += st != 0;
         if (smp) {
             /* [6][C][S] -> [6][n_gal][C][S] */

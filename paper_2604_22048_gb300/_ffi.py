@@ -28,7 +28,7 @@ EXPORTED = ["bs_prior_default", "bs_last_error", "bs_version", "bs_render", "bs_
             "bs_fit_resident_galaxies", "bs_fit_plan_num_launches", "bs_fit_plan_info", "bs_serve_request_bytes", "bs_serve_create", "bs_serve_submit",
             "bs_serve_poll", "bs_serve_get_stats", "bs_serve_now_ns", "bs_serve_destroy",
             "bs_shear_hyperprior_default", "bs_shear_sample", "bs_fp32_peak", "bs_fp64_peak", "bs_shear_loglike_multi",
-            "bs_kernel_launches"]
+            "bs_kernel_launches", "bs_shear_bias", "bs_shear_bias_custom"]
 
 
 class BsError(RuntimeError):
@@ -62,7 +62,9 @@ class FitArgs(C.Structure):
 class FitOut(C.Structure):
     _fields_ = [("samples", C.c_void_p), ("logp", C.c_void_p), ("accepted", C.c_void_p),
                 ("accept_rate", C.c_void_p), ("step_size", C.c_void_p), ("inv_mass", C.c_void_p),
-                ("n_divergent", C.c_void_p), ("status", C.c_void_p), ("n_grad", C.c_void_p)]
+                ("n_divergent", C.c_void_p), ("status", C.c_void_p), ("n_grad", C.c_void_p),
+                ("warmup_accepted", C.c_void_p), ("warmup_accept_stat", C.c_void_p),
+                ("warmup_step_size", C.c_void_p)]
 
 
 class ShearData(C.Structure):
@@ -78,6 +80,15 @@ class EstimateCfg(C.Structure):
     _fields_ = [("free_alpha", C.c_int32), ("alpha", C.c_double), ("alpha_lo", C.c_double),
                 ("alpha_hi", C.c_double), ("n_gh", C.c_int32), ("allreduce", ALLREDUCE_FN),
                 ("allreduce_user", C.c_void_p)]
+
+
+G_ESTIMATOR_FN = C.CFUNCTYPE(C.c_int32, C.POINTER(C.c_float), C.c_double, C.POINTER(C.c_double), C.c_void_p)
+BS_BIAS_QUADRATURE, BS_BIAS_HMC = 0, 1
+
+
+class BiasCfg(C.Structure):
+    _fields_ = [("g_abs", C.c_double), ("n_boot", C.c_int32), ("seed", C.c_uint64), ("base_weight", C.c_void_p),
+                ("m_boot", C.c_void_p), ("c_boot", C.c_void_p)]
 
 
 BS_PLAN_CAPTURE, BS_PLAN_AUTOTUNE = 1, 2
@@ -188,6 +199,9 @@ def lib():
     L.bs_shear_hyperprior_default.argtypes = [vp, vp]
     L.bs_shear_hyperprior_default.restype = None
     L.bs_shear_sample.argtypes = [C.POINTER(ShearData), C.POINTER(ShearSampleCfg), vp, vp, vp, vp, vp, sz, vp]
+    L.bs_shear_bias_custom.argtypes = [i64, G_ESTIMATOR_FN, vp, G_ESTIMATOR_FN, vp, C.POINTER(BiasCfg), vp]
+    L.bs_shear_bias.argtypes = [C.POINTER(ShearData), C.POINTER(ShearData), i32, C.POINTER(EstimateCfg),
+                                C.POINTER(ShearSampleCfg), C.POINTER(BiasCfg), vp, vp, vp, sz, vp]
     L.bs_fit_plan_num_launches.argtypes = [vp]
     L.bs_fit_plan_num_launches.restype = i32
     L.bs_fit_plan_info.argtypes = [vp, i32, C.POINTER(PlanLaunchInfo)]

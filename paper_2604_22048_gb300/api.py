@@ -164,6 +164,10 @@ class FitPlan:
         self.n_div = torch.empty((n_gal, Cn), dtype=torch.int32, device=dev) if "n_div" in want else None
         self.status = torch.empty((n_gal,), dtype=torch.int32, device=dev) if "status" in want else None
         self.n_grad = torch.empty((n_gal, Cn), dtype=torch.int32, device=dev) if "n_grad" in want else None
+        self.warm_accepted = (torch.empty((n_gal, Cn, cfg.n_warmup), dtype=torch.uint8, device=dev)
+                              if "warm_accepted" in want else None)
+        self.warm_stat = torch.empty((n_gal, Cn, cfg.n_warmup), **f32) if "warm_stat" in want else None
+        self.warm_step = torch.empty((n_gal, Cn, cfg.n_warmup), **f32) if "warm_step" in want else None
         o = F.FitOut()
         o.samples = _p(self.samples)
         o.logp = _p(self.logp)
@@ -174,6 +178,9 @@ class FitPlan:
         o.n_divergent = _p(self.n_div)
         o.status = _p(self.status)
         o.n_grad = _p(self.n_grad)
+        o.warmup_accepted = _p(self.warm_accepted)
+        o.warmup_accept_stat = _p(self.warm_stat)
+        o.warmup_step_size = _p(self.warm_step)
         self.out = o
         self.ws_bytes = F.lib().bs_fit_workspace_bytes(C.byref(a))
         self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=dev)
@@ -187,7 +194,8 @@ class FitPlan:
     def result(self):
         return dict(samples=self.samples, logp=self.logp, accepted=self.accepted,
                     accept_rate=self.accept_rate, step_size=self.step_size, inv_mass=self.inv_mass,
-                    n_div=self.n_div, status=self.status, n_grad=self.n_grad)
+                    n_div=self.n_div, status=self.status, n_grad=self.n_grad,
+                    warm_accepted=self.warm_accepted, warm_stat=self.warm_stat, warm_step=self.warm_step)
 
 
 class RaggedFitPlan(FitPlan):
@@ -520,13 +528,10 @@ class ShearPlan:
                                               _stream()))
         return buf[0], buf[1:].copy()
 
-    def sample(self, theta0, *, free=("g1", "g2"), lf=None, ls=None, lo=None, hi=None, n_warmup=500,
-               n_samples=1000, n_leapfrog=8, target_accept=0.8, random_steps=True, seed=2604,
-               interim=(-1.0, 9.0, -2.0, 1.0), allreduce=None):
-        """HMC over g and the named hyperparameters (bs_shear_sample).
-        theta0: (g1, g2, sigma_e, mu_f, sigma_f, a_f, mu_s, sigma_s) start and
-        fixed values; lf, ls: log-flux / log-size samples (CUDA, [n_gal, K]) for
-        the all-free likelihood.  Returns (samples [n_samples, 8], info)."""
+    def _sample_cfg(self, theta0, *, free=("g1", "g2"), lf=None, ls=None, lo=None, hi=None, n_warmup=500,
+                    n_samples=1000, n_leapfrog=8, target_accept=0.8, random_steps=True, seed=2604,
+                    interim=(-1.0, 9.0, -2.0, 1.0), allreduce=None):
+        """bs_shear_sample_cfg and the objects it points to (kept alive by the caller)."""
         names = ("g1", "g2", "sigma_e", "mu_f", "sigma_f", "a_f", "mu_s", "sigma_s")
         c = F.ShearSampleCfg()
         c.free_mask = sum(1 << names.index(n) for n in free)
@@ -545,107 +550,150 @@ class ShearPlan:
             c.interim[i] = float(interim[i])
         c.n_warmup, c.n_samples, c.n_leapfrog = n_warmup, n_samples, n_leapfrog
         c.target_accept, c.random_steps, c.seed = target_accept, int(random_steps), seed
-        cb = None
-        if allreduce is not None:
-            def _cb(buf, user):
-                arr = np.ctypeslib.as_array(buf, shape=(4,))
-                arr[:] = allreduce(arr.copy())
-            cb = F.ALLREDUCE_FN(_cb)
+        cb = _allreduce_cb(allreduce)
+        if cb is not None:
             c.allreduce = cb
-        out = np.zeros((n_samples, 8))
+        return c, (keep, cb)
+
+    def sample(self, theta0, **kw):
+        """HMC over g and the named hyperparameters (bs_shear_sample).
+        theta0: (g1, g2, sigma_e, mu_f, sigma_f, a_f, mu_s, sigma_s) start and
+        fixed values; keywords free, lf, ls (log-flux / log-size samples, CUDA
+        [n_gal, K], for the all-free likelihood), lo, hi, n_warmup, n_samples,
+        n_leapfrog, target_accept, random_steps, seed, interim, allreduce.
+        Returns (samples [n_samples, 8], info)."""
+        c, keep = self._sample_cfg(theta0, **kw)
+        out = np.zeros((c.n_samples, 8))
         acc, eps, nev = C.c_double(0), C.c_double(0), C.c_int32(0)
         F.check(F.lib().bs_shear_sample(C.byref(self.data), C.byref(c), out.ctypes.data_as(C.c_void_p),
                                         C.cast(C.byref(acc), C.c_void_p), C.cast(C.byref(eps), C.c_void_p),
                                         C.cast(C.byref(nev), C.c_void_p), _p(self.ws), self.ws_bytes, _stream()))
-        del keep, cb
+        del keep
         return out, {"accept_rate": acc.value, "step_size": eps.value, "n_evals": nev.value}
 
-    def estimate(self, *, free_alpha=False, alpha=0.2, alpha_lo=1e-4, alpha_hi=1.0, n_gh=7, allreduce=None):
-        """Posterior mean and covariance of (g1, g2[, alpha]) (numpy)."""
+    @staticmethod
+    def _estimate_cfg(*, free_alpha=False, alpha=0.2, alpha_lo=1e-4, alpha_hi=1.0, n_gh=7, allreduce=None):
         cfg = F.EstimateCfg()
         cfg.free_alpha = int(free_alpha)
         cfg.alpha = alpha
         cfg.alpha_lo = alpha_lo
         cfg.alpha_hi = alpha_hi
         cfg.n_gh = n_gh
-        cb = None
-        if allreduce is not None:
-            def _cb(buf, user):
-                arr = np.ctypeslib.as_array(buf, shape=(4,))
-                arr[:] = allreduce(arr.copy())
-            cb = F.ALLREDUCE_FN(_cb)
+        cb = _allreduce_cb(allreduce)
+        if cb is not None:
             cfg.allreduce = cb
+        return cfg, cb
+
+    def estimate(self, **kw):
+        """Posterior mean and covariance of (g1, g2[, alpha]) (numpy);
+        keywords free_alpha, alpha, alpha_lo, alpha_hi, n_gh, allreduce."""
+        cfg, cb = self._estimate_cfg(**kw)
         mean = np.zeros(3)
         cov = np.zeros(9)
         nev = C.c_int32(0)
         F.check(F.lib().bs_shear_estimate(C.byref(self.data), C.byref(cfg), mean.ctypes.data_as(C.c_void_p),
                                           cov.ctypes.data_as(C.c_void_p), C.cast(C.byref(nev), C.c_void_p),
                                           _p(self.ws), self.ws_bytes, _stream()))
+        del cb
         self.last_n_evals = nev.value
-        n = 3 if free_alpha else 2
+        n = 3 if cfg.free_alpha else 2
         return mean[:n], cov.reshape(3, 3)[:n, :n]
 
 
-def bootstrap_weights(n_gal, rng):
-    """One bootstrap resample of n_gal galaxies drawn with replacement, as
-    per-galaxy counts (float32 [n_gal], summing to n_gal)."""
-    return np.bincount(rng.integers(0, n_gal, n_gal), minlength=n_gal).astype(np.float32)
+def _allreduce_cb(allreduce):
+    """The C callback summing the 4 doubles of an evaluation over ranks."""
+    if allreduce is None:
+        return None
+
+    def _cb(buf, user):
+        arr = np.ctypeslib.as_array(buf, shape=(4,))
+        arr[:] = allreduce(arr.copy())
+    return F.ALLREDUCE_FN(_cb)
 
 
-def shear_bias(estimate_plus, estimate_minus, n_gal, *, g_abs=0.02, n_boot=500, seed=0):
+def _bias_cfg(n_gal, g_abs, n_boot, seed, base_weights):
+    cfg = F.BiasCfg()
+    cfg.g_abs, cfg.n_boot, cfg.seed = float(g_abs), int(n_boot), int(seed)
+    base = None
+    if base_weights is not None:
+        base = np.ascontiguousarray(base_weights, dtype=np.float32)
+        if base.shape != (n_gal,):
+            raise ValueError("base_weights must be [n_gal]")
+        cfg.base_weight = base.ctypes.data_as(C.c_void_p)
+    boot = np.full((2, max(int(n_boot), 0)), np.nan)
+    cfg.m_boot = boot[0].ctypes.data_as(C.c_void_p)
+    cfg.c_boot = boot[1].ctypes.data_as(C.c_void_p)
+    return cfg, base, boot
+
+
+def _bias_result(out, boot):
+    return {"m": float(out[0]), "c": float(out[1]), "m_sd": float(out[2]), "c_sd": float(out[3]),
+            "m_boot": boot[0].copy(), "c_boot": boot[1].copy()}
+
+
+def shear_bias(estimate_plus, estimate_minus, n_gal, *, g_abs=0.02, n_boot=500, seed=0, base_weights=None):
     """Multiplicative and additive bias by shape-noise cancellation (Sec. 3.4)
-    with bootstrap errors.  estimate_plus / estimate_minus map per-galaxy
-    weights (None for the original sample) to the shear estimate (g1, g2) of
-    the datasets sheared by +g and -g, g = (g_abs, 0), which share their
-    galaxies and noise:
-        m = (g+_1 - g-_1) / (2 |g|) - 1,   c = (g+_2 + g-_2) / 2.
-    Each bootstrap resample draws the galaxies once and applies the same
-    counts to both datasets (the image-phase samples are reused); the errors
-    are the standard deviations of m and c over the resamples, while m and c
-    themselves come from the original sample."""
-    def mc(gp, gm):
-        return (gp[0] - gm[0]) / (2.0 * g_abs) - 1.0, 0.5 * (gp[1] + gm[1])
+    with bootstrap errors, through bs_shear_bias_custom: estimate_plus /
+    estimate_minus map per-galaxy weights (numpy float32 [n_gal], or None for
+    the original sample) to the estimate (g1, g2) of the datasets sheared by
+    +g and -g, g = (g_abs, 0).  Returns m, c, their bootstrap standard
+    deviations m_sd, c_sd and the per-resample m_boot, c_boot."""
+    cfg, base, boot = _bias_cfg(n_gal, g_abs, n_boot, seed, base_weights)
+    errors = []
 
-    m, c = mc(estimate_plus(None), estimate_minus(None))
-    rng = np.random.default_rng(seed)
-    boot = np.empty((n_boot, 2))
-    for i in range(n_boot):
-        w = bootstrap_weights(n_gal, rng)
-        boot[i] = mc(estimate_plus(w), estimate_minus(w))
-    sd = boot.std(axis=0, ddof=1) if n_boot > 1 else np.full(2, np.nan)
-    return {"m": m, "c": c, "m_sd": float(sd[0]), "c_sd": float(sd[1]), "m_boot": boot[:, 0], "c_boot": boot[:, 1]}
+    def wrap(f):
+        def cb(wp, wsum, gout, user):
+            try:
+                w = np.ctypeslib.as_array(wp, shape=(n_gal,)).copy() if wp else None
+                g = f(w)
+                gout[0], gout[1] = float(g[0]), float(g[1])
+                return 0
+            except Exception as e:          # reported after the call returns
+                errors.append(e)
+                return 1
+        return F.G_ESTIMATOR_FN(cb)
+
+    cbp, cbm = wrap(estimate_plus), wrap(estimate_minus)
+    out = np.zeros(4)
+    st = F.lib().bs_shear_bias_custom(int(n_gal), cbp, None, cbm, None, C.byref(cfg), out.ctypes.data_as(C.c_void_p))
+    if errors:
+        raise errors[0]
+    F.check(st)
+    del cbp, cbm, base
+    return _bias_result(out, boot)
 
 
 def shear_bias_plans(plan_plus, plan_minus, *, g_abs=0.02, n_boot=500, seed=0, method="quadrature",
                      base_weights=None, **kw):
-    """shear_bias with the posterior mean of g from two ShearPlans as the
-    estimator: method "quadrature" (ShearPlan.estimate, keyword arguments kw)
-    or "hmc" (the mean of ShearPlan.sample draws, keyword arguments kw).
-    base_weights (numpy [n_gal], optional) multiply every resample's counts,
-    e.g. 0 for galaxies left out of both datasets.  The plans' weights are
-    reset afterwards."""
+    """shear_bias on the GPU (bs_shear_bias) with the posterior mean of g from
+    two ShearPlans as the estimator: method "quadrature" (bs_shear_estimate,
+    keywords as ShearPlan.estimate) or "hmc" (the mean of bs_shear_sample's g
+    draws, keywords as ShearPlan.sample, theta0 included).  base_weights
+    (numpy [n_gal], optional) multiply every resample's counts, e.g. 0 for
+    galaxies left out of both datasets.  The plans' own weights are not used
+    and not changed."""
     n = plan_plus.data.n_gal
     if plan_minus.data.n_gal != n:
         raise ValueError("the +g and -g datasets must hold the same galaxies")
-    base = None if base_weights is None else np.ascontiguousarray(base_weights, dtype=np.float32)
-
-    def estimator(plan):
-        def f(w):
-            if base is not None:
-                w = base if w is None else w * base
-            plan.set_weights(w, None if w is None else float(w.astype(np.float64).sum()))
-            if method == "quadrature":
-                return plan.estimate(**kw)[0][:2]
-            if method == "hmc":
-                return plan.sample(**kw)[0][:, :2].mean(axis=0)
-            raise ValueError("method: quadrature or hmc")
-        return f
-
-    try:
-        return shear_bias(estimator(plan_plus), estimator(plan_minus), n, g_abs=g_abs, n_boot=n_boot, seed=seed)
-    finally:
-        plan_plus.set_weights(None)
-        plan_minus.set_weights(None)
+    cfg, base, boot = _bias_cfg(n, g_abs, n_boot, seed, base_weights)
+    est = smp = keep = None
+    if method == "quadrature":
+        est, keep = ShearPlan._estimate_cfg(**kw)
+        mcode = F.BS_BIAS_QUADRATURE
+    elif method == "hmc":
+        smp, keep = plan_plus._sample_cfg(**kw)
+        mcode = F.BS_BIAS_HMC
+    else:
+        raise ValueError("method: quadrature or hmc")
+    big = plan_plus if plan_plus.ws_bytes >= plan_minus.ws_bytes else plan_minus
+    wdev = torch.empty(n, dtype=torch.float32, device=plan_plus.keep[0].device)
+    out = np.zeros(4)
+    F.check(F.lib().bs_shear_bias(C.byref(plan_plus.data), C.byref(plan_minus.data), mcode,
+                                  C.byref(est) if est is not None else None,
+                                  C.byref(smp) if smp is not None else None, C.byref(cfg), _p(wdev),
+                                  out.ctypes.data_as(C.c_void_p), _p(big.ws), big.ws_bytes, _stream()))
+    del keep, base
+    return _bias_result(out, boot)
 
 
 def shear_loglike(e1, e2, g1, g2, alpha, *, b=None, family=F.BS_EPRIOR_BA14, trunc_r=0.7, sigma_e0=0.3):

@@ -262,6 +262,9 @@ bs_status fit_params_from_args(const bs_fit_args *a, const bs_fit_out *o, FitPar
     p.n_div = o->n_divergent;
     p.status = o->status;
     p.n_grad = o->n_grad;
+    p.warm_accepted = o->warmup_accepted;
+    p.warm_stat = o->warmup_accept_stat;
+    p.warm_step = o->warmup_step_size;
     p.work = nullptr;
     p.n_work = a->n_gal;
     p.queue = nullptr;

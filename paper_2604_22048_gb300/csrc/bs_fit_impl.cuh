@@ -1192,6 +1192,12 @@ __device__ void run_chain(const FitParams &P, const GalCtx &gc, const SmemView &
             lp = lpp;
         }
         if (it < W) {
+            if (lane == 7) {
+                const size_t wi0 = ci0 * (size_t)W + it;
+                if (P.warm_accepted) P.warm_accepted[wi0] = acc ? 1 : 0;
+                if (P.warm_stat) P.warm_stat[wi0] = a;
+                if (P.warm_step) P.warm_step[wi0] = eps;
+            }
             // dual averaging
             da_m += 1;
             const float m = (float)da_m;

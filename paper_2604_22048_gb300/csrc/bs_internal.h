@@ -54,6 +54,9 @@ struct FitParams {
     int32_t *n_div;
     int32_t *status;
     int32_t *n_grad;
+    uint8_t *warm_accepted;
+    float *warm_stat;
+    float *warm_step;
     // scheduling: the CTAs take positions 0..n_work-1 of `work` (galaxy
     // indices; NULL = identity) from the atomic counter `queue`
     const int32_t *work;

@@ -137,7 +137,8 @@ def test_fit_sampling_phase_coupled_to_oracle(cuda):
                          seed=7, random_steps=False, init_step_size=_f32(step), init_inv_mass=_f32(im))
     assert (res["status"] == 0).all()
     coupled = (res["accepted"] == ref["accept"]).all(axis=-1)           # [n_gal, C]
-    assert coupled.mean() >= 0.9, coupled
+    print(f"\nsampling phase coupled: {int(coupled.sum())}/{coupled.size} chains")
+    assert coupled.sum() >= coupled.size - 1, coupled
     assert (res["n_grad"][coupled] == ref["n_grad"][coupled]).all()
     s_gpu, s_ref = res["samples"], ref["samples"]
     worst = 0.0
@@ -150,6 +151,86 @@ def test_fit_sampling_phase_coupled_to_oracle(cuda):
                 mcse = y.std() / np.sqrt(O.ess(y[None, :]))
                 worst = max(worst, abs(x.mean() - y.mean()) / mcse)
     assert worst <= 1e-3, worst
+
+
+def _fit_traces(cuda, truth, cfg, init_step=None):
+    ds = datagen.make_dataset(truth, cfg.n_chains)
+    flat, data, offsets, side, psf, sigma = _upload(ds, cuda, np.float64)
+    st = None if init_step is None else torch.full((truth.n, cfg.n_chains), init_step, dtype=torch.float32,
+                                                    device=cuda)
+    res = api.fit_galaxies(data, offsets, side, psf, sigma, torch.from_numpy(_f32(ds.init).astype(np.float32)).to(cuda),
+                           cfg, init_step_size=st,
+                           want=("accepted", "warm_accepted", "warm_stat", "warm_step", "step_size", "inv_mass",
+                                 "status"))
+    torch.cuda.synchronize()
+    res = {k: v.cpu().numpy().astype(np.float64) if v.dtype == torch.float32 else v.cpu().numpy()
+           for k, v in res.items() if v is not None}
+    offs, sides = offsets.cpu().numpy(), side.cpu().numpy()
+    stamps = np.stack([_stamp(flat, offs, sides, i) for i in range(truth.n)])
+    return ds, stamps, res
+
+
+def test_fit_warmup_adaptation_replays_on_the_oracle(cuda):
+    """The GPU's step-size adaptation, checked exactly on its own trace
+    (10 galaxies x 4 chains, 300 warmup iterations with three metric windows):
+    - the initial search from eps = 1 returns the oracle's step for every chain;
+    - in each dual-averaging segment (restarted after every window), the step
+      each transition starts from is exp of the oracle's dual-averaging iterate
+      over the GPU's own accept statistics, and the final step is exp of the
+      averaged iterate (FP32 recursion against FP64: 2e-5 relative);
+    - each search after a window returns the step it started from times a
+      power of two."""
+    truth = synth.draw_plain(10, 25)
+    W, delta = 300, 0.8
+    cfg = api.FitConfig(n_chains=4, n_warmup=W, n_samples=20, n_leapfrog=16, random_steps=True,
+                        target_accept=delta, seed=31)
+    ds, stamps, res = _fit_traces(cuda, truth, cfg)
+    assert (res["status"] == 0).all()
+    ref = O.fit_galaxies(stamps, 1.0, datagen.psf_tuple(truth, 0), _f32(ds.init), n_warmup=1, n_samples=0,
+                         n_leapfrog=16, seed=cfg.seed, random_steps=True, target_accept=delta)
+    assert np.abs(res["warm_step"][..., 0] / ref["warm_step"][..., 0] - 1).max() <= 1e-6
+    restarts = [0] + [e for (_, e) in O.window_schedule(W)]
+    a, eps = res["warm_stat"], res["warm_step"]
+    for i in range(truth.n):
+        for c in range(cfg.n_chains):
+            prev = 1.0
+            for k, s0 in enumerate(restarts):
+                s1 = restarts[k + 1] if k + 1 < len(restarts) else W
+                doublings = np.log2(eps[i, c, s0] / prev)
+                assert abs(doublings - round(doublings)) <= 1e-4, (i, c, s0, doublings)
+                le, lebar = O.dual_averaging(a[i, c, s0:s1], delta, eps[i, c, s0])
+                assert np.abs(eps[i, c, s0 + 1:s1] / np.exp(le[:-1]) - 1).max() <= 2e-5, (i, c, s0)
+                prev = np.exp(le[-1])
+            assert abs(res["step_size"][i, c] / np.exp(lebar[-1]) - 1) <= 2e-5, (i, c)
+
+
+def test_fit_warmup_coupled_to_oracle(cuda):
+    """Warmup on both sides from the same start, step (1e-4) and Philox stream,
+    in the regime where leapfrog is accurate (target acceptance 0.99, so dual
+    averaging keeps the step below a tenth of the stable one through the
+    metric window [15, 90) of 100 iterations): a chain is coupled when every
+    accept decision up to the window's end agrees; for coupled chains the
+    steps of every transition, the adapted inverse metric and the step of the
+    search after the window agree element by element.  The tolerance, 2e-3
+    relative, covers the FP32 energies: accept statistics differing by up to
+    ~1e-4 move the dual-averaging steps by a few 1e-4, and the window's
+    variance of a slowly moving chain inherits that."""
+    truth = synth.draw_plain(10, 25)
+    W = 100
+    cfg = api.FitConfig(n_chains=4, n_warmup=W, n_samples=10, n_leapfrog=8, random_steps=True,
+                        target_accept=0.99, seed=31)
+    ds, stamps, res = _fit_traces(cuda, truth, cfg, init_step=1e-4)
+    ref = O.fit_galaxies(stamps, 1.0, datagen.psf_tuple(truth, 0), _f32(ds.init), n_warmup=W, n_samples=10,
+                         n_leapfrog=8, jitter=0.0, seed=cfg.seed, random_steps=True, target_accept=0.99,
+                         init_step_size=np.full((truth.n, 4), np.float32(1e-4), dtype=np.float64))
+    (w0, we), = O.window_schedule(W)
+    coupled = (res["warm_accepted"][..., :we] == ref["warm_accept"][..., :we]).all(axis=-1)
+    print(f"\nwarmup coupled through the metric window: {int(coupled.sum())}/{coupled.size} chains")
+    assert coupled.sum() >= coupled.size - 2, coupled
+    rel = lambda x, y: np.abs(x / y - 1)
+    assert rel(res["warm_step"][..., :we], ref["warm_step"][..., :we]).max(axis=-1)[coupled].max() <= 2e-3
+    assert rel(res["inv_mass"], ref["inv_mass"]).max(axis=-1)[coupled].max() <= 2e-3
+    assert rel(res["warm_step"][..., we], ref["warm_step"][..., we])[coupled].max() <= 2e-3
 
 
 def test_fit_warmup_statistically_matches_oracle(cuda):
@@ -200,7 +281,7 @@ def test_shear_loglike_matches_oracle(cuda, family, K, with_b):
         v, gr = O.shear_loglike(e1, e2, g1, g2, a, b=b, family=family)
         assert np.isfinite(v)
         assert abs(got[0] - v) <= 1e-5 * max(abs(v), n), (got[0], v)
-        assert np.abs(got[1:] - gr).max() <= 1e-4 * np.abs(gr).max() + 1e-6 * n, (got[1:], gr)
+        assert np.abs(got[1:] - gr).max() <= 1e-4 * np.abs(gr).max(), (got[1:], gr)
 
 
 @pytest.mark.parametrize("family", [O.EPRIOR_BA14, O.EPRIOR_TRUNC_GAUSS])
@@ -224,7 +305,7 @@ def test_shear_loglike_full_matches_oracle(cuda, family):
         v, g = O.shear_loglike_full(e1, e2, lf, ls, th, family=family)
         assert np.isfinite(v)
         assert abs(got_v - v) <= 1e-5 * max(abs(v), n), (got_v, v)
-        assert np.abs(got_g - g).max() <= 1e-4 * np.abs(g).max() + 1e-6 * n, (th, got_g, g)
+        assert np.abs(got_g - g).max() <= 1e-4 * np.abs(g).max(), (th, got_g, g)
 
 
 def test_shear_empty_and_zero_weight(cuda):

@@ -14,6 +14,11 @@ from paper_2604_22048_gb300 import api, synth
 pytestmark = pytest.mark.gpu
 
 
+def _resample(n, rng):
+    """Counts of n galaxies drawn with replacement (float32 [n])."""
+    return np.bincount(rng.integers(0, n, n), minlength=n).astype(np.float32)
+
+
 def _samples(rng, n, K, spread):
     e = rng.normal(0.0, spread, (n, K, 2))
     r = np.hypot(e[..., 0], e[..., 1])
@@ -97,7 +102,7 @@ def test_weighted_estimate_matches_oracle(cuda):
     n, K = 3000, 32
     e_int = synth.draw_ba14_e(rng, n, sigma=0.2)
     e1, e2 = synth.toy_interim_ellipticities(e_int, (0.02, -0.01), K, rng, n_prop=300)
-    w = api.bootstrap_weights(n, rng)
+    w = _resample(n, rng)
     plan = api.ShearPlan(torch.from_numpy(e1).to(cuda), torch.from_numpy(e2).to(cuda), weights=w)
     mg, cg = plan.estimate(free_alpha=True, alpha=0.2, alpha_lo=0.1, alpha_hi=0.4)
     mo, co = O.shear_estimate(e1, e2, family=O.EPRIOR_BA14, free_alpha=True, alpha=0.2, alpha_lo=0.1,
@@ -133,7 +138,7 @@ def test_bootstrap_bias_on_the_toy(cuda):
     boot = []
     brng = np.random.default_rng(5)
     for _ in range(100):
-        plans[0].set_weights(api.bootstrap_weights(n, brng), float(n))
+        plans[0].set_weights(_resample(n, brng), float(n))
         boot.append(plans[0].estimate(alpha=0.2)[0][0])
     ratio = np.std(boot, ddof=1) / np.sqrt(cov[0, 0])
     assert 0.75 < ratio < 1.3, ratio
