@@ -92,14 +92,6 @@ def make_truth(a, rank):
     return synth.draw_plain(a.n_gal, a.side, seed=synth.SEED_DATA + 97 * rank)
 
 
-def sheared(e_int, g):
-    """Sheared ellipticity (reduced-shear convention) for input preparation."""
-    e = e_int[:, 0] + 1j * e_int[:, 1]
-    gc = g[0] + 1j * g[1]
-    ep = (e + gc) / (1 + np.conj(gc) * e)
-    return np.stack([ep.real, ep.imag], axis=1)
-
-
 def make_inputs_gpu(a, rank, dev):
     """Noisy stamps rendered on the device by bs_render (unit flux, scaled to
     the drawn S/N), plus chain starts (Eq. initialize)."""
@@ -107,7 +99,7 @@ def make_inputs_gpu(a, rank, dev):
     from paper_2604_22048_gb300 import api, synth
     t = make_truth(a, rank)
     n = t.n
-    ep = sheared(t.e_int, t.g)
+    ep = synth.shear_ellipticity_pairs(t.e_int, t.g)
     theta = np.column_stack([np.zeros(n), np.log10(t.hlr), ep, t.offset]).astype(np.float32)
     side = torch.from_numpy(t.side.astype(np.int32)).to(dev)
     if t.psf_kind == "gaussian":
@@ -247,7 +239,7 @@ def reference_arm(a, world, rank):
     a2 = argparse.Namespace(**vars(a))
     a2.n_gal = n
     t = make_truth(a2, 0)
-    ep = sheared(t.e_int, t.g)
+    ep = synth.shear_ellipticity_pairs(t.e_int, t.g)
     theta = np.column_stack([np.zeros(n), np.log10(t.hlr), ep, t.offset])
     noise = synth.noise_fields(t)
     if t.psf_kind == "gaussian":
@@ -522,6 +514,7 @@ def toy_interim_samples(n, K, g, alpha, dev, *, sigma_eta=0.1, n_prop=3000, seed
     sampling-importance-resampling of n_prop proposals from the likelihood.
     Returns e1, e2 [n, K] float32 on `dev` (sheared-ellipticity samples)."""
     import torch
+    from paper_2604_22048_gb300 import synth
     gen = torch.Generator(device=dev)
     gen.manual_seed(seed)
     e1 = torch.empty((n, K), dtype=torch.float32, device=dev)
@@ -540,7 +533,7 @@ def toy_interim_samples(n, K, g, alpha, dev, *, sigma_eta=0.1, n_prop=3000, seed
             ok = zc.abs() < 0.7
             idx = torch.nonzero(todo).squeeze(1)
             todo[idx[ok]] = False
-        ep = (eps + gc) / (1 + gc.conjugate() * eps)
+        ep = synth.shear_ellipticity(eps, gc)
         r = ep.abs().clamp_min(1e-12)
         eta = ep * (2 * torch.atanh(r) / r)
         eta_obs = eta + sigma_eta * torch.complex(torch.randn(m, generator=gen, device=dev, dtype=torch.float64),

@@ -20,15 +20,12 @@ using FitKernel = void (*)(const FitParams);
     }
 
 // Register budget of a launch (128, 96 or 80; 96 only for blocks of up to 4
-// chains); 0 takes the process default (BS_FIT_REGS, else 128).
+// chains); 0 takes 128.  Only the caller's explicit choice selects another
+// instance: the 80-register one rounds some operations differently, so its
+// chains are valid draws that differ from the others'.
 FitKernel fit_kernel_for(int max_side, int regs, int n_chains)
 {
-    static const int dflt = [] {
-        const char *s = getenv("BS_FIT_REGS");
-        const int r = s ? atoi(s) : 128;
-        return (r == 96 || r == 80) ? r : 128;
-    }();
-    if (regs != 128 && regs != 96 && regs != 80) regs = dflt;
+    if (regs != 128 && regs != 96 && regs != 80) regs = 128;
     if (regs == 96 && n_chains > 4) regs = 128;
     if (regs == 80) BS_FIT_NC_SWITCH(fit_kernel_r80)
     if (regs == 96) BS_FIT_NC_SWITCH(fit_kernel_r96)

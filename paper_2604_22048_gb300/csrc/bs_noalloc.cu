@@ -5,8 +5,8 @@
 // that runs under a fixed device-memory budget owned by another framework,
 // real-time loops that must not allocate between iterations, or a sampler
 // embedded in a host program with no allocator of its own.  This entry point
-// runs the same kernels as bs_shear_loglike, but keeps their scratch -- one
-// FP64 partial (value, d/dg1, d/dg2, sum of weighted |eps|^2) per thread
+// runs the same kernels as bs_shear_loglike, but keeps their scratch -- four
+// FP64 partials (value, d/dg1, d/dg2, sum of weighted |eps|^2) per thread
 // block of the reduction -- in a file-scope device array instead of a
 // caller workspace.
 //
@@ -14,11 +14,14 @@
 // library holds it (64 KB) until the process exits.  Host code cannot use the
 // array's name as a device address, so the first call on each device looks up
 // the address with cudaGetSymbolAddress (with that device current) and caches
-// it; make that first call before any stream capture.  Every call shares the
-// array and it keeps the last call's contents: each launch writes every slot
-// it later reads, so nothing has to start at zero, but calls that overlap on
-// the GPU (on different streams, or from different host threads without
-// ordering) race on it.
+// it for the life of the process; make that first call before any stream
+// capture.  A cudaDeviceReset unloads the library's device data, so the
+// cached address does not survive it: the entry point must not be called on
+// a device after its reset.  Every call shares the array and it keeps the
+// last call's contents: each launch writes every slot it later reads, so
+// nothing has to start at zero, but calls that overlap on the GPU (on
+// different streams, or from different host threads without ordering) race
+// on it.
 #include <mutex>
 
 #include "bs_device.cuh"

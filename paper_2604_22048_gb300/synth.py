@@ -1,10 +1,15 @@
 """Seeded synthetic inputs for the galaxy-fit and shear stages.
 
-This module only draws random numbers: the true parameters of each galaxy,
-pixel-noise fields and the random parts of the chain initialisation.  It holds
-none of the method's arithmetic (no rendering, no shear transform, no
-likelihood): callers turn the draws into images with a renderer of their own.
-Every draw comes from ``numpy.random.Generator(PCG64(seed))``.
+This module draws the random inputs: the true parameters of each galaxy,
+pixel-noise fields and the random parts of the chain initialisation, every
+draw from ``numpy.random.Generator(PCG64(seed))``.  It renders nothing and
+evaluates no likelihood: callers turn the draws into images with a renderer of
+their own.  Two pieces of input preparation do touch the method's formulas:
+``shear_ellipticity`` applies the shear transform (Eq. shear-transform) to
+make the sheared truths, and ``toy_interim_ellipticities`` builds the
+Appendix-A toy's interim samples (that transform, the eta map and importance
+resampling).  They make inputs only; the library never calls this module, and
+the oracle neither imports it nor shares its code.
 
 Workloads (stand-ins for the paper's 320k GalSim images of Sec. 2, which are
 not available): isolated exponential galaxies at 0.2 arcsec / pixel with
@@ -148,6 +153,19 @@ def draw_ba14_e(rng, n, sigma=0.2):
     return out
 
 
+def shear_ellipticity(e, g):
+    """Sheared ellipticity (e + g) / (1 + conj(g) e) of complex ellipticities e
+    (numpy array or torch tensor) under the shear g (a complex number), in the
+    reduced-shear convention of Eq. shear-transform."""
+    return (e + g) / (1 + g.conjugate() * e)
+
+
+def shear_ellipticity_pairs(e_int, g):
+    """shear_ellipticity on (e1, e2) rows: e_int [n, 2], g (g1, g2) -> [n, 2]."""
+    ep = shear_ellipticity(e_int[:, 0] + 1j * e_int[:, 1], complex(g[0], g[1]))
+    return np.stack([ep.real, ep.imag], axis=1)
+
+
 def toy_interim_ellipticities(e_int, g, K, rng, *, sigma_eta=0.1, n_prop=3000, sigma_e0=0.3):
     """Appendix-A toy, first phase: the intrinsic ellipticities e_int [n, 2] are
     sheared by g (Eq. shear-transform), mapped to eta = 2 atanh|e| e/|e|
@@ -158,9 +176,7 @@ def toy_interim_ellipticities(e_int, g, K, rng, *, sigma_eta=0.1, n_prop=3000, s
     n_prop proposals drawn from the likelihood.  Returns the sheared
     ellipticity samples e1, e2 [n, K] (float32)."""
     n = len(e_int)
-    e = e_int[:, 0] + 1j * e_int[:, 1]
-    gc = complex(g[0], g[1])
-    ep = (e + gc) / (1 + np.conj(gc) * e)
+    ep = shear_ellipticity(e_int[:, 0] + 1j * e_int[:, 1], complex(g[0], g[1]))
     r = np.maximum(np.abs(ep), 1e-12)
     eta = ep * (2 * np.arctanh(r) / r)
     eta_obs = eta + sigma_eta * (rng.normal(size=n) + 1j * rng.normal(size=n))

@@ -56,42 +56,3 @@ def test_spergel_half_matches_the_exponential_kernel(cuda):
     a, b, ga, gb = a.cpu().numpy(), b.cpu().numpy(), ga.cpu().numpy(), gb.cpu().numpy()
     assert np.all(np.abs(a - b) <= 1e-5 * np.maximum(np.abs(a), 33 * 33))
     assert np.all(np.abs(ga - gb) <= 1e-4 * np.abs(ga).max(axis=1, keepdims=True) + 1e-3)
-
-
-def test_model_bias_of_the_wrong_profile(cuda):
-    """Exponential galaxies sheared by +-g (same noise) fitted with the
-    exponential, a Spergel profile of index -0.6 (close to de Vaucouleurs) and
-    a Gaussian: the exponential recovers m = 0 within its bootstrap errors;
-    the wrong profiles give significant multiplicative biases of opposite
-    signs, positive for nu = -0.6 and negative for the Gaussian (Appendix B,
-    Fig. model-bias)."""
-    n, side, C = 3000, 33, 4
-    truth = synth.draw_plain(n, side, seed=77)
-    t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(cuda)
-    data = {}
-    for sgn in (1, -1):
-        ds = datagen.make_dataset(truth, C, g=(0.02 * sgn, 0.0))
-        flat, offs, sides = datagen.pack(ds)
-        data[sgn] = (t(flat), t(offs), t(sides), t(ds.sigma.astype(np.float32)), t(ds.init.astype(np.float32)))
-    psf = api.psf_table("gaussian", 0.7, device=cuda)
-    m = {}
-    for name, prof, nu in (("exp", 0, 0.5), ("spergel", 1, -0.6), ("gauss", 2, 0.0)):
-        cfg = api.FitConfig(n_chains=C, n_warmup=150, n_samples=100, n_leapfrog=16, profile=prof, spergel_nu=nu)
-        plans, keep = [], np.ones(n, bool)
-        for sgn in (1, -1):
-            fl, of, si, sg, ini = data[sgn]
-            res = api.fit_galaxies(fl, of, si, psf, sg, ini, cfg)
-            assert (res["status"] == 0).all()
-            e1 = res["samples"][2].reshape(n, -1).contiguous()
-            e2 = res["samples"][3].reshape(n, -1).contiguous()
-            keep &= (torch.hypot(e1, e2).min(dim=1).values < 0.65).cpu().numpy()
-            plans.append(api.ShearPlan(e1, e2, family=O.EPRIOR_TRUNC_GAUSS, trunc_r=0.7))
-        m[name] = api.shear_bias_plans(*plans, g_abs=0.02, n_boot=40, seed=3, base_weights=keep.astype(np.float32),
-                                       alpha=0.2)
-    print({k: (v["m"], v["m_sd"]) for k, v in m.items()})
-    e = m["exp"]
-    assert abs(e["m"]) < 4 * e["m_sd"] + 0.005, e
-    for name, sign in (("spergel", 1), ("gauss", -1)):
-        d = m[name]["m"] - e["m"]
-        sd = np.hypot(m[name]["m_sd"], e["m_sd"])
-        assert sign * d > max(5 * sd, 0.01), (name, m[name]["m"], e["m"], sd)
