@@ -594,6 +594,19 @@ bs_status bs_shear_estimate(const bs_shear_data *data, const bs_estimate_cfg *cf
                             double *mean, double *cov, int32_t *n_evals, void *workspace,
                             size_t workspace_bytes, void *stream);
 
+/* A log-likelihood over (g1, g2, alpha) supplied by the caller: for m points
+ * x[m][3] write out[m][4] = {value, d/dg1, d/dg2, d/dalpha}; return 0 on
+ * success. */
+typedef int32_t (*bs_loglike_points_fn)(const double *x, int32_t m, double *out, void *user);
+
+/* The same estimate (Newton, Laplace-scaled Gauss-Hermite quadrature, the
+ * optional all-reduce of cfg after every evaluation) over the caller's
+ * likelihood instead of a GPU pass: host code only, e.g. a rank's share of a
+ * galaxy set evaluated elsewhere.  A failing callback gives
+ * BS_ERR_INVALID_ARG. */
+bs_status bs_shear_estimate_custom(bs_loglike_points_fn fn, void *user, const bs_estimate_cfg *cfg,
+                                   double *mean, double *cov, int32_t *n_evals);
+
 /* ------------------------------------------------------------------------ */
 /* Shear sampling phase as MCMC (Sec. 3.2 "Shear Sampling Phase")            */
 /* ------------------------------------------------------------------------ */

@@ -28,7 +28,7 @@ EXPORTED = ["bs_prior_default", "bs_last_error", "bs_version", "bs_render", "bs_
             "bs_fit_resident_galaxies", "bs_fit_plan_num_launches", "bs_fit_plan_info", "bs_serve_request_bytes", "bs_serve_create", "bs_serve_submit",
             "bs_serve_poll", "bs_serve_get_stats", "bs_serve_now_ns", "bs_serve_destroy",
             "bs_shear_hyperprior_default", "bs_shear_sample", "bs_fp32_peak", "bs_fp64_peak", "bs_shear_loglike_multi",
-            "bs_kernel_launches", "bs_shear_bias", "bs_shear_bias_custom"]
+            "bs_kernel_launches", "bs_shear_bias", "bs_shear_bias_custom", "bs_shear_estimate_custom"]
 
 
 class BsError(RuntimeError):
@@ -90,6 +90,8 @@ class BiasCfg(C.Structure):
     _fields_ = [("g_abs", C.c_double), ("n_boot", C.c_int32), ("seed", C.c_uint64), ("base_weight", C.c_void_p),
                 ("m_boot", C.c_void_p), ("c_boot", C.c_void_p)]
 
+
+LOGLIKE_POINTS_FN = C.CFUNCTYPE(C.c_int32, C.POINTER(C.c_double), C.c_int32, C.POINTER(C.c_double), C.c_void_p)
 
 BS_PLAN_CAPTURE, BS_PLAN_AUTOTUNE = 1, 2
 
@@ -200,6 +202,7 @@ def lib():
     L.bs_shear_hyperprior_default.restype = None
     L.bs_shear_sample.argtypes = [C.POINTER(ShearData), C.POINTER(ShearSampleCfg), vp, vp, vp, vp, vp, sz, vp]
     L.bs_shear_bias_custom.argtypes = [i64, G_ESTIMATOR_FN, vp, G_ESTIMATOR_FN, vp, C.POINTER(BiasCfg), vp]
+    L.bs_shear_estimate_custom.argtypes = [LOGLIKE_POINTS_FN, vp, C.POINTER(EstimateCfg), vp, vp, vp]
     L.bs_shear_bias.argtypes = [C.POINTER(ShearData), C.POINTER(ShearData), i32, C.POINTER(EstimateCfg),
                                 C.POINTER(ShearSampleCfg), C.POINTER(BiasCfg), vp, vp, vp, sz, vp]
     L.bs_fit_plan_num_launches.argtypes = [vp]

@@ -600,6 +600,36 @@ class ShearPlan:
         return mean[:n], cov.reshape(3, 3)[:n, :n]
 
 
+def shear_estimate_custom(loglike, **kw):
+    """bs_shear_estimate_custom: the library's posterior-mean estimate of g
+    (and alpha) over the caller's likelihood loglike(points [m, 3]) ->
+    [m, 4] (value, d/dg1, d/dg2, d/dalpha; numpy), on the host.  Keywords as
+    ShearPlan.estimate (allreduce included).  Returns (mean, cov, n_evals)."""
+    cfg, cb = ShearPlan._estimate_cfg(**kw)
+    errors = []
+
+    def f(xp, m, outp, user):
+        try:
+            x = np.ctypeslib.as_array(xp, shape=(m, 3)).copy()
+            o = np.asarray(loglike(x), dtype=np.float64).reshape(m, 4)
+            np.ctypeslib.as_array(outp, shape=(m, 4))[:] = o
+            return 0
+        except Exception as e:          # reported after the call returns
+            errors.append(e)
+            return 1
+
+    fn = F.LOGLIKE_POINTS_FN(f)
+    mean, cov, nev = np.zeros(3), np.zeros(9), C.c_int32(0)
+    st = F.lib().bs_shear_estimate_custom(fn, None, C.byref(cfg), mean.ctypes.data_as(C.c_void_p),
+                                          cov.ctypes.data_as(C.c_void_p), C.cast(C.byref(nev), C.c_void_p))
+    if errors:
+        raise errors[0]
+    F.check(st)
+    del fn, cb
+    n = 3 if cfg.free_alpha else 2
+    return mean[:n], cov.reshape(3, 3)[:n, :n], nev.value
+
+
 def _allreduce_cb(allreduce):
     """The C callback summing the 4 doubles of an evaluation over ranks."""
     if allreduce is None:

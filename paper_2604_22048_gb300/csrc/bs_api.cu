@@ -573,16 +573,32 @@ struct ShearObjective {
     size_t wsb;
     void *stream;
     int n;
+    bs_loglike_points_fn fn = nullptr;   // the caller's likelihood instead of the GPU pass
+    void *user = nullptr;
     bs_status err = BS_OK;
     int32_t n_evals = 0;
 
+    bool custom(const double *x, int m, double *out)
+    {
+        if (fn(x, m, out, user) != 0) {
+            err = fail(BS_ERR_INVALID_ARG, "bs_shear_estimate_custom: the likelihood callback failed");
+            return false;
+        }
+        return true;
+    }
     // value and gradient over (g1, g2[, alpha]); false on failure
     bool eval(const double *x, double &v, double *g)
     {
         const double alpha = n == 3 ? x[2] : cfg->alpha;
         double buf[4];
         ++n_evals;
-        bs_status st = bs_shear_loglike(d, x[0], x[1], alpha, buf, 1, ws, wsb, stream);
+        bs_status st = BS_OK;
+        if (fn) {
+            const double pt[3] = {x[0], x[1], alpha};
+            if (!custom(pt, 1, buf)) return false;
+        } else {
+            st = bs_shear_loglike(d, x[0], x[1], alpha, buf, 1, ws, wsb, stream);
+        }
         if (st != BS_OK) {
             err = st;
             return false;
@@ -603,7 +619,9 @@ struct ShearObjective {
     {
         if (m == 0) return true;
         std::vector<double> buf((size_t)4 * m);
-        if (d->b) {
+        if (fn) {
+            if (!custom(x, m, buf.data())) return false;
+        } else if (d->b) {
             for (int i = 0; i < m; ++i) {
                 bs_status st = bs_shear_loglike(d, x[3 * i], x[3 * i + 1], x[3 * i + 2], &buf[4 * (size_t)i], 1, ws,
                                                 wsb, stream);
@@ -711,17 +729,19 @@ void hermite_rule(int n, double *x, double *w)
 
 static bs_status shear_estimate_impl(const bs_shear_data *d, const bs_estimate_cfg *cfg, double *mean,
                                      double *cov, int32_t *n_evals, void *workspace, size_t workspace_bytes,
-                                     void *stream)
+                                     void *stream, bs_loglike_points_fn fn = nullptr, void *user = nullptr)
 {
-    bs_status st = validate_shear(d, "bs_shear_estimate");
-    if (st != BS_OK) return st;
+    if (!fn) {
+        bs_status st = validate_shear(d, "bs_shear_estimate");
+        if (st != BS_OK) return st;
+    }
     if (!cfg || !mean) return fail(BS_ERR_INVALID_ARG, "bs_shear_estimate: NULL cfg/mean");
     if (cfg->n_gh < 1 || cfg->n_gh > 32) return fail(BS_ERR_INVALID_ARG, "bs_shear_estimate: n_gh 1..32");
     const int n = cfg->free_alpha ? 3 : 2;
     if (cfg->free_alpha && !(cfg->alpha_lo < cfg->alpha && cfg->alpha < cfg->alpha_hi && cfg->alpha_lo > 0.0))
         return fail(BS_ERR_INVALID_ARG, "bs_shear_estimate: alpha start outside (alpha_lo, alpha_hi)");
     if (!(cfg->alpha > 0.0)) return fail(BS_ERR_INVALID_ARG, "bs_shear_estimate: alpha <= 0");
-    ShearObjective f{d, cfg, workspace, workspace_bytes, stream, n};
+    ShearObjective f{d, cfg, workspace, workspace_bytes, stream, n, fn, user};
     struct EvalCount {
         int32_t *dst;
         ShearObjective *f;
@@ -900,6 +920,17 @@ extern "C" bs_status bs_shear_estimate(const bs_shear_data *d, const bs_estimate
         return shear_estimate_impl(d, cfg, mean, cov, n_evals, workspace, workspace_bytes, stream);
     } catch (const std::bad_alloc &) {
         return fail(BS_ERR_OUT_OF_MEMORY, "bs_shear_estimate: host allocation failed");
+    }
+}
+
+extern "C" bs_status bs_shear_estimate_custom(bs_loglike_points_fn fn, void *user, const bs_estimate_cfg *cfg,
+                                              double *mean, double *cov, int32_t *n_evals)
+{
+    if (!fn) return fail(BS_ERR_INVALID_ARG, "bs_shear_estimate_custom: NULL likelihood");
+    try {
+        return shear_estimate_impl(nullptr, cfg, mean, cov, n_evals, nullptr, 0, nullptr, fn, user);
+    } catch (const std::bad_alloc &) {
+        return fail(BS_ERR_OUT_OF_MEMORY, "bs_shear_estimate_custom: host allocation failed");
     }
 }
 

@@ -55,6 +55,14 @@ class Truth:
         return len(self.hlr)
 
 
+def subset(truth: Truth, idx):
+    """The galaxies idx of a draw (one rank's share of a dataset)."""
+    idx = np.asarray(idx, dtype=np.int64)
+    return Truth(hlr=truth.hlr[idx], e_int=truth.e_int[idx], offset=truth.offset[idx], snr=truth.snr[idx],
+                 side=truth.side[idx], psf_fwhm=truth.psf_fwhm[idx], psf_kind=truth.psf_kind,
+                 psf_beta=truth.psf_beta, g=truth.g, extra=dict(truth.extra))
+
+
 def _trunc_gauss_e(rng, n, sigma=0.2, rmax=0.7):
     out = np.empty((n, 2))
     filled = 0

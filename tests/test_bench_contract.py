@@ -27,3 +27,21 @@ def test_reference_arm_prints_the_contract_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert "workload" in d["config"]
+
+
+def test_gpus_2_starts_two_ranks_and_rank_0_prints_one_line():
+    """--gpus 2 outside a launcher starts two ranks on this node (the driver's
+    torchrun form); for the reference arm rank 0 alone measures and prints,
+    reporting two GPUs, and the other rank exits 0."""
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--gpus", "2", "--impl", "reference",
+           "--ref-galaxies", "2", "--steps", "1", "--warmup", "0", "--n-warmup", "10", "--n-samples", "10",
+           "--leapfrog", "4"]
+    env = dict(os.environ)
+    for k in ("WORLD_SIZE", "RANK", "LOCAL_RANK", "MASTER_ADDR", "MASTER_PORT"):
+        env.pop(k, None)
+    out = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=600, env=env)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [l for l in out.stdout.splitlines() if l.strip().startswith("{")]
+    assert len(lines) == 1, out.stdout
+    d = json.loads(lines[0])
+    assert d["n_gpus"] == 2 and d["impl"] == "reference" and d["value"] > 0

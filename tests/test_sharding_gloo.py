@@ -1,7 +1,9 @@
 """Multi-rank host logic on CPU: two gloo ranks each evaluate the shear
 likelihood of their galaxy shard (with the oracle) and sum the (value,
 gradient) vector through the same all-reduce hook the GPU path uses; the sum
-equals the unsharded value.  Also the size-balanced galaxy partition."""
+equals the unsharded value, and the library's shear estimate run on both
+ranks with that all-reduce (bs_shear_estimate_custom) equals the one-process
+estimate.  Also the size-balanced galaxy partition."""
 import os
 import socket
 
@@ -61,6 +63,58 @@ def test_sharded_shear_loglike_sums_to_unsharded():
         for r in range(2):
             got = np.array(out[r][j])
             assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
+
+
+def _shard_loglike(e1, e2):
+    import oracle as O
+
+    def f(x):
+        return np.array([[v, *g] for v, g in (O.shear_loglike(e1, e2, p[0], p[1], p[2],
+                                                              family=O.EPRIOR_TRUNC_GAUSS) for p in x)])
+    return f
+
+
+def _estimate_worker(rank, world, port, e1, e2, parts, out):
+    import torch.distributed as dist
+    from paper_2604_22048_gb300 import api
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    idx = parts[rank]
+    mean, cov, nev = api.shear_estimate_custom(_shard_loglike(e1[idx], e2[idx]), free_alpha=True, alpha=0.2,
+                                               alpha_lo=0.1, alpha_hi=0.4, allreduce=sharding.make_allreduce())
+    out[rank].append([*mean.tolist(), *cov.ravel().tolist(), nev])
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_library_estimate_over_gloo_ranks_equals_one_process():
+    """Every rank runs the library's Newton and quadrature on the likelihood
+    all-reduced over the ranks (each summing its shard with the oracle); the
+    ranks agree with each other exactly and with the one-process estimate of
+    the same library code on all galaxies to rounding (1e-9)."""
+    from paper_2604_22048_gb300 import api
+    rng = np.random.default_rng(5)
+    n, K = 240, 16
+    e = rng.normal(0, 0.2, (n, K, 2)) * 0.6
+    e1, e2 = e[..., 0].astype(np.float32), e[..., 1].astype(np.float32)
+    parts = sharding.partition_galaxies(rng.choice([25, 53, 101], size=n), 2)
+    ctx = mp.get_context("spawn")
+    mgr = ctx.Manager()
+    out = [mgr.list(), mgr.list()]
+    port = _free_port()
+    procs = [ctx.Process(target=_estimate_worker, args=(r, 2, port, e1, e2, parts, out)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(300)
+        assert p.exitcode == 0
+    r0, r1 = np.array(out[0][0]), np.array(out[1][0])
+    assert np.array_equal(r0, r1)
+    mean, cov, nev = api.shear_estimate_custom(_shard_loglike(e1, e2), free_alpha=True, alpha=0.2,
+                                               alpha_lo=0.1, alpha_hi=0.4)
+    assert np.abs(r0[:3] - mean).max() <= 1e-9, (r0[:3], mean)
+    assert np.abs(r0[3:12] - cov.ravel()).max() <= 1e-9 * np.abs(cov).max()
 
 
 def test_partition_is_complete_and_balanced():
