@@ -97,6 +97,8 @@ def lib():
         L.or_profile_ft.argtypes = [C.c_int, C.c_double, C.c_double]
         L.or_hlr_over_r0_p.restype = C.c_double
         L.or_hlr_over_r0_p.argtypes = [C.c_int, C.c_double]
+        L.or_loglike_dense.restype = C.c_double
+        L.or_loglike_dense.argtypes = [C.c_int, C.c_double, C.POINTER(_Psf), _D, _D, _D, _D]
         L.or_loglike_cov.restype = C.c_double
         L.or_loglike_cov.argtypes = [C.c_int, C.c_int, C.c_double, C.POINTER(_Psf), _D, _D, _D, _D, _D]
         L.or_logpost.restype = C.c_double
@@ -318,6 +320,16 @@ def loglike_p(profile, nu, N, p, psf, data, sigma, theta):
     ps = _psf(psf)
     g = np.zeros(6)
     v = lib().or_loglike_p(profile, nu, N, p, C.byref(ps), _dp(_d(data)), sigma, _dp(_d(theta)), _dp(g))
+    return v, g
+
+
+def loglike_dense(N, p, psf, data, Sigma, theta):
+    """Appendix C, general covariance: (value, gradient[6]); Sigma [N*N, N*N]."""
+    data = _d(data)
+    S = _d(Sigma)
+    g = np.zeros(6)
+    ps = _psf(psf)
+    v = lib().or_loglike_dense(N, p, C.byref(ps), _dp(data), _dp(S), _dp(_d(theta)), _dp(g))
     return v, g
 
 

@@ -141,6 +141,13 @@ double or_loglike_t(int N, double p, const double *T, const double *data,
  * with Sigma_j built densely in pixel space and solved by Cholesky, and the
  * gradient sum_j (Sigma_j^-1 (d_j - m_j))^T dm_j/dtheta by the adjoint DFT;
  * NAN when some Sigma_j is not positive definite. */
+/* Appendix C with a general pixel covariance: -1/2 (d - m)^T Sigma^-1 (d - m)
+ * for one exposure, Sigma [N*N][N*N] (row-major over pixels iy*N + ix,
+ * symmetric positive definite), solved by Cholesky, and its gradient
+ * (Sigma^-1 (d - m))^T dm/dtheta by the adjoint DFT; NAN when Sigma is not
+ * positive definite. */
+double or_loglike_dense(int N, double p, const or_psf *psf, const double *data, const double *Sigma,
+                        const double theta[6], double grad[6]);
 double or_loglike_cov(int J, int N, double p, const or_psf *psf, const double *data, const double *sigma,
                       const double *corr, const double theta[6], double grad[6]);
 /* Eq. likelihood-pixels with the galaxy profile of Appendix B (profile, nu),

@@ -20,6 +20,7 @@
 #include <complex.h>
 #include <math.h>
 #include <stdlib.h>
+#include <string.h>
 
 #define OR_PI 3.14159265358979323846
 #define OR_LN10 2.30258509299404568402
@@ -277,6 +278,41 @@ double or_loglike_cov(int J, int N, double p, const or_psf *psf, const double *d
         }
     }
     free(M); free(m); free(T); free(S); free(z);
+    return logl;
+}
+
+double or_loglike_dense(int N, double p, const or_psf *psf, const double *data, const double *Sigma,
+                        const double theta[6], double grad[6])
+{
+    size_t n = (size_t)N * N;
+    double *M = malloc(sizeof(double) * 2 * n);
+    double *m = malloc(sizeof(double) * n);
+    double *T = malloc(sizeof(double) * n);
+    double *L = malloc(sizeof(double) * n * n);
+    double *z = malloc(sizeof(double) * n);
+    double logl = NAN;
+    or_transfer_table(N, p, psf, T);
+    or_model_spectrum_t(N, p, T, theta, M);
+    or_idft_image(N, M, m, 0);
+    memcpy(L, Sigma, sizeof(double) * n * n);
+    if (cholesky(L, (int)n)) {
+        /* z = Sigma^-1 (d - m): L y = r, then L^T z = y */
+        for (size_t a = 0; a < n; ++a) {
+            double t = data[a] - m[a];
+            for (size_t k = 0; k < a; ++k) t -= L[a * n + k] * z[k];
+            z[a] = t / L[a * n + a];
+        }
+        for (size_t a = n; a-- > 0;) {
+            double t = z[a];
+            for (size_t k = a + 1; k < n; ++k) t -= L[k * n + a] * z[k];
+            z[a] = t / L[a * n + a];
+        }
+        double q = 0.0;
+        for (size_t a = 0; a < n; ++a) q += (data[a] - m[a]) * z[a];
+        logl = -0.5 * q;
+        if (grad) adjoint_grad_p(N, p, M, z, theta, OR_PROFILE_EXPONENTIAL, 0.0, grad);
+    }
+    free(M); free(m); free(T); free(L); free(z);
     return logl;
 }
 

@@ -230,3 +230,29 @@ def correlated_noise(rng, n, N, a, sigma=1.0):
     x = sum(k[i] * np.roll(w, i - 1, axis=2) for i in range(3))
     y = sum(k[i] * np.roll(x, i - 1, axis=1) for i in range(3))
     return sigma * y / float((k ** 2).sum())
+
+
+def dense_covariance(N, rng, *, a=0.3, sigma=(0.7, 1.5), stray=0.4):
+    """A pixel covariance that is neither stationary nor diagonal (Appendix C,
+    general Sigma): Sigma = D^1/2 C D^1/2 + s^2 v v^T, with C the periodic
+    correlation of noise_correlation(N, a), D the pixel variances of a noise
+    level rising linearly across the stamp from sigma[0] to sigma[1] with a
+    random tilt, and v a smooth stray-light pattern (a random plane wave of
+    amplitude `stray`).  Returns Sigma [N*N, N*N] (float64, rows iy*N + ix)."""
+    c = (N - 1) // 2
+    corr = noise_correlation(N, a)
+    y, x = np.divmod(np.arange(N * N), N)
+    C = corr[(y[:, None] - y[None, :] + c) % N, (x[:, None] - x[None, :] + c) % N]
+    ang = rng.uniform(0.0, 2.0 * np.pi)
+    t = ((x - c) * np.cos(ang) + (y - c) * np.sin(ang)) / max(c, 1)
+    sd = sigma[0] + (sigma[1] - sigma[0]) * 0.5 * (t + 1.0)
+    kx, ky = rng.uniform(-0.5, 0.5, 2)
+    v = np.cos(kx * (x - c) + ky * (y - c) + rng.uniform(0.0, 2.0 * np.pi))
+    return sd[:, None] * C * sd[None, :] + stray ** 2 * np.outer(v, v)
+
+
+def dense_noise(Sigma, rng):
+    """One noise field with covariance Sigma (through its Cholesky factor)."""
+    n = Sigma.shape[0]
+    N = int(round(np.sqrt(n)))
+    return (np.linalg.cholesky(Sigma) @ rng.normal(size=n)).reshape(N, N)

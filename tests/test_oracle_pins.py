@@ -673,6 +673,52 @@ def test_loglike_cov_gradient_central_differences():
         assert abs(fd - g[i]) <= 1e-5 * max(1.0, abs(g[i])), (i, fd, g[i])
 
 
+def _dense_case(N=11, seed=8):
+    rng = np.random.default_rng(seed)
+    th = np.array([2.3, -0.45, 0.12, -0.2, 0.3, -0.25])
+    psf = (O.PSF_MOFFAT, 0.8, 3.0)
+    S = synth.dense_covariance(N, rng)
+    data = O.render(N, 0.2, psf, th) + synth.dense_noise(S, rng)
+    return N, th, psf, S, data
+
+
+def test_loglike_dense_reduces_to_the_white_and_stationary_cases():
+    """Sigma = sigma^2 I is Eq. likelihood-pixels; a circulant Sigma is the
+    stationary correlated-noise likelihood of one exposure."""
+    N, th, psf, _, data = _dense_case()
+    v, g = O.loglike_dense(N, 0.2, psf, data, 1.7 ** 2 * np.eye(N * N), th)
+    vr, gr = O.loglike(N, 0.2, psf, data, 1.7, th)
+    assert abs(v - vr) <= 1e-11 * abs(vr) and np.allclose(g, gr, rtol=1e-10, atol=1e-10)
+    corr = synth.noise_correlation(N, 0.3)
+    v, g = O.loglike_dense(N, 0.2, psf, data, _circulant(corr, 1.3 ** 2), th)
+    vr, gr = O.loglike_cov(N, 0.2, [psf], data[None], np.array([1.3]), th, corr=corr[None])
+    assert abs(v - vr) <= 1e-9 * abs(vr) and np.allclose(g, gr, rtol=1e-8, atol=1e-9)
+
+
+def test_loglike_dense_matches_multivariate_normal():
+    """A Sigma that is neither stationary nor diagonal: the value is scipy's
+    multivariate normal log density of the stamp without its normalisation."""
+    from scipy import stats
+    N, th, psf, S, data = _dense_case()
+    v, _ = O.loglike_dense(N, 0.2, psf, data, S, th)
+    m = O.render(N, 0.2, psf, th)
+    _, logdet = np.linalg.slogdet(2 * np.pi * S)
+    ref = stats.multivariate_normal(mean=m.ravel(), cov=S).logpdf(data.ravel()) + 0.5 * logdet
+    assert abs(v - ref) <= 1e-9 * abs(ref), (v, ref)
+
+
+def test_loglike_dense_gradient_central_differences():
+    N, th, psf, S, data = _dense_case()
+    _, g = O.loglike_dense(N, 0.2, psf, data, S, th)
+    for i in range(6):
+        h = 1e-6
+        tp, tm = th.copy(), th.copy()
+        tp[i] += h
+        tm[i] -= h
+        fd = (O.loglike_dense(N, 0.2, psf, data, S, tp)[0] - O.loglike_dense(N, 0.2, psf, data, S, tm)[0]) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-5 * max(1.0, abs(g[i])), (i, fd, g[i])
+
+
 def test_loglike_cov_rejects_a_covariance_that_is_not_positive_definite():
     N, th, psfs, sig, corr, data = _cov_case(J=1)
     bad = np.zeros((1, N, N))
