@@ -962,6 +962,15 @@ def serve_compare(a, dev, n_req, n_pool):
     res["served_over_plain_at_1.2x"] = (res["served_at_1.2x"]["galaxies_per_s"] /
                                         res["plain_at_1.2x"]["galaxies_per_s"])
     res["arrival_rate_1x"] = lam
+    # the comparison at equal offered load first: latency, then throughput
+    lead = {"latency_at_equal_load_ms": {
+        f"{f}x": {"arrivals_per_s": f * lam,
+                  "served": {k: res[f"served_at_{f}x"][k] for k in ("p50_ms", "p99_ms", "galaxies_per_s")},
+                  "plain": {k: res[f"plain_at_{f}x"][k] for k in ("p50_ms", "p99_ms", "galaxies_per_s")}}
+        for f in (0.8, 1.2)},
+        "throughput_saturated": {"served": sat_served["galaxies_per_s"], "plain": sat_plain["galaxies_per_s"],
+                                 "ratio": sat_served["galaxies_per_s"] / sat_plain["galaxies_per_s"]}}
+    res = lead | res
     sides = pool["sides"][np.arange(n_req) % n_pool].astype(np.int64)
     res["h2d_bytes"] = int(np.sum(4 * sides ** 2) + n_req * (24 * a.chains + 40))
     res["d2h_bytes"] = int(n_req * (29 * a.chains * a.n_samples + 40 * a.chains + 4))

@@ -210,6 +210,24 @@ typedef struct {
                                      exponential profile, one exposure, no
                                      noise_corr, max_side <= 63 and at most 4
                                      chains (shared memory). */
+    const float *pixel_prec;      /* NULL, or device float: a general pixel
+                                     covariance Sigma (Appendix C,
+                                     Eq. covar-pixel-likelihood: spatially
+                                     variable and correlated at once) given as
+                                     its precision P = Sigma^-1, which
+                                     bs_dense_precision computes: galaxy n's
+                                     block [N^2][N^2] (pixels iy N + ix,
+                                     symmetric) starts at prec_offsets[n];
+                                     log L = -1/2 (d - m)^T P (d - m) and
+                                     noise_sigma is not used.  Each evaluation
+                                     renders the model image, multiplies the
+                                     residual by P (N^4 multiply-adds, P read
+                                     from L2) and transforms the product back.
+                                     Requires the exponential profile, one
+                                     exposure, no noise_corr or pixel_weight,
+                                     max_side <= 31 and at most 4 chains. */
+    const int64_t *prec_offsets;  /* device [n_gal]: float offset of each
+                                     galaxy's block (with pixel_prec) */
 } bs_fit_args;
 
 enum { BS_PROFILE_EXPONENTIAL = 0, BS_PROFILE_SPERGEL = 1, BS_PROFILE_GAUSSIAN = 2 };
@@ -245,6 +263,26 @@ typedef struct {
     float *warmup_accept_stat;
     float *warmup_step_size;
 } bs_fit_out;
+
+/* The precision matrices P = Sigma^-1 of general pixel covariances (Appendix
+ * C, Eq. covar-pixel-likelihood), once per galaxy, for bs_fit_args.pixel_prec:
+ * in FP64 on the device, by the Cholesky factor L of Sigma, W = L^-1 and
+ * P = W^T W, stored as FP32.
+ *   side    device int32 [n_gal] (odd, 3..max_side);
+ *   cov     device float: galaxy n's Sigma, [N^2][N^2] row-major over pixels
+ *           iy N + ix, at cov_offsets[n] (device int64 [n_gal]);
+ *   prec    device float, the same layout (may not alias cov);
+ *   status  device int32 [n_gal] or NULL: set to 3 where Sigma is not
+ *           positive definite (that block of prec is zeroed), to 2 where the
+ *           side is not odd in 3..max_side (that block is not written);
+ *           other entries are left unchanged.
+ * max_side <= 31.  Workspace: bs_dense_precision_workspace_bytes(max_side)
+ * (an FP64 scratch of 2 max_side^4 doubles per SM).  About N^6 / 2 FP64
+ * multiply-adds per galaxy.  Asynchronous on `stream`. */
+size_t bs_dense_precision_workspace_bytes(int32_t max_side);
+bs_status bs_dense_precision(int32_t n_gal, const int32_t *side, int32_t max_side, const float *cov,
+                             const int64_t *cov_offsets, float *prec, int32_t *status, void *workspace,
+                             size_t workspace_bytes, void *stream);
 
 /* Bytes of device workspace bs_fit_galaxies needs (a work-queue counter). */
 size_t bs_fit_workspace_bytes(const bs_fit_args *args);

@@ -28,7 +28,8 @@ EXPORTED = ["bs_prior_default", "bs_last_error", "bs_version", "bs_render", "bs_
             "bs_fit_resident_galaxies", "bs_fit_plan_num_launches", "bs_fit_plan_info", "bs_serve_request_bytes", "bs_serve_create", "bs_serve_submit",
             "bs_serve_poll", "bs_serve_get_stats", "bs_serve_now_ns", "bs_serve_destroy",
             "bs_shear_hyperprior_default", "bs_shear_sample", "bs_fp32_peak", "bs_fp64_peak", "bs_shear_loglike_multi",
-            "bs_kernel_launches", "bs_shear_bias", "bs_shear_bias_custom", "bs_shear_estimate_custom"]
+            "bs_kernel_launches", "bs_shear_bias", "bs_shear_bias_custom", "bs_shear_estimate_custom",
+            "bs_dense_precision", "bs_dense_precision_workspace_bytes"]
 
 
 class BsError(RuntimeError):
@@ -56,7 +57,8 @@ class FitArgs(C.Structure):
                 ("jitter", C.c_float), ("adapt_mass", C.c_int32), ("random_steps", C.c_int32),
                 ("seed", C.c_uint64), ("init_step_size", C.c_void_p), ("init_inv_mass", C.c_void_p),
                 ("registers", C.c_int32), ("n_exposures", C.c_int32), ("noise_corr", C.c_void_p),
-                ("profile", C.c_int32), ("spergel_nu", C.c_float), ("pixel_weight", C.c_void_p)]
+                ("profile", C.c_int32), ("spergel_nu", C.c_float), ("pixel_weight", C.c_void_p),
+                ("pixel_prec", C.c_void_p), ("prec_offsets", C.c_void_p)]
 
 
 class FitOut(C.Structure):
@@ -202,6 +204,9 @@ def lib():
     L.bs_shear_hyperprior_default.restype = None
     L.bs_shear_sample.argtypes = [C.POINTER(ShearData), C.POINTER(ShearSampleCfg), vp, vp, vp, vp, vp, sz, vp]
     L.bs_shear_bias_custom.argtypes = [i64, G_ESTIMATOR_FN, vp, G_ESTIMATOR_FN, vp, C.POINTER(BiasCfg), vp]
+    L.bs_dense_precision_workspace_bytes.argtypes = [i32]
+    L.bs_dense_precision_workspace_bytes.restype = sz
+    L.bs_dense_precision.argtypes = [i32, vp, i32, vp, vp, vp, vp, vp, sz, vp]
     L.bs_shear_estimate_custom.argtypes = [LOGLIKE_POINTS_FN, vp, C.POINTER(EstimateCfg), vp, vp, vp]
     L.bs_shear_bias.argtypes = [C.POINTER(ShearData), C.POINTER(ShearData), i32, C.POINTER(EstimateCfg),
                                 C.POINTER(ShearSampleCfg), C.POINTER(BiasCfg), vp, vp, vp, sz, vp]

@@ -101,7 +101,7 @@ class FitPlan:
 
     def __init__(self, data, offsets, side, psf, noise_sigma, init, cfg: FitConfig, *, gal_id=None,
                  max_side=None, init_step_size=None, init_inv_mass=None, registers=0, n_exposures=1,
-                 noise_corr=None, pixel_weight=None,
+                 noise_corr=None, pixel_weight=None, pixel_prec=None, prec_offsets=None,
                  want=("logp", "accept_rate", "step_size", "inv_mass", "n_div", "status", "n_grad")):
         """init_step_size [n_gal, C] / init_inv_mass [n_gal, C, 6] (optional):
         resume adapted chains (no initial step-size search).  registers: the
@@ -111,15 +111,17 @@ class FitPlan:
         offset, psf has n_gal * J entries (or one), noise_sigma n_gal * J;
         noise_corr (float32, layout of data): per-exposure noise correlation
         at pixel lag, centred; pixel_weight (float32, layout of data):
-        per-pixel inverse-variance factors, 0 masks a pixel (Appendix C)."""
+        per-pixel inverse-variance factors, 0 masks a pixel (Appendix C);
+        pixel_prec, prec_offsets: a general pixel covariance as its precision
+        matrices (dense_precision), Appendix C."""
         _need_cuda(data, offsets, side, noise_sigma, init, gal_id, init_step_size, init_inv_mass, noise_corr,
-                   pixel_weight)
+                   pixel_weight, pixel_prec, prec_offsets)
         dev = data.device
         n_gal, n_chains = init.shape[0], init.shape[1]
         assert n_chains == cfg.n_chains, "init must be [n_gal, n_chains, 6]"
         self.cfg = cfg
         self.keep = (data, offsets, side, psf, noise_sigma, init, gal_id, init_step_size, init_inv_mass, noise_corr,
-                     pixel_weight)
+                     pixel_weight, pixel_prec, prec_offsets)
         table, n_psf = psf
         a = F.FitArgs()
         a.n_gal = n_gal
@@ -152,6 +154,8 @@ class FitPlan:
         a.profile = int(cfg.profile)
         a.spergel_nu = float(cfg.spergel_nu)
         a.pixel_weight = _p(pixel_weight)
+        a.pixel_prec = _p(pixel_prec)
+        a.prec_offsets = _p(prec_offsets)
         self.args = a
         S, Cn = cfg.n_samples, cfg.n_chains
         f32 = dict(dtype=torch.float32, device=dev)
@@ -388,11 +392,12 @@ def fit_galaxies(data, offsets, side, psf, noise_sigma, init, cfg: FitConfig | N
 
 def logpost_points(data, offsets, side, psf, noise_sigma, gal_index, theta, *, max_side=None,
                    pixel_scale=PIXEL_SCALE, prior=DEFAULT_PRIOR, n_exposures=1, noise_corr=None, profile=0,
-                   spergel_nu=0.5, pixel_weight=None):
+                   spergel_nu=0.5, pixel_weight=None, pixel_prec=None, prec_offsets=None):
     """Log posterior (float64) and gradient (float32) at points theta [n, 6]
-    (n_exposures, noise_corr as in FitPlan; profile, spergel_nu as in
-    FitConfig)."""
-    _need_cuda(data, offsets, side, noise_sigma, gal_index, theta, noise_corr, pixel_weight)
+    (n_exposures, noise_corr, pixel_weight, pixel_prec, prec_offsets as in
+    FitPlan; profile, spergel_nu as in FitConfig)."""
+    _need_cuda(data, offsets, side, noise_sigma, gal_index, theta, noise_corr, pixel_weight, pixel_prec,
+               prec_offsets)
     table, n_psf = psf
     a = F.FitArgs()
     a.n_gal = int(side.shape[0])
@@ -411,12 +416,32 @@ def logpost_points(data, offsets, side, psf, noise_sigma, gal_index, theta, *, m
     a.profile = int(profile)
     a.spergel_nu = float(spergel_nu)
     a.pixel_weight = _p(pixel_weight)
+    a.pixel_prec = _p(pixel_prec)
+    a.prec_offsets = _p(prec_offsets)
     n = theta.shape[0]
     lp = torch.empty(n, dtype=torch.float64, device=theta.device)
     g = torch.empty((n, 6), dtype=torch.float32, device=theta.device)
     F.check(F.lib().bs_logpost_points(C.byref(a), n, _p(gal_index), _p(theta.contiguous()), _p(lp),
                                       _p(g), _stream()))
     return lp, g
+
+
+def dense_precision(cov, cov_offsets, side, max_side=None):
+    """Precision matrices Sigma^-1 of general pixel covariances
+    (bs_dense_precision; Appendix C): cov float32 CUDA, galaxy n's
+    [N^2, N^2] block at cov_offsets[n] (int64 CUDA), side int32 CUDA.
+    Returns (prec in the same layout, status int32 [n_gal]: 3 where Sigma is
+    not positive definite)."""
+    _need_cuda(cov, cov_offsets, side)
+    n_gal = int(side.shape[0])
+    ms = int(max_side or int(side.max().item()))
+    prec = torch.empty_like(cov)
+    status = torch.zeros(n_gal, dtype=torch.int32, device=cov.device)
+    wsb = F.lib().bs_dense_precision_workspace_bytes(ms)
+    ws = torch.empty(max(int(wsb), 1), dtype=torch.uint8, device=cov.device)
+    F.check(F.lib().bs_dense_precision(n_gal, _p(side), ms, _p(cov.contiguous()), _p(cov_offsets), _p(prec),
+                                       _p(status), _p(ws), wsb, _stream()))
+    return prec, status
 
 
 def chain_ess(samples):

@@ -191,7 +191,18 @@ static bs_status fill_fit_params(const bs_fit_args *a, bs::FitParams &p, const c
     p.prof_npow = a->profile == BS_PROFILE_SPERGEL ? -(1.0f + a->spergel_nu) : -1.5f;
     p.inv_hlr_r0 = (float)(1.0 / bs::profile_hlr_over_r0(a->profile, a->spergel_nu));
     p.pix_w = a->pixel_weight;
-    if (a->pixel_weight) {
+    p.pix_prec = a->pixel_prec;
+    p.prec_offs = a->prec_offsets;
+    if (a->pixel_prec) {
+        if (a->pixel_weight || !a->prec_offsets)
+            return fail(BS_ERR_INVALID_ARG, "%s: pixel_prec needs prec_offsets and no pixel_weight", who);
+        if (a->profile != BS_PROFILE_EXPONENTIAL || a->n_exposures > 1 || a->noise_corr)
+            return fail(BS_ERR_INVALID_ARG,
+                        "%s: pixel_prec needs the exponential profile, one exposure and no noise_corr", who);
+        if (a->max_side > bs::kDenseMaxSide)
+            return fail(BS_ERR_INVALID_ARG, "%s: pixel_prec needs max_side <= %d", who, bs::kDenseMaxSide);
+        p.profile = 4;
+    } else if (a->pixel_weight) {
         if (a->profile != BS_PROFILE_EXPONENTIAL || n_exp > 1 || a->noise_corr)
             return fail(BS_ERR_INVALID_ARG,
                         "%s: pixel_weight needs the exponential profile, one exposure and no noise_corr", who);
@@ -232,7 +243,7 @@ bs_status fit_params_from_args(const bs_fit_args *a, const bs_fit_out *o, FitPar
     if (!o) return fail(BS_ERR_INVALID_ARG, "%s: NULL outputs", who);
     if (a->n_gal > 0 && !o->samples) return fail(BS_ERR_INVALID_ARG, "%s: NULL samples output", who);
     if (a->n_gal > 0 && !a->init) return fail(BS_ERR_INVALID_ARG, "%s: NULL init", who);
-    if (p.profile == 3 && a->n_chains > 4)
+    if ((p.profile == 3 || p.profile == 4) && a->n_chains > 4)
         return fail(BS_ERR_INVALID_ARG, "%s: pixel_weight allows at most 4 chains", who);
     if (a->n_chains < 1 || a->n_chains > bs::kMaxChains)
         return fail(BS_ERR_INVALID_ARG, "%s: n_chains must be 1..%d", who, bs::kMaxChains);

@@ -107,20 +107,25 @@ __device__ __forceinline__ SmemView smem_view(unsigned char *base, int h_max, in
     return v;
 }
 
-// Spatially variable noise (Appendix C, per-pixel weights; kernel instance
-// PROF 3): after the shared region, the twiddles exp(+2 pi i m / N) (max_side
-// float2) and, per chain, a private copy of the table ([h_max][3 npad]: the D
-// slots hold the evaluation's effective spectrum, the T slots the transfer),
-// the half-transformed image ([h_max][max_side] float2) and one pixel row (64
-// floats).  Sizes in floats, each chain's block a multiple of 4 floats.
-__host__ __device__ __forceinline__ int pix_chain_floats(int h_max, int npad, int max_side)
+// Pixel-space noise models (Appendix C; kernel instance PROF 3): per-pixel
+// weights, or a general covariance given as its precision matrix.  After the
+// shared region, the twiddles exp(+2 pi i m / N) (max_side float2) and, per
+// chain, a private copy of the table ([h_max][3 npad]: the D slots hold the
+// evaluation's effective spectrum, the T slots the transfer), the
+// half-transformed image ([h_max][max_side] float2), one pixel row (64
+// floats) and, with a covariance, the residual image and its product with
+// the precision (max_side^2 floats each).  Sizes in floats, each chain's
+// block a multiple of 4 floats.
+__host__ __device__ __forceinline__ int pix_chain_floats(int h_max, int npad, int max_side, bool dense)
 {
-    const int n = h_max * row_floats(npad) + 2 * h_max * max_side + 64;
+    const int n = h_max * row_floats(npad) + 2 * h_max * max_side + 64 + (dense ? 2 * max_side * max_side : 0);
     return (n + 3) & ~3;
 }
-__host__ __device__ __forceinline__ size_t pix_region_bytes(int h_max, int npad, int max_side, int n_chains)
+__host__ __device__ __forceinline__ size_t pix_region_bytes(int h_max, int npad, int max_side, int n_chains,
+                                                            bool dense)
 {
-    return ((size_t)2 * ((max_side + 1) & ~1) + (size_t)n_chains * pix_chain_floats(h_max, npad, max_side)) *
+    return ((size_t)2 * ((max_side + 1) & ~1) +
+            (size_t)n_chains * pix_chain_floats(h_max, npad, max_side, dense)) *
            sizeof(float);
 }
 struct PixView {
@@ -128,17 +133,21 @@ struct PixView {
     float *tab;    // this chain's table
     float2 *G;     // [h_max][max_side]
     float *row;    // [64]
+    float *rb;     // [max_side^2] residual d - m (covariance only)
+    float *yb;     // [max_side^2] precision x residual (covariance only)
 };
 // kxr ends at h_max + 1 float2 after its start; the region follows, 16-byte aligned.
-__device__ __forceinline__ PixView pix_view(float2 *kxr, int h_max, int npad, int max_side, int chain)
+__device__ __forceinline__ PixView pix_view(float2 *kxr, int h_max, int npad, int max_side, int chain, bool dense)
 {
     float *base = reinterpret_cast<float *>(kxr + ((h_max + 2) & ~1));
     PixView v;
     v.tw = reinterpret_cast<float2 *>(base);
-    float *c0 = base + 2 * ((max_side + 1) & ~1) + (size_t)chain * pix_chain_floats(h_max, npad, max_side);
+    float *c0 = base + 2 * ((max_side + 1) & ~1) + (size_t)chain * pix_chain_floats(h_max, npad, max_side, dense);
     v.tab = c0;
     v.G = reinterpret_cast<float2 *>(c0 + (size_t)h_max * row_floats(npad));
     v.row = reinterpret_cast<float *>(v.G + (size_t)h_max * max_side);
+    v.rb = v.row + 64;
+    v.yb = v.rb + max_side * max_side;
     return v;
 }
 
@@ -397,7 +406,7 @@ __device__ bool setup_galaxy(const FitParams &P, int gal, const SmemView &sm, Ga
     if (P.n_exp > 1 || P.noise_corr) return setup_folded(P, gal, sm, gc);
 
     const float sig = P.sigma[gal];
-    gc.inv_b = 1.0f / (sig * sig);
+    gc.inv_b = P.pix_prec ? 1.0f : 1.0f / (sig * sig);   // a covariance carries the noise level
     const int64_t off = P.offsets[gal];
     const bs_psf ps = P.psf[P.n_psf == 1 ? 0 : gal];
     const float sqrt2 = 1.41421356237309515f;
@@ -851,7 +860,7 @@ __device__ __forceinline__ double eval_logpost(const FitParams &P, const GalCtx 
 __device__ void pix_setup(const FitParams &P, const GalCtx &gc, const SmemView &sm, int n_tables)
 {
     const int tid = threadIdx.x, nth = blockDim.x;
-    const PixView p0 = pix_view(sm.kxr, P.h_max, P.npad, P.max_side, 0);
+    const PixView p0 = pix_view(sm.kxr, P.h_max, P.npad, P.max_side, 0, P.pix_prec != nullptr);
     for (int m = tid; m < gc.N; m += nth) {
         float s, co;
         sincospif(2.0f * (float)m * gc.invN, &s, &co);
@@ -860,7 +869,7 @@ __device__ void pix_setup(const FitParams &P, const GalCtx &gc, const SmemView &
     const int rowf = row_floats(P.npad);
     const int nrow = gc.H * rowf;
     for (int t = 0; t < n_tables; ++t) {
-        float *dst = pix_view(sm.kxr, P.h_max, P.npad, P.max_side, t).tab;
+        float *dst = pix_view(sm.kxr, P.h_max, P.npad, P.max_side, t, P.pix_prec != nullptr).tab;
         for (int i = tid; i < nrow; i += nth) dst[i] = sm.tab[i];
     }
     __syncthreads();
@@ -948,10 +957,28 @@ __device__ double eval_pix(const FitParams &P, const GalCtx &gc, const PixView &
             if (lane + 32 * r < N) grow[lane + 32 * r] = res[r];
         __syncwarp();
     }
-    // (b2) per pixel row: m(ix, iy), r = w (d - m), then Q(u, iy) = sum_ix r exp(-2 pi i u (ix - c) / N)
+    // (b2) per pixel row: m(ix, iy), r = w (d - m), then Q(u, iy) = sum_ix r exp(-2 pi i u (ix - c) / N);
+    // with a covariance, r = Sigma^-1 (d - m) needs every row of d - m first
     const int64_t off = P.offsets[gal];
     const float invN2 = gc.invN * gc.invN;
+    const bool dense = P.pix_prec != nullptr;
     double chi = 0.0;
+    auto row_forward = [&](const float *rrow, int iy) {
+        for (int u = lane; u < H; u += 32) {
+            float re = 0.f, im = 0.f;
+            int k = ((u * c) % N + N) % N;               // -u (ix - c) at ix = 0
+            const int dk = (N - u % N) % N;
+            for (int ix = 0; ix < N; ++ix) {
+                const float r = rrow[ix];
+                const float2 t = pv.tw[k];
+                re = fmaf(r, t.x, re);
+                im = fmaf(r, t.y, im);
+                k += dk;
+                if (k >= N) k -= N;
+            }
+            pv.G[(size_t)u * N + iy] = make_float2(re, im);
+        }
+    };
     for (int iy = 0; iy < N; ++iy) {
         for (int ix = lane; ix < N; ix += 32) {
             const int dk = ((ix - c) % N + N) % N;      // u (ix - c) mod N, advanced per u
@@ -967,25 +994,47 @@ __device__ double eval_pix(const FitParams &P, const GalCtx &gc, const PixView &
             const float m = acc * invN2;
             const int64_t idx = off + (int64_t)iy * N + ix;
             const float res = load_pix(P.data, P.data_f64, idx) - m;
-            const float r = __ldg(P.pix_w + idx) * res;
-            chi += (double)(r * res);
-            pv.row[ix] = r;
+            if (dense) {
+                pv.rb[iy * N + ix] = res;
+            } else {
+                const float r = __ldg(P.pix_w + idx) * res;
+                chi += (double)(r * res);
+                pv.row[ix] = r;
+            }
         }
         __syncwarp();
-        for (int u = lane; u < H; u += 32) {
-            float re = 0.f, im = 0.f;
-            int k = ((u * c) % N + N) % N;               // -u (ix - c) at ix = 0
-            const int dk = (N - u % N) % N;
-            for (int ix = 0; ix < N; ++ix) {
-                const float r = pv.row[ix];
-                const float2 t = pv.tw[k];
-                re = fmaf(r, t.x, re);
-                im = fmaf(r, t.y, im);
-                k += dk;
-                if (k >= N) k -= N;
+        if (!dense) row_forward(pv.row, iy);
+        __syncwarp();
+    }
+    if (dense) {
+        // y = Sigma^-1 r: the precision is symmetric, so y_a = sum_b P[b][a] r_b with
+        // lanes over a reads each row b of it coalesced (from L2: tens of
+        // evaluations of the galaxy's chains share it); chi^2 = r.y
+        constexpr int kSlots = (kDenseMaxSide * kDenseMaxSide + 31) / 32;
+        const int n = N * N;
+        const float *Pg = P.pix_prec + P.prec_offs[gal];
+        float yv[kSlots];
+#pragma unroll
+        for (int j = 0; j < kSlots; ++j) yv[j] = 0.f;
+        for (int b = 0; b < n; ++b) {
+            const float rb = pv.rb[b];
+            const float *prow = Pg + (size_t)b * n;
+#pragma unroll
+            for (int j = 0; j < kSlots; ++j) {
+                const int a = lane + 32 * j;
+                if (a < n) yv[j] = fmaf(__ldg(prow + a), rb, yv[j]);
             }
-            pv.G[(size_t)u * N + iy] = make_float2(re, im);
         }
+#pragma unroll
+        for (int j = 0; j < kSlots; ++j) {
+            const int a = lane + 32 * j;
+            if (a < n) {
+                pv.yb[a] = yv[j];
+                chi += (double)pv.rb[a] * (double)yv[j];
+            }
+        }
+        __syncwarp();
+        for (int iy = 0; iy < N; ++iy) row_forward(pv.yb + iy * N, iy);
         __syncwarp();
     }
     // (b3) D' = Mt + scale_u R(u, v), R(u, v) = sum_iy Q(u, iy) exp(-2 pi i v (iy - c) / N);
@@ -1127,7 +1176,8 @@ __device__ void run_chain(const FitParams &P, const GalCtx &gc, const SmemView &
             double v;
             float2 *xph_c = sm.xph + (size_t)chain * phase_stride(P.h_max);
             if constexpr (PROF == 3)
-                v = eval_pix<NC>(P, gc, pix_view(sm.kxr, P.h_max, P.npad, P.max_side, chain), gal, sm.kxr, xph_c,
+                v = eval_pix<NC>(P, gc, pix_view(sm.kxr, P.h_max, P.npad, P.max_side, chain, P.pix_prec != nullptr),
+                                 gal, sm.kxr, xph_c,
                                  vcol, x, gg, l == nst - 1);
             else
                 v = eval_logpost<NC, PROF>(P, gc, sm.tab, sm.kxr, xph_c, vcol, x, gg, l == nst - 1);
@@ -1355,7 +1405,8 @@ __device__ void point_eval(const FitParams &P, const GalCtx &gc, const SmemView 
     double v = -INFINITY;
     if (in_support(P, th)) {
         if constexpr (PROF == 3)
-            v = eval_pix<NC>(P, gc, pix_view(sm.kxr, P.h_max, P.npad, P.max_side, 0), gal, sm.kxr, sm.xph, vcol, th,
+            v = eval_pix<NC>(P, gc, pix_view(sm.kxr, P.h_max, P.npad, P.max_side, 0, P.pix_prec != nullptr), gal,
+                             sm.kxr, sm.xph, vcol, th,
                              g, true);
         else
             v = eval_logpost<NC, PROF>(P, gc, sm.tab, sm.kxr, sm.xph, vcol, th, g, true);

@@ -23,7 +23,8 @@ FitKernel prof_kernel(int max_side)
     }
 }
 
-// Per-pixel weights (profile 3, exponential): stamps of at most 63 px.
+// Per-pixel weights (profile 3) or a dense covariance (profile 4, the same
+// instance; at most 31 px), exponential: stamps of at most 63 px.
 FitKernel pix_kernel(int max_side)
 {
     return max_side <= 31 ? fit_kernel_r128<1, 3> : fit_kernel_r128<2, 3>;
@@ -31,13 +32,13 @@ FitKernel pix_kernel(int max_side)
 
 FitKernel kernel_for(int profile, int max_side)
 {
-    if (profile == 3) return pix_kernel(max_side);
+    if (profile == 3 || profile == 4) return pix_kernel(max_side);
     return profile == BS_PROFILE_SPERGEL ? prof_kernel<1>(max_side) : prof_kernel<2>(max_side);
 }
 
 PointsKernel points_for(int profile)
 {
-    if (profile == 3) return logpost_points_kernel<3>;
+    if (profile == 3 || profile == 4) return logpost_points_kernel<3>;
     return profile == BS_PROFILE_SPERGEL ? logpost_points_kernel<1> : logpost_points_kernel<2>;
 }
 
@@ -46,9 +47,9 @@ PointsKernel points_for(int profile)
 size_t smem_for(int profile, int max_side, int n_chains)
 {
     size_t b = fit_smem_bytes(max_side, n_chains);
-    if (profile == 3) {
+    if (profile == 3 || profile == 4) {
         const int h = (max_side + 1) / 2, npad = 32 * ((max_side + 31) / 32);
-        b += 16 + pix_region_bytes(h, npad, max_side, n_chains);
+        b += 16 + pix_region_bytes(h, npad, max_side, n_chains, profile == 4);
     }
     return b;
 }

@@ -10,6 +10,7 @@ namespace bs {
 
 constexpr int kMaxChains = 8;
 constexpr int kMaxWindows = 24;
+constexpr int kDenseMaxSide = 31;   // largest stamp with a general pixel covariance
 
 // Everything one fit launch needs, filled by the C-ABI layer.
 struct FitParams {
@@ -28,6 +29,8 @@ struct FitParams {
     float prof_npow;           // -(1 + nu) (Spergel)
     float inv_hlr_r0;          // r0 / hlr of the profile
     const float *pix_w;        // per-pixel weights (layout of data) or NULL; profile 3 when set
+    const float *pix_prec;     // per-galaxy precision Sigma^-1 [N^2][N^2] at prec_offs[gal], or NULL;
+    const int64_t *prec_offs;  // profile 4 when set (the pixel-space kernel with a dense covariance)
     const uint64_t *gal_id;
     const float *init;
     const float *init_step;
