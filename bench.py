@@ -213,9 +213,9 @@ CAPTURED_TRAFFIC = {
     # 53x53 galaxy of the plain workload: (13,925,888 + 7,424) B / 1,216 galaxies
     "fit": ("paper_2604_22048_gb300/csrc/bs_fit_impl.cuh",
             "fac4c852b2dffa6918a2498ce0d1fa6e10a205ed8b6e2a958882df1a8b7fc176", 11458.3),
-    # one interim sample of the shear workload: (489,382,400 + 3,253,248) B / (200,000 x 300)
+    # one interim sample of the shear workload: (489,468,416 + 3,221,248) B / (200,000 x 300)
     "shear": ("paper_2604_22048_gb300/csrc/bs_shear.cu",
-              "b4890a1fdfa8e5daa61ed60ed9961e71679d96605796c19047562104d32f052d", 8.2106),
+              "d664605cb7387c74c2607a07146e84be989c00e4134f73773bdafca158c849a5", 8.2115),
 }
 
 

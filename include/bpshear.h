@@ -228,6 +228,14 @@ typedef struct {
                                      max_side <= 31 and at most 4 chains. */
     const int64_t *prec_offsets;  /* device [n_gal]: float offset of each
                                      galaxy's block (with pixel_prec) */
+    int32_t chains_per_cta;       /* launch layout: 0 (all of a galaxy's chains
+                                     in one CTA) or a divisor of n_chains below
+                                     it (the chains split over several CTAs,
+                                     each staging the galaxy); the same results
+                                     either way.  Nonzero only for the
+                                     exponential profile with one exposure and
+                                     white noise.  The ragged plan's autotuner
+                                     chooses it itself. */
 } bs_fit_args;
 
 enum { BS_PROFILE_EXPONENTIAL = 0, BS_PROFILE_SPERGEL = 1, BS_PROFILE_GAUSSIAN = 2 };
@@ -344,8 +352,15 @@ typedef struct {
     int32_t max_side;        /* largest stamp of the class */
     int32_t n_gal;           /* galaxies in the class */
     int32_t grid;            /* persistent CTAs */
-    int32_t registers;       /* register cap of the kernel instance: 128, 96 or 80 */
+    int32_t registers;       /* register cap of the kernel instance: 128, 96 or 80
+                                (the same results with each) */
     float trial_ms_128, trial_ms_96, trial_ms_80;  /* autotune trial times (0 if not tuned) */
+    int32_t chains_per_cta;  /* layout: warps (chains) per CTA; below n_chains a
+                                galaxy's chains are split over several CTAs,
+                                each staging the galaxy */
+    float trial_ms_128_half, trial_ms_96_half, trial_ms_80_half;  /* trial
+                                times with half the chains per CTA (0 if that
+                                layout was not a candidate) */
 } bs_fit_plan_launch_info;
 int32_t bs_fit_plan_num_launches(bs_fit_plan plan);
 bs_status bs_fit_plan_info(bs_fit_plan plan, int32_t i, bs_fit_plan_launch_info *info);

@@ -58,7 +58,7 @@ class FitArgs(C.Structure):
                 ("seed", C.c_uint64), ("init_step_size", C.c_void_p), ("init_inv_mass", C.c_void_p),
                 ("registers", C.c_int32), ("n_exposures", C.c_int32), ("noise_corr", C.c_void_p),
                 ("profile", C.c_int32), ("spergel_nu", C.c_float), ("pixel_weight", C.c_void_p),
-                ("pixel_prec", C.c_void_p), ("prec_offsets", C.c_void_p)]
+                ("pixel_prec", C.c_void_p), ("prec_offsets", C.c_void_p), ("chains_per_cta", C.c_int32)]
 
 
 class FitOut(C.Structure):
@@ -101,7 +101,8 @@ BS_PLAN_CAPTURE, BS_PLAN_AUTOTUNE = 1, 2
 class PlanLaunchInfo(C.Structure):
     _fields_ = [("slot_class", C.c_int32), ("max_side", C.c_int32), ("n_gal", C.c_int32), ("grid", C.c_int32),
                 ("registers", C.c_int32), ("trial_ms_128", C.c_float), ("trial_ms_96", C.c_float),
-                ("trial_ms_80", C.c_float)]
+                ("trial_ms_80", C.c_float), ("chains_per_cta", C.c_int32), ("trial_ms_128_half", C.c_float),
+                ("trial_ms_96_half", C.c_float), ("trial_ms_80_half", C.c_float)]
 
 
 class ServeCfg(C.Structure):

@@ -101,7 +101,7 @@ class FitPlan:
 
     def __init__(self, data, offsets, side, psf, noise_sigma, init, cfg: FitConfig, *, gal_id=None,
                  max_side=None, init_step_size=None, init_inv_mass=None, registers=0, n_exposures=1,
-                 noise_corr=None, pixel_weight=None, pixel_prec=None, prec_offsets=None,
+                 noise_corr=None, pixel_weight=None, pixel_prec=None, prec_offsets=None, chains_per_cta=0,
                  want=("logp", "accept_rate", "step_size", "inv_mass", "n_div", "status", "n_grad")):
         """init_step_size [n_gal, C] / init_inv_mass [n_gal, C, 6] (optional):
         resume adapted chains (no initial step-size search).  registers: the
@@ -156,6 +156,7 @@ class FitPlan:
         a.pixel_weight = _p(pixel_weight)
         a.pixel_prec = _p(pixel_prec)
         a.prec_offsets = _p(prec_offsets)
+        a.chains_per_cta = int(chains_per_cta)
         self.args = a
         S, Cn = cfg.n_samples, cfg.n_chains
         f32 = dict(dtype=torch.float32, device=dev)

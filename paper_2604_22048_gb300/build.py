@@ -41,7 +41,11 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
     if not force and not _stale():
         return LIB
     cc = nvcc()
-    flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE,
+    # -fmad=false: only the multiply-adds the source writes (fmaf, the packed
+    # intrinsics) are fused, so the fit kernel's register budgets and layouts,
+    # compiled with different register pressure, round every operation alike
+    # and give the same chains bit for bit
+    flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC", "-I", INCLUDE,
                     "-Xptxas", "-v" if verbose else "-O3"] + list(extra_flags or [])
     tmpdir = tempfile.mkdtemp(prefix="bpshear_build_", dir=CSRC)
     try:

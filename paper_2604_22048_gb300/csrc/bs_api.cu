@@ -227,6 +227,14 @@ static bs_status fill_fit_params(const bs_fit_args *a, bs::FitParams &p, const c
     p.max_side = a->max_side;
     p.h_max = (a->max_side + 1) / 2;
     p.npad = 32 * ((a->max_side + 31) / 32);
+    if (a->chains_per_cta != 0) {
+        if (a->chains_per_cta < 1 || a->chains_per_cta >= a->n_chains || a->n_chains % a->chains_per_cta != 0)
+            return fail(BS_ERR_INVALID_ARG, "%s: chains_per_cta must be 0 or a divisor of n_chains below it", who);
+        if (p.profile != 0 || n_exp > 1 || a->noise_corr)
+            return fail(BS_ERR_INVALID_ARG,
+                        "%s: chains_per_cta needs the exponential profile, one exposure and white noise", who);
+        p.cpc = a->chains_per_cta;
+    }
     return BS_OK;
 }
 
@@ -308,9 +316,10 @@ bs_status bs_fit_galaxies(const bs_fit_args *a, const bs_fit_out *o, void *works
     int dev = 0, sms = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int per_sm = bs::fit_blocks_per_sm(a->n_chains, a->max_side, p.regs, p.profile);
+    const int per_sm = bs::fit_blocks_per_sm(bs::cta_chains(p), a->max_side, p.regs, p.profile);
     long long grid = (long long)sms * per_sm;
-    if (grid > a->n_gal) grid = a->n_gal;
+    const long long items = (long long)a->n_gal * (a->n_chains / bs::cta_chains(p));
+    if (grid > items) grid = items;
     e = bs::launch_fit(p, (int)grid, s);
     return e == cudaSuccess ? BS_OK : cuda_fail(e, "bs_fit_galaxies: launch");
 }

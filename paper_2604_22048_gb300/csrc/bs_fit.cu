@@ -59,11 +59,12 @@ int fit_blocks_per_sm(int n_chains, int max_side, int regs, int profile)
 cudaError_t launch_fit(const FitParams &p, int grid, cudaStream_t stream)
 {
     if (p.profile != 0) return launch_fit_profile(p, grid, stream);
-    const size_t smem = fit_smem_bytes(p.max_side, p.n_chains);
-    FitKernel k = fit_kernel_for(p.max_side, p.regs, p.n_chains);
+    const int cc = cta_chains(p);
+    const size_t smem = fit_smem_bytes(p.max_side, cc);
+    FitKernel k = fit_kernel_for(p.max_side, p.regs, cc);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k<<<grid, 32 * p.n_chains, smem, stream>>>(p);
+    k<<<grid, 32 * cc, smem, stream>>>(p);
     bs::count_launches(1);
     return cudaGetLastError();
 }

@@ -1087,9 +1087,55 @@ __device__ __forceinline__ double kinetic(float pm, float im, bool own)
 
 enum { MODE_INIT = 0, MODE_SEARCH = 1, MODE_STEP = 2 };
 
+// One trajectory of nst leapfrog steps from (tp, tpl, gp, pm) (updated in
+// place); lpp receives the log posterior at its end; returns false when it
+// leaves the prior support.  The warp of the CTA's `slot` uses that slot's
+// phase table.
+template <int NC, int PROF>
+__device__ __forceinline__ bool trajectory(const FitParams &P, const GalCtx &gc, const SmemView &sm, int gal,
+                                        int slot, float eps_use, int nst, float im, float &tp, float &tpl,
+                                        float &gp, float &pm, double &lpp, int &ngrad)
+{
+    const int lane = threadIdx.x & 31;
+    const int pi = lane < 6 ? lane : 5;
+    float vcol[NC];
+#pragma unroll
+    for (int j = 0; j < NC; ++j) vcol[j] = (float)(lane + 32 * j - gc.c);
+    float2 *xph_c = sm.xph + (size_t)slot * phase_stride(P.h_max);   // this warp's phase table
+    for (int l = 0; l < nst; ++l) {
+        const float he = 0.5f * eps_use;
+        pm = fmaf(he, gp, pm);
+        {
+            // compensated position update (hi, lo) += eps m p
+            const float d = fmaf(eps_use * im, pm, tpl);
+            float s, e;
+            two_sum(tp, d, s, e);
+            tp = s;
+            tpl = e;
+        }
+        float x[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) x[k] = __shfl_sync(BS_FULL_MASK, tp, k);
+        if (!in_support(P, x)) return false;
+        float gg[6];
+        double v;
+        if constexpr (PROF == 3)
+            v = eval_pix<NC>(P, gc, pix_view(sm.kxr, P.h_max, P.npad, P.max_side, slot, P.pix_prec != nullptr),
+                             gal, sm.kxr, xph_c, vcol, x, gg, l == nst - 1);
+        else
+            v = eval_logpost<NC, PROF>(P, gc, sm.tab, sm.kxr, xph_c, vcol, x, gg, l == nst - 1);
+        ++ngrad;
+        if (l == nst - 1) lpp = v;
+        gp = pick6(gg, pi);
+        pm = fmaf(he, gp, pm);
+    }
+    return true;
+}
+
+// Chain `chain` of galaxy gal, run by the warp of the CTA's `slot`.
 template <int NC, int PROF>
 __device__ void run_chain(const FitParams &P, const GalCtx &gc, const SmemView &sm, int gal,
-                          int chain)
+                          int chain, int slot)
 {
     const int lane = threadIdx.x & 31;
     const int pi = lane < 6 ? lane : 5;     // parameter of this lane (lanes 6.. shadow parameter 5)
@@ -1097,9 +1143,6 @@ __device__ void run_chain(const FitParams &P, const GalCtx &gc, const SmemView &
     const int C = P.n_chains, W = P.n_warmup, S = P.n_samples, L = P.n_leapfrog;
     const uint64_t gid = P.gal_id ? P.gal_id[gal] : (uint64_t)gal;
     const uint64_t key = gid * (uint64_t)C + (uint64_t)chain;
-    float vcol[NC];
-#pragma unroll
-    for (int j = 0; j < NC; ++j) vcol[j] = (float)(lane + 32 * j - gc.c);
 
     const size_t ci0 = (size_t)gal * C + chain;
     // this lane's parameter: position (hi, lo), gradient, inverse metric
@@ -1156,36 +1199,7 @@ __device__ void run_chain(const FitParams &P, const GalCtx &gc, const SmemView &
         const double H0 = -lp + kinetic(pm, im, own);
         float tp = th, tpl = thl, gp = g;
         double lpp = lp;
-        bool ok = true;
-        for (int l = 0; l < nst; ++l) {
-            const float he = 0.5f * eps_use;
-            pm = fmaf(he, gp, pm);
-            {
-                // compensated position update (hi, lo) += eps m p
-                const float d = fmaf(eps_use * im, pm, tpl);
-                float s, e;
-                two_sum(tp, d, s, e);
-                tp = s;
-                tpl = e;
-            }
-            float x[6];
-#pragma unroll
-            for (int k = 0; k < 6; ++k) x[k] = __shfl_sync(BS_FULL_MASK, tp, k);
-            if (!in_support(P, x)) { ok = false; break; }
-            float gg[6];
-            double v;
-            float2 *xph_c = sm.xph + (size_t)chain * phase_stride(P.h_max);
-            if constexpr (PROF == 3)
-                v = eval_pix<NC>(P, gc, pix_view(sm.kxr, P.h_max, P.npad, P.max_side, chain, P.pix_prec != nullptr),
-                                 gal, sm.kxr, xph_c,
-                                 vcol, x, gg, l == nst - 1);
-            else
-                v = eval_logpost<NC, PROF>(P, gc, sm.tab, sm.kxr, xph_c, vcol, x, gg, l == nst - 1);
-            ++ngrad;
-            if (l == nst - 1) lpp = v;
-            gp = pick6(gg, pi);
-            pm = fmaf(he, gp, pm);
-        }
+        bool ok = trajectory<NC, PROF>(P, gc, sm, gal, slot, eps_use, nst, im, tp, tpl, gp, pm, lpp, ngrad);
         if (mode == MODE_INIT) {
             th = tp;
             thl = tpl;
@@ -1339,20 +1353,26 @@ template <int NC, int PROF>
 __device__ __forceinline__ void fit_loop(const FitParams &P)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int s_gal;
-    const SmemView sm = smem_view(smem_raw, P.h_max, P.npad, P.max_side, P.n_chains);
+    __shared__ int s_gal, s_grp;
+    const int cc = cta_chains(P);              // chains of this CTA
+    const int groups = P.n_chains / cc;        // CTAs a galaxy's chains are split over
+    const SmemView sm = smem_view(smem_raw, P.h_max, P.npad, P.max_side, cc);
     const int warp = threadIdx.x >> 5;
     bool first = true;
     for (;;) {
         if (threadIdx.x == 0) {
+            s_grp = 0;
             if (P.done) {
                 // serving: galaxy blockIdx.x only, so that nothing of the
                 // launch's memory is touched after its completion flag
                 s_gal = first ? (int)blockIdx.x : -1;
             } else {
-                // positions in the work list (or galaxy indices when there is none)
+                // items (position in the work list, chain group), or galaxy
+                // indices when there is no list
                 const int q = (int)atomicAdd(P.queue, 1u);
-                s_gal = q < P.n_work ? (P.work ? P.work[q] : q) : -1;
+                const int wq = q / groups;
+                s_gal = q < P.n_work * groups ? (P.work ? P.work[wq] : wq) : -1;
+                s_grp = q - wq * groups;
             }
         }
         first = false;
@@ -1372,8 +1392,8 @@ __device__ __forceinline__ void fit_loop(const FitParams &P)
             if (P.done) publish_galaxy(P, gal);
             continue;
         }
-        if constexpr (PROF == 3) pix_setup(P, gc, sm, P.n_chains);
-        if (warp < P.n_chains) run_chain<NC, PROF>(P, gc, sm, gal, warp);
+        if constexpr (PROF == 3) pix_setup(P, gc, sm, cc);
+        if (warp < cc) run_chain<NC, PROF>(P, gc, sm, gal, s_grp * cc + warp, warp);
         __syncthreads();
         if (P.done) publish_galaxy(P, gal);
     }

@@ -100,11 +100,12 @@ int fit_blocks_per_sm_profile(int profile, int n_chains, int max_side)
 
 cudaError_t launch_fit_profile(const FitParams &p, int grid, cudaStream_t stream)
 {
-    const size_t smem = smem_for(p.profile, p.max_side, p.n_chains);
+    const int cc = cta_chains(p);
+    const size_t smem = smem_for(p.profile, p.max_side, cc);
     FitKernel k = kernel_for(p.profile, p.max_side);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k<<<grid, 32 * p.n_chains, smem, stream>>>(p);
+    k<<<grid, 32 * cc, smem, stream>>>(p);
     bs::count_launches(1);
     return cudaGetLastError();
 }

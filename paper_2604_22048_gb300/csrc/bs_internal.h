@@ -67,6 +67,8 @@ struct FitParams {
     unsigned int *queue;
     int max_side;
     int h_max, npad;   // shared-memory geometry for max_side
+    int cpc;           // chains per CTA (0: all n_chains): a galaxy's chains may be split
+                       // over n_chains / cpc CTAs, each staging the galaxy itself
     int regs;          // register cap of the kernel instance (128, 96 or 80;
                        // 0 = default)
     // serving: when `done` is set (host-mapped), each CTA copies its galaxy's
@@ -75,6 +77,9 @@ struct FitParams {
     uint32_t *done;
     long long pub_shift;
 };
+
+// Chains (warps) of one CTA of a fit launch.
+__host__ __device__ inline int cta_chains(const FitParams &p) { return p.cpc > 0 ? p.cpc : p.n_chains; }
 
 // Shared memory bytes per CTA for a given max stamp side and chains per galaxy.
 size_t fit_smem_bytes(int max_side, int n_chains);

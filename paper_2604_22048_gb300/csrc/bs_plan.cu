@@ -30,6 +30,7 @@ struct bs_fit_plan_s {
         unsigned int *queue;
         int slot_class;
         float trial_ms[3];   // autotune: time of the 128-, 96- and 80-register instance (0 = not timed)
+        float trial_half[3]; // the same instances with half the chains per CTA
     };
     std::vector<Launch> launches;
     cudaStream_t streams[4] = {};
@@ -84,8 +85,8 @@ cudaError_t time_variant(const bs_fit_plan_s::Launch &L, int regs, int n_trial, 
     bs::FitParams p = L.p;
     p.regs = regs;
     p.n_work = n_trial;
-    const int per_sm = bs::fit_blocks_per_sm(p.n_chains, p.max_side, regs, p.profile);
-    const int grid = std::min(n_trial, sms * per_sm);
+    const int per_sm = bs::fit_blocks_per_sm(bs::cta_chains(p), p.max_side, regs, p.profile);
+    const int grid = std::min(n_trial * (p.n_chains / bs::cta_chains(p)), sms * per_sm);
     cudaError_t e = cudaSuccess;
     for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
         e = cudaMemsetAsync(L.queue, 0, sizeof(unsigned int), st);
@@ -100,6 +101,14 @@ cudaError_t time_variant(const bs_fit_plan_s::Launch &L, int regs, int n_trial, 
 
 constexpr int kRegVariants[3] = {128, 96, 80};
 
+// Half the chains per CTA is a candidate layout where a CTA's results do not
+// depend on how many threads staged the galaxy: the one-exposure white-noise
+// spectral path of the exponential profile.
+bool half_layout_ok(const bs::FitParams &p)
+{
+    return p.profile == 0 && p.n_exp == 1 && !p.noise_corr && !p.done && p.n_chains >= 2 && p.n_chains % 2 == 0;
+}
+
 cudaError_t autotune(bs_fit_plan_s *pl, int sms)
 {
     cudaStream_t st = nullptr;
@@ -113,24 +122,40 @@ cudaError_t autotune(bs_fit_plan_s *pl, int sms)
         for (int r : kRegVariants) waves = std::max(waves, bs::fit_blocks_per_sm(L.p.n_chains, L.p.max_side, r, L.p.profile));
         const int n_trial = std::min(L.p.n_work, 2 * sms * waves);
         float best = 0.f;
-        int best_regs = 128;
-        // All three are timed (reported by bs_fit_plan_info), but the choice
-        // is between the 128- and 96-register instances, which give the same
-        // chains bit for bit: the compiler's code for the 80-register budget
-        // rounds some operations differently, so taking it on a timing would
-        // make a plan's results depend on timing noise.
+        int best_regs = 128, best_cpc = 0;
+        // Candidates: the 128-, 96- and 80-register instances, with all of a
+        // galaxy's chains in one CTA or half of them (two CTAs per galaxy,
+        // each staging it).  All give the same chains bit for bit (the library
+        // is built without implicit multiply-add contraction, so every budget
+        // rounds alike), so the choice changes speed only.
         for (int v = 0; v < 3 && e == cudaSuccess; ++v) {
             if (kRegVariants[v] == 96 && L.p.n_chains > 4) continue;   // that instance takes <= 128 threads
             float ms = 0.f;
+            L.p.cpc = 0;
             e = time_variant(L, kRegVariants[v], n_trial, sms, st, e0, e1, ms);
             L.trial_ms[v] = ms;
-            if (e == cudaSuccess && kRegVariants[v] != 80 && (v == 0 || ms < best)) {
+            if (e == cudaSuccess && (v == 0 || ms < best)) {
                 best = ms;
                 best_regs = kRegVariants[v];
+                best_cpc = 0;
+            }
+            if (e == cudaSuccess && half_layout_ok(L.p)) {
+                L.p.cpc = L.p.n_chains / 2;
+                e = time_variant(L, kRegVariants[v], n_trial, sms, st, e0, e1, ms);
+                L.trial_half[v] = ms;
+                L.p.cpc = 0;
+                if (e == cudaSuccess && ms < best) {
+                    best = ms;
+                    best_regs = kRegVariants[v];
+                    best_cpc = L.p.n_chains / 2;
+                }
             }
         }
         L.p.regs = best_regs;
-        L.grid = std::min(L.p.n_work, sms * bs::fit_blocks_per_sm(L.p.n_chains, L.p.max_side, best_regs, L.p.profile));
+        L.p.cpc = best_cpc;
+        const int groups = L.p.n_chains / bs::cta_chains(L.p);
+        L.grid = std::min(L.p.n_work * groups,
+                          sms * bs::fit_blocks_per_sm(bs::cta_chains(L.p), L.p.max_side, best_regs, L.p.profile));
     }
     if (st) cudaStreamDestroy(st);
     if (e0) cudaEventDestroy(e0);
@@ -224,6 +249,7 @@ bs_status plan_create(const bs_fit_args *a, const bs_fit_out *o, const int32_t *
         L.p.queue = L.queue;
         L.slot_class = c + 1;
         L.trial_ms[0] = L.trial_ms[1] = L.trial_ms[2] = 0.f;
+        L.trial_half[0] = L.trial_half[1] = L.trial_half[2] = 0.f;
         const int per_sm = bs::fit_blocks_per_sm(a->n_chains, maxs[c], L.p.regs, L.p.profile);
         L.grid = std::min(count[c], sms * per_sm);
         pl->launches.push_back(L);
@@ -247,7 +273,7 @@ bs_status plan_create(const bs_fit_args *a, const bs_fit_out *o, const int32_t *
             return bs::set_error(BS_ERR_CUDA, "bs_fit_plan_create: streams: %s", cudaGetErrorString(e));
         }
         // kernel attributes are set outside the capture
-        for (auto &L : pl->launches) bs::fit_blocks_per_sm(a->n_chains, L.p.max_side, L.p.regs, L.p.profile);
+        for (auto &L : pl->launches) bs::fit_blocks_per_sm(bs::cta_chains(L.p), L.p.max_side, L.p.regs, L.p.profile);
         e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
             bs::capture_launches(&pl->graph_kernels);   // recorded, not launched
@@ -314,6 +340,10 @@ bs_status bs_fit_plan_info(bs_fit_plan plan, int32_t i, bs_fit_plan_launch_info 
     info->trial_ms_128 = L.trial_ms[0];
     info->trial_ms_96 = L.trial_ms[1];
     info->trial_ms_80 = L.trial_ms[2];
+    info->chains_per_cta = bs::cta_chains(L.p);
+    info->trial_ms_128_half = L.trial_half[0];
+    info->trial_ms_96_half = L.trial_half[1];
+    info->trial_ms_80_half = L.trial_half[2];
     return BS_OK;
 }
 
