@@ -210,20 +210,27 @@ def flops_per_eval(N):
 # the kernel source it was taken on, identified by its sha256; after any change
 # to that file the traffic is reported as null until the next capture.
 CAPTURED_TRAFFIC = {
-    # 53x53 galaxy of the plain workload: (13,925,888 + 7,424) B / 1,216 galaxies
+    # one galaxy of the plain workload (53x53, 4 chains x (200 + 300) draws), from a one-pass
+    # capture of the full 10,000-galaxy launch: (133,440,768 + 292,742,656) B / 10,000
     "fit": ("paper_2604_22048_gb300/csrc/bs_fit_impl.cuh",
-            "fac4c852b2dffa6918a2498ce0d1fa6e10a205ed8b6e2a958882df1a8b7fc176", 11458.3),
+            "98e044a466c5d40d65fc5c172499dacd90b6e32c94bb63bea526c182c2d1d40b", 42618.3,
+            {"side": 53, "chains": 4, "n_warmup": 200, "n_samples": 300}),
     # one interim sample of the shear workload: (489,468,416 + 3,221,248) B / (200,000 x 300)
     "shear": ("paper_2604_22048_gb300/csrc/bs_shear.cu",
-              "d664605cb7387c74c2607a07146e84be989c00e4134f73773bdafca158c849a5", 8.2115),
+              "d664605cb7387c74c2607a07146e84be989c00e4134f73773bdafca158c849a5", 8.2115, {}),
 }
 
 
-def captured_traffic(kind, units):
+def captured_traffic(kind, units, settings=None):
+    """Captured DRAM bytes per unit x units, or None once the kernel source or the
+    settings that fix the bytes per unit (stamp side, chains, draws) differ from the
+    capture's."""
     if kind not in CAPTURED_TRAFFIC:
         return None
     import hashlib
-    path, sha, per_unit = CAPTURED_TRAFFIC[kind]
+    path, sha, per_unit, fixed = CAPTURED_TRAFFIC[kind]
+    if any((settings or {}).get(k) != v for k, v in fixed.items()):
+        return None
     with open(os.path.join(ROOT, path), "rb") as fh:
         if hashlib.sha256(fh.read()).hexdigest() != sha:
             return None
@@ -421,9 +428,13 @@ def our_arm(a, world, rank, local_rank):
            "config": workload_config(a) | {"parallelism": f"dp{world}: galaxies per rank, shear sums all-reduced"},
            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                         "frac": achieved / peak_tflops,
-                        "traffic": captured_traffic("fit", n_local) if a.workload == "plain" else None,
-                        "traffic_note": "DRAM read+write per launch, scaled from a 1,216-galaxy ncu capture "
-                                        "of the same kernel source by the galaxies per launch",
+                        "traffic": captured_traffic("fit", n_local, {"side": a.side, "chains": a.chains,
+                                                                     "n_warmup": a.n_warmup,
+                                                                     "n_samples": a.n_samples})
+                        if a.workload == "plain" else None,
+                        "traffic_note": "DRAM read+write per launch, from a one-pass ncu capture of the "
+                                        "10,000-galaxy launch of the same kernel source and sampler settings, "
+                                        "per galaxy x the galaxies per launch",
                         "kernel": ", ".join(f"fit_kernel_r{i['registers']}<{i['slot_class']}>" for i in plan.info()),
                         "peak_how": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
                                     f"{sm_max:.0f} MHz (max SM clock)",

@@ -45,3 +45,22 @@ def test_gpus_2_starts_two_ranks_and_rank_0_prints_one_line():
     assert len(lines) == 1, out.stdout
     d = json.loads(lines[0])
     assert d["n_gpus"] == 2 and d["impl"] == "reference" and d["value"] > 0
+
+
+def test_captured_traffic_applies_only_to_the_captured_source_and_settings():
+    """The roofline's traffic is a captured figure per unit: it is reported for
+    the kernel source and sampler settings it was captured on, and null once
+    either differs."""
+    sys.path.insert(0, ROOT)
+    import bench
+    _, _, per_gal, fixed = bench.CAPTURED_TRAFFIC["fit"]
+    assert bench.captured_traffic("fit", 10_000, dict(fixed)) == per_gal * 10_000
+    assert bench.captured_traffic("fit", 10_000, dict(fixed, n_samples=100)) is None
+    assert bench.captured_traffic("fit", 10_000, dict(fixed, side=63)) is None
+    saved = bench.CAPTURED_TRAFFIC["shear"]
+    try:
+        bench.CAPTURED_TRAFFIC["shear"] = (saved[0], "0" * 64, saved[2], saved[3])
+        assert bench.captured_traffic("shear", 1) is None
+    finally:
+        bench.CAPTURED_TRAFFIC["shear"] = saved
+    assert bench.captured_traffic("shear", 300) == saved[2] * 300
