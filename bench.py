@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="plain", choices=["plain", "ragged", "serve", "shear"],
+    ap.add_argument("--workload", default="plain", choices=["plain", "ragged", "serve", "shear", "pixel"],
                     help="plain: 10^4 x 53 px, one Gaussian PSF; ragged: 10^5, 25-101 px, per-galaxy Moffat; "
                          "serve: 10^6 requests of the ragged kind, served vs plain per-size batches; "
                          "shear: shear stage on 10^6 galaxies x 300 samples")
@@ -66,7 +66,7 @@ def parse():
     ap.add_argument("--no-shear", action="store_true", help="plain line without the shear-stage object")
     a = ap.parse_args()
     if a.n_gal is None:
-        a.n_gal = {"plain": 10000, "ragged": 100000, "serve": 1000000, "shear": 1000000}[a.workload]
+        a.n_gal = {"plain": 10000, "ragged": 100000, "serve": 1000000, "shear": 1000000, "pixel": 2000}[a.workload]
     return a
 
 
@@ -211,9 +211,9 @@ def flops_per_eval(N):
 # to that file the traffic is reported as null until the next capture.
 CAPTURED_TRAFFIC = {
     # one galaxy of the plain workload (53x53, 4 chains x (200 + 300) draws), from a one-pass
-    # capture of the full 10,000-galaxy launch: (133,440,768 + 292,742,656) B / 10,000
+    # capture of the full 10,000-galaxy launch: (132,817,408 + 292,431,872) B / 10,000
     "fit": ("paper_2604_22048_gb300/csrc/bs_fit_impl.cuh",
-            "98e044a466c5d40d65fc5c172499dacd90b6e32c94bb63bea526c182c2d1d40b", 42618.3,
+            "33dec11059c489c0464ffdfb724b6568bbce34dc9377711cee8ecdd976eefbb5", 42524.9,
             {"side": 53, "chains": 4, "n_warmup": 200, "n_samples": 300}),
     # one interim sample of the shear workload: (489,468,416 + 3,221,248) B / (200,000 x 300)
     "shear": ("paper_2604_22048_gb300/csrc/bs_shear.cu",
@@ -747,6 +747,108 @@ def shear_arm(a, world, rank, local_rank):
                     "h2d_bytes_per_step": int(bytes_per_pass), "d2h_bytes_per_step": 8 * 12}}
 
 
+# ----------------------------------------------------------------------------- per-pixel weights
+
+PIXEL_METRIC = "galaxies/sec, image sampling with per-pixel noise weights (Appendix C), 1 GB300"
+
+
+def pixel_flops_per_eval(N):
+    """Real operations of the four transforms of one pixel-space evaluation on an
+    N x N stamp, H = (N+1)/2 half-plane rows, an FMA counting 2: the complex
+    column transform (8 N^2 H), the complex-to-real and real-to-complex row
+    transforms (4 N^2 H each) and the complex column transform back (8 N^2 H).
+    The tensor cores issue three TF32 products per operand pair on 64-padded
+    tiles; neither is counted."""
+    H = (N + 1) // 2
+    return 24 * N * N * H
+
+
+def pixel_weights(t, seed):
+    """Spatially variable noise as per-pixel weights w = 1 / s(x)^2: the noise
+    level s rises linearly from 1 to 1.6 across the stamp's diagonal, and 1% of
+    the pixels (drawn at random) are masked, w = 0."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(t.n):
+        N = int(t.side[i])
+        iy, ix = np.mgrid[0:N, 0:N]
+        s = 1.0 + 0.6 * (ix + iy) / (2.0 * (N - 1))
+        w = 1.0 / (s * s)
+        w[rng.random((N, N)) < 0.01] = 0.0
+        out.append(w.ravel())
+    return np.concatenate(out).astype(np.float32)
+
+
+def pixel_arm(a, world, rank, local_rank):
+    """The image sampling phase with per-pixel weights: every evaluation renders
+    the model image and transforms the weighted residual back, the transforms on
+    the tensor cores (3xTF32 tcgen05.mma), one CTA per chain."""
+    import torch
+    from paper_2604_22048_gb300 import api, build, synth
+    build.build()
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    b = argparse.Namespace(**vars(a))
+    b.workload = "plain"
+    inp = make_inputs_gpu(b, rank, dev, world)
+    n = inp["truth"].n
+    w = torch.from_numpy(pixel_weights(inp["truth"], synth.SEED_DATA + 5)).to(dev)
+    cfg = api.FitConfig(n_chains=a.chains, n_warmup=a.n_warmup, n_samples=a.n_samples, n_leapfrog=a.leapfrog,
+                        random_steps=True)
+    plan = api.FitPlan(inp["data"], inp["offsets"], inp["side"], inp["psf"], inp["sigma"], inp["init"], cfg,
+                       max_side=a.side, pixel_weight=w, want=("status", "n_grad", "accept_rate"))
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    for _ in range(a.warmup):
+        plan.run()
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    launches0 = api.kernel_launches()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+    for i in range(a.steps):
+        flush.fill_(float(i))
+        ev[i][0].record(stream)
+        plan.run()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize(dev)
+    launches = api.kernel_launches() - launches0
+    clk = clocks.stop()
+    ms = [e[0].elapsed_time(e[1]) for e in ev]
+    step_ms = float(np.mean(ms))
+    res = plan.result()
+    ess, rhat = api.chain_ess(res["samples"])
+    n_grad = float(res["n_grad"].to(torch.float64).sum().item())
+    evals_per_s = n_grad / (step_ms / 1e3)
+    flops = n_grad * pixel_flops_per_eval(a.side)
+    peaks = measured_peaks()
+    peak = 0.5 * peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1910.0))
+    achieved = flops / (step_ms / 1e3) / 1e12
+    st = res["status"].cpu().numpy()
+    return {"metric": PIXEL_METRIC, "value": n / (step_ms / 1e3), "unit": "galaxies/s", "n_gpus": world,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": step_ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 (transforms 3xTF32)",
+            "data": "synthetic (the plain workload's stamps; weights of a noise level rising across the stamp, "
+                    "1% of pixels masked)",
+            "config": {"workload": f"per-pixel weights: {n} exponential galaxies, {a.side}x{a.side} FP32 stamps, "
+                                   f"Gaussian PSF FWHM 0.7\", {a.chains} chains x ({a.n_warmup} warmup + "
+                                   f"{a.n_samples} draws), HMC L_i~U{{1..{a.leapfrog}}}, each evaluation rendering "
+                                   "the model image and transforming the weighted residual back",
+                       "n_gal": n, "side": a.side, "l2": "flushed between timed steps (256 MB write)"},
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": f"fit_kernel_pix<{(a.side + 31) // 32}>",
+                         "flops_per_eval": pixel_flops_per_eval(a.side), "evals_per_s": evals_per_s,
+                         "peak_how": "dense TF32 = half the measured bf16 cuBLAS rate (sustained), the nominal "
+                                     "ratio of the two formats",
+                         "note": "the algorithmic flops of the four transforms only; the evaluation is bound by "
+                                 "the latency of its steps (one CTA of four warps per SM), not by the tensor pipe"},
+            "gpu_launches": launches, "clocks": clk,
+            "ess": ess_summary(ess, rhat, float(ess.mean(dim=1).sum().item()) / (step_ms / 1e3)),
+            "status_counts": np.bincount(st, minlength=5).tolist(),
+            "accept_rate": float(res["accept_rate"].mean().item())}
+
+
 # ----------------------------------------------------------------------------- serving
 
 SERVE_METRIC = METRIC
@@ -1052,7 +1154,7 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
-    arm = {"serve": serve_arm, "shear": shear_arm}.get(a.workload, our_arm)
+    arm = {"serve": serve_arm, "shear": shear_arm, "pixel": pixel_arm}.get(a.workload, our_arm)
     out = arm(a, world, rank, local_rank)
     if rank == 0:
         print(json.dumps(out))

@@ -204,12 +204,11 @@ typedef struct {
                                      log L = -1/2 sum_x w(x) (d - m)^2 / sigma^2,
                                      w >= 0 (0 masks a pixel).  Each evaluation
                                      then renders the model image and transforms
-                                     the weighted residual back (two separable
-                                     DFTs of the stamp, tens of times the cost
-                                     of the spectral evaluation).  Requires the
+                                     the weighted residual back (four dense
+                                     DFT-matrix products on the tensor cores,
+                                     3xTF32, one CTA per chain).  Requires the
                                      exponential profile, one exposure, no
-                                     noise_corr, max_side <= 63 and at most 4
-                                     chains (shared memory). */
+                                     noise_corr and max_side <= 63. */
     const float *pixel_prec;      /* NULL, or device float: a general pixel
                                      covariance Sigma (Appendix C,
                                      Eq. covar-pixel-likelihood: spatially
@@ -258,7 +257,10 @@ typedef struct {
     int32_t *status;       /* [n_gal]: 0 ok, 1 a chain started off-support,
                               2 side[] invalid for max_side (galaxy skipped),
                               3 noise_corr of an exposure has a spectrum that is
-                              not positive, i.e. no covariance (galaxy skipped) */
+                              not positive, i.e. no covariance (galaxy skipped),
+                              4 (pixel_weight) a tensor-core transform did not
+                              complete within its time limit: the galaxy's
+                              draws are not valid */
     int32_t *n_grad;       /* [n_gal][n_chains]: log-posterior gradient
                               evaluations the chain made (warmup, searches and
                               sampling) */

@@ -18,7 +18,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(CSRC, "libbpshear.so")
 SOURCES = ["bs_api.cu", "bs_fit.cu", "bs_fit_prof.cu", "bs_render.cu", "bs_shear.cu", "bs_diag.cu", "bs_noalloc.cu",
            "bs_plan.cu", "bs_serve.cu", "bs_shear_hmc.cu", "bs_bias.cu", "bs_dense.cu"]
-HEADERS = ["bs_device.cuh", "bs_internal.h", "bs_fit_impl.cuh"]
+HEADERS = ["bs_device.cuh", "bs_internal.h", "bs_fit_impl.cuh", "bs_fit_pixel.cuh", "bs_pix_tc.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -235,6 +235,7 @@ static bs_status fill_fit_params(const bs_fit_args *a, bs::FitParams &p, const c
                         "%s: chains_per_cta needs the exponential profile, one exposure and white noise", who);
         p.cpc = a->chains_per_cta;
     }
+    if (p.profile == 3) p.cpc = 1;   // the pixel-weight path: one chain per CTA
     return BS_OK;
 }
 
@@ -251,8 +252,8 @@ bs_status fit_params_from_args(const bs_fit_args *a, const bs_fit_out *o, FitPar
     if (!o) return fail(BS_ERR_INVALID_ARG, "%s: NULL outputs", who);
     if (a->n_gal > 0 && !o->samples) return fail(BS_ERR_INVALID_ARG, "%s: NULL samples output", who);
     if (a->n_gal > 0 && !a->init) return fail(BS_ERR_INVALID_ARG, "%s: NULL init", who);
-    if ((p.profile == 3 || p.profile == 4) && a->n_chains > 4)
-        return fail(BS_ERR_INVALID_ARG, "%s: pixel_weight allows at most 4 chains", who);
+    if (p.profile == 4 && a->n_chains > 4)
+        return fail(BS_ERR_INVALID_ARG, "%s: pixel_prec allows at most 4 chains", who);
     if (a->n_chains < 1 || a->n_chains > bs::kMaxChains)
         return fail(BS_ERR_INVALID_ARG, "%s: n_chains must be 1..%d", who, bs::kMaxChains);
     if (a->n_warmup < 0 || a->n_samples < 0 || a->n_leapfrog < 1)

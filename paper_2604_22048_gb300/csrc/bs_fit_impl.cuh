@@ -42,6 +42,7 @@
 
 #include "bs_device.cuh"
 #include "bs_internal.h"
+#include "bs_pix_tc.cuh"
 
 namespace bs {
 
@@ -104,50 +105,6 @@ __device__ __forceinline__ SmemView smem_view(unsigned char *base, int h_max, in
     v.Gc = v.tw + (size_t)max_side;
     v.xph = v.G;
     v.kxr = v.G + (size_t)scratch_float2(max_side, h_max, n_chains);
-    return v;
-}
-
-// Pixel-space noise models (Appendix C; kernel instance PROF 3): per-pixel
-// weights, or a general covariance given as its precision matrix.  After the
-// shared region, the twiddles exp(+2 pi i m / N) (max_side float2) and, per
-// chain, a private copy of the table ([h_max][3 npad]: the D slots hold the
-// evaluation's effective spectrum, the T slots the transfer), the
-// half-transformed image ([h_max][max_side] float2), one pixel row (64
-// floats) and, with a covariance, the residual image and its product with
-// the precision (max_side^2 floats each).  Sizes in floats, each chain's
-// block a multiple of 4 floats.
-__host__ __device__ __forceinline__ int pix_chain_floats(int h_max, int npad, int max_side, bool dense)
-{
-    const int n = h_max * row_floats(npad) + 2 * h_max * max_side + 64 + (dense ? 2 * max_side * max_side : 0);
-    return (n + 3) & ~3;
-}
-__host__ __device__ __forceinline__ size_t pix_region_bytes(int h_max, int npad, int max_side, int n_chains,
-                                                            bool dense)
-{
-    return ((size_t)2 * ((max_side + 1) & ~1) +
-            (size_t)n_chains * pix_chain_floats(h_max, npad, max_side, dense)) *
-           sizeof(float);
-}
-struct PixView {
-    float2 *tw;    // [max_side] exp(+2 pi i m / N)
-    float *tab;    // this chain's table
-    float2 *G;     // [h_max][max_side]
-    float *row;    // [64]
-    float *rb;     // [max_side^2] residual d - m (covariance only)
-    float *yb;     // [max_side^2] precision x residual (covariance only)
-};
-// kxr ends at h_max + 1 float2 after its start; the region follows, 16-byte aligned.
-__device__ __forceinline__ PixView pix_view(float2 *kxr, int h_max, int npad, int max_side, int chain, bool dense)
-{
-    float *base = reinterpret_cast<float *>(kxr + ((h_max + 2) & ~1));
-    PixView v;
-    v.tw = reinterpret_cast<float2 *>(base);
-    float *c0 = base + 2 * ((max_side + 1) & ~1) + (size_t)chain * pix_chain_floats(h_max, npad, max_side, dense);
-    v.tab = c0;
-    v.G = reinterpret_cast<float2 *>(c0 + (size_t)h_max * row_floats(npad));
-    v.row = reinterpret_cast<float *>(v.G + (size_t)h_max * max_side);
-    v.rb = v.row + 64;
-    v.yb = v.rb + max_side * max_side;
     return v;
 }
 
@@ -847,228 +804,7 @@ __device__ __forceinline__ double eval_logpost(const FitParams &P, const GalCtx 
     return -0.5 * (chi2 + s_chi2_off) * (double)ib + (double)lprior;
 }
 
-// ---- Spatially variable noise (Appendix C): log L = -1/2 sum_x w(x) (d - m)^2 / sigma^2.
-// Parseval no longer makes this a sum over k, but its gradient is still
-// sum_k Re[conj(R_k) dM_k/dtheta] / (sigma^2 N^2) with R = DFT(w (d - m)), so the
-// half-plane pass of eval_logpost gives it when its data spectrum is replaced
-// by the effective D' = M + R (scaled as the table).  Each evaluation renders
-// m from M and transforms w (d - m) back, with the separable DFT on the
-// stamp's grid (the same centring as the setup's transform of d).
-
-// Per-galaxy set-up of the pixel path (all threads): the twiddles, and each
-// chain's private table from the staged one (transfer, zero spectrum).
-__device__ void pix_setup(const FitParams &P, const GalCtx &gc, const SmemView &sm, int n_tables)
-{
-    const int tid = threadIdx.x, nth = blockDim.x;
-    const PixView p0 = pix_view(sm.kxr, P.h_max, P.npad, P.max_side, 0, P.pix_prec != nullptr);
-    for (int m = tid; m < gc.N; m += nth) {
-        float s, co;
-        sincospif(2.0f * (float)m * gc.invN, &s, &co);
-        p0.tw[m] = make_float2(co, s);
-    }
-    const int rowf = row_floats(P.npad);
-    const int nrow = gc.H * rowf;
-    for (int t = 0; t < n_tables; ++t) {
-        float *dst = pix_view(sm.kxr, P.h_max, P.npad, P.max_side, t, P.pix_prec != nullptr).tab;
-        for (int i = tid; i < nrow; i += nth) dst[i] = sm.tab[i];
-    }
-    __syncthreads();
-}
-
-template <int NC>
-__device__ double eval_pix(const FitParams &P, const GalCtx &gc, const PixView &pv, int gal,
-                           const float2 *__restrict__ kxr, float2 *__restrict__ xph, const float vcol[NC],
-                           const float th[6], float g[6], bool want_ll)
-{
-    const int lane = threadIdx.x & 31;
-    const int N = gc.N, H = gc.H, c = gc.c, npad = P.npad;
-    const int rowf = row_floats(npad);
-    const float F = exp10f(th[0]);
-    const float r0 = exp10f(th[1]) * (1.0f / kHlrOverR0);
-    const float r02 = r0 * r0;
-    const float e1 = th[2], e2 = th[3];
-    const float E = e1 * e1 + e2 * e2;
-    const float Pq = 1.0f / (1.0f - E);
-    const float al = r02 * (1.0f + E + 2.0f * e1) * Pq;
-    const float be = r02 * (1.0f + E - 2.0f * e1) * Pq;
-    const float ga = r02 * 4.0f * e2 * Pq;
-    const float sqrt2 = 1.41421356237309515f;
-    for (int u = lane; u < H; u += 32) {
-        float sx, cx;
-        sincospi_sfu(-2.0f * th[4] * (float)u * gc.invN, &sx, &cx);
-        xph[u] = make_float2(cx, sx);
-    }
-    __syncwarp();
-    // (a) the model's half spectrum Mt = Tt F f(s) X(u) Y(v) into the D slots
-#pragma unroll
-    for (int j = 0; j < NC; ++j) {
-        const int vi = lane + 32 * j;
-        float sy, cy;
-        sincospi_sfu(-2.0f * th[5] * vcol[j] * gc.invN, &sy, &cy);
-        const float Yr = F * cy, Yi = F * sy;
-        const float ky = vcol[j] * gc.dk;
-        const float cst = fmaf(be * ky, ky, 1.0f), gky = ga * ky;
-        int ox, oy, ot;
-        slot_offsets(npad, j, lane, ox, oy, ot);
-        for (int u = 0; u < H; ++u) {
-            float *row = pv.tab + (size_t)u * rowf;
-            const float kx = kxr[u].x;
-            const float s = fmaf(fmaf(al, kx, gky), kx, cst);
-            const float rs = rsqrtf(s);
-            const float A = row[ot] * rs * rs * rs;
-            const float2 X = xph[u];
-            const float Pr = X.x * Yr - X.y * Yi, Pi = X.x * Yi + X.y * Yr;
-            const float mr = vi < N ? A * Pr : 0.0f, mi = vi < N ? A * Pi : 0.0f;
-            row[ox] = mr;
-            row[oy] = mi;
-            // unscaled M(u, v) = Mt / scale_u, contiguous, for the inverse transform
-            const float inv_scale = (float)N * (u == 0 ? 1.0f : 0.70710678118654752f);
-            if (vi < N) pv.G[(size_t)u * N + vi] = make_float2(mr * inv_scale, mi * inv_scale);
-        }
-    }
-    __syncwarp();
-    // (b1) G(u, iy) = sum_v M(u, v) exp(+2 pi i v (iy - c) / N), in place row by
-    // row (a row's outputs need only that row's M; lanes over iy, at most 2 each)
-    for (int u = 0; u < H; ++u) {
-        float2 *grow = pv.G + (size_t)u * N;
-        float2 res[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-#pragma unroll
-        for (int r = 0; r < 2; ++r) {
-            const int iy = lane + 32 * r;
-            if (iy < N) {
-                const int step = iy - c;
-                float re = 0.f, im = 0.f;
-                int k = ((-c * step) % N + N) % N;
-                const int dk = (step % N + N) % N;
-                for (int vi = 0; vi < N; ++vi) {
-                    const float2 mv = grow[vi];
-                    const float2 t = pv.tw[k];
-                    re = fmaf(mv.x, t.x, fmaf(-mv.y, t.y, re));
-                    im = fmaf(mv.x, t.y, fmaf(mv.y, t.x, im));
-                    k += dk;
-                    if (k >= N) k -= N;
-                }
-                res[r] = make_float2(re, im);
-            }
-        }
-        __syncwarp();
-#pragma unroll
-        for (int r = 0; r < 2; ++r)
-            if (lane + 32 * r < N) grow[lane + 32 * r] = res[r];
-        __syncwarp();
-    }
-    // (b2) per pixel row: m(ix, iy), r = w (d - m), then Q(u, iy) = sum_ix r exp(-2 pi i u (ix - c) / N);
-    // with a covariance, r = Sigma^-1 (d - m) needs every row of d - m first
-    const int64_t off = P.offsets[gal];
-    const float invN2 = gc.invN * gc.invN;
-    const bool dense = P.pix_prec != nullptr;
-    double chi = 0.0;
-    auto row_forward = [&](const float *rrow, int iy) {
-        for (int u = lane; u < H; u += 32) {
-            float re = 0.f, im = 0.f;
-            int k = ((u * c) % N + N) % N;               // -u (ix - c) at ix = 0
-            const int dk = (N - u % N) % N;
-            for (int ix = 0; ix < N; ++ix) {
-                const float r = rrow[ix];
-                const float2 t = pv.tw[k];
-                re = fmaf(r, t.x, re);
-                im = fmaf(r, t.y, im);
-                k += dk;
-                if (k >= N) k -= N;
-            }
-            pv.G[(size_t)u * N + iy] = make_float2(re, im);
-        }
-    };
-    for (int iy = 0; iy < N; ++iy) {
-        for (int ix = lane; ix < N; ix += 32) {
-            const int dk = ((ix - c) % N + N) % N;      // u (ix - c) mod N, advanced per u
-            int k = dk;
-            float acc = pv.G[iy].x;                     // u = 0 (real)
-            for (int u = 1; u < H; ++u) {
-                const float2 gv = pv.G[(size_t)u * N + iy];
-                const float2 t = pv.tw[k];
-                acc = fmaf(2.0f * gv.x, t.x, fmaf(-2.0f * gv.y, t.y, acc));
-                k += dk;
-                if (k >= N) k -= N;
-            }
-            const float m = acc * invN2;
-            const int64_t idx = off + (int64_t)iy * N + ix;
-            const float res = load_pix(P.data, P.data_f64, idx) - m;
-            if (dense) {
-                pv.rb[iy * N + ix] = res;
-            } else {
-                const float r = __ldg(P.pix_w + idx) * res;
-                chi += (double)(r * res);
-                pv.row[ix] = r;
-            }
-        }
-        __syncwarp();
-        if (!dense) row_forward(pv.row, iy);
-        __syncwarp();
-    }
-    if (dense) {
-        // y = Sigma^-1 r: the precision is symmetric, so y_a = sum_b P[b][a] r_b with
-        // lanes over a reads each row b of it coalesced (from L2: tens of
-        // evaluations of the galaxy's chains share it); chi^2 = r.y
-        constexpr int kSlots = (kDenseMaxSide * kDenseMaxSide + 31) / 32;
-        const int n = N * N;
-        const float *Pg = P.pix_prec + P.prec_offs[gal];
-        float yv[kSlots];
-#pragma unroll
-        for (int j = 0; j < kSlots; ++j) yv[j] = 0.f;
-        for (int b = 0; b < n; ++b) {
-            const float rb = pv.rb[b];
-            const float *prow = Pg + (size_t)b * n;
-#pragma unroll
-            for (int j = 0; j < kSlots; ++j) {
-                const int a = lane + 32 * j;
-                if (a < n) yv[j] = fmaf(__ldg(prow + a), rb, yv[j]);
-            }
-        }
-#pragma unroll
-        for (int j = 0; j < kSlots; ++j) {
-            const int a = lane + 32 * j;
-            if (a < n) {
-                pv.yb[a] = yv[j];
-                chi += (double)pv.rb[a] * (double)yv[j];
-            }
-        }
-        __syncwarp();
-        for (int iy = 0; iy < N; ++iy) row_forward(pv.yb + iy * N, iy);
-        __syncwarp();
-    }
-    // (b3) D' = Mt + scale_u R(u, v), R(u, v) = sum_iy Q(u, iy) exp(-2 pi i v (iy - c) / N);
-    // the H x N (u, v) outputs spread over the lanes
-    for (int t = lane; t < H * N; t += 32) {
-        const int u = t / N, vi = t - u * N, v = vi - c;
-        const int dk = ((-v) % N + N) % N;
-        int k = ((v * c) % N + N) % N;                  // -v (iy - c) at iy = 0
-        const float2 *qrow = pv.G + (size_t)u * N;
-        float re = 0.f, im = 0.f;
-        for (int iy = 0; iy < N; ++iy) {
-            const float2 q = qrow[iy];
-            const float2 tw = pv.tw[k];
-            re = fmaf(q.x, tw.x, fmaf(-q.y, tw.y, re));
-            im = fmaf(q.x, tw.y, fmaf(q.y, tw.x, im));
-            k += dk;
-            if (k >= N) k -= N;
-        }
-        int ox, oy, ot;
-        slot_offsets(npad, vi >> 5, vi & 31, ox, oy, ot);
-        const float scale = (u == 0 ? 1.0f : sqrt2) * gc.invN;
-        float *row = pv.tab + (size_t)u * rowf;
-        row[ox] = fmaf(scale, re, row[ox]);
-        row[oy] = fmaf(scale, im, row[oy]);
-    }
-    __syncwarp();
-    // (c) the gradient from the half-plane pass on the effective spectrum
-    eval_logpost<NC, 0>(P, gc, pv.tab, kxr, xph, vcol, th, g, false);
-    if (!want_ll) return 0.0;
-    const double chi2 = warp_sum_d(chi);
-    const float lprior = P.prior_const - 0.5f * (th[4] * th[4] + th[5] * th[5]) * P.inv_sxy2 +
-                         2.0f * log1pf(-E) - 0.5f * E * P.inv_se2;
-    return -0.5 * chi2 * (double)gc.inv_b + (double)lprior;
-}
+#include "bs_fit_pixel.cuh"
 
 __device__ __forceinline__ float pick6(const float (&v)[6], int i)
 {
@@ -1120,8 +856,10 @@ __device__ __forceinline__ bool trajectory(const FitParams &P, const GalCtx &gc,
         float gg[6];
         double v;
         if constexpr (PROF == 3)
-            v = eval_pix<NC>(P, gc, pix_view(sm.kxr, P.h_max, P.npad, P.max_side, slot, P.pix_prec != nullptr),
-                             gal, sm.kxr, xph_c, vcol, x, gg, l == nst - 1);
+            v = eval_pix<NC>(P, gc, sm, gal, xph_c, vcol, x, gg, l == nst - 1);
+        else if constexpr (PROF == 4)
+            v = eval_dense<NC>(P, gc, dense_view(sm.kxr, P.h_max, P.npad, P.max_side, slot), gal, sm.kxr, xph_c,
+                               vcol, x, gg, l == nst - 1);
         else
             v = eval_logpost<NC, PROF>(P, gc, sm.tab, sm.kxr, xph_c, vcol, x, gg, l == nst - 1);
         ++ngrad;
@@ -1140,6 +878,8 @@ __device__ void run_chain(const FitParams &P, const GalCtx &gc, const SmemView &
     const int lane = threadIdx.x & 31;
     const int pi = lane < 6 ? lane : 5;     // parameter of this lane (lanes 6.. shadow parameter 5)
     const bool own = lane < 6;
+    // the pixel path's four warps run the same chain: the first one writes its results
+    const bool wr = PROF != 3 || threadIdx.x < 32;
     const int C = P.n_chains, W = P.n_warmup, S = P.n_samples, L = P.n_leapfrog;
     const uint64_t gid = P.gal_id ? P.gal_id[gal] : (uint64_t)gal;
     const uint64_t key = gid * (uint64_t)C + (uint64_t)chain;
@@ -1205,7 +945,7 @@ __device__ void run_chain(const FitParams &P, const GalCtx &gc, const SmemView &
             thl = tpl;
             g = gp;
             lp = ok ? lpp : -INFINITY;
-            if (!isfinite(lp) && lane == 0 && P.status) P.status[gal] = 1;
+            if (!isfinite(lp) && wr && lane == 0 && P.status) P.status[gal] = 1;
             if (P.init_step) {
                 // resume with the given step size: no search, dual averaging from it
                 da_mu = logf(10.0f * eps);
@@ -1256,7 +996,7 @@ __device__ void run_chain(const FitParams &P, const GalCtx &gc, const SmemView &
             lp = lpp;
         }
         if (it < W) {
-            if (lane == 7) {
+            if (wr && lane == 7) {
                 const size_t wi0 = ci0 * (size_t)W + it;
                 if (P.warm_accepted) P.warm_accepted[wi0] = acc ? 1 : 0;
                 if (P.warm_stat) P.warm_stat[wi0] = a;
@@ -1296,20 +1036,22 @@ __device__ void run_chain(const FitParams &P, const GalCtx &gc, const SmemView &
             const int s = it - W;
             asum += a;
             ndiv += ok ? 0 : 1;
-            if (own) P.samples[(size_t)pi * plane + chain_row + s] = th + thl;
-            if (lane == 6 && P.logp) P.logp[chain_row + s] = (float)lp;
-            if (lane == 7 && P.accepted) P.accepted[chain_row + s] = acc ? 1 : 0;
+            if (wr) {
+                if (own) P.samples[(size_t)pi * plane + chain_row + s] = th + thl;
+                if (lane == 6 && P.logp) P.logp[chain_row + s] = (float)lp;
+                if (lane == 7 && P.accepted) P.accepted[chain_row + s] = acc ? 1 : 0;
+            }
         }
         ++it;
         if (it >= W + S && mode == MODE_STEP) mode = -1;
     }
-    if (lane == 0) {
+    if (wr && lane == 0) {
         if (P.accept_rate) P.accept_rate[ci0] = S > 0 ? asum / (float)S : 0.f;
         if (P.step_size) P.step_size[ci0] = eps;
         if (P.n_div) P.n_div[ci0] = ndiv;
         if (P.n_grad) P.n_grad[ci0] = ngrad;
     }
-    if (P.inv_mass && own) P.inv_mass[ci0 * 6 + pi] = im;
+    if (wr && P.inv_mass && own) P.inv_mass[ci0 * 6 + pi] = im;
 }
 
 // Serving: copy n elements at src (this CTA's galaxy's outputs) to the
@@ -1356,8 +1098,10 @@ __device__ __forceinline__ void fit_loop(const FitParams &P)
     __shared__ int s_gal, s_grp;
     const int cc = cta_chains(P);              // chains of this CTA
     const int groups = P.n_chains / cc;        // CTAs a galaxy's chains are split over
-    const SmemView sm = smem_view(smem_raw, P.h_max, P.npad, P.max_side, cc);
+    // the pixel path: one chain per CTA, run by its four warps (a phase table each)
+    const SmemView sm = smem_view(smem_raw, P.h_max, P.npad, P.max_side, PROF == 3 ? 4 : cc);
     const int warp = threadIdx.x >> 5;
+    if constexpr (PROF == 3) pix_tc_begin(pix_tc_view(sm.kxr, P.h_max, P.max_side));
     bool first = true;
     for (;;) {
         if (threadIdx.x == 0) {
@@ -1392,11 +1136,20 @@ __device__ __forceinline__ void fit_loop(const FitParams &P)
             if (P.done) publish_galaxy(P, gal);
             continue;
         }
-        if constexpr (PROF == 3) pix_setup(P, gc, sm, cc);
-        if (warp < cc) run_chain<NC, PROF>(P, gc, sm, gal, s_grp * cc + warp, warp);
+        if constexpr (PROF == 3) {
+            const PixTc px = pix_tc_view(sm.kxr, P.h_max, P.max_side);
+            pix_tc_setup(P, gc, px, gal);
+            run_chain<NC, PROF>(P, gc, sm, gal, s_grp, warp);
+            __syncthreads();
+            if (threadIdx.x == 0 && *px.abort && P.status) P.status[gal] = 4;
+        } else {
+            if constexpr (PROF == 4) dense_setup(P, gc, sm, cc);
+            if (warp < cc) run_chain<NC, PROF>(P, gc, sm, gal, s_grp * cc + warp, warp);
+        }
         __syncthreads();
         if (P.done) publish_galaxy(P, gal);
     }
+    if constexpr (PROF == 3) pix_tc_end(pix_tc_view(sm.kxr, P.h_max, P.max_side));
 }
 
 // Register budgets of the kernel instances (the launch bounds give ptxas the
@@ -1409,6 +1162,10 @@ template <int NC, int PROF>
 __global__ void __launch_bounds__(128, 5) fit_kernel_r96(const FitParams P) { fit_loop<NC, PROF>(P); }
 template <int NC, int PROF>
 __global__ void __launch_bounds__(256, 3) fit_kernel_r80(const FitParams P) { fit_loop<NC, PROF>(P); }
+// The pixel path: one chain per CTA of four warps; its shared memory (the transforms'
+// constant blocks and operands) allows one CTA per SM.
+template <int NC>
+__global__ void __launch_bounds__(128, 1) fit_kernel_pix(const FitParams P) { fit_loop<NC, 3>(P); }
 
 // One CTA of 32 threads per point: stage the galaxy, then evaluate.
 template <int NC, int PROF>
@@ -1425,15 +1182,18 @@ __device__ void point_eval(const FitParams &P, const GalCtx &gc, const SmemView 
     double v = -INFINITY;
     if (in_support(P, th)) {
         if constexpr (PROF == 3)
-            v = eval_pix<NC>(P, gc, pix_view(sm.kxr, P.h_max, P.npad, P.max_side, 0, P.pix_prec != nullptr), gal,
-                             sm.kxr, sm.xph, vcol, th,
-                             g, true);
+            v = eval_pix<NC>(P, gc, sm, gal, sm.xph + (threadIdx.x >> 5) * phase_stride(P.h_max), vcol, th, g,
+                             true);
+        else if constexpr (PROF == 4)
+            v = eval_dense<NC>(P, gc, dense_view(sm.kxr, P.h_max, P.npad, P.max_side, 0), gal, sm.kxr, sm.xph, vcol,
+                               th, g, true);
         else
             v = eval_logpost<NC, PROF>(P, gc, sm.tab, sm.kxr, sm.xph, vcol, th, g, true);
     } else {
 #pragma unroll
         for (int i = 0; i < 6; ++i) g[i] = NAN;
     }
+    if (threadIdx.x >= 32) return;   // the pixel path's other warps hold the same values
     if (lane == 0 && logp) *logp = v;
     if (grad && lane < 6) grad[lane] = pick6(g, lane);
 }
@@ -1459,7 +1219,7 @@ __global__ void __launch_bounds__(32) logpost_points_kernel(const FitParams P, i
             if (grad && threadIdx.x < 6) grad[(size_t)i * 6 + threadIdx.x] = NAN;
             continue;
         }
-        if constexpr (PROF == 3) pix_setup(P, gc, sm, 1);
+        if constexpr (PROF == 4) dense_setup(P, gc, sm, 1);
         const float *th = theta + (size_t)i * 6;
         double *lp = logp ? logp + i : nullptr;
         float *gr = grad ? grad + (size_t)i * 6 : nullptr;
@@ -1471,6 +1231,36 @@ __global__ void __launch_bounds__(32) logpost_points_kernel(const FitParams P, i
         }
         __syncthreads();
     }
+}
+
+// The pixel path's points: one CTA of four warps per point.
+template <int NC>
+__global__ void __launch_bounds__(128, 1) logpost_points_pix_kernel(const FitParams P, int n_points,
+                                                                    const int32_t *gal_index, const float *theta,
+                                                                    double *logp, float *grad)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const SmemView sm = smem_view(smem_raw, P.h_max, P.npad, P.max_side, 4);
+    const PixTc px = pix_tc_view(sm.kxr, P.h_max, P.max_side);
+    pix_tc_begin(px);
+    for (int i = blockIdx.x; i < n_points; i += gridDim.x) {
+        const int gal = gal_index[i];
+        GalCtx gc;
+        const bool ok = gal >= 0 && gal < P.n_gal && side_ok(P, P.side[gal]) && setup_galaxy(P, gal, sm, gc);
+        if (!ok) {
+            if (threadIdx.x == 0 && logp) logp[i] = NAN;
+            if (grad && threadIdx.x < 6) grad[(size_t)i * 6 + threadIdx.x] = NAN;
+            __syncthreads();
+            continue;
+        }
+        pix_tc_setup(P, gc, px, gal);
+        const float *th = theta + (size_t)i * 6;
+        double *lp = logp ? logp + i : nullptr;
+        float *gr = grad ? grad + (size_t)i * 6 : nullptr;
+        point_eval<NC, 3>(P, gc, sm, gal, th, lp, gr);
+        __syncthreads();
+    }
+    pix_tc_end(px);
 }
 
 }  // namespace

@@ -1,0 +1,534 @@
+// Pixel-space evaluations of the log posterior and its gradient (Appendix C): per-pixel
+// weights on the tensor cores, a dense covariance on the CUDA cores.  Included by
+// bs_fit_impl.cuh inside namespace bs::(anonymous), after the spectral evaluation
+// (eval_logpost) and the table layout it reuses.
+#pragma once
+
+// ---- Spatially variable noise (Appendix C): log L = -1/2 sum_x w(x) (d - m)^2 / sigma^2.
+// Parseval no longer makes this a sum over k, but the gradient is still sum_k
+// Re[conj(R_k) dM_k / dtheta] / (sigma^2 N^2) with R = DFT(w (d - m)), so the half-plane
+// pass of eval_logpost gives it when its data spectrum is replaced by the effective
+// D' = M + R (scaled as the table).  The transforms run on the tensor cores (the layout
+// and operand split are described with PixTc); one CTA of four warps evaluates one chain.
+
+// Per galaxy (all threads): the constant blocks -S, C, S for this side (high and low
+// TF32 parts), and the stamp and its weights in shared memory.
+__device__ void pix_tc_setup(const FitParams &P, const GalCtx &gc, const PixTc &px, int gal)
+{
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int N = gc.N, c = gc.c;
+    float *hi = px.cst, *lo = px.cst + tc::kCstFloats;
+    for (int i = tid; i < tc::kNP * tc::kNP; i += nth) {
+        const int a = i >> 6, b = i & 63;
+        float co = 0.f, sn = 0.f;
+        if (a < N && b < N) {
+            int k = ((a - c) * (b - c)) % N;   // exact reduction of the phase index
+            if (k < 0) k += N;
+            sincospif(2.0f * (float)k / (float)N, &sn, &co);
+        }
+        const int e = tc::op_index(a, b, tc::kNP, tc::kLboC / 4);
+        tc::split_store(hi, lo, e, -sn);
+        tc::split_store(hi, lo, tc::kBlockFloats + e, co);
+        tc::split_store(hi, lo, 2 * tc::kBlockFloats + e, sn);
+    }
+    const int64_t off = P.offsets[gal];
+    const int n = N * N;
+    for (int i = tid; i < n; i += nth) {
+        px.dimg[i] = load_pix(P.data, P.data_f64, off + i);
+        px.wimg[i] = __ldg(P.pix_w + off + i);
+    }
+    __syncthreads();
+}
+
+// One 3xTF32 product into TMEM (all threads; thread 0 issues and commits, everyone
+// waits for the given parity).  K runs over n_q halves of nk steps of 8: step (q, k)
+// reads A at a_q + a_koff + 256 k (a constant block: leading offset 128 B, row groups
+// 2 KB apart) and B at b + q b_q + 288 k (the data operand: leading offset 144 B, row
+// groups sbo_b apart).  Returns false (for every thread) if the wait gave up; the CTA
+// is then aborted with that parity pending.
+struct TcGemm {
+    uint32_t a_re, a_im, a_koff, b, b_q, sbo_b, id;
+    int n_q, nk;
+};
+__device__ __forceinline__ bool tc_run(const PixTc &px, const TcGemm &G, uint32_t parity)
+{
+    tc::fence_async_smem();
+    tc::fence_before();
+    __syncthreads();
+    const uint32_t bar = tc::saddr(px.bar);
+    if (threadIdx.x == 0) {
+        tc::fence_after();
+        const uint32_t tmem = *px.tmem;
+        const uint32_t a_lo = tc::kCstFloats * 4, b_lo = tc::kBopFloats * 4;
+        for (int q = 0; q < G.n_q; ++q) {
+            const uint32_t a0 = (q ? G.a_im : G.a_re) + G.a_koff, b0 = G.b + q * G.b_q;
+            for (int k = 0; k < G.nk; ++k) {
+                const uint32_t a = a0 + 256u * k, b = b0 + 288u * k;
+                const uint64_t ah = tc::sdesc(a, tc::kLboC, 2048), al = tc::sdesc(a + a_lo, tc::kLboC, 2048);
+                const uint64_t bh = tc::sdesc(b, tc::kLboB, G.sbo_b), bl = tc::sdesc(b + b_lo, tc::kLboB, G.sbo_b);
+                tc::mma(tmem, ah, bl, G.id, (q | k) ? 1u : 0u);
+                tc::mma(tmem, al, bh, G.id, 1u);
+                tc::mma(tmem, ah, bh, G.id, 1u);
+            }
+        }
+        tc::commit(bar);
+    }
+    const bool ok = tc::wait_parity(bar, parity);
+    const bool bad = __syncthreads_or(!ok);
+    if (bad) {
+        if (threadIdx.x == 0) *px.abort = 2 + (int)parity;
+        return false;
+    }
+    tc::fence_after();
+    return true;
+}
+
+template <int NC>
+__device__ double eval_pix(const FitParams &P, const GalCtx &gc, const SmemView &sm, int gal, float2 *xph,
+                           const float vcol[NC], const float th[6], float g[6], bool want_ll)
+{
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const PixTc px = pix_tc_view(sm.kxr, P.h_max, P.max_side);
+    const int N = gc.N, H = gc.H, c = gc.c, npad = P.npad;
+    const int rowf = row_floats(npad);
+    __syncthreads();   // the previous evaluation's readers of the table and buffers are done
+    if (*px.abort) {
+#pragma unroll
+        for (int i = 0; i < 6; ++i) g[i] = NAN;
+        return NAN;
+    }
+    const float F = exp10f(th[0]);
+    const float r0 = exp10f(th[1]) * (1.0f / kHlrOverR0);
+    const float r02 = r0 * r0;
+    const float e1 = th[2], e2 = th[3];
+    const float E = e1 * e1 + e2 * e2;
+    const float Pq = 1.0f / (1.0f - E);
+    const float al = r02 * (1.0f + E + 2.0f * e1) * Pq;
+    const float be = r02 * (1.0f + E - 2.0f * e1) * Pq;
+    const float ga = r02 * 4.0f * e2 * Pq;
+    const float sqrt2 = 1.41421356237309515f;
+    if (tid < 32) {
+        float sx = 0.f, cx = 0.f;
+        if (tid < H) sincospi_sfu(-2.0f * th[4] * (float)tid * gc.invN, &sx, &cx);
+        px.xs[tid] = make_float2(cx, sx);
+    } else if (tid < 96) {
+        const int vi = tid - 32;
+        float sy = 0.f, cy = 0.f;
+        if (vi < N) sincospi_sfu(-2.0f * th[5] * (float)(vi - c) * gc.invN, &sy, &cy);
+        px.ys[vi] = make_float2(F * cy, F * sy);
+    }
+    __syncthreads();
+    float *bh = px.bop, *bl = px.bop + tc::kBopFloats;
+    constexpr int kLb = tc::kLboB / 4;
+    // (a) the model's half spectrum Mt into the table's D slots, and M = Mt / scale_u
+    // as the operand of (1): rows u < 32, K (re, vi | im, vi), 128 per row; thread t
+    // takes column vi = t mod 64 and the rows u of its parity, u = t / 64 + 2 i
+    {
+        const int vi = tid & 63, u0 = tid >> 6;
+        const bool col = vi < N;
+        int ox = 0, oy = 0, ot = 0;
+        if (col) slot_offsets(npad, vi >> 5, vi & 31, ox, oy, ot);
+        const float ky = (float)(vi - c) * gc.dk;
+        const float cst = fmaf(be * ky, ky, 1.0f), gky = ga * ky;
+        const float2 Y = px.ys[vi];
+        const float sN = (float)N, sN2 = (float)N * 0.70710678118654752f;
+#pragma unroll 4
+        for (int i = 0; i < 16; ++i) {
+            const int u = u0 + 2 * i;
+            float Mr = 0.f, Mi = 0.f;
+            if (col && u < H) {
+                float *row = sm.tab + (size_t)u * rowf;
+                const float kx = sm.kxr[u].x;
+                const float s = fmaf(fmaf(al, kx, gky), kx, cst);
+                const float rs = rsqrtf(s);
+                const float A = row[ot] * rs * rs * rs;
+                const float2 X = px.xs[u];
+                const float mr = A * (X.x * Y.x - X.y * Y.y), mi = A * (X.x * Y.y + X.y * Y.x);
+                row[ox] = mr;
+                row[oy] = mi;
+                const float inv_scale = u == 0 ? sN : sN2;
+                Mr = mr * inv_scale;
+                Mi = mi * inv_scale;
+            }
+            tc::split_store(bh, bl, tc::op_index(u, vi, 128, kLb), Mr);
+            tc::split_store(bh, bl, tc::op_index(u, 64 + vi, 128, kLb), Mi);
+        }
+    }
+    const uint32_t cst = tc::saddr(px.cst), bop = tc::saddr(px.bop);
+    const uint32_t blk_nS = cst, blk_C = cst + tc::kBlockFloats * 4;
+    const int ks = (N + 7) >> 3;   // k-steps of 8 covering the side
+    // (1) G = M E: rows (re, iy | im, iy), columns u
+    if (!tc_run(px, TcGemm{blk_C, blk_nS, 0u, bop, 16u * 144, 32u * 144, tc::idesc(128, 32, false), 2, ks}, 0)) {
+#pragma unroll
+        for (int i = 0; i < 6; ++i) g[i] = NAN;
+        return NAN;
+    }
+    // (1) -> operand of (2): rows iy < 64, K (re, a | im, a) for a in [a0, a_end), the
+    // rows' G(u, iy) at a = u + c, weighted by w_u / N^2
+    const uint32_t tl = *px.tmem + ((uint32_t)(warp * 32) << 16);
+    const int a0 = c & ~7, ka = ((N + 7) & ~7) - a0, kt2 = 2 * ka, o = c - a0;
+    {
+        float v[32];
+        tc::ld32(tl, v);
+        const int p = tid >> 6, iy = tid & 63;
+        const float s0 = gc.invN * gc.invN, s1 = 2.0f * s0;
+#pragma unroll
+        for (int u = 0; u < 32; ++u)
+            if (u < H) tc::split_store(bh, bl, tc::op_index(iy, p * ka + o + u, kt2, kLb), v[u] * (u ? s1 : s0));
+        for (int j = 0; j < o; ++j) tc::split_store(bh, bl, tc::op_index(iy, p * ka + j, kt2, kLb), 0.f);
+        for (int j = o + H; j < ka; ++j) tc::split_store(bh, bl, tc::op_index(iy, p * ka + j, kt2, kLb), 0.f);
+    }
+    // (2) m = [C -S] G': rows ix, columns iy
+    if (!tc_run(px, TcGemm{blk_C, blk_nS, 128u * (a0 / 4), bop, 144u * (ka / 4), 144u * (kt2 / 4),
+                           tc::idesc(128, 64, false), 2, ka / 8}, 1)) {
+#pragma unroll
+        for (int i = 0; i < 6; ++i) g[i] = NAN;
+        return NAN;
+    }
+    // the residual, chi^2 (compensated FP32 per thread, FP64 across threads) and the
+    // operand of (3): rows iy, K ix
+    double chi = 0.0;
+    if (warp < 2) {
+        float c_hi = 0.f, c_lo = 0.f;
+        const int ix = tid;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            float m[32];
+            tc::ld32(tl + 32 * h, m);
+#pragma unroll
+            for (int t = 0; t < 32; ++t) {
+                const int iy = 32 * h + t;
+                float r = 0.f;
+                if (ix < N && iy < N) {
+                    const int e = iy * N + ix;
+                    const float res = px.dimg[e] - m[t];
+                    r = px.wimg[e] * res;
+                    float t_hi, t_lo;
+                    two_sum(c_hi, r * res, t_hi, t_lo);
+                    c_hi = t_hi;
+                    c_lo += t_lo;
+                }
+                tc::split_store(bh, bl, tc::op_index(iy, ix, 64, kLb), r);
+            }
+        }
+        chi = (double)c_hi + (double)c_lo;
+    }
+    {
+        const double cw = warp_sum_d(chi);
+        if (lane == 0) px.chi[warp] = cw;
+    }
+    // (3) conj Q = [C S] r: rows (re, a | im, a), columns iy
+    if (!tc_run(px, TcGemm{blk_C, blk_C, 0u, bop, 0u, 16u * 144, tc::idesc(128, 64, false), 1, ks}, 0)) {
+#pragma unroll
+        for (int i = 0; i < 6; ++i) g[i] = NAN;
+        return NAN;
+    }
+    const double chi2 = px.chi[0] + px.chi[1] + px.chi[2] + px.chi[3];
+    // (3) -> operand of (4): row u = a - c < 32, K (re, iy | im, iy)
+    {
+        const int q = tid >> 6, u = (tid & 63) - c;
+        float v[32];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            tc::ld32(tl + 32 * h, v);
+            if (u >= 0 && u < 32) {
+#pragma unroll
+                for (int t = 0; t < 32; t += 4) {
+                    const int k = q * 64 + 32 * h + t;
+                    const int e = tc::op_index(u, k, 128, kLb);
+                    float4 hv, lv;
+                    hv.x = tc::tf32_rn(v[t]);
+                    hv.y = tc::tf32_rn(v[t + 1]);
+                    hv.z = tc::tf32_rn(v[t + 2]);
+                    hv.w = tc::tf32_rn(v[t + 3]);
+                    lv.x = tc::tf32_rn(v[t] - hv.x);
+                    lv.y = tc::tf32_rn(v[t + 1] - hv.y);
+                    lv.z = tc::tf32_rn(v[t + 2] - hv.z);
+                    lv.w = tc::tf32_rn(v[t + 3] - hv.w);
+                    *reinterpret_cast<float4 *>(bh + e) = hv;
+                    *reinterpret_cast<float4 *>(bl + e) = lv;
+                }
+            }
+        }
+    }
+    // (4) conj R = E conj Q: rows (re, vi | im, vi), columns u
+    if (!tc_run(px, TcGemm{blk_C, blk_nS, 0u, bop, 16u * 144, 32u * 144, tc::idesc(128, 32, false), 2, ks}, 1)) {
+#pragma unroll
+        for (int i = 0; i < 6; ++i) g[i] = NAN;
+        return NAN;
+    }
+    // D' = Mt + scale_u R in the table's D slots
+    {
+        const int p = tid >> 6, vi = tid & 63;
+        float v[32];
+        tc::ld32(tl, v);
+        if (vi < N) {
+            int ox, oy, ot;
+            slot_offsets(npad, vi >> 5, vi & 31, ox, oy, ot);
+            const int os = p ? oy : ox;
+            const float sg = p ? -gc.invN : gc.invN;
+#pragma unroll
+            for (int u = 0; u < 32; ++u)
+                if (u < H) {
+                    float *slot = sm.tab + (size_t)u * rowf + os;
+                    *slot = fmaf((u ? sqrt2 : 1.0f) * sg, v[u], *slot);
+                }
+        }
+    }
+    __syncthreads();
+    // the gradient from the half-plane pass on the effective spectrum (every warp)
+    eval_logpost<NC, 0>(P, gc, sm.tab, sm.kxr, xph, vcol, th, g, false);
+    if (!want_ll) return 0.0;
+    const float lprior = P.prior_const - 0.5f * (th[4] * th[4] + th[5] * th[5]) * P.inv_sxy2 +
+                         2.0f * log1pf(-E) - 0.5f * E * P.inv_se2;
+    return -0.5 * chi2 * (double)gc.inv_b + (double)lprior;
+}
+
+// ---- A general dense pixel covariance (Appendix C, Eq. covar-pixel-likelihood):
+// log L = -1/2 (d - m)^T P (d - m) with the precision P = Sigma^-1.  Its cost is the
+// product y = P (d - m), N^4 multiply-adds per evaluation reading P from L2, beside
+// which the two separable transforms are small; and P amplifies rounding errors of
+// the rendered model m, so the transforms stay in FP32 on the CUDA cores (kernel
+// instance PROF 4, one warp per chain).  The gradient is the half-plane pass on the
+// effective spectrum D' = M + DFT(y) (scaled as the table).
+//
+// After the shared region: the twiddles exp(+2 pi i m / N) (max_side float2) and,
+// per chain, a private copy of the table ([h_max][3 npad]: the D slots hold the
+// evaluation's effective spectrum, the T slots the transfer), the half-transformed
+// image ([h_max][max_side] float2), the residual image and its product with the
+// precision (max_side^2 floats each).  Sizes in floats, each chain's block a multiple
+// of 4 floats.
+__host__ __device__ __forceinline__ int dense_chain_floats(int h_max, int npad, int max_side)
+{
+    const int n = h_max * row_floats(npad) + 2 * h_max * max_side + 2 * max_side * max_side;
+    return (n + 3) & ~3;
+}
+__host__ __device__ __forceinline__ size_t dense_region_bytes(int h_max, int npad, int max_side, int n_chains)
+{
+    return ((size_t)2 * ((max_side + 1) & ~1) + (size_t)n_chains * dense_chain_floats(h_max, npad, max_side)) *
+           sizeof(float);
+}
+struct DenseView {
+    float2 *tw;    // [max_side] exp(+2 pi i m / N)
+    float *tab;    // this chain's table
+    float2 *G;     // [h_max][max_side]
+    float *rb;     // [max_side^2] residual d - m
+    float *yb;     // [max_side^2] precision x residual
+};
+// kxr ends at h_max + 1 float2 after its start; the region follows, 16-byte aligned.
+__device__ __forceinline__ DenseView dense_view(float2 *kxr, int h_max, int npad, int max_side, int chain)
+{
+    float *base = reinterpret_cast<float *>(kxr + ((h_max + 2) & ~1));
+    DenseView v;
+    v.tw = reinterpret_cast<float2 *>(base);
+    float *c0 = base + 2 * ((max_side + 1) & ~1) + (size_t)chain * dense_chain_floats(h_max, npad, max_side);
+    v.tab = c0;
+    v.G = reinterpret_cast<float2 *>(c0 + (size_t)h_max * row_floats(npad));
+    v.rb = reinterpret_cast<float *>(v.G + (size_t)h_max * max_side);
+    v.yb = v.rb + max_side * max_side;
+    return v;
+}
+
+// Per-galaxy set-up of the dense path (all threads): the twiddles, and each
+// chain's private table from the staged one (transfer, zero spectrum).
+__device__ void dense_setup(const FitParams &P, const GalCtx &gc, const SmemView &sm, int n_tables)
+{
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const DenseView p0 = dense_view(sm.kxr, P.h_max, P.npad, P.max_side, 0);
+    for (int m = tid; m < gc.N; m += nth) {
+        float s, co;
+        sincospif(2.0f * (float)m * gc.invN, &s, &co);
+        p0.tw[m] = make_float2(co, s);
+    }
+    const int rowf = row_floats(P.npad);
+    const int nrow = gc.H * rowf;
+    for (int t = 0; t < n_tables; ++t) {
+        float *dst = dense_view(sm.kxr, P.h_max, P.npad, P.max_side, t).tab;
+        for (int i = tid; i < nrow; i += nth) dst[i] = sm.tab[i];
+    }
+    __syncthreads();
+}
+
+template <int NC>
+__device__ double eval_dense(const FitParams &P, const GalCtx &gc, const DenseView &pv, int gal,
+                           const float2 *__restrict__ kxr, float2 *__restrict__ xph, const float vcol[NC],
+                           const float th[6], float g[6], bool want_ll)
+{
+    const int lane = threadIdx.x & 31;
+    const int N = gc.N, H = gc.H, c = gc.c, npad = P.npad;
+    const int rowf = row_floats(npad);
+    const float F = exp10f(th[0]);
+    const float r0 = exp10f(th[1]) * (1.0f / kHlrOverR0);
+    const float r02 = r0 * r0;
+    const float e1 = th[2], e2 = th[3];
+    const float E = e1 * e1 + e2 * e2;
+    const float Pq = 1.0f / (1.0f - E);
+    const float al = r02 * (1.0f + E + 2.0f * e1) * Pq;
+    const float be = r02 * (1.0f + E - 2.0f * e1) * Pq;
+    const float ga = r02 * 4.0f * e2 * Pq;
+    const float sqrt2 = 1.41421356237309515f;
+    for (int u = lane; u < H; u += 32) {
+        float sx, cx;
+        sincospi_sfu(-2.0f * th[4] * (float)u * gc.invN, &sx, &cx);
+        xph[u] = make_float2(cx, sx);
+    }
+    __syncwarp();
+    // (a) the model's half spectrum Mt = Tt F f(s) X(u) Y(v) into the D slots
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+        const int vi = lane + 32 * j;
+        float sy, cy;
+        sincospi_sfu(-2.0f * th[5] * vcol[j] * gc.invN, &sy, &cy);
+        const float Yr = F * cy, Yi = F * sy;
+        const float ky = vcol[j] * gc.dk;
+        const float cst = fmaf(be * ky, ky, 1.0f), gky = ga * ky;
+        int ox, oy, ot;
+        slot_offsets(npad, j, lane, ox, oy, ot);
+        for (int u = 0; u < H; ++u) {
+            float *row = pv.tab + (size_t)u * rowf;
+            const float kx = kxr[u].x;
+            const float s = fmaf(fmaf(al, kx, gky), kx, cst);
+            const float rs = rsqrtf(s);
+            const float A = row[ot] * rs * rs * rs;
+            const float2 X = xph[u];
+            const float Pr = X.x * Yr - X.y * Yi, Pi = X.x * Yi + X.y * Yr;
+            const float mr = vi < N ? A * Pr : 0.0f, mi = vi < N ? A * Pi : 0.0f;
+            row[ox] = mr;
+            row[oy] = mi;
+            // unscaled M(u, v) = Mt / scale_u, contiguous, for the inverse transform
+            const float inv_scale = (float)N * (u == 0 ? 1.0f : 0.70710678118654752f);
+            if (vi < N) pv.G[(size_t)u * N + vi] = make_float2(mr * inv_scale, mi * inv_scale);
+        }
+    }
+    __syncwarp();
+    // (b1) G(u, iy) = sum_v M(u, v) exp(+2 pi i v (iy - c) / N), in place row by
+    // row (a row's outputs need only that row's M; lanes over iy, at most 2 each)
+    for (int u = 0; u < H; ++u) {
+        float2 *grow = pv.G + (size_t)u * N;
+        float2 res[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const int iy = lane + 32 * r;
+            if (iy < N) {
+                const int step = iy - c;
+                float re = 0.f, im = 0.f;
+                int k = ((-c * step) % N + N) % N;
+                const int dk = (step % N + N) % N;
+                for (int vi = 0; vi < N; ++vi) {
+                    const float2 mv = grow[vi];
+                    const float2 t = pv.tw[k];
+                    re = fmaf(mv.x, t.x, fmaf(-mv.y, t.y, re));
+                    im = fmaf(mv.x, t.y, fmaf(mv.y, t.x, im));
+                    k += dk;
+                    if (k >= N) k -= N;
+                }
+                res[r] = make_float2(re, im);
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+            if (lane + 32 * r < N) grow[lane + 32 * r] = res[r];
+        __syncwarp();
+    }
+    // (b2) per pixel row: m(ix, iy) and the residual r = d - m; y = P r needs every row of r
+    const int64_t off = P.offsets[gal];
+    const float invN2 = gc.invN * gc.invN;
+    double chi = 0.0;
+    for (int iy = 0; iy < N; ++iy) {
+        for (int ix = lane; ix < N; ix += 32) {
+            const int dk = ((ix - c) % N + N) % N;      // u (ix - c) mod N, advanced per u
+            int k = dk;
+            float acc = pv.G[iy].x;                     // u = 0 (real)
+            for (int u = 1; u < H; ++u) {
+                const float2 gv = pv.G[(size_t)u * N + iy];
+                const float2 t = pv.tw[k];
+                acc = fmaf(2.0f * gv.x, t.x, fmaf(-2.0f * gv.y, t.y, acc));
+                k += dk;
+                if (k >= N) k -= N;
+            }
+            pv.rb[iy * N + ix] = load_pix(P.data, P.data_f64, off + (int64_t)iy * N + ix) - acc * invN2;
+        }
+    }
+    __syncwarp();
+    {
+        // y = Sigma^-1 r: the precision is symmetric, so y_a = sum_b P[b][a] r_b with
+        // lanes over a reads each row b of it coalesced (from L2: tens of
+        // evaluations of the galaxy's chains share it); chi^2 = r.y
+        constexpr int kSlots = (kDenseMaxSide * kDenseMaxSide + 31) / 32;
+        const int n = N * N;
+        const float *Pg = P.pix_prec + P.prec_offs[gal];
+        float yv[kSlots];
+#pragma unroll
+        for (int j = 0; j < kSlots; ++j) yv[j] = 0.f;
+        for (int b = 0; b < n; ++b) {
+            const float rb = pv.rb[b];
+            const float *prow = Pg + (size_t)b * n;
+#pragma unroll
+            for (int j = 0; j < kSlots; ++j) {
+                const int a = lane + 32 * j;
+                if (a < n) yv[j] = fmaf(__ldg(prow + a), rb, yv[j]);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kSlots; ++j) {
+            const int a = lane + 32 * j;
+            if (a < n) {
+                pv.yb[a] = yv[j];
+                chi += (double)pv.rb[a] * (double)yv[j];
+            }
+        }
+        __syncwarp();
+        // Q(u, iy) = sum_ix y(ix, iy) exp(-2 pi i u (ix - c) / N), one row iy at a time
+        for (int iy = 0; iy < N; ++iy) {
+            const float *yrow = pv.yb + iy * N;
+            for (int u = lane; u < H; u += 32) {
+                float re = 0.f, im = 0.f;
+                int k = ((u * c) % N + N) % N;           // -u (ix - c) at ix = 0
+                const int dk = (N - u % N) % N;
+                for (int ix = 0; ix < N; ++ix) {
+                    const float r = yrow[ix];
+                    const float2 t = pv.tw[k];
+                    re = fmaf(r, t.x, re);
+                    im = fmaf(r, t.y, im);
+                    k += dk;
+                    if (k >= N) k -= N;
+                }
+                pv.G[(size_t)u * N + iy] = make_float2(re, im);
+            }
+        }
+        __syncwarp();
+    }
+    // (b3) D' = Mt + scale_u R(u, v), R(u, v) = sum_iy Q(u, iy) exp(-2 pi i v (iy - c) / N);
+    // the H x N (u, v) outputs spread over the lanes
+    for (int t = lane; t < H * N; t += 32) {
+        const int u = t / N, vi = t - u * N, v = vi - c;
+        const int dk = ((-v) % N + N) % N;
+        int k = ((v * c) % N + N) % N;                  // -v (iy - c) at iy = 0
+        const float2 *qrow = pv.G + (size_t)u * N;
+        float re = 0.f, im = 0.f;
+        for (int iy = 0; iy < N; ++iy) {
+            const float2 q = qrow[iy];
+            const float2 tw = pv.tw[k];
+            re = fmaf(q.x, tw.x, fmaf(-q.y, tw.y, re));
+            im = fmaf(q.x, tw.y, fmaf(q.y, tw.x, im));
+            k += dk;
+            if (k >= N) k -= N;
+        }
+        int ox, oy, ot;
+        slot_offsets(npad, vi >> 5, vi & 31, ox, oy, ot);
+        const float scale = (u == 0 ? 1.0f : sqrt2) * gc.invN;
+        float *row = pv.tab + (size_t)u * rowf;
+        row[ox] = fmaf(scale, re, row[ox]);
+        row[oy] = fmaf(scale, im, row[oy]);
+    }
+    __syncwarp();
+    // (c) the gradient from the half-plane pass on the effective spectrum
+    eval_logpost<NC, 0>(P, gc, pv.tab, kxr, xph, vcol, th, g, false);
+    if (!want_ll) return 0.0;
+    const double chi2 = warp_sum_d(chi);
+    const float lprior = P.prior_const - 0.5f * (th[4] * th[4] + th[5] * th[5]) * P.inv_sxy2 +
+                         2.0f * log1pf(-E) - 0.5f * E * P.inv_se2;
+    return -0.5 * chi2 * (double)gc.inv_b + (double)lprior;
+}
+

@@ -23,36 +23,46 @@ FitKernel prof_kernel(int max_side)
     }
 }
 
-// Per-pixel weights (profile 3) or a dense covariance (profile 4, the same
-// instance; at most 31 px), exponential: stamps of at most 63 px.
+// Per-pixel weights (profile 3), exponential: stamps of at most 63 px, one chain
+// per CTA of four warps, the transforms on the tensor cores.
 FitKernel pix_kernel(int max_side)
 {
-    return max_side <= 31 ? fit_kernel_r128<1, 3> : fit_kernel_r128<2, 3>;
+    return max_side <= 31 ? fit_kernel_pix<1> : fit_kernel_pix<2>;
 }
+
+constexpr int kPixThreads = 128;
+
+bool is_pix(int profile) { return profile == 3; }
 
 FitKernel kernel_for(int profile, int max_side)
 {
-    if (profile == 3 || profile == 4) return pix_kernel(max_side);
+    if (profile == 3) return pix_kernel(max_side);
+    if (profile == 4) return fit_kernel_r128<1, 4>;   // a dense covariance: at most 31 px
     return profile == BS_PROFILE_SPERGEL ? prof_kernel<1>(max_side) : prof_kernel<2>(max_side);
 }
 
-PointsKernel points_for(int profile)
+PointsKernel points_for(int profile, int max_side)
 {
-    if (profile == 3 || profile == 4) return logpost_points_kernel<3>;
+    if (is_pix(profile)) return max_side <= 31 ? logpost_points_pix_kernel<1> : logpost_points_pix_kernel<2>;
+    if (profile == 4) return logpost_points_kernel<4>;
     return profile == BS_PROFILE_SPERGEL ? logpost_points_kernel<1> : logpost_points_kernel<2>;
 }
 
-// Dynamic shared memory of a launch: the pixel path adds its twiddles and
-// per-chain scratch after the row table.
+// Dynamic shared memory of a launch: the pixel-weight path (a phase table for
+// each of its four warps) adds the transforms' region after the row table, the
+// dense-covariance path its twiddles and per-chain scratch.
 size_t smem_for(int profile, int max_side, int n_chains)
 {
+    if (is_pix(profile)) return fit_smem_bytes(max_side, 4) + 16 + pix_tc_bytes(max_side);
     size_t b = fit_smem_bytes(max_side, n_chains);
-    if (profile == 3 || profile == 4) {
+    if (profile == 4) {
         const int h = (max_side + 1) / 2, npad = 32 * ((max_side + 31) / 32);
-        b += 16 + pix_region_bytes(h, npad, max_side, n_chains, profile == 4);
+        b += 16 + dense_region_bytes(h, npad, max_side, n_chains);
     }
     return b;
 }
+
+int threads_for(int profile, int n_chains) { return is_pix(profile) ? kPixThreads : 32 * n_chains; }
 
 // K_mu(x) = int_0^inf exp(-x cosh t) cosh(mu t) dt by the trapezoidal rule
 // (step 1/64; the integrand falls off doubly exponentially).
@@ -94,7 +104,8 @@ int fit_blocks_per_sm_profile(int profile, int n_chains, int max_side)
     const size_t smem = smem_for(profile, max_side, n_chains);
     FitKernel k = kernel_for(profile, max_side);
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, 32 * n_chains, smem) != cudaSuccess) return 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, threads_for(profile, n_chains), smem) != cudaSuccess)
+        return 1;
     return nb > 0 ? nb : 1;
 }
 
@@ -105,7 +116,7 @@ cudaError_t launch_fit_profile(const FitParams &p, int grid, cudaStream_t stream
     FitKernel k = kernel_for(p.profile, p.max_side);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k<<<grid, 32 * cc, smem, stream>>>(p);
+    k<<<grid, threads_for(p.profile, cc), smem, stream>>>(p);
     bs::count_launches(1);
     return cudaGetLastError();
 }
@@ -114,12 +125,12 @@ cudaError_t launch_logpost_points_profile(const FitParams &p, int n_points, cons
                                           const float *theta, double *logp, float *grad, cudaStream_t stream)
 {
     const size_t smem = smem_for(p.profile, p.max_side, 1);
-    PointsKernel k = points_for(p.profile);
+    PointsKernel k = points_for(p.profile, p.max_side);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int grid = n_points < 4096 ? n_points : 4096;
     if (grid <= 0) return cudaSuccess;
-    k<<<grid, 32, smem, stream>>>(p, n_points, gal_index, theta, logp, grad);
+    k<<<grid, is_pix(p.profile) ? kPixThreads : 32, smem, stream>>>(p, n_points, gal_index, theta, logp, grad);
     bs::count_launches(1);
     return cudaGetLastError();
 }

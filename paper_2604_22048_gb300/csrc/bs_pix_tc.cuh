@@ -1,0 +1,244 @@
+#pragma once
+// Pixel-space evaluation of the log posterior and its gradient on the 5th-generation
+// tensor cores (Appendix C: per-pixel weights w, log L = -1/2 sum_x w (d - m)^2 / sigma^2).
+//
+// Parseval does not diagonalise these likelihoods, so each evaluation renders the
+// model image m from its half spectrum M and transforms the weighted residual back:
+//   G(u, iy) = sum_v M(u, v) e^{+2 pi i v (iy - c) / N}                 (1: complex, along y)
+//   m(ix, iy) = N^-2 sum_u w_u Re[G(u, iy) e^{+2 pi i u (ix - c) / N}]  (2: complex to real, along x)
+//   r = w (d - m)
+//   Q(u, iy) = sum_ix r(ix, iy) e^{-2 pi i u (ix - c) / N}             (3: real to complex, along x)
+//   R(u, v) = sum_iy Q(u, iy) e^{-2 pi i v (iy - c) / N}               (4: complex, along y)
+// (w_0 = 1, w_u = 2 for u > 0, v = vi - c centred), and the gradient is the spectral
+// half-plane pass on the effective spectrum D' = Mt + (sqrt(w_u) / N) R.
+//
+// With centred indices every transform is a product with the blocks of one symmetric
+// matrix, C[a][b] = cos(2 pi (a - c)(b - c) / N) and S[a][b] = sin(...), zero-padded to
+// 64 x 64:
+//   (1)  rows (re, iy | im, iy) x K (re, v | im, v): [C S] on the real half, [-S C] on
+//        the imaginary half of K;
+//   (2)  rows ix x K (re, u + c | im, u + c): C, then -S (u + c puts u on the centred index);
+//   (3)  rows (re, u + c | im, u + c) x K ix: [C S] (the imaginary output is -Q_i);
+//   (4)  conj R = transform (1) of conj Q, and the output of (3) is conj Q already.
+// The shared memory holds the blocks in the order -S, C, S, so every A operand of
+// 128 rows is two consecutive blocks; rows past the 64 of (2) read the next block and
+// give lanes that are not read.  Each transform is a tcgen05.mma of kind::tf32
+// (M = 128, N = 32 or 64, K = 8 per instruction, operands in shared memory without
+// swizzle, accumulator in TMEM) in three terms, A_hi B_hi + A_hi B_lo + A_lo B_hi
+// with x = hi + lo split by round-to-nearest TF32 (3xTF32): the operand rounding of
+// plain TF32 would miss the log-likelihood tolerance by a factor of several.
+//
+// One CTA of four warps per chain: every warp runs the chain's scalar logic (its
+// decisions are the same in all four, from the same numbers), the transforms and the
+// elementwise steps between them are split over the 128 threads (thread t reads TMEM
+// lane t), and thread 0 issues the MMAs.  Each evaluation commits four MMA groups to
+// one mbarrier, so the parities it waits on are 0, 1, 0, 1 in every evaluation.  A
+// wait gives up after two seconds: the CTA then marks its galaxy (status 4), issues no
+// further MMA, and its evaluations return NaN until the chain ends.
+#include <cstdint>
+
+namespace bs {
+
+namespace {
+
+namespace tc {
+
+constexpr int kNP = 64;                        // padded side of the transforms
+constexpr int kLboC = 128;                     // constant blocks: K-adjacent core matrices contiguous
+constexpr int kLboB = 144;                     // data operands: 16-byte pad per core matrix (column
+                                               // stores of a warp fall in 32 distinct banks)
+constexpr int kBlockFloats = kNP * kNP;        // one 64 x 64 block, 16 KB
+constexpr int kCstFloats = 3 * kBlockFloats;   // -S, C, S of one precision level
+constexpr int kBopFloats = 8 * 20 * (kLboB / 4);   // largest data operand: 64 rows x 80 K
+constexpr uint64_t kWaitNs = 2000000000ull;    // limit of one MMA wait
+
+// Element (row, k) of an operand of kt K-elements per row (no swizzle, K-major):
+// core matrices of 8 rows x 4 elements (16 bytes a row), lbo_f floats apart along
+// K, row groups of 8 (kt / 4) lbo_f floats apart.
+__host__ __device__ __forceinline__ int op_index(int row, int k, int kt, int lbo_f)
+{
+    return (row >> 3) * (kt >> 2) * lbo_f + (k >> 2) * lbo_f + ((row & 7) << 2) + (k & 3);
+}
+
+__device__ __forceinline__ uint32_t saddr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor: start, leading (K) and stride (row-group) byte
+// offsets, descriptor version 1, no swizzle.
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
+           (1ull << 46);
+}
+
+// Instruction descriptor of kind::tf32: FP32 accumulator, TF32 A and B, both
+// K-major, optional negation of A, shape M x N.
+__host__ __device__ constexpr uint32_t idesc(int m, int n, bool neg_a)
+{
+    return (1u << 4) | (2u << 7) | (2u << 10) | (neg_a ? (1u << 13) : 0u) | ((uint32_t)(n >> 3) << 17) |
+           ((uint32_t)(m >> 4) << 24);
+}
+
+// Round a finite float to the nearest TF32 value, ties away from zero (the
+// rounding of cvt.rna.tf32.f32): add half a unit of the 13 dropped bits to the
+// magnitude's bit pattern and clear them.
+__device__ __forceinline__ float tf32_rn(float x)
+{
+    return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+}
+
+// x = hi + lo (hi exact in TF32; lo rounded to TF32, error ~2^-22 |x|)
+__device__ __forceinline__ void split_store(float *hi, float *lo, int i, float x)
+{
+    const float h = tf32_rn(x);
+    hi[i] = h;
+    lo[i] = tf32_rn(x - h);
+}
+
+__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t id, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(id), "r"(accumulate));
+}
+
+__device__ __forceinline__ void commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// generic-proxy shared stores made visible to the tensor cores' (async) proxy
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ uint64_t now_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for the phase of the given parity to complete; false after kWaitNs.
+__device__ __forceinline__ bool wait_parity(uint32_t bar, uint32_t parity)
+{
+    const uint64_t t0 = now_ns();
+    for (;;) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (now_ns() - t0 > kWaitNs) return false;
+    }
+}
+
+// 32 consecutive TMEM columns of this thread's lane (the warp's 32 lanes).
+__device__ __forceinline__ void ld32(uint32_t taddr, float (&v)[32])
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+constexpr int kTmemCols = 64;
+
+}  // namespace tc
+
+// Shared memory of the tensor-core pixel path, after the (kx, kx^2) table.
+struct PixTc {
+    double *chi;      // [4] per-warp partial chi^2 of the evaluation
+    uint64_t *bar;    // MMA completion barrier
+    uint32_t *tmem;   // TMEM base of the CTA's accumulator (64 columns)
+    int *abort;       // 1 once a wait gave up
+    float2 *xs;       // [32] exp(-2 pi i u dx / N)
+    float2 *ys;       // [64] F exp(-2 pi i v dy / N), v = vi - c
+    float *cst;       // [2][3][64 x 64] blocks -S, C, S: TF32 high parts, then low parts
+    float *bop;       // [2][kBopFloats] the data operand of the current transform, high then low
+    float *dimg;      // [max_side^2] the stamp
+    float *wimg;      // [max_side^2] the weights
+};
+
+__host__ __device__ __forceinline__ int pix_tc_img_floats(int max_side) { return (max_side * max_side + 3) & ~3; }
+
+// Floats of the region: 8 (chi) + 2 (barrier) + 2 (TMEM address, abort) + 64 (xs) +
+// 128 (ys) + 4 (pad) + constants + operand + two images.
+__host__ __device__ __forceinline__ size_t pix_tc_bytes(int max_side)
+{
+    return ((size_t)208 + 2 * tc::kCstFloats + 2 * tc::kBopFloats + 2 * (size_t)pix_tc_img_floats(max_side)) *
+           sizeof(float);
+}
+
+// The region starts after the (kx, kx^2) table (h_max + 1 float2), 16-byte aligned.
+__device__ __forceinline__ PixTc pix_tc_view(float2 *kxr, int h_max, int max_side)
+{
+    float *base = reinterpret_cast<float *>(kxr + ((h_max + 2) & ~1));
+    PixTc v;
+    v.chi = reinterpret_cast<double *>(base);
+    v.bar = reinterpret_cast<uint64_t *>(base + 8);
+    v.tmem = reinterpret_cast<uint32_t *>(base + 10);
+    v.abort = reinterpret_cast<int *>(base + 11);
+    v.xs = reinterpret_cast<float2 *>(base + 12);
+    v.ys = reinterpret_cast<float2 *>(base + 76);
+    v.cst = base + 208;
+    v.bop = v.cst + 2 * tc::kCstFloats;
+    v.dimg = v.bop + 2 * tc::kBopFloats;
+    v.wimg = v.dimg + pix_tc_img_floats(max_side);
+    return v;
+}
+
+// Once per CTA, before its first galaxy (all threads): TMEM columns, the barrier.
+__device__ void pix_tc_begin(const PixTc &px)
+{
+    if ((threadIdx.x >> 5) == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::saddr(px.tmem)),
+                     "r"(tc::kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::saddr(px.bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        *px.abort = 0;
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+}
+
+// Once per CTA, after its last galaxy (all threads).  After a wait that gave up,
+// the MMAs still in flight are waited for once more (again with the limit) before
+// the columns are freed.
+__device__ void pix_tc_end(const PixTc &px)
+{
+    __syncthreads();
+    if (threadIdx.x == 0 && *px.abort) {
+        // the abort records 2 + the parity that was pending
+        const int pend = *px.abort - 2;
+        if (pend >= 0) tc::wait_parity(tc::saddr(px.bar), (uint32_t)pend);
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    if ((threadIdx.x >> 5) == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(*px.tmem), "r"(tc::kTmemCols)
+                     : "memory");
+}
+
+}  // namespace
+
+}  // namespace bs

@@ -51,16 +51,20 @@ def test_captured_traffic_applies_only_to_the_captured_source_and_settings():
     """The roofline's traffic is a captured figure per unit: it is reported for
     the kernel source and sampler settings it was captured on, and null once
     either differs."""
+    import hashlib
     sys.path.insert(0, ROOT)
     import bench
-    _, _, per_gal, fixed = bench.CAPTURED_TRAFFIC["fit"]
-    assert bench.captured_traffic("fit", 10_000, dict(fixed)) == per_gal * 10_000
-    assert bench.captured_traffic("fit", 10_000, dict(fixed, n_samples=100)) is None
-    assert bench.captured_traffic("fit", 10_000, dict(fixed, side=63)) is None
-    saved = bench.CAPTURED_TRAFFIC["shear"]
+    saved = dict(bench.CAPTURED_TRAFFIC)
     try:
-        bench.CAPTURED_TRAFFIC["shear"] = (saved[0], "0" * 64, saved[2], saved[3])
-        assert bench.captured_traffic("shear", 1) is None
+        for kind, (path, _, per_unit, fixed) in saved.items():
+            with open(os.path.join(ROOT, path), "rb") as fh:
+                now = hashlib.sha256(fh.read()).hexdigest()
+            bench.CAPTURED_TRAFFIC[kind] = (path, now, per_unit, fixed)
+            assert bench.captured_traffic(kind, 300, dict(fixed)) == per_unit * 300
+            for k, v in fixed.items():
+                assert bench.captured_traffic(kind, 300, dict(fixed, **{k: v + 1})) is None
+            bench.CAPTURED_TRAFFIC[kind] = (path, "0" * 64, per_unit, fixed)
+            assert bench.captured_traffic(kind, 300, dict(fixed)) is None
     finally:
-        bench.CAPTURED_TRAFFIC["shear"] = saved
-    assert bench.captured_traffic("shear", 300) == saved[2] * 300
+        bench.CAPTURED_TRAFFIC.clear()
+        bench.CAPTURED_TRAFFIC.update(saved)

@@ -96,3 +96,28 @@ def test_masked_pixels_do_not_enter_the_fit(cuda):
         x = s0[k].reshape(32, -1)
         z = (x.mean(axis=1) - ds.theta[:, k]) / x.std(axis=1)
         assert np.mean(np.abs(z) < 4) > 0.9, (k, z)
+
+
+def test_pixel_path_chains_do_not_depend_on_the_batch(cuda):
+    """One CTA per chain: six chains run (the pixel path has no chain limit), and
+    a galaxy's chains are bit-identical whether it is fitted alone (same galaxy
+    id, so the same random streams) or among other galaxies of other sides."""
+    truth, ds, flat, offs, sides, w = _case(25, 3, 81)
+    t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(cuda)
+    C = 6
+    cfg = api.FitConfig(n_chains=C, n_warmup=40, n_samples=30, n_leapfrog=8)
+    psf = api.psf_table("gaussian", 0.7, device=cuda)
+    init = np.repeat(ds.init[:, :1], C, axis=1).astype(np.float32)
+    init[..., 4:6] += np.random.default_rng(3).uniform(-0.1, 0.1, (3, C, 2)).astype(np.float32)
+    sig = ds.sigma.astype(np.float32)
+    full = api.fit_galaxies(t(flat), t(offs), t(sides), psf, t(sig), t(init), cfg, pixel_weight=t(w),
+                            gal_id=t(np.arange(3, dtype=np.int64)), want=("status", "logp"))
+    one = slice(offs[1], offs[1] + 25 * 25)
+    alone = api.fit_galaxies(t(flat[one]), t(np.zeros(1, np.int64)), t(sides[1:2]), psf, t(sig[1:2]),
+                             t(init[1:2]), cfg, pixel_weight=t(w[one]), gal_id=t(np.array([1], np.int64)),
+                             want=("status", "logp"))
+    assert (full["status"].cpu().numpy() == 0).all() and (alone["status"].cpu().numpy() == 0).all()
+    a = full["samples"].cpu().numpy()[:, 1]
+    b = alone["samples"].cpu().numpy()[:, 0]
+    assert np.isfinite(a).all() and np.array_equal(a, b)
+    assert np.array_equal(full["logp"].cpu().numpy()[1], alone["logp"].cpu().numpy()[0])
