@@ -878,7 +878,7 @@ __device__ void run_chain(const FitParams &P, const GalCtx &gc, const SmemView &
     const int lane = threadIdx.x & 31;
     const int pi = lane < 6 ? lane : 5;     // parameter of this lane (lanes 6.. shadow parameter 5)
     const bool own = lane < 6;
-    // the pixel path's four warps run the same chain: the first one writes its results
+    // the pixel path's eight warps run the same chain: the first one writes its results
     const bool wr = PROF != 3 || threadIdx.x < 32;
     const int C = P.n_chains, W = P.n_warmup, S = P.n_samples, L = P.n_leapfrog;
     const uint64_t gid = P.gal_id ? P.gal_id[gal] : (uint64_t)gal;
@@ -1098,8 +1098,9 @@ __device__ __forceinline__ void fit_loop(const FitParams &P)
     __shared__ int s_gal, s_grp;
     const int cc = cta_chains(P);              // chains of this CTA
     const int groups = P.n_chains / cc;        // CTAs a galaxy's chains are split over
-    // the pixel path: one chain per CTA, run by its four warps (a phase table each)
-    const SmemView sm = smem_view(smem_raw, P.h_max, P.npad, P.max_side, PROF == 3 ? 4 : cc);
+    // the pixel path: one chain per CTA, run by its eight warps (the first one's phase
+    // table serves the spectral pass)
+    const SmemView sm = smem_view(smem_raw, P.h_max, P.npad, P.max_side, PROF == 3 ? 1 : cc);
     const int warp = threadIdx.x >> 5;
     if constexpr (PROF == 3) pix_tc_begin(pix_tc_view(sm.kxr, P.h_max, P.max_side));
     bool first = true;
@@ -1139,7 +1140,7 @@ __device__ __forceinline__ void fit_loop(const FitParams &P)
         if constexpr (PROF == 3) {
             const PixTc px = pix_tc_view(sm.kxr, P.h_max, P.max_side);
             pix_tc_setup(P, gc, px, gal);
-            run_chain<NC, PROF>(P, gc, sm, gal, s_grp, warp);
+            run_chain<NC, PROF>(P, gc, sm, gal, s_grp, 0);
             __syncthreads();
             if (threadIdx.x == 0 && *px.abort && P.status) P.status[gal] = 4;
         } else {
@@ -1162,10 +1163,10 @@ template <int NC, int PROF>
 __global__ void __launch_bounds__(128, 5) fit_kernel_r96(const FitParams P) { fit_loop<NC, PROF>(P); }
 template <int NC, int PROF>
 __global__ void __launch_bounds__(256, 3) fit_kernel_r80(const FitParams P) { fit_loop<NC, PROF>(P); }
-// The pixel path: one chain per CTA of four warps; its shared memory (the transforms'
-// constant blocks and operands) allows one CTA per SM.
+// The pixel path: one chain per CTA of eight warps; its shared memory (the transforms'
+// constants and operands) allows one CTA per SM.
 template <int NC>
-__global__ void __launch_bounds__(128, 1) fit_kernel_pix(const FitParams P) { fit_loop<NC, 3>(P); }
+__global__ void __launch_bounds__(tc::kThreads, 1) fit_kernel_pix(const FitParams P) { fit_loop<NC, 3>(P); }
 
 // One CTA of 32 threads per point: stage the galaxy, then evaluate.
 template <int NC, int PROF>
@@ -1182,8 +1183,7 @@ __device__ void point_eval(const FitParams &P, const GalCtx &gc, const SmemView 
     double v = -INFINITY;
     if (in_support(P, th)) {
         if constexpr (PROF == 3)
-            v = eval_pix<NC>(P, gc, sm, gal, sm.xph + (threadIdx.x >> 5) * phase_stride(P.h_max), vcol, th, g,
-                             true);
+            v = eval_pix<NC>(P, gc, sm, gal, sm.xph, vcol, th, g, true);
         else if constexpr (PROF == 4)
             v = eval_dense<NC>(P, gc, dense_view(sm.kxr, P.h_max, P.npad, P.max_side, 0), gal, sm.kxr, sm.xph, vcol,
                                th, g, true);
@@ -1233,14 +1233,14 @@ __global__ void __launch_bounds__(32) logpost_points_kernel(const FitParams P, i
     }
 }
 
-// The pixel path's points: one CTA of four warps per point.
+// The pixel path's points: one CTA of eight warps per point.
 template <int NC>
-__global__ void __launch_bounds__(128, 1) logpost_points_pix_kernel(const FitParams P, int n_points,
+__global__ void __launch_bounds__(tc::kThreads, 1) logpost_points_pix_kernel(const FitParams P, int n_points,
                                                                     const int32_t *gal_index, const float *theta,
                                                                     double *logp, float *grad)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const SmemView sm = smem_view(smem_raw, P.h_max, P.npad, P.max_side, 4);
+    const SmemView sm = smem_view(smem_raw, P.h_max, P.npad, P.max_side, 1);
     const PixTc px = pix_tc_view(sm.kxr, P.h_max, P.max_side);
     pix_tc_begin(px);
     for (int i = blockIdx.x; i < n_points; i += gridDim.x) {

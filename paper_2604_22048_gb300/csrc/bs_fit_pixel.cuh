@@ -9,14 +9,15 @@
 // Re[conj(R_k) dM_k / dtheta] / (sigma^2 N^2) with R = DFT(w (d - m)), so the half-plane
 // pass of eval_logpost gives it when its data spectrum is replaced by the effective
 // D' = M + R (scaled as the table).  The transforms run on the tensor cores (the layout
-// and operand split are described with PixTc); one CTA of four warps evaluates one chain.
+// and operand split are described with PixTc); one CTA of eight warps evaluates one chain.
 
-// Per galaxy (all threads): the constant blocks -S, C, S for this side (high and low
-// TF32 parts), and the stamp and its weights in shared memory.
+// Per galaxy (all threads): the constant blocks -S, C, S and the complex-to-real
+// constant of transform (2) for this side (high and low TF32 parts), and the stamp
+// and its weights in shared memory.
 __device__ void pix_tc_setup(const FitParams &P, const GalCtx &gc, const PixTc &px, int gal)
 {
     const int tid = threadIdx.x, nth = blockDim.x;
-    const int N = gc.N, c = gc.c;
+    const int N = gc.N, c = gc.c, H = gc.H;
     float *hi = px.cst, *lo = px.cst + tc::kCstFloats;
     for (int i = tid; i < tc::kNP * tc::kNP; i += nth) {
         const int a = i >> 6, b = i & 63;
@@ -31,6 +32,22 @@ __device__ void pix_tc_setup(const FitParams &P, const GalCtx &gc, const PixTc &
         tc::split_store(hi, lo, tc::kBlockFloats + e, co);
         tc::split_store(hi, lo, 2 * tc::kBlockFloats + e, sn);
     }
+    // rows ix, K (re, u | im, u): (w_u / N^2) (cos, -sin)(2 pi u (ix - c) / N)
+    const float wn = 1.0f / ((float)N * (float)N);
+    for (int i = tid; i < tc::kNP * 32; i += nth) {
+        const int ix = i >> 5, u = i & 31;
+        float co = 0.f, sn = 0.f;
+        if (ix < N && u < H) {
+            int k = (u * (ix - c)) % N;
+            if (k < 0) k += N;
+            sincospif(2.0f * (float)k / (float)N, &sn, &co);
+            const float wu = u ? 2.0f * wn : wn;
+            co *= wu;
+            sn *= wu;
+        }
+        tc::split_store(px.c2r, px.c2r + tc::kC2rFloats, tc::op_index(ix, u, 64, tc::kLboC / 4), co);
+        tc::split_store(px.c2r, px.c2r + tc::kC2rFloats, tc::op_index(ix, 32 + u, 64, tc::kLboC / 4), -sn);
+    }
     const int64_t off = P.offsets[gal];
     const int n = N * N;
     for (int i = tid; i < n; i += nth) {
@@ -42,12 +59,12 @@ __device__ void pix_tc_setup(const FitParams &P, const GalCtx &gc, const PixTc &
 
 // One 3xTF32 product into TMEM (all threads; thread 0 issues and commits, everyone
 // waits for the given parity).  K runs over n_q halves of nk steps of 8: step (q, k)
-// reads A at a_q + a_koff + 256 k (a constant block: leading offset 128 B, row groups
-// 2 KB apart) and B at b + q b_q + 288 k (the data operand: leading offset 144 B, row
-// groups sbo_b apart).  Returns false (for every thread) if the wait gave up; the CTA
-// is then aborted with that parity pending.
+// reads A at a_q + 256 k (a constant: leading offset 128 B, row groups 2 KB apart,
+// its low part a_lo bytes after the high part) and B at b + q b_q + 288 k (the data
+// operand: leading offset 144 B, row groups sbo_b apart).  Returns false (for every
+// thread) if the wait gave up; the CTA is then aborted with that parity pending.
 struct TcGemm {
-    uint32_t a_re, a_im, a_koff, b, b_q, sbo_b, id;
+    uint32_t a_re, a_im, a_lo, b, b_q, sbo_b, id;
     int n_q, nk;
 };
 __device__ __forceinline__ bool tc_run(const PixTc &px, const TcGemm &G, uint32_t parity)
@@ -59,16 +76,21 @@ __device__ __forceinline__ bool tc_run(const PixTc &px, const TcGemm &G, uint32_
     if (threadIdx.x == 0) {
         tc::fence_after();
         const uint32_t tmem = *px.tmem;
-        const uint32_t a_lo = tc::kCstFloats * 4, b_lo = tc::kBopFloats * 4;
+        const uint32_t b_lo = tc::kBopFloats * 4;
         for (int q = 0; q < G.n_q; ++q) {
-            const uint32_t a0 = (q ? G.a_im : G.a_re) + G.a_koff, b0 = G.b + q * G.b_q;
+            const uint32_t a0 = q ? G.a_im : G.a_re, b0 = G.b + q * G.b_q;
+            // a k-step advances the start-address field (bytes / 16, the low 14 bits;
+            // every address stays below 256 KB, so the field does not carry)
+            uint64_t ah = tc::sdesc(a0, tc::kLboC, 2048), al = tc::sdesc(a0 + G.a_lo, tc::kLboC, 2048);
+            uint64_t bh = tc::sdesc(b0, tc::kLboB, G.sbo_b), bl = tc::sdesc(b0 + b_lo, tc::kLboB, G.sbo_b);
             for (int k = 0; k < G.nk; ++k) {
-                const uint32_t a = a0 + 256u * k, b = b0 + 288u * k;
-                const uint64_t ah = tc::sdesc(a, tc::kLboC, 2048), al = tc::sdesc(a + a_lo, tc::kLboC, 2048);
-                const uint64_t bh = tc::sdesc(b, tc::kLboB, G.sbo_b), bl = tc::sdesc(b + b_lo, tc::kLboB, G.sbo_b);
                 tc::mma(tmem, ah, bl, G.id, (q | k) ? 1u : 0u);
                 tc::mma(tmem, al, bh, G.id, 1u);
                 tc::mma(tmem, ah, bh, G.id, 1u);
+                ah += 256 / 16;
+                al += 256 / 16;
+                bh += 288 / 16;
+                bl += 288 / 16;
             }
         }
         tc::commit(bar);
@@ -83,20 +105,154 @@ __device__ __forceinline__ bool tc_run(const PixTc &px, const TcGemm &G, uint32_
     return true;
 }
 
+__device__ __forceinline__ double pix_nan(float g[6])
+{
+#pragma unroll
+    for (int i = 0; i < 6; ++i) g[i] = NAN;
+    return NAN;
+}
+
+// The gradient of the log posterior from the half-plane pass on the effective
+// spectrum in the table, with the rows split over the eight warps: warp w sums the
+// terms of its rows u in [r w, r (w + 1)), r even (the pass reads rows in pairs), and
+// the six warp sums meet in shared memory, where every thread adds them in warp order
+// and forms the gradient.  The per-point terms, the sums and the gradient formulas are
+// those of eval_logpost (exponential profile, no chi^2).
+template <int NC>
+__device__ void pix_grad(const FitParams &P, const GalCtx &gc, const SmemView &sm, const PixTc &px, float2 *xph,
+                         const float vcol[NC], const float th[6], float g[6])
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int per = 2 * ((gc.H + 15) >> 4);
+    const int u0 = min(gc.H, warp * per), u1 = min(gc.H, u0 + per);
+    const float F = exp10f(th[0]);
+    const float r0 = exp10f(th[1]) * (1.0f / kHlrOverR0);
+    const float r02 = r0 * r0;
+    const float e1 = th[2], e2 = th[3];
+    const float E = e1 * e1 + e2 * e2;
+    const float Pq = 1.0f / (1.0f - E);
+    const float al = r02 * (1.0f + E + 2.0f * e1) * Pq;
+    const float be = r02 * (1.0f + E - 2.0f * e1) * Pq;
+    const float ga = r02 * 4.0f * e2 * Pq;
+    const float F2 = F * F;
+    const float dk = gc.dk;
+    for (int u = u0 + lane; u < u1; u += 32) {
+        float sx, cx;
+        sincospi_sfu(-2.0f * th[4] * (float)u * gc.invN, &sx, &cx);
+        xph[u] = make_float2(cx, sx);
+    }
+    __syncwarp();
+    float Yr[NC], Yi[NC], cst[NC], gky[NC], ky[NC];
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+        float sn, co;
+        sincospi_sfu(-2.0f * th[5] * vcol[j] * gc.invN, &sn, &co);
+        Yr[j] = F * co;
+        Yi[j] = F * sn;
+        ky[j] = vcol[j] * dk;
+        cst[j] = fmaf(be * ky[j], ky[j], 1.0f);
+        gky[j] = ga * ky[j];
+    }
+    SlotConst<NC> K;
+    Sums<NC> S;
+    constexpr int NPAIR = NC / 2;
+#pragma unroll
+    for (int p = 0; p < NPAIR; ++p) {
+        K.Yr[p] = make_float2(Yr[2 * p], Yr[2 * p + 1]);
+        K.Yi[p] = make_float2(Yi[2 * p], Yi[2 * p + 1]);
+        K.nYi[p] = make_float2(-Yi[2 * p], -Yi[2 * p + 1]);
+        K.cst[p] = make_float2(cst[2 * p], cst[2 * p + 1]);
+        K.gky[p] = make_float2(gky[2 * p], gky[2 * p + 1]);
+        S.Wc[p] = f2(0.f);
+        S.Wkx[p] = f2(0.f);
+        S.Bc[p] = f2(0.f);
+    }
+    if (NC & 1) {
+        K.sYr = Yr[NC - 1];
+        K.sYi = Yi[NC - 1];
+        K.scst = cst[NC - 1];
+        K.sgky = gky[NC - 1];
+    }
+    S.Swkx2 = f2(0.f);
+    S.Sbkx = f2(0.f);
+    S.sWc = 0.f;
+    S.sWkx = 0.f;
+    S.sBc = 0.f;
+    S.chi_hi = f2(0.f);
+    S.chi_lo = f2(0.f);
+    if (u1 > u0)
+        half_plane<NC, false, 0>(S, K, sm.tab + (size_t)u0 * row_floats(P.npad), sm.kxr + u0, xph + u0, u1 - u0,
+                                 al, F2, P.prof_npow);
+    float Swkx2 = S.Swkx2.x + S.Swkx2.y, Sbkx = S.Sbkx.x + S.Sbkx.y;
+    float Sw = 0.f, Swky2 = 0.f, Swkxky = 0.f, Sbky = 0.f;
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+        float wc, wkx, bc;
+        if (j < 2 * NPAIR) {
+            const int p = j >> 1;
+            wc = (j & 1) ? S.Wc[p].y : S.Wc[p].x;
+            wkx = (j & 1) ? S.Wkx[p].y : S.Wkx[p].x;
+            bc = (j & 1) ? S.Bc[p].y : S.Bc[p].x;
+        } else {
+            wc = S.sWc;
+            wkx = S.sWkx;
+            bc = S.sBc;
+        }
+        Sw += wc;
+        Swky2 = fmaf(ky[j] * ky[j], wc, Swky2);
+        Swkxky = fmaf(ky[j], wkx, Swkxky);
+        Sbky = fmaf(ky[j], bc, Sbky);
+    }
+    float sums[6] = {Sw, Swkx2, Swky2, Swkxky, Sbkx, Sbky};
+    warp_sum_n(sums);
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) px.gsum[6 * warp + k] = sums[k];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        float t = 0.f;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) t += px.gsum[6 * w + k];
+        sums[k] = t;
+    }
+    Sw = sums[0];
+    Swkx2 = sums[1];
+    Swky2 = sums[2];
+    Swkxky = sums[3];
+    Sbkx = sums[4];
+    Sbky = sums[5];
+    const float st = al * Swkx2 + be * Swky2 + ga * Swkxky;
+    const float Sa = Sw + st;
+    const float ib = gc.inv_b;
+    const float P2 = Pq * Pq;
+    const float da1 = r02 * ((2.0f * e1 + 2.0f) * Pq + (1.0f + E + 2.0f * e1) * 2.0f * e1 * P2);
+    const float da2 = r02 * (2.0f * e2 * Pq + (1.0f + E + 2.0f * e1) * 2.0f * e2 * P2);
+    const float db1 = r02 * ((2.0f * e1 - 2.0f) * Pq + (1.0f + E - 2.0f * e1) * 2.0f * e1 * P2);
+    const float db2 = r02 * (2.0f * e2 * Pq + (1.0f + E - 2.0f * e1) * 2.0f * e2 * P2);
+    const float dg1 = r02 * 8.0f * e1 * e2 * P2;
+    const float dg2 = r02 * (4.0f * Pq + 8.0f * e2 * e2 * P2);
+    g[0] = kLn10 * Sa * ib;
+    g[1] = -3.0f * kLn10 * st * ib;
+    g[2] = -1.5f * (da1 * Swkx2 + db1 * Swky2 + dg1 * Swkxky) * ib - 4.0f * e1 * Pq - e1 * P.inv_se2;
+    g[3] = -1.5f * (da2 * Swkx2 + db2 * Swky2 + dg2 * Swkxky) * ib - 4.0f * e2 * Pq - e2 * P.inv_se2;
+    g[4] = gc.p * Sbkx * ib - th[4] * P.inv_sxy2;
+    g[5] = gc.p * Sbky * ib - th[5] * P.inv_sxy2;
+}
+
 template <int NC>
 __device__ double eval_pix(const FitParams &P, const GalCtx &gc, const SmemView &sm, int gal, float2 *xph,
                            const float vcol[NC], const float th[6], float g[6], bool want_ll)
 {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int half = warp >> 2;                       // column half of the TMEM reads
+    const int L = 32 * (warp & 3) + lane;             // this thread's TMEM lane
     const PixTc px = pix_tc_view(sm.kxr, P.h_max, P.max_side);
     const int N = gc.N, H = gc.H, c = gc.c, npad = P.npad;
     const int rowf = row_floats(npad);
     __syncthreads();   // the previous evaluation's readers of the table and buffers are done
-    if (*px.abort) {
-#pragma unroll
-        for (int i = 0; i < 6; ++i) g[i] = NAN;
-        return NAN;
-    }
+    if (*px.abort) return pix_nan(g);
     const float F = exp10f(th[0]);
     const float r0 = exp10f(th[1]) * (1.0f / kHlrOverR0);
     const float r02 = r0 * r0;
@@ -122,7 +278,7 @@ __device__ double eval_pix(const FitParams &P, const GalCtx &gc, const SmemView 
     constexpr int kLb = tc::kLboB / 4;
     // (a) the model's half spectrum Mt into the table's D slots, and M = Mt / scale_u
     // as the operand of (1): rows u < 32, K (re, vi | im, vi), 128 per row; thread t
-    // takes column vi = t mod 64 and the rows u of its parity, u = t / 64 + 2 i
+    // takes column vi = t mod 64 and the rows u = t / 64 + 4 i
     {
         const int vi = tid & 63, u0 = tid >> 6;
         const bool col = vi < N;
@@ -133,8 +289,8 @@ __device__ double eval_pix(const FitParams &P, const GalCtx &gc, const SmemView 
         const float2 Y = px.ys[vi];
         const float sN = (float)N, sN2 = (float)N * 0.70710678118654752f;
 #pragma unroll 4
-        for (int i = 0; i < 16; ++i) {
-            const int u = u0 + 2 * i;
+        for (int i = 0; i < 8; ++i) {
+            const int u = u0 + 4 * i;
             float Mr = 0.f, Mi = 0.f;
             if (col && u < H) {
                 float *row = sm.tab + (size_t)u * rowf;
@@ -154,131 +310,110 @@ __device__ double eval_pix(const FitParams &P, const GalCtx &gc, const SmemView 
             tc::split_store(bh, bl, tc::op_index(u, 64 + vi, 128, kLb), Mi);
         }
     }
-    const uint32_t cst = tc::saddr(px.cst), bop = tc::saddr(px.bop);
-    const uint32_t blk_nS = cst, blk_C = cst + tc::kBlockFloats * 4;
+    const uint32_t cst = tc::saddr(px.cst), bop = tc::saddr(px.bop), c2r = tc::saddr(px.c2r);
+    const uint32_t blk_nS = cst, blk_C = cst + tc::kBlockFloats * 4, cst_lo = tc::kCstFloats * 4;
     const int ks = (N + 7) >> 3;   // k-steps of 8 covering the side
+    const uint32_t tl = *px.tmem + ((uint32_t)(32 * (warp & 3)) << 16);
     // (1) G = M E: rows (re, iy | im, iy), columns u
-    if (!tc_run(px, TcGemm{blk_C, blk_nS, 0u, bop, 16u * 144, 32u * 144, tc::idesc(128, 32, false), 2, ks}, 0)) {
-#pragma unroll
-        for (int i = 0; i < 6; ++i) g[i] = NAN;
-        return NAN;
-    }
-    // (1) -> operand of (2): rows iy < 64, K (re, a | im, a) for a in [a0, a_end), the
-    // rows' G(u, iy) at a = u + c, weighted by w_u / N^2
-    const uint32_t tl = *px.tmem + ((uint32_t)(warp * 32) << 16);
-    const int a0 = c & ~7, ka = ((N + 7) & ~7) - a0, kt2 = 2 * ka, o = c - a0;
+    if (!tc_run(px, TcGemm{blk_C, blk_nS, cst_lo, bop, 16u * 144, 32u * 144, tc::idesc(128, 32, false), 2, ks}, 0))
+        return pix_nan(g);
+    // (1) -> operand of (2): row iy, K (re, u | im, u), G as it is (the weights are in
+    // the constant); this thread's 16 columns u of its lane (p, iy)
     {
-        float v[32];
-        tc::ld32(tl, v);
-        const int p = tid >> 6, iy = tid & 63;
-        const float s0 = gc.invN * gc.invN, s1 = 2.0f * s0;
+        float v[16];
+        tc::ld16(tl + 16 * half, v);
+        const int p = L >> 6, iy = L & 63;
+        const int e0 = tc::op_index(iy, p * 32 + 16 * half, 64, kLb);
 #pragma unroll
-        for (int u = 0; u < 32; ++u)
-            if (u < H) tc::split_store(bh, bl, tc::op_index(iy, p * ka + o + u, kt2, kLb), v[u] * (u ? s1 : s0));
-        for (int j = 0; j < o; ++j) tc::split_store(bh, bl, tc::op_index(iy, p * ka + j, kt2, kLb), 0.f);
-        for (int j = o + H; j < ka; ++j) tc::split_store(bh, bl, tc::op_index(iy, p * ka + j, kt2, kLb), 0.f);
+        for (int m = 0; m < 4; ++m)
+            tc::split_store4(bh, bl, e0 + m * kLb, v[4 * m], v[4 * m + 1], v[4 * m + 2], v[4 * m + 3]);
     }
-    // (2) m = [C -S] G': rows ix, columns iy
-    if (!tc_run(px, TcGemm{blk_C, blk_nS, 128u * (a0 / 4), bop, 144u * (ka / 4), 144u * (kt2 / 4),
-                           tc::idesc(128, 64, false), 2, ka / 8}, 1)) {
-#pragma unroll
-        for (int i = 0; i < 6; ++i) g[i] = NAN;
-        return NAN;
-    }
+    // (2) m = W G: rows ix, columns iy
+    if (!tc_run(px, TcGemm{c2r, c2r + 8u * 128, tc::kC2rFloats * 4, bop, 8u * 144, 16u * 144,
+                           tc::idesc(128, 64, false), 2, (H + 7) >> 3},
+                1))
+        return pix_nan(g);
     // the residual, chi^2 (compensated FP32 per thread, FP64 across threads) and the
-    // operand of (3): rows iy, K ix
+    // operand of (3): rows iy, K ix; lanes ix < 64 of warps 0, 1, 4, 5, the columns iy
+    // of this thread's half
     double chi = 0.0;
-    if (warp < 2) {
+    if ((warp & 3) < 2) {
+        const int ix = L;
         float c_hi = 0.f, c_lo = 0.f;
-        const int ix = tid;
+        float m[32];
+        tc::ld32(tl + 32 * half, m);
+        const int eb = (ix >> 2) * kLb + (ix & 3);
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            float m[32];
-            tc::ld32(tl + 32 * h, m);
-#pragma unroll
-            for (int t = 0; t < 32; ++t) {
-                const int iy = 32 * h + t;
-                float r = 0.f;
-                if (ix < N && iy < N) {
-                    const int e = iy * N + ix;
-                    const float res = px.dimg[e] - m[t];
-                    r = px.wimg[e] * res;
+        for (int t = 0; t < 32; ++t) {
+            const int iy = 32 * half + t;
+            float r = 0.f;
+            if (ix < N && iy < N) {
+                const int e = iy * N + ix;
+                const float res = px.dimg[e] - m[t];
+                r = px.wimg[e] * res;
+                if (want_ll) {
                     float t_hi, t_lo;
                     two_sum(c_hi, r * res, t_hi, t_lo);
                     c_hi = t_hi;
                     c_lo += t_lo;
                 }
-                tc::split_store(bh, bl, tc::op_index(iy, ix, 64, kLb), r);
             }
+            tc::split_store(bh, bl, eb + (iy >> 3) * 16 * kLb + ((iy & 7) << 2), r);
         }
         chi = (double)c_hi + (double)c_lo;
     }
-    {
+    if (want_ll) {
         const double cw = warp_sum_d(chi);
         if (lane == 0) px.chi[warp] = cw;
     }
     // (3) conj Q = [C S] r: rows (re, a | im, a), columns iy
-    if (!tc_run(px, TcGemm{blk_C, blk_C, 0u, bop, 0u, 16u * 144, tc::idesc(128, 64, false), 1, ks}, 0)) {
-#pragma unroll
-        for (int i = 0; i < 6; ++i) g[i] = NAN;
-        return NAN;
-    }
-    const double chi2 = px.chi[0] + px.chi[1] + px.chi[2] + px.chi[3];
-    // (3) -> operand of (4): row u = a - c < 32, K (re, iy | im, iy)
+    if (!tc_run(px, TcGemm{blk_C, blk_C, cst_lo, bop, 0u, 16u * 144, tc::idesc(128, 64, false), 1, ks}, 0))
+        return pix_nan(g);
+    // (3) -> operand of (4): row u = a - c < 32, K (re, iy | im, iy); this thread's 32
+    // columns iy of its lane (q, a)
     {
-        const int q = tid >> 6, u = (tid & 63) - c;
+        const int q = L >> 6, u = (L & 63) - c;
         float v[32];
+        tc::ld32(tl + 32 * half, v);
+        if (u >= 0 && u < 32) {
+            const int e0 = tc::op_index(u, q * 64 + 32 * half, 128, kLb);
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            tc::ld32(tl + 32 * h, v);
-            if (u >= 0 && u < 32) {
-#pragma unroll
-                for (int t = 0; t < 32; t += 4) {
-                    const int k = q * 64 + 32 * h + t;
-                    const int e = tc::op_index(u, k, 128, kLb);
-                    float4 hv, lv;
-                    hv.x = tc::tf32_rn(v[t]);
-                    hv.y = tc::tf32_rn(v[t + 1]);
-                    hv.z = tc::tf32_rn(v[t + 2]);
-                    hv.w = tc::tf32_rn(v[t + 3]);
-                    lv.x = tc::tf32_rn(v[t] - hv.x);
-                    lv.y = tc::tf32_rn(v[t + 1] - hv.y);
-                    lv.z = tc::tf32_rn(v[t + 2] - hv.z);
-                    lv.w = tc::tf32_rn(v[t + 3] - hv.w);
-                    *reinterpret_cast<float4 *>(bh + e) = hv;
-                    *reinterpret_cast<float4 *>(bl + e) = lv;
-                }
-            }
+            for (int m = 0; m < 8; ++m)
+                tc::split_store4(bh, bl, e0 + m * kLb, v[4 * m], v[4 * m + 1], v[4 * m + 2], v[4 * m + 3]);
         }
     }
     // (4) conj R = E conj Q: rows (re, vi | im, vi), columns u
-    if (!tc_run(px, TcGemm{blk_C, blk_nS, 0u, bop, 16u * 144, 32u * 144, tc::idesc(128, 32, false), 2, ks}, 1)) {
-#pragma unroll
-        for (int i = 0; i < 6; ++i) g[i] = NAN;
-        return NAN;
-    }
-    // D' = Mt + scale_u R in the table's D slots
+    if (!tc_run(px, TcGemm{blk_C, blk_nS, cst_lo, bop, 16u * 144, 32u * 144, tc::idesc(128, 32, false), 2, ks}, 1))
+        return pix_nan(g);
+    // D' = Mt + scale_u R in the table's D slots; this thread's 16 columns u of its
+    // lane (p, vi)
     {
-        const int p = tid >> 6, vi = tid & 63;
-        float v[32];
-        tc::ld32(tl, v);
+        const int p = L >> 6, vi = L & 63;
+        float v[16];
+        tc::ld16(tl + 16 * half, v);
         if (vi < N) {
             int ox, oy, ot;
             slot_offsets(npad, vi >> 5, vi & 31, ox, oy, ot);
             const int os = p ? oy : ox;
             const float sg = p ? -gc.invN : gc.invN;
 #pragma unroll
-            for (int u = 0; u < 32; ++u)
+            for (int j = 0; j < 16; ++j) {
+                const int u = 16 * half + j;
                 if (u < H) {
                     float *slot = sm.tab + (size_t)u * rowf + os;
-                    *slot = fmaf((u ? sqrt2 : 1.0f) * sg, v[u], *slot);
+                    *slot = fmaf((u ? sqrt2 : 1.0f) * sg, v[j], *slot);
                 }
+            }
         }
     }
     __syncthreads();
-    // the gradient from the half-plane pass on the effective spectrum (every warp)
-    eval_logpost<NC, 0>(P, gc, sm.tab, sm.kxr, xph, vcol, th, g, false);
+    // the gradient from the half-plane pass on the effective spectrum, its rows over
+    // the eight warps
+    pix_grad<NC>(P, gc, sm, px, xph, vcol, th, g);
     if (!want_ll) return 0.0;
+    double chi2 = 0.0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) chi2 += px.chi[w];
     const float lprior = P.prior_const - 0.5f * (th[4] * th[4] + th[5] * th[5]) * P.inv_sxy2 +
                          2.0f * log1pf(-E) - 0.5f * E * P.inv_se2;
     return -0.5 * chi2 * (double)gc.inv_b + (double)lprior;

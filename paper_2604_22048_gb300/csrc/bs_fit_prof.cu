@@ -24,13 +24,13 @@ FitKernel prof_kernel(int max_side)
 }
 
 // Per-pixel weights (profile 3), exponential: stamps of at most 63 px, one chain
-// per CTA of four warps, the transforms on the tensor cores.
+// per CTA of eight warps, the transforms on the tensor cores.
 FitKernel pix_kernel(int max_side)
 {
     return max_side <= 31 ? fit_kernel_pix<1> : fit_kernel_pix<2>;
 }
 
-constexpr int kPixThreads = 128;
+constexpr int kPixThreads = tc::kThreads;
 
 bool is_pix(int profile) { return profile == 3; }
 
@@ -48,12 +48,12 @@ PointsKernel points_for(int profile, int max_side)
     return profile == BS_PROFILE_SPERGEL ? logpost_points_kernel<1> : logpost_points_kernel<2>;
 }
 
-// Dynamic shared memory of a launch: the pixel-weight path (a phase table for
-// each of its four warps) adds the transforms' region after the row table, the
-// dense-covariance path its twiddles and per-chain scratch.
+// Dynamic shared memory of a launch: the pixel-weight path adds the transforms'
+// region after the row table, the dense-covariance path its twiddles and
+// per-chain scratch.
 size_t smem_for(int profile, int max_side, int n_chains)
 {
-    if (is_pix(profile)) return fit_smem_bytes(max_side, 4) + 16 + pix_tc_bytes(max_side);
+    if (is_pix(profile)) return fit_smem_bytes(max_side, 1) + 16 + pix_tc_bytes(max_side);
     size_t b = fit_smem_bytes(max_side, n_chains);
     if (profile == 4) {
         const int h = (max_side + 1) / 2, npad = 32 * ((max_side + 31) / 32);

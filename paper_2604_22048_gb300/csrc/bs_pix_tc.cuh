@@ -17,21 +17,23 @@
 // 64 x 64:
 //   (1)  rows (re, iy | im, iy) x K (re, v | im, v): [C S] on the real half, [-S C] on
 //        the imaginary half of K;
-//   (2)  rows ix x K (re, u + c | im, u + c): C, then -S (u + c puts u on the centred index);
+//   (2)  rows ix x K (re, u | im, u): its own complex-to-real constant with the weights
+//        w_u / N^2 folded in, so that the operand is G as the first product leaves it;
 //   (3)  rows (re, u + c | im, u + c) x K ix: [C S] (the imaginary output is -Q_i);
 //   (4)  conj R = transform (1) of conj Q, and the output of (3) is conj Q already.
 // The shared memory holds the blocks in the order -S, C, S, so every A operand of
-// 128 rows is two consecutive blocks; rows past the 64 of (2) read the next block and
-// give lanes that are not read.  Each transform is a tcgen05.mma of kind::tf32
+// 128 rows is two consecutive blocks; rows past the 64 of (2) read the memory after its
+// constant and give lanes that are not read.  Each transform is a tcgen05.mma of kind::tf32
 // (M = 128, N = 32 or 64, K = 8 per instruction, operands in shared memory without
 // swizzle, accumulator in TMEM) in three terms, A_hi B_hi + A_hi B_lo + A_lo B_hi
 // with x = hi + lo split by round-to-nearest TF32 (3xTF32): the operand rounding of
 // plain TF32 would miss the log-likelihood tolerance by a factor of several.
 //
-// One CTA of four warps per chain: every warp runs the chain's scalar logic (its
-// decisions are the same in all four, from the same numbers), the transforms and the
-// elementwise steps between them are split over the 128 threads (thread t reads TMEM
-// lane t), and thread 0 issues the MMAs.  Each evaluation commits four MMA groups to
+// One CTA of eight warps per chain: every warp runs the chain's scalar logic (its
+// decisions are the same in all eight, from the same numbers), the transforms and the
+// elementwise steps between them are split over the 256 threads (warps w and w + 4
+// read the two column halves of TMEM lanes 32 (w mod 4) .. + 31), the first warp runs
+// the spectral gradient pass and shares its result, and thread 0 issues the MMAs.  Each evaluation commits four MMA groups to
 // one mbarrier, so the parities it waits on are 0, 1, 0, 1 in every evaluation.  A
 // wait gives up after two seconds: the CTA then marks its galaxy (status 4), issues no
 // further MMA, and its evaluations return NaN until the chain ends.
@@ -49,7 +51,8 @@ constexpr int kLboB = 144;                     // data operands: 16-byte pad per
                                                // stores of a warp fall in 32 distinct banks)
 constexpr int kBlockFloats = kNP * kNP;        // one 64 x 64 block, 16 KB
 constexpr int kCstFloats = 3 * kBlockFloats;   // -S, C, S of one precision level
-constexpr int kBopFloats = 8 * 20 * (kLboB / 4);   // largest data operand: 64 rows x 80 K
+constexpr int kBopFloats = 8 * 16 * (kLboB / 4);   // largest data operand: 64 rows x 64 K (or 32 x 128)
+constexpr int kC2rFloats = kNP * kNP;           // the complex-to-real constant, 64 x 64
 constexpr uint64_t kWaitNs = 2000000000ull;    // limit of one MMA wait
 
 // Element (row, k) of an operand of kt K-elements per row (no swizzle, K-major):
@@ -155,18 +158,52 @@ __device__ __forceinline__ void ld32(uint32_t taddr, float (&v)[32])
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 16 consecutive TMEM columns of this thread's lane.
+__device__ __forceinline__ void ld16(uint32_t taddr, float (&v)[16])
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Four consecutive K-elements (one core-matrix row) as high and low TF32 parts.
+__device__ __forceinline__ void split_store4(float *hi, float *lo, int i, float a, float b, float c, float d)
+{
+    float4 h, l;
+    h.x = tf32_rn(a);
+    h.y = tf32_rn(b);
+    h.z = tf32_rn(c);
+    h.w = tf32_rn(d);
+    l.x = tf32_rn(a - h.x);
+    l.y = tf32_rn(b - h.y);
+    l.z = tf32_rn(c - h.z);
+    l.w = tf32_rn(d - h.w);
+    *reinterpret_cast<float4 *>(hi + i) = h;
+    *reinterpret_cast<float4 *>(lo + i) = l;
+}
+
 constexpr int kTmemCols = 64;
+constexpr int kThreads = 256;                  // eight warps: lane quadrant warp % 4, column half warp / 4
 
 }  // namespace tc
 
 // Shared memory of the tensor-core pixel path, after the (kx, kx^2) table.
 struct PixTc {
-    double *chi;      // [4] per-warp partial chi^2 of the evaluation
+    double *chi;      // [8] per-warp partial chi^2 of the evaluation
     uint64_t *bar;    // MMA completion barrier
     uint32_t *tmem;   // TMEM base of the CTA's accumulator (64 columns)
     int *abort;       // 1 once a wait gave up
     float2 *xs;       // [32] exp(-2 pi i u dx / N)
     float2 *ys;       // [64] F exp(-2 pi i v dy / N), v = vi - c
+    float *gsum;      // [8][6] each warp's six gradient sums
+    float *c2r;       // [2][64 x 64] the complex-to-real constant of transform (2), high then low
     float *cst;       // [2][3][64 x 64] blocks -S, C, S: TF32 high parts, then low parts
     float *bop;       // [2][kBopFloats] the data operand of the current transform, high then low
     float *dimg;      // [max_side^2] the stamp
@@ -175,11 +212,14 @@ struct PixTc {
 
 __host__ __device__ __forceinline__ int pix_tc_img_floats(int max_side) { return (max_side * max_side + 3) & ~3; }
 
-// Floats of the region: 8 (chi) + 2 (barrier) + 2 (TMEM address, abort) + 64 (xs) +
-// 128 (ys) + 4 (pad) + constants + operand + two images.
+// Floats of the region: 16 (chi) + 2 (barrier) + 2 (TMEM address, abort) + 64 (xs) +
+// 128 (ys) + 48 (gradient sums) + 4 (pad) + constants + operand + two images.  The
+// complex-to-real constant lies before the blocks, so the 64 rows past its own that
+// an M = 128 product reads are in the region.
 __host__ __device__ __forceinline__ size_t pix_tc_bytes(int max_side)
 {
-    return ((size_t)208 + 2 * tc::kCstFloats + 2 * tc::kBopFloats + 2 * (size_t)pix_tc_img_floats(max_side)) *
+    return ((size_t)264 + 2 * tc::kC2rFloats + 2 * tc::kCstFloats + 2 * tc::kBopFloats +
+            2 * (size_t)pix_tc_img_floats(max_side)) *
            sizeof(float);
 }
 
@@ -189,12 +229,14 @@ __device__ __forceinline__ PixTc pix_tc_view(float2 *kxr, int h_max, int max_sid
     float *base = reinterpret_cast<float *>(kxr + ((h_max + 2) & ~1));
     PixTc v;
     v.chi = reinterpret_cast<double *>(base);
-    v.bar = reinterpret_cast<uint64_t *>(base + 8);
-    v.tmem = reinterpret_cast<uint32_t *>(base + 10);
-    v.abort = reinterpret_cast<int *>(base + 11);
-    v.xs = reinterpret_cast<float2 *>(base + 12);
-    v.ys = reinterpret_cast<float2 *>(base + 76);
-    v.cst = base + 208;
+    v.bar = reinterpret_cast<uint64_t *>(base + 16);
+    v.tmem = reinterpret_cast<uint32_t *>(base + 18);
+    v.abort = reinterpret_cast<int *>(base + 19);
+    v.xs = reinterpret_cast<float2 *>(base + 20);
+    v.ys = reinterpret_cast<float2 *>(base + 84);
+    v.gsum = base + 212;
+    v.c2r = base + 264;
+    v.cst = v.c2r + 2 * tc::kC2rFloats;
     v.bop = v.cst + 2 * tc::kCstFloats;
     v.dimg = v.bop + 2 * tc::kBopFloats;
     v.wimg = v.dimg + pix_tc_img_floats(max_side);
