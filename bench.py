@@ -211,9 +211,9 @@ def flops_per_eval(N):
 # to that file the traffic is reported as null until the next capture.
 CAPTURED_TRAFFIC = {
     # one galaxy of the plain workload (53x53, 4 chains x (200 + 300) draws), from a one-pass
-    # capture of the full 10,000-galaxy launch: (132,817,408 + 292,431,872) B / 10,000
+    # capture of the full 10,000-galaxy launch: (134,292,480 + 293,008,896) B / 10,000
     "fit": ("paper_2604_22048_gb300/csrc/bs_fit_impl.cuh",
-            "33dec11059c489c0464ffdfb724b6568bbce34dc9377711cee8ecdd976eefbb5", 42524.9,
+            "2c3a5b881660fbf9d9cbb7f8375b91cb282ca41b67f10c6b2200fcf3fa3217de", 42730.1,
             {"side": 53, "chains": 4, "n_warmup": 200, "n_samples": 300}),
     # one interim sample of the shear workload: (489,468,416 + 3,221,248) B / (200,000 x 300)
     "shear": ("paper_2604_22048_gb300/csrc/bs_shear.cu",
