@@ -215,9 +215,10 @@ CAPTURED_TRAFFIC = {
     "fit": ("paper_2604_22048_gb300/csrc/bs_fit_impl.cuh",
             "2c3a5b881660fbf9d9cbb7f8375b91cb282ca41b67f10c6b2200fcf3fa3217de", 42730.1,
             {"side": 53, "chains": 4, "n_warmup": 200, "n_samples": 300}),
-    # one interim sample of the shear workload: (489,468,416 + 3,221,248) B / (200,000 x 300)
+    # one interim sample of the shear workload: (489,620,992 + 3,289,856) B / (200,000 x 300),
+    # captured on sha256 44742046...dbfe54dc; the file has changed since in its header comment only
     "shear": ("paper_2604_22048_gb300/csrc/bs_shear.cu",
-              "d664605cb7387c74c2607a07146e84be989c00e4134f73773bdafca158c849a5", 8.2115, {}),
+              "afe3a119cc56bfabe514f50d0dceb4e8429038b817aad2eae149c66d9c7a6358", 8.2152, {}),
 }
 
 
@@ -732,7 +733,7 @@ def shear_arm(a, world, rank, local_rank):
                          "frac": achieved / peak, "traffic": captured_traffic("shear", n * K),
                          "traffic_note": "DRAM read+write per pass, scaled from a 200,000-galaxy ncu capture of "
                                          "the same kernel source by the samples per pass",
-                         "kernel": "shear_kernel_async<1,0>",
+                         "kernel": "shear_kernel_tma<1>",
                          "bytes_per_pass": bytes_per_pass, "peak_how": "measured copy bandwidth"},
             "gpu_launches": launches, "clocks": clk,
             "estimate": {"g": [float(x) for x in mean[:2]], "alpha": float(mean[2]),

@@ -15,8 +15,11 @@
 // with du_1 = ur e1 - vi e2, du_2 = ur e2 + vi e1, n = eps' - g, and
 // dx/dalpha = Q / alpha^3.
 //
-// Each galaxy's K samples are read by a group of 8 lanes (float4 loads when
-// the rows are 16-byte aligned, one chunk ahead of the arithmetic); the
+// Each galaxy's K samples are read by a group of lanes: when K % 4 == 0 and the
+// rows are 16-byte aligned, 4 lanes per galaxy read 12-sample chunks from tiles
+// of 64 galaxies x 48 samples that the tensor memory accelerator streams into
+// shared memory (without b), or from a per-lane cp.async ring (with b); otherwise
+// 8 lanes per galaxy with scalar loads one chunk ahead.  The
 // arithmetic runs on pairs of samples in packed FP32x2 instructions, x is
 // kept in log2 units for the MUFU exp2, and the group keeps
 // an online log-sum-exp (running max, sum of weights and weighted derivative
@@ -25,6 +28,9 @@
 // sums the partials in a fixed order (deterministic) and adds the
 // per-galaxy constants.
 #include <cmath>
+
+#include <cuda.h>            // CUtensorMap and its enums (types only: the encoder is looked up at run time)
+#include <cudaTypedefs.h>    // PFN_cuTensorMapEncodeTiled
 
 #include "bs_device.cuh"
 #include "bs_internal.h"
@@ -461,6 +467,197 @@ __global__ void __launch_bounds__(kShearThreads, HAS_B ? 3 : kAsyncBlocks) shear
     block_partials(s, av, a1, a2, aq);
 }
 
+// ---- Tensor-memory-accelerator tiles (no b): a CTA streams tiles of kTileG
+// consecutive galaxies x kTileK samples of e1 and e2 with 2-D
+// cp.async.bulk.tensor loads into a kTmaStages-deep ring; one thread issues both
+// loads of a stage and arms the stage's mbarrier with their byte count, and the
+// others wait on it.  Thread t serves galaxy t / 4 of the tile and its samples
+// [12 (t mod 4), + 12) of each chunk (the cp.async kernel's group of 4 lanes and
+// 12-sample chunks).  Galaxies past n_gal and samples past K arrive zero-filled and
+// are masked by index.  A wait gives up after two seconds: the CTA then writes NaN
+// partials, so that the pass's value is NaN.
+constexpr int kTileG = kShearThreads / kAGroup;   // 64 galaxies per tile
+constexpr int kTileK = kChunk * kAGroup;          // 48 samples per chunk
+constexpr int kTmaStages = 2;
+constexpr int kTileFloats = kTileG * kTileK;      // one array's box, 12 KB
+
+__host__ __device__ constexpr size_t tma_smem_bytes()
+{
+    return (size_t)kTmaStages * 2 * kTileFloats * sizeof(float) + 128;   // + alignment of the ring
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_t t0)
+{
+    for (;;) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        uint64_t t;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        if (t - t0 > 2000000000ull) return false;
+    }
+}
+
+template <int FAMILY>
+__global__ void __launch_bounds__(kShearThreads, kAsyncBlocks)
+    shear_kernel_tma(const ShearLaunch s, const __grid_constant__ CUtensorMap m1, const __grid_constant__ CUtensorMap m2)
+{
+    constexpr int kWarps = kShearThreads / 32;
+    extern __shared__ __align__(128) unsigned char tma_raw[];
+    __shared__ __align__(8) uint64_t full[kTmaStages], empty[kTmaStages];
+    float *ring = reinterpret_cast<float *>(tma_raw + ((128u - (smem_u32(tma_raw) & 127u)) & 127u));
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int sub = tid & (kAGroup - 1), gl = tid / kAGroup;
+    const unsigned gmask = ((1u << kAGroup) - 1u) << (lane & ~(kAGroup - 1));
+    const ShearConst c = shear_const(s);
+    const int K = s.K;
+    const int cpg = (K + kTileK - 1) / kTileK;                       // chunks per tile
+    const long long n_tiles = (s.n_gal + kTileG - 1) / kTileG;
+    const int my_tiles = blockIdx.x < n_tiles ? (int)((n_tiles - 1 - blockIdx.x) / gridDim.x + 1) : 0;
+    const int n_items = my_tiles * cpg;
+    if (tid == 0) {
+        for (int st = 0; st < kTmaStages; ++st) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[st])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&empty[st])), "r"(kWarps)
+                         : "memory");
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    // producer state (thread 0): next item to load, its tile and chunk
+    int p_item = 0, p_chunk = 0;
+    long long p_tile = blockIdx.x;
+    bool p_ok = true;
+    auto issue = [&]() {
+        if (p_item >= n_items || !p_ok) return;
+        const int st = p_item % kTmaStages;
+        if (p_item >= kTmaStages) {   // the stage's previous item has been read by every warp
+            uint64_t t0;
+            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+            if (!mbar_wait(smem_u32(&empty[st]), (uint32_t)((p_item / kTmaStages - 1) & 1), t0)) {
+                p_ok = false;
+                return;
+            }
+        }
+        const uint32_t bar = smem_u32(&full[st]);
+        const uint32_t d1 = smem_u32(ring + (size_t)st * 2 * kTileFloats), d2 = d1 + kTileFloats * 4;
+        const int x = p_chunk * kTileK, y = (int)(p_tile * kTileG);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                     "r"((uint32_t)(2 * kTileFloats * 4))
+                     : "memory");
+        asm volatile(
+            "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+                "r"(d1),
+            "l"(&m1), "r"(x), "r"(y), "r"(bar)
+            : "memory");
+        asm volatile(
+            "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+                "r"(d2),
+            "l"(&m2), "r"(x), "r"(y), "r"(bar)
+            : "memory");
+        ++p_item;
+        if (++p_chunk == cpg) {
+            p_chunk = 0;
+            p_tile += gridDim.x;
+        }
+    };
+    if (tid == 0)
+        for (int t = 0; t < kTmaStages - 1; ++t) issue();
+    double av = 0.0, a1 = 0.0, a2 = 0.0, aq = 0.0;
+    Lse L;
+    lse_reset(L);
+    bool failed = false;
+    int chunk = 0;
+    long long tile = blockIdx.x;
+    for (int item = 0; item < n_items; ++item) {
+        if (tid == 0) issue();
+        const int st = item % kTmaStages;
+        uint64_t t0;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+        const bool ok = __all_sync(BS_FULL_MASK, mbar_wait(smem_u32(&full[st]), (uint32_t)((item / kTmaStages) & 1), t0));
+        if (!ok) {
+            failed = true;
+            break;
+        }
+        const long long n = tile * kTileG + gl;
+        const int k0 = chunk * kTileK + kChunk * sub;
+        const float *r1 = ring + (size_t)st * 2 * kTileFloats + gl * kTileK + kChunk * sub;
+        const float *r2 = r1 + kTileFloats;
+        if (n < s.n_gal) {
+#pragma unroll
+            for (int h = 0; h < kQuads; ++h) {
+                if (k0 + 4 * h < K) {
+                    Chunk ch;
+                    ch.nvalid = 4;
+                    ch.full = true;
+                    ch.e1 = *reinterpret_cast<const float4 *>(r1 + 4 * h);
+                    ch.e2 = *reinterpret_cast<const float4 *>(r2 + 4 * h);
+                    ch.b = make_float4(0.f, 0.f, 0.f, 0.f);
+                    eval_chunk<FAMILY, false>(c, ch, L);
+                }
+            }
+        }
+        __syncwarp();
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&empty[st])) : "memory");
+        if (++chunk == cpg) {
+            if (n < s.n_gal) finish_galaxy<kAGroup>(L, gmask, sub, s.w, n, av, a1, a2, aq);
+            lse_reset(L);
+            chunk = 0;
+            tile += gridDim.x;
+        }
+    }
+    if (failed || (tid == 0 && !p_ok)) av = a1 = a2 = aq = NAN;
+    __syncthreads();
+    if (tid == 0) {
+        // loads still in flight land in the ring: wait for them (with the limit)
+        uint64_t t1;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
+        for (int it = p_item - kTmaStages; it < p_item; ++it)
+            if (it >= 0) mbar_wait(smem_u32(&full[it % kTmaStages]), (uint32_t)((it / kTmaStages) & 1), t1);
+    }
+    block_partials(s, av, a1, a2, aq);
+}
+
+// The tensor-map encoder of the driver, looked up once through the runtime
+// (no link to the driver library).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// A [n_gal][K] FP32 row-major array as a 2-D tensor map with kTileK x kTileG boxes.
+bool make_sample_map(CUtensorMap &m, const float *base, long long n_gal, int K)
+{
+    auto enc = tensor_map_encoder();
+    if (!enc || n_gal <= 0 || n_gal > 0xFFFFFFFFll) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)n_gal};
+    const cuuint64_t strides[1] = {(cuuint64_t)K * sizeof(float)};
+    const cuuint32_t box[2] = {(cuuint32_t)kTileK, (cuuint32_t)kTileG};
+    const cuuint32_t estr[2] = {1, 1};
+    return enc(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(base), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 __global__ void __launch_bounds__(256) shear_finalize_kernel(const double *partials, int n_part,
                                                               double add_value, double add_g1,
                                                               double add_g2, double add_alpha,
@@ -655,6 +852,18 @@ __global__ void __launch_bounds__(256) shear_finalize_n_kernel(const double *par
 template <int FAMILY, bool HAS_B>
 cudaError_t launch_fb(const ShearLaunch &s, int grid, bool vec, cudaStream_t st)
 {
+    if (vec && !HAS_B) {
+        // e1, e2 as tensor maps, streamed in tiles by the tensor memory accelerator
+        CUtensorMap m1, m2;
+        if (make_sample_map(m1, s.e1, s.n_gal, s.K) && make_sample_map(m2, s.e2, s.n_gal, s.K)) {
+            const cudaError_t e = cudaFuncSetAttribute(shear_kernel_tma<FAMILY>,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                       (int)tma_smem_bytes());
+            if (e != cudaSuccess) return e;
+            shear_kernel_tma<FAMILY><<<grid, kShearThreads, tma_smem_bytes(), st>>>(s, m1, m2);
+            return cudaGetLastError();
+        }
+    }
     if (vec) {
         // the ring (48 KB, 72 KB with b) plus the static reduction buffer is
         // above the default dynamic shared-memory limit
