@@ -264,7 +264,7 @@ def _ellipticity_samples(rng, n, K, spread=0.25):
 
 
 @pytest.mark.parametrize("family", [O.EPRIOR_BA14, O.EPRIOR_TRUNC_GAUSS])
-@pytest.mark.parametrize("K,with_b", [(300, False), (300, True), (37, False), (1, True)])
+@pytest.mark.parametrize("K,with_b", [(300, False), (300, True), (37, False), (1, True), (52, False), (4, False)])
 def test_shear_loglike_matches_oracle(cuda, family, K, with_b):
     rng = np.random.default_rng(K + 7 * family)
     n = 2000
