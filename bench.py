@@ -215,10 +215,9 @@ CAPTURED_TRAFFIC = {
     "fit": ("paper_2604_22048_gb300/csrc/bs_fit_impl.cuh",
             "2c3a5b881660fbf9d9cbb7f8375b91cb282ca41b67f10c6b2200fcf3fa3217de", 42730.1,
             {"side": 53, "chains": 4, "n_warmup": 200, "n_samples": 300}),
-    # one interim sample of the shear workload: (489,620,992 + 3,289,856) B / (200,000 x 300),
-    # captured on sha256 44742046...dbfe54dc; the file has changed since in its header comment only
+    # one interim sample of the shear workload: (489,555,712 + 3,329,280) B / (200,000 x 300)
     "shear": ("paper_2604_22048_gb300/csrc/bs_shear.cu",
-              "afe3a119cc56bfabe514f50d0dceb4e8429038b817aad2eae149c66d9c7a6358", 8.2152, {}),
+              "e19c1f47b4eaafc2034dbb2986948ab4fdf98ed1bb5bda2692073845426dd5fe", 8.2148, {}),
 }
 
 

@@ -123,17 +123,19 @@ __device__ __forceinline__ uint64_t now_ns()
     return t;
 }
 
-// Wait for the phase of the given parity to complete; false after kWaitNs.
+// Wait for the phase of the given parity to complete; false after kWaitNs.  Each
+// try_wait may suspend the warp in hardware for up to 20 us until the phase
+// completes; the limit is checked between tries.
 __device__ __forceinline__ bool wait_parity(uint32_t bar, uint32_t parity)
 {
     const uint64_t t0 = now_ns();
     for (;;) {
         uint32_t ok;
         asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
             "selp.u32 %0, 1, 0, p;\n\t}"
             : "=r"(ok)
-            : "r"(bar), "r"(parity)
+            : "r"(bar), "r"(parity), "r"(20000u)
             : "memory");
         if (ok) return true;
         if (now_ns() - t0 > kWaitNs) return false;

@@ -488,15 +488,18 @@ __host__ __device__ constexpr size_t tma_smem_bytes()
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
+// Wait for the phase of the given parity.  Each try_wait may suspend the warp
+// in hardware for up to 20 us until the phase completes (no busy loop taking
+// issue slots from the computing warps); the limit is checked between tries.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_t t0)
 {
     for (;;) {
         uint32_t ok;
         asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
             "selp.u32 %0, 1, 0, p;\n\t}"
             : "=r"(ok)
-            : "r"(bar), "r"(parity)
+            : "r"(bar), "r"(parity), "r"(20000u)
             : "memory");
         if (ok) return true;
         uint64_t t;
