@@ -235,7 +235,7 @@ static bs_status fill_fit_params(const bs_fit_args *a, bs::FitParams &p, const c
                         "%s: chains_per_cta needs the exponential profile, one exposure and white noise", who);
         p.cpc = a->chains_per_cta;
     }
-    if (p.profile == 3) p.cpc = 1;   // the pixel-weight path: one chain per CTA
+    if (p.profile == 3) p.cpc = 2;   // the pixel-weight path: two chains per CTA
     return BS_OK;
 }
 
@@ -319,7 +319,7 @@ bs_status bs_fit_galaxies(const bs_fit_args *a, const bs_fit_out *o, void *works
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int per_sm = bs::fit_blocks_per_sm(bs::cta_chains(p), a->max_side, p.regs, p.profile);
     long long grid = (long long)sms * per_sm;
-    const long long items = (long long)a->n_gal * (a->n_chains / bs::cta_chains(p));
+    const long long items = (long long)a->n_gal * bs::cta_groups(p);
     if (grid > items) grid = items;
     e = bs::launch_fit(p, (int)grid, s);
     return e == cudaSuccess ? BS_OK : cuda_fail(e, "bs_fit_galaxies: launch");

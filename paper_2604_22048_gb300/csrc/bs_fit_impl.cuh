@@ -856,7 +856,7 @@ __device__ __forceinline__ bool trajectory(const FitParams &P, const GalCtx &gc,
         float gg[6];
         double v;
         if constexpr (PROF == 3)
-            v = eval_pix<NC>(P, gc, sm, gal, xph_c, vcol, x, gg, l == nst - 1);
+            v = eval_pix<NC>(P, gc, sm, gal, xph_c, vcol, x, gg, l == nst - 1, nullptr);
         else if constexpr (PROF == 4)
             v = eval_dense<NC>(P, gc, dense_view(sm.kxr, P.h_max, P.npad, P.max_side, slot), gal, sm.kxr, xph_c,
                                vcol, x, gg, l == nst - 1);
@@ -878,8 +878,8 @@ __device__ void run_chain(const FitParams &P, const GalCtx &gc, const SmemView &
     const int lane = threadIdx.x & 31;
     const int pi = lane < 6 ? lane : 5;     // parameter of this lane (lanes 6.. shadow parameter 5)
     const bool own = lane < 6;
-    // the pixel path's eight warps run the same chain: the first one writes its results
-    const bool wr = PROF != 3 || threadIdx.x < 32;
+    // the pixel path's groups of four warps run one chain each: their first warp writes
+    const bool wr = PROF != 3 || (threadIdx.x & 127) < 32;
     const int C = P.n_chains, W = P.n_warmup, S = P.n_samples, L = P.n_leapfrog;
     const uint64_t gid = P.gal_id ? P.gal_id[gal] : (uint64_t)gal;
     const uint64_t key = gid * (uint64_t)C + (uint64_t)chain;
@@ -1097,12 +1097,12 @@ __device__ __forceinline__ void fit_loop(const FitParams &P)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_gal, s_grp;
     const int cc = cta_chains(P);              // chains of this CTA
-    const int groups = P.n_chains / cc;        // CTAs a galaxy's chains are split over
-    // the pixel path: one chain per CTA, run by its eight warps (the first one's phase
-    // table serves the spectral pass)
-    const SmemView sm = smem_view(smem_raw, P.h_max, P.npad, P.max_side, PROF == 3 ? 1 : cc);
+    const int groups = cta_groups(P);          // CTAs a galaxy's chains are split over
+    // the pixel path: two chains per CTA, each run by a group of four warps (a phase
+    // table per group)
+    const SmemView sm = smem_view(smem_raw, P.h_max, P.npad, P.max_side, PROF == 3 ? 2 : cc);
     const int warp = threadIdx.x >> 5;
-    if constexpr (PROF == 3) pix_tc_begin(pix_tc_view(sm.kxr, P.h_max, P.max_side));
+    if constexpr (PROF == 3) pix_tc_begin(pix_tc_view(sm.kxr, P.h_max, P.npad, P.max_side));
     bool first = true;
     for (;;) {
         if (threadIdx.x == 0) {
@@ -1138,9 +1138,16 @@ __device__ __forceinline__ void fit_loop(const FitParams &P)
             continue;
         }
         if constexpr (PROF == 3) {
-            const PixTc px = pix_tc_view(sm.kxr, P.h_max, P.max_side);
-            pix_tc_setup(P, gc, px, gal);
-            run_chain<NC, PROF>(P, gc, sm, gal, s_grp, 0);
+            const PixTc px = pix_tc_view(sm.kxr, P.h_max, P.npad, P.max_side);
+            if (threadIdx.x == 0) px.done[0] = px.done[1] = 0;
+            pix_tc_setup(P, gc, sm, px, gal);
+            const int grp = warp >> 2, chain = 2 * s_grp + grp;
+            float vcol[NC];
+#pragma unroll
+            for (int j = 0; j < NC; ++j) vcol[j] = (float)((threadIdx.x & 31) + 32 * j - gc.c);
+            float2 *xph = sm.xph + (size_t)grp * phase_stride(P.h_max);
+            if (chain < P.n_chains) run_chain<NC, PROF>(P, gc, sm, gal, chain, grp);
+            pix_drain<NC>(P, gc, sm, gal, xph, vcol);
             __syncthreads();
             if (threadIdx.x == 0 && *px.abort && P.status) P.status[gal] = 4;
         } else {
@@ -1150,7 +1157,7 @@ __device__ __forceinline__ void fit_loop(const FitParams &P)
         __syncthreads();
         if (P.done) publish_galaxy(P, gal);
     }
-    if constexpr (PROF == 3) pix_tc_end(pix_tc_view(sm.kxr, P.h_max, P.max_side));
+    if constexpr (PROF == 3) pix_tc_end(pix_tc_view(sm.kxr, P.h_max, P.npad, P.max_side));
 }
 
 // Register budgets of the kernel instances (the launch bounds give ptxas the
@@ -1163,8 +1170,8 @@ template <int NC, int PROF>
 __global__ void __launch_bounds__(128, 5) fit_kernel_r96(const FitParams P) { fit_loop<NC, PROF>(P); }
 template <int NC, int PROF>
 __global__ void __launch_bounds__(256, 3) fit_kernel_r80(const FitParams P) { fit_loop<NC, PROF>(P); }
-// The pixel path: one chain per CTA of eight warps; its shared memory (the transforms'
-// constants and operands) allows one CTA per SM.
+// The pixel path: two chains per CTA of eight warps; its tensor memory (the transforms'
+// constants and accumulator: all 512 columns) allows one CTA per SM.
 template <int NC>
 __global__ void __launch_bounds__(tc::kThreads, 1) fit_kernel_pix(const FitParams P) { fit_loop<NC, 3>(P); }
 
@@ -1183,7 +1190,7 @@ __device__ void point_eval(const FitParams &P, const GalCtx &gc, const SmemView 
     double v = -INFINITY;
     if (in_support(P, th)) {
         if constexpr (PROF == 3)
-            v = eval_pix<NC>(P, gc, sm, gal, sm.xph, vcol, th, g, true);
+            v = eval_pix<NC>(P, gc, sm, gal, sm.xph, vcol, th, g, true, nullptr);
         else if constexpr (PROF == 4)
             v = eval_dense<NC>(P, gc, dense_view(sm.kxr, P.h_max, P.npad, P.max_side, 0), gal, sm.kxr, sm.xph, vcol,
                                th, g, true);
@@ -1233,16 +1240,18 @@ __global__ void __launch_bounds__(32) logpost_points_kernel(const FitParams P, i
     }
 }
 
-// The pixel path's points: one CTA of eight warps per point.
+// The pixel path's points: one CTA of eight warps per point; the first group of four
+// warps evaluates it, the second joins with a skip flag.
 template <int NC>
 __global__ void __launch_bounds__(tc::kThreads, 1) logpost_points_pix_kernel(const FitParams P, int n_points,
-                                                                    const int32_t *gal_index, const float *theta,
-                                                                    double *logp, float *grad)
+                                                                            const int32_t *gal_index, const float *theta,
+                                                                            double *logp, float *grad)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const SmemView sm = smem_view(smem_raw, P.h_max, P.npad, P.max_side, 1);
-    const PixTc px = pix_tc_view(sm.kxr, P.h_max, P.max_side);
+    const SmemView sm = smem_view(smem_raw, P.h_max, P.npad, P.max_side, 2);
+    const PixTc px = pix_tc_view(sm.kxr, P.h_max, P.npad, P.max_side);
     pix_tc_begin(px);
+    const int grp = threadIdx.x >> 7, lane = threadIdx.x & 31;
     for (int i = blockIdx.x; i < n_points; i += gridDim.x) {
         const int gal = gal_index[i];
         GalCtx gc;
@@ -1253,11 +1262,28 @@ __global__ void __launch_bounds__(tc::kThreads, 1) logpost_points_pix_kernel(con
             __syncthreads();
             continue;
         }
-        pix_tc_setup(P, gc, px, gal);
-        const float *th = theta + (size_t)i * 6;
-        double *lp = logp ? logp + i : nullptr;
-        float *gr = grad ? grad + (size_t)i * 6 : nullptr;
-        point_eval<NC, 3>(P, gc, sm, gal, th, lp, gr);
+        if (threadIdx.x == 0) px.done[0] = px.done[1] = 0;
+        pix_tc_setup(P, gc, sm, px, gal);
+        float vcol[NC];
+#pragma unroll
+        for (int j = 0; j < NC; ++j) vcol[j] = (float)(lane + 32 * j - gc.c);
+        float2 *xph = sm.xph + (size_t)grp * phase_stride(P.h_max);
+        if (grp == 0) {
+            const float *th = theta + (size_t)i * 6;
+            float t[6], g[6];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) t[k] = th[k];
+            double v = -INFINITY;
+            if (in_support(P, t)) {
+                v = eval_pix<NC>(P, gc, sm, gal, xph, vcol, t, g, true, nullptr);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 6; ++k) g[k] = NAN;
+            }
+            if (threadIdx.x == 0 && logp) logp[i] = v;
+            if (grad && threadIdx.x < 6) grad[(size_t)i * 6 + threadIdx.x] = pick6(g, threadIdx.x);
+        }
+        pix_drain<NC>(P, gc, sm, gal, xph, vcol);
         __syncthreads();
     }
     pix_tc_end(px);

@@ -11,60 +11,78 @@
 // D' = M + R (scaled as the table).  The transforms run on the tensor cores (the layout
 // and operand split are described with PixTc); one CTA of eight warps evaluates one chain.
 
-// Per galaxy (all threads): the constant blocks -S, C, S and the complex-to-real
-// constant of transform (2) for this side (high and low TF32 parts), and the stamp
-// and its weights in shared memory.
-__device__ void pix_tc_setup(const FitParams &P, const GalCtx &gc, const PixTc &px, int gal)
+// Per galaxy (all threads): the A operands of the four products for this side into
+// tensor memory (warp w writes lanes 32 (w mod 4) .. + 31, the high parts for w < 4 and
+// the low parts otherwise), the second chain's copy of the table, and the stamp and
+// its weights in shared memory.
+__device__ void pix_tc_setup(const FitParams &P, const GalCtx &gc, const SmemView &sm, const PixTc &px, int gal)
 {
-    const int tid = threadIdx.x, nth = blockDim.x;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int N = gc.N, c = gc.c, H = gc.H;
-    float *hi = px.cst, *lo = px.cst + tc::kCstFloats;
-    for (int i = tid; i < tc::kNP * tc::kNP; i += nth) {
-        const int a = i >> 6, b = i & 63;
-        float co = 0.f, sn = 0.f;
-        if (a < N && b < N) {
-            int k = ((a - c) * (b - c)) % N;   // exact reduction of the phase index
-            if (k < 0) k += N;
-            sincospif(2.0f * (float)k / (float)N, &sn, &co);
+    const int row = 32 * (warp & 3) + lane;      // the TMEM lane this thread writes
+    const bool lo = warp >= 4;
+    const uint32_t tl = *px.tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+    auto part = [&](float x) { const float h = tc::tf32_rn(x); return lo ? tc::tf32_rn(x - h) : h; };
+    // [[C, -S], [S, C]]: row r = (p, a), column k = (q, b): p = q gives C, else -S (p = 0) or S
+    const int p = row >> 6, a = row & 63;
+    for (int k0 = 0; k0 < 128; k0 += 8) {
+        float v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int k = k0 + j, q = k >> 6, b = k & 63;
+            float co = 0.f, sn = 0.f;
+            if (a < N && b < N) {
+                int m = ((a - c) * (b - c)) % N;   // exact reduction of the phase index
+                if (m < 0) m += N;
+                sincospif(2.0f * (float)m / (float)N, &sn, &co);
+            }
+            v[j] = part(p == q ? co : (p == 0 ? -sn : sn));
         }
-        const int e = tc::op_index(a, b, tc::kNP, tc::kLboC / 4);
-        tc::split_store(hi, lo, e, -sn);
-        tc::split_store(hi, lo, tc::kBlockFloats + e, co);
-        tc::split_store(hi, lo, 2 * tc::kBlockFloats + e, sn);
+        tc::st8(tl + (lo ? tc::kColAFlo : tc::kColAF) + k0, v);
     }
-    // rows ix, K (re, u | im, u): (w_u / N^2) (cos, -sin)(2 pi u (ix - c) / N)
+    // the complex-to-real constant: rows ix < 64, K (re, u | im, u):
+    // (w_u / N^2) (cos, -sin)(2 pi u (ix - c) / N); rows 64.. zero
     const float wn = 1.0f / ((float)N * (float)N);
-    for (int i = tid; i < tc::kNP * 32; i += nth) {
-        const int ix = i >> 5, u = i & 31;
-        float co = 0.f, sn = 0.f;
-        if (ix < N && u < H) {
-            int k = (u * (ix - c)) % N;
-            if (k < 0) k += N;
-            sincospif(2.0f * (float)k / (float)N, &sn, &co);
-            const float wu = u ? 2.0f * wn : wn;
-            co *= wu;
-            sn *= wu;
+    for (int k0 = 0; k0 < 64; k0 += 8) {
+        float v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int k = k0 + j, q = k >> 5, u = k & 31;
+            float co = 0.f, sn = 0.f;
+            if (row < N && u < H) {
+                int m = (u * (row - c)) % N;
+                if (m < 0) m += N;
+                sincospif(2.0f * (float)m / (float)N, &sn, &co);
+                const float wu = u ? 2.0f * wn : wn;
+                co *= wu;
+                sn *= wu;
+            }
+            v[j] = part(q ? -sn : co);
         }
-        tc::split_store(px.c2r, px.c2r + tc::kC2rFloats, tc::op_index(ix, u, 64, tc::kLboC / 4), co);
-        tc::split_store(px.c2r, px.c2r + tc::kC2rFloats, tc::op_index(ix, 32 + u, 64, tc::kLboC / 4), -sn);
+        tc::st8(tl + (lo ? tc::kColA2lo : tc::kColA2) + k0, v);
     }
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    const int nrow = gc.H * row_floats(P.npad);
+    for (int i = tid; i < nrow; i += blockDim.x) px.tab1[i] = sm.tab[i];
     const int64_t off = P.offsets[gal];
     const int n = N * N;
-    for (int i = tid; i < n; i += nth) {
+    for (int i = tid; i < n; i += blockDim.x) {
         px.dimg[i] = load_pix(P.data, P.data_f64, off + i);
         px.wimg[i] = __ldg(P.pix_w + off + i);
     }
+    tc::fence_before();
     __syncthreads();
+    tc::fence_after();
 }
 
-// One 3xTF32 product into TMEM (all threads; thread 0 issues and commits, everyone
-// waits for the given parity).  K runs over n_q halves of nk steps of 8: step (q, k)
-// reads A at a_q + 256 k (a constant: leading offset 128 B, row groups 2 KB apart,
-// its low part a_lo bytes after the high part) and B at b + q b_q + 288 k (the data
-// operand: leading offset 144 B, row groups sbo_b apart).  Returns false (for every
-// thread) if the wait gave up; the CTA is then aborted with that parity pending.
+// One 3xTF32 product into TMEM columns [0, N) (all threads; thread 0 issues and
+// commits, everyone waits for the given parity).  K runs over n_q halves of nk steps
+// of 8: step (q, k) reads A at TMEM column a + q a_q + 8 k (its low part a_lo columns
+// further) and B at b + q b_q + 288 k bytes (the data operand: leading offset 144 B,
+// row groups sbo_b apart).  Returns false (for every thread) if the wait gave up; the
+// CTA is then aborted with that parity pending.
 struct TcGemm {
-    uint32_t a_re, a_im, a_lo, b, b_q, sbo_b, id;
+    uint32_t a, a_q, a_lo, b, b_q, sbo_b, id;
     int n_q, nk;
 };
 __device__ __forceinline__ bool tc_run(const PixTc &px, const TcGemm &G, uint32_t parity)
@@ -78,17 +96,16 @@ __device__ __forceinline__ bool tc_run(const PixTc &px, const TcGemm &G, uint32_
         const uint32_t tmem = *px.tmem;
         const uint32_t b_lo = tc::kBopFloats * 4;
         for (int q = 0; q < G.n_q; ++q) {
-            const uint32_t a0 = q ? G.a_im : G.a_re, b0 = G.b + q * G.b_q;
-            // a k-step advances the start-address field (bytes / 16, the low 14 bits;
-            // every address stays below 256 KB, so the field does not carry)
-            uint64_t ah = tc::sdesc(a0, tc::kLboC, 2048), al = tc::sdesc(a0 + G.a_lo, tc::kLboC, 2048);
+            // a k-step advances the B descriptor's start-address field (bytes / 16, the
+            // low 14 bits; every address stays below 256 KB, so the field does not carry)
+            uint32_t a = tmem + G.a + q * G.a_q;
+            const uint32_t b0 = G.b + q * G.b_q;
             uint64_t bh = tc::sdesc(b0, tc::kLboB, G.sbo_b), bl = tc::sdesc(b0 + b_lo, tc::kLboB, G.sbo_b);
             for (int k = 0; k < G.nk; ++k) {
-                tc::mma(tmem, ah, bl, G.id, (q | k) ? 1u : 0u);
-                tc::mma(tmem, al, bh, G.id, 1u);
-                tc::mma(tmem, ah, bh, G.id, 1u);
-                ah += 256 / 16;
-                al += 256 / 16;
+                tc::mma_ta(tmem, a, bl, G.id, (q | k) ? 1u : 0u);
+                tc::mma_ta(tmem, a + G.a_lo, bh, G.id, 1u);
+                tc::mma_ta(tmem, a, bh, G.id, 1u);
+                a += 8;
                 bh += 288 / 16;
                 bl += 288 / 16;
             }
@@ -112,19 +129,20 @@ __device__ __forceinline__ double pix_nan(float g[6])
     return NAN;
 }
 
-// The gradient of the log posterior from the half-plane pass on the effective
-// spectrum in the table, with the rows split over the eight warps: warp w sums the
-// terms of its rows u in [r w, r (w + 1)), r even (the pass reads rows in pairs), and
-// the six warp sums meet in shared memory, where every thread adds them in warp order
-// and forms the gradient.  The per-point terms, the sums and the gradient formulas are
-// those of eval_logpost (exponential profile, no chi^2).
+// The gradient of the log posterior of this group's chain from the half-plane pass on
+// its effective spectrum, with the rows split over the group's four warps: warp j of
+// the group sums the terms of its rows u in [r j, r (j + 1)), r even (the pass reads
+// rows in pairs); the four warp sums meet in shared memory, where every thread of the
+// group adds them in warp order and forms the gradient.  The per-point terms, the sums
+// and the gradient formulas are those of eval_logpost (exponential profile, no chi^2).
 template <int NC>
-__device__ void pix_grad(const FitParams &P, const GalCtx &gc, const SmemView &sm, const PixTc &px, float2 *xph,
-                         const float vcol[NC], const float th[6], float g[6])
+__device__ void pix_grad(const FitParams &P, const GalCtx &gc, const float *tab, const float2 *kxr, const PixTc &px,
+                         float2 *xph, const float vcol[NC], const float th[6], float g[6])
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int per = 2 * ((gc.H + 15) >> 4);
-    const int u0 = min(gc.H, warp * per), u1 = min(gc.H, u0 + per);
+    const int grp = warp >> 2, wj = warp & 3;
+    const int per = 2 * ((gc.H + 7) >> 3);
+    const int u0 = min(gc.H, wj * per), u1 = min(gc.H, u0 + per);
     const float F = exp10f(th[0]);
     const float r0 = exp10f(th[1]) * (1.0f / kHlrOverR0);
     const float r02 = r0 * r0;
@@ -181,8 +199,8 @@ __device__ void pix_grad(const FitParams &P, const GalCtx &gc, const SmemView &s
     S.chi_hi = f2(0.f);
     S.chi_lo = f2(0.f);
     if (u1 > u0)
-        half_plane<NC, false, 0>(S, K, sm.tab + (size_t)u0 * row_floats(P.npad), sm.kxr + u0, xph + u0, u1 - u0,
-                                 al, F2, P.prof_npow);
+        half_plane<NC, false, 0>(S, K, tab + (size_t)u0 * row_floats(P.npad), kxr + u0, xph + u0,
+                                 u1 - u0, al, F2, P.prof_npow);
     float Swkx2 = S.Swkx2.x + S.Swkx2.y, Sbkx = S.Sbkx.x + S.Sbkx.y;
     float Sw = 0.f, Swky2 = 0.f, Swkxky = 0.f, Sbky = 0.f;
 #pragma unroll
@@ -205,18 +223,14 @@ __device__ void pix_grad(const FitParams &P, const GalCtx &gc, const SmemView &s
     }
     float sums[6] = {Sw, Swkx2, Swky2, Swkxky, Sbkx, Sbky};
     warp_sum_n(sums);
+    float *gs = px.gsum + grp * 24;
     if (lane == 0) {
 #pragma unroll
-        for (int k = 0; k < 6; ++k) px.gsum[6 * warp + k] = sums[k];
+        for (int k = 0; k < 6; ++k) gs[6 * wj + k] = sums[k];
     }
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < 6; ++k) {
-        float t = 0.f;
-#pragma unroll
-        for (int w = 0; w < 8; ++w) t += px.gsum[6 * w + k];
-        sums[k] = t;
-    }
+    for (int k = 0; k < 6; ++k) sums[k] = ((gs[k] + gs[6 + k]) + gs[12 + k]) + gs[18 + k];
     Sw = sums[0];
     Swkx2 = sums[1];
     Swky2 = sums[2];
@@ -241,17 +255,26 @@ __device__ void pix_grad(const FitParams &P, const GalCtx &gc, const SmemView &s
     g[5] = gc.p * Sbky * ib - th[5] * P.inv_sxy2;
 }
 
+// One evaluation of both chains of the CTA (all threads; each group passes its own
+// chain's th; a group with skip set passes any finite th and ignores the results).
+// Returns the log posterior of the caller's chain if want_ll (the caller's group's
+// flag), else 0; *all_done is set when both groups have raised their done flags (the
+// evaluation then does nothing).
 template <int NC>
 __device__ double eval_pix(const FitParams &P, const GalCtx &gc, const SmemView &sm, int gal, float2 *xph,
-                           const float vcol[NC], const float th[6], float g[6], bool want_ll)
+                           const float vcol[NC], const float th[6], float g[6], bool want_ll, bool *all_done)
 {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int half = warp >> 2;                       // column half of the TMEM reads
+    const int grp = warp >> 2;                        // the chain of this thread's group
     const int L = 32 * (warp & 3) + lane;             // this thread's TMEM lane
-    const PixTc px = pix_tc_view(sm.kxr, P.h_max, P.max_side);
+    const int tg = tid & 127;                         // thread within the group
+    const PixTc px = pix_tc_view(sm.kxr, P.h_max, P.npad, P.max_side);
     const int N = gc.N, H = gc.H, c = gc.c, npad = P.npad;
     const int rowf = row_floats(npad);
-    __syncthreads();   // the previous evaluation's readers of the table and buffers are done
+    float *tab = grp ? px.tab1 : sm.tab;
+    __syncthreads();   // the previous evaluation's readers of the tables and buffers are done
+    if (all_done) *all_done = px.done[0] && px.done[1];
+    if (px.done[0] && px.done[1]) return 0.0;
     if (*px.abort) return pix_nan(g);
     const float F = exp10f(th[0]);
     const float r0 = exp10f(th[1]) * (1.0f / kHlrOverR0);
@@ -263,42 +286,43 @@ __device__ double eval_pix(const FitParams &P, const GalCtx &gc, const SmemView 
     const float be = r02 * (1.0f + E - 2.0f * e1) * Pq;
     const float ga = r02 * 4.0f * e2 * Pq;
     const float sqrt2 = 1.41421356237309515f;
-    if (tid < 32) {
+    float2 *xs = px.xs + 32 * grp, *ys = px.ys + 64 * grp;
+    if (tg < 32) {
         float sx = 0.f, cx = 0.f;
-        if (tid < H) sincospi_sfu(-2.0f * th[4] * (float)tid * gc.invN, &sx, &cx);
-        px.xs[tid] = make_float2(cx, sx);
-    } else if (tid < 96) {
-        const int vi = tid - 32;
+        if (tg < H) sincospi_sfu(-2.0f * th[4] * (float)tg * gc.invN, &sx, &cx);
+        xs[tg] = make_float2(cx, sx);
+    } else if (tg < 96) {
+        const int vi = tg - 32;
         float sy = 0.f, cy = 0.f;
         if (vi < N) sincospi_sfu(-2.0f * th[5] * (float)(vi - c) * gc.invN, &sy, &cy);
-        px.ys[vi] = make_float2(F * cy, F * sy);
+        ys[vi] = make_float2(F * cy, F * sy);
     }
     __syncthreads();
     float *bh = px.bop, *bl = px.bop + tc::kBopFloats;
     constexpr int kLb = tc::kLboB / 4;
-    // (a) the model's half spectrum Mt into the table's D slots, and M = Mt / scale_u
-    // as the operand of (1): rows u < 32, K (re, vi | im, vi), 128 per row; thread t
-    // takes column vi = t mod 64 and the rows u = t / 64 + 4 i
+    // (a) the model's half spectrum Mt into the chain's table D slots, and M = Mt /
+    // scale_u as the operand of (1): rows (chain, u < 32), K (re, vi | im, vi); thread
+    // tg of the group takes column vi = tg mod 64 and the rows u = tg / 64 + 2 i
     {
-        const int vi = tid & 63, u0 = tid >> 6;
+        const int vi = tg & 63, u0 = tg >> 6;
         const bool col = vi < N;
         int ox = 0, oy = 0, ot = 0;
         if (col) slot_offsets(npad, vi >> 5, vi & 31, ox, oy, ot);
         const float ky = (float)(vi - c) * gc.dk;
         const float cst = fmaf(be * ky, ky, 1.0f), gky = ga * ky;
-        const float2 Y = px.ys[vi];
+        const float2 Y = ys[vi];
         const float sN = (float)N, sN2 = (float)N * 0.70710678118654752f;
 #pragma unroll 4
-        for (int i = 0; i < 8; ++i) {
-            const int u = u0 + 4 * i;
+        for (int i = 0; i < 16; ++i) {
+            const int u = u0 + 2 * i;
             float Mr = 0.f, Mi = 0.f;
             if (col && u < H) {
-                float *row = sm.tab + (size_t)u * rowf;
+                float *row = tab + (size_t)u * rowf;
                 const float kx = sm.kxr[u].x;
                 const float s = fmaf(fmaf(al, kx, gky), kx, cst);
                 const float rs = rsqrtf(s);
                 const float A = row[ot] * rs * rs * rs;
-                const float2 X = px.xs[u];
+                const float2 X = xs[u];
                 const float mr = A * (X.x * Y.x - X.y * Y.y), mi = A * (X.x * Y.y + X.y * Y.x);
                 row[ox] = mr;
                 row[oy] = mi;
@@ -306,59 +330,63 @@ __device__ double eval_pix(const FitParams &P, const GalCtx &gc, const SmemView 
                 Mr = mr * inv_scale;
                 Mi = mi * inv_scale;
             }
-            tc::split_store(bh, bl, tc::op_index(u, vi, 128, kLb), Mr);
-            tc::split_store(bh, bl, tc::op_index(u, 64 + vi, 128, kLb), Mi);
+            tc::split_store(bh, bl, tc::op_index(32 * grp + u, vi, 128, kLb), Mr);
+            tc::split_store(bh, bl, tc::op_index(32 * grp + u, 64 + vi, 128, kLb), Mi);
         }
     }
-    const uint32_t cst = tc::saddr(px.cst), bop = tc::saddr(px.bop), c2r = tc::saddr(px.c2r);
-    const uint32_t blk_nS = cst, blk_C = cst + tc::kBlockFloats * 4, cst_lo = tc::kCstFloats * 4;
+    const uint32_t bop = tc::saddr(px.bop);
     const int ks = (N + 7) >> 3;   // k-steps of 8 covering the side
     const uint32_t tl = *px.tmem + ((uint32_t)(32 * (warp & 3)) << 16);
-    // (1) G = M E: rows (re, iy | im, iy), columns u
-    if (!tc_run(px, TcGemm{blk_C, blk_nS, cst_lo, bop, 16u * 144, 32u * 144, tc::idesc(128, 32, false), 2, ks}, 0))
+    constexpr uint32_t aflo = tc::kColAFlo - tc::kColAF, a2lo = tc::kColA2lo - tc::kColA2;
+    // (1) G = M E for both chains: rows (re, iy | im, iy), columns (chain, u)
+    if (!tc_run(px, TcGemm{tc::kColAF, 64u, aflo, bop, 16u * 144, 32u * 144, tc::idesc(128, 64, false), 2, ks}, 0))
         return pix_nan(g);
-    // (1) -> operand of (2): row iy, K (re, u | im, u), G as it is (the weights are in
-    // the constant); this thread's 16 columns u of its lane (p, iy)
+    // (1) -> operand of (2): row (chain, iy), K (re, u | im, u), G as it is (the weights
+    // are in the constant); this thread's lane (p, iy), its chain's 32 columns
     {
-        float v[16];
-        tc::ld16(tl + 16 * half, v);
+        float v[32];
+        tc::ld32(tl + 32 * grp, v);
         const int p = L >> 6, iy = L & 63;
-        const int e0 = tc::op_index(iy, p * 32 + 16 * half, 64, kLb);
+        const int e0 = tc::op_index(64 * grp + iy, p * 32, 64, kLb);
 #pragma unroll
-        for (int m = 0; m < 4; ++m)
+        for (int m = 0; m < 8; ++m)
             tc::split_store4(bh, bl, e0 + m * kLb, v[4 * m], v[4 * m + 1], v[4 * m + 2], v[4 * m + 3]);
     }
-    // (2) m = W G: rows ix, columns iy
-    if (!tc_run(px, TcGemm{c2r, c2r + 8u * 128, tc::kC2rFloats * 4, bop, 8u * 144, 16u * 144,
-                           tc::idesc(128, 64, false), 2, (H + 7) >> 3},
+    // (2) m = W G: rows ix, columns (chain, iy)
+    if (!tc_run(px, TcGemm{tc::kColA2, 32u, a2lo, bop, 8u * 144, 16u * 144, tc::idesc(128, 128, false), 2,
+                           (H + 7) >> 3},
                 1))
         return pix_nan(g);
     // the residual, chi^2 (compensated FP32 per thread, FP64 across threads) and the
-    // operand of (3): rows iy, K ix; lanes ix < 64 of warps 0, 1, 4, 5, the columns iy
-    // of this thread's half
+    // operand of (3): rows (chain, iy), K ix; lanes ix < 64 of the group's warps 0 and
+    // 1, the chain's 64 columns iy
     double chi = 0.0;
     if ((warp & 3) < 2) {
         const int ix = L;
         float c_hi = 0.f, c_lo = 0.f;
-        float m[32];
-        tc::ld32(tl + 32 * half, m);
         const int eb = (ix >> 2) * kLb + (ix & 3);
 #pragma unroll
-        for (int t = 0; t < 32; ++t) {
-            const int iy = 32 * half + t;
-            float r = 0.f;
-            if (ix < N && iy < N) {
-                const int e = iy * N + ix;
-                const float res = px.dimg[e] - m[t];
-                r = px.wimg[e] * res;
-                if (want_ll) {
-                    float t_hi, t_lo;
-                    two_sum(c_hi, r * res, t_hi, t_lo);
-                    c_hi = t_hi;
-                    c_lo += t_lo;
+        for (int h = 0; h < 2; ++h) {
+            float m[32];
+            tc::ld32(tl + 64 * grp + 32 * h, m);
+#pragma unroll
+            for (int t = 0; t < 32; ++t) {
+                const int iy = 32 * h + t;
+                float r = 0.f;
+                if (ix < N && iy < N) {
+                    const int e = iy * N + ix;
+                    const float res = px.dimg[e] - m[t];
+                    r = px.wimg[e] * res;
+                    if (want_ll) {
+                        float t_hi, t_lo;
+                        two_sum(c_hi, r * res, t_hi, t_lo);
+                        c_hi = t_hi;
+                        c_lo += t_lo;
+                    }
                 }
+                const int rr = 64 * grp + iy;
+                tc::split_store(bh, bl, eb + (rr >> 3) * 16 * kLb + ((rr & 7) << 2), r);
             }
-            tc::split_store(bh, bl, eb + (iy >> 3) * 16 * kLb + ((iy & 7) << 2), r);
         }
         chi = (double)c_hi + (double)c_lo;
     }
@@ -366,57 +394,74 @@ __device__ double eval_pix(const FitParams &P, const GalCtx &gc, const SmemView 
         const double cw = warp_sum_d(chi);
         if (lane == 0) px.chi[warp] = cw;
     }
-    // (3) conj Q = [C S] r: rows (re, a | im, a), columns iy
-    if (!tc_run(px, TcGemm{blk_C, blk_C, cst_lo, bop, 0u, 16u * 144, tc::idesc(128, 64, false), 1, ks}, 0))
+    // (3) conj Q = [C; S] r: rows (re, a | im, a), columns (chain, iy)
+    if (!tc_run(px, TcGemm{tc::kColAF, 0u, aflo, bop, 0u, 16u * 144, tc::idesc(128, 128, false), 1, ks}, 0))
         return pix_nan(g);
-    // (3) -> operand of (4): row u = a - c < 32, K (re, iy | im, iy); this thread's 32
-    // columns iy of its lane (q, a)
+    // (3) -> operand of (4): row (chain, u = a - c < 32), K (re, iy | im, iy); this
+    // thread's lane (q, a), its chain's 64 columns iy
     {
         const int q = L >> 6, u = (L & 63) - c;
-        float v[32];
-        tc::ld32(tl + 32 * half, v);
-        if (u >= 0 && u < 32) {
-            const int e0 = tc::op_index(u, q * 64 + 32 * half, 128, kLb);
 #pragma unroll
-            for (int m = 0; m < 8; ++m)
-                tc::split_store4(bh, bl, e0 + m * kLb, v[4 * m], v[4 * m + 1], v[4 * m + 2], v[4 * m + 3]);
+        for (int h = 0; h < 2; ++h) {
+            float v[32];
+            tc::ld32(tl + 64 * grp + 32 * h, v);
+            if (u >= 0 && u < 32) {
+                const int e0 = tc::op_index(32 * grp + u, q * 64 + 32 * h, 128, kLb);
+#pragma unroll
+                for (int m = 0; m < 8; ++m)
+                    tc::split_store4(bh, bl, e0 + m * kLb, v[4 * m], v[4 * m + 1], v[4 * m + 2], v[4 * m + 3]);
+            }
         }
     }
-    // (4) conj R = E conj Q: rows (re, vi | im, vi), columns u
-    if (!tc_run(px, TcGemm{blk_C, blk_nS, cst_lo, bop, 16u * 144, 32u * 144, tc::idesc(128, 32, false), 2, ks}, 1))
+    // (4) conj R = E conj Q: rows (re, vi | im, vi), columns (chain, u)
+    if (!tc_run(px, TcGemm{tc::kColAF, 64u, aflo, bop, 16u * 144, 32u * 144, tc::idesc(128, 64, false), 2, ks}, 1))
         return pix_nan(g);
-    // D' = Mt + scale_u R in the table's D slots; this thread's 16 columns u of its
-    // lane (p, vi)
+    // D' = Mt + scale_u R in the chain's table D slots; this thread's lane (p, vi), its
+    // chain's 32 columns u
     {
         const int p = L >> 6, vi = L & 63;
-        float v[16];
-        tc::ld16(tl + 16 * half, v);
+        float v[32];
+        tc::ld32(tl + 32 * grp, v);
         if (vi < N) {
             int ox, oy, ot;
             slot_offsets(npad, vi >> 5, vi & 31, ox, oy, ot);
             const int os = p ? oy : ox;
             const float sg = p ? -gc.invN : gc.invN;
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const int u = 16 * half + j;
+            for (int u = 0; u < 32; ++u) {
                 if (u < H) {
-                    float *slot = sm.tab + (size_t)u * rowf + os;
-                    *slot = fmaf((u ? sqrt2 : 1.0f) * sg, v[j], *slot);
+                    float *slot = tab + (size_t)u * rowf + os;
+                    *slot = fmaf((u ? sqrt2 : 1.0f) * sg, v[u], *slot);
                 }
             }
         }
     }
     __syncthreads();
-    // the gradient from the half-plane pass on the effective spectrum, its rows over
-    // the eight warps
-    pix_grad<NC>(P, gc, sm, px, xph, vcol, th, g);
+    // the gradient from the half-plane pass on the chain's effective spectrum, its rows
+    // over the group's four warps
+    pix_grad<NC>(P, gc, tab, sm.kxr, px, xph, vcol, th, g);
     if (!want_ll) return 0.0;
-    double chi2 = 0.0;
-#pragma unroll
-    for (int w = 0; w < 8; ++w) chi2 += px.chi[w];
+    const double chi2 = px.chi[4 * grp] + px.chi[4 * grp + 1];
     const float lprior = P.prior_const - 0.5f * (th[4] * th[4] + th[5] * th[5]) * P.inv_sxy2 +
                          2.0f * log1pf(-E) - 0.5f * E * P.inv_se2;
     return -0.5 * chi2 * (double)gc.inv_b + (double)lprior;
+}
+
+// A group whose chain has no further evaluations (all threads of the group): raise
+// its done flag, then join the other group's evaluations until both are done.
+template <int NC>
+__device__ void pix_drain(const FitParams &P, const GalCtx &gc, const SmemView &sm, int gal, float2 *xph,
+                          const float vcol[NC])
+{
+    const PixTc px = pix_tc_view(sm.kxr, P.h_max, P.npad, P.max_side);
+    if ((threadIdx.x & 127) == 0) px.done[threadIdx.x >> 7] = 1;
+    const float th[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};   // any finite point: the results are not used
+    float g[6];
+    for (;;) {
+        bool all = false;
+        eval_pix<NC>(P, gc, sm, gal, xph, vcol, th, g, false, &all);
+        if (all) break;
+    }
 }
 
 // ---- A general dense pixel covariance (Appendix C, Eq. covar-pixel-likelihood):

@@ -23,7 +23,7 @@ FitKernel prof_kernel(int max_side)
     }
 }
 
-// Per-pixel weights (profile 3), exponential: stamps of at most 63 px, one chain
+// Per-pixel weights (profile 3), exponential: stamps of at most 63 px, two chains
 // per CTA of eight warps, the transforms on the tensor cores.
 FitKernel pix_kernel(int max_side)
 {
@@ -53,7 +53,10 @@ PointsKernel points_for(int profile, int max_side)
 // per-chain scratch.
 size_t smem_for(int profile, int max_side, int n_chains)
 {
-    if (is_pix(profile)) return fit_smem_bytes(max_side, 1) + 16 + pix_tc_bytes(max_side);
+    if (is_pix(profile)) {
+        const int h = (max_side + 1) / 2, npad = 32 * ((max_side + 31) / 32);
+        return fit_smem_bytes(max_side, 2) + 16 + pix_tc_bytes(max_side, h, npad);
+    }
     size_t b = fit_smem_bytes(max_side, n_chains);
     if (profile == 4) {
         const int h = (max_side + 1) / 2, npad = 32 * ((max_side + 31) / 32);

@@ -80,6 +80,12 @@ struct FitParams {
 
 // Chains (warps) of one CTA of a fit launch.
 __host__ __device__ inline int cta_chains(const FitParams &p) { return p.cpc > 0 ? p.cpc : p.n_chains; }
+// CTAs a galaxy's chains are split over (the pixel-weight path: pairs of chains, the
+// last one alone for an odd count).
+__host__ __device__ inline int cta_groups(const FitParams &p)
+{
+    return p.profile == 3 ? (p.n_chains + 1) / 2 : p.n_chains / cta_chains(p);
+}
 
 // Shared memory bytes per CTA for a given max stamp side and chains per galaxy.
 size_t fit_smem_bytes(int max_side, int n_chains);

@@ -12,31 +12,34 @@
 // (w_0 = 1, w_u = 2 for u > 0, v = vi - c centred), and the gradient is the spectral
 // half-plane pass on the effective spectrum D' = Mt + (sqrt(w_u) / N) R.
 //
-// With centred indices every transform is a product with the blocks of one symmetric
-// matrix, C[a][b] = cos(2 pi (a - c)(b - c) / N) and S[a][b] = sin(...), zero-padded to
-// 64 x 64:
-//   (1)  rows (re, iy | im, iy) x K (re, v | im, v): [C S] on the real half, [-S C] on
-//        the imaginary half of K;
+// With centred indices every transform is a product with one matrix built from
+// C[a][b] = cos(2 pi (a - c)(b - c) / N) and S[a][b] = sin(...), zero-padded to 64 x 64:
+//   (1)  rows (re, iy | im, iy) x K (re, v | im, v): A = [[C, -S], [S, C]];
 //   (2)  rows ix x K (re, u | im, u): its own complex-to-real constant with the weights
 //        w_u / N^2 folded in, so that the operand is G as the first product leaves it;
-//   (3)  rows (re, u + c | im, u + c) x K ix: [C S] (the imaginary output is -Q_i);
-//   (4)  conj R = transform (1) of conj Q, and the output of (3) is conj Q already.
-// The shared memory holds the blocks in the order -S, C, S, so every A operand of
-// 128 rows is two consecutive blocks; rows past the 64 of (2) read the memory after its
-// constant and give lanes that are not read.  Each transform is a tcgen05.mma of kind::tf32
-// (M = 128, N = 32 or 64, K = 8 per instruction, operands in shared memory without
-// swizzle, accumulator in TMEM) in three terms, A_hi B_hi + A_hi B_lo + A_lo B_hi
-// with x = hi + lo split by round-to-nearest TF32 (3xTF32): the operand rounding of
-// plain TF32 would miss the log-likelihood tolerance by a factor of several.
+//   (3)  rows (re, u + c | im, u + c) x K ix: the first half [C; S] of (1)'s A (the
+//        imaginary output is -Q_i: conj Q);
+//   (4)  conj R = transform (1) of conj Q.
+// These A operands live in tensor memory (lane = row, column = K index), high and
+// low TF32 parts: 384 of the CTA's 512 columns, the accumulator the other 128.  Each
+// transform is a tcgen05.mma of kind::tf32 (M = 128, N = 64 or 128, K = 8 per
+// instruction; B, the data, in shared memory without swizzle) in three terms,
+// A_hi B_hi + A_hi B_lo + A_lo B_hi with x = hi + lo split by round-to-nearest TF32
+// (3xTF32): the operand rounding of plain TF32 would miss the log-likelihood
+// tolerance by a factor of several.
 //
-// One CTA of eight warps per chain: every warp runs the chain's scalar logic (its
-// decisions are the same in all eight, from the same numbers), the transforms and the
-// elementwise steps between them are split over the 256 threads (warps w and w + 4
-// read the two column halves of TMEM lanes 32 (w mod 4) .. + 31), the first warp runs
-// the spectral gradient pass and shares its result, and thread 0 issues the MMAs.  Each evaluation commits four MMA groups to
-// one mbarrier, so the parities it waits on are 0, 1, 0, 1 in every evaluation.  A
-// wait gives up after two seconds: the CTA then marks its galaxy (status 4), issues no
-// further MMA, and its evaluations return NaN until the chain ends.
+// One CTA of eight warps runs two chains in lockstep: warps 0-3 the first, 4-7 the
+// second (each group's warps run the same chain logic and make the same decisions,
+// from the same numbers).  Every step of a chain is one evaluation, so the two meet
+// at each one; every product carries both chains' data (B rows (chain, u) or (chain,
+// iy)), so each barrier and MMA round trip serves two evaluations.  Thread t reads TMEM
+// lane 32 (w mod 4) + (t mod 32) and its chain's columns (w / 4), the group's warps
+// split the spectral gradient pass by rows, and thread 0 issues the MMAs.  A chain that
+// has finished, or has no evaluation at a step, joins with a skip flag until both are
+// done.  Each evaluation commits four MMA groups to one mbarrier, so the parities it
+// waits on are 0, 1, 0, 1 in every evaluation.  A wait gives up after two seconds: the
+// CTA then marks its galaxy (status 4), issues no further MMA, and its evaluations
+// return NaN until the chains end.
 #include <cstdint>
 
 namespace bs {
@@ -46,13 +49,9 @@ namespace {
 namespace tc {
 
 constexpr int kNP = 64;                        // padded side of the transforms
-constexpr int kLboC = 128;                     // constant blocks: K-adjacent core matrices contiguous
 constexpr int kLboB = 144;                     // data operands: 16-byte pad per core matrix (column
                                                // stores of a warp fall in 32 distinct banks)
-constexpr int kBlockFloats = kNP * kNP;        // one 64 x 64 block, 16 KB
-constexpr int kCstFloats = 3 * kBlockFloats;   // -S, C, S of one precision level
-constexpr int kBopFloats = 8 * 16 * (kLboB / 4);   // largest data operand: 64 rows x 64 K (or 32 x 128)
-constexpr int kC2rFloats = kNP * kNP;           // the complex-to-real constant, 64 x 64
+constexpr int kBopFloats = 16 * 16 * (kLboB / 4);   // one data operand: 128 rows x 64 K or 64 x 128
 constexpr uint64_t kWaitNs = 2000000000ull;    // limit of one MMA wait
 
 // Element (row, k) of an operand of kt K-elements per row (no swizzle, K-major):
@@ -95,14 +94,6 @@ __device__ __forceinline__ void split_store(float *hi, float *lo, int i, float x
     const float h = tf32_rn(x);
     hi[i] = h;
     lo[i] = tf32_rn(x - h);
-}
-
-__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t id, uint32_t accumulate)
-{
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(id), "r"(accumulate));
 }
 
 __device__ __forceinline__ void commit(uint32_t bar)
@@ -191,8 +182,31 @@ __device__ __forceinline__ void split_store4(float *hi, float *lo, int i, float 
     *reinterpret_cast<float4 *>(lo + i) = l;
 }
 
-constexpr int kTmemCols = 64;
-constexpr int kThreads = 256;                  // eight warps: lane quadrant warp % 4, column half warp / 4
+// TMEM columns of the CTA: the accumulator, then the A operands (high, low).
+constexpr int kTmemCols = 512;
+constexpr int kColAF = 128;                    // [[C, -S], [S, C]], 128 columns: K (re, v | im, v)
+constexpr int kColAFlo = 256;
+constexpr int kColA2 = 384;                    // the complex-to-real constant, 64 columns: K (re, u | im, u)
+constexpr int kColA2lo = 448;
+constexpr int kThreads = 256;                  // eight warps: lane quadrant w % 4, chain w / 4
+
+__device__ __forceinline__ void mma_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t id, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(b), "r"(id), "r"(accumulate));
+}
+
+// Eight consecutive TMEM columns of this thread's lane.
+__device__ __forceinline__ void st8(uint32_t taddr, const float (&v)[8])
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr),
+                 "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+                 "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+                 "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7]))
+                 : "memory");
+}
 
 }  // namespace tc
 
@@ -200,33 +214,31 @@ constexpr int kThreads = 256;                  // eight warps: lane quadrant war
 struct PixTc {
     double *chi;      // [8] per-warp partial chi^2 of the evaluation
     uint64_t *bar;    // MMA completion barrier
-    uint32_t *tmem;   // TMEM base of the CTA's accumulator (64 columns)
-    int *abort;       // 1 once a wait gave up
-    float2 *xs;       // [32] exp(-2 pi i u dx / N)
-    float2 *ys;       // [64] F exp(-2 pi i v dy / N), v = vi - c
-    float *gsum;      // [8][6] each warp's six gradient sums
-    float *c2r;       // [2][64 x 64] the complex-to-real constant of transform (2), high then low
-    float *cst;       // [2][3][64 x 64] blocks -S, C, S: TF32 high parts, then low parts
+    uint32_t *tmem;   // TMEM base of the CTA (512 columns)
+    int *abort;       // 2 + the pending parity once a wait gave up, else 0
+    int *done;        // [2] a chain group has no more evaluations
+    float2 *xs;       // [2][32] per chain: exp(-2 pi i u dx / N)
+    float2 *ys;       // [2][64] per chain: F exp(-2 pi i v dy / N), v = vi - c
+    float *gsum;      // [2][4][6] per chain and warp of its group: the six gradient sums
     float *bop;       // [2][kBopFloats] the data operand of the current transform, high then low
+    float *tab1;      // [h_max][3 npad] the second chain's table (the first's is the staged one)
     float *dimg;      // [max_side^2] the stamp
     float *wimg;      // [max_side^2] the weights
 };
 
 __host__ __device__ __forceinline__ int pix_tc_img_floats(int max_side) { return (max_side * max_side + 3) & ~3; }
 
-// Floats of the region: 16 (chi) + 2 (barrier) + 2 (TMEM address, abort) + 64 (xs) +
-// 128 (ys) + 48 (gradient sums) + 4 (pad) + constants + operand + two images.  The
-// complex-to-real constant lies before the blocks, so the 64 rows past its own that
-// an M = 128 product reads are in the region.
-__host__ __device__ __forceinline__ size_t pix_tc_bytes(int max_side)
+// Floats of the region: 16 (chi) + 2 (barrier) + 1 (TMEM address) + 1 (abort) + 2
+// (done) + 2 (pad) + 128 (xs) + 256 (ys) + 48 (gradient sums) + operand + table + two
+// images.
+__host__ __device__ __forceinline__ size_t pix_tc_bytes(int max_side, int h_max, int npad)
 {
-    return ((size_t)264 + 2 * tc::kC2rFloats + 2 * tc::kCstFloats + 2 * tc::kBopFloats +
-            2 * (size_t)pix_tc_img_floats(max_side)) *
+    return ((size_t)456 + 2 * tc::kBopFloats + (size_t)h_max * 3 * npad + 2 * (size_t)pix_tc_img_floats(max_side)) *
            sizeof(float);
 }
 
 // The region starts after the (kx, kx^2) table (h_max + 1 float2), 16-byte aligned.
-__device__ __forceinline__ PixTc pix_tc_view(float2 *kxr, int h_max, int max_side)
+__device__ __forceinline__ PixTc pix_tc_view(float2 *kxr, int h_max, int npad, int max_side)
 {
     float *base = reinterpret_cast<float *>(kxr + ((h_max + 2) & ~1));
     PixTc v;
@@ -234,13 +246,13 @@ __device__ __forceinline__ PixTc pix_tc_view(float2 *kxr, int h_max, int max_sid
     v.bar = reinterpret_cast<uint64_t *>(base + 16);
     v.tmem = reinterpret_cast<uint32_t *>(base + 18);
     v.abort = reinterpret_cast<int *>(base + 19);
-    v.xs = reinterpret_cast<float2 *>(base + 20);
-    v.ys = reinterpret_cast<float2 *>(base + 84);
-    v.gsum = base + 212;
-    v.c2r = base + 264;
-    v.cst = v.c2r + 2 * tc::kC2rFloats;
-    v.bop = v.cst + 2 * tc::kCstFloats;
-    v.dimg = v.bop + 2 * tc::kBopFloats;
+    v.done = reinterpret_cast<int *>(base + 20);
+    v.xs = reinterpret_cast<float2 *>(base + 24);
+    v.ys = reinterpret_cast<float2 *>(base + 152);
+    v.gsum = base + 408;
+    v.bop = base + 456;
+    v.tab1 = v.bop + 2 * tc::kBopFloats;
+    v.dimg = v.tab1 + (size_t)h_max * 3 * npad;
     v.wimg = v.dimg + pix_tc_img_floats(max_side);
     return v;
 }
@@ -271,7 +283,6 @@ __device__ void pix_tc_end(const PixTc &px)
 {
     __syncthreads();
     if (threadIdx.x == 0 && *px.abort) {
-        // the abort records 2 + the parity that was pending
         const int pend = *px.abort - 2;
         if (pend >= 0) tc::wait_parity(tc::saddr(px.bar), (uint32_t)pend);
     }

@@ -86,7 +86,7 @@ cudaError_t time_variant(const bs_fit_plan_s::Launch &L, int regs, int n_trial, 
     p.regs = regs;
     p.n_work = n_trial;
     const int per_sm = bs::fit_blocks_per_sm(bs::cta_chains(p), p.max_side, regs, p.profile);
-    const int grid = std::min(n_trial * (p.n_chains / bs::cta_chains(p)), sms * per_sm);
+    const int grid = std::min(n_trial * bs::cta_groups(p), sms * per_sm);
     cudaError_t e = cudaSuccess;
     for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
         e = cudaMemsetAsync(L.queue, 0, sizeof(unsigned int), st);
@@ -153,7 +153,7 @@ cudaError_t autotune(bs_fit_plan_s *pl, int sms)
         }
         L.p.regs = best_regs;
         L.p.cpc = best_cpc;
-        const int groups = L.p.n_chains / bs::cta_chains(L.p);
+        const int groups = bs::cta_groups(L.p);
         L.grid = std::min(L.p.n_work * groups,
                           sms * bs::fit_blocks_per_sm(bs::cta_chains(L.p), L.p.max_side, best_regs, L.p.profile));
     }
