@@ -782,7 +782,7 @@ def pixel_weights(t, seed):
 def pixel_arm(a, world, rank, local_rank):
     """The image sampling phase with per-pixel weights: every evaluation renders
     the model image and transforms the weighted residual back, the transforms on
-    the tensor cores (3xTF32 tcgen05.mma), one CTA of eight warps per chain."""
+    the tensor cores (3xTF32 tcgen05.mma), two chains per CTA of eight warps."""
     import torch
     from paper_2604_22048_gb300 import api, build, synth
     build.build()
@@ -842,7 +842,7 @@ def pixel_arm(a, world, rank, local_rank):
                          "peak_how": "dense TF32 = half the measured bf16 cuBLAS rate (sustained), the nominal "
                                      "ratio of the two formats",
                          "note": "the algorithmic flops of the four transforms only; the evaluation is bound by "
-                                 "the latency of its dependent steps (one CTA of eight warps per SM), not by the tensor pipe"},
+                                 "the latency of its dependent steps (one CTA per SM), not by the tensor pipe"},
             "gpu_launches": launches, "clocks": clk,
             "ess": ess_summary(ess, rhat, float(ess.mean(dim=1).sum().item()) / (step_ms / 1e3)),
             "status_counts": np.bincount(st, minlength=5).tolist(),

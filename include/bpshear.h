@@ -206,7 +206,7 @@ typedef struct {
                                      then renders the model image and transforms
                                      the weighted residual back (four dense
                                      DFT-matrix products on the tensor cores,
-                                     3xTF32, one CTA per chain).  Requires the
+                                     3xTF32, two chains per CTA).  Requires the
                                      exponential profile, one exposure, no
                                      noise_corr and max_side <= 63. */
     const float *pixel_prec;      /* NULL, or device float: a general pixel

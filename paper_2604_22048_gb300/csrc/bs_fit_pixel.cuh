@@ -9,7 +9,7 @@
 // Re[conj(R_k) dM_k / dtheta] / (sigma^2 N^2) with R = DFT(w (d - m)), so the half-plane
 // pass of eval_logpost gives it when its data spectrum is replaced by the effective
 // D' = M + R (scaled as the table).  The transforms run on the tensor cores (the layout
-// and operand split are described with PixTc); one CTA of eight warps evaluates one chain.
+// and operand split are described with PixTc); one CTA of eight warps evaluates two chains.
 
 // Per galaxy (all threads): the A operands of the four products for this side into
 // tensor memory (warp w writes lanes 32 (w mod 4) .. + 31, the high parts for w < 4 and
