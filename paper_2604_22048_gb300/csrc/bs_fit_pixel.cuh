@@ -339,7 +339,7 @@ __device__ double eval_pix(const FitParams &P, const GalCtx &gc, const SmemView 
     const uint32_t tl = *px.tmem + ((uint32_t)(32 * (warp & 3)) << 16);
     constexpr uint32_t aflo = tc::kColAFlo - tc::kColAF, a2lo = tc::kColA2lo - tc::kColA2;
     // (1) G = M E for both chains: rows (re, iy | im, iy), columns (chain, u)
-    if (!tc_run(px, TcGemm{tc::kColAF, 64u, aflo, bop, 16u * 144, 32u * 144, tc::idesc(128, 64, false), 2, ks}, 0))
+    if (!tc_run(px, TcGemm{tc::kColAF, 64u, aflo, bop, 16u * 144, 32u * 144, tc::idesc(128, 64), 2, ks}, 0))
         return pix_nan(g);
     // (1) -> operand of (2): row (chain, iy), K (re, u | im, u), G as it is (the weights
     // are in the constant); this thread's lane (p, iy), its chain's 32 columns
@@ -353,7 +353,7 @@ __device__ double eval_pix(const FitParams &P, const GalCtx &gc, const SmemView 
             tc::split_store4(bh, bl, e0 + m * kLb, v[4 * m], v[4 * m + 1], v[4 * m + 2], v[4 * m + 3]);
     }
     // (2) m = W G: rows ix, columns (chain, iy)
-    if (!tc_run(px, TcGemm{tc::kColA2, 32u, a2lo, bop, 8u * 144, 16u * 144, tc::idesc(128, 128, false), 2,
+    if (!tc_run(px, TcGemm{tc::kColA2, 32u, a2lo, bop, 8u * 144, 16u * 144, tc::idesc(128, 128), 2,
                            (H + 7) >> 3},
                 1))
         return pix_nan(g);
@@ -395,7 +395,7 @@ __device__ double eval_pix(const FitParams &P, const GalCtx &gc, const SmemView 
         if (lane == 0) px.chi[warp] = cw;
     }
     // (3) conj Q = [C; S] r: rows (re, a | im, a), columns (chain, iy)
-    if (!tc_run(px, TcGemm{tc::kColAF, 0u, aflo, bop, 0u, 16u * 144, tc::idesc(128, 128, false), 1, ks}, 0))
+    if (!tc_run(px, TcGemm{tc::kColAF, 0u, aflo, bop, 0u, 16u * 144, tc::idesc(128, 128), 1, ks}, 0))
         return pix_nan(g);
     // (3) -> operand of (4): row (chain, u = a - c < 32), K (re, iy | im, iy); this
     // thread's lane (q, a), its chain's 64 columns iy
@@ -414,7 +414,7 @@ __device__ double eval_pix(const FitParams &P, const GalCtx &gc, const SmemView 
         }
     }
     // (4) conj R = E conj Q: rows (re, vi | im, vi), columns (chain, u)
-    if (!tc_run(px, TcGemm{tc::kColAF, 64u, aflo, bop, 16u * 144, 32u * 144, tc::idesc(128, 64, false), 2, ks}, 1))
+    if (!tc_run(px, TcGemm{tc::kColAF, 64u, aflo, bop, 16u * 144, 32u * 144, tc::idesc(128, 64), 2, ks}, 1))
         return pix_nan(g);
     // D' = Mt + scale_u R in the chain's table D slots; this thread's lane (p, vi), its
     // chain's 32 columns u

@@ -48,7 +48,6 @@ namespace {
 
 namespace tc {
 
-constexpr int kNP = 64;                        // padded side of the transforms
 constexpr int kLboB = 144;                     // data operands: 16-byte pad per core matrix (column
                                                // stores of a warp fall in 32 distinct banks)
 constexpr int kBopFloats = 16 * 16 * (kLboB / 4);   // one data operand: 128 rows x 64 K or 64 x 128
@@ -73,11 +72,10 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t 
 }
 
 // Instruction descriptor of kind::tf32: FP32 accumulator, TF32 A and B, both
-// K-major, optional negation of A, shape M x N.
-__host__ __device__ constexpr uint32_t idesc(int m, int n, bool neg_a)
+// K-major, shape M x N.
+__host__ __device__ constexpr uint32_t idesc(int m, int n)
 {
-    return (1u << 4) | (2u << 7) | (2u << 10) | (neg_a ? (1u << 13) : 0u) | ((uint32_t)(n >> 3) << 17) |
-           ((uint32_t)(m >> 4) << 24);
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
 
 // Round a finite float to the nearest TF32 value, ties away from zero (the
@@ -149,21 +147,6 @@ __device__ __forceinline__ void ld32(uint32_t taddr, float (&v)[32])
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// 16 consecutive TMEM columns of this thread's lane.
-__device__ __forceinline__ void ld16(uint32_t taddr, float (&v)[16])
-{
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 // Four consecutive K-elements (one core-matrix row) as high and low TF32 parts.
