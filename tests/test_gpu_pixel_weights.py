@@ -121,3 +121,41 @@ def test_pixel_path_chains_do_not_depend_on_the_batch(cuda):
     b = alone["samples"].cpu().numpy()[:, 0]
     assert np.isfinite(a).all() and np.array_equal(a, b)
     assert np.array_equal(full["logp"].cpu().numpy()[1], alone["logp"].cpu().numpy()[0])
+
+
+@pytest.mark.parametrize("C", [1, 3])
+def test_pixel_path_odd_chain_counts(cuda, C):
+    """Two chains per CTA: with an odd count the last CTA of a galaxy runs one chain
+    while its second group of warps joins each evaluation with a skip flag; the
+    lone chain's draws are those it has in a batch of other galaxies."""
+    truth, ds, flat, offs, sides, w = _case(25, 2, 91)
+    t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(cuda)
+    cfg = api.FitConfig(n_chains=C, n_warmup=40, n_samples=30, n_leapfrog=8)
+    psf = api.psf_table("gaussian", 0.7, device=cuda)
+    init = np.repeat(ds.init[:, :1], C, axis=1).astype(np.float32)
+    init[..., 4:6] += np.random.default_rng(5).uniform(-0.1, 0.1, (2, C, 2)).astype(np.float32)
+    sig = ds.sigma.astype(np.float32)
+    both = api.fit_galaxies(t(flat), t(offs), t(sides), psf, t(sig), t(init), cfg, pixel_weight=t(w),
+                            gal_id=t(np.arange(2, dtype=np.int64)), want=("status", "accept_rate"))
+    one = slice(offs[1], offs[1] + 25 * 25)
+    alone = api.fit_galaxies(t(flat[one]), t(np.zeros(1, np.int64)), t(sides[1:2]), psf, t(sig[1:2]), t(init[1:2]),
+                             cfg, pixel_weight=t(w[one]), gal_id=t(np.array([1], np.int64)), want=("status",))
+    assert (both["status"].cpu().numpy() == 0).all() and (alone["status"].cpu().numpy() == 0).all()
+    s = both["samples"].cpu().numpy()
+    assert np.isfinite(s).all() and both["accept_rate"].cpu().numpy().mean() > 0.5
+    assert np.array_equal(s[:, 1], alone["samples"].cpu().numpy()[:, 0])
+
+
+def test_pixel_points_outside_the_support(cuda):
+    """A point outside the prior's support is -inf with NaN gradients, and does not
+    disturb the points after it in the same launch."""
+    truth, ds, flat, offs, sides, w = _case(25, 2, 93, mask=False)
+    pts = np.array([ds.theta[0], ds.theta[1], ds.theta[0]], np.float32)
+    pts[1, 2] = 1.2                       # |e| > 1
+    gal = np.array([0, 1, 0], np.int32)
+    t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(cuda)
+    lp, g = api.logpost_points(t(flat), t(offs), t(sides), api.psf_table("gaussian", 0.7, device=cuda),
+                               t(ds.sigma.astype(np.float32)), t(gal), t(pts), pixel_weight=t(w))
+    lp, g = lp.cpu().numpy(), g.cpu().numpy()
+    assert lp[1] == -np.inf and np.isnan(g[1]).all()
+    assert np.isfinite(lp[[0, 2]]).all() and lp[0] == lp[2] and np.array_equal(g[0], g[2])
