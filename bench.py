@@ -211,9 +211,9 @@ def flops_per_eval(N):
 # to that file the traffic is reported as null until the next capture.
 CAPTURED_TRAFFIC = {
     # one galaxy of the plain workload (53x53, 4 chains x (200 + 300) draws), from a one-pass
-    # capture of the full 10,000-galaxy launch: (134,292,480 + 293,008,896) B / 10,000
+    # capture of the full 10,000-galaxy launch: (133,924,096 + 293,116,928) B / 10,000
     "fit": ("paper_2604_22048_gb300/csrc/bs_fit_impl.cuh",
-            "2c3a5b881660fbf9d9cbb7f8375b91cb282ca41b67f10c6b2200fcf3fa3217de", 42730.1,
+            "d67b4aae68f05596651a0a1cc0e95e8fec139a1986a1617d11cb1ec3d16ac602", 42704.1,
             {"side": 53, "chains": 4, "n_warmup": 200, "n_samples": 300}),
     # one interim sample of the shear workload: (489,555,712 + 3,329,280) B / (200,000 x 300)
     "shear": ("paper_2604_22048_gb300/csrc/bs_shear.cu",
