@@ -662,29 +662,44 @@ __device__ __forceinline__ void warp_sum_n(float (&v)[NV])
     for (int j = 0; j < NV; ++j) v[j] = __shfl_sync(BS_FULL_MASK, r, 4 * j);
 }
 
-// Log posterior (if want_ll) and gradient at th, warp-cooperative.
-template <int NC, int PROF>
-__device__ __forceinline__ double eval_logpost(const FitParams &P, const GalCtx &gc,
-                                               const float *__restrict__ tab, const float2 *__restrict__ kxr,
-                                               float2 *__restrict__ xph, const float vcol[NC], const float th[6],
-                                               float g[6], bool want_ll)
+// The model's shape at th (Sec. 3.3 forward model): flux, r0^2 and the coefficients
+// of the sheared quadratic form r0^2 q(k) = al kx^2 + be ky^2 + ga kx ky.
+struct Shape {
+    float F, r02, e1, e2, E, Pq, al, be, ga;
+};
+template <int PROF>
+__device__ __forceinline__ Shape model_shape(const FitParams &P, const float th[6])
 {
-    const float F = exp10f(th[0]);
+    Shape m;
+    m.F = exp10f(th[0]);
     const float r0 = exp10f(th[1]) * (PROF == 0 ? 1.0f / kHlrOverR0 : P.inv_hlr_r0);
-    const float r02 = r0 * r0;
-    const float e1 = th[2], e2 = th[3];
-    const float E = e1 * e1 + e2 * e2;
-    const float Pq = 1.0f / (1.0f - E);
-    const float al = r02 * (1.0f + E + 2.0f * e1) * Pq;   // coefficient of kx^2 in r0^2 q
-    const float be = r02 * (1.0f + E - 2.0f * e1) * Pq;   // ky^2
-    const float ga = r02 * 4.0f * e2 * Pq;                // kx ky
-    const float F2 = F * F;
-    const float dk = gc.dk;
+    m.r02 = r0 * r0;
+    m.e1 = th[2];
+    m.e2 = th[3];
+    m.E = m.e1 * m.e1 + m.e2 * m.e2;
+    m.Pq = 1.0f / (1.0f - m.E);
+    m.al = m.r02 * (1.0f + m.E + 2.0f * m.e1) * m.Pq;   // coefficient of kx^2 in r0^2 q
+    m.be = m.r02 * (1.0f + m.E - 2.0f * m.e1) * m.Pq;   // ky^2
+    m.ga = m.r02 * 4.0f * m.e2 * m.Pq;                  // kx ky
+    return m;
+}
 
-    // this chain's phase table X(u) = exp(-2 pi i u dx / N), u < H
+// The half-plane pass over rows [u0, u1) (warp-cooperative; u0 even): the warp's
+// phase table X(u) = exp(-2 pi i u dx / N) for those rows, then the six sums of the
+// gradient, reduced over the warp into sums[] (identical in all lanes): sum w,
+// sum w kx^2, sum w ky^2, sum w kx ky, sum b kx, sum b ky; and, if LL, this lane's
+// compensated chi^2 parts.
+template <int NC, bool LL, int PROF>
+__device__ __forceinline__ void spectral_sums(const FitParams &P, const GalCtx &gc, const Shape &m,
+                                              const float *__restrict__ tab, const float2 *__restrict__ kxr,
+                                              float2 *__restrict__ xph, const float vcol[NC], const float th[6],
+                                              int u0, int u1, float (&sums)[6], float &chi_hi, float &chi_lo)
+{
+    const float F2 = m.F * m.F;
+    const float dk = gc.dk;
     {
         const int lane = threadIdx.x & 31;
-        for (int u = lane; u < gc.H; u += 32) {
+        for (int u = u0 + lane; u < u1; u += 32) {
             float sx, cx;
             sincospi_sfu(-2.0f * th[4] * (float)u * gc.invN, &sx, &cx);
             xph[u] = make_float2(cx, sx);
@@ -696,11 +711,11 @@ __device__ __forceinline__ double eval_logpost(const FitParams &P, const GalCtx 
     for (int j = 0; j < NC; ++j) {
         float s, co;
         sincospi_sfu(-2.0f * th[5] * vcol[j] * gc.invN, &s, &co);   // exp(-2 pi i v dy / N)
-        Yr[j] = F * co;
-        Yi[j] = F * s;
+        Yr[j] = m.F * co;
+        Yi[j] = m.F * s;
         ky[j] = vcol[j] * dk;
-        cst[j] = fmaf(be * ky[j], ky[j], 1.0f);
-        gky[j] = ga * ky[j];
+        cst[j] = fmaf(m.be * ky[j], ky[j], 1.0f);
+        gky[j] = m.ga * ky[j];
     }
     SlotConst<NC> K;
     Sums<NC> S;
@@ -729,10 +744,9 @@ __device__ __forceinline__ double eval_logpost(const FitParams &P, const GalCtx 
     S.sBc = 0.f;
     S.chi_hi = f2(0.f);
     S.chi_lo = f2(0.f);
-    if (want_ll)
-        half_plane<NC, true, PROF>(S, K, tab, kxr, xph, gc.H, al, F2, P.prof_npow);
-    else
-        half_plane<NC, false, PROF>(S, K, tab, kxr, xph, gc.H, al, F2, P.prof_npow);
+    if (u1 > u0)
+        half_plane<NC, LL, PROF>(S, K, tab + (size_t)u0 * row_floats(P.npad), kxr + u0, xph + u0, u1 - u0, m.al,
+                                 F2, P.prof_npow);
     __syncwarp();   // the table is rewritten by the next evaluation
 
     float Swkx2 = S.Swkx2.x + S.Swkx2.y, Sbkx = S.Sbkx.x + S.Sbkx.y;
@@ -755,14 +769,28 @@ __device__ __forceinline__ double eval_logpost(const FitParams &P, const GalCtx 
         Swkxky = fmaf(ky[j], wkx, Swkxky);
         Sbky = fmaf(ky[j], bc, Sbky);
     }
-    float sums[6] = {Sw, Swkx2, Swky2, Swkxky, Sbkx, Sbky};
+    sums[0] = Sw;
+    sums[1] = Swkx2;
+    sums[2] = Swky2;
+    sums[3] = Swkxky;
+    sums[4] = Sbkx;
+    sums[5] = Sbky;
     warp_sum_n(sums);
-    Sw = sums[0];
-    Swkx2 = sums[1];
-    Swky2 = sums[2];
-    Swkxky = sums[3];
-    Sbkx = sums[4];
-    Sbky = sums[5];
+    if (LL) {
+        // merge the two halves of the compensated pair
+        two_sum(S.chi_hi.x, S.chi_hi.y, chi_hi, chi_lo);
+        chi_lo += S.chi_lo.x + S.chi_lo.y;
+    }
+}
+
+// The gradient of the log posterior from the six sums of the half-plane pass (the
+// likelihood's part, over sigma^2) and the interim prior's part.
+template <int PROF>
+__device__ __forceinline__ void spectral_grad(const FitParams &P, const GalCtx &gc, const Shape &m,
+                                              const float (&sums)[6], const float th[6], float g[6])
+{
+    const float Sw = sums[0], Swkx2 = sums[1], Swky2 = sums[2], Swkxky = sums[3], Sbkx = sums[4], Sbky = sums[5];
+    const float al = m.al, be = m.be, ga = m.ga, r02 = m.r02, e1 = m.e1, e2 = m.e2, E = m.E, Pq = m.Pq;
     // sum of w (s - 1) = al sum w kx^2 + be sum w ky^2 + ga sum w kx ky.  With
     // psi = 1/s (exponential, Spergel) a = w s, so sum a = sum w + that; with
     // psi = 1 (Gaussian) a = w.  The sum of a is therefore not accumulated.
@@ -793,15 +821,30 @@ __device__ __forceinline__ double eval_logpost(const FitParams &P, const GalCtx 
     }
     g[4] = gc.p * Sbkx * ib - th[4] * P.inv_sxy2;
     g[5] = gc.p * Sbky * ib - th[5] * P.inv_sxy2;
+}
+
+// Log posterior (if want_ll) and gradient at th, warp-cooperative.
+template <int NC, int PROF>
+__device__ __forceinline__ double eval_logpost(const FitParams &P, const GalCtx &gc,
+                                               const float *__restrict__ tab, const float2 *__restrict__ kxr,
+                                               float2 *__restrict__ xph, const float vcol[NC], const float th[6],
+                                               float g[6], bool want_ll)
+{
+    const Shape m = model_shape<PROF>(P, th);
+    float sums[6];
+    float chi_hi = 0.f, chi_lo = 0.f;
+    if (want_ll)
+        spectral_sums<NC, true, PROF>(P, gc, m, tab, kxr, xph, vcol, th, 0, gc.H, sums, chi_hi, chi_lo);
+    else
+        spectral_sums<NC, false, PROF>(P, gc, m, tab, kxr, xph, vcol, th, 0, gc.H, sums, chi_hi, chi_lo);
+    spectral_grad<PROF>(P, gc, m, sums, th, g);
     if (!want_ll) return 0.0;
-    // merge the two halves of the compensated pair, then the warp
-    float chi_hi, chi_lo;
-    two_sum(S.chi_hi.x, S.chi_hi.y, chi_hi, chi_lo);
-    chi_lo += S.chi_lo.x + S.chi_lo.y;
+    // then the warp
     const double chi2 = warp_sum_comp(chi_hi, chi_lo);
+    const float E = m.E;
     const float lprior = P.prior_const - 0.5f * (th[4] * th[4] + th[5] * th[5]) * P.inv_sxy2 +
                          2.0f * log1pf(-E) - 0.5f * E * P.inv_se2;
-    return -0.5 * (chi2 + s_chi2_off) * (double)ib + (double)lprior;
+    return -0.5 * (chi2 + s_chi2_off) * (double)gc.inv_b + (double)lprior;
 }
 
 #include "bs_fit_pixel.cuh"

@@ -133,8 +133,8 @@ __device__ __forceinline__ double pix_nan(float g[6])
 // its effective spectrum, with the rows split over the group's four warps: warp j of
 // the group sums the terms of its rows u in [r j, r (j + 1)), r even (the pass reads
 // rows in pairs); the four warp sums meet in shared memory, where every thread of the
-// group adds them in warp order and forms the gradient.  The per-point terms, the sums
-// and the gradient formulas are those of eval_logpost (exponential profile, no chi^2).
+// group adds them in warp order and forms the gradient (the sums and the gradient of
+// eval_logpost, exponential profile, no chi^2).
 template <int NC>
 __device__ void pix_grad(const FitParams &P, const GalCtx &gc, const float *tab, const float2 *kxr, const PixTc &px,
                          float2 *xph, const float vcol[NC], const float th[6], float g[6])
@@ -143,86 +143,9 @@ __device__ void pix_grad(const FitParams &P, const GalCtx &gc, const float *tab,
     const int grp = warp >> 2, wj = warp & 3;
     const int per = 2 * ((gc.H + 7) >> 3);
     const int u0 = min(gc.H, wj * per), u1 = min(gc.H, u0 + per);
-    const float F = exp10f(th[0]);
-    const float r0 = exp10f(th[1]) * (1.0f / kHlrOverR0);
-    const float r02 = r0 * r0;
-    const float e1 = th[2], e2 = th[3];
-    const float E = e1 * e1 + e2 * e2;
-    const float Pq = 1.0f / (1.0f - E);
-    const float al = r02 * (1.0f + E + 2.0f * e1) * Pq;
-    const float be = r02 * (1.0f + E - 2.0f * e1) * Pq;
-    const float ga = r02 * 4.0f * e2 * Pq;
-    const float F2 = F * F;
-    const float dk = gc.dk;
-    for (int u = u0 + lane; u < u1; u += 32) {
-        float sx, cx;
-        sincospi_sfu(-2.0f * th[4] * (float)u * gc.invN, &sx, &cx);
-        xph[u] = make_float2(cx, sx);
-    }
-    __syncwarp();
-    float Yr[NC], Yi[NC], cst[NC], gky[NC], ky[NC];
-#pragma unroll
-    for (int j = 0; j < NC; ++j) {
-        float sn, co;
-        sincospi_sfu(-2.0f * th[5] * vcol[j] * gc.invN, &sn, &co);
-        Yr[j] = F * co;
-        Yi[j] = F * sn;
-        ky[j] = vcol[j] * dk;
-        cst[j] = fmaf(be * ky[j], ky[j], 1.0f);
-        gky[j] = ga * ky[j];
-    }
-    SlotConst<NC> K;
-    Sums<NC> S;
-    constexpr int NPAIR = NC / 2;
-#pragma unroll
-    for (int p = 0; p < NPAIR; ++p) {
-        K.Yr[p] = make_float2(Yr[2 * p], Yr[2 * p + 1]);
-        K.Yi[p] = make_float2(Yi[2 * p], Yi[2 * p + 1]);
-        K.nYi[p] = make_float2(-Yi[2 * p], -Yi[2 * p + 1]);
-        K.cst[p] = make_float2(cst[2 * p], cst[2 * p + 1]);
-        K.gky[p] = make_float2(gky[2 * p], gky[2 * p + 1]);
-        S.Wc[p] = f2(0.f);
-        S.Wkx[p] = f2(0.f);
-        S.Bc[p] = f2(0.f);
-    }
-    if (NC & 1) {
-        K.sYr = Yr[NC - 1];
-        K.sYi = Yi[NC - 1];
-        K.scst = cst[NC - 1];
-        K.sgky = gky[NC - 1];
-    }
-    S.Swkx2 = f2(0.f);
-    S.Sbkx = f2(0.f);
-    S.sWc = 0.f;
-    S.sWkx = 0.f;
-    S.sBc = 0.f;
-    S.chi_hi = f2(0.f);
-    S.chi_lo = f2(0.f);
-    if (u1 > u0)
-        half_plane<NC, false, 0>(S, K, tab + (size_t)u0 * row_floats(P.npad), kxr + u0, xph + u0,
-                                 u1 - u0, al, F2, P.prof_npow);
-    float Swkx2 = S.Swkx2.x + S.Swkx2.y, Sbkx = S.Sbkx.x + S.Sbkx.y;
-    float Sw = 0.f, Swky2 = 0.f, Swkxky = 0.f, Sbky = 0.f;
-#pragma unroll
-    for (int j = 0; j < NC; ++j) {
-        float wc, wkx, bc;
-        if (j < 2 * NPAIR) {
-            const int p = j >> 1;
-            wc = (j & 1) ? S.Wc[p].y : S.Wc[p].x;
-            wkx = (j & 1) ? S.Wkx[p].y : S.Wkx[p].x;
-            bc = (j & 1) ? S.Bc[p].y : S.Bc[p].x;
-        } else {
-            wc = S.sWc;
-            wkx = S.sWkx;
-            bc = S.sBc;
-        }
-        Sw += wc;
-        Swky2 = fmaf(ky[j] * ky[j], wc, Swky2);
-        Swkxky = fmaf(ky[j], wkx, Swkxky);
-        Sbky = fmaf(ky[j], bc, Sbky);
-    }
-    float sums[6] = {Sw, Swkx2, Swky2, Swkxky, Sbkx, Sbky};
-    warp_sum_n(sums);
+    const Shape m = model_shape<0>(P, th);
+    float sums[6], chi_hi = 0.f, chi_lo = 0.f;
+    spectral_sums<NC, false, 0>(P, gc, m, tab, kxr, xph, vcol, th, u0, u1, sums, chi_hi, chi_lo);
     float *gs = px.gsum + grp * 24;
     if (lane == 0) {
 #pragma unroll
@@ -231,28 +154,7 @@ __device__ void pix_grad(const FitParams &P, const GalCtx &gc, const float *tab,
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < 6; ++k) sums[k] = ((gs[k] + gs[6 + k]) + gs[12 + k]) + gs[18 + k];
-    Sw = sums[0];
-    Swkx2 = sums[1];
-    Swky2 = sums[2];
-    Swkxky = sums[3];
-    Sbkx = sums[4];
-    Sbky = sums[5];
-    const float st = al * Swkx2 + be * Swky2 + ga * Swkxky;
-    const float Sa = Sw + st;
-    const float ib = gc.inv_b;
-    const float P2 = Pq * Pq;
-    const float da1 = r02 * ((2.0f * e1 + 2.0f) * Pq + (1.0f + E + 2.0f * e1) * 2.0f * e1 * P2);
-    const float da2 = r02 * (2.0f * e2 * Pq + (1.0f + E + 2.0f * e1) * 2.0f * e2 * P2);
-    const float db1 = r02 * ((2.0f * e1 - 2.0f) * Pq + (1.0f + E - 2.0f * e1) * 2.0f * e1 * P2);
-    const float db2 = r02 * (2.0f * e2 * Pq + (1.0f + E - 2.0f * e1) * 2.0f * e2 * P2);
-    const float dg1 = r02 * 8.0f * e1 * e2 * P2;
-    const float dg2 = r02 * (4.0f * Pq + 8.0f * e2 * e2 * P2);
-    g[0] = kLn10 * Sa * ib;
-    g[1] = -3.0f * kLn10 * st * ib;
-    g[2] = -1.5f * (da1 * Swkx2 + db1 * Swky2 + dg1 * Swkxky) * ib - 4.0f * e1 * Pq - e1 * P.inv_se2;
-    g[3] = -1.5f * (da2 * Swkx2 + db2 * Swky2 + dg2 * Swkxky) * ib - 4.0f * e2 * Pq - e2 * P.inv_se2;
-    g[4] = gc.p * Sbkx * ib - th[4] * P.inv_sxy2;
-    g[5] = gc.p * Sbky * ib - th[5] * P.inv_sxy2;
+    spectral_grad<0>(P, gc, m, sums, th, g);
 }
 
 // One evaluation of both chains of the CTA (all threads; each group passes its own
