@@ -159,3 +159,40 @@ def test_pixel_points_outside_the_support(cuda):
     lp, g = lp.cpu().numpy(), g.cpu().numpy()
     assert lp[1] == -np.inf and np.isnan(g[1]).all()
     assert np.isfinite(lp[[0, 2]]).all() and lp[0] == lp[2] and np.array_equal(g[0], g[2])
+
+
+def test_pixel_path_mixed_sides_in_one_launch(cuda):
+    """Stamps of 25, 41 and 63 px in one launch (the transforms' constants are
+    rebuilt for each galaxy's side, the tables sized for the largest): each galaxy's
+    chains are those it has when fitted alone with the same launch shape."""
+    parts = [_case(s, 1, 100 + s, mask=False) for s in (25, 41, 63)]
+    flats, ws, offs, sides, sig, init = [], [], [], [], [], []
+    pos = 0
+    for truth, ds, flat, off, side, w in parts:
+        n = int(side[0]) ** 2
+        size = (n + 3) // 4 * 4
+        flats.append(np.pad(flat[:n], (0, size - n)))
+        ws.append(np.pad(w[:n], (0, size - n)))
+        offs.append(pos)
+        pos += size
+        sides.append(int(side[0]))
+        sig.append(ds.sigma[0])
+        init.append(np.repeat(ds.init[0:1, :1], 2, axis=1))
+    flat, w = np.concatenate(flats), np.concatenate(ws)
+    offs, sides = np.array(offs, np.int64), np.array(sides, np.int32)
+    sig, init = np.array(sig, np.float32), np.concatenate(init).astype(np.float32)
+    init[:, 1, 4:6] += 0.05
+    t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(cuda)
+    cfg = api.FitConfig(n_chains=2, n_warmup=40, n_samples=30, n_leapfrog=8)
+    psf = api.psf_table("gaussian", 0.7, device=cuda)
+    allr = api.fit_galaxies(t(flat), t(offs), t(sides), psf, t(sig), t(init), cfg, pixel_weight=t(w), max_side=63,
+                            gal_id=t(np.arange(3, dtype=np.int64)), want=("status",))
+    s_all = allr["samples"].cpu().numpy()
+    assert (allr["status"].cpu().numpy() == 0).all() and np.isfinite(s_all).all()
+    for i in range(3):
+        n = int(sides[i]) ** 2
+        sl = slice(int(offs[i]), int(offs[i]) + n)
+        one = api.fit_galaxies(t(flat[sl]), t(np.zeros(1, np.int64)), t(sides[i:i + 1]), psf, t(sig[i:i + 1]),
+                               t(init[i:i + 1]), cfg, pixel_weight=t(w[sl]), max_side=63,
+                               gal_id=t(np.array([i], np.int64)), want=("status",))
+        assert np.array_equal(s_all[:, i], one["samples"].cpu().numpy()[:, 0]), sides[i]
