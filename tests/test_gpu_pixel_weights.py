@@ -30,7 +30,7 @@ def _case(side, n, seed, mask=True):
     return truth, ds, flat, offs, sides, w
 
 
-@pytest.mark.parametrize("side", [25, 41, 63])
+@pytest.mark.parametrize("side", [3, 9, 25, 41, 63])
 def test_pixel_weighted_logpost_matches_oracle(cuda, side):
     truth, ds, flat, offs, sides, w = _case(side, 3, 50 + side)
     rng = np.random.default_rng(side)
