@@ -23,8 +23,9 @@
 // per point, three of them per column and weighted by ky once at the end)
 // and reduced with an xor butterfly (identical bits in all lanes, so
 // warp-uniform decisions stay uniform), and the seventh follows from them;
-// chi^2 is accumulated with compensated FP32 per lane and finished in FP64
-// at the warp total.
+// chi^2 (only on the last step of a trajectory) is accumulated per lane in
+// FP32 as F^2 |Dt - Mt|^2 from the terms the gradient already forms (positive
+// terms, each accumulator ~14 rows long) and finished in FP64 at the warp total.
 //
 // Chain state.  Lane i < 6 owns parameter i of the chain (position hi/lo,
 // momentum, gradient, inverse metric, Welford moments) as scalars; the six
@@ -72,8 +73,8 @@ __host__ __device__ __forceinline__ int row_floats(int npad) { return 3 * npad; 
 // Per-chain phase tables X(u) = exp(-2 pi i u dx / N) of one evaluation, in
 // the setup scratch (free once the galaxy is staged), extended when the
 // chains need more than it holds.
-// Per-chain stride of the phase tables: even, so that every table (read as
-// pairs X(u), X(u+1) with 16-byte loads, u even) starts 16-byte aligned.
+// Entry u of a table is (Re X(u), Im X(u), -Im X(u), 0), one 16-byte load.
+// Per-chain stride of the phase tables, in entries (even).
 __host__ __device__ __forceinline__ int phase_stride(int h_max) { return (h_max + 1) & ~1; }
 
 // float2 slots of the scratch: the setup's three rows, or the chains' phase
@@ -82,7 +83,7 @@ __host__ __device__ __forceinline__ int phase_stride(int h_max) { return (h_max 
 __host__ __device__ __forceinline__ int scratch_float2(int max_side, int h_max, int n_chains)
 {
     const int setup = 3 * max_side + 4;
-    const int phase = n_chains * phase_stride(h_max);
+    const int phase = 2 * n_chains * phase_stride(h_max);
     const int n = setup > phase ? setup : phase;
     return (n + 1) & ~1;
 }
@@ -92,7 +93,7 @@ struct SmemView {
     float2 *G;     // [max_side], setup scratch (one frequency row)
     float2 *tw;    // [max_side]
     float2 *Gc;    // [max_side], setup scratch (a row of the noise correlation's transform)
-    float2 *xph;   // [n_chains][phase_stride(h_max)] phase tables (aliases G, tw after setup)
+    float4 *xph;   // [n_chains][phase_stride(h_max)] phase tables (aliases G, tw after setup)
     float2 *kxr;   // [h_max]: (kx, kx^2) of row u
 };
 
@@ -103,7 +104,7 @@ __device__ __forceinline__ SmemView smem_view(unsigned char *base, int h_max, in
     v.G = reinterpret_cast<float2 *>(v.tab + (size_t)h_max * row_floats(npad));
     v.tw = v.G + (size_t)max_side;
     v.Gc = v.tw + (size_t)max_side;
-    v.xph = v.G;
+    v.xph = reinterpret_cast<float4 *>(v.G);
     v.kxr = v.G + (size_t)scratch_float2(max_side, h_max, n_chains);
     return v;
 }
@@ -470,14 +471,14 @@ struct Sums {
     float2 Swkx2, Sbkx;                     // sum w kx^2, sum b kx (both halves)
     float2 Wc[NP], Wkx[NP], Bc[NP];         // per slot: sum w, sum w kx, sum b
     float sWc, sWkx, sBc;                   // odd slot
-    float2 chi_hi, chi_lo;                  // compensated sum |Dt - Mt|^2
+    float2 chi0, chi1;                      // F^2 sum |Dt - Mt|^2, even and odd rows
 };
 
 // Per-lane, per-slot constants of one evaluation.
 template <int NCT>
 struct SlotConst {
     static constexpr int NP = NCT / 2 > 0 ? NCT / 2 : 1;
-    float2 Yr[NP], Yi[NP], nYi[NP], cst[NP], gky[NP];   // F exp(-i ky p dy) (and -Im), 1 + be ky^2, ga ky
+    float2 Yr[NP], Yi[NP], nYr[NP], cst[NP], gky[NP];   // F exp(-i ky p dy) (and -Re), 1 + be ky^2, ga ky
     float sYr, sYi, scst, sgky;
 };
 
@@ -525,14 +526,22 @@ __device__ __forceinline__ void profile_amp1(float s, float npow, float &f, floa
     psi = pp.x;
 }
 
+// The phase of the model at (u, v) is P = X(u) Y(v) with X(u) = exp(-2 pi i u dx / N)
+// (row, in the warp's phase table as (Re, Im, -Im)) and Y(v) = F exp(-2 pi i v dy / N)
+// (column, in registers).  The point needs z = conj(D) P = (conj(D) Y) X: the column
+// factor first, whose negated real part is a register, then the row factor, whose
+// negated imaginary part the table holds, so that both complex products are two
+// multiplies and two multiply-adds.  With c = Re z - A F^2 (the real part of
+// conj(D - M) P, M = A P), the residual is |D - M|^2 = (c^2 + (Im z)^2) / F^2, since
+// |P| = F; the log-likelihood pass accumulates c^2 + (Im z)^2 and scales once.
 template <int NCT, bool LL, int PROF>
-__device__ __forceinline__ void row_terms(Sums<NCT> &S, const SlotConst<NCT> &K,
+__device__ __forceinline__ void row_terms(Sums<NCT> &S, float2 &chi, const SlotConst<NCT> &K,
                                           const float *__restrict__ row, float kx, float kx2, float al,
-                                          float Xr, float Xi, float F2, float npow)
+                                          float4 X, float F2, float npow)
 {
     constexpr int NPAIR = NCT / 2;
     const int lane = threadIdx.x & 31;
-    const float2 kxv = f2(kx), kx2v = f2(kx2), alv = f2(al), Xrv = f2(Xr), Xiv = f2(Xi);
+    const float2 kxv = f2(kx), kx2v = f2(kx2), alv = f2(al), Xrv = f2(X.x), Xiv = f2(X.y), nXiv = f2(X.z);
     const float2 nF2v = f2(-F2);
 #pragma unroll
     for (int p = 0; p < NPAIR; ++p) {
@@ -551,11 +560,12 @@ __device__ __forceinline__ void row_terms(Sums<NCT> &S, const SlotConst<NCT> &K,
             profile_amp<PROF>(s, npow, fa, rs2);
             A = mul2(T, fa);
         }
-        const float2 Pr = fma2(Xiv, K.nYi[p], mul2(Xrv, K.Yr[p]));      // F exp(-i k.delta)
-        const float2 Pi = fma2(Xiv, K.Yr[p], mul2(Xrv, K.Yi[p]));
-        const float2 zr = fma2(Dx, Pr, mul2(Dy, Pi));                  // conj(D) * phase
-        const float2 zi = sub2(mul2(Dx, Pi), mul2(Dy, Pr));
-        const float2 a = mul2(A, fma2(A, nF2v, zr));                    // Re conj(D - M) M
+        const float2 Er = fma2(Dx, K.Yr[p], mul2(Dy, K.Yi[p]));         // conj(D) Y
+        const float2 Ei = fma2(Dx, K.Yi[p], mul2(Dy, K.nYr[p]));
+        const float2 zr = fma2(Er, Xrv, mul2(Ei, nXiv));                 // z = conj(D) Y X
+        const float2 zi = fma2(Er, Xiv, mul2(Ei, Xrv));
+        const float2 c = fma2(A, nF2v, zr);                             // Re conj(D - M) P
+        const float2 a = mul2(A, c);                                    // Re conj(D - M) M
         const float2 bb = mul2(A, zi);                                  // Im conj(D - M) M
         const float2 w = mul2(a, rs2);                                  // a / s
         S.Wc[p] = add2(S.Wc[p], w);
@@ -563,11 +573,7 @@ __device__ __forceinline__ void row_terms(Sums<NCT> &S, const SlotConst<NCT> &K,
         S.Swkx2 = fma2(w, kx2v, S.Swkx2);
         S.Bc[p] = add2(S.Bc[p], bb);
         S.Sbkx = fma2(bb, kxv, S.Sbkx);
-        if (LL) {
-            const float2 Rr = sub2(Dx, mul2(A, Pr));
-            const float2 Ri = sub2(Dy, mul2(A, Pi));
-            comp_add2(S.chi_hi, S.chi_lo, fma2(Rr, Rr, mul2(Ri, Ri)));
-        }
+        if (LL) chi = fma2(c, c, fma2(zi, zi, chi));
     }
     if (NCT & 1) {
         const float *b = row + NPAIR * 192;
@@ -584,11 +590,12 @@ __device__ __forceinline__ void row_terms(Sums<NCT> &S, const SlotConst<NCT> &K,
             profile_amp1<PROF>(s, npow, fa, rs2);
             A = T * fa;
         }
-        const float Pr = Xr * K.sYr - Xi * K.sYi;
-        const float Pi = Xr * K.sYi + Xi * K.sYr;
-        const float zr = fmaf(D.x, Pr, D.y * Pi);
-        const float zi = fmaf(D.x, Pi, -D.y * Pr);
-        const float a = A * fmaf(-A, F2, zr);
+        const float Er = fmaf(D.x, K.sYr, D.y * K.sYi);
+        const float Ei = fmaf(D.x, K.sYi, -(D.y * K.sYr));
+        const float zr = fmaf(Er, X.x, Ei * X.z);
+        const float zi = fmaf(Er, X.y, Ei * X.x);
+        const float c = fmaf(A, -F2, zr);
+        const float a = A * c;
         const float bb = A * zi;
         const float w = a * rs2;
         S.sWc += w;
@@ -596,35 +603,29 @@ __device__ __forceinline__ void row_terms(Sums<NCT> &S, const SlotConst<NCT> &K,
         S.Swkx2.x = fmaf(w, kx2, S.Swkx2.x);
         S.sBc += bb;
         S.Sbkx.x = fmaf(bb, kx, S.Sbkx.x);
-        if (LL) {
-            const float Rr = fmaf(-A, Pr, D.x);
-            const float Ri = fmaf(-A, Pi, D.y);
-            comp_add(S.chi_hi.x, S.chi_lo.x, fmaf(Rr, Rr, Ri * Ri));
-        }
+        if (LL) chi.x = fmaf(c, c, fmaf(zi, zi, chi.x));
     }
 }
 
-// Half-plane pass, two rows per iteration (the row phase advances by
-// exp(-2 pi i dx / N) per row).
+// Half-plane pass, two rows per iteration; each row reads its (kx, kx^2) from the
+// galaxy's row table and X(u) from the warp's phase table.
 template <int NCT, bool LL, int PROF>
 __device__ __forceinline__ void half_plane(Sums<NCT> &S, const SlotConst<NCT> &K,
                                            const float *__restrict__ tab, const float2 *__restrict__ kxr,
-                                           const float2 *__restrict__ xph, int H, float al, float F2, float npow)
+                                           const float4 *__restrict__ xph, int H, float al, float F2, float npow)
 {
     constexpr int ROWF = 96 * NCT;
     const float *row = tab;
     int u = 0;
     for (; u + 1 < H; u += 2) {
         const float4 k01 = *reinterpret_cast<const float4 *>(kxr + u);   // (kx, kx^2) of rows u, u+1
-        const float4 x01 = *reinterpret_cast<const float4 *>(xph + u);   // X(u), X(u+1)
-        row_terms<NCT, LL, PROF>(S, K, row, k01.x, k01.y, al, x01.x, x01.y, F2, npow);
-        row_terms<NCT, LL, PROF>(S, K, row + ROWF, k01.z, k01.w, al, x01.z, x01.w, F2, npow);
+        row_terms<NCT, LL, PROF>(S, S.chi0, K, row, k01.x, k01.y, al, xph[u], F2, npow);
+        row_terms<NCT, LL, PROF>(S, S.chi1, K, row + ROWF, k01.z, k01.w, al, xph[u + 1], F2, npow);
         row += 2 * ROWF;
     }
     if (u < H) {
         const float2 k0 = kxr[u];
-        const float2 x0 = xph[u];
-        row_terms<NCT, LL, PROF>(S, K, row, k0.x, k0.y, al, x0.x, x0.y, F2, npow);
+        row_terms<NCT, LL, PROF>(S, S.chi0, K, row, k0.x, k0.y, al, xph[u], F2, npow);
     }
 }
 
@@ -688,11 +689,11 @@ __device__ __forceinline__ Shape model_shape(const FitParams &P, const float th[
 // phase table X(u) = exp(-2 pi i u dx / N) for those rows, then the six sums of the
 // gradient, reduced over the warp into sums[] (identical in all lanes): sum w,
 // sum w kx^2, sum w ky^2, sum w kx ky, sum b kx, sum b ky; and, if LL, this lane's
-// compensated chi^2 parts.
+// part of F^2 chi^2 as a compensated pair (hi, lo).
 template <int NC, bool LL, int PROF>
 __device__ __forceinline__ void spectral_sums(const FitParams &P, const GalCtx &gc, const Shape &m,
                                               const float *__restrict__ tab, const float2 *__restrict__ kxr,
-                                              float2 *__restrict__ xph, const float vcol[NC], const float th[6],
+                                              float4 *__restrict__ xph, const float vcol[NC], const float th[6],
                                               int u0, int u1, float (&sums)[6], float &chi_hi, float &chi_lo)
 {
     const float F2 = m.F * m.F;
@@ -702,7 +703,7 @@ __device__ __forceinline__ void spectral_sums(const FitParams &P, const GalCtx &
         for (int u = u0 + lane; u < u1; u += 32) {
             float sx, cx;
             sincospi_sfu(-2.0f * th[4] * (float)u * gc.invN, &sx, &cx);
-            xph[u] = make_float2(cx, sx);
+            xph[u] = make_float4(cx, sx, -sx, 0.0f);
         }
         __syncwarp();
     }
@@ -724,7 +725,7 @@ __device__ __forceinline__ void spectral_sums(const FitParams &P, const GalCtx &
     for (int p = 0; p < NPAIR; ++p) {
         K.Yr[p] = make_float2(Yr[2 * p], Yr[2 * p + 1]);
         K.Yi[p] = make_float2(Yi[2 * p], Yi[2 * p + 1]);
-        K.nYi[p] = make_float2(-Yi[2 * p], -Yi[2 * p + 1]);
+        K.nYr[p] = make_float2(-Yr[2 * p], -Yr[2 * p + 1]);
         K.cst[p] = make_float2(cst[2 * p], cst[2 * p + 1]);
         K.gky[p] = make_float2(gky[2 * p], gky[2 * p + 1]);
         S.Wc[p] = f2(0.f);
@@ -742,8 +743,8 @@ __device__ __forceinline__ void spectral_sums(const FitParams &P, const GalCtx &
     S.sWc = 0.f;
     S.sWkx = 0.f;
     S.sBc = 0.f;
-    S.chi_hi = f2(0.f);
-    S.chi_lo = f2(0.f);
+    S.chi0 = f2(0.f);
+    S.chi1 = f2(0.f);
     if (u1 > u0)
         half_plane<NC, LL, PROF>(S, K, tab + (size_t)u0 * row_floats(P.npad), kxr + u0, xph + u0, u1 - u0, m.al,
                                  F2, P.prof_npow);
@@ -777,9 +778,9 @@ __device__ __forceinline__ void spectral_sums(const FitParams &P, const GalCtx &
     sums[5] = Sbky;
     warp_sum_n(sums);
     if (LL) {
-        // merge the two halves of the compensated pair
-        two_sum(S.chi_hi.x, S.chi_hi.y, chi_hi, chi_lo);
-        chi_lo += S.chi_lo.x + S.chi_lo.y;
+        // the lane's residual sums (positive terms, each at most ~14 rows long)
+        const float2 t = add2(S.chi0, S.chi1);
+        two_sum(t.x, t.y, chi_hi, chi_lo);
     }
 }
 
@@ -827,7 +828,7 @@ __device__ __forceinline__ void spectral_grad(const FitParams &P, const GalCtx &
 template <int NC, int PROF>
 __device__ __forceinline__ double eval_logpost(const FitParams &P, const GalCtx &gc,
                                                const float *__restrict__ tab, const float2 *__restrict__ kxr,
-                                               float2 *__restrict__ xph, const float vcol[NC], const float th[6],
+                                               float4 *__restrict__ xph, const float vcol[NC], const float th[6],
                                                float g[6], bool want_ll)
 {
     const Shape m = model_shape<PROF>(P, th);
@@ -840,7 +841,7 @@ __device__ __forceinline__ double eval_logpost(const FitParams &P, const GalCtx 
     spectral_grad<PROF>(P, gc, m, sums, th, g);
     if (!want_ll) return 0.0;
     // then the warp
-    const double chi2 = warp_sum_comp(chi_hi, chi_lo);
+    const double chi2 = warp_sum_comp(chi_hi, chi_lo) / ((double)m.F * (double)m.F);
     const float E = m.E;
     const float lprior = P.prior_const - 0.5f * (th[4] * th[4] + th[5] * th[5]) * P.inv_sxy2 +
                          2.0f * log1pf(-E) - 0.5f * E * P.inv_se2;
@@ -880,7 +881,7 @@ __device__ __forceinline__ bool trajectory(const FitParams &P, const GalCtx &gc,
     float vcol[NC];
 #pragma unroll
     for (int j = 0; j < NC; ++j) vcol[j] = (float)(lane + 32 * j - gc.c);
-    float2 *xph_c = sm.xph + (size_t)slot * phase_stride(P.h_max);   // this warp's phase table
+    float4 *xph_c = sm.xph + (size_t)slot * phase_stride(P.h_max);   // this warp's phase table
     for (int l = 0; l < nst; ++l) {
         const float he = 0.5f * eps_use;
         pm = fmaf(he, gp, pm);
@@ -1188,7 +1189,7 @@ __device__ __forceinline__ void fit_loop(const FitParams &P)
             float vcol[NC];
 #pragma unroll
             for (int j = 0; j < NC; ++j) vcol[j] = (float)((threadIdx.x & 31) + 32 * j - gc.c);
-            float2 *xph = sm.xph + (size_t)grp * phase_stride(P.h_max);
+            float4 *xph = sm.xph + (size_t)grp * phase_stride(P.h_max);
             if (chain < P.n_chains) run_chain<NC, PROF>(P, gc, sm, gal, chain, grp);
             pix_drain<NC>(P, gc, sm, gal, xph, vcol);
             __syncthreads();
@@ -1310,7 +1311,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1) logpost_points_pix_kernel(con
         float vcol[NC];
 #pragma unroll
         for (int j = 0; j < NC; ++j) vcol[j] = (float)(lane + 32 * j - gc.c);
-        float2 *xph = sm.xph + (size_t)grp * phase_stride(P.h_max);
+        float4 *xph = sm.xph + (size_t)grp * phase_stride(P.h_max);
         if (grp == 0) {
             const float *th = theta + (size_t)i * 6;
             float t[6], g[6];

@@ -137,7 +137,7 @@ __device__ __forceinline__ double pix_nan(float g[6])
 // eval_logpost, exponential profile, no chi^2).
 template <int NC>
 __device__ void pix_grad(const FitParams &P, const GalCtx &gc, const float *tab, const float2 *kxr, const PixTc &px,
-                         float2 *xph, const float vcol[NC], const float th[6], float g[6])
+                         float4 *xph, const float vcol[NC], const float th[6], float g[6])
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int grp = warp >> 2, wj = warp & 3;
@@ -163,7 +163,7 @@ __device__ void pix_grad(const FitParams &P, const GalCtx &gc, const float *tab,
 // flag), else 0; *all_done is set when both groups have raised their done flags (the
 // evaluation then does nothing).
 template <int NC>
-__device__ double eval_pix(const FitParams &P, const GalCtx &gc, const SmemView &sm, int gal, float2 *xph,
+__device__ double eval_pix(const FitParams &P, const GalCtx &gc, const SmemView &sm, int gal, float4 *xph,
                            const float vcol[NC], const float th[6], float g[6], bool want_ll, bool *all_done)
 {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -352,7 +352,7 @@ __device__ double eval_pix(const FitParams &P, const GalCtx &gc, const SmemView 
 // A group whose chain has no further evaluations (all threads of the group): raise
 // its done flag, then join the other group's evaluations until both are done.
 template <int NC>
-__device__ void pix_drain(const FitParams &P, const GalCtx &gc, const SmemView &sm, int gal, float2 *xph,
+__device__ void pix_drain(const FitParams &P, const GalCtx &gc, const SmemView &sm, int gal, float4 *xph,
                           const float vcol[NC])
 {
     const PixTc px = pix_tc_view(sm.kxr, P.h_max, P.npad, P.max_side);
@@ -433,7 +433,7 @@ __device__ void dense_setup(const FitParams &P, const GalCtx &gc, const SmemView
 
 template <int NC>
 __device__ double eval_dense(const FitParams &P, const GalCtx &gc, const DenseView &pv, int gal,
-                           const float2 *__restrict__ kxr, float2 *__restrict__ xph, const float vcol[NC],
+                           const float2 *__restrict__ kxr, float4 *__restrict__ xph, const float vcol[NC],
                            const float th[6], float g[6], bool want_ll)
 {
     const int lane = threadIdx.x & 31;
@@ -452,7 +452,7 @@ __device__ double eval_dense(const FitParams &P, const GalCtx &gc, const DenseVi
     for (int u = lane; u < H; u += 32) {
         float sx, cx;
         sincospi_sfu(-2.0f * th[4] * (float)u * gc.invN, &sx, &cx);
-        xph[u] = make_float2(cx, sx);
+        xph[u] = make_float4(cx, sx, -sx, 0.0f);
     }
     __syncwarp();
     // (a) the model's half spectrum Mt = Tt F f(s) X(u) Y(v) into the D slots
@@ -472,7 +472,7 @@ __device__ double eval_dense(const FitParams &P, const GalCtx &gc, const DenseVi
             const float s = fmaf(fmaf(al, kx, gky), kx, cst);
             const float rs = rsqrtf(s);
             const float A = row[ot] * rs * rs * rs;
-            const float2 X = xph[u];
+            const float4 X = xph[u];
             const float Pr = X.x * Yr - X.y * Yi, Pi = X.x * Yi + X.y * Yr;
             const float mr = vi < N ? A * Pr : 0.0f, mi = vi < N ? A * Pi : 0.0f;
             row[ox] = mr;
