@@ -74,6 +74,20 @@ __device__ __forceinline__ void uniforms8(uint64_t seed, uint64_t key, uint64_t 
     }
 }
 
+// Uniform k (0..7) of the block uniforms8 draws for the same counter.
+__device__ __forceinline__ float uniform_of8(uint64_t seed, uint64_t key, uint64_t c0, uint64_t c1, uint64_t c2,
+                                             int k)
+{
+    const Philox4x64 r = philox4x64_10(c0, c1, c2, 0ull, seed, key);
+    const int j = k >> 1;
+    uint64_t w = r.w[0];
+    if (j == 1) w = r.w[1];
+    if (j == 2) w = r.w[2];
+    if (j == 3) w = r.w[3];
+    const uint32_t h = (k & 1) ? (uint32_t)w : (uint32_t)(w >> 32);
+    return ((float)(h >> 8) + 0.5f) * 5.9604644775390625e-08f;
+}
+
 // ---------------------------------------------------------------------------
 // Warp reductions.  The xor butterfly leaves the same bits in every lane
 // (each step adds the same two operands in both partner lanes), which keeps

@@ -948,6 +948,11 @@ __device__ void run_chain(const FitParams &P, const GalCtx &gc, const SmemView &
     const double thr_search = -0.22314355131420976;   // ln 0.8
     const size_t chain_row = ci0 * (size_t)S;
     const size_t plane = (size_t)P.n_gal * C * S;
+    // the uniforms of four transitions at a time: lane 8 j + k holds uniform k of
+    // transition u_base + j (the lanes run four Philox blocks side by side, in the
+    // time of one; a transition gathers its eight with shuffles)
+    float u_cache = 0.f;
+    int u_base = -4;
 
     if (W + S == 0) mode = -1;
     while (mode >= 0) {
@@ -958,7 +963,12 @@ __device__ void run_chain(const FitParams &P, const GalCtx &gc, const SmemView &
             uniforms8(P.seed, key, (uint64_t)s_idx, 1ull, (uint64_t)s_t, u);
             eps_use = s_eps;
         } else if (mode == MODE_STEP) {
-            uniforms8(P.seed, key, (uint64_t)it, 0ull, 0ull, u);
+            if (it - u_base >= 4) {   // transitions run in order, each once
+                u_base = it;
+                u_cache = uniform_of8(P.seed, key, (uint64_t)(it + (lane >> 3)), 0ull, 0ull, lane & 7);
+            }
+#pragma unroll
+            for (int q = 0; q < 8; ++q) u[q] = __shfl_sync(BS_FULL_MASK, u_cache, 8 * (it - u_base) + q);
             eps_use = eps;
             if (P.random_steps) {
                 // L_i = 1 + floor(u7 L), in integers: u7 = (2j + 1) 2^-25
