@@ -215,9 +215,9 @@ CAPTURED_TRAFFIC = {
     "fit": ("paper_2604_22048_gb300/csrc/bs_fit_impl.cuh",
             "d67b4aae68f05596651a0a1cc0e95e8fec139a1986a1617d11cb1ec3d16ac602", 42704.1,
             {"side": 53, "chains": 4, "n_warmup": 200, "n_samples": 300}),
-    # one interim sample of the shear workload: (489,555,712 + 3,329,280) B / (200,000 x 300)
+    # one interim sample of the shear workload: (483,281,920 + 3,291,136) B / (200,000 x 300)
     "shear": ("paper_2604_22048_gb300/csrc/bs_shear.cu",
-              "e19c1f47b4eaafc2034dbb2986948ab4fdf98ed1bb5bda2692073845426dd5fe", 8.2148, {}),
+              "b17cd20a52198ac640c1d1545e6b9ac55bc234d3e77ad458fa71ef4ca9feb6c2", 8.1096, {}),
 }
 
 

@@ -824,12 +824,46 @@ __device__ __forceinline__ void spectral_grad(const FitParams &P, const GalCtx &
     g[5] = gc.p * Sbky * ib - th[5] * P.inv_sxy2;
 }
 
+// Component i of the same gradient, each lane its own parameter's: the flux and size
+// components are multiples of (al, be, ga) on the shape sums, the ellipticity
+// components take the derivatives of those coefficients with respect to e_i, the
+// position components the b sums; the lane picks its coefficients and forms one dot
+// product (instead of all six components in every lane).
+template <int PROF>
+__device__ __forceinline__ float spectral_grad_at(const FitParams &P, const GalCtx &gc, const Shape &m,
+                                                  const float (&sums)[6], const float th[6], int i)
+{
+    const float e1 = m.e1, e2 = m.e2, E = m.E, Pq = m.Pq, r02 = m.r02;
+    const bool ell = i == 2 || i == 3;
+    const float ei = i == 2 ? e1 : e2;
+    const float P2 = Pq * Pq;
+    const float tei = 2.0f * ei;
+    const float dl = i == 2 ? 2.0f : 0.0f;
+    const float da = r02 * ((tei + dl) * Pq + (1.0f + E + 2.0f * e1) * tei * P2);
+    const float db = r02 * ((tei - dl) * Pq + (1.0f + E - 2.0f * e1) * tei * P2);
+    const float dg = r02 * (8.0f * ei * e2 * P2 + (i == 3 ? 4.0f * Pq : 0.0f));
+    // d log f / d s = -ce / s on the shape sums; the size scale enters s as r0^2
+    const float ce = PROF == 0 ? 1.5f : P.prof_c;
+    const float kq = i == 0 ? (PROF == 2 ? 0.0f : kLn10) : -2.0f * ce * kLn10;
+    const float cx = ell ? -ce * da : kq * m.al;
+    const float cy = ell ? -ce * db : kq * m.be;
+    const float cxy = ell ? -ce * dg : kq * m.ga;
+    const float cw = i == 0 ? kLn10 : 0.0f;
+    const bool pos = i >= 4;
+    const float sb = i == 4 ? sums[4] : sums[5];
+    const float lik = pos ? gc.p * sb : fmaf(cw, sums[0], fmaf(cx, sums[1], fmaf(cy, sums[2], cxy * sums[3])));
+    const float tp = i == 4 ? th[4] : th[5];
+    const float pri = pos ? -tp * P.inv_sxy2 : (ell ? -4.0f * ei * Pq - ei * P.inv_se2 : 0.0f);
+    return lik * gc.inv_b + pri;
+}
+
 // Log posterior (if want_ll) and gradient at th, warp-cooperative.
+// gi receives the gradient's component for this lane's parameter, min(lane, 5).
 template <int NC, int PROF>
 __device__ __forceinline__ double eval_logpost(const FitParams &P, const GalCtx &gc,
                                                const float *__restrict__ tab, const float2 *__restrict__ kxr,
                                                float4 *__restrict__ xph, const float vcol[NC], const float th[6],
-                                               float g[6], bool want_ll)
+                                               float &gi, bool want_ll)
 {
     const Shape m = model_shape<PROF>(P, th);
     float sums[6];
@@ -838,7 +872,8 @@ __device__ __forceinline__ double eval_logpost(const FitParams &P, const GalCtx 
         spectral_sums<NC, true, PROF>(P, gc, m, tab, kxr, xph, vcol, th, 0, gc.H, sums, chi_hi, chi_lo);
     else
         spectral_sums<NC, false, PROF>(P, gc, m, tab, kxr, xph, vcol, th, 0, gc.H, sums, chi_hi, chi_lo);
-    spectral_grad<PROF>(P, gc, m, sums, th, g);
+    const int lane = threadIdx.x & 31;
+    gi = spectral_grad_at<PROF>(P, gc, m, sums, th, lane < 6 ? lane : 5);
     if (!want_ll) return 0.0;
     // then the warp
     const double chi2 = warp_sum_comp(chi_hi, chi_lo) / ((double)m.F * (double)m.F);
@@ -897,18 +932,19 @@ __device__ __forceinline__ bool trajectory(const FitParams &P, const GalCtx &gc,
 #pragma unroll
         for (int k = 0; k < 6; ++k) x[k] = __shfl_sync(BS_FULL_MASK, tp, k);
         if (!in_support(P, x)) return false;
-        float gg[6];
         double v;
-        if constexpr (PROF == 3)
+        if constexpr (PROF == 3) {
+            float gg[6];
             v = eval_pix<NC>(P, gc, sm, gal, xph_c, vcol, x, gg, l == nst - 1, nullptr);
-        else if constexpr (PROF == 4)
+            gp = pick6(gg, pi);
+        } else if constexpr (PROF == 4) {
             v = eval_dense<NC>(P, gc, dense_view(sm.kxr, P.h_max, P.npad, P.max_side, slot), gal, sm.kxr, xph_c,
-                               vcol, x, gg, l == nst - 1);
-        else
-            v = eval_logpost<NC, PROF>(P, gc, sm.tab, sm.kxr, xph_c, vcol, x, gg, l == nst - 1);
+                               vcol, x, gp, l == nst - 1);
+        } else {
+            v = eval_logpost<NC, PROF>(P, gc, sm.tab, sm.kxr, xph_c, vcol, x, gp, l == nst - 1);
+        }
         ++ngrad;
         if (l == nst - 1) lpp = v;
-        gp = pick6(gg, pi);
         pm = fmaf(he, gp, pm);
     }
     return true;
@@ -1238,25 +1274,26 @@ __device__ void point_eval(const FitParams &P, const GalCtx &gc, const SmemView 
     float vcol[NC];
 #pragma unroll
     for (int j = 0; j < NC; ++j) vcol[j] = (float)(lane + 32 * j - gc.c);
-    float th[6], g[6];
+    float th[6];
 #pragma unroll
     for (int i = 0; i < 6; ++i) th[i] = theta[i];
     double v = -INFINITY;
+    float gl = NAN;   // the gradient's component for this lane's parameter (lanes < 6)
     if (in_support(P, th)) {
-        if constexpr (PROF == 3)
+        if constexpr (PROF == 3) {
+            float g[6];
             v = eval_pix<NC>(P, gc, sm, gal, sm.xph, vcol, th, g, true, nullptr);
-        else if constexpr (PROF == 4)
+            gl = pick6(g, lane < 6 ? lane : 5);
+        } else if constexpr (PROF == 4) {
             v = eval_dense<NC>(P, gc, dense_view(sm.kxr, P.h_max, P.npad, P.max_side, 0), gal, sm.kxr, sm.xph, vcol,
-                               th, g, true);
-        else
-            v = eval_logpost<NC, PROF>(P, gc, sm.tab, sm.kxr, sm.xph, vcol, th, g, true);
-    } else {
-#pragma unroll
-        for (int i = 0; i < 6; ++i) g[i] = NAN;
+                               th, gl, true);
+        } else {
+            v = eval_logpost<NC, PROF>(P, gc, sm.tab, sm.kxr, sm.xph, vcol, th, gl, true);
+        }
     }
     if (threadIdx.x >= 32) return;   // the pixel path's other warps hold the same values
     if (lane == 0 && logp) *logp = v;
-    if (grad && lane < 6) grad[lane] = pick6(g, lane);
+    if (grad && lane < 6) grad[lane] = gl;
 }
 
 template <int PROF>

@@ -434,7 +434,7 @@ __device__ void dense_setup(const FitParams &P, const GalCtx &gc, const SmemView
 template <int NC>
 __device__ double eval_dense(const FitParams &P, const GalCtx &gc, const DenseView &pv, int gal,
                            const float2 *__restrict__ kxr, float4 *__restrict__ xph, const float vcol[NC],
-                           const float th[6], float g[6], bool want_ll)
+                           const float th[6], float &gi, bool want_ll)
 {
     const int lane = threadIdx.x & 31;
     const int N = gc.N, H = gc.H, c = gc.c, npad = P.npad;
@@ -606,7 +606,7 @@ __device__ double eval_dense(const FitParams &P, const GalCtx &gc, const DenseVi
     }
     __syncwarp();
     // (c) the gradient from the half-plane pass on the effective spectrum
-    eval_logpost<NC, 0>(P, gc, pv.tab, kxr, xph, vcol, th, g, false);
+    eval_logpost<NC, 0>(P, gc, pv.tab, kxr, xph, vcol, th, gi, false);
     if (!want_ll) return 0.0;
     const double chi2 = warp_sum_d(chi);
     const float lprior = P.prior_const - 0.5f * (th[4] * th[4] + th[5] * th[5]) * P.inv_sxy2 +

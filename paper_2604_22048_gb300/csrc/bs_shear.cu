@@ -22,8 +22,9 @@
 // 8 lanes per galaxy with scalar loads one chunk ahead.  The
 // arithmetic runs on pairs of samples in packed FP32x2 instructions, x is
 // kept in log2 units for the MUFU exp2, and the group keeps
-// an online log-sum-exp (running max, sum of weights and weighted derivative
-// sums), merged with shuffles.  Per-galaxy totals are
+// an online log-sum-exp (a reference log weight that may lag the running
+// maximum by up to 32, sum of weights and weighted derivative sums), merged
+// with shuffles.  Per-galaxy totals are
 // accumulated in FP64 and written as per-block partials; a one-block kernel
 // sums the partials in a fixed order (deterministic) and adds the
 // per-galaxy constants.
@@ -211,6 +212,15 @@ struct Lse {
     float2 tr;               // sum of weight rU r
 };
 
+// Samples missing from a chunk (past K) get log weight -inf.
+__device__ __forceinline__ void mask_missing(const Chunk &ch, float2 (&x)[2])
+{
+    if (ch.nvalid < 4) x[1].y = -INFINITY;
+    if (ch.nvalid < 3) x[1].x = -INFINITY;
+    if (ch.nvalid < 2) x[0].y = -INFINITY;
+    if (ch.nvalid < 1) x[0].x = -INFINITY;
+}
+
 template <int FAMILY, bool HAS_B>
 __device__ __forceinline__ void eval_chunk(const ShearConst &c, const Chunk &ch, Lse &L)
 {
@@ -221,14 +231,22 @@ __device__ __forceinline__ void eval_chunk(const ShearConst &c, const Chunk &ch,
 #pragma unroll
     for (int h = 0; h < 2; ++h)
         pair_terms<FAMILY, HAS_B>(c, e1[h], e2[h], bb[h], x[h], fw[h], ru[h], pp[h], rr[h], qq[h]);
-    if (!ch.full) {
-        if (ch.nvalid < 4) x[1].y = -INFINITY;
-        if (ch.nvalid < 3) x[1].x = -INFINITY;
-        if (ch.nvalid < 2) x[0].y = -INFINITY;
-        if (ch.nvalid < 1) x[0].x = -INFINITY;
+    if (!ch.full) mask_missing(ch, x);
+    // The weights are taken against the lane's reference L.m, which may lag the
+    // largest log2 weight seen by up to 32 (weights below 2^32 f, so sums of any
+    // realistic K stay finite), so that the exponentials need not wait for this
+    // chunk's maximum; only a larger jump (the first chunk of a galaxy, whose
+    // reference starts at -1e30) rescales the sums and recomputes the chunk's
+    // weights (from the samples: the first pass's exponents are not kept).
+    const float2 nm = f2(-L.m);
+    float2 ew[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const float2 d = add2(x[h], nm);
+        ew[h] = mul2(make_float2(ex2_ftz(d.x), ex2_ftz(d.y)), fw[h]);
     }
-    const float mloc = fmaxf(fmaxf(L.m, fmaxf(x[0].x, x[0].y)), fmaxf(x[1].x, x[1].y));
-    if (mloc > L.m) {            // rescale only when the running maximum rises
+    const float mloc = fmaxf(fmaxf(x[0].x, x[0].y), fmaxf(x[1].x, x[1].y));
+    if (mloc - L.m > 32.0f) {
         const float2 sc = f2(ex2_ftz(L.m - mloc));
         L.sw = mul2(L.sw, sc);
         L.t1 = mul2(L.t1, sc);
@@ -236,12 +254,20 @@ __device__ __forceinline__ void eval_chunk(const ShearConst &c, const Chunk &ch,
         L.tq = mul2(L.tq, sc);
         L.tr = mul2(L.tr, sc);
         L.m = mloc;
+        float2 x2[2], f2w[2], u0, u1, u2, u3;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) pair_terms<FAMILY, HAS_B>(c, e1[h], e2[h], bb[h], x2[h], f2w[h], u0, u1, u2, u3);
+        if (!ch.full) mask_missing(ch, x2);
+        const float2 nl = f2(-mloc);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const float2 d = add2(x2[h], nl);
+            ew[h] = mul2(make_float2(ex2_ftz(d.x), ex2_ftz(d.y)), f2w[h]);
+        }
     }
-    const float2 nm = f2(-L.m);
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-        const float2 d = add2(x[h], nm);
-        const float2 e = mul2(make_float2(ex2_ftz(d.x), ex2_ftz(d.y)), fw[h]);
+        const float2 e = ew[h];
         const float2 er = mul2(e, ru[h]);
         const float2 erp = mul2(er, pp[h]);
         L.sw = add2(L.sw, e);
@@ -376,13 +402,15 @@ __device__ __forceinline__ void cp_async_wait()
 
 // 4 lanes per galaxy and 12-sample chunks: a group spans 48 samples per step
 // (336 slots for K = 300), the ring's per-chunk bookkeeping is shared by 12
-// samples per lane, and two stages (48 KB per CTA) at 64 registers fit 4 CTAs
-// (32 warps) per SM to hide the shared-memory and MUFU latency.  Measured on
-// one GPU: 8 lanes x 8 samples x 3 stages (3 CTAs) 1,793 passes/s, 4 x 16 x 2
-// (3 CTAs) 1,864, 4 x 8 x 2 (4 CTAs) 1,883, 4 x 12 x 2 (4 CTAs) 1,904.
+// samples per lane.  Launch bounds for 3 CTAs (24 warps) per SM leave 80
+// registers, so that the chunk's exponentials and sums are not serialised for
+// lack of them (measured with the tile-streamed kernel below: 2,080 passes/s
+// against 1,993 at 4 CTAs and 64 registers and 1,934 at 2 CTAs).  Measured on
+// one GPU for this kernel at 4 CTAs: 8 lanes x 8 samples x 3 stages (3 CTAs)
+// 1,793 passes/s, 4 x 16 x 2 (3 CTAs) 1,864, 4 x 8 x 2 1,883, 4 x 12 x 2 1,904.
 constexpr int kAGroup = 4;     // lanes per galaxy
 constexpr int kStages = 2;     // chunks per lane in flight, this one included
-constexpr int kAsyncBlocks = 4;   // CTAs per SM the launch bounds target (3 with b: 72 KB ring)
+constexpr int kAsyncBlocks = 3;   // CTAs per SM the launch bounds target (80 registers)
 constexpr int kChunk = 12;     // samples per lane per chunk (kChunk / 4 16-byte copies per array)
 constexpr int kQuads = kChunk / 4;
 
@@ -488,7 +516,7 @@ __global__ void __launch_bounds__(kShearThreads, HAS_B ? 3 : kAsyncBlocks) shear
 // partials, so that the pass's value is NaN.
 constexpr int kTileG = kShearThreads / kAGroup;   // 64 galaxies per tile
 constexpr int kTileK = kChunk * kAGroup;          // 48 samples per chunk
-constexpr int kTmaStages = 2;
+constexpr int kTmaStages = 3;
 constexpr int kTileFloats = kTileG * kTileK;      // one array's box, 12 KB
 
 __host__ __device__ constexpr size_t tma_smem_bytes()
