@@ -284,6 +284,31 @@ def test_shear_loglike_matches_oracle(cuda, family, K, with_b):
         assert np.abs(got[1:] - gr).max() <= 1e-4 * np.abs(gr).max(), (got[1:], gr)
 
 
+@pytest.mark.parametrize("K,with_b", [(300, False), (300, True), (37, False)])
+def test_shear_loglike_with_large_weight_jumps(cuda, K, with_b):
+    """Each galaxy's samples ordered by decreasing |e| at a small alpha (0.05), so that a
+    lane's log2 weights rise by far more than 32 from one chunk to the next: the kernels
+    take a chunk's weights against a reference that may lag the largest log weight by up
+    to 32, and a larger jump rescales the sums and recomputes the chunk's weights.  The
+    value and gradient must still match the oracle (tile-streamed, cp.async and register
+    paths)."""
+    rng = np.random.default_rng(31 + K)
+    n = 500
+    r = np.linspace(0.85, 0.0, K)[None, :] * rng.uniform(0.9, 1.0, (n, 1))
+    phi = rng.uniform(0.0, 2.0 * np.pi, (n, K))
+    e1 = (r * np.cos(phi)).astype(np.float32)
+    e2 = (r * np.sin(phi)).astype(np.float32)
+    b = rng.normal(0, 0.7, (n, K)).astype(np.float32) if with_b else None
+    plan = api.ShearPlan(torch.from_numpy(e1).to(cuda), torch.from_numpy(e2).to(cuda),
+                         None if b is None else torch.from_numpy(b).to(cuda), family=O.EPRIOR_BA14)
+    for (g1, g2, a) in [(0.02, -0.01, 0.05), (0.0, 0.03, 0.08)]:
+        got = plan.loglike(g1, g2, a, host=True)
+        v, gr = O.shear_loglike(e1, e2, g1, g2, a, b=b, family=O.EPRIOR_BA14)
+        assert np.isfinite(v) and np.isfinite(got).all()
+        assert abs(got[0] - v) <= 1e-5 * max(abs(v), n), (got[0], v)
+        assert np.abs(got[1:] - gr).max() <= 1e-4 * np.abs(gr).max(), (got[1:], gr)
+
+
 @pytest.mark.parametrize("family", [O.EPRIOR_BA14, O.EPRIOR_TRUNC_GAUSS])
 def test_shear_loglike_full_matches_oracle(cuda, family):
     """All properties free: value within 1e-5 relative and the 8 derivatives
