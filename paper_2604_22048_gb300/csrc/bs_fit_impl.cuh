@@ -950,6 +950,24 @@ __device__ __forceinline__ bool trajectory(const FitParams &P, const GalCtx &gc,
     return true;
 }
 
+// The state of a chain that changes only between trajectories, in shared memory (one
+// slot per warp of the CTA: the pixel path's four warps of a chain keep a copy each),
+// so that it holds no registers while the trajectory's evaluations run: the warp's
+// scalars (step size, dual-averaging and window state, search and transition
+// counters, log posterior, the trajectory's start energy and accept uniform) and each
+// lane's parameter position, gradient and window moments.
+struct ChainScalars {
+    double lp, H0;
+    uint64_t key;
+    float eps, da_mu, da_hbar, da_lebar, s_eps, asum, lu6;
+    int da_m, wn, wi, s_idx, s_t, s_dir, it, ndiv, mode, u_base;
+};
+struct ChainLanes {
+    float th[32], thl[32], g[32], wmean[32], wm2[32];
+};
+__shared__ ChainScalars s_chain_scal[kMaxChains];
+__shared__ ChainLanes s_chain_lanes[kMaxChains];
+
 // Chain `chain` of galaxy gal, run by the warp of the CTA's `slot`.
 template <int NC, int PROF>
 __device__ void run_chain(const FitParams &P, const GalCtx &gc, const SmemView &sm, int gal,
@@ -961,26 +979,36 @@ __device__ void run_chain(const FitParams &P, const GalCtx &gc, const SmemView &
     // the pixel path's groups of four warps run one chain each: their first warp writes
     const bool wr = PROF != 3 || (threadIdx.x & 127) < 32;
     const int C = P.n_chains, W = P.n_warmup, S = P.n_samples, L = P.n_leapfrog;
+    ChainScalars &cs = s_chain_scal[threadIdx.x >> 5];
+    ChainLanes &cl = s_chain_lanes[threadIdx.x >> 5];
     const uint64_t gid = P.gal_id ? P.gal_id[gal] : (uint64_t)gal;
-    const uint64_t key = gid * (uint64_t)C + (uint64_t)chain;
+    cs.key = gid * (uint64_t)C + (uint64_t)chain;
 
     const size_t ci0 = (size_t)gal * C + chain;
     // this lane's parameter: position (hi, lo), gradient, inverse metric
-    float th = P.init[ci0 * 6 + pi], thl = 0.f, g = 0.f;
+    cl.th[lane] = P.init[ci0 * 6 + pi];
+    cl.thl[lane] = 0.f;
+    cl.g[lane] = 0.f;
     float im = P.init_im ? P.init_im[ci0 * 6 + pi] : 1.f;
-    float wmean = 0.f, wm2 = 0.f;
-    double lp = -INFINITY;
-    float eps = P.init_step ? P.init_step[ci0] : 1.0f;
-    float da_mu = 0.f, da_hbar = 0.f, da_lebar = 0.f;
-    int da_m = 0;
-    int wn = 0, wi = 0;
-    int s_idx = 0, s_t = 0, s_dir = 0;
-    float s_eps = 1.0f;
-    int it = 0;
-    float asum = 0.f;
-    int ndiv = 0;
+    cl.wmean[lane] = 0.f;
+    cl.wm2[lane] = 0.f;
+    cs.lp = -INFINITY;
+    cs.eps = P.init_step ? P.init_step[ci0] : 1.0f;
+    cs.da_mu = 0.f;
+    cs.da_hbar = 0.f;
+    cs.da_lebar = 0.f;
+    cs.da_m = 0;
+    cs.wn = 0;
+    cs.wi = 0;
+    cs.s_idx = 0;
+    cs.s_t = 0;
+    cs.s_dir = 0;
+    cs.s_eps = 1.0f;
+    cs.it = 0;
+    cs.asum = 0.f;
+    cs.ndiv = 0;
     int ngrad = 0;
-    int mode = MODE_INIT;
+    cs.mode = MODE_INIT;
     const double thr_search = -0.22314355131420976;   // ln 0.8
     const size_t chain_row = ci0 * (size_t)S;
     const size_t plane = (size_t)P.n_gal * C * S;
@@ -988,36 +1016,37 @@ __device__ void run_chain(const FitParams &P, const GalCtx &gc, const SmemView &
     // transition u_base + j (the lanes run four Philox blocks side by side, in the
     // time of one; a transition gathers its eight with shuffles)
     float u_cache = 0.f;
-    int u_base = -4;
+    cs.u_base = -4;
 
-    if (W + S == 0) mode = -1;
-    while (mode >= 0) {
+    if (W + S == 0) cs.mode = -1;
+    while (cs.mode >= 0) {
         float u[8];
         float eps_use = 0.f;
         int nst = 1;
-        if (mode == MODE_SEARCH) {
-            uniforms8(P.seed, key, (uint64_t)s_idx, 1ull, (uint64_t)s_t, u);
-            eps_use = s_eps;
-        } else if (mode == MODE_STEP) {
-            if (it - u_base >= 4) {   // transitions run in order, each once
-                u_base = it;
-                u_cache = uniform_of8(P.seed, key, (uint64_t)(it + (lane >> 3)), 0ull, 0ull, lane & 7);
+        if (cs.mode == MODE_SEARCH) {
+            uniforms8(P.seed, cs.key, (uint64_t)cs.s_idx, 1ull, (uint64_t)cs.s_t, u);
+            eps_use = cs.s_eps;
+        } else if (cs.mode == MODE_STEP) {
+            if (cs.it - cs.u_base >= 4) {   // transitions run in order, each once
+                cs.u_base = cs.it;
+                u_cache = uniform_of8(P.seed, cs.key, (uint64_t)(cs.it + (lane >> 3)), 0ull, 0ull, lane & 7);
             }
 #pragma unroll
-            for (int q = 0; q < 8; ++q) u[q] = __shfl_sync(BS_FULL_MASK, u_cache, 8 * (it - u_base) + q);
-            eps_use = eps;
+            for (int q = 0; q < 8; ++q) u[q] = __shfl_sync(BS_FULL_MASK, u_cache, 8 * (cs.it - cs.u_base) + q);
+            eps_use = cs.eps;
+            cs.lu6 = logf(u[6]);
             if (P.random_steps) {
                 // L_i = 1 + floor(u7 L), in integers: u7 = (2j + 1) 2^-25
                 const unsigned twoj1 = (unsigned)(u[7] * 33554432.0f);
                 nst = 1 + (int)(((unsigned long long)twoj1 * (unsigned)L) >> 25);
             } else {
                 nst = L;
-                eps_use = eps * (1.0f + P.jitter * (2.0f * u[7] - 1.0f));
+                eps_use = cs.eps * (1.0f + P.jitter * (2.0f * u[7] - 1.0f));
             }
         }
         // momentum of this lane's parameter: Box-Muller on the pair (u_2j, u_2j+1)
         float pm = 0.f;
-        if (mode != MODE_INIT) {
+        if (cs.mode != MODE_INIT) {
             const int j = pi >> 1;
             const float ua = j == 0 ? u[0] : (j == 1 ? u[2] : u[4]);
             const float ub = j == 0 ? u[1] : (j == 1 ? u[3] : u[5]);
@@ -1026,119 +1055,119 @@ __device__ void run_chain(const FitParams &P, const GalCtx &gc, const SmemView &
             sincospif(2.0f * ub, &sn, &cs);
             pm = ((pi & 1) ? r * sn : r * cs) / sqrtf(im);
         }
-        const double H0 = -lp + kinetic(pm, im, own);
-        float tp = th, tpl = thl, gp = g;
-        double lpp = lp;
+        cs.H0 = -cs.lp + kinetic(pm, im, own);
+        float tp = cl.th[lane], tpl = cl.thl[lane], gp = cl.g[lane];
+        double lpp = cs.lp;
         bool ok = trajectory<NC, PROF>(P, gc, sm, gal, slot, eps_use, nst, im, tp, tpl, gp, pm, lpp, ngrad);
-        if (mode == MODE_INIT) {
-            th = tp;
-            thl = tpl;
-            g = gp;
-            lp = ok ? lpp : -INFINITY;
-            if (!isfinite(lp) && wr && lane == 0 && P.status) P.status[gal] = 1;
+        if (cs.mode == MODE_INIT) {
+            cl.th[lane] = tp;
+            cl.thl[lane] = tpl;
+            cl.g[lane] = gp;
+            cs.lp = ok ? lpp : -INFINITY;
+            if (!isfinite(cs.lp) && wr && lane == 0 && P.status) P.status[gal] = 1;
             if (P.init_step) {
                 // resume with the given step size: no search, dual averaging from it
-                da_mu = logf(10.0f * eps);
-                mode = MODE_STEP;
+                cs.da_mu = logf(10.0f * cs.eps);
+                cs.mode = MODE_STEP;
             } else {
-                mode = MODE_SEARCH;
-                s_idx = 0;
-                s_t = 0;
-                s_eps = 1.0f;
+                cs.mode = MODE_SEARCH;
+                cs.s_idx = 0;
+                cs.s_t = 0;
+                cs.s_eps = 1.0f;
             }
             continue;
         }
         double dH = INFINITY;
         if (ok) {
-            dH = (-lpp + kinetic(pm, im, own)) - H0;
+            dH = (-lpp + kinetic(pm, im, own)) - cs.H0;
             if (!isfinite(dH) || dH > 1000.0) ok = false;
         }
-        if (mode == MODE_SEARCH) {
+        if (cs.mode == MODE_SEARCH) {
             const double la = ok ? -dH : -INFINITY;
             const bool good = la > thr_search;
             bool done = false;
-            if (s_t == 0)
-                s_dir = good ? 1 : -1;
-            else if ((s_dir > 0 && !good) || (s_dir < 0 && good))
+            if (cs.s_t == 0)
+                cs.s_dir = good ? 1 : -1;
+            else if ((cs.s_dir > 0 && !good) || (cs.s_dir < 0 && good))
                 done = true;
-            if (s_t == 60) done = true;
+            if (cs.s_t == 60) done = true;
             if (!done) {
-                ++s_t;
-                s_eps = s_dir > 0 ? 2.0f * s_eps : 0.5f * s_eps;
+                ++cs.s_t;
+                cs.s_eps = cs.s_dir > 0 ? 2.0f * cs.s_eps : 0.5f * cs.s_eps;
                 continue;
             }
-            eps = s_eps;
-            da_mu = logf(10.0f * eps);
-            da_hbar = 0.f;
-            da_lebar = 0.f;
-            da_m = 0;
-            mode = MODE_STEP;
-            if (it >= W + S) mode = -1;
+            cs.eps = cs.s_eps;
+            cs.da_mu = logf(10.0f * cs.eps);
+            cs.da_hbar = 0.f;
+            cs.da_lebar = 0.f;
+            cs.da_m = 0;
+            cs.mode = MODE_STEP;
+            if (cs.it >= W + S) cs.mode = -1;
             continue;
         }
         // ---- transition at iteration `it`
         const float a = ok ? (dH < 0.0 ? 1.0f : expf((float)-dH)) : 0.0f;
-        const bool acc = ok && ((double)logf(u[6]) < -dH);
+        const bool acc = ok && ((double)cs.lu6 < -dH);
         if (acc) {
-            th = tp;
-            thl = tpl;
-            g = gp;
-            lp = lpp;
+            cl.th[lane] = tp;
+            cl.thl[lane] = tpl;
+            cl.g[lane] = gp;
+            cs.lp = lpp;
         }
-        if (it < W) {
+        if (cs.it < W) {
             if (wr && lane == 7) {
-                const size_t wi0 = ci0 * (size_t)W + it;
+                const size_t wi0 = ci0 * (size_t)W + cs.it;
                 if (P.warm_accepted) P.warm_accepted[wi0] = acc ? 1 : 0;
                 if (P.warm_stat) P.warm_stat[wi0] = a;
-                if (P.warm_step) P.warm_step[wi0] = eps;
+                if (P.warm_step) P.warm_step[wi0] = cs.eps;
             }
             // dual averaging
-            da_m += 1;
-            const float m = (float)da_m;
+            cs.da_m += 1;
+            const float m = (float)cs.da_m;
             const float eta = 1.0f / (m + 10.0f);
-            da_hbar = (1.0f - eta) * da_hbar + eta * (P.target_accept - a);
-            const float le = da_mu - sqrtf(m) * 20.0f * da_hbar;
+            cs.da_hbar = (1.0f - eta) * cs.da_hbar + eta * (P.target_accept - a);
+            const float le = cs.da_mu - sqrtf(m) * 20.0f * cs.da_hbar;
             const float xe = powf(m, -0.75f);
-            da_lebar = xe * le + (1.0f - xe) * da_lebar;
-            eps = expf(le);
-            if (wi < P.n_windows && it >= P.win_start[wi] && it < P.win_end[wi]) {
-                ++wn;
-                const float x = th + thl;
-                const float d = x - wmean;
-                wmean = fmaf(d, 1.0f / (float)wn, wmean);
-                wm2 = fmaf(d, x - wmean, wm2);
+            cs.da_lebar = xe * le + (1.0f - xe) * cs.da_lebar;
+            cs.eps = expf(le);
+            if (cs.wi < P.n_windows && cs.it >= P.win_start[cs.wi] && cs.it < P.win_end[cs.wi]) {
+                ++cs.wn;
+                const float x = cl.th[lane] + cl.thl[lane];
+                const float d = x - cl.wmean[lane];
+                cl.wmean[lane] = fmaf(d, 1.0f / (float)cs.wn, cl.wmean[lane]);
+                cl.wm2[lane] = fmaf(d, x - cl.wmean[lane], cl.wm2[lane]);
             }
-            if (wi < P.n_windows && it == P.win_end[wi] - 1) {
-                const float n = (float)wn;
-                const float var = wm2 / (n - 1.0f);
+            if (cs.wi < P.n_windows && cs.it == P.win_end[cs.wi] - 1) {
+                const float n = (float)cs.wn;
+                const float var = cl.wm2[lane] / (n - 1.0f);
                 im = (n / (n + 5.0f)) * var + 1e-3f * (5.0f / (n + 5.0f));
-                wmean = 0.f;
-                wm2 = 0.f;
-                wn = 0;
-                mode = MODE_SEARCH;
-                s_idx = wi + 1;
-                s_t = 0;
-                s_eps = eps;
-                ++wi;
+                cl.wmean[lane] = 0.f;
+                cl.wm2[lane] = 0.f;
+                cs.wn = 0;
+                cs.mode = MODE_SEARCH;
+                cs.s_idx = cs.wi + 1;
+                cs.s_t = 0;
+                cs.s_eps = cs.eps;
+                ++cs.wi;
             }
-            if (it == W - 1) eps = expf(da_lebar);
+            if (cs.it == W - 1) cs.eps = expf(cs.da_lebar);
         } else {
-            const int s = it - W;
-            asum += a;
-            ndiv += ok ? 0 : 1;
+            const int s = cs.it - W;
+            cs.asum += a;
+            cs.ndiv += ok ? 0 : 1;
             if (wr) {
-                if (own) P.samples[(size_t)pi * plane + chain_row + s] = th + thl;
-                if (lane == 6 && P.logp) P.logp[chain_row + s] = (float)lp;
+                if (own) P.samples[(size_t)pi * plane + chain_row + s] = cl.th[lane] + cl.thl[lane];
+                if (lane == 6 && P.logp) P.logp[chain_row + s] = (float)cs.lp;
                 if (lane == 7 && P.accepted) P.accepted[chain_row + s] = acc ? 1 : 0;
             }
         }
-        ++it;
-        if (it >= W + S && mode == MODE_STEP) mode = -1;
+        ++cs.it;
+        if (cs.it >= W + S && cs.mode == MODE_STEP) cs.mode = -1;
     }
     if (wr && lane == 0) {
-        if (P.accept_rate) P.accept_rate[ci0] = S > 0 ? asum / (float)S : 0.f;
-        if (P.step_size) P.step_size[ci0] = eps;
-        if (P.n_div) P.n_div[ci0] = ndiv;
+        if (P.accept_rate) P.accept_rate[ci0] = S > 0 ? cs.asum / (float)S : 0.f;
+        if (P.step_size) P.step_size[ci0] = cs.eps;
+        if (P.n_div) P.n_div[ci0] = cs.ndiv;
         if (P.n_grad) P.n_grad[ci0] = ngrad;
     }
     if (wr && P.inv_mass && own) P.inv_mass[ci0 * 6 + pi] = im;
