@@ -969,7 +969,9 @@ __device__ __forceinline__ bool trajectory(const FitParams &P, const GalCtx &gc,
 // so that it holds no registers while the trajectory's evaluations run: the warp's
 // scalars (step size, dual-averaging and window state, search and transition
 // counters, log posterior, the trajectory's start energy and accept uniform) and each
-// lane's parameter position, gradient and window moments.
+// parameter's position, gradient and window moments, written by the parameter's lane
+// (lanes 6.. read parameter 5's slot; their copies of the chain's per-parameter values
+// are never used: only lanes 0-5 feed the gathers, the energies and the outputs).
 struct ChainScalars {
     double lp, H0;
     uint64_t key;
@@ -977,7 +979,7 @@ struct ChainScalars {
     int da_m, wn, wi, s_idx, s_t, s_dir, it, ndiv, mode, u_base;
 };
 struct ChainLanes {
-    float th[32], thl[32], g[32], wmean[32], wm2[32];
+    float th[8], thl[8], g[8], wmean[8], wm2[8];
 };
 __shared__ ChainScalars s_chain_scal[kMaxChains];
 __shared__ ChainLanes s_chain_lanes[kMaxChains];
@@ -1000,12 +1002,12 @@ __device__ void run_chain(const FitParams &P, const GalCtx &gc, const SmemView &
 
     const size_t ci0 = (size_t)gal * C + chain;
     // this lane's parameter: position (hi, lo), gradient, inverse metric
-    cl.th[lane] = P.init[ci0 * 6 + pi];
-    cl.thl[lane] = 0.f;
-    cl.g[lane] = 0.f;
+    if (own) cl.th[pi] = P.init[ci0 * 6 + pi];
+    if (own) cl.thl[pi] = 0.f;
+    if (own) cl.g[pi] = 0.f;
     float im = P.init_im ? P.init_im[ci0 * 6 + pi] : 1.f;
-    cl.wmean[lane] = 0.f;
-    cl.wm2[lane] = 0.f;
+    if (own) cl.wmean[pi] = 0.f;
+    if (own) cl.wm2[pi] = 0.f;
     cs.lp = -INFINITY;
     cs.eps = P.init_step ? P.init_step[ci0] : 1.0f;
     cs.da_mu = 0.f;
@@ -1070,13 +1072,13 @@ __device__ void run_chain(const FitParams &P, const GalCtx &gc, const SmemView &
             pm = ((pi & 1) ? r * sn : r * cs) / sqrtf(im);
         }
         cs.H0 = -cs.lp + kinetic(pm, im, own);
-        float tp = cl.th[lane], tpl = cl.thl[lane], gp = cl.g[lane];
+        float tp = cl.th[pi], tpl = cl.thl[pi], gp = cl.g[pi];
         double lpp = cs.lp;
         bool ok = trajectory<NC, PROF>(P, gc, sm, gal, slot, eps_use, nst, im, tp, tpl, gp, pm, lpp, ngrad);
         if (cs.mode == MODE_INIT) {
-            cl.th[lane] = tp;
-            cl.thl[lane] = tpl;
-            cl.g[lane] = gp;
+            if (own) cl.th[pi] = tp;
+            if (own) cl.thl[pi] = tpl;
+            if (own) cl.g[pi] = gp;
             cs.lp = ok ? lpp : -INFINITY;
             if (!isfinite(cs.lp) && wr && lane == 0 && P.status) P.status[gal] = 1;
             if (P.init_step) {
@@ -1123,9 +1125,9 @@ __device__ void run_chain(const FitParams &P, const GalCtx &gc, const SmemView &
         const float a = ok ? (dH < 0.0 ? 1.0f : expf((float)-dH)) : 0.0f;
         const bool acc = ok && ((double)cs.lu6 < -dH);
         if (acc) {
-            cl.th[lane] = tp;
-            cl.thl[lane] = tpl;
-            cl.g[lane] = gp;
+            if (own) cl.th[pi] = tp;
+            if (own) cl.thl[pi] = tpl;
+            if (own) cl.g[pi] = gp;
             cs.lp = lpp;
         }
         if (cs.it < W) {
@@ -1146,17 +1148,17 @@ __device__ void run_chain(const FitParams &P, const GalCtx &gc, const SmemView &
             cs.eps = expf(le);
             if (cs.wi < P.n_windows && cs.it >= P.win_start[cs.wi] && cs.it < P.win_end[cs.wi]) {
                 ++cs.wn;
-                const float x = cl.th[lane] + cl.thl[lane];
-                const float d = x - cl.wmean[lane];
-                cl.wmean[lane] = fmaf(d, 1.0f / (float)cs.wn, cl.wmean[lane]);
-                cl.wm2[lane] = fmaf(d, x - cl.wmean[lane], cl.wm2[lane]);
+                const float x = cl.th[pi] + cl.thl[pi];
+                const float d = x - cl.wmean[pi];
+                if (own) cl.wmean[pi] = fmaf(d, 1.0f / (float)cs.wn, cl.wmean[pi]);
+                if (own) cl.wm2[pi] = fmaf(d, x - cl.wmean[pi], cl.wm2[pi]);
             }
             if (cs.wi < P.n_windows && cs.it == P.win_end[cs.wi] - 1) {
                 const float n = (float)cs.wn;
-                const float var = cl.wm2[lane] / (n - 1.0f);
+                const float var = cl.wm2[pi] / (n - 1.0f);
                 im = (n / (n + 5.0f)) * var + 1e-3f * (5.0f / (n + 5.0f));
-                cl.wmean[lane] = 0.f;
-                cl.wm2[lane] = 0.f;
+                if (own) cl.wmean[pi] = 0.f;
+                if (own) cl.wm2[pi] = 0.f;
                 cs.wn = 0;
                 cs.mode = MODE_SEARCH;
                 cs.s_idx = cs.wi + 1;
@@ -1170,7 +1172,7 @@ __device__ void run_chain(const FitParams &P, const GalCtx &gc, const SmemView &
             cs.asum += a;
             cs.ndiv += ok ? 0 : 1;
             if (wr) {
-                if (own) P.samples[(size_t)pi * plane + chain_row + s] = cl.th[lane] + cl.thl[lane];
+                if (own) P.samples[(size_t)pi * plane + chain_row + s] = cl.th[pi] + cl.thl[pi];
                 if (lane == 6 && P.logp) P.logp[chain_row + s] = (float)cs.lp;
                 if (lane == 7 && P.accepted) P.accepted[chain_row + s] = acc ? 1 : 0;
             }
