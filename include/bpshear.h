@@ -157,11 +157,12 @@ typedef struct {
     const float *init_inv_mass;   /* device [n_gal][n_chains][6] or NULL
                                      (= identity metric) */
     int32_t registers;            /* register cap of the fit kernel: 128, 96
-                                     (up to 4 chains) or 80; 0 = 128.  128 and
-                                     96 give bit-identical chains; the code the
-                                     compiler makes for 80 rounds some
-                                     operations differently, so its chains are
-                                     equally valid draws but not the same. */
+                                     (up to 4 chains) or 80; 0 = 128.  The
+                                     library is built without implicit
+                                     multiply-add contraction, so all three
+                                     round every operation alike and give the
+                                     same chains bit for bit: the cap changes
+                                     only the speed. */
     /* Pixel-likelihood extensions of Appendix C (zero-initialised: one
      * exposure, white noise, the likelihood of Eq. likelihood-pixels). */
     int32_t n_exposures;          /* J, 0 or 1..BS_MAX_EXPOSURES: exposures of
@@ -322,14 +323,13 @@ bs_status bs_fit_galaxies(const bs_fit_args *args, const bs_fit_out *out,
  *                     are issued one after another;
  *   BS_PLAN_AUTOTUNE: per class, the kernel's register cap (128: 4 CTAs =
  *                     16 warps of 4-chain galaxies per SM; 96: 5 CTAs, for
- *                     up to 4 chains; the smaller cap spills a little; as
- *                     far as shared memory allows) is chosen by timing them
- *                     on the class's first galaxies at creation (their
- *                     outputs are overwritten by every later launch); the
- *                     results are the same whichever is chosen.  The
- *                     80-register instance (6 CTAs) is timed too and
- *                     reported, but not chosen: its chains differ in
- *                     rounding (see bs_fit_args.registers).
+ *                     up to 4 chains; 80: 6 CTAs; the smaller caps spill a
+ *                     little; as far as shared memory allows) and layout (all
+ *                     or half of a galaxy's chains per CTA) are chosen by
+ *                     timing them on the class's first galaxies at creation
+ *                     (their outputs are overwritten by every later launch);
+ *                     the results are the same whichever is chosen (see
+ *                     bs_fit_args.registers).
  *   side_host: host copy of args->side (n_gal).
  *   workspace: bs_fit_plan_workspace_bytes(args) bytes of device memory
  *              (work lists and per-class counters), owned by the caller.

@@ -105,8 +105,8 @@ class FitPlan:
                  want=("logp", "accept_rate", "step_size", "inv_mass", "n_div", "status", "n_grad")):
         """init_step_size [n_gal, C] / init_inv_mass [n_gal, C, 6] (optional):
         resume adapted chains (no initial step-size search).  registers: the
-        fit kernel's register cap (128, 96, 80; 0 = 128): 128 and 96 give the
-        same chains bit for bit, 80 rounds some operations differently.
+        fit kernel's register cap (128, 96, 80; 0 = 128): all three give the
+        same chains bit for bit (the cap changes only the speed).
         n_exposures J: each galaxy's J stamps lie one after another from its
         offset, psf has n_gal * J entries (or one), noise_sigma n_gal * J;
         noise_corr (float32, layout of data): per-exposure noise correlation

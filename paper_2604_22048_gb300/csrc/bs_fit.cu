@@ -20,9 +20,8 @@ using FitKernel = void (*)(const FitParams);
     }
 
 // Register budget of a launch (128, 96 or 80; 96 only for blocks of up to 4
-// chains); 0 takes 128.  Only the caller's explicit choice selects another
-// instance: the 80-register one rounds some operations differently, so its
-// chains are valid draws that differ from the others'.
+// chains); 0 takes 128.  The library is built without implicit multiply-add
+// contraction, so the three instances round alike and give the same chains.
 FitKernel fit_kernel_for(int max_side, int regs, int n_chains)
 {
     if (regs != 128 && regs != 96 && regs != 80) regs = 128;
