@@ -607,9 +607,9 @@ __device__ __forceinline__ void row_terms(Sums<NCT> &S, float2 &chi, const SlotC
     }
 }
 
-// Half-plane pass, two rows per iteration (four with one pair of slots per row); each
-// row reads its (kx, kx^2) from the galaxy's row table and X(u) from the warp's phase
-// table.
+// Half-plane pass, two rows per iteration (four with at most one pair of slots per
+// row); each row reads its (kx, kx^2) from the galaxy's row table and X(u) from the
+// warp's phase table.
 template <int NCT, bool LL, int PROF>
 __device__ __forceinline__ void half_plane(Sums<NCT> &S, const SlotConst<NCT> &K,
                                            const float *__restrict__ tab, const float2 *__restrict__ kxr,
@@ -618,9 +618,10 @@ __device__ __forceinline__ void half_plane(Sums<NCT> &S, const SlotConst<NCT> &K
     constexpr int ROWF = 96 * NCT;
     const float *row = tab;
     int u = 0;
-    if constexpr (NCT == 2) {
-        // one pair of column slots per row: four rows in flight (the 10^4-galaxy 53 px
-        // launch 244.6 -> 237.2 ms)
+    if constexpr (NCT <= 2) {
+        // one pair of column slots (or one slot) per row: four rows in flight (10^4
+        // galaxies at 53 px 244.6 -> 237.2 ms, at 25 px 138.2 -> 116.7 ms; with two
+        // pairs per row, 65-95 px, it was slower: 477.6 -> 484.6 ms at 75 px)
         for (; u + 3 < H; u += 4) {
             const float4 k01 = *reinterpret_cast<const float4 *>(kxr + u);
             const float4 k23 = *reinterpret_cast<const float4 *>(kxr + u + 2);
