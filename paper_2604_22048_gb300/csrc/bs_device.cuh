@@ -117,15 +117,6 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
     e = (a - ap) + (b - bp);
 }
 
-// Compensated (hi, lo) pair accumulate.
-__device__ __forceinline__ void comp_add(float &hi, float &lo, float x)
-{
-    float s, e;
-    two_sum(hi, x, s, e);
-    hi = s;
-    lo += e;
-}
-
 // Warp-wide sum of compensated pairs, finished in double on return.
 __device__ __forceinline__ double warp_sum_comp(float hi, float lo)
 {

@@ -439,30 +439,6 @@ __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-// a - b on both halves in one packed instruction (no packed negation exists
-// to fold into an add).
-__device__ __forceinline__ float2 sub2(float2 a, float2 b)
-{
-    float2 d;
-    asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
-        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
-        "sub.rn.f32x2 rd, ra, rb;\n\t"
-        "mov.b64 {%0, %1}, rd;\n\t}"
-        : "=f"(d.x), "=f"(d.y)
-        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
-    return d;
-}
-
-// Compensated accumulation of both halves (Knuth's TwoSum, packed).
-__device__ __forceinline__ void comp_add2(float2 &hi, float2 &lo, float2 x)
-{
-    const float2 s = add2(hi, x);
-    const float2 bp = sub2(s, hi);
-    const float2 ap = sub2(s, bp);
-    const float2 e = add2(sub2(hi, ap), sub2(x, bp));
-    hi = s;
-    lo = add2(lo, e);
-}
 
 // Per-lane partial sums of one evaluation: slot pairs packed, odd slot scalar.
 template <int NCT>
