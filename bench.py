@@ -211,9 +211,9 @@ def flops_per_eval(N):
 # to that file the traffic is reported as null until the next capture.
 CAPTURED_TRAFFIC = {
     # one galaxy of the plain workload (53x53, 4 chains x (200 + 300) draws), from a one-pass
-    # capture of the full 10,000-galaxy launch: (133,801,472 + 292,942,080) B / 10,000
+    # capture of the full 10,000-galaxy launch: (133,567,488 + 292,933,632) B / 10,000
     "fit": ("paper_2604_22048_gb300/csrc/bs_fit_impl.cuh",
-            "364a8078d800303660d7c0cbbc608546ffeafdcf45d3e433ece9cdc8756728b4", 42674.4,
+            "e9f67fed04fb016f403a11a2e5d9ea4f97cb15a9d1a18d7f51d4a859bae988e2", 42650.1,
             {"side": 53, "chains": 4, "n_warmup": 200, "n_samples": 300}),
     # one interim sample of the shear workload: (483,281,920 + 3,291,136) B / (200,000 x 300)
     "shear": ("paper_2604_22048_gb300/csrc/bs_shear.cu",
