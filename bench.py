@@ -215,9 +215,9 @@ CAPTURED_TRAFFIC = {
     "fit": ("paper_2604_22048_gb300/csrc/bs_fit_impl.cuh",
             "e9f67fed04fb016f403a11a2e5d9ea4f97cb15a9d1a18d7f51d4a859bae988e2", 42650.1,
             {"side": 53, "chains": 4, "n_warmup": 200, "n_samples": 300}),
-    # one interim sample of the shear workload: (483,281,920 + 3,291,136) B / (200,000 x 300)
+    # one interim sample of the shear workload: (483,096,576 + 3,097,088) B / (200,000 x 300)
     "shear": ("paper_2604_22048_gb300/csrc/bs_shear.cu",
-              "b17cd20a52198ac640c1d1545e6b9ac55bc234d3e77ad458fa71ef4ca9feb6c2", 8.1096, {}),
+              "5e102b705e1ea3da5d060dc3ac880c763355d9247f1fc83031b22cb8fe2683d7", 8.1032, {}),
 }
 
 

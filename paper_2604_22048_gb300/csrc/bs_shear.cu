@@ -546,38 +546,43 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_
     }
 }
 
-template <int FAMILY>
-__global__ void __launch_bounds__(kShearThreads, kAsyncBlocks)
-    shear_kernel_tma(const ShearLaunch s, const __grid_constant__ CUtensorMap m1, const __grid_constant__ CUtensorMap m2)
-{
-    constexpr int kWarps = kShearThreads / 32;
-    extern __shared__ __align__(128) unsigned char tma_raw[];
-    __shared__ __align__(8) uint64_t full[kTmaStages], empty[kTmaStages];
-    float *ring = reinterpret_cast<float *>(tma_raw + ((128u - (smem_u32(tma_raw) & 127u)) & 127u));
-    const int tid = threadIdx.x;
-    const int lane = tid & 31;
-    const int sub = tid & (kAGroup - 1), gl = tid / kAGroup;
-    const unsigned gmask = ((1u << kAGroup) - 1u) << (lane & ~(kAGroup - 1));
-    const ShearConst c = shear_const(s);
-    const int K = s.K;
-    const int cpg = (K + kTileK - 1) / kTileK;                       // chunks per tile
-    const long long n_tiles = (s.n_gal + kTileG - 1) / kTileG;
-    const int my_tiles = blockIdx.x < n_tiles ? (int)((n_tiles - 1 - blockIdx.x) / gridDim.x + 1) : 0;
-    const int n_items = my_tiles * cpg;
-    if (tid == 0) {
-        for (int st = 0; st < kTmaStages; ++st) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[st])) : "memory");
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&empty[st])), "r"(kWarps)
-                         : "memory");
-        }
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncthreads();
+// The CTA's ring of kTmaStages stages, each one tile-chunk of e1 and e2, with a
+// "full" mbarrier per stage (armed by the producer with the stage's byte count) and an
+// "empty" one (one arrival per warp once the warp has read the stage).  Thread 0 is
+// the producer: it issues item i (tile blockIdx.x + t gridDim.x, chunk c) after the
+// stage's previous item has been released.  Every wait gives up after two seconds.
+struct TmaRing {
+    float *ring;
+    uint64_t *full, *empty;
+    int cpg, n_items;
     // producer state (thread 0): next item to load, its tile and chunk
     int p_item = 0, p_chunk = 0;
-    long long p_tile = blockIdx.x;
+    long long p_tile;
     bool p_ok = true;
-    auto issue = [&]() {
+
+    __device__ void init(unsigned char *raw, uint64_t *f, uint64_t *e, long long n_gal, int K)
+    {
+        constexpr int kWarps = kShearThreads / 32;
+        ring = reinterpret_cast<float *>(raw + ((128u - (smem_u32(raw) & 127u)) & 127u));
+        full = f;
+        empty = e;
+        cpg = (K + kTileK - 1) / kTileK;   // chunks per tile
+        const long long n_tiles = (n_gal + kTileG - 1) / kTileG;
+        const int my_tiles = blockIdx.x < n_tiles ? (int)((n_tiles - 1 - blockIdx.x) / gridDim.x + 1) : 0;
+        n_items = my_tiles * cpg;
+        p_tile = blockIdx.x;
+        if (threadIdx.x == 0) {
+            for (int st = 0; st < kTmaStages; ++st) {
+                asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[st])) : "memory");
+                asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&empty[st])), "r"(kWarps)
+                             : "memory");
+            }
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        __syncthreads();
+    }
+    __device__ void issue(const CUtensorMap *m1, const CUtensorMap *m2)
+    {
         if (p_item >= n_items || !p_ok) return;
         const int st = p_item % kTmaStages;
         if (p_item >= kTmaStages) {   // the stage's previous item has been read by every warp
@@ -597,73 +602,109 @@ __global__ void __launch_bounds__(kShearThreads, kAsyncBlocks)
         asm volatile(
             "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
                 "r"(d1),
-            "l"(&m1), "r"(x), "r"(y), "r"(bar)
+            "l"(m1), "r"(x), "r"(y), "r"(bar)
             : "memory");
         asm volatile(
             "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
                 "r"(d2),
-            "l"(&m2), "r"(x), "r"(y), "r"(bar)
+            "l"(m2), "r"(x), "r"(y), "r"(bar)
             : "memory");
         ++p_item;
         if (++p_chunk == cpg) {
             p_chunk = 0;
             p_tile += gridDim.x;
         }
-    };
+    }
+    // all threads: wait until item's stage has landed (false, in every lane, on a timeout)
+    __device__ bool wait_full(int item) const
+    {
+        uint64_t t0;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+        return __all_sync(BS_FULL_MASK,
+                          mbar_wait(smem_u32(&full[item % kTmaStages]), (uint32_t)((item / kTmaStages) & 1), t0));
+    }
+    // all threads of a warp, after reading item's stage
+    __device__ void release(int item) const
+    {
+        __syncwarp();
+        if ((threadIdx.x & 31) == 0)
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&empty[item % kTmaStages]))
+                         : "memory");
+    }
+    // all threads, at the end: loads still in flight land in the ring (waited for, with the limit)
+    __device__ void drain() const
+    {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint64_t t1;
+            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
+            for (int it = p_item - kTmaStages; it < p_item; ++it)
+                if (it >= 0) mbar_wait(smem_u32(&full[it % kTmaStages]), (uint32_t)((it / kTmaStages) & 1), t1);
+        }
+    }
+};
+
+// Quad h (4 consecutive samples) of this thread's part of chunk `chunk` of its
+// galaxy (4 lanes per galaxy, 12 samples each) in item's stage; false past K.
+__device__ __forceinline__ bool tma_quad(const TmaRing &R, int item, int K, int chunk, int h, Chunk &ch)
+{
+    const int tid = threadIdx.x, sub = tid & (kAGroup - 1), gl = tid / kAGroup;
+    if (chunk * kTileK + kChunk * sub + 4 * h >= K) return false;
+    const float *r1 = R.ring + (size_t)(item % kTmaStages) * 2 * kTileFloats + gl * kTileK + kChunk * sub + 4 * h;
+    ch.nvalid = 4;
+    ch.full = true;
+    ch.e1 = *reinterpret_cast<const float4 *>(r1);
+    ch.e2 = *reinterpret_cast<const float4 *>(r1 + kTileFloats);
+    ch.b = make_float4(0.f, 0.f, 0.f, 0.f);
+    return true;
+}
+
+template <int FAMILY>
+__global__ void __launch_bounds__(kShearThreads, kAsyncBlocks)
+    shear_kernel_tma(const ShearLaunch s, const __grid_constant__ CUtensorMap m1, const __grid_constant__ CUtensorMap m2)
+{
+    extern __shared__ __align__(128) unsigned char tma_raw[];
+    __shared__ __align__(8) uint64_t full[kTmaStages], empty[kTmaStages];
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int sub = tid & (kAGroup - 1), gl = tid / kAGroup;
+    const unsigned gmask = ((1u << kAGroup) - 1u) << (lane & ~(kAGroup - 1));
+    const ShearConst c = shear_const(s);
+    const int K = s.K;
+    TmaRing R;
+    R.init(tma_raw, full, empty, s.n_gal, K);
     if (tid == 0)
-        for (int t = 0; t < kTmaStages - 1; ++t) issue();
+        for (int t = 0; t < kTmaStages - 1; ++t) R.issue(&m1, &m2);
     double av = 0.0, a1 = 0.0, a2 = 0.0, aq = 0.0;
     Lse L;
     lse_reset(L);
     bool failed = false;
     int chunk = 0;
     long long tile = blockIdx.x;
-    for (int item = 0; item < n_items; ++item) {
-        if (tid == 0) issue();
-        const int st = item % kTmaStages;
-        uint64_t t0;
-        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
-        const bool ok = __all_sync(BS_FULL_MASK, mbar_wait(smem_u32(&full[st]), (uint32_t)((item / kTmaStages) & 1), t0));
-        if (!ok) {
+    for (int item = 0; item < R.n_items; ++item) {
+        if (tid == 0) R.issue(&m1, &m2);
+        if (!R.wait_full(item)) {
             failed = true;
             break;
         }
         const long long n = tile * kTileG + gl;
-        const int k0 = chunk * kTileK + kChunk * sub;
-        const float *r1 = ring + (size_t)st * 2 * kTileFloats + gl * kTileK + kChunk * sub;
-        const float *r2 = r1 + kTileFloats;
         if (n < s.n_gal) {
 #pragma unroll
             for (int h = 0; h < kQuads; ++h) {
-                if (k0 + 4 * h < K) {
-                    Chunk ch;
-                    ch.nvalid = 4;
-                    ch.full = true;
-                    ch.e1 = *reinterpret_cast<const float4 *>(r1 + 4 * h);
-                    ch.e2 = *reinterpret_cast<const float4 *>(r2 + 4 * h);
-                    ch.b = make_float4(0.f, 0.f, 0.f, 0.f);
-                    eval_chunk<FAMILY, false>(c, ch, L);
-                }
+                Chunk ch;
+                if (tma_quad(R, item, K, chunk, h, ch)) eval_chunk<FAMILY, false>(c, ch, L);
             }
         }
-        __syncwarp();
-        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&empty[st])) : "memory");
-        if (++chunk == cpg) {
+        R.release(item);
+        if (++chunk == R.cpg) {
             if (n < s.n_gal) finish_galaxy<kAGroup>(L, s.g1, s.g2, gmask, sub, s.w, n, av, a1, a2, aq);
             lse_reset(L);
             chunk = 0;
             tile += gridDim.x;
         }
     }
-    if (failed || (tid == 0 && !p_ok)) av = a1 = a2 = aq = NAN;
-    __syncthreads();
-    if (tid == 0) {
-        // loads still in flight land in the ring: wait for them (with the limit)
-        uint64_t t1;
-        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
-        for (int it = p_item - kTmaStages; it < p_item; ++it)
-            if (it >= 0) mbar_wait(smem_u32(&full[it % kTmaStages]), (uint32_t)((it / kTmaStages) & 1), t1);
-    }
+    if (failed || (tid == 0 && !R.p_ok)) av = a1 = a2 = aq = NAN;
+    R.drain();
     block_partials(s, av, a1, a2, aq);
 }
 
@@ -1073,8 +1114,109 @@ int shear_multi_grid_blocks()
     return sms * nb;
 }
 
+// Several points per pass with the samples streamed in tiles (K a multiple of 4,
+// 16-byte aligned rows, no b): the one-point tile kernel's ring and lane layout, each
+// quad of samples evaluated for every point, each point keeping its own log-sum-exp
+// state; a galaxy's 4 lanes put their FP64 totals per point in their own shared-memory
+// slot, summed over the block in a fixed order.  On a wait that gives up, the block's
+// partials are NaN.
+template <int FAMILY>
+__global__ void __launch_bounds__(kShearThreads, 2)
+    shear_kernel_tma_multi(const ShearMultiLaunch m, const __grid_constant__ CUtensorMap m1,
+                           const __grid_constant__ CUtensorMap m2)
+{
+    constexpr int NP = kMultiPoints;
+    extern __shared__ __align__(128) unsigned char tma_raw[];
+    __shared__ __align__(8) uint64_t full[kTmaStages], empty[kTmaStages];
+    __shared__ double acc[kTileG][NP][4];
+    __shared__ int s_fail;
+    const ShearLaunch &s = m.s;
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int sub = tid & (kAGroup - 1), gl = tid / kAGroup;
+    const unsigned gmask = ((1u << kAGroup) - 1u) << (lane & ~(kAGroup - 1));
+    const int K = s.K;
+    if (sub == 0)
+        for (int p = 0; p < NP; ++p)
+            for (int i = 0; i < 4; ++i) acc[gl][p][i] = 0.0;
+    if (tid == 0) s_fail = 0;
+    TmaRing R;
+    R.init(tma_raw, full, empty, s.n_gal, K);   // (its barrier also orders the resets above)
+    if (tid == 0)
+        for (int t = 0; t < kTmaStages - 1; ++t) R.issue(&m1, &m2);
+    Lse L[NP];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) lse_reset(L[p]);
+    bool failed = false;
+    int chunk = 0;
+    long long tile = blockIdx.x;
+    for (int item = 0; item < R.n_items; ++item) {
+        if (tid == 0) R.issue(&m1, &m2);
+        if (!R.wait_full(item)) {
+            failed = true;
+            break;
+        }
+        const long long n = tile * kTileG + gl;
+        if (n < s.n_gal) {
+#pragma unroll
+            for (int h = 0; h < kQuads; ++h) {
+                Chunk ch;
+                if (tma_quad(R, item, K, chunk, h, ch)) {
+#pragma unroll
+                    for (int p = 0; p < NP; ++p)
+                        if (p < m.n_points) eval_chunk<FAMILY, false>(shear_const_point(m, p), ch, L[p]);
+                }
+            }
+        }
+        R.release(item);
+        if (++chunk == R.cpg) {
+            if (n < s.n_gal) {
+#pragma unroll
+                for (int p = 0; p < NP; ++p) {
+                    if (p < m.n_points) {
+                        double av = 0.0, a1 = 0.0, a2 = 0.0, aq = 0.0;
+                        finish_galaxy<kAGroup>(L[p], m.g1[p], m.g2[p], gmask, sub, s.w, n, av, a1, a2, aq);
+                        if (sub == 0) {
+                            acc[gl][p][0] += av;
+                            acc[gl][p][1] += a1;
+                            acc[gl][p][2] += a2;
+                            acc[gl][p][3] += aq;
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int p = 0; p < NP; ++p) lse_reset(L[p]);
+            chunk = 0;
+            tile += gridDim.x;
+        }
+    }
+    if (failed || (tid == 0 && !R.p_ok)) s_fail = 1;
+    R.drain();
+    __syncthreads();
+    if (tid < NP * 4) {
+        const int p = tid >> 2, i = tid & 3;
+        double t = 0.0;
+        for (int k = 0; k < kTileG; ++k) t += acc[k][p][i];
+        m.partials[((size_t)p * gridDim.x + blockIdx.x) * 4 + i] = s_fail ? NAN : t;
+    }
+}
+
 cudaError_t launch_shear_multi(const ShearMultiLaunch &m, int grid, cudaStream_t stream)
 {
+    const ShearLaunch &s = m.s;
+    const bool vec = (s.K % 4 == 0) && ((reinterpret_cast<uintptr_t>(s.e1) & 15) == 0) &&
+                     ((reinterpret_cast<uintptr_t>(s.e2) & 15) == 0) && s.b == nullptr;
+    CUtensorMap m1, m2;
+    if (vec && make_sample_map(m1, s.e1, s.n_gal, s.K) && make_sample_map(m2, s.e2, s.n_gal, s.K)) {
+        auto k = s.family == BS_EPRIOR_BA14 ? shear_kernel_tma_multi<BS_EPRIOR_BA14>
+                                            : shear_kernel_tma_multi<BS_EPRIOR_TRUNC_GAUSS>;
+        const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)tma_smem_bytes());
+        if (e != cudaSuccess) return e;
+        k<<<grid, kShearThreads, tma_smem_bytes(), stream>>>(m, m1, m2);
+        return cudaGetLastError();
+    }
     if (m.s.family == BS_EPRIOR_BA14)
         shear_kernel_multi<BS_EPRIOR_BA14><<<grid, kShearThreads, 0, stream>>>(m);
     else
